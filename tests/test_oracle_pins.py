@@ -1,0 +1,380 @@
+"""Pins for the FP64 oracle: each check ties a part of the oracle to something
+other than itself (closed forms, library routines, brute force, theorems of the
+paper) so that a dropped term, a wrong sign or index, or a transposed operand
+fails at least one of them."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.special as sp
+from scipy.spatial.distance import cdist
+
+import ciq_inputs as ci
+from oracle import ciq, eig, kernels
+from oracle.elliptic import agm, ellipj, ellipk_mc
+from oracle.lanczos import lanczos, ritz_extremes, tridiagonal
+from oracle.msminres import msminres
+from oracle.quadrature import quad_nodes, scalar_approx
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_ints(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [int(x) for x in f.read().split("\n") if x and not x.startswith("#")]
+
+
+# ---------------------------------------------------------------- inputs ----
+def test_splitmix64_published_sequence():
+    ref = _golden_ints("splitmix64_seed1234567.txt")
+    got = ci.splitmix64(1234567, 5)
+    assert [int(v) for v in got] == ref
+    # Counter-based access equals sequential access.
+    assert int(ci.splitmix64(1234567, 2, offset=3)[1]) == ref[4]
+
+
+def test_uniform_and_normal_ranges():
+    u = ci.uniform(7, 100000)
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 5e-3
+    z = ci.normal(7, 100000)
+    assert abs(z.mean()) < 2e-2 and abs(z.std() - 1.0) < 2e-2
+    s = ci.start_vector(9, 1000)
+    assert s.min() >= -1.0 and s.max() < 1.0
+
+
+# --------------------------------------------------------------- kernels ----
+def test_sqdist_matches_scipy():
+    X = ci.points(1, 50, 5)
+    Y = ci.points(2, 30, 5)
+    np.testing.assert_allclose(kernels.sqdist(X, Y), cdist(X, Y, "sqeuclidean"), rtol=1e-13, atol=1e-15)
+
+
+def test_matern52_matches_bessel_form():
+    # Matern with nu = 5/2 in its general Bessel form (Rasmussen & Williams eq. 4.14):
+    # k(r) = s 2^{1-nu}/Gamma(nu) (sqrt(2 nu) r / l)^nu K_nu(sqrt(2 nu) r / l).
+    r = np.linspace(1e-3, 3.0, 200)
+    ls, s, nu = 0.37, 1.7, 2.5
+    z = np.sqrt(2 * nu) * r / ls
+    ref = s * 2 ** (1 - nu) / math.gamma(nu) * z ** nu * sp.kv(nu, z)
+    np.testing.assert_allclose(kernels.kernel_of_r2(r * r, "matern52", ls, s), ref, rtol=1e-10)
+    assert kernels.kernel_of_r2(np.array([0.0]), "matern52", ls, s)[0] == s
+
+
+def test_rbf_factorises_over_dimensions():
+    X = ci.points(3, 20, 4)
+    Y = ci.points(4, 25, 4)
+    ls, s = 0.3, 2.0
+    K = kernels.kernel_matrix(X, Y, "rbf", ls, s)
+    prod = np.ones((20, 25)) * s
+    for k in range(4):
+        prod *= kernels.kernel_matrix(X[:, k:k + 1], Y[:, k:k + 1], "rbf", ls, 1.0)
+    np.testing.assert_allclose(K, prod, rtol=1e-12)
+    # Convention of the reading: k(l) = s exp(-1/2).
+    assert np.isclose(kernels.kernel_of_r2(np.array([ls * ls]), "rbf", ls, s)[0], s * math.exp(-0.5))
+
+
+@pytest.mark.parametrize("kind", ["rbf", "matern52"])
+def test_dense_K_and_blocked_mvm(kind):
+    X = ci.points(5, 300, 3)
+    K = kernels.dense_K(X, kind, 0.2, 1.3, 1e-2)
+    assert np.allclose(K, K.T)
+    assert np.allclose(np.diag(K), 1.3 + 1e-2)
+    assert np.linalg.eigvalsh(K)[0] >= 1e-2 * (1 - 1e-9)     # K_XX PSD => lambda_min >= sigma^2
+    V = ci.rhs(6, 300, 3).T
+    np.testing.assert_allclose(kernels.mvm(X, kind, 0.2, 1.3, 1e-2, V, rows_per_block=37), K @ V,
+                               rtol=1e-12, atol=1e-12)
+
+
+# -------------------------------------------------------------- elliptic ----
+def test_agm_closed_form_lemniscatic():
+    # K(m = 1/2) = Gamma(1/4)^2 / (4 sqrt(pi)); K(0) = pi/2.
+    assert abs(ellipk_mc(0.5) - math.gamma(0.25) ** 2 / (4 * math.sqrt(math.pi))) < 1e-15 * 2
+    assert abs(ellipk_mc(1.0) - math.pi / 2) < 1e-15
+    # AGM(1, sqrt(2)) is Gauss's constant reciprocal relation: 1/AGM(1, sqrt 2) = 0.8346268...
+    assert abs(1.0 / agm(1.0, math.sqrt(2.0)) - 0.8346268416740731) < 1e-15
+
+
+@pytest.mark.parametrize("mc", [1e-12, 1e-8, 1e-4, 0.01, 0.3, 0.9])
+def test_ellipk_matches_scipy(mc):
+    assert np.isclose(ellipk_mc(mc), sp.ellipkm1(mc), rtol=1e-14)
+
+
+def test_ellipj_matches_scipy_and_identities():
+    for m in [0.0, 0.05, 0.5, 0.9, 0.99999]:
+        for u in [0.0, 0.3, 1.1, 2.5, -0.7]:
+            sn, cn, dn = ellipj(u, m)
+            rs, rc, rd, _ = sp.ellipj(u, m)
+            assert abs(sn - rs) < 1e-14 and abs(cn - rc) < 1e-14 and abs(dn - rd) < 1e-14
+            assert abs(sn * sn + cn * cn - 1) < 1e-14
+            assert abs(dn * dn + m * sn * sn - 1) < 1e-14
+
+
+def test_ellipj_special_cases():
+    # m = 0: circular functions; m = 1: hyperbolic (A&S 16.6).
+    assert np.allclose(ellipj(0.8, 0.0), (math.sin(0.8), math.cos(0.8), 1.0), atol=1e-16)
+    s = 1.0 / math.cosh(0.8)
+    assert np.allclose(ellipj(0.8, 1.0, mc=0.0), (math.tanh(0.8), s, s), atol=1e-16)
+    # Quarter period: sn(K|m) = 1, cn(K|m) = 0, dn(K|m) = sqrt(1 - m)  (A&S 16.5).
+    for mc in [1e-6, 0.2, 0.7]:
+        K = ellipk_mc(mc)
+        sn, cn, dn = ellipj(K, 1 - mc, mc=mc)
+        assert abs(sn - 1) < 1e-13 and abs(cn) < 1e-7 and abs(dn - math.sqrt(mc)) < 1e-7 * max(1, math.sqrt(mc))
+
+
+# ------------------------------------------------------------ quadrature ----
+def test_nodes_closed_form_at_kappa_one():
+    # lambda_min = lambda_max = lam: k = 1, K' = K(0) = pi/2, m' = 0, so
+    # t_q = lam tan^2(pi u_q / 2) and w_q = sqrt(lam) / (Q cos^2(pi u_q / 2)).
+    lam, Q = 2.5, 7
+    w, t = quad_nodes(lam, lam, Q)
+    u = (np.arange(1, Q + 1) - 0.5) / Q
+    np.testing.assert_allclose(t, lam * np.tan(np.pi * u / 2) ** 2, rtol=1e-13)
+    np.testing.assert_allclose(w, np.sqrt(lam) / (Q * np.cos(np.pi * u / 2) ** 2), rtol=1e-13)
+    assert abs(scalar_approx(np.array([lam]), w, t)[0] * math.sqrt(lam) - 1) < 1e-14
+
+
+@pytest.mark.parametrize("kappa,Q", [(1e2, 6), (1e4, 8), (1e6, 8), (1e6, 15), (1e8, 12), (1e10, 20)])
+def test_scalar_identity_within_hale_bound(kappa, Q):
+    # Lemma "hale": error O(exp(-2 Q pi^2 / (log kappa + 3))); constant 10 covers it.
+    lmin = 0.37
+    w, t = quad_nodes(lmin, lmin * kappa, Q)
+    assert (w > 0).all() and (t > 0).all()                 # Eq. contour_integral_quad_4
+    lam = lmin * np.logspace(0, np.log10(kappa), 3000)
+    err = np.max(np.abs(scalar_approx(lam, w, t) * np.sqrt(lam) - 1))
+    assert err <= 10 * math.exp(-2 * Q * math.pi ** 2 / (math.log(kappa) + 3))
+
+
+def test_quadrature_error_falls_with_Q():
+    kappa = 1e5
+    lam = np.logspace(0, 5, 2000)
+    errs = []
+    for Q in range(2, 17):
+        w, t = quad_nodes(1.0, kappa, Q)
+        errs.append(np.max(np.abs(scalar_approx(lam, w, t) * np.sqrt(lam) - 1)))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_weight_shift_ratio_lemma_and_trig_identity():
+    # Lemma "quad_ratio": sum w_q/t_q < 4 Q log(5 sqrt(kappa)) / (pi sqrt(lambda_min)).
+    for Q in [3, 8, 15]:
+        assert np.isclose(sum(1 / (Q * math.sin(math.pi * (q - 0.5) / (2 * Q)) ** 2)
+                              for q in range(1, Q + 1)), 2 * Q)
+        for kappa in [10.0, 1e4, 1e8]:
+            lmin = 0.05
+            w, t = quad_nodes(lmin, lmin * kappa, Q)
+            assert np.sum(w / t) < 4 * Q * math.log(5 * math.sqrt(kappa)) / (math.pi * math.sqrt(lmin))
+
+
+def test_matrix_quadrature_matches_inverse_sqrtm():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((40, 40))
+    K = A @ A.T + 0.5 * np.eye(40)
+    lam = np.linalg.eigvalsh(K)
+    w, t = quad_nodes(lam[0], lam[-1], 14)
+    approx = sum(wq * np.linalg.inv(tq * np.eye(40) + K) for wq, tq in zip(w, t))
+    ref = np.linalg.inv(scipy.linalg.sqrtm(K).real)
+    assert np.linalg.norm(approx - ref, 2) / np.linalg.norm(ref, 2) < 1e-8
+
+
+# --------------------------------------------------------------- Lanczos ----
+def _spd(n, seed, spectrum):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (U * spectrum) @ U.T
+
+
+def test_lanczos_matches_full_gram_schmidt():
+    # Arnoldi with full (twice-applied) Gram-Schmidt gives H = Q^T K Q; for
+    # symmetric K it is the Lanczos tridiagonal.
+    K = _spd(30, 1, np.linspace(1, 5, 30))
+    b = np.random.default_rng(2).standard_normal(30)
+    J = 8
+    alpha, beta = lanczos(lambda v: K @ v, b, J)
+    Qm = np.zeros((30, J))
+    Qm[:, 0] = b / np.linalg.norm(b)
+    for j in range(1, J):
+        v = K @ Qm[:, j - 1]
+        for _ in range(2):
+            v -= Qm[:, :j] @ (Qm[:, :j].T @ v)
+        Qm[:, j] = v / np.linalg.norm(v)
+    H = Qm.T @ K @ Qm
+    np.testing.assert_allclose(tridiagonal(alpha, beta), H, atol=1e-10)
+
+
+def test_ritz_values_interlace_and_converge():
+    spec = np.linspace(1.0, 40.0, 40)
+    K = _spd(40, 3, spec)
+    b = np.random.default_rng(4).standard_normal(40)
+    for J in [3, 6, 10]:
+        a, bt = lanczos(lambda v: K @ v, b, J)
+        tmin, tmax = ritz_extremes(a, bt)
+        assert spec[0] - 1e-10 <= tmin <= tmax <= spec[-1] + 1e-10
+    # J = N steps recover the whole spectrum (small N, before orthogonality is lost).
+    spec12 = np.linspace(1.0, 12.0, 12)
+    K12 = _spd(12, 30, spec12)
+    a, bt = lanczos(lambda v: K12 @ v, b[:12], 12)
+    ev = np.linalg.eigvalsh(tridiagonal(a, bt))
+    np.testing.assert_allclose(ev, spec12, rtol=1e-9)
+
+
+# -------------------------------------------------------------- msMINRES ----
+def test_msminres_equals_krylov_least_squares():
+    # c_J = argmin over K_J(K, b) of ||(K + t I) c - b||  (Eq. minres_krylov).
+    n = 48
+    K = _spd(n, 5, np.geomspace(0.01, 10, n))
+    b = np.random.default_rng(6).standard_normal(n)
+    shifts = np.array([0.0, 0.03, 1.0, 7.5])
+    for J in [1, 2, 5, 9]:
+        Xs, _ = msminres(lambda V: K @ V, b[:, None], shifts, J)
+        Kry = np.stack([np.linalg.matrix_power(K, i) @ b for i in range(J)], axis=1)
+        Vb, _ = np.linalg.qr(Kry)
+        for q, t in enumerate(shifts):
+            A = (K + t * np.eye(n)) @ Vb
+            y = np.linalg.lstsq(A, b, rcond=None)[0]
+            ref = Vb @ y
+            assert np.linalg.norm(Xs[q, :, 0] - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_msminres_exact_after_n_steps_and_residual_estimate():
+    n = 24
+    K = _spd(n, 7, np.linspace(1, 3, n))
+    B = np.random.default_rng(8).standard_normal((n, 3))
+    shifts = np.array([0.1, 2.0])
+    Xs, info = msminres(lambda V: K @ V, B, shifts, n)
+    for q, t in enumerate(shifts):
+        ref = np.linalg.solve(K + t * np.eye(n), B)
+        assert np.linalg.norm(Xs[q] - ref) <= 1e-9 * np.linalg.norm(ref)
+    # |phibar| equals the explicit residual norm.
+    Xs, info = msminres(lambda V: K @ V, B, shifts, 6)
+    for q, t in enumerate(shifts):
+        r = np.linalg.norm((K + t * np.eye(n)) @ Xs[q] - B, axis=0)
+        np.testing.assert_allclose(np.abs(info["phibar"][q]), r, rtol=1e-8)
+
+
+def test_msminres_diagonal_m_distinct_values_converges_in_m_steps():
+    lam = np.repeat([0.5, 1.5, 4.0, 9.0], 10)                  # 4 distinct eigenvalues
+    K = np.diag(lam)
+    b = np.random.default_rng(9).standard_normal(40)
+    Xs, info = msminres(lambda V: K @ V, b[:, None], np.array([0.2, 3.0]), 30)
+    assert info["iters"][0] == 4
+    for q, t in enumerate([0.2, 3.0]):
+        np.testing.assert_allclose(Xs[q, :, 0], b / (lam + t), rtol=1e-10)
+
+
+def test_msminres_residual_obeys_lemma_minres():
+    # Lemma "minres" is printed without the factor 2 of the Chebyshev bound it
+    # cites (Greenbaum 1997, ch. 3); exact MINRES can exceed the printed form
+    # (this case reaches 1.27x of it), so the pin uses 2 ((sqrt k - 1)/(sqrt k + 1))^J ||b||.
+    n = 60
+    spec = np.geomspace(0.1, 100, n)
+    K = _spd(n, 10, spec)
+    b = np.random.default_rng(11).standard_normal(n)
+    shifts = np.array([0.0, 0.5, 5.0])
+    for J in [2, 5, 10, 20]:
+        Xs, info = msminres(lambda V: K @ V, b[:, None], shifts, J)
+        for q, t in enumerate(shifts):
+            kap = (spec[-1] + t) / (spec[0] + t)
+            bound = 2 * ((math.sqrt(kap) - 1) / (math.sqrt(kap) + 1)) ** J * np.linalg.norm(b)
+            assert np.linalg.norm((K + t * np.eye(n)) @ Xs[q, :, 0] - b) <= bound * (1 + 1e-9)
+
+
+# ------------------------------------------------------------------- CIQ ----
+def _matern_problem(n=400, seed=12):
+    X = ci.points(seed, n, 3)
+    K = kernels.dense_K(X, "matern52", 0.2, 1.0, 1e-2)
+    B = ci.rhs(seed, n, 2)
+    return X, K, B
+
+
+def test_eig_oracle_matches_sqrtm():
+    _, K, B = _matern_problem(200)
+    S = scipy.linalg.sqrtm(K).real
+    np.testing.assert_allclose(eig.sqrt_apply(K, B.T), S @ B.T, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(eig.invsqrt_apply(K, S @ B.T), B.T, rtol=1e-7, atol=1e-8)
+
+
+@pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
+def test_ciq_matches_eig_oracle(op):
+    X, K, B = _matern_problem()
+    start = ci.start_vector(13, K.shape[0])
+    A, info = ciq.ciq_apply(ciq.dense_mvm(K), B, 15, op, tol=1e-10, max_iter=600,
+                            noise=1e-2, start=start)
+    ref = (eig.sqrt_apply if op == "sqrt" else eig.invsqrt_apply)(K, B.T).T
+    assert np.linalg.norm(A - ref) / np.linalg.norm(ref) < 1e-6
+    lam = np.linalg.eigvalsh(K)
+    assert info["lmin"] <= lam[0] and info["lmax"] >= lam[-1]
+
+
+def test_ciq_diagonal_closed_form():
+    lam = np.repeat(np.geomspace(0.01, 50.0, 12), 5)
+    K = np.diag(lam)
+    B = ci.rhs(14, 60, 3)
+    w, t = quad_nodes(lam.min(), lam.max(), 12)
+    A, _ = ciq.ciq_apply(ciq.dense_mvm(K), B, 12, "invsqrt", nodes=(w, t), max_iter=60,
+                         lmin=lam.min(), lmax=lam.max())
+    np.testing.assert_allclose(A, B / np.sqrt(lam), rtol=2e-5)
+    A, _ = ciq.ciq_apply(ciq.dense_mvm(K), B, 12, "sqrt", nodes=(w, t), max_iter=60,
+                         lmin=lam.min(), lmax=lam.max())
+    np.testing.assert_allclose(A, B * np.sqrt(lam), rtol=2e-5)
+
+
+def test_ciq_square_root_identities():
+    X, K, B = _matern_problem(300, 15)
+    start = ci.start_vector(16, 300)
+    kw = dict(tol=1e-11, max_iter=800, noise=1e-2, start=start)
+    S1, _ = ciq.ciq_apply(ciq.dense_mvm(K), B, 15, "sqrt", **kw)
+    S2, _ = ciq.ciq_apply(ciq.dense_mvm(K), S1, 15, "sqrt", **kw)
+    KB = (K @ B.T).T
+    assert np.linalg.norm(S2 - KB) / np.linalg.norm(KB) < 1e-6          # K^{1/2} K^{1/2} b = K b
+    R, _ = ciq.ciq_apply(ciq.dense_mvm(K), S1, 15, "invsqrt", **kw)
+    assert np.linalg.norm(R - B) / np.linalg.norm(B) < 1e-6             # K^{-1/2} K^{1/2} b = b
+
+
+def test_ciq_sqrt_forms_agree():
+    X, K, B = _matern_problem(200, 17)
+    start = ci.start_vector(18, 200)
+    kw = dict(tol=1e-11, max_iter=600, noise=1e-2, start=start)
+    A1, _ = ciq.ciq_apply(ciq.dense_mvm(K), B, 12, "sqrt", sqrt_form="identity", **kw)
+    A2, _ = ciq.ciq_apply(ciq.dense_mvm(K), B, 12, "sqrt", sqrt_form="mvm", **kw)
+    assert np.linalg.norm(A1 - A2) / np.linalg.norm(A1) < 1e-6
+
+
+@pytest.mark.parametrize("spectrum", ["inv_sqrt", "inv_square"])
+def test_ciq_error_falls_with_Q_and_J_on_synthetic_spectra(spectrum):
+    # Sec. 4 / Fig. 1: random matrices with lambda_t = t^{-1/2} or t^{-2}; Q = 8 gives < 1e-4.
+    n = 256
+    tt = np.arange(1, n + 1, dtype=np.float64)
+    spec = tt ** -0.5 if spectrum == "inv_sqrt" else tt ** -2.0
+    K = _spd(n, 19, spec)
+    b = ci.rhs(20, n, 1)
+    ref = eig.sqrt_apply(K, b.T).T
+    errs = []
+    for Q in [2, 4, 6, 8]:
+        w, t = quad_nodes(spec.min(), spec.max(), Q)
+        A, _ = ciq.ciq_apply(ciq.dense_mvm(K), b, Q, "sqrt", nodes=(w, t), tol=1e-12,
+                             max_iter=n, lmin=spec.min(), lmax=spec.max())
+        errs.append(np.linalg.norm(A - ref) / np.linalg.norm(ref))
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-4
+    w, t = quad_nodes(spec.min(), spec.max(), 8)
+    errJ = []
+    for J in [5, 20, 80]:
+        A, _ = ciq.ciq_apply(ciq.dense_mvm(K), b, 8, "sqrt", nodes=(w, t), max_iter=J,
+                             lmin=spec.min(), lmax=spec.max())
+        errJ.append(np.linalg.norm(A - ref) / np.linalg.norm(ref))
+    assert errJ[0] > errJ[1] > errJ[2]
+
+
+def test_errbound_stop_rule_bounds_true_error():
+    X, K, B = _matern_problem(300, 21)
+    lam = np.linalg.eigvalsh(K)
+    w, t = quad_nodes(lam[0], lam[-1], 15)
+    ref = eig.invsqrt_apply(K, B.T).T
+    A, info = ciq.ciq_apply(ciq.dense_mvm(K), B, 15, "invsqrt", nodes=(w, t), tol=1e-3,
+                            stop_rule="errbound", max_iter=500, lmin=lam[0], lmax=lam[-1])
+    err = np.linalg.norm(A - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert (err <= 1.05e-3).all()
+    assert (info["iters"] < 500).all()
