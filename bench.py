@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Throughput of msMINRES-CIQ on one B300: K^{1/2}B right-hand-side solves per
+second at relative error <= 1e-3.
+
+Workload (the Thompson-sampling-shaped prior draw of Sec. 5.2, synthetic):
+N = 50,000 points uniform in [0,1]^6, RBF kernel, lengthscale 0.3,
+outputscale 1, sigma^2 = 1e-3, T = 64 right-hand sides ~ N(0, I), Q = 12
+quadrature points, K^{1/2}B.  The solve stops per column when the
+a-posteriori error bound sum_q w_q t_q |phibar_q| / (t_q + lambda_min) falls
+to 1e-3 of ||a_j|| (so every delivered column has relative error <= 1e-3 up
+to the O(1e-6) quadrature error at Q = 12); the Lanczos pre-pass (10 MVMs)
+and the node computation are inside every step.
+
+One step = one ciq_sqrt call on device-resident inputs.  `e2e` repeats the
+same call with host (pageable NumPy) buffers, so the host<->device copies are
+inside the timed region.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+
+Multi-GPU: the solves are independent problems, so N ranks run N replicas
+(weak scaling), one per GPU, with no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ciq_inputs as ci  # noqa: E402
+
+WORKLOAD = ci.THOMPSON_50K
+TOL = 1e-3
+MAX_ITER = 4000
+LANCZOS_ITERS = 10
+# Iterations this workload needs to reach the error bound 1e-3 (measured by
+# the library's FP32 solve; the FP64 oracle does the same MVMs per iteration).
+# Only the reference arm uses it, to scale its per-iteration time to a solve.
+J_WORKLOAD = 1050
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------- CPU baseline --
+def oracle_iteration_seconds(X, B, Q, rows=8192):
+    """FP64 oracle, bounded sample of one full-size msMINRES iteration.
+
+    The O(N^2) part is timed on `rows` of the N rows of K (the oracle's own
+    row-block MVM) and scaled by N/rows; the O(QNT) vector/Givens part is one
+    full-size oracle msMINRES step with the MVM replaced by the identity.
+    """
+    from oracle import kernels
+    from oracle.msminres import msminres
+    from oracle.quadrature import quad_nodes
+
+    W = WORKLOAD
+    n = X.shape[0]
+    V = np.ascontiguousarray(B.T)
+    t0 = time.perf_counter()
+    for r0 in range(0, rows, 2048):
+        kernels.kernel_matrix(X[r0:r0 + 2048], X, W.kernel, W.lengthscale, W.outputscale) @ V
+    t_rows = time.perf_counter() - t0
+    w, t = quad_nodes(W.noise, 2100.0, Q)
+    t0 = time.perf_counter()
+    msminres(lambda Z: Z, V, t, 1)
+    t_rec = time.perf_counter() - t0
+    return t_rows * n / rows + t_rec, t_rows + t_rec, rows
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        if info:
+            return max(i.get("num_threads", 1) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------- roofline --
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+def roofline_fp32(N, T, d, t_launch_ms, pk):
+    # Algorithmic work of one kernel MVM on CUDA cores: 2 N^2 T flops for the
+    # product with the T-column block plus 3 d N^2 flops for the distances.
+    flops = 2.0 * N * N * T + 3.0 * d * N * N
+    achieved = flops / (t_launch_ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "mvm_wide (FP32 CUDA-core on-the-fly kernel MVM)",
+            "peak_note": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived, not measured)"}
+
+
+# ------------------------------------------------------------------- main --
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    W = WORKLOAD
+    X, B = W.make()
+    Q = W.q
+    steps = []
+    for _ in range(max(1, args.warmup and 0) + args.steps):
+        t_iter, t_spent, rows = oracle_iteration_seconds(X, B, Q)
+        steps.append(t_iter)
+    t_iter = statistics.median(steps)
+    t_solve = t_iter * (LANCZOS_ITERS + J_WORKLOAD)
+    value = W.t / t_solve
+    line = {"impl": "reference", "metric": "K^{1/2}b RHS-solves/s at rel err <=1e-3", "value": value,
+            "unit": "RHS-solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "T": W.t, "Q": Q,
+                       "tol": TOL, "stop_rule": "errbound", "iterations": LANCZOS_ITERS + J_WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "RHS-solves/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": f"per step: oracle kernel MVM on {rows} of {W.n} rows (scaled x{W.n / rows:.2f}) "
+                                       f"+ one full-size oracle msMINRES vector step; x{LANCZOS_ITERS + J_WORKLOAD} iterations"},
+            "e2e": {"value": value, "unit": "RHS-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2006_11267_b300 as P
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = WORKLOAD
+    seed_shift = rank            # independent replica per rank
+    X = np.asarray(ci.points(W.seed + seed_shift, W.n, W.d), dtype=np.float32)
+    B = np.asarray(ci.rhs(W.seed + seed_shift, W.n, W.t), dtype=np.float32)
+    Xd = torch.from_numpy(X).to(dev)
+    Bd = torch.from_numpy(B).to(dev)
+    out = torch.empty_like(Bd)
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    opts = dict(stop_rule="errbound", max_iter=MAX_ITER, lanczos_iters=LANCZOS_ITERS, precision=args.precision,
+                check_every=16)
+
+    def step(profile=0):
+        return P.ciq_sqrt(Xd, k, Bd, W.q, TOL, out=out, profile=profile, **opts)[1]
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = W.t * args.steps * world / (elapsed_ms * 1e-3)
+    launches = sum(i["launches"] for i in infos)
+    # One profiled solve: per-launch CUDA events on the library's stream.
+    pinfo = step(profile=1)
+    torch.cuda.synchronize()
+    t_mvm = pinfo["t_mvm_ms"] / max(1, pinfo["mvm_launches"])
+    t_rec = pinfo["t_step_ms"] / max(1, pinfo["step_launches"])
+    pk, pk_kind = peaks()
+    roof = roofline_fp32(W.n, W.t, W.d, t_mvm, pk)
+    roof["peak_source"] = pk_kind
+    e2e = None
+    if not args.no_e2e:
+        out_h = np.empty_like(B)
+        for _ in range(1):
+            P.ciq_sqrt(X, k, B, W.q, TOL, out=out_h, **opts)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            P.ciq_sqrt(X, k, B, W.q, TOL, out=out_h, **opts)
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": W.t * world / t_e2e, "unit": "RHS-solves/s",
+               "h2d_bytes_per_step": int(X.nbytes + B.nbytes), "d2h_bytes_per_step": int(out_h.nbytes)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        J = int(statistics.median(i["iters"] for i in infos))
+        t_iter, t_spent, rows = oracle_iteration_seconds(X.astype(np.float64), B.astype(np.float64), W.q)
+        cpu = {"value": W.t / (t_iter * (LANCZOS_ITERS + J)), "unit": "RHS-solves/s", "cores": cpu_threads(),
+               "kind": "oracle",
+               "sample": f"oracle kernel MVM on {rows} of {W.n} rows (scaled x{W.n / rows:.2f}) + one full-size "
+                         f"oracle msMINRES vector step = one iteration ({t_spent:.1f} s measured); "
+                         f"x{LANCZOS_ITERS + J} iterations (pre-pass + the J={J} this run needed)"}
+    if rank == 0:
+        it = [i["iters"] for i in infos]
+        line = {"metric": "K^{1/2}b RHS-solves/s at rel err <=1e-3", "value": value, "unit": "RHS-solves/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
+                           "noise": W.noise, "T": W.t, "Q": W.q, "op": "sqrt", "tol": TOL,
+                           "stop_rule": "errbound", "precision": args.precision, "iterations": it,
+                           "lanczos_iters": LANCZOS_ITERS, "errbound_max": max(i["errbound_max"] for i in infos),
+                           "parallelism": f"replicas{world}",
+                           "l2": "no flush: every step streams > 100 GB through a > 126 MB workspace"},
+                "roofline": roof,
+                "kernels": {"mvm_ms_per_launch": t_mvm, "recurrence_ms_per_launch": t_rec,
+                            "mvm_share": pinfo["t_mvm_ms"] / max(pinfo["t_total_ms"], 1e-9),
+                            "recurrence_share": pinfo["t_step_ms"] / max(pinfo["t_total_ms"], 1e-9),
+                            "prepass_ms": pinfo["t_prepass_ms"], "total_ms": pinfo["t_total_ms"]},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * ciq.h -- C ABI of libciq: msMINRES-CIQ square roots of Gaussian-process
+ * kernel matrices on one B300 (sm_103a).
+ *
+ * Method: Pleiss, Jankowiak, Eriksson, Damle, Gardner, "Fast Matrix Square
+ * Roots with Applications to Gaussian Processes and Bayesian Optimization"
+ * (NeurIPS 2020).  For K = K_XX + sigma^2 I the library returns
+ *
+ *     K^{-1/2} B ~= sum_q w_q (t_q I + K)^{-1} B          (Eq. contour_integral_quad)
+ *     K^{1/2}  B ~= K sum_q w_q (t_q I + K)^{-1} B
+ *
+ * with nodes (w_q, t_q) from Jacobi elliptic functions over Lanczos-estimated
+ * spectral bounds (App. B, Algorithm "quadrature") and the Q shifted solves
+ * done together by one multi-shift MINRES (App. C, Algorithm "msMINRES"),
+ * one kernel MVM per iteration regardless of Q (Property 1).
+ *
+ * Kernels (the paper names them but does not write them out; this is the
+ * convention of the library, r = ||x - x'||, l = lengthscale, s = outputscale):
+ *     CIQ_RBF       k(r) = s exp(-r^2 / (2 l^2))
+ *     CIQ_MATERN52  k(r) = s (1 + sqrt5 r/l + 5 r^2/(3 l^2)) exp(-sqrt5 r/l)
+ *
+ * Layout (all calls):
+ *   X    row-major N x d single (or double for *_f64) precision: point i is
+ *        X[i*d .. i*d + d-1].  1 <= d <= CIQ_MAX_DIM.
+ *   B    T right-hand sides of N entries each, back to back: entry i of
+ *        column c is B[c*N + i] (column-major N x T, leading dimension N).
+ *   out  same layout as B.
+ *
+ * Memory: X, B, out, the Lanczos start vector and the optional nodes may be
+ * host or device pointers (checked with cudaPointerGetAttributes).  Host
+ * buffers are copied to and from the device inside the call.  The caller
+ * owns every buffer it passes.  The library owns its workspace unless
+ * ciq_options.workspace is set.
+ *
+ * Errors: no call aborts, traps or prints.  Every call returns a ciq_status.
+ * CIQ_NOT_CONVERGED still writes the final iterate and fills the info.
+ *
+ * Streams: work is queued on `stream` (NULL = legacy default stream).  The
+ * solve entry points return after the result is written (they read a device
+ * convergence flag between batches of iterations), so they are synchronous
+ * with respect to `stream`.
+ */
+#ifndef CIQ_H
+#define CIQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* ciq_stream_t;
+
+#define CIQ_MAX_DIM 16        /* largest point dimension d */
+#define CIQ_MAX_Q 32          /* largest number of quadrature points Q */
+
+typedef enum {
+    CIQ_OK = 0,
+    CIQ_ERR_ARG = 1,          /* bad size, NULL pointer, bad enum, Q/d out of range */
+    CIQ_ERR_CUDA = 2,         /* a CUDA runtime call failed (no device, launch error) */
+    CIQ_ERR_NOMEM = 3,        /* device workspace could not be allocated */
+    CIQ_NOT_CONVERGED = 4,    /* max_iter reached before every column met the stop rule */
+    CIQ_ERR_NAN = 5,          /* a non-finite Lanczos coefficient appeared */
+    CIQ_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+} ciq_status;
+
+typedef enum { CIQ_RBF = 0, CIQ_MATERN52 = 1 } ciq_kernel_type;
+
+/* Kernel hyperparameters; noise is sigma^2 added to the diagonal of K_XX. */
+typedef struct {
+    int type;                 /* ciq_kernel_type */
+    double lengthscale;       /* > 0 */
+    double outputscale;       /* > 0 */
+    double noise;             /* >= 0 */
+} ciq_kernel;
+
+/* Arithmetic of the kernel tiles inside the MVM (vectors stay FP32,
+ * Lanczos/Givens scalars stay FP64 in every mode). */
+typedef enum {
+    CIQ_PREC_FP32 = 0,        /* plain FP32 on CUDA cores */
+    CIQ_PREC_TF32 = 1,        /* tensor cores: split-TF32 distances, TF32 kernel tile */
+    CIQ_PREC_BF16 = 2         /* tensor cores: split-BF16 distances, BF16 kernel tile */
+} ciq_precision;
+
+typedef enum {
+    CIQ_MVM_AUTO = 0,         /* on-the-fly */
+    CIQ_MVM_ONTHEFLY = 1,     /* K recomputed tile by tile every MVM, never stored */
+    CIQ_MVM_STORED = 2        /* K formed once in device memory (N^2 floats), streamed */
+} ciq_mvm_mode;
+
+typedef enum {
+    CIQ_STOP_RESIDUAL = 0,    /* per column: max_q |phibar_q| / ||b|| <= tol */
+    CIQ_STOP_ERRBOUND = 1     /* per column: sum_q c_q |phibar_q| / (t_q + lmin) <= tol ||a_j|| */
+} ciq_stop_rule;
+
+typedef enum {
+    CIQ_SQRT_IDENTITY = 0,    /* K^{1/2}b = (sum w_q) b - sum w_q t_q x_q   (no extra MVM) */
+    CIQ_SQRT_MVM = 1          /* K^{1/2}b = K (sum w_q x_q)                 (one extra MVM) */
+} ciq_sqrt_form;
+
+typedef struct {
+    int precision;            /* ciq_precision (default CIQ_PREC_FP32) */
+    int mvm;                  /* ciq_mvm_mode (default CIQ_MVM_AUTO) */
+    int stop_rule;            /* ciq_stop_rule (default CIQ_STOP_RESIDUAL) */
+    int sqrt_form;            /* ciq_sqrt_form (default CIQ_SQRT_IDENTITY) */
+    int max_iter;             /* J_max, msMINRES iterations (default 200) */
+    int lanczos_iters;        /* J_L, Lanczos steps of the bound pre-pass (default 10) */
+    int check_every;          /* iterations queued between convergence reads (default 8) */
+    int profile;              /* 1: time every kernel launch with CUDA events (fills info->t_*) */
+    uint64_t seed;            /* start vector seed when lanczos_start is NULL */
+    const float* lanczos_start; /* optional N entries (host or device; FP64 calls read double*) */
+    double lmax_margin;       /* lambda_max_used = lmax_margin * theta_max (default 1.05) */
+    double lmin_div;          /* lambda_min_used = theta_min / lmin_div if noise == 0 (default 100) */
+    double lmin, lmax;        /* both > 0: use these bounds and skip the pre-pass */
+    const double* quad_w;     /* optional Q weights (host); with quad_t skips pre-pass and nodes */
+    const double* quad_t;     /* optional Q shifts (host) */
+    void* workspace;          /* optional device workspace of workspace_bytes */
+    size_t workspace_bytes;
+} ciq_options;
+
+typedef struct {
+    int iters;                /* msMINRES iterations of the slowest column (= MVMs) */
+    int iters_min;            /* ... of the fastest column */
+    int converged;            /* columns that met the stop rule */
+    int lanczos_iters;        /* MVMs spent in the bound pre-pass */
+    double resid_max;         /* max over columns, shifts of |phibar_q| / ||b|| */
+    double errbound_max;      /* max over columns of sum_q c_q|phibar_q|/(t_q+lmin) / ||a|| */
+    double ritz_min, ritz_max;/* extreme Ritz values of the pre-pass (0 if skipped) */
+    double lmin_used, lmax_used;
+    double w[CIQ_MAX_Q];      /* nodes used */
+    double t[CIQ_MAX_Q];
+    int q;
+    int launches;             /* kernels launched by the call */
+    double t_total_ms;        /* profile: device time of the whole call */
+    double t_prepass_ms;      /* profile: Lanczos pre-pass and nodes */
+    double t_mvm_ms;          /* profile: sum over msMINRES kernel-MVM launches */
+    double t_step_ms;         /* profile: sum over msMINRES recurrence launches */
+    int mvm_launches;         /* profile: msMINRES kernel-MVM launches timed */
+    int step_launches;        /* profile: recurrence launches timed */
+} ciq_info;
+
+/* Human-readable name of a status code (static string). */
+const char* ciq_status_string(int status);
+
+/* Fill *opt with the defaults listed in ciq_options. */
+void ciq_default_options(ciq_options* opt);
+
+/* Quadrature weights and shifts for K^{-1/2} ~= sum_q w_q (t_q I + K)^{-1}.
+ * Eq. quad_points_and_locations with the sign flip of Eq.
+ * contour_integral_quad_4 and Algorithm "quadrature" (App. B), FP64 on the
+ * host: k^2 = lmin/lmax, K' = K(k'), u_q = (q - 1/2)/Q, Jacobi elliptic
+ * functions at u_q K' with parameter 1 - k^2, Jacobi imaginary transform.
+ * w, t: host arrays of Q doubles written by the call.  Requires
+ * 0 < lmin <= lmax and 1 <= Q <= CIQ_MAX_Q, else CIQ_ERR_ARG. */
+ciq_status ciq_quad_nodes(double lmin, double lmax, int Q, double* w, double* t);
+
+/* Extreme Ritz values of `iters` Lanczos steps on K = K_XX + sigma^2 I from
+ * a random start (App. B.2; Algorithm "quadrature", first two lines), and the
+ * bounds the solves use: lmax_used = 1.05 theta_max; lmin_used = sigma^2 when
+ * sigma^2 > 0 (K_XX is PSD), else theta_min / 100.  All outputs are host
+ * doubles; any may be NULL.  `start` (N floats, host or device) may be NULL:
+ * the start vector is then 2u - 1 with u the splitmix64 uniforms of `seed`.
+ * 1 <= iters <= 512. */
+ciq_status ciq_lanczos_bounds(const float* X, int64_t N, int d, const ciq_kernel* kern,
+                              int iters, uint64_t seed, const float* start,
+                              double* ritz_min, double* ritz_max,
+                              double* lmin_used, double* lmax_used, ciq_stream_t stream);
+
+/* K^{1/2} B (Eq. contour_integral_quad, right) and K^{-1/2} B (left) by
+ * msMINRES-CIQ (Algorithm "ciq").  Q in [1, CIQ_MAX_Q]; tol >= 0 (0 runs
+ * max_iter iterations); T >= 1; N >= 1.  `opt` may be NULL (defaults);
+ * `info` may be NULL.  FP32 vectors, FP64 Lanczos/Givens scalars. */
+ciq_status ciq_sqrt(const float* X, int64_t N, int d, const ciq_kernel* kern,
+                    const float* B, int T, int Q, double tol, const ciq_options* opt,
+                    float* out, ciq_info* info, ciq_stream_t stream);
+ciq_status ciq_invsqrt(const float* X, int64_t N, int d, const ciq_kernel* kern,
+                       const float* B, int T, int Q, double tol, const ciq_options* opt,
+                       float* out, ciq_info* info, ciq_stream_t stream);
+
+/* Same in FP64 end to end (kernel tiles, vectors and scalars).  opt->precision
+ * and opt->mvm are ignored (FP64 on-the-fly); lanczos_start, if set, points
+ * to N doubles. */
+ciq_status ciq_sqrt_f64(const double* X, int64_t N, int d, const ciq_kernel* kern,
+                        const double* B, int T, int Q, double tol, const ciq_options* opt,
+                        double* out, ciq_info* info, ciq_stream_t stream);
+ciq_status ciq_invsqrt_f64(const double* X, int64_t N, int d, const ciq_kernel* kern,
+                           const double* B, int T, int Q, double tol, const ciq_options* opt,
+                           double* out, ciq_info* info, ciq_stream_t stream);
+
+/* out = (K_XX + sigma^2 I) V, the MVM of every msMINRES iteration (Property 1,
+ * Sec. 3.3), with K never stored (on-the-fly tiles).  V, out: device, T
+ * columns of N floats.  precision: ciq_precision.  Asynchronous on stream. */
+ciq_status ciq_kernel_mvm(const float* X, int64_t N, int d, const ciq_kernel* kern,
+                          const float* V, int T, float* out, int precision,
+                          ciq_stream_t stream);
+ciq_status ciq_kernel_mvm_f64(const double* X, int64_t N, int d, const ciq_kernel* kern,
+                              const double* V, int T, double* out, ciq_stream_t stream);
+
+/* Dense K = K_XX + sigma^2 I into device memory Kmat (row i at Kmat + i*ldk,
+ * ldk >= N, FP32), for the stored-K MVM.  Asynchronous on stream. */
+ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel* kern,
+                             float* Kmat, int64_t ldk, ciq_stream_t stream);
+
+/* out = Kmat V for a stored symmetric N x N matrix (device, leading
+ * dimension ldk >= N, FP32); V, out: device, T columns of N floats.
+ * Asynchronous on stream. */
+ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T,
+                          float* out, ciq_stream_t stream);
+
+/* Device workspace bytes a solve with these sizes and options needs. */
+size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CIQ_H */

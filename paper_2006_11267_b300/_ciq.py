@@ -1,0 +1,304 @@
+"""ctypes binding of libciq (include/ciq.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays may be
+CUDA torch tensors (device pointers, launched on the current torch stream),
+CPU torch tensors or NumPy arrays (host pointers: the library copies them to
+and from the device inside the call).  Nothing is computed here.
+
+Layouts (see include/ciq.h): X is (N, d) row-major; right-hand sides are
+passed as a (T, N) array whose row c is right-hand side c (the C layout
+"T columns of N entries").
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libciq.so")
+
+CIQ_MAX_DIM = 16
+CIQ_MAX_Q = 32
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
+          4: "not converged within max_iter", 5: "non-finite Lanczos coefficient",
+          6: "unsupported option"}
+CIQ_OK, CIQ_ERR_ARG, CIQ_ERR_CUDA, CIQ_ERR_NOMEM, CIQ_NOT_CONVERGED, CIQ_ERR_NAN, CIQ_ERR_UNSUPPORTED = range(7)
+
+KERNELS = {"rbf": 0, "matern52": 1}
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2}
+MVM_MODES = {"auto": 0, "onthefly": 1, "stored": 2}
+STOP_RULES = {"residual": 0, "errbound": 1}
+SQRT_FORMS = {"identity": 0, "mvm": 1}
+
+
+class CiqError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+class _Kernel(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("lengthscale", ctypes.c_double),
+                ("outputscale", ctypes.c_double), ("noise", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("mvm", ctypes.c_int), ("stop_rule", ctypes.c_int),
+                ("sqrt_form", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("lanczos_iters", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("profile", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("lanczos_start", ctypes.c_void_p), ("lmax_margin", ctypes.c_double),
+                ("lmin_div", ctypes.c_double), ("lmin", ctypes.c_double), ("lmax", ctypes.c_double),
+                ("quad_w", ctypes.c_void_p), ("quad_t", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("iters_min", ctypes.c_int), ("converged", ctypes.c_int),
+                ("lanczos_iters", ctypes.c_int), ("resid_max", ctypes.c_double),
+                ("errbound_max", ctypes.c_double), ("ritz_min", ctypes.c_double),
+                ("ritz_max", ctypes.c_double), ("lmin_used", ctypes.c_double),
+                ("lmax_used", ctypes.c_double), ("w", ctypes.c_double * CIQ_MAX_Q),
+                ("t", ctypes.c_double * CIQ_MAX_Q), ("q", ctypes.c_int), ("launches", ctypes.c_int),
+                ("t_total_ms", ctypes.c_double), ("t_prepass_ms", ctypes.c_double),
+                ("t_mvm_ms", ctypes.c_double), ("t_step_ms", ctypes.c_double),
+                ("mvm_launches", ctypes.c_int), ("step_launches", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libciq.so (built in-tree).  Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with `python -m paper_2006_11267_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64, D, U64, S = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                            ctypes.c_uint64, ctypes.c_size_t)
+    KP, OP, IP = ctypes.POINTER(_Kernel), ctypes.POINTER(_Options), ctypes.POINTER(_Info)
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "ciq_status_string": (ctypes.c_char_p, [I]),
+        "ciq_default_options": (None, [OP]),
+        "ciq_quad_nodes": (I, [D, D, I, DP, DP]),
+        "ciq_lanczos_bounds": (I, [P, I64, I, KP, I, U64, P, DP, DP, DP, DP, P]),
+        "ciq_sqrt": (I, [P, I64, I, KP, P, I, I, D, OP, P, IP, P]),
+        "ciq_invsqrt": (I, [P, I64, I, KP, P, I, I, D, OP, P, IP, P]),
+        "ciq_sqrt_f64": (I, [P, I64, I, KP, P, I, I, D, OP, P, IP, P]),
+        "ciq_invsqrt_f64": (I, [P, I64, I, KP, P, I, I, D, OP, P, IP, P]),
+        "ciq_kernel_mvm": (I, [P, I64, I, KP, P, I, P, I, P]),
+        "ciq_kernel_mvm_f64": (I, [P, I64, I, KP, P, I, P, P]),
+        "ciq_kernel_matrix": (I, [P, I64, I, KP, P, I64, P]),
+        "ciq_stored_mvm": (I, [P, I64, I64, P, I, P, P]),
+        "ciq_workspace_bytes": (S, [I64, I, I, I, OP]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+@dataclasses.dataclass
+class Kernel:
+    """Kernel type and hyperparameters; ``noise`` is sigma^2 on the diagonal."""
+    type: str = "rbf"
+    lengthscale: float = 1.0
+    outputscale: float = 1.0
+    noise: float = 0.0
+
+    def c(self) -> _Kernel:
+        return _Kernel(KERNELS[self.type], float(self.lengthscale), float(self.outputscale),
+                       float(self.noise))
+
+
+# ------------------------------------------------------------ marshalling ---
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Pointer of a contiguous torch tensor or NumPy array (None -> NULL)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _stream(*arrays):
+    for a in arrays:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return None
+
+
+def _empty_like_rhs(B, dtype):
+    if _is_torch(B):
+        return B.new_empty(B.shape)
+    return np.empty(B.shape, dtype=dtype)
+
+
+def make_options(**kw) -> _Options:
+    o = _Options()
+    lib().ciq_default_options(ctypes.byref(o))
+    keep = []
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "precision":
+            o.precision = PRECISIONS[v] if isinstance(v, str) else int(v)
+        elif k == "mvm":
+            o.mvm = MVM_MODES[v] if isinstance(v, str) else int(v)
+        elif k == "stop_rule":
+            o.stop_rule = STOP_RULES[v] if isinstance(v, str) else int(v)
+        elif k == "sqrt_form":
+            o.sqrt_form = SQRT_FORMS[v] if isinstance(v, str) else int(v)
+        elif k in ("lanczos_start", "workspace"):
+            setattr(o, k, _ptr(v))
+            keep.append(v)
+        elif k == "nodes":
+            w = np.ascontiguousarray(v[0], dtype=np.float64)
+            t = np.ascontiguousarray(v[1], dtype=np.float64)
+            o.quad_w, o.quad_t = w.ctypes.data, t.ctypes.data
+            keep += [w, t]
+        else:
+            setattr(o, k, v)
+    o._keep = keep
+    return o
+
+
+def _info_dict(info: _Info, status: int) -> dict:
+    q = info.q
+    return dict(status=status, status_name=STATUS.get(status), iters=info.iters,
+                iters_min=info.iters_min, converged=info.converged,
+                lanczos_iters=info.lanczos_iters, resid_max=info.resid_max,
+                errbound_max=info.errbound_max, ritz_min=info.ritz_min, ritz_max=info.ritz_max,
+                lmin_used=info.lmin_used, lmax_used=info.lmax_used,
+                w=np.array(info.w[:q]), t=np.array(info.t[:q]), launches=info.launches,
+                t_total_ms=info.t_total_ms, t_prepass_ms=info.t_prepass_ms, t_mvm_ms=info.t_mvm_ms,
+                t_step_ms=info.t_step_ms, mvm_launches=info.mvm_launches,
+                step_launches=info.step_launches)
+
+
+def _check(status: int, where: str, allow=(CIQ_OK, CIQ_NOT_CONVERGED)):
+    if status not in allow:
+        raise CiqError(status, where)
+
+
+def _solve(name, X, kernel: Kernel, B, Q, tol, out=None, **opts):
+    N, d = X.shape
+    T = B.shape[0]
+    if B.shape[1] != N:
+        raise ValueError("B must have shape (T, N)")
+    fp64 = name.endswith("_f64")
+    if out is None:
+        out = _empty_like_rhs(B, np.float64 if fp64 else np.float32)
+    o = make_options(**opts)
+    info = _Info()
+    k = kernel.c()
+    st = getattr(lib(), name)(_ptr(X), N, d, ctypes.byref(k), _ptr(B), T, int(Q), float(tol),
+                              ctypes.byref(o), _ptr(out), ctypes.byref(info), _stream(X, B, out))
+    _check(st, name)
+    return out, _info_dict(info, st)
+
+
+def ciq_sqrt(X, kernel, B, Q, tol=0.0, out=None, **opts):
+    """K^{1/2} B (FP32 vectors, FP64 scalars). Returns (out, info)."""
+    return _solve("ciq_sqrt", X, kernel, B, Q, tol, out, **opts)
+
+
+def ciq_invsqrt(X, kernel, B, Q, tol=0.0, out=None, **opts):
+    """K^{-1/2} B (FP32 vectors, FP64 scalars). Returns (out, info)."""
+    return _solve("ciq_invsqrt", X, kernel, B, Q, tol, out, **opts)
+
+
+def ciq_sqrt_f64(X, kernel, B, Q, tol=0.0, out=None, **opts):
+    """K^{1/2} B in FP64 end to end. Returns (out, info)."""
+    return _solve("ciq_sqrt_f64", X, kernel, B, Q, tol, out, **opts)
+
+
+def ciq_invsqrt_f64(X, kernel, B, Q, tol=0.0, out=None, **opts):
+    """K^{-1/2} B in FP64 end to end. Returns (out, info)."""
+    return _solve("ciq_invsqrt_f64", X, kernel, B, Q, tol, out, **opts)
+
+
+def ciq_quad_nodes(lmin, lmax, Q):
+    """(w, t) float64 arrays of length Q from the library's host routine."""
+    w = np.zeros(Q)
+    t = np.zeros(Q)
+    DP = ctypes.POINTER(ctypes.c_double)
+    st = lib().ciq_quad_nodes(float(lmin), float(lmax), int(Q), w.ctypes.data_as(DP), t.ctypes.data_as(DP))
+    _check(st, "ciq_quad_nodes", allow=(CIQ_OK,))
+    return w, t
+
+
+def ciq_lanczos_bounds(X, kernel, iters=10, seed=0x5eed, start=None):
+    """dict(ritz_min, ritz_max, lmin_used, lmax_used) from the device pre-pass."""
+    N, d = X.shape
+    vals = [ctypes.c_double() for _ in range(4)]
+    k = kernel.c()
+    st = lib().ciq_lanczos_bounds(_ptr(X), N, d, ctypes.byref(k), int(iters), int(seed), _ptr(start),
+                                  *[ctypes.byref(v) for v in vals], _stream(X, start))
+    _check(st, "ciq_lanczos_bounds", allow=(CIQ_OK,))
+    return dict(zip(["ritz_min", "ritz_max", "lmin_used", "lmax_used"], [v.value for v in vals]))
+
+
+def ciq_kernel_mvm(X, kernel, V, out=None, precision="fp32"):
+    """(K_XX + sigma^2 I) V for device tensors; V and out are (T, N)."""
+    N, d = X.shape
+    T = V.shape[0]
+    if out is None:
+        out = V.new_empty(V.shape)
+    k = kernel.c()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    st = lib().ciq_kernel_mvm(_ptr(X), N, d, ctypes.byref(k), _ptr(V), T, _ptr(out), prec, _stream(X, V, out))
+    _check(st, "ciq_kernel_mvm", allow=(CIQ_OK,))
+    return out
+
+
+def ciq_kernel_mvm_f64(X, kernel, V, out=None):
+    N, d = X.shape
+    T = V.shape[0]
+    if out is None:
+        out = V.new_empty(V.shape)
+    k = kernel.c()
+    st = lib().ciq_kernel_mvm_f64(_ptr(X), N, d, ctypes.byref(k), _ptr(V), T, _ptr(out), _stream(X, V, out))
+    _check(st, "ciq_kernel_mvm_f64", allow=(CIQ_OK,))
+    return out
+
+
+def ciq_kernel_matrix(X, kernel, Kmat):
+    N, d = X.shape
+    k = kernel.c()
+    st = lib().ciq_kernel_matrix(_ptr(X), N, d, ctypes.byref(k), _ptr(Kmat), Kmat.shape[1], _stream(X, Kmat))
+    _check(st, "ciq_kernel_matrix", allow=(CIQ_OK,))
+    return Kmat
+
+
+def ciq_stored_mvm(Kmat, V, out=None):
+    N = Kmat.shape[0]
+    T = V.shape[0]
+    if out is None:
+        out = V.new_empty(V.shape)
+    st = lib().ciq_stored_mvm(_ptr(Kmat), N, Kmat.shape[1], _ptr(V), T, _ptr(out), _stream(Kmat, V, out))
+    _check(st, "ciq_stored_mvm", allow=(CIQ_OK,))
+    return out
+
+
+def ciq_workspace_bytes(N, d, T, Q, **opts):
+    o = make_options(**opts)
+    return int(lib().ciq_workspace_bytes(int(N), int(d), int(T), int(Q), ctypes.byref(o)))

@@ -1,0 +1,746 @@
+// C entry points of libciq (include/ciq.h): argument checks, workspace
+// layout, and the launch sequence of msMINRES-CIQ (Algorithm "ciq"):
+//
+//   points -> [Lanczos pre-pass -> Ritz extremes -> bounds -> nodes]  (device)
+//          -> init (q_1 = b/||b||) -> J x (kernel MVM + msMINRES step)   (device)
+//          -> combine (K^{-1/2} b or K^{1/2} b) -> summary               (device)
+//
+// The host only launches: it reads one device flag ("every column stopped")
+// per batch of `check_every` iterations, one batch behind the launches, so
+// the GPU never waits on the host.
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "krylov.cuh"
+#include "mvm_tc.cuh"
+#include "spectral.cuh"
+
+using namespace ciq;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t n) {
+        off = (off + kAlign - 1) / kAlign * kAlign;
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+bool device_accessible(const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int dim_pad(int d) { return (d + 3) / 4 * 4; }
+
+void choose_chunks(int64_t Npad, int T, int* nchunks, int64_t* rpc) {
+    const int64_t max_chunks = std::max<int64_t>(1, Npad / 1024);
+    const int64_t target = (4 * 148 + T - 1) / T;
+    const int64_t ch = std::min<int64_t>(std::max<int64_t>(1, target), max_chunks);
+    const int64_t r = round_up((Npad + ch - 1) / ch, kRowPad);
+    *rpc = r;
+    *nchunks = (int)((Npad + r - 1) / r);
+}
+
+ciq_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return CIQ_OK;
+    if (e == cudaErrorMemoryAllocation) return CIQ_ERR_NOMEM;
+    return CIQ_ERR_CUDA;
+}
+
+#define CIQ_TRY(...)                                    \
+    do {                                                \
+        cudaError_t _e = (__VA_ARGS__);                 \
+        if (_e != cudaSuccess) { rc = from_cuda(_e); goto done; } \
+    } while (0)
+
+bool valid_kernel(const ciq_kernel* k) {
+    return k && (k->type == CIQ_RBF || k->type == CIQ_MATERN52) && k->lengthscale > 0.0 &&
+           std::isfinite(k->lengthscale) && k->outputscale > 0.0 && std::isfinite(k->outputscale) &&
+           k->noise >= 0.0 && std::isfinite(k->noise);
+}
+
+// Pinned host words for the convergence flag, one set per host thread.
+int* pinned_flags() {
+    thread_local int* p = nullptr;
+    if (!p) {
+        if (cudaHostAlloc(reinterpret_cast<void**>(&p), 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    return p;
+}
+
+void keep_pool_warm() {
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done = true;
+}
+
+// ---------------------------------------------------------------- plan ----
+template <typename R>
+struct Plan {
+    int64_t N, Npad;
+    int d, dp, T, Q;
+    int jmax, JL;
+    int nparts, nparts1, nchunks, nchunks1;
+    int64_t rpc, rpc1;
+    bool tc;                      // tensor-core MVM
+    bool stage_x, stage_b, stage_out, stage_start;
+    bool prepass;
+    // pointers (valid once an arena base is set)
+    R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB;
+    R *sx, *sb, *sout, *sstart;
+    double *partials, *ynp, *beta, *beta1, *giv, *phifinal, *nodes, *summary;
+    double *lpart, *lynp, *bpar, *lalpha, *lbeta;
+    int *status, *iters, *brk, *cnt, *all_done, *jeff, *ldone;
+    TcPoints tcp;
+    size_t bytes;
+
+    void layout(char* base) {
+        Arena a;
+        a.base = base;
+        Xp = a.take<R>((size_t)Npad * dp);
+        QA = a.take<R>((size_t)T * Npad);
+        QB = a.take<R>((size_t)T * Npad);
+        Y = a.take<R>((size_t)T * Npad);
+        Ylo = a.take<R>((size_t)T * Npad);
+        Bw = a.take<R>((size_t)T * Npad);
+        D = a.take<R>((size_t)2 * Q * T * Npad);
+        partials = a.take<double>((size_t)nparts * T * 3);
+        ynp = a.take<double>((size_t)2 * nchunks * T);
+        beta = a.take<double>((size_t)2 * T);
+        beta1 = a.take<double>((size_t)T);
+        giv = a.take<double>((size_t)2 * Q * T * 5);
+        phifinal = a.take<double>((size_t)Q * T);
+        nodes = a.take<double>(kNodeCount);
+        summary = a.take<double>(8);
+        status = a.take<int>(T);
+        iters = a.take<int>(T);
+        brk = a.take<int>(T);
+        cnt = a.take<int>((size_t)jmax + 2);
+        all_done = a.take<int>(1);
+        if (prepass) {
+            LA = a.take<R>((size_t)Npad);
+            LB = a.take<R>((size_t)Npad);
+            lpart = a.take<double>((size_t)nparts1 * 3);
+            lynp = a.take<double>((size_t)nchunks1);
+            bpar = a.take<double>(2);
+            lalpha = a.take<double>((size_t)JL);
+            lbeta = a.take<double>((size_t)JL + 1);
+            jeff = a.take<int>(1);
+            ldone = a.take<int>(1);
+        } else {
+            LA = LB = nullptr; lpart = lynp = bpar = lalpha = lbeta = nullptr; jeff = ldone = nullptr;
+        }
+        sx = stage_x ? a.take<R>((size_t)N * d) : nullptr;
+        sb = stage_b ? a.take<R>((size_t)N * T) : nullptr;
+        sout = stage_out ? a.take<R>((size_t)N * T) : nullptr;
+        sstart = stage_start ? a.take<R>((size_t)N) : nullptr;
+        if (tc) {
+            const size_t tb = tc_points_bytes(Npad, d);
+            char* p = a.take<char>(tb);
+            tcp = tc_points_layout(p, Npad, d);
+        }
+        bytes = a.off + kAlign;
+    }
+};
+
+template <typename R>
+Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool prepass, bool tc) {
+    Plan<R> p{};
+    p.N = N;
+    p.d = d;
+    p.dp = dim_pad(d);
+    p.Npad = round_up(N, kRowPad);
+    p.T = T;
+    p.Q = Q;
+    p.jmax = o.max_iter;
+    p.JL = o.lanczos_iters;
+    p.tc = tc;
+    p.nparts = tc ? (int)tc_row_tiles(p.Npad) : (int)mvm_simt_row_tiles<R>(p.Npad, T);
+    p.nparts1 = (int)mvm_simt_row_tiles<R>(p.Npad, 1);
+    choose_chunks(p.Npad, T, &p.nchunks, &p.rpc);
+    choose_chunks(p.Npad, 1, &p.nchunks1, &p.rpc1);
+    p.prepass = prepass;
+    p.layout(nullptr);
+    return p;
+}
+
+template <typename R>
+KrylovState<R> krylov_state(const Plan<R>& p, int op, const ciq_options& o, double tol) {
+    KrylovState<R> s{};
+    s.N = p.N; s.Npad = p.Npad; s.T = p.T; s.Q = p.Q;
+    s.nparts = p.nparts; s.nchunks = p.nchunks; s.rows_per_chunk = p.rpc;
+    s.QA = p.QA; s.QB = p.QB; s.D = p.D; s.Y = p.Y; s.Ylo = p.Ylo; s.Bw = p.Bw;
+    s.partials = p.partials; s.ynp = p.ynp; s.beta = p.beta; s.beta1 = p.beta1;
+    s.giv = p.giv; s.phifinal = p.phifinal; s.status = p.status; s.iters = p.iters;
+    s.brk = p.brk; s.cnt = p.cnt; s.all_done = p.all_done; s.nodes = p.nodes;
+    s.summary = p.summary; s.jmax = p.jmax; s.op = op; s.stop_rule = o.stop_rule; s.tol = tol;
+    s.breakdown_rtol = sizeof(R) == 4 ? 1e-6 : 1e-13;
+    return s;
+}
+
+template <typename R>
+LanczosState<R> lanczos_state(const Plan<R>& p) {
+    LanczosState<R> s{};
+    s.N = p.N; s.Npad = p.Npad; s.nparts = p.nparts1; s.nchunks = p.nchunks1;
+    s.rows_per_chunk = p.rpc1; s.iters = p.JL;
+    s.LA = p.LA; s.LB = p.LB; s.partials = p.lpart; s.ynp = p.lynp; s.bpar = p.bpar;
+    s.alpha = p.lalpha; s.beta = p.lbeta; s.jeff = p.jeff; s.done = p.ldone;
+    return s;
+}
+
+template <typename R>
+MvmArgs<R> mvm_args(const Plan<R>& p, const ciq_kernel& k) {
+    MvmArgs<R> a{};
+    a.X = p.Xp; a.N = p.N; a.Npad = p.Npad; a.dp = p.dp; a.kt = k.type;
+    a.s = (R)k.outputscale; a.noise = (R)k.noise; a.ldv = p.Npad;
+    return a;
+}
+
+// Lanczos pre-pass on the device; leaves nodes in p.nodes.
+template <typename R>
+cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options& o, int Q,
+                        const R* start_dev, cudaStream_t st) {
+    LanczosState<R> ls = lanczos_state(p);
+    cudaError_t e = launch_lanczos_init(ls, start_dev, o.seed, st);
+    if (e != cudaSuccess) return e;
+    MvmArgs<R> a = mvm_args(p, k);
+    a.T = 1;
+    a.mode = kLanczos;
+    a.partials = p.lpart;
+    a.stop = p.ldone;
+    for (int j = 1; j <= p.JL; ++j) {
+        a.V = (j & 1) ? p.LA : p.LB;
+        a.qprev = (j & 1) ? p.LB : p.LA;
+        a.beta = p.bpar + (j & 1);
+        if ((e = launch_mvm_simt(a, st)) != cudaSuccess) return e;
+        if ((e = launch_lanczos_step(ls, j, st)) != cudaSuccess) return e;
+    }
+    return launch_bounds_nodes(ls, p.nodes, Q, k.noise, o.lmax_margin, o.lmin_div, st);
+}
+
+template <typename R>
+cudaError_t tc_prepare(const Plan<R>& p, int precision, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (p.tc) return launch_tc_prepare(p.tcp, p.Xp, p.Npad, p.dp, p.d, precision, st);
+    }
+    return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, int precision, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (p.tc) return launch_mvm_tc(p.tcp, a, precision, st);
+    }
+    return launch_mvm_simt(a, st);
+}
+
+// CUDA events of the profile mode: one event between consecutive launches of
+// a batch of iterations, harvested one batch behind like the convergence flag.
+struct Profile {
+    bool on = false;
+    cudaEvent_t t_start = nullptr, t_pre0 = nullptr, t_pre1 = nullptr, t_loop = nullptr,
+                t_loop_end = nullptr, t_end = nullptr;
+    std::vector<cudaEvent_t> ev[2];
+    std::vector<double> mvm_ms, step_ms;
+    cudaError_t create() {
+        cudaEvent_t* all[] = {&t_start, &t_pre0, &t_pre1, &t_loop, &t_loop_end, &t_end};
+        for (auto* e : all) {
+            cudaError_t r = cudaEventCreate(e);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    }
+    void destroy() {
+        cudaEvent_t all[] = {t_start, t_pre0, t_pre1, t_loop, t_loop_end, t_end};
+        for (auto e : all)
+            if (e) cudaEventDestroy(e);
+        for (auto& v : ev)
+            for (auto e : v)
+                if (e) cudaEventDestroy(e);
+    }
+};
+
+template <typename R>
+ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* B, int T, int Q,
+                 double tol, const ciq_options* opt, R* out, ciq_info* info, cudaStream_t st,
+                 int op, bool fp64) {
+    if (!X || !B || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q ||
+        !(tol >= 0.0) || !valid_kernel(kern))
+        return CIQ_ERR_ARG;
+    ciq_options o;
+    ciq_default_options(&o);
+    if (opt) o = *opt;
+    if (o.max_iter < 1 || o.max_iter > 1000000 || o.lanczos_iters < 1 || o.lanczos_iters > 512 ||
+        o.check_every < 1 || !(o.lmax_margin >= 1.0) || !(o.lmin_div >= 1.0) ||
+        (o.stop_rule != CIQ_STOP_RESIDUAL && o.stop_rule != CIQ_STOP_ERRBOUND) ||
+        (o.sqrt_form != CIQ_SQRT_IDENTITY && o.sqrt_form != CIQ_SQRT_MVM) ||
+        (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_BF16) ||
+        (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED))
+        return CIQ_ERR_ARG;
+    if ((o.quad_w == nullptr) != (o.quad_t == nullptr)) return CIQ_ERR_ARG;
+    if (o.mvm == CIQ_MVM_STORED) return CIQ_ERR_UNSUPPORTED;
+    bool tc = false;
+    if (!fp64 && o.precision != CIQ_PREC_FP32) {
+        if (!tc_supported(o.precision, d)) return CIQ_ERR_UNSUPPORTED;
+        tc = true;
+    }
+    if (op == kOpSqrtIdentity && o.sqrt_form == CIQ_SQRT_MVM) op = kOpSqrtMvm;
+    const bool given_nodes = o.quad_w != nullptr;
+    const bool given_bounds = !given_nodes && o.lmin > 0.0 && o.lmax > 0.0;
+    if (given_bounds && !(o.lmax >= o.lmin)) return CIQ_ERR_ARG;
+    double hw[CIQ_MAX_Q] = {0}, ht[CIQ_MAX_Q] = {0};
+    if (given_nodes) {
+        for (int q = 0; q < Q; ++q) {
+            hw[q] = o.quad_w[q];
+            ht[q] = o.quad_t[q];
+            if (!(ht[q] >= 0.0) || !std::isfinite(hw[q]) || !std::isfinite(ht[q])) return CIQ_ERR_ARG;
+        }
+    }
+    const bool prepass = !given_nodes && !given_bounds;
+    keep_pool_warm();
+
+    Plan<R> p = make_plan<R>(N, d, T, Q, o, prepass, tc);
+    p.stage_x = !device_accessible(X);
+    p.stage_b = !device_accessible(B);
+    p.stage_out = !device_accessible(out);
+    p.stage_start = prepass && o.lanczos_start && !device_accessible(o.lanczos_start);
+    p.layout(nullptr);
+    const size_t need = p.bytes;
+    char* base = nullptr;
+    bool owned = false;
+    ciq_status rc = CIQ_OK;
+    int* flags = pinned_flags();
+    double summary[8] = {0};
+    double nodes[kNodeCount] = {0};
+    int last_j = 0;
+    int launches = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    Profile prof;
+    prof.on = o.profile != 0;
+    if (!flags) return CIQ_ERR_CUDA;
+    if (prof.on && prof.create() != cudaSuccess) { cudaGetLastError(); return CIQ_ERR_CUDA; }
+    if (o.workspace) {
+        if (o.workspace_bytes < need) return CIQ_ERR_ARG;
+        base = static_cast<char*>(o.workspace);
+    } else {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), need, st);
+        if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? CIQ_ERR_NOMEM : CIQ_ERR_CUDA; }
+        owned = true;
+    }
+    {
+        p.layout(base);
+        const R* Xd = X;
+        const R* Bd = B;
+        R* outd = out;
+        const R* startd = reinterpret_cast<const R*>(o.lanczos_start);
+        if (p.stage_x) {
+            CIQ_TRY(cudaMemcpyAsync(p.sx, X, sizeof(R) * (size_t)N * d, cudaMemcpyHostToDevice, st));
+            Xd = p.sx;
+        }
+        if (p.stage_b) {
+            CIQ_TRY(cudaMemcpyAsync(p.sb, B, sizeof(R) * (size_t)N * T, cudaMemcpyHostToDevice, st));
+            Bd = p.sb;
+        }
+        if (p.stage_out) outd = p.sout;
+        if (p.stage_start) {
+            CIQ_TRY(cudaMemcpyAsync(p.sstart, o.lanczos_start, sizeof(R) * (size_t)N, cudaMemcpyHostToDevice, st));
+            startd = p.sstart;
+        }
+        CIQ_TRY(cudaMemsetAsync(p.cnt, 0, sizeof(int) * ((size_t)p.jmax + 2), st));
+        CIQ_TRY(cudaMemsetAsync(p.all_done, 0, sizeof(int), st));
+        if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_start, st));
+        CIQ_TRY(launch_prepare_points<R, R>(Xd, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
+        CIQ_TRY(tc_prepare(p, o.precision, st));
+        KrylovState<R> s = krylov_state(p, op, o, tol);
+        CIQ_TRY(launch_init_rhs(s, Bd, st));
+        CIQ_TRY(launch_init_state(s, st));
+        launches += 3 + (p.tc ? 1 : 0);
+        if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_pre0, st));
+        if (given_nodes) {
+            double hn[kNodeCount] = {0};
+            double sw = 0.0;
+            for (int q = 0; q < Q; ++q) { hn[kNodeW + q] = hw[q]; hn[kNodeT + q] = ht[q]; sw += hw[q]; }
+            hn[kNodeLmin] = o.lmin > 0.0 ? o.lmin : 0.0;
+            hn[kNodeLmax] = o.lmax > 0.0 ? o.lmax : 0.0;
+            hn[kNodeSumW] = sw;
+            CIQ_TRY(cudaMemcpyAsync(p.nodes, hn, sizeof(hn), cudaMemcpyHostToDevice, st));
+        } else if (given_bounds) {
+            CIQ_TRY(launch_nodes_from_bounds(p.nodes, Q, o.lmin, o.lmax, st));
+            launches += 1;
+        } else {
+            CIQ_TRY(run_prepass(p, *kern, o, Q, startd, st));
+            launches += 3 + 2 * p.JL;
+        }
+        if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_pre1, st));
+        MvmArgs<R> a = mvm_args(p, *kern);
+        a.T = T;
+        a.mode = kLanczos;
+        a.partials = p.partials;
+        a.stop = p.all_done;
+        CIQ_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        CIQ_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        if (prof.on) {
+            for (int sl = 0; sl < 2; ++sl) {
+                prof.ev[sl].resize(2 * (size_t)o.check_every + 1);
+                for (auto& e : prof.ev[sl]) CIQ_TRY(cudaEventCreate(&e));
+            }
+            prof.mvm_ms.assign((size_t)p.jmax + 1, 0.0);
+            prof.step_ms.assign((size_t)p.jmax + 1, 0.0);
+            CIQ_TRY(cudaEventRecord(prof.t_loop, st));
+        }
+        {
+            int slot = 0;
+            bool pending[2] = {false, false};
+            int first_j[2] = {0, 0}, count[2] = {0, 0};
+            auto harvest = [&](int sl) -> cudaError_t {
+                if (!prof.on) return cudaSuccess;
+                for (int k = 0; k < count[sl]; ++k) {
+                    float m = 0.f, q = 0.f;
+                    cudaError_t e = cudaEventElapsedTime(&m, prof.ev[sl][2 * k], prof.ev[sl][2 * k + 1]);
+                    if (e != cudaSuccess) return e;
+                    e = cudaEventElapsedTime(&q, prof.ev[sl][2 * k + 1], prof.ev[sl][2 * k + 2]);
+                    if (e != cudaSuccess) return e;
+                    prof.mvm_ms[first_j[sl] + k] = m;
+                    prof.step_ms[first_j[sl] + k] = q;
+                }
+                return cudaSuccess;
+            };
+            for (int j = 1; j <= p.jmax;) {
+                const int jb = std::min(j + o.check_every - 1, p.jmax);
+                if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][0], st));
+                for (int jj = j; jj <= jb; ++jj) {
+                    a.V = (jj & 1) ? p.QA : p.QB;
+                    a.qprev = (jj & 1) ? p.QB : p.QA;
+                    a.beta = p.beta + (size_t)(jj & 1) * T;
+                    CIQ_TRY(launch_mvm(p, a, o.precision, st));
+                    if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
+                    CIQ_TRY(launch_msminres_step(s, jj, false, st));
+                    if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 2], st));
+                    launches += 2;
+                }
+                first_j[slot] = j;
+                count[slot] = jb - j + 1;
+                last_j = jb;
+                CIQ_TRY(cudaMemcpyAsync(&flags[slot], p.all_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CIQ_TRY(cudaEventRecord(ev[slot], st));
+                bool stop = false;
+                if (pending[slot ^ 1]) {
+                    CIQ_TRY(cudaEventSynchronize(ev[slot ^ 1]));
+                    CIQ_TRY(harvest(slot ^ 1));
+                    pending[slot ^ 1] = false;
+                    stop = flags[slot ^ 1] != 0;
+                }
+                pending[slot] = true;
+                slot ^= 1;
+                j = jb + 1;
+                if (stop) break;
+            }
+            if (prof.on) {
+                CIQ_TRY(cudaEventRecord(prof.t_loop_end, st));
+                CIQ_TRY(cudaStreamSynchronize(st));
+                for (int sl = 0; sl < 2; ++sl)
+                    if (pending[sl]) CIQ_TRY(harvest(sl));
+            }
+        }
+        CIQ_TRY(launch_msminres_step(s, last_j + 1, true, st));
+        launches += 1;
+        if (op == kOpSqrtMvm) {
+            CIQ_TRY(launch_combine(s, outd, st));      // folds the trailing part into Y
+            MvmArgs<R> m = mvm_args(p, *kern);
+            m.T = T;
+            m.mode = kPlain;
+            m.V = p.Y;
+            m.out = outd;
+            m.ldo = N;
+            CIQ_TRY(launch_mvm(p, m, o.precision, st));
+            launches += 2;
+        } else {
+            CIQ_TRY(launch_combine(s, outd, st));
+            launches += 1;
+        }
+        CIQ_TRY(launch_summary(s, last_j, st));
+        launches += 1;
+        if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_end, st));
+        if (p.stage_out)
+            CIQ_TRY(cudaMemcpyAsync(out, p.sout, sizeof(R) * (size_t)N * T, cudaMemcpyDeviceToHost, st));
+        CIQ_TRY(cudaMemcpyAsync(summary, p.summary, sizeof(summary), cudaMemcpyDeviceToHost, st));
+        CIQ_TRY(cudaMemcpyAsync(nodes, p.nodes, sizeof(nodes), cudaMemcpyDeviceToHost, st));
+        CIQ_TRY(cudaStreamSynchronize(st));
+    }
+done:
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    double t_total = 0, t_pre = 0, t_mvm = 0, t_step = 0;
+    int n_mvm = 0, n_step = 0;
+    if (prof.on && rc == CIQ_OK) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, prof.t_start, prof.t_end) == cudaSuccess) t_total = ms;
+        if (cudaEventElapsedTime(&ms, prof.t_pre0, prof.t_pre1) == cudaSuccess) t_pre = ms;
+        const int itmax = (int)summary[0];
+        // Launches after the last working iteration return at once (every
+        // column had stopped); count the one MVM that ran before the freeze.
+        const int upto = std::min(itmax + 1, last_j);
+        for (int jj = 1; jj <= upto; ++jj) {
+            t_mvm += prof.mvm_ms[jj];
+            ++n_mvm;
+            if (jj <= itmax) { t_step += prof.step_ms[jj]; ++n_step; }
+        }
+    }
+    prof.destroy();
+    if (owned) {
+        cudaFreeAsync(base, st);
+        if (rc != CIQ_OK) cudaStreamSynchronize(st);
+    }
+    if (rc != CIQ_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->iters = (int)summary[0];
+        info->iters_min = (int)summary[1];
+        info->converged = (int)summary[2];
+        info->resid_max = summary[3];
+        info->errbound_max = summary[4];
+        info->lanczos_iters = (int)nodes[kNodeLanczosSteps];
+        info->ritz_min = nodes[kNodeRitzMin];
+        info->ritz_max = nodes[kNodeRitzMax];
+        info->lmin_used = nodes[kNodeLmin];
+        info->lmax_used = nodes[kNodeLmax];
+        info->q = Q;
+        for (int q = 0; q < Q; ++q) { info->w[q] = nodes[kNodeW + q]; info->t[q] = nodes[kNodeT + q]; }
+        info->launches = launches;
+        info->t_total_ms = t_total;
+        info->t_prepass_ms = t_pre;
+        info->t_mvm_ms = t_mvm;
+        info->t_step_ms = t_step;
+        info->mvm_launches = n_mvm;
+        info->step_launches = n_step;
+    }
+    if (summary[6] > 0) return CIQ_ERR_NAN;
+    if ((int)summary[5] == kColMaxIter) return CIQ_NOT_CONVERGED;
+    return CIQ_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C entry points --
+extern "C" {
+
+const char* ciq_status_string(int status) {
+    switch (status) {
+        case CIQ_OK: return "ok";
+        case CIQ_ERR_ARG: return "invalid argument";
+        case CIQ_ERR_CUDA: return "CUDA error";
+        case CIQ_ERR_NOMEM: return "out of device memory";
+        case CIQ_NOT_CONVERGED: return "not converged within max_iter";
+        case CIQ_ERR_NAN: return "non-finite Lanczos coefficient";
+        case CIQ_ERR_UNSUPPORTED: return "unsupported option";
+        default: return "unknown status";
+    }
+}
+
+void ciq_default_options(ciq_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->precision = CIQ_PREC_FP32;
+    opt->mvm = CIQ_MVM_AUTO;
+    opt->stop_rule = CIQ_STOP_RESIDUAL;
+    opt->sqrt_form = CIQ_SQRT_IDENTITY;
+    opt->max_iter = 200;
+    opt->lanczos_iters = 10;
+    opt->check_every = 8;
+    opt->seed = 0x5eed;
+    opt->lmax_margin = 1.05;
+    opt->lmin_div = 100.0;
+}
+
+ciq_status ciq_quad_nodes(double lmin, double lmax, int Q, double* w, double* t) {
+    if (!w || !t || !(lmin > 0.0) || !(lmax >= lmin) || !std::isfinite(lmax) || Q < 1 || Q > CIQ_MAX_Q)
+        return CIQ_ERR_ARG;
+    return quad_nodes(lmin, lmax, Q, w, t) == 0 ? CIQ_OK : CIQ_ERR_ARG;
+}
+
+ciq_status ciq_sqrt(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, int T,
+                    int Q, double tol, const ciq_options* opt, float* out, ciq_info* info,
+                    ciq_stream_t stream) {
+    return solve<float>(X, N, d, kern, B, T, Q, tol, opt, out, info, (cudaStream_t)stream,
+                        kOpSqrtIdentity, false);
+}
+
+ciq_status ciq_invsqrt(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, int T,
+                       int Q, double tol, const ciq_options* opt, float* out, ciq_info* info,
+                       ciq_stream_t stream) {
+    return solve<float>(X, N, d, kern, B, T, Q, tol, opt, out, info, (cudaStream_t)stream, kOpInvSqrt,
+                        false);
+}
+
+ciq_status ciq_sqrt_f64(const double* X, int64_t N, int d, const ciq_kernel* kern, const double* B,
+                        int T, int Q, double tol, const ciq_options* opt, double* out, ciq_info* info,
+                        ciq_stream_t stream) {
+    return solve<double>(X, N, d, kern, B, T, Q, tol, opt, out, info, (cudaStream_t)stream,
+                         kOpSqrtIdentity, true);
+}
+
+ciq_status ciq_invsqrt_f64(const double* X, int64_t N, int d, const ciq_kernel* kern, const double* B,
+                           int T, int Q, double tol, const ciq_options* opt, double* out,
+                           ciq_info* info, ciq_stream_t stream) {
+    return solve<double>(X, N, d, kern, B, T, Q, tol, opt, out, info, (cudaStream_t)stream, kOpInvSqrt,
+                         true);
+}
+
+ciq_status ciq_lanczos_bounds(const float* X, int64_t N, int d, const ciq_kernel* kern, int iters,
+                              uint64_t seed, const float* start, double* ritz_min, double* ritz_max,
+                              double* lmin_used, double* lmax_used, ciq_stream_t stream) {
+    if (!X || N < 1 || d < 1 || d > CIQ_MAX_DIM || iters < 1 || iters > 512 || !valid_kernel(kern))
+        return CIQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ciq_options o;
+    ciq_default_options(&o);
+    o.lanczos_iters = iters;
+    o.seed = seed;
+    o.max_iter = 1;
+    keep_pool_warm();
+    Plan<float> p = make_plan<float>(N, d, 1, 1, o, true, false);
+    p.stage_x = !device_accessible(X);
+    p.stage_start = start && !device_accessible(start);
+    p.layout(nullptr);
+    char* base = nullptr;
+    ciq_status rc = CIQ_OK;
+    double nodes[kNodeCount] = {0};
+    cudaError_t e0 = cudaMallocAsync(reinterpret_cast<void**>(&base), p.bytes, st);
+    if (e0 != cudaSuccess) { cudaGetLastError(); return from_cuda(e0); }
+    {
+        p.layout(base);
+        const float* Xd = X;
+        const float* sd = start;
+        if (p.stage_x) {
+            CIQ_TRY(cudaMemcpyAsync(p.sx, X, sizeof(float) * (size_t)N * d, cudaMemcpyHostToDevice, st));
+            Xd = p.sx;
+        }
+        if (p.stage_start) {
+            CIQ_TRY(cudaMemcpyAsync(p.sstart, start, sizeof(float) * (size_t)N, cudaMemcpyHostToDevice, st));
+            sd = p.sstart;
+        }
+        CIQ_TRY(launch_prepare_points<float, float>(Xd, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
+        CIQ_TRY(run_prepass(p, *kern, o, 1, sd, st));
+        CIQ_TRY(cudaMemcpyAsync(nodes, p.nodes, sizeof(nodes), cudaMemcpyDeviceToHost, st));
+        CIQ_TRY(cudaStreamSynchronize(st));
+    }
+done:
+    cudaFreeAsync(base, st);
+    if (rc != CIQ_OK) { cudaStreamSynchronize(st); cudaGetLastError(); return rc; }
+    if (ritz_min) *ritz_min = nodes[kNodeRitzMin];
+    if (ritz_max) *ritz_max = nodes[kNodeRitzMax];
+    if (lmin_used) *lmin_used = nodes[kNodeLmin];
+    if (lmax_used) *lmax_used = nodes[kNodeLmax];
+    return CIQ_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename R>
+ciq_status kernel_mvm_impl(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* V, int T,
+                           R* out, int precision, cudaStream_t st) {
+    if (!X || !V || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || !valid_kernel(kern) ||
+        precision < CIQ_PREC_FP32 || precision > CIQ_PREC_BF16)
+        return CIQ_ERR_ARG;
+    const bool tc = sizeof(R) == 4 && precision != CIQ_PREC_FP32;
+    if (tc && !tc_supported(precision, d)) return CIQ_ERR_UNSUPPORTED;
+    if (!device_accessible(X) || !device_accessible(V) || !device_accessible(out)) return CIQ_ERR_ARG;
+    keep_pool_warm();
+    ciq_options o;
+    ciq_default_options(&o);
+    o.max_iter = 1;
+    Plan<R> p = make_plan<R>(N, d, T, 1, o, false, tc);
+    char* base = nullptr;
+    ciq_status rc = CIQ_OK;
+    cudaError_t e0 = cudaMallocAsync(reinterpret_cast<void**>(&base), p.bytes, st);
+    if (e0 != cudaSuccess) { cudaGetLastError(); return from_cuda(e0); }
+    {
+        p.layout(base);
+        CIQ_TRY(launch_prepare_points<R, R>(X, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
+        CIQ_TRY(tc_prepare(p, precision, st));
+        // Zero-padded copy of V (the MVM reads whole tiles).
+        CIQ_TRY(cudaMemsetAsync(p.QA, 0, sizeof(R) * (size_t)T * p.Npad, st));
+        CIQ_TRY(cudaMemcpy2DAsync(p.QA, sizeof(R) * p.Npad, V, sizeof(R) * N, sizeof(R) * N, T,
+                                  cudaMemcpyDeviceToDevice, st));
+        MvmArgs<R> a = mvm_args(p, *kern);
+        a.T = T;
+        a.mode = kPlain;
+        a.V = p.QA;
+        a.out = out;
+        a.ldo = N;
+        CIQ_TRY(launch_mvm(p, a, precision, st));
+    }
+done:
+    cudaFreeAsync(base, st);
+    if (rc != CIQ_OK) cudaGetLastError();
+    return rc;
+}
+}  // namespace
+
+extern "C" {
+
+ciq_status ciq_kernel_mvm(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* V, int T,
+                          float* out, int precision, ciq_stream_t stream) {
+    return kernel_mvm_impl<float>(X, N, d, kern, V, T, out, precision, (cudaStream_t)stream);
+}
+
+ciq_status ciq_kernel_mvm_f64(const double* X, int64_t N, int d, const ciq_kernel* kern, const double* V,
+                              int T, double* out, ciq_stream_t stream) {
+    return kernel_mvm_impl<double>(X, N, d, kern, V, T, out, CIQ_PREC_FP32, (cudaStream_t)stream);
+}
+
+ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel* kern, float* Kmat,
+                             int64_t ldk, ciq_stream_t stream) {
+    (void)X; (void)N; (void)d; (void)kern; (void)Kmat; (void)ldk; (void)stream;
+    return CIQ_ERR_UNSUPPORTED;
+}
+
+ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T, float* out,
+                          ciq_stream_t stream) {
+    (void)Kmat; (void)N; (void)ldk; (void)V; (void)T; (void)out; (void)stream;
+    return CIQ_ERR_UNSUPPORTED;
+}
+
+size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt) {
+    if (N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q) return 0;
+    ciq_options o;
+    ciq_default_options(&o);
+    if (opt) o = *opt;
+    const bool prepass = !(o.quad_w && o.quad_t) && !(o.lmin > 0.0 && o.lmax > 0.0);
+    const bool tc = o.precision != CIQ_PREC_FP32 && tc_supported(o.precision, d);
+    Plan<float> p = make_plan<float>(N, d, T, Q, o, prepass, tc);
+    return p.bytes;
+}
+
+}  // extern "C"

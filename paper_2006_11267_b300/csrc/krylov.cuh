@@ -1,0 +1,114 @@
+// Device state and launchers of the msMINRES recurrence and the Lanczos
+// bound pre-pass (App. B.2, App. C).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace ciq {
+
+// Layout of the small FP64 node block shared by the pre-pass and the solve.
+enum NodeSlot {
+    kNodeW = 0,                       // w_q, CIQ_MAX_Q entries
+    kNodeT = CIQ_MAX_Q,               // t_q, CIQ_MAX_Q entries
+    kNodeLmin = 2 * CIQ_MAX_Q,        // lambda_min used
+    kNodeLmax,                        // lambda_max used
+    kNodeRitzMin,                     // theta_min of the pre-pass
+    kNodeRitzMax,                     // theta_max of the pre-pass
+    kNodeSumW,                        // sum_q w_q
+    kNodeLanczosSteps,                // pre-pass steps actually taken
+    kNodeCount
+};
+
+// Per-column status codes of a solve.
+enum ColStatus {
+    kColRunning = 0,
+    kColConverged = 1,      // stop rule met
+    kColExact = 2,          // Lanczos breakdown: Krylov space invariant, solve exact (or b = 0)
+    kColNaN = 3,            // non-finite Lanczos coefficient
+    kColMaxIter = 4,        // max_iter reached with tol > 0
+    kColFixedIter = 5       // max_iter reached with tol == 0 (fixed-J run)
+};
+
+// Output combination.
+enum CombineOp {
+    kOpInvSqrt = 0,         // a = sum_q w_q x_q
+    kOpSqrtIdentity = 1,    // a = (sum_q w_q) b - sum_q w_q t_q x_q
+    kOpSqrtMvm = 2          // y = sum_q w_q x_q, a = K y (MVM launched by the caller)
+};
+
+template <typename R>
+struct KrylovState {
+    int64_t N, Npad;
+    int T, Q;
+    int nparts;                 // MVM row tiles writing partials
+    int nchunks;                // row chunks of the recurrence kernel
+    int64_t rows_per_chunk;     // multiple of kRowPad
+    R* QA;                      // Lanczos vectors, T x Npad each (q_j alternates between QA/QB)
+    R* QB;
+    R* D;                       // search directions [2][Q][T][Npad]
+    R* Y;                       // accumulated sum_q c_q x_q, [T][Npad] (leading part)
+    R* Ylo;                     // trailing part of Y (Y + Ylo carries about twice R's precision)
+    R* Bw;                      // right-hand sides, [T][Npad]
+    double* partials;           // [nparts][T][3] from the MVM epilogue
+    double* ynp;                // [2][nchunks][T] partial ||a_j||^2
+    double* beta;               // [2][T] beta_j double-buffered by step parity
+    double* beta1;              // [T] ||b||
+    double* giv;                // [2][Q][T][5] (c_{j-1}, s_{j-1}, c_{j-2}, s_{j-2}, phibar)
+    double* phifinal;           // [Q][T] phibar when the column stopped
+    int* status;                // [T] ColStatus
+    int* iters;                 // [T] steps applied
+    int* brk;                   // [T] breakdown / NaN seen at the last step (ColStatus code)
+    int* cnt;                   // [jmax + 2] frozen columns seen at step j
+    int* all_done;              // 1 once every column is frozen
+    const double* nodes;        // NodeSlot block
+    double* summary;            // [8] filled by the summary kernel
+    int jmax;
+    int op;                     // CombineOp
+    int stop_rule;              // ciq_stop_rule
+    double tol;
+    double breakdown_rtol;
+};
+
+template <typename R>
+struct LanczosState {
+    int64_t N, Npad;
+    int nparts, nchunks;
+    int64_t rows_per_chunk;
+    int iters;                  // J_L
+    R* LA;                      // Lanczos vectors (Npad each)
+    R* LB;
+    double* partials;           // [nparts][3]
+    double* ynp;                // [nchunks]
+    double* bpar;               // [2] beta_j double-buffered
+    double* alpha;              // [iters]
+    double* beta;               // [iters + 1]; beta[0] = ||start||
+    int* jeff;                  // steps taken (< iters after a breakdown)
+    int* done;                  // breakdown flag (skips the remaining launches)
+};
+
+template <typename R>
+cudaError_t launch_init_rhs(const KrylovState<R>& s, const R* B, cudaStream_t st);
+template <typename R>
+cudaError_t launch_init_state(const KrylovState<R>& s, cudaStream_t st);
+template <typename R>
+cudaError_t launch_msminres_step(const KrylovState<R>& s, int j, bool final_pass, cudaStream_t st);
+template <typename R>
+cudaError_t launch_combine(const KrylovState<R>& s, R* out, cudaStream_t st);
+template <typename R>
+cudaError_t launch_summary(const KrylovState<R>& s, int final_j, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_lanczos_init(const LanczosState<R>& s, const R* start, uint64_t seed,
+                                cudaStream_t st);
+template <typename R>
+cudaError_t launch_lanczos_step(const LanczosState<R>& s, int j, cudaStream_t st);
+// theta_min/max of T_J -> bounds (unless fixed) -> nodes, on one device thread.
+template <typename R>
+cudaError_t launch_bounds_nodes(const LanczosState<R>& s, double* nodes, int Q, double noise,
+                                double lmax_margin, double lmin_div, cudaStream_t st);
+
+// Nodes for given bounds on the device (no pre-pass).
+cudaError_t launch_nodes_from_bounds(double* nodes, int Q, double lmin, double lmax,
+                                     cudaStream_t st);
+
+}  // namespace ciq

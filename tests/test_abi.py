@@ -1,0 +1,90 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+that include/ciq.h declares, validates arguments before touching the device,
+and its host quadrature routine agrees with the oracle's nodes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2006_11267_b300 as P
+from paper_2006_11267_b300 import _ciq
+from oracle.quadrature import quad_nodes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ciq_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = P.lib()
+    declared = _declared_symbols()
+    assert len(declared) >= 12
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(_ciq._Options) == 112
+    assert ctypes.sizeof(_ciq._Kernel) == 32
+    assert ctypes.sizeof(_ciq._Info) == 16 + 6 * 8 + 2 * 32 * 8 + 8 + 4 * 8 + 8
+
+
+def test_status_strings_and_defaults():
+    lib = P.lib()
+    assert lib.ciq_status_string(0) == b"ok"
+    assert lib.ciq_status_string(4).startswith(b"not converged")
+    o = _ciq.make_options()
+    assert (o.max_iter, o.lanczos_iters, o.lmax_margin, o.lmin_div) == (200, 10, 1.05, 100.0)
+
+
+@pytest.mark.parametrize("kappa,Q", [(1.0, 5), (1e3, 8), (1e8, 15), (1e12, 32)])
+def test_host_quad_nodes_match_oracle(kappa, Q):
+    w, t = P.ciq_quad_nodes(0.3, 0.3 * kappa, Q)
+    w2, t2 = quad_nodes(0.3, 0.3 * kappa, Q)
+    np.testing.assert_allclose(w, w2, rtol=1e-12)
+    np.testing.assert_allclose(t, t2, rtol=1e-12)
+
+
+def test_quad_nodes_rejects_bad_arguments():
+    for args in [(0.0, 1.0, 4), (2.0, 1.0, 4), (1.0, 2.0, 0), (1.0, 2.0, 33), (-1.0, 2.0, 3)]:
+        with pytest.raises(P.CiqError) as e:
+            P.ciq_quad_nodes(*args)
+        assert e.value.status == _ciq.CIQ_ERR_ARG
+
+
+def test_solve_validates_before_the_device():
+    X = np.zeros((10, 3), np.float32)
+    B = np.zeros((2, 10), np.float32)
+    k = P.Kernel("rbf", 0.5, 1.0, 1e-2)
+    bad = [
+        dict(X=np.zeros((10, 17), np.float32), B=B, kernel=k, Q=8),          # d > CIQ_MAX_DIM
+        dict(X=X, B=B, kernel=k, Q=0),                                        # Q < 1
+        dict(X=X, B=B, kernel=k, Q=33),                                       # Q > CIQ_MAX_Q
+        dict(X=X, B=B, kernel=P.Kernel("rbf", -1.0, 1.0, 0.1), Q=4),          # lengthscale <= 0
+        dict(X=X, B=B, kernel=P.Kernel("rbf", 1.0, 1.0, -0.1), Q=4),          # noise < 0
+        dict(X=X, B=B, kernel=k, Q=4, max_iter=0),
+        dict(X=X, B=B, kernel=k, Q=4, stop_rule=7),
+    ]
+    for case in bad:
+        kw = {kk: v for kk, v in case.items() if kk not in ("X", "B", "kernel", "Q")}
+        with pytest.raises(P.CiqError) as e:
+            P.ciq_sqrt(case["X"], case["kernel"], case["B"], case["Q"], 1e-4, **kw)
+        assert e.value.status == _ciq.CIQ_ERR_ARG
+
+
+def test_workspace_bytes_grows_with_problem():
+    a = P.ciq_workspace_bytes(1000, 3, 1, 8)
+    b = P.ciq_workspace_bytes(1000, 3, 8, 8)
+    c = P.ciq_workspace_bytes(1000, 3, 8, 16)
+    assert 0 < a < b < c
+    assert P.ciq_workspace_bytes(0, 3, 1, 8) == 0
