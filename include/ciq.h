@@ -63,7 +63,8 @@ typedef enum {
     CIQ_ERR_NOMEM = 3,        /* device workspace could not be allocated */
     CIQ_NOT_CONVERGED = 4,    /* max_iter reached before every column met the stop rule */
     CIQ_ERR_NAN = 5,          /* a non-finite Lanczos coefficient appeared */
-    CIQ_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+    CIQ_ERR_UNSUPPORTED = 6,  /* valid request this build does not implement */
+    CIQ_ERR_SCRATCH_TOO_SMALL = 7 /* problem larger than the static scratch of ciq_kernel_mvm_noalloc */
 } ciq_status;
 
 typedef enum { CIQ_RBF = 0, CIQ_MATERN52 = 1 } ciq_kernel_type;
@@ -211,6 +212,30 @@ ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float
 
 /* Device workspace bytes a solve with these sizes and options needs. */
 size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt);
+
+/* Allocation-free kernel MVM (the paper has no counterpart: this is a
+ * library convenience).  Same result as ciq_kernel_mvm with CIQ_PREC_FP32,
+ * out = (K_XX + sigma^2 I) V, for callers that cannot call cudaMalloc --
+ * code whose device memory belongs to another allocator, or latency-critical
+ * loops where an allocation and the synchronisation it can imply are not
+ * allowed.  Its scratch is one static device array of
+ * ciq_noalloc_scratch_floats() floats (16 MiB) that every GPU loading the
+ * library holds until the process exits; the call needs
+ * round_up(round_up(N,128) * round_up(d,4), 64) + T * round_up(N,128) floats
+ * of it and returns CIQ_ERR_SCRATCH_TOO_SMALL, touching nothing, when that is
+ * more.  X, V, out: device pointers (layouts as above), else CIQ_ERR_ARG.
+ * The first call on a device looks up the scratch's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's contents (the call clears what must start at zero): calls that
+ * overlap on the GPU, e.g. on two streams, race on it.  Allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).  Asynchronous on
+ * stream. */
+ciq_status ciq_kernel_mvm_noalloc(const float* X, int64_t N, int d, const ciq_kernel* kern,
+                                  const float* V, int T, float* out, ciq_stream_t stream);
+
+/* Size in floats of the static scratch behind ciq_kernel_mvm_noalloc. */
+size_t ciq_noalloc_scratch_floats(void);
 
 #ifdef __cplusplus
 }

@@ -25,8 +25,9 @@ CIQ_MAX_Q = 32
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
           4: "not converged within max_iter", 5: "non-finite Lanczos coefficient",
-          6: "unsupported option"}
-CIQ_OK, CIQ_ERR_ARG, CIQ_ERR_CUDA, CIQ_ERR_NOMEM, CIQ_NOT_CONVERGED, CIQ_ERR_NAN, CIQ_ERR_UNSUPPORTED = range(7)
+          6: "unsupported option", 7: "problem exceeds the static scratch of the allocation-free entry point"}
+(CIQ_OK, CIQ_ERR_ARG, CIQ_ERR_CUDA, CIQ_ERR_NOMEM, CIQ_NOT_CONVERGED, CIQ_ERR_NAN, CIQ_ERR_UNSUPPORTED,
+ CIQ_ERR_SCRATCH_TOO_SMALL) = range(8)
 
 KERNELS = {"rbf": 0, "matern52": 1}
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2}
@@ -98,6 +99,8 @@ def lib() -> ctypes.CDLL:
         "ciq_kernel_matrix": (I, [P, I64, I, KP, P, I64, P]),
         "ciq_stored_mvm": (I, [P, I64, I64, P, I, P, P]),
         "ciq_workspace_bytes": (S, [I64, I, I, I, OP]),
+        "ciq_kernel_mvm_noalloc": (I, [P, I64, I, KP, P, I, P, P]),
+        "ciq_noalloc_scratch_floats": (S, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -302,3 +305,20 @@ def ciq_stored_mvm(Kmat, V, out=None):
 def ciq_workspace_bytes(N, d, T, Q, **opts):
     o = make_options(**opts)
     return int(lib().ciq_workspace_bytes(int(N), int(d), int(T), int(Q), ctypes.byref(o)))
+
+
+def ciq_kernel_mvm_noalloc(X, kernel, V, out=None):
+    """(K_XX + sigma^2 I) V through the allocation-free entry point.
+
+    For callers that cannot allocate device memory: the library's scratch is
+    a static device array (see include/ciq.h); ``out`` must be preallocated
+    by such a caller.  V and out are (T, N) device tensors.
+    """
+    N, d = X.shape
+    T = V.shape[0]
+    if out is None:
+        out = V.new_empty(V.shape)
+    k = kernel.c()
+    st = lib().ciq_kernel_mvm_noalloc(_ptr(X), N, d, ctypes.byref(k), _ptr(V), T, _ptr(out), _stream(X, V, out))
+    _check(st, "ciq_kernel_mvm_noalloc", allow=(CIQ_OK,))
+    return out

@@ -563,6 +563,7 @@ const char* ciq_status_string(int status) {
         case CIQ_NOT_CONVERGED: return "not converged within max_iter";
         case CIQ_ERR_NAN: return "non-finite Lanczos coefficient";
         case CIQ_ERR_UNSUPPORTED: return "unsupported option";
+        case CIQ_ERR_SCRATCH_TOO_SMALL: return "problem exceeds the static scratch of the allocation-free entry point";
         default: return "unknown status";
     }
 }
