@@ -81,8 +81,9 @@ typedef struct {
  * Lanczos/Givens scalars stay FP64 in every mode). */
 typedef enum {
     CIQ_PREC_FP32 = 0,        /* plain FP32 on CUDA cores */
-    CIQ_PREC_TF32 = 1,        /* tensor cores: split-TF32 distances, TF32 kernel tile */
-    CIQ_PREC_BF16 = 2         /* tensor cores: split-BF16 distances, BF16 kernel tile */
+    CIQ_PREC_TF32 = 1,        /* reserved: tensor cores with TF32 operands (not built) */
+    CIQ_PREC_BF16 = 2,        /* tensor cores (tcgen05): every operand split into two BF16 parts */
+    CIQ_PREC_FP16 = 3         /* tensor cores (tcgen05): every operand split into two FP16 parts */
 } ciq_precision;
 
 typedef enum {

@@ -30,7 +30,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device mem
  CIQ_ERR_SCRATCH_TOO_SMALL) = range(8)
 
 KERNELS = {"rbf": 0, "matern52": 1}
-PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2}
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16": 3}
 MVM_MODES = {"auto": 0, "onthefly": 1, "stored": 2}
 STOP_RULES = {"residual": 0, "errbound": 1}
 SQRT_FORMS = {"identity": 0, "mvm": 1}

@@ -110,6 +110,7 @@ struct Plan {
     int nparts, nparts1, nchunks, nchunks1;
     int64_t rpc, rpc1;
     bool tc;                      // tensor-core MVM
+    int precision;
     bool stage_x, stage_b, stage_out, stage_start;
     bool prepass;
     // pointers (valid once an arena base is set)
@@ -162,9 +163,8 @@ struct Plan {
         sout = stage_out ? a.take<R>((size_t)N * T) : nullptr;
         sstart = stage_start ? a.take<R>((size_t)N) : nullptr;
         if (tc) {
-            const size_t tb = tc_points_bytes(Npad, d);
-            char* p = a.take<char>(tb);
-            tcp = tc_points_layout(p, Npad, d);
+            char* q = a.take<char>(tc_points_bytes(Npad, T));
+            tcp = tc_points_layout(q, Npad, T, precision);
         }
         bytes = a.off + kAlign;
     }
@@ -173,6 +173,7 @@ struct Plan {
 template <typename R>
 Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool prepass, bool tc) {
     Plan<R> p{};
+    p.precision = o.precision;
     p.N = N;
     p.d = d;
     p.dp = dim_pad(d);
@@ -246,17 +247,19 @@ cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options
 }
 
 template <typename R>
-cudaError_t tc_prepare(const Plan<R>& p, int precision, cudaStream_t st) {
+cudaError_t tc_prepare(const Plan<R>& p, int kt, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (p.tc) return launch_tc_prepare(p.tcp, p.Xp, p.Npad, p.dp, p.d, precision, st);
+        if (p.tc) return launch_tc_prepare(p.tcp, p.Xp, p.N, p.dp, p.d, kt, st);
     }
     return cudaSuccess;
 }
 
+// unit_columns: V's columns have norm 1 (Lanczos vectors), which fixes the
+// power-of-two operand scale of the tensor-core MVM.
 template <typename R>
-cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, int precision, cudaStream_t st) {
+cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (p.tc) return launch_mvm_tc(p.tcp, a, precision, st);
+        if (p.tc) return launch_mvm_tc(p.tcp, a, unit_columns, st);
     }
     return launch_mvm_simt(a, st);
 }
@@ -301,14 +304,14 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         o.check_every < 1 || !(o.lmax_margin >= 1.0) || !(o.lmin_div >= 1.0) ||
         (o.stop_rule != CIQ_STOP_RESIDUAL && o.stop_rule != CIQ_STOP_ERRBOUND) ||
         (o.sqrt_form != CIQ_SQRT_IDENTITY && o.sqrt_form != CIQ_SQRT_MVM) ||
-        (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_BF16) ||
+        (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_FP16) ||
         (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED))
         return CIQ_ERR_ARG;
     if ((o.quad_w == nullptr) != (o.quad_t == nullptr)) return CIQ_ERR_ARG;
     if (o.mvm == CIQ_MVM_STORED) return CIQ_ERR_UNSUPPORTED;
     bool tc = false;
     if (!fp64 && o.precision != CIQ_PREC_FP32) {
-        if (!tc_supported(o.precision, d)) return CIQ_ERR_UNSUPPORTED;
+        if (!tc_supported(o.precision, d) || tc_padded_t(T) < 0) return CIQ_ERR_UNSUPPORTED;
         tc = true;
     }
     if (op == kOpSqrtIdentity && o.sqrt_form == CIQ_SQRT_MVM) op = kOpSqrtMvm;
@@ -377,7 +380,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         CIQ_TRY(cudaMemsetAsync(p.all_done, 0, sizeof(int), st));
         if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_start, st));
         CIQ_TRY(launch_prepare_points<R, R>(Xd, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
-        CIQ_TRY(tc_prepare(p, o.precision, st));
+        CIQ_TRY(tc_prepare(p, kern->type, st));
         KrylovState<R> s = krylov_state(p, op, o, tol);
         CIQ_TRY(launch_init_rhs(s, Bd, st));
         CIQ_TRY(launch_init_state(s, st));
@@ -439,7 +442,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                     a.V = (jj & 1) ? p.QA : p.QB;
                     a.qprev = (jj & 1) ? p.QB : p.QA;
                     a.beta = p.beta + (size_t)(jj & 1) * T;
-                    CIQ_TRY(launch_mvm(p, a, o.precision, st));
+                    CIQ_TRY(launch_mvm(p, a, true, st));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
                     CIQ_TRY(launch_msminres_step(s, jj, false, st));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 2], st));
@@ -479,7 +482,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             m.V = p.Y;
             m.out = outd;
             m.ldo = N;
-            CIQ_TRY(launch_mvm(p, m, o.precision, st));
+            CIQ_TRY(launch_mvm(p, m, false, st));
             launches += 2;
         } else {
             CIQ_TRY(launch_combine(s, outd, st));
@@ -672,15 +675,16 @@ template <typename R>
 ciq_status kernel_mvm_impl(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* V, int T,
                            R* out, int precision, cudaStream_t st) {
     if (!X || !V || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || !valid_kernel(kern) ||
-        precision < CIQ_PREC_FP32 || precision > CIQ_PREC_BF16)
+        precision < CIQ_PREC_FP32 || precision > CIQ_PREC_FP16)
         return CIQ_ERR_ARG;
     const bool tc = sizeof(R) == 4 && precision != CIQ_PREC_FP32;
-    if (tc && !tc_supported(precision, d)) return CIQ_ERR_UNSUPPORTED;
+    if (tc && (!tc_supported(precision, d) || tc_padded_t(T) < 0)) return CIQ_ERR_UNSUPPORTED;
     if (!device_accessible(X) || !device_accessible(V) || !device_accessible(out)) return CIQ_ERR_ARG;
     keep_pool_warm();
     ciq_options o;
     ciq_default_options(&o);
     o.max_iter = 1;
+    o.precision = precision;
     Plan<R> p = make_plan<R>(N, d, T, 1, o, false, tc);
     char* base = nullptr;
     ciq_status rc = CIQ_OK;
@@ -689,7 +693,7 @@ ciq_status kernel_mvm_impl(const R* X, int64_t N, int d, const ciq_kernel* kern,
     {
         p.layout(base);
         CIQ_TRY(launch_prepare_points<R, R>(X, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
-        CIQ_TRY(tc_prepare(p, precision, st));
+        CIQ_TRY(tc_prepare(p, kern->type, st));
         // Zero-padded copy of V (the MVM reads whole tiles).
         CIQ_TRY(cudaMemsetAsync(p.QA, 0, sizeof(R) * (size_t)T * p.Npad, st));
         CIQ_TRY(cudaMemcpy2DAsync(p.QA, sizeof(R) * p.Npad, V, sizeof(R) * N, sizeof(R) * N, T,
@@ -700,7 +704,7 @@ ciq_status kernel_mvm_impl(const R* X, int64_t N, int d, const ciq_kernel* kern,
         a.V = p.QA;
         a.out = out;
         a.ldo = N;
-        CIQ_TRY(launch_mvm(p, a, precision, st));
+        CIQ_TRY(launch_mvm(p, a, false, st));
     }
 done:
     cudaFreeAsync(base, st);
@@ -739,7 +743,7 @@ size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* op
     ciq_default_options(&o);
     if (opt) o = *opt;
     const bool prepass = !(o.quad_w && o.quad_t) && !(o.lmin > 0.0 && o.lmax > 0.0);
-    const bool tc = o.precision != CIQ_PREC_FP32 && tc_supported(o.precision, d);
+    const bool tc = o.precision != CIQ_PREC_FP32 && tc_supported(o.precision, d) && tc_padded_t(T) > 0;
     Plan<float> p = make_plan<float>(N, d, T, Q, o, prepass, tc);
     return p.bytes;
 }

@@ -33,6 +33,26 @@ struct MvmArgs {
     const int* stop;       // optional: skip the launch when *stop != 0
 };
 
+// Epilogue of one output entry O[i][col] (before the noise term): kPlain
+// stores O + sigma^2 v; kLanczos forms p = O + sigma^2 v - beta q_prev (0 on
+// padded rows), writes it over q_prev and accumulates q.p, p.p, q.q in FP64.
+template <typename R>
+__device__ __forceinline__ void lanczos_epilogue_value(const MvmArgs<R>& a, int64_t i, int col, R o,
+                                                       double& qp, double& pp, double& qq) {
+    const int64_t idx = (int64_t)col * a.ldv + i;
+    const R v = a.V[idx];
+    o += a.noise * v;
+    if (a.mode == kPlain) {
+        if (i < a.N) a.out[(int64_t)col * a.ldo + i] = o;
+        return;
+    }
+    R p = (i < a.N) ? (R)(o - (R)a.beta[col] * a.qprev[idx]) : (R)0;
+    a.qprev[idx] = p;
+    qp += (double)v * (double)p;
+    pp += (double)p * (double)p;
+    qq += (double)v * (double)v;
+}
+
 // Number of row tiles (entries of `partials`) the SIMT MVM uses for T columns.
 template <typename R>
 int64_t mvm_simt_row_tiles(int64_t Npad, int T);

@@ -21,23 +21,6 @@ namespace ciq {
 
 namespace {
 
-template <typename R>
-__device__ __forceinline__ void lanczos_epilogue_value(const MvmArgs<R>& a, int64_t i, int col, R o,
-                                                       double& qp, double& pp, double& qq) {
-    const int64_t idx = (int64_t)col * a.ldv + i;
-    const R v = a.V[idx];
-    o += a.noise * v;
-    if (a.mode == kPlain) {
-        if (i < a.N) a.out[(int64_t)col * a.ldo + i] = o;
-        return;
-    }
-    R p = (i < a.N) ? (R)(o - (R)a.beta[col] * a.qprev[idx]) : (R)0;
-    a.qprev[idx] = p;
-    qp += (double)v * (double)p;
-    pp += (double)p * (double)p;
-    qq += (double)v * (double)v;
-}
-
 template <typename R, int KT, int TC, int DP>
 __global__ void __launch_bounds__(256) mvm_narrow(MvmArgs<R> a) {
     if (a.stop && *a.stop) return;

@@ -1,17 +1,631 @@
-// Tensor-core (tcgen05) on-the-fly kernel MVM.
+// On-the-fly kernel MVM on the tcgen05 tensor cores (sm_103a).
+//
+// O = (K_XX + sigma^2 I) V without storing K (the map-reduce MVM of Sec. 3.3).
+// One CTA owns 128 rows of K and streams the points and V in tiles of 64:
+//
+//   S   = U_i V_j^T on tensor cores, kind::f16, accumulator in TMEM.  Rows are
+//         augmented, u = [c(x - m), -c^2 |x - m|^2 / 2, 1] and v = [c(x - m), 1,
+//         -c^2 |x - m|^2 / 2], so S = -c^2 r^2 / 2 directly (norm expansion of
+//         the distance; m is the centre of the points).  Each operand is split
+//         into a 16-bit leading part and a 16-bit trailing part and S =
+//         U_h V_h + U_h V_l + U_l V_h (three K-chunks of one MMA sequence):
+//         about 22 significant bits with FP16 parts.
+//   P   = k(r) / s from S on the SFU (RBF: ex2(S) with c^2 = log2 e; Matern-5/2:
+//         a = sqrt(-10 S), (1 + a + a^2/3) ex2(-a log2 e)), split again into
+//         leading/trailing 16-bit parts and stored to shared memory in the
+//         canonical K-major layout.
+//   O  += P_h Vt_h + P_h Vt_l + P_l Vt_h on tensor cores, accumulator in TMEM,
+//         with Vt = V times a power of two per column, split like U.
+//
+// The operands are pre-arranged in global memory in the shared-memory layout
+// of the MMA, so every tile is one bulk copy (cp.async.bulk) completing on
+// an mbarrier, double-buffered.  The epilogue reads O from TMEM and applies
+// the same Lanczos epilogue as the CUDA-core MVM.  Every wait is bounded: on
+// timeout the CTA records an error flag, skips the rest and frees its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
 #include "mvm_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace ciq {
 
-bool tc_supported(int precision, int d) { (void)precision; (void)d; return false; }
-int64_t tc_row_tiles(int64_t Npad) { return Npad / 128; }
-size_t tc_points_bytes(int64_t Npad, int d) { (void)Npad; (void)d; return 0; }
-TcPoints tc_points_layout(char* base, int64_t Npad, int d) { (void)Npad; (void)d; TcPoints p; p.a = base; return p; }
-cudaError_t launch_tc_prepare(const TcPoints&, const float*, int64_t, int, int, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr long long kWaitLimit = 4000000000LL;   // clock cycles, ~2 s at 2 GHz
+constexpr int kUBytes = kTcBM * kTcRowBytes;      // 12 KiB
+constexpr int kXBytes = kTcBN * kTcRowBytes;      // 6 KiB
+constexpr int kPPart = kTcBM * kTcBN * 2;         // 16 KiB per 16-bit part
+
+template <bool HALF>
+__device__ __forceinline__ uint16_t to16(float x) {
+    if (HALF) return __half_as_ushort(__float2half_rn(x));
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
-cudaError_t launch_mvm_tc(const TcPoints&, const MvmArgs<float>&, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+template <bool HALF>
+__device__ __forceinline__ float from16(uint16_t u) {
+    if (HALF) return __half2float(__ushort_as_half(u));
+    return __bfloat162float(__ushort_as_bfloat16(u));
+}
+
+__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) {
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// Convert a pair to 16-bit leading parts (packed) and the trailing parts.
+template <bool HALF>
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+    if (HALF) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 f = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 f = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - f.x, b - f.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
+}
+
+// ---------------------------------------------------------- operand prep --
+__global__ void tc_mean_kernel(const float* Xp, int64_t N, int dp, double* mean) {
+    double acc[kMaxDimPad];
+#pragma unroll
+    for (int k = 0; k < kMaxDimPad; ++k) acc[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < dp; ++k) acc[k] += (double)Xp[i * dp + k];
+    for (int k = 0; k < dp; ++k) {
+        const double v = warp_sum(acc[k]);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&mean[k], v / (double)N);
+    }
+}
+
+// One thread per row: u, v augmented and split, written in the operand layout
+// [row/8][chunk 0..2][K-core 0..1][row%8][element%8] (16-bit elements).
+template <bool HALF>
+__global__ void tc_points_kernel(const float* Xp, int64_t N, int64_t Npad, int dp, int d, float c,
+                                 float c2half, const double* mean, uint8_t* ua, uint8_t* ub) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= Npad) return;
+    float u[16], v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { u[k] = 0.f; v[k] = 0.f; }
+    if (row < N) {
+        float n2 = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float xc = Xp[row * dp + k] - (float)mean[k];
+            n2 = fmaf(xc, xc, n2);
+            u[k] = c * xc;
+            v[k] = c * xc;
+        }
+        u[d] = -c2half * n2;
+        u[d + 1] = 1.f;
+        v[d] = 1.f;
+        v[d + 1] = -c2half * n2;
+    }
+    uint16_t uh[16], ul[16], vh[16], vl[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        uh[k] = to16<HALF>(u[k]);
+        ul[k] = to16<HALF>(u[k] - from16<HALF>(uh[k]));
+        vh[k] = to16<HALF>(v[k]);
+        vl[k] = to16<HALF>(v[k] - from16<HALF>(vh[k]));
+    }
+    const uint16_t* achunk[3] = {uh, uh, ul};
+    const uint16_t* bchunk[3] = {vh, vl, vh};
+    const size_t base = (size_t)(row >> 3) * kTcRowBytes * 8 + (size_t)(row & 7) * 16;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {
+            const uint16_t* a = achunk[ch] + kc * 8;
+            const uint16_t* b = bchunk[ch] + kc * 8;
+            const size_t off = base + (size_t)ch * 256 + (size_t)kc * 128;
+            *reinterpret_cast<uint4*>(ua + off) =
+                make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
+            *reinterpret_cast<uint4*>(ub + off) =
+                make_uint4(pack2(b[0], b[1]), pack2(b[2], b[3]), pack2(b[4], b[5]), pack2(b[6], b[7]));
+        }
+    }
+}
+
+// Power-of-two scale per column so the scaled entries sit near 1.
+__global__ void tc_vscale_kernel(const float* V, int64_t ldv, int64_t N, int T, int TP, float unit_scale,
+                                 int unit, float* vscale) {
+    const int c = blockIdx.x;
+    if (c >= TP) return;
+    if (unit || c >= T) {
+        if (threadIdx.x == 0) vscale[c] = unit_scale;
+        return;
+    }
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double x = V[(int64_t)c * ldv + i];
+        acc += x * x;
+    }
+    __shared__ double red[8];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        const double nrm = sqrt(s);
+        float sc = 1.f;
+        if (nrm > 0.0) sc = ldexpf(1.f, (int)floor(log2(sqrt((double)N) / nrm)));
+        vscale[c] = sc;
+    }
+}
+
+// One thread per (column, 8 consecutive rows): scaled V split into the
+// B-operand layout.  Columns come in launch groups of tpg; group g holds
+// [tile][part][col/8][K-core][col%8][row%8] at vblk + g * (Npad/64) * 2 tpg 128.
+template <bool HALF>
+__global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
+                                  const float* vscale, uint8_t* vblk) {
+    const int64_t groups = Npad / 8;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= groups * TP) return;
+    const int c = (int)(idx / groups);
+    const int64_t j0 = (idx % groups) * 8;
+    float x[8];
+    if (c < T) {
+        const float4 a = *reinterpret_cast<const float4*>(V + (int64_t)c * ldv + j0);
+        const float4 b = *reinterpret_cast<const float4*>(V + (int64_t)c * ldv + j0 + 4);
+        const float s = vscale[c];
+        x[0] = a.x * s; x[1] = a.y * s; x[2] = a.z * s; x[3] = a.w * s;
+        x[4] = b.x * s; x[5] = b.y * s; x[6] = b.z * s; x[7] = b.w * s;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = 0.f;
+    }
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) split_pair<HALF>(x[2 * e], x[2 * e + 1], h[e], l[e]);
+    const int g = c / tpg, cl = c % tpg;
+    const int64_t tile_bytes = 2 * (int64_t)tpg * 128;
+    uint8_t* base = vblk + (int64_t)g * (Npad / kTcBN) * tile_bytes + (j0 / kTcBN) * tile_bytes;
+    const int jj = (int)(j0 % kTcBN);
+    const int64_t off = (int64_t)(cl >> 3) * 1024 + (jj >> 3) * 128 + (cl & 7) * 16;
+    *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(base + (int64_t)tpg * 128 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int TP>
+__host__ __device__ constexpr int tc_stages() {
+    return TP <= 64 ? 3 : 2;
+}
+
+// Tiles of K's columns accumulated in TMEM before the partial sum is folded
+// into the compensated running sum (keeps the tensor core's FP32 accumulation
+// to 16 x 4 x 3 = 192 steps per partial sum).
+constexpr int kTcChunk = 16;
+
+// TMEM: S buffers [0, 64) and [64, 128); O [128, 128 + TP); running sum
+// leading part [128 + TP, 128 + 2 TP) and trailing part [128 + 2 TP, 128 + 3 TP).
+template <int TP>
+__host__ __device__ constexpr uint32_t tmem_cols() {
+    return (2 * kTcBN + 3 * TP <= 256) ? 256u : 512u;
+}
+
+template <int TP>
+__host__ __device__ constexpr int tc_smem_bytes() {
+    return kUBytes + tc_stages<TP>() * (kXBytes + 2 * TP * 128) + 2 * (2 * kPPart) + 256;
+}
+
+// Barrier slots in shared memory.
+enum TcBar {
+    kBarU = 0,             // U tile landed
+    kBarLoadFull = 1,      // [NS] X/V stage landed
+    kBarLoadFree = 4,      // [NS] X/V stage consumed by both products
+    kBarSFull = 7,         // [2] S buffer written by the MMA
+    kBarSFree = 9,         // [2] S buffer read by its exp warpgroup
+    kBarPFull = 11,        // [2] P buffer written by its exp warpgroup
+    kBarPFree = 13,        // [2] P buffer consumed by the second product
+    kBarOChunk = 15,       // a chunk of O is complete (to be folded)
+    kBarOFree = 16,        // O folded into the running sum, accumulator free
+    kBarOFull = 17,        // last chunk of O complete
+    kBarCount = 18
+};
+
+// Kernel value / outputscale from S = -c^2 r^2 / 2 (RBF: S <= 0 up to
+// rounding, and ex2 of a rounding-level positive S is harmless).
+template <int KT>
+__device__ __forceinline__ float p_of_s(float S) {
+    if (KT == CIQ_RBF) return ex2_approx(S);
+    const float a = sqrt_approx(fmaxf(-10.f * S, 0.f));
+    return fmaf(a, fmaf(a, 1.0f / 3.0f, 1.0f), 1.0f) * ex2_approx(a * (float)(-kLog2e));
+}
+
+// --------------------------------------------------------------- kernel --
+// Warp roles (384 threads): warp 0 lane 0 issues the bulk copies, warp 1
+// lane 0 issues the MMAs, warps 4-7 and 8-11 are two exp warpgroups taking
+// even and odd tiles (S and P double-buffered).  Warps 8-11 also fold each
+// completed chunk of O into the running sum; warps 4-7 run the epilogue.
+// Tensor pipe order: S(t) = U X_t^T, then O += P(t-1) V(t-1), so the exp of
+// one tile overlaps the products of its neighbours.  Columns [c0, c0 + TP)
+// of V (those below a.T) are handled.
+template <int KT, int TP, bool HALF>
+__global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
+    if (a.stop && *a.stop) return;
+    constexpr int NS = tc_stages<TP>();
+    constexpr int VBYTES = 2 * TP * 128;
+    constexpr int PBUF = 2 * kPPart;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sU = smem;
+    uint8_t* sX0 = sU + kUBytes;
+    uint8_t* sV0 = sX0 + NS * kXBytes;
+    uint8_t* sP0 = sV0 + NS * VBYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sP0 + 2 * PBUF);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kBarCount);
+    volatile int* serr = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t tile = blockIdx.x;
+    const int64_t i0 = tile * kTcBM;
+    const int nt = (int)(a.Npad / kTcBN);
+    const int nfold = (nt - 1) / kTcChunk;               // chunks folded before the last one
+    constexpr uint32_t NCOLS = tmem_cols<TP>();
+    constexpr uint32_t IDESC_S = tc::idesc_f16(kTcBM, kTcBN, !HALF);
+    constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
+
+    if (tid == 0) {
+        tc::mbar_init(&bars[kBarU], 1);
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&bars[kBarLoadFull + s], 1);
+            tc::mbar_init(&bars[kBarLoadFree + s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&bars[kBarSFull + b], 1);
+            tc::mbar_init(&bars[kBarSFree + b], 128);
+            tc::mbar_init(&bars[kBarPFull + b], 128);
+            tc::mbar_init(&bars[kBarPFree + b], 1);
+        }
+        tc::mbar_init(&bars[kBarOChunk], 1);
+        tc::mbar_init(&bars[kBarOFree], 128);
+        tc::mbar_init(&bars[kBarOFull], 1);
+        tc::fence_mbarrier_init();
+        *serr = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, NCOLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tO = tmem + 2 * kTcBN;
+    const uint32_t tRh = tO + TP;
+    const uint32_t tRl = tO + 2 * TP;
+    const uint8_t* vblk = p.vblk;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- loader
+        if (lane == 0) {
+            tc::mbar_expect_tx(&bars[kBarU], kUBytes);
+            tc::bulk_g2s(sU, p.ua + tile * kUBytes, kUBytes, &bars[kBarU]);
+            for (int t = 0; t < nt && !*serr; ++t) {
+                const int st = t % NS;
+                if (t >= NS && !tc::mbar_wait(&bars[kBarLoadFree + st], (uint32_t)((t / NS - 1) & 1), kWaitLimit)) {
+                    *serr = 1;
+                    break;
+                }
+                tc::mbar_expect_tx(&bars[kBarLoadFull + st], kXBytes + VBYTES);
+                tc::bulk_g2s(sX0 + st * kXBytes, p.ub + (int64_t)t * kXBytes, kXBytes, &bars[kBarLoadFull + st]);
+                tc::bulk_g2s(sV0 + st * VBYTES, vblk + (int64_t)t * VBYTES, VBYTES, &bars[kBarLoadFull + st]);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t aU = tc::smem_u32(sU);
+            auto product = [&](int u) -> bool {     // O (+)= P(u) V(u)
+                const int bu = u & 1, su = u % NS;
+                const bool fresh = (u % kTcChunk) == 0;
+                if (fresh && u > 0 &&
+                    !tc::mbar_wait(&bars[kBarOFree], (uint32_t)((u / kTcChunk - 1) & 1), kWaitLimit))
+                    return false;
+                if (!tc::mbar_wait(&bars[kBarPFull + bu], (uint32_t)((u >> 1) & 1), kWaitLimit)) return false;
+                tc::fence_after_sync();
+                const uint32_t aP = tc::smem_u32(sP0 + bu * PBUF);
+                const uint32_t aV = tc::smem_u32(sV0 + su * VBYTES);
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                    const uint32_t pa = aP + (g == 2 ? kPPart : 0);
+                    const uint32_t vb = aV + (g == 1 ? TP * 128 : 0);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_f16(tO, tc::smem_desc(pa + kk * 256, 128, 1024),
+                                    tc::smem_desc(vb + kk * 256, 128, 1024), IDESC_O,
+                                    (!fresh || g > 0 || kk > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(&bars[kBarPFree + bu]);
+                tc::mma_commit(&bars[kBarLoadFree + su]);
+                if ((u % kTcChunk) == kTcChunk - 1 && u != nt - 1) tc::mma_commit(&bars[kBarOChunk]);
+                return true;
+            };
+            bool good = tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
+            for (int t = 0; t < nt && good && !*serr; ++t) {
+                const int st = t % NS, b = t & 1;
+                good = tc::mbar_wait(&bars[kBarLoadFull + st], (uint32_t)((t / NS) & 1), kWaitLimit);
+                if (good && t >= 2) good = tc::mbar_wait(&bars[kBarSFree + b], (uint32_t)(((t >> 1) - 1) & 1), kWaitLimit);
+                if (!good) break;
+                tc::fence_after_sync();
+                const uint32_t aX = tc::smem_u32(sX0 + st * kXBytes);
+                const uint32_t tS = tmem + b * kTcBN;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    tc::mma_f16(tS, tc::smem_desc(aU + ch * 256, 128, 768), tc::smem_desc(aX + ch * 256, 128, 768),
+                                IDESC_S, ch > 0 ? 1u : 0u);
+                tc::mma_commit(&bars[kBarSFull + b]);
+                if (t >= 1) good = product(t - 1);
+            }
+            if (good) good = product(nt - 1);
+            if (good) tc::mma_commit(&bars[kBarOFull]);
+            if (!good) *serr = 1;
+        }
+    } else if (warp >= 4) {
+        // --------------------------------------------------- exp warpgroups
+        const int g = (warp - 4) >> 2;                    // 0: even tiles, 1: odd tiles
+        const int r = 32 * (warp & 3) + lane;             // row in the tile = TMEM lane
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const uint32_t tS = tmem + g * kTcBN + lane_base;
+        uint8_t* sP = sP0 + g * PBUF;
+        const int base = (r >> 3) * 1024 + (r & 7) * 16;
+        for (int t = g; t < nt; t += 2) {
+            const int k = t >> 1;
+            bool good = tc::mbar_wait(&bars[kBarSFull + g], (uint32_t)(k & 1), kWaitLimit);
+            if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
+            tc::fence_after_sync();
+            uint32_t s0[32], s1[32];
+            tc::tmem_ld32(tS, s0);
+            tc::tmem_ld32(tS + 32, s1);
+            tc::fence_before_sync();
+            tc::mbar_arrive(&bars[kBarSFree + g]);
+            uint32_t hq[32], lq[32];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float pa = p_of_s<KT>(__uint_as_float(s0[2 * e]));
+                const float pb = p_of_s<KT>(__uint_as_float(s0[2 * e + 1]));
+                split_pair<HALF>(pa, pb, hq[e], lq[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float pa = p_of_s<KT>(__uint_as_float(s1[2 * e]));
+                const float pb = p_of_s<KT>(__uint_as_float(s1[2 * e + 1]));
+                split_pair<HALF>(pa, pb, hq[16 + e], lq[16 + e]);
+            }
+            if (t >= 2) {
+                good = tc::mbar_wait(&bars[kBarPFree + g], (uint32_t)((k - 1) & 1), kWaitLimit);
+                if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
+            }
+#pragma unroll
+            for (int jc = 0; jc < 8; ++jc) {
+                *reinterpret_cast<uint4*>(sP + base + jc * 128) =
+                    make_uint4(hq[4 * jc], hq[4 * jc + 1], hq[4 * jc + 2], hq[4 * jc + 3]);
+                *reinterpret_cast<uint4*>(sP + kPPart + base + jc * 128) =
+                    make_uint4(lq[4 * jc], lq[4 * jc + 1], lq[4 * jc + 2], lq[4 * jc + 3]);
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&bars[kBarPFull + g]);
+            // Fold a completed chunk of O into the running sum (odd warpgroup).
+            if (g == 1 && (t % kTcChunk) == kTcChunk - 1 && t != nt - 1) {
+                const int c = t / kTcChunk;
+                good = tc::mbar_wait(&bars[kBarOChunk], (uint32_t)(c & 1), kWaitLimit);
+                if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
+                tc::fence_after_sync();
+#pragma unroll 1
+                for (int cc = 0; cc < TP / 32; ++cc) {
+                    uint32_t o[32], rh[32], rl[32];
+                    tc::tmem_ld32(tO + lane_base + 32 * cc, o);
+                    if (c > 0) {
+                        tc::tmem_ld32(tRh + lane_base + 32 * cc, rh);
+                        tc::tmem_ld32(tRl + lane_base + 32 * cc, rl);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        float h = c > 0 ? __uint_as_float(rh[e]) : 0.f;
+                        float l = c > 0 ? __uint_as_float(rl[e]) : 0.f;
+                        two_sum_into(h, l, __uint_as_float(o[e]));
+                        rh[e] = __float_as_uint(h);
+                        rl[e] = __float_as_uint(l);
+                    }
+                    tc::tmem_st32(tRh + lane_base + 32 * cc, rh);
+                    tc::tmem_st32(tRl + lane_base + 32 * cc, rl);
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&bars[kBarOFree]);
+            }
+        }
+    }
+
+    // ------------------------------------------------------------ epilogue
+    double* red = reinterpret_cast<double*>(sP0);         // [4 warps][TP][3], free once O is complete
+    if (warp >= 4 && warp < 8) {
+        const int r = 32 * (warp & 3) + lane;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        bool good = !*serr && tc::mbar_wait(&bars[kBarOFull], 0, kWaitLimit);
+        const bool ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
+        if (!ok) *serr = 1;
+        tc::fence_after_sync();
+        const int64_t i = i0 + r;
+        const double outscale = a.s;
+        const int wl = warp & 3;
+#pragma unroll 1
+        for (int cc = 0; cc < TP / 32; ++cc) {
+            uint32_t o[32], rh[32], rl[32];
+            if (ok) {
+                tc::tmem_ld32(tO + lane_base + 32 * cc, o);
+                if (nfold > 0) {
+                    tc::tmem_ld32(tRh + lane_base + 32 * cc, rh);
+                    tc::tmem_ld32(tRl + lane_base + 32 * cc, rl);
+                }
+            }
+#pragma unroll 1
+            for (int e = 0; e < 32; ++e) {
+                const int cl = 32 * cc + e;
+                const int c = c0 + cl;
+                if (c >= a.T) break;
+                double qp = 0.0, pp = 0.0, qq = 0.0;
+                if (ok) {
+                    double sum = (double)__uint_as_float(o[e]);
+                    if (nfold > 0) sum += (double)__uint_as_float(rh[e]) + (double)__uint_as_float(rl[e]);
+                    const float val = (float)(sum * (outscale / (double)p.vscale[c]));
+                    lanczos_epilogue_value(a, i, c, val, qp, pp, qq);
+                }
+                if (a.mode == kLanczos) {
+                    qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
+                    if (lane == 0) {
+                        red[(wl * TP + cl) * 3 + 0] = qp;
+                        red[(wl * TP + cl) * 3 + 1] = pp;
+                        red[(wl * TP + cl) * 3 + 2] = qq;
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (a.mode == kLanczos) {
+        const int ncol = min(TP, a.T - c0);
+        for (int cl = tid; cl < ncol; cl += blockDim.x) {
+            double* dst = a.partials + ((int64_t)tile * a.T + c0 + cl) * 3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                dst[k] = red[(0 * TP + cl) * 3 + k] + red[(1 * TP + cl) * 3 + k] + red[(2 * TP + cl) * 3 + k] +
+                         red[(3 * TP + cl) * 3 + k];
+        }
+    }
+    if (tid == 0 && *serr) atomicExch(p.err, 1);
+    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+template <int KT, int TP, bool HALF>
+cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaStream_t st) {
+    constexpr int smem = tc_smem_bytes<TP>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(mvm_tc_kernel<KT, TP, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    mvm_tc_kernel<KT, TP, HALF><<<(unsigned)(a.Npad / kTcBM), 384, smem, st>>>(p, a, c0);
+    return cudaGetLastError();
+}
+
+template <int KT, bool HALF>
+cudaError_t launch_kt_half(const TcPoints& p, const MvmArgs<float>& a, int tpg, int c0, cudaStream_t st) {
+    switch (tpg) {
+        case 32: return launch_tp<KT, 32, HALF>(p, a, c0, st);
+        case 64: return launch_tp<KT, 64, HALF>(p, a, c0, st);
+        case 128: return launch_tp<KT, 128, HALF>(p, a, c0, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool tc_supported(int precision, int d) {
+    return (precision == CIQ_PREC_BF16 || precision == CIQ_PREC_FP16) && d >= 1 && d <= 14;
+}
+
+// Columns of V per MVM launch group (T > 128 runs as groups of 128; the
+// TMEM loads and stores move 32 columns, so a group is at least 32 wide).
+int tc_group_t(int T) {
+    if (T <= 32) return 32;
+    if (T <= 64) return 64;
+    return 128;
+}
+
+int tc_padded_t(int T) {
+    if (T < 1 || T > 1024) return -1;
+    const int g = tc_group_t(T);
+    return (T + g - 1) / g * g;
+}
+
+int64_t tc_row_tiles(int64_t Npad) { return Npad / kTcBM; }
+
+size_t tc_points_bytes(int64_t Npad, int T) {
+    const int TP = tc_padded_t(T);
+    if (TP < 0) return 0;
+    const size_t pts = (size_t)Npad * kTcRowBytes;
+    const size_t vb = (size_t)(Npad / kTcBN) * 2 * TP * 128;
+    return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256;
+}
+
+TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision) {
+    TcPoints p;
+    p.Npad = Npad;
+    p.TP = tc_padded_t(T);
+    p.half = precision == CIQ_PREC_FP16 ? 1 : 0;
+    auto take = [&](size_t bytes) {
+        char* q = base;
+        base += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    const size_t pts = (size_t)Npad * kTcRowBytes;
+    p.ua = reinterpret_cast<uint8_t*>(take(pts));
+    p.ub = reinterpret_cast<uint8_t*>(take(pts));
+    p.vblk = reinterpret_cast<uint8_t*>(take((size_t)(Npad / kTcBN) * 2 * p.TP * 128));
+    p.vscale = reinterpret_cast<float*>(take((size_t)p.TP * sizeof(float)));
+    p.mean = reinterpret_cast<double*>(take(16 * sizeof(double)));
+    p.err = reinterpret_cast<int*>(take(sizeof(int)));
+    return p;
+}
+
+cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int dp, int d, int kt,
+                              cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(p.mean, 0, 16 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.err, 0, sizeof(int), st)) != cudaSuccess) return e;
+    tc_mean_kernel<<<148, 256, 0, st>>>(Xp, N, dp, p.mean);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double c2 = kt == CIQ_RBF ? kLog2e : 1.0;
+    const unsigned blocks = (unsigned)((p.Npad + 127) / 128);
+    if (p.half)
+        tc_points_kernel<true><<<blocks, 128, 0, st>>>(Xp, N, p.Npad, dp, d, (float)sqrt(c2), (float)(0.5 * c2),
+                                                       p.mean, p.ua, p.ub);
+    else
+        tc_points_kernel<false><<<blocks, 128, 0, st>>>(Xp, N, p.Npad, dp, d, (float)sqrt(c2), (float)(0.5 * c2),
+                                                        p.mean, p.ua, p.ub);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_columns, cudaStream_t st) {
+    if (p.TP < 0 || a.T > p.TP || a.Npad != p.Npad || a.ldv != a.Npad) return cudaErrorInvalidValue;
+    const float unit_scale = ldexpf(1.f, (int)floor(0.5 * log2((double)a.N)));
+    tc_vscale_kernel<<<p.TP, 256, 0, st>>>(a.V, a.ldv, a.N, a.T, p.TP, unit_scale, unit_columns ? 1 : 0, p.vscale);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t work = (a.Npad / 8) * p.TP;
+    if (p.half)
+        tc_split_v_kernel<true><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a.V, a.ldv, a.T, p.TP,
+                                                                                 tc_group_t(a.T), a.Npad,
+                                                                                 p.vscale, p.vblk);
+    else
+        tc_split_v_kernel<false><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a.V, a.ldv, a.T, p.TP,
+                                                                                  tc_group_t(a.T), a.Npad,
+                                                                                  p.vscale, p.vblk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // V is split into groups of tpg columns; group g's tiles start at
+    // vblk + g * (Npad / 64) * 2 * tpg * 128.
+    const int tpg = tc_group_t(a.T);
+    for (int c0 = 0; c0 < a.T && e == cudaSuccess; c0 += tpg) {
+        TcPoints pg = p;
+        pg.vblk = p.vblk + (size_t)(c0 / tpg) * (size_t)(a.Npad / kTcBN) * 2 * tpg * 128;
+        if (a.kt == CIQ_RBF)
+            e = p.half ? launch_kt_half<CIQ_RBF, true>(pg, a, tpg, c0, st) : launch_kt_half<CIQ_RBF, false>(pg, a, tpg, c0, st);
+        else
+            e = p.half ? launch_kt_half<CIQ_MATERN52, true>(pg, a, tpg, c0, st)
+                       : launch_kt_half<CIQ_MATERN52, false>(pg, a, tpg, c0, st);
+    }
+    return e;
 }
 
 }  // namespace ciq

@@ -5,18 +5,39 @@
 
 namespace ciq {
 
-// Device copies of the points in the operand formats of the tensor-core MVM.
+// Rows of K per CTA (the MMA M) and columns of K per pipeline step.
+constexpr int kTcBM = 128;
+constexpr int kTcBN = 64;
+// Bytes of one row of the augmented, split point operand: 3 chunks x 16
+// 16-bit elements (x scaled and centred, the half squared norm, 1; hi/lo).
+constexpr int kTcRowBytes = 96;
+
+// Device buffers of the tensor-core MVM (inside the solve workspace).
 struct TcPoints {
-    void* a = nullptr;        // augmented, split operand rows (format depends on precision)
-    size_t bytes = 0;
+    uint8_t* ua = nullptr;     // points as the M operand of S = U V^T   [Npad/8][3][2][8][8] 16-bit
+    uint8_t* ub = nullptr;     // points as the N operand                 same layout
+    uint8_t* vblk = nullptr;   // V split hi/lo, per 64-row tile          [Npad/64][2][TP/8][8][8][8]
+    float* vscale = nullptr;   // power-of-two scale per column of V      [TP]
+    double* mean = nullptr;    // centre of the points                    [16]
+    int* err = nullptr;        // set to 1 if a bounded wait gave up
+    int64_t Npad = 0;
+    int TP = 0;                // T rounded up to whole launch groups (32, 64 or k x 128)
+    int half = 0;              // 1: FP16 operands; 0: BF16
 };
 
 bool tc_supported(int precision, int d);
+int tc_padded_t(int T);
+int tc_group_t(int T);
 int64_t tc_row_tiles(int64_t Npad);
-size_t tc_points_bytes(int64_t Npad, int d);
-TcPoints tc_points_layout(char* base, int64_t Npad, int d);
-cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t Npad, int dp, int d,
-                              int precision, cudaStream_t st);
-cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, int precision, cudaStream_t st);
+size_t tc_points_bytes(int64_t Npad, int T);
+TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision);
+// Centre/scale/augment/split the points (Xp: Npad x dp, already divided by
+// the lengthscale) into ua/ub; clears the error flag.
+cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int dp, int d, int kt,
+                              cudaStream_t st);
+// Split V into vblk (unit_columns: every column has norm 1, so one fixed
+// power-of-two scale is used; otherwise per-column scales from the norms)
+// and run the tensor-core MVM with the epilogue of `a`.
+cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_columns, cudaStream_t st);
 
 }  // namespace ciq

@@ -1,0 +1,99 @@
+"""Tensor-core (tcgen05) MVM and solves against the FP64 oracle, through the C ABI.
+
+Precision modes split every 16-bit operand into a leading and a trailing part
+(three products: hi*hi + hi*lo + lo*hi).  With FP16 parts that keeps about 22
+significant bits; with BF16 parts 16 bits, which the norm expansion of the
+distance (terms of size |x/l|^2 that cancel) turns into larger absolute
+errors for small lengthscales.  The tensor core accumulates in FP32 with a
+bias that grows with the number of accumulation steps, so O is accumulated in
+chunks of 1,024 points and folded into a compensated sum; the 50,000-point
+check below guards that.
+
+Tolerances (relative, Frobenius): FP16 MVM 2e-5 (measured 2-7e-6); BF16 MVM
+1e-4 at lengthscale >= 0.2 (measured 1-3e-5); FP16 solves against the
+eigendecomposition 1e-3, the accuracy target of the mixed-precision mode.
+"""
+import numpy as np
+import pytest
+import torch
+
+import ciq_inputs as ci
+import paper_2006_11267_b300 as P
+from oracle import eig, kernels
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 2e-5), ("bf16", 1e-4)])
+@pytest.mark.parametrize("n,d,t,kind,ls", [(1000, 3, 8, "rbf", 0.3), (1000, 3, 16, "matern52", 0.3),
+                                           (1300, 6, 64, "rbf", 0.3), (2000, 12, 33, "matern52", 0.5),
+                                           (777, 2, 128, "rbf", 0.2), (5000, 6, 200, "rbf", 0.3),
+                                           (513, 5, 256, "matern52", 0.25), (129, 14, 1, "rbf", 1.0)])
+def test_tc_mvm_matches_oracle(prec, tol, n, d, t, kind, ls):
+    X = f32(ci.points(n + d, n, d))
+    V = f32(ci.rhs(n + t, n, t))
+    k = P.Kernel(kind, ls, 1.3, 1e-3)
+    ref = kernels.dense_K(X.astype(np.float64), kind, ls, 1.3, 1e-3) @ V.T.astype(np.float64)
+    out = P.ciq_kernel_mvm(torch.from_numpy(X).cuda(), k, torch.from_numpy(V).cuda(), precision=prec)
+    assert rel(out.cpu().numpy().T, ref) < tol
+
+
+def test_tc_mvm_fp16_small_lengthscale():
+    X = f32(ci.points(9, 900, 4))
+    V = f32(ci.rhs(10, 900, 17))
+    k = P.Kernel("matern52", 0.1, 1.0, 1e-2)
+    ref = kernels.dense_K(X.astype(np.float64), "matern52", 0.1, 1.0, 1e-2) @ V.T.astype(np.float64)
+    out = P.ciq_kernel_mvm(torch.from_numpy(X).cuda(), k, torch.from_numpy(V).cuda(), precision="fp16")
+    assert rel(out.cpu().numpy().T, ref) < 2e-5
+
+
+def test_tc_mvm_accumulation_at_50k_points_sampled_rows():
+    W = ci.THOMPSON_50K
+    X = f32(ci.points(W.seed, W.n, W.d))
+    V = f32(ci.rhs(W.seed, W.n, W.t))
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    out = P.ciq_kernel_mvm(torch.from_numpy(X).cuda(), k, torch.from_numpy(V).cuda(), precision="fp16")
+    rows = np.concatenate([np.arange(0, 64), np.arange(W.n - 64, W.n), np.arange(20000, 20128)])
+    Kr = kernels.kernel_matrix(X[rows].astype(np.float64), X.astype(np.float64), W.kernel, W.lengthscale,
+                               W.outputscale)
+    ref = Kr @ V.T.astype(np.float64) + W.noise * V.T[rows].astype(np.float64)
+    assert rel(out.cpu().numpy().T[rows], ref) < 2e-5
+
+
+@pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
+def test_tc_fp16_solve_against_eig_oracle(op):
+    X = f32(ci.points(20201106, 2048, 3))
+    B = f32(ci.rhs(20201106, 2048, 40))
+    k = P.Kernel("matern52", 0.2, 1.0, 1e-2)
+    K = kernels.dense_K(X.astype(np.float64), "matern52", 0.2, 1.0, 1e-2)
+    ref = (eig.sqrt_apply if op == "sqrt" else eig.invsqrt_apply)(K, B.T.astype(np.float64)).T
+    fn = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
+    out, info = fn(torch.from_numpy(X).cuda(), k, torch.from_numpy(B).cuda(), 15, 1e-4, stop_rule="errbound",
+                   max_iter=2000, precision="fp16")
+    assert info["status"] == 0
+    err = np.linalg.norm(out.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() < 1e-3
+
+
+def test_tc_fp16_full_size_square_root_property():
+    # K^{1/2}(K^{1/2} b) = K b on the 50,000-point RBF workload (error bound 1e-3 per solve).
+    W = ci.THOMPSON_50K
+    X = torch.from_numpy(f32(ci.points(W.seed, W.n, W.d))).cuda()
+    B = torch.from_numpy(f32(ci.rhs(W.seed, W.n, W.t))).cuda()
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    A, info = P.ciq_sqrt(X, k, B, W.q, 1e-3, stop_rule="errbound", max_iter=4000, precision="fp16")
+    assert info["status"] == 0
+    A2, _ = P.ciq_sqrt(X, k, A[:4].contiguous(), W.q, 1e-4, stop_rule="errbound", max_iter=4000, precision="fp16")
+    KB = P.ciq_kernel_mvm(X, k, B[:4].contiguous(), precision="fp32")
+    e = (torch.linalg.norm(A2 - KB, dim=1) / torch.linalg.norm(KB, dim=1)).cpu().numpy()
+    assert e.max() < 3e-4
