@@ -58,9 +58,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
+                    help="time only the kernel MVM on the first N points of the workload (for profiling)")
     return ap.parse_args()
 
 
@@ -161,6 +164,47 @@ def peaks():
                 "sm_max_mhz": 2032.0}, "fallback"
 
 
+def device_peaks():
+    """SFU ex2, FP32 and FP64 FMA rates measured on this device (libciq_peaks)."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2006_11267_b300", "libciq_peaks.so")
+    L = ctypes.CDLL(path)
+    out, ms = ctypes.c_double(), ctypes.c_double()
+    L.ciq_peak_sfu_ex2.argtypes = [ctypes.POINTER(ctypes.c_double)] * 2
+    L.ciq_peak_fma.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 2
+    res = {}
+    if L.ciq_peak_sfu_ex2(ctypes.byref(out), ctypes.byref(ms)) == 0:
+        res["sfu_ex2_per_s"] = out.value
+    if L.ciq_peak_fma(0, ctypes.byref(out), ctypes.byref(ms)) == 0:
+        res["fp32_flops"] = out.value
+    if L.ciq_peak_fma(1, ctypes.byref(out), ctypes.byref(ms)) == 0:
+        res["fp64_flops"] = out.value
+    return res
+
+
+def roofline_tc(W, t_launch_ms, dev, pk):
+    # One kernel MVM on tensor cores: N^2 kernel entries, each one SFU exp2
+    # (RBF) or exp2 + sqrt (Matern-5/2) -- the bound of the on-the-fly tile --
+    # and 2T (product with V) + 2(d+2) (augmented distance) algorithmic
+    # tensor flops; the operand split executes 3x those on the tensor pipe.
+    N, T, d = W.n, W.t, W.d
+    sfu_per_entry = 1 if W.kernel == "rbf" else 2
+    entries = float(N) * N
+    achieved = entries * sfu_per_entry / (t_launch_ms * 1e-3)
+    peak = dev.get("sfu_ex2_per_s")
+    tflops_alg = entries * (2 * T + 2 * (d + 2)) / (t_launch_ms * 1e-3) / 1e12
+    tp = max(32, -(-T // 32) * 32) if T <= 64 else -(-T // 128) * 128
+    tflops_exec = entries * 3 * (2 * tp + 2 * 16) / (t_launch_ms * 1e-3) / 1e12
+    return {"bound": "sfu", "achieved": achieved / 1e12, "peak": (peak or 0) / 1e12, "unit": "Tex2/s",
+            "frac": achieved / peak if peak else None, "traffic": None,
+            "kernel": "mvm_tc_kernel (tcgen05 on-the-fly kernel MVM, FP16 split operands)",
+            "peak_source": "measured by libciq_peaks (ex2.approx throughput, 8 CTAs x 256 threads per SM)",
+            "tensor": {"algorithmic_tflops": tflops_alg, "executed_tflops": tflops_exec,
+                       "peak_tflops": pk.get("bf16_tflops"),
+                       "frac_executed": tflops_exec / pk["bf16_tflops"] if pk.get("bf16_tflops") else None,
+                       "peak_note": "FP16 dense rate taken equal to the measured BF16 cuBLAS rate"}}
+
+
 def roofline_fp32(N, T, d, t_launch_ms, pk):
     # Algorithmic work of one kernel MVM on CUDA cores: 2 N^2 T flops for the
     # product with the T-column block plus 3 d N^2 flops for the distances.
@@ -234,6 +278,23 @@ def run_ours(args):
     def step(profile=0):
         return P.ciq_sqrt(Xd, k, Bd, W.q, TOL, out=out, profile=profile, **opts)[1]
 
+    if args.mvm_only:
+        n = args.mvm_only
+        Xs, Vs = Xd[:n].contiguous(), Bd[:, :n].contiguous()
+        for _ in range(max(1, args.warmup)):
+            P.ciq_kernel_mvm(Xs, k, Vs, precision=args.precision)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            P.ciq_kernel_mvm(Xs, k, Vs, precision=args.precision)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"mvm_only": n, "T": W.t, "precision": args.precision,
+                          "ms_per_call": e0.elapsed_time(e1) / args.steps}), flush=True)
+        return 0
+
     for _ in range(args.warmup):
         info = step()
     torch.cuda.synchronize()
@@ -268,8 +329,27 @@ def run_ours(args):
     t_mvm = pinfo["t_mvm_ms"] / max(1, pinfo["mvm_launches"])
     t_rec = pinfo["t_step_ms"] / max(1, pinfo["step_launches"])
     pk, pk_kind = peaks()
-    roof = roofline_fp32(W.n, W.t, W.d, t_mvm, pk)
-    roof["peak_source"] = pk_kind
+    dev = device_peaks()
+    if args.precision == "fp32":
+        roof = roofline_fp32(W.n, W.t, W.d, t_mvm, pk)
+        roof["peak_source"] = pk_kind
+    else:
+        roof = roofline_tc(W, t_mvm, dev, pk)
+    fp32 = None
+    if not args.no_fp32_compare and args.precision != "fp32":
+        o32 = dict(opts, precision="fp32")
+        P.ciq_sqrt(Xd, k, Bd, W.q, TOL, out=out, **o32)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        i32 = P.ciq_sqrt(Xd, k, Bd, W.q, TOL, out=out, **o32)[1]
+        f1.record()
+        torch.cuda.synchronize()
+        t32 = f0.elapsed_time(f1)
+        fp32 = {"value": W.t / (t32 * 1e-3), "ms_per_step": t32, "iterations": i32["iters"],
+                "speedup": (W.t / (t32 * 1e-3)) / (W.t * args.steps / (elapsed_ms * 1e-3) / world)}
+        fp32["speedup"] = 1.0 / fp32["speedup"]
     e2e = None
     if not args.no_e2e:
         out_h = np.empty_like(B)
@@ -294,7 +374,8 @@ def run_ours(args):
         it = [i["iters"] for i in infos]
         line = {"metric": "K^{1/2}b RHS-solves/s at rel err <=1e-3", "value": value, "unit": "RHS-solves/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else f"{args.precision}x2-split tiles, f32 vectors, f64 scalars",
                 "data": "synthetic",
                 "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
                            "noise": W.noise, "T": W.t, "Q": W.q, "op": "sqrt", "tol": TOL,
@@ -307,7 +388,8 @@ def run_ours(args):
                             "mvm_share": pinfo["t_mvm_ms"] / max(pinfo["t_total_ms"], 1e-9),
                             "recurrence_share": pinfo["t_step_ms"] / max(pinfo["t_total_ms"], 1e-9),
                             "prepass_ms": pinfo["t_prepass_ms"], "total_ms": pinfo["t_total_ms"]},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "plain_fp32_gpu_path": fp32, "device_peaks": dev}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -89,7 +89,8 @@ typedef enum {
 typedef enum {
     CIQ_MVM_AUTO = 0,         /* on-the-fly */
     CIQ_MVM_ONTHEFLY = 1,     /* K recomputed tile by tile every MVM, never stored */
-    CIQ_MVM_STORED = 2        /* K formed once in device memory (N^2 floats), streamed */
+    CIQ_MVM_STORED = 2        /* K formed once in the workspace (Npad^2 floats, FP32), streamed
+                                 every iteration; FP32 precision only */
 } ciq_mvm_mode;
 
 typedef enum {
@@ -200,13 +201,18 @@ ciq_status ciq_kernel_mvm(const float* X, int64_t N, int d, const ciq_kernel* ke
 ciq_status ciq_kernel_mvm_f64(const double* X, int64_t N, int d, const ciq_kernel* kern,
                               const double* V, int T, double* out, ciq_stream_t stream);
 
-/* Dense K = K_XX + sigma^2 I into device memory Kmat (row i at Kmat + i*ldk,
- * ldk >= N, FP32), for the stored-K MVM.  Asynchronous on stream. */
+/* Stored K for the stored-K MVM (the explicit-matrix case of Sec. 3.3,
+ * O(J N^2) with K resident): K = K_XX + sigma^2 I written in FP32 into
+ * device memory Kmat laid out as Npad = round_up(N, 128) rows of ldk floats
+ * (ldk >= Npad, ldk % 4 == 0); rows and columns in [N, Npad) are set to 0.
+ * The caller allocates Npad * ldk floats.  X: device.  Asynchronous on
+ * stream; CIQ_ERR_ARG on a bad size or host pointer. */
 ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel* kern,
                              float* Kmat, int64_t ldk, ciq_stream_t stream);
 
-/* out = Kmat V for a stored symmetric N x N matrix (device, leading
- * dimension ldk >= N, FP32); V, out: device, T columns of N floats.
+/* out = Kmat V for a matrix in the layout ciq_kernel_matrix writes (Npad
+ * rows of ldk floats, zero padding).  V, out: device, T columns of N floats.
+ * FP32 on CUDA cores, compensated accumulation; HBM-bound for T <= 16.
  * Asynchronous on stream. */
 ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T,
                           float* out, ciq_stream_t stream);

@@ -292,8 +292,10 @@ def ciq_kernel_matrix(X, kernel, Kmat):
     return Kmat
 
 
-def ciq_stored_mvm(Kmat, V, out=None):
-    N = Kmat.shape[0]
+def ciq_stored_mvm(Kmat, V, out=None, n=None):
+    """Kmat V for a matrix in the layout ciq_kernel_matrix writes
+    (round_up(N,128) rows of ldk floats); V and out are (T, N)."""
+    N = V.shape[1] if n is None else n
     T = V.shape[0]
     if out is None:
         out = V.new_empty(V.shape)

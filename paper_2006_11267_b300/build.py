@@ -16,6 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libciq.so")
+PEAKS_SRC = os.path.join(CSRC, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "libciq_peaks.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -57,6 +59,11 @@ def build(force: bool = False, jobs: int | None = None, verbose_ptxas: bool = Fa
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(PEAKS_LIB) < os.path.getmtime(PEAKS_SRC):
+        cmd = [NVCC, *ARCH, *FLAGS, "-shared", "-o", PEAKS_LIB, PEAKS_SRC, "-lcudart"]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"peaks build failed:\n{res.stdout}\n{res.stderr}")
     return LIB
 
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "krylov.cuh"
+#include "mvm_stored.cuh"
 #include "mvm_tc.cuh"
 #include "spectral.cuh"
 
@@ -110,12 +111,14 @@ struct Plan {
     int nparts, nparts1, nchunks, nchunks1;
     int64_t rpc, rpc1;
     bool tc;                      // tensor-core MVM
+    bool stored;                  // stored-K MVM (K formed once, Npad x Npad)
     int precision;
     bool stage_x, stage_b, stage_out, stage_start;
     bool prepass;
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB;
     R *sx, *sb, *sout, *sstart;
+    float* Kst;
     double *partials, *ynp, *beta, *beta1, *giv, *phifinal, *nodes, *summary;
     double *lpart, *lynp, *bpar, *lalpha, *lbeta;
     int *status, *iters, *brk, *cnt, *all_done, *jeff, *ldone;
@@ -166,6 +169,7 @@ struct Plan {
             char* q = a.take<char>(tc_points_bytes(Npad, T));
             tcp = tc_points_layout(q, Npad, T, precision);
         }
+        Kst = stored ? a.take<float>((size_t)Npad * Npad) : nullptr;
         bytes = a.off + kAlign;
     }
 };
@@ -183,8 +187,10 @@ Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool pre
     p.jmax = o.max_iter;
     p.JL = o.lanczos_iters;
     p.tc = tc;
-    p.nparts = tc ? (int)tc_row_tiles(p.Npad) : (int)mvm_simt_row_tiles<R>(p.Npad, T);
-    p.nparts1 = (int)mvm_simt_row_tiles<R>(p.Npad, 1);
+    p.stored = sizeof(R) == 4 && o.mvm == CIQ_MVM_STORED;
+    p.nparts = tc ? (int)tc_row_tiles(p.Npad)
+                  : p.stored ? (int)stored_row_tiles(p.Npad, T) : (int)mvm_simt_row_tiles<R>(p.Npad, T);
+    p.nparts1 = p.stored ? (int)stored_row_tiles(p.Npad, 1) : (int)mvm_simt_row_tiles<R>(p.Npad, 1);
     choose_chunks(p.Npad, T, &p.nchunks, &p.rpc);
     choose_chunks(p.Npad, 1, &p.nchunks1, &p.rpc1);
     p.prepass = prepass;
@@ -240,7 +246,7 @@ cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options
         a.V = (j & 1) ? p.LA : p.LB;
         a.qprev = (j & 1) ? p.LB : p.LA;
         a.beta = p.bpar + (j & 1);
-        if ((e = launch_mvm_simt(a, st)) != cudaSuccess) return e;
+        if ((e = p.stored ? launch_mvm(p, a, true, st) : launch_mvm_simt(a, st)) != cudaSuccess) return e;
         if ((e = launch_lanczos_step(ls, j, st)) != cudaSuccess) return e;
     }
     return launch_bounds_nodes(ls, p.nodes, Q, k.noise, o.lmax_margin, o.lmin_div, st);
@@ -260,8 +266,20 @@ template <typename R>
 cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
         if (p.tc) return launch_mvm_tc(p.tcp, a, unit_columns, st);
+        if (p.stored) return launch_stored_mvm(p.Kst, p.Npad, a, st);
     }
     return launch_mvm_simt(a, st);
+}
+
+// Form the stored K once (stored-K mode only).
+template <typename R>
+cudaError_t form_stored(const Plan<R>& p, const ciq_kernel& k, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (p.stored)
+            return launch_kernel_matrix(p.Xp, p.N, p.Npad, p.dp, k.type, (float)k.outputscale, (float)k.noise, p.Kst,
+                                        p.Npad, p.Npad, st);
+    }
+    return cudaSuccess;
 }
 
 // CUDA events of the profile mode: one event between consecutive launches of
@@ -308,7 +326,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED))
         return CIQ_ERR_ARG;
     if ((o.quad_w == nullptr) != (o.quad_t == nullptr)) return CIQ_ERR_ARG;
-    if (o.mvm == CIQ_MVM_STORED) return CIQ_ERR_UNSUPPORTED;
+    if (o.mvm == CIQ_MVM_STORED && !fp64 && o.precision != CIQ_PREC_FP32) return CIQ_ERR_UNSUPPORTED;
     bool tc = false;
     if (!fp64 && o.precision != CIQ_PREC_FP32) {
         if (!tc_supported(o.precision, d) || tc_padded_t(T) < 0) return CIQ_ERR_UNSUPPORTED;
@@ -381,10 +399,12 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_start, st));
         CIQ_TRY(launch_prepare_points<R, R>(Xd, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
         CIQ_TRY(tc_prepare(p, kern->type, st));
+        CIQ_TRY(form_stored(p, *kern, st));
+        launches += p.stored ? 1 : 0;
         KrylovState<R> s = krylov_state(p, op, o, tol);
         CIQ_TRY(launch_init_rhs(s, Bd, st));
         CIQ_TRY(launch_init_state(s, st));
-        launches += 3 + (p.tc ? 1 : 0);
+        launches += 3 + (p.tc ? 2 : 0);
         if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_pre0, st));
         if (given_nodes) {
             double hn[kNodeCount] = {0};
@@ -407,6 +427,9 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         a.mode = kLanczos;
         a.partials = p.partials;
         a.stop = p.all_done;
+        // Kernels per MVM: one on CUDA cores; on tensor cores the V scale,
+        // the V split and one launch per column group.
+        const int mvm_launches = p.tc ? 2 + (T + tc_group_t(T) - 1) / tc_group_t(T) : 1;
         CIQ_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
         CIQ_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         if (prof.on) {
@@ -446,7 +469,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
                     CIQ_TRY(launch_msminres_step(s, jj, false, st));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 2], st));
-                    launches += 2;
+                    launches += 1 + mvm_launches;
                 }
                 first_j[slot] = j;
                 count[slot] = jb - j + 1;
@@ -727,14 +750,54 @@ ciq_status ciq_kernel_mvm_f64(const double* X, int64_t N, int d, const ciq_kerne
 
 ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel* kern, float* Kmat,
                              int64_t ldk, ciq_stream_t stream) {
-    (void)X; (void)N; (void)d; (void)kern; (void)Kmat; (void)ldk; (void)stream;
-    return CIQ_ERR_UNSUPPORTED;
+    const int64_t Npad = round_up(N, kRowPad);
+    if (!X || !Kmat || N < 1 || d < 1 || d > CIQ_MAX_DIM || !valid_kernel(kern) || ldk < Npad || ldk % 4 != 0)
+        return CIQ_ERR_ARG;
+    if (!device_accessible(X) || !device_accessible(Kmat)) return CIQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_warm();
+    const int dp = dim_pad(d);
+    float* Xp = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&Xp), sizeof(float) * (size_t)Npad * dp, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    e = launch_prepare_points<float, float>(X, N, d, Npad, dp, 1.0 / kern->lengthscale, Xp, st);
+    if (e == cudaSuccess)
+        e = launch_kernel_matrix(Xp, N, Npad, dp, kern->type, (float)kern->outputscale, (float)kern->noise, Kmat, ldk,
+                                 Npad, st);
+    cudaFreeAsync(Xp, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    return CIQ_OK;
 }
 
 ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T, float* out,
                           ciq_stream_t stream) {
-    (void)Kmat; (void)N; (void)ldk; (void)V; (void)T; (void)out; (void)stream;
-    return CIQ_ERR_UNSUPPORTED;
+    const int64_t Npad = round_up(N, kRowPad);
+    if (!Kmat || !V || !out || N < 1 || T < 1 || ldk < Npad || ldk % 4 != 0) return CIQ_ERR_ARG;
+    if (!device_accessible(Kmat) || !device_accessible(V) || !device_accessible(out)) return CIQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_warm();
+    float* Vp = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&Vp), sizeof(float) * (size_t)T * Npad, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    e = cudaMemsetAsync(Vp, 0, sizeof(float) * (size_t)T * Npad, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(Vp, sizeof(float) * Npad, V, sizeof(float) * N, sizeof(float) * N, T,
+                              cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        MvmArgs<float> a{};
+        a.N = N;
+        a.Npad = Npad;
+        a.V = Vp;
+        a.ldv = Npad;
+        a.T = T;
+        a.mode = kPlain;
+        a.out = out;
+        a.ldo = N;
+        e = launch_stored_mvm(Kmat, ldk, a, st);
+    }
+    cudaFreeAsync(Vp, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    return CIQ_OK;
 }
 
 size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt) {

@@ -12,8 +12,9 @@
 //         about 22 significant bits with FP16 parts.
 //   P   = k(r) / s from S on the SFU (RBF: ex2(S) with c^2 = log2 e; Matern-5/2:
 //         a = sqrt(-10 S), (1 + a + a^2/3) ex2(-a log2 e)), split again into
-//         leading/trailing 16-bit parts and stored to shared memory in the
-//         canonical K-major layout.
+//         leading/trailing 16-bit parts and written back over S in tensor
+//         memory (tcgen05.st), so the product reads its A operand from TMEM
+//         and shared-memory bandwidth is left to the B operands and copies.
 //   O  += P_h Vt_h + P_h Vt_l + P_l Vt_h on tensor cores, accumulator in TMEM,
 //         with Vt = V times a power of two per column, split like U.
 //
@@ -196,9 +197,13 @@ __global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, in
     *reinterpret_cast<uint4*>(base + (int64_t)tpg * 128 + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Separate rings for the point tiles (released when S is computed) and the
+// V tiles (released when the product with P completes), as deep as shared
+// memory allows, so the bulk copies run well ahead of the MMAs.
+constexpr int kTcXStages = 8;
 template <int TP>
-__host__ __device__ constexpr int tc_stages() {
-    return TP <= 64 ? 3 : 2;
+__host__ __device__ constexpr int tc_vstages() {
+    return TP <= 64 ? 8 : 4;
 }
 
 // Tiles of K's columns accumulated in TMEM before the partial sum is folded
@@ -206,31 +211,42 @@ __host__ __device__ constexpr int tc_stages() {
 // to 16 x 4 x 3 = 192 steps per partial sum).
 constexpr int kTcChunk = 16;
 
-// TMEM: S buffers [0, 64) and [64, 128); O [128, 128 + TP); running sum
-// leading part [128 + TP, 128 + 2 TP) and trailing part [128 + 2 TP, 128 + 3 TP).
+// TMEM: NB S buffers of 64 columns, each overwritten by its P (leading part
+// in the first 32 columns, trailing part in the next 32, two 16-bit values
+// per column); O [64 NB, 64 NB + TP); running sum leading part
+// [64 NB + TP, 64 NB + 2 TP) and trailing part [64 NB + 2 TP, 64 NB + 3 TP).
+// Four S/P buffers when they fit (T <= 64), two otherwise: tile t uses
+// buffer t % NB and exp warpgroup t % 2, so each buffer serves one
+// warpgroup and its barrier phases advance one at a time.
+template <int TP>
+__host__ __device__ constexpr int tc_sbuffers() {
+    return (4 * kTcBN + 3 * TP <= 512) ? 4 : 2;
+}
+
 template <int TP>
 __host__ __device__ constexpr uint32_t tmem_cols() {
-    return (2 * kTcBN + 3 * TP <= 256) ? 256u : 512u;
+    return (tc_sbuffers<TP>() * kTcBN + 3 * TP <= 256) ? 256u : 512u;
 }
 
 template <int TP>
 __host__ __device__ constexpr int tc_smem_bytes() {
-    return kUBytes + tc_stages<TP>() * (kXBytes + 2 * TP * 128) + 2 * (2 * kPPart) + 256;
+    return kUBytes + kTcXStages * kXBytes + tc_vstages<TP>() * (2 * TP * 128) + 512;
 }
 
 // Barrier slots in shared memory.
 enum TcBar {
     kBarU = 0,             // U tile landed
-    kBarLoadFull = 1,      // [NS] X/V stage landed
-    kBarLoadFree = 4,      // [NS] X/V stage consumed by both products
-    kBarSFull = 7,         // [2] S buffer written by the MMA
-    kBarSFree = 9,         // [2] S buffer read by its exp warpgroup
-    kBarPFull = 11,        // [2] P buffer written by its exp warpgroup
-    kBarPFree = 13,        // [2] P buffer consumed by the second product
-    kBarOChunk = 15,       // a chunk of O is complete (to be folded)
-    kBarOFree = 16,        // O folded into the running sum, accumulator free
-    kBarOFull = 17,        // last chunk of O complete
-    kBarCount = 18
+    kBarXFull = 1,         // [8] point tile landed
+    kBarXFree = 9,         // [8] point tile consumed by S
+    kBarVFull = 17,        // [8] V tile landed
+    kBarVFree = 25,        // [8] V tile consumed by the product
+    kBarSFull = 33,        // [4] S buffer written by the MMA
+    kBarSFree = 37,        // [4] S/P buffer released by the product that read P
+    kBarPFull = 41,        // [4] P written over S by its exp warpgroup
+    kBarOChunk = 45,       // a chunk of O is complete (to be folded)
+    kBarOFree = 46,        // O folded into the running sum, accumulator free
+    kBarOFull = 47,        // last chunk of O complete
+    kBarCount = 48
 };
 
 // Kernel value / outputscale from S = -c^2 r^2 / 2 (RBF: S <= 0 up to
@@ -253,15 +269,15 @@ __device__ __forceinline__ float p_of_s(float S) {
 template <int KT, int TP, bool HALF>
 __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
     if (a.stop && *a.stop) return;
-    constexpr int NS = tc_stages<TP>();
+    constexpr int NX = kTcXStages;
+    constexpr int NV = tc_vstages<TP>();
+    constexpr int NB = tc_sbuffers<TP>();
     constexpr int VBYTES = 2 * TP * 128;
-    constexpr int PBUF = 2 * kPPart;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sU = smem;
     uint8_t* sX0 = sU + kUBytes;
-    uint8_t* sV0 = sX0 + NS * kXBytes;
-    uint8_t* sP0 = sV0 + NS * VBYTES;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sP0 + 2 * PBUF);
+    uint8_t* sV0 = sX0 + NX * kXBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sV0 + NV * VBYTES);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kBarCount);
     volatile int* serr = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -276,15 +292,18 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
 
     if (tid == 0) {
         tc::mbar_init(&bars[kBarU], 1);
-        for (int s = 0; s < NS; ++s) {
-            tc::mbar_init(&bars[kBarLoadFull + s], 1);
-            tc::mbar_init(&bars[kBarLoadFree + s], 1);
+        for (int s = 0; s < NX; ++s) {
+            tc::mbar_init(&bars[kBarXFull + s], 1);
+            tc::mbar_init(&bars[kBarXFree + s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int s = 0; s < NV; ++s) {
+            tc::mbar_init(&bars[kBarVFull + s], 1);
+            tc::mbar_init(&bars[kBarVFree + s], 1);
+        }
+        for (int b = 0; b < NB; ++b) {
             tc::mbar_init(&bars[kBarSFull + b], 1);
-            tc::mbar_init(&bars[kBarSFree + b], 128);
+            tc::mbar_init(&bars[kBarSFree + b], 1);
             tc::mbar_init(&bars[kBarPFull + b], 128);
-            tc::mbar_init(&bars[kBarPFree + b], 1);
         }
         tc::mbar_init(&bars[kBarOChunk], 1);
         tc::mbar_init(&bars[kBarOFree], 128);
@@ -300,94 +319,154 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t tO = tmem + 2 * kTcBN;
+    const uint32_t tO = tmem + NB * kTcBN;
     const uint32_t tRh = tO + TP;
     const uint32_t tRl = tO + 2 * TP;
     const uint8_t* vblk = p.vblk;
 
     if (warp == 0) {
         // ---------------------------------------------------------- loader
-        if (lane == 0) {
-            tc::mbar_expect_tx(&bars[kBarU], kUBytes);
-            tc::bulk_g2s(sU, p.ua + tile * kUBytes, kUBytes, &bars[kBarU]);
-            for (int t = 0; t < nt && !*serr; ++t) {
-                const int st = t % NS;
-                if (t >= NS && !tc::mbar_wait(&bars[kBarLoadFree + st], (uint32_t)((t / NS - 1) & 1), kWaitLimit)) {
-                    *serr = 1;
+        // Two independent rings, polled without blocking: point tile tx
+        // waits for S(tx - NX) to free its stage, V tile tv for the product
+        // of tile tv - NV.  The whole warp runs the loop (uniform control
+        // flow, addresses in uniform registers); one elected lane issues.
+        {
+            const bool leader = tc::elect_one();
+            if (leader) {
+                tc::mbar_expect_tx(&bars[kBarU], kUBytes);
+                tc::bulk_g2s(sU, p.ua + tile * kUBytes, kUBytes, &bars[kBarU]);
+            }
+            __syncwarp();
+            int tx = 0, tv = 0;
+            long long last = clock64();
+            while (tx < nt || tv < nt) {
+                if (__shfl_sync(0xffffffffu, (int)*serr, 0)) break;
+                bool progressed = false;
+                if (tx < nt) {
+                    const int st = tx % NX;
+                    const bool ok = tx < NX || tc::mbar_test(&bars[kBarXFree + st], (uint32_t)((tx / NX - 1) & 1));
+                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
+                        if (tc::elect_one()) {
+                            tc::mbar_expect_tx(&bars[kBarXFull + st], kXBytes);
+                            tc::bulk_g2s(sX0 + st * kXBytes, p.ub + (int64_t)tx * kXBytes, kXBytes,
+                                         &bars[kBarXFull + st]);
+                        }
+                        __syncwarp();
+                        ++tx;
+                        progressed = true;
+                    }
+                }
+                if (tv < nt) {
+                    const int st = tv % NV;
+                    const bool ok = tv < NV || tc::mbar_test(&bars[kBarVFree + st], (uint32_t)((tv / NV - 1) & 1));
+                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
+                        if (tc::elect_one()) {
+                            tc::mbar_expect_tx(&bars[kBarVFull + st], VBYTES);
+                            tc::bulk_g2s(sV0 + st * VBYTES, vblk + (int64_t)tv * VBYTES, VBYTES, &bars[kBarVFull + st]);
+                        }
+                        __syncwarp();
+                        ++tv;
+                        progressed = true;
+                    }
+                }
+                if (progressed) last = clock64();
+                else if (__shfl_sync(0xffffffffu, (int)(clock64() - last > kWaitLimit), 0)) {
+                    if (lane == 0) *serr = 1;
                     break;
                 }
-                tc::mbar_expect_tx(&bars[kBarLoadFull + st], kXBytes + VBYTES);
-                tc::bulk_g2s(sX0 + st * kXBytes, p.ub + (int64_t)t * kXBytes, kXBytes, &bars[kBarLoadFull + st]);
-                tc::bulk_g2s(sV0 + st * VBYTES, vblk + (int64_t)t * VBYTES, VBYTES, &bars[kBarLoadFull + st]);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        // Event-driven: S(g1) = U X^T is issued as soon as its S buffer and
+        // point tile are ready, O += P(g2) V(g2) as soon as P(g2) and its V
+        // tile are ready; S is preferred so the in-order tensor pipe never
+        // waits behind a product whose P is late.  Each barrier's next phase
+        // can only complete after this warp issues the matching MMA, so parity
+        // tests are unambiguous; test_wait never suspends the warp.  The whole
+        // warp runs the loop with uniform control flow, so the descriptors
+        // stay in uniform registers; one elected lane issues each MMA.
+        {
             const uint32_t aU = tc::smem_u32(sU);
-            auto product = [&](int u) -> bool {     // O (+)= P(u) V(u)
-                const int bu = u & 1, su = u % NS;
-                const bool fresh = (u % kTcChunk) == 0;
-                if (fresh && u > 0 &&
-                    !tc::mbar_wait(&bars[kBarOFree], (uint32_t)((u / kTcChunk - 1) & 1), kWaitLimit))
-                    return false;
-                if (!tc::mbar_wait(&bars[kBarPFull + bu], (uint32_t)((u >> 1) & 1), kWaitLimit)) return false;
-                tc::fence_after_sync();
-                const uint32_t aP = tc::smem_u32(sP0 + bu * PBUF);
-                const uint32_t aV = tc::smem_u32(sV0 + su * VBYTES);
-#pragma unroll
-                for (int g = 0; g < 3; ++g) {
-                    const uint32_t pa = aP + (g == 2 ? kPPart : 0);
-                    const uint32_t vb = aV + (g == 1 ? TP * 128 : 0);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc::mma_f16(tO, tc::smem_desc(pa + kk * 256, 128, 1024),
-                                    tc::smem_desc(vb + kk * 256, 128, 1024), IDESC_O,
-                                    (!fresh || g > 0 || kk > 0) ? 1u : 0u);
-                }
-                tc::mma_commit(&bars[kBarPFree + bu]);
-                tc::mma_commit(&bars[kBarLoadFree + su]);
-                if ((u % kTcChunk) == kTcChunk - 1 && u != nt - 1) tc::mma_commit(&bars[kBarOChunk]);
-                return true;
-            };
             bool good = tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
-            for (int t = 0; t < nt && good && !*serr; ++t) {
-                const int st = t % NS, b = t & 1;
-                good = tc::mbar_wait(&bars[kBarLoadFull + st], (uint32_t)((t / NS) & 1), kWaitLimit);
-                if (good && t >= 2) good = tc::mbar_wait(&bars[kBarSFree + b], (uint32_t)(((t >> 1) - 1) & 1), kWaitLimit);
-                if (!good) break;
-                tc::fence_after_sync();
-                const uint32_t aX = tc::smem_u32(sX0 + st * kXBytes);
-                const uint32_t tS = tmem + b * kTcBN;
+            good = __shfl_sync(0xffffffffu, (int)good, 0) != 0;
+            int g1 = 0, g2 = 0;
+            long long last = clock64();
+            while (good && g2 < nt) {
+                if (__shfl_sync(0xffffffffu, (int)*serr, 0)) { good = false; break; }
+                bool progressed = false;
+                if (g1 < nt) {
+                    const int st = g1 % NX, b = g1 % NB;
+                    const bool ok = tc::mbar_test(&bars[kBarXFull + st], (uint32_t)((g1 / NX) & 1)) &&
+                                    (g1 < NB || tc::mbar_test(&bars[kBarSFree + b], (uint32_t)((g1 / NB - 1) & 1)));
+                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
+                        tc::fence_after_sync();
+                        const uint32_t aX = tc::smem_u32(sX0 + st * kXBytes);
+                        const uint32_t tS = tmem + b * kTcBN;
+                        if (tc::elect_one()) {
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch)
-                    tc::mma_f16(tS, tc::smem_desc(aU + ch * 256, 128, 768), tc::smem_desc(aX + ch * 256, 128, 768),
-                                IDESC_S, ch > 0 ? 1u : 0u);
-                tc::mma_commit(&bars[kBarSFull + b]);
-                if (t >= 1) good = product(t - 1);
+                            for (int ch = 0; ch < 3; ++ch)
+                                tc::mma_f16(tS, tc::smem_desc(aU + ch * 256, 128, 768),
+                                            tc::smem_desc(aX + ch * 256, 128, 768), IDESC_S, ch > 0 ? 1u : 0u);
+                            tc::mma_commit(&bars[kBarSFull + b]);
+                            tc::mma_commit(&bars[kBarXFree + st]);
+                        }
+                        __syncwarp();
+                        ++g1;
+                        progressed = true;
+                    }
+                }
+                if (!progressed && g2 < g1) {
+                    const int bu = g2 % NB, su = g2 % NV;
+                    const bool fresh = (g2 % kTcChunk) == 0;
+                    const bool ok = tc::mbar_test(&bars[kBarPFull + bu], (uint32_t)((g2 / NB) & 1)) &&
+                                    tc::mbar_test(&bars[kBarVFull + su], (uint32_t)((g2 / NV) & 1)) &&
+                                    (!fresh || g2 == 0 ||
+                                     tc::mbar_test(&bars[kBarOFree], (uint32_t)((g2 / kTcChunk - 1) & 1)));
+                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
+                        tc::fence_after_sync();
+                        const uint32_t tP = tmem + bu * kTcBN;     // P over S: hi cols [0,32), lo [32,64)
+                        const uint32_t aV = tc::smem_u32(sV0 + su * VBYTES);
+                        if (tc::elect_one()) {
+#pragma unroll
+                            for (int g = 0; g < 3; ++g) {
+                                const uint32_t pa = tP + (g == 2 ? 32 : 0);
+                                const uint32_t vb = aV + (g == 1 ? TP * 128 : 0);
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk)
+                                    tc::mma_f16_ts(tO, pa + kk * 8, tc::smem_desc(vb + kk * 256, 128, 1024), IDESC_O,
+                                                   (!fresh || g > 0 || kk > 0) ? 1u : 0u);
+                            }
+                            tc::mma_commit(&bars[kBarSFree + bu]);
+                            tc::mma_commit(&bars[kBarVFree + su]);
+                            if ((g2 % kTcChunk) == kTcChunk - 1 && g2 != nt - 1) tc::mma_commit(&bars[kBarOChunk]);
+                        }
+                        __syncwarp();
+                        ++g2;
+                        progressed = true;
+                    }
+                }
+                if (progressed) last = clock64();
+                else if (__shfl_sync(0xffffffffu, (int)(clock64() - last > kWaitLimit), 0)) good = false;
             }
-            if (good) good = product(nt - 1);
-            if (good) tc::mma_commit(&bars[kBarOFull]);
-            if (!good) *serr = 1;
+            if (good && tc::elect_one()) tc::mma_commit(&bars[kBarOFull]);
+            __syncwarp();
+            if (!good && lane == 0) *serr = 1;
         }
     } else if (warp >= 4) {
         // --------------------------------------------------- exp warpgroups
         const int g = (warp - 4) >> 2;                    // 0: even tiles, 1: odd tiles
         const int r = 32 * (warp & 3) + lane;             // row in the tile = TMEM lane
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        const uint32_t tS = tmem + g * kTcBN + lane_base;
-        uint8_t* sP = sP0 + g * PBUF;
-        const int base = (r >> 3) * 1024 + (r & 7) * 16;
         for (int t = g; t < nt; t += 2) {
-            const int k = t >> 1;
-            bool good = tc::mbar_wait(&bars[kBarSFull + g], (uint32_t)(k & 1), kWaitLimit);
+            const int b = t % NB;
+            const uint32_t tS = tmem + b * kTcBN + lane_base;
+            const bool good = tc::mbar_wait(&bars[kBarSFull + b], (uint32_t)((t / NB) & 1), kWaitLimit);
             if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
             tc::fence_after_sync();
             uint32_t s0[32], s1[32];
             tc::tmem_ld32(tS, s0);
             tc::tmem_ld32(tS + 32, s1);
-            tc::fence_before_sync();
-            tc::mbar_arrive(&bars[kBarSFree + g]);
             uint32_t hq[32], lq[32];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -401,24 +480,16 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                 const float pb = p_of_s<KT>(__uint_as_float(s1[2 * e + 1]));
                 split_pair<HALF>(pa, pb, hq[16 + e], lq[16 + e]);
             }
-            if (t >= 2) {
-                good = tc::mbar_wait(&bars[kBarPFree + g], (uint32_t)((k - 1) & 1), kWaitLimit);
-                if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
-            }
-#pragma unroll
-            for (int jc = 0; jc < 8; ++jc) {
-                *reinterpret_cast<uint4*>(sP + base + jc * 128) =
-                    make_uint4(hq[4 * jc], hq[4 * jc + 1], hq[4 * jc + 2], hq[4 * jc + 3]);
-                *reinterpret_cast<uint4*>(sP + kPPart + base + jc * 128) =
-                    make_uint4(lq[4 * jc], lq[4 * jc + 1], lq[4 * jc + 2], lq[4 * jc + 3]);
-            }
-            tc::fence_proxy_async_smem();
-            tc::mbar_arrive(&bars[kBarPFull + g]);
+            // P over S in tensor memory: 64 values per row -> 32 columns per part.
+            tc::tmem_st32(tS, hq);
+            tc::tmem_st32(tS + 32, lq);
+            tc::fence_before_sync();
+            tc::mbar_arrive(&bars[kBarPFull + b]);
             // Fold a completed chunk of O into the running sum (odd warpgroup).
             if (g == 1 && (t % kTcChunk) == kTcChunk - 1 && t != nt - 1) {
                 const int c = t / kTcChunk;
-                good = tc::mbar_wait(&bars[kBarOChunk], (uint32_t)(c & 1), kWaitLimit);
-                if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
+                const bool okc = tc::mbar_wait(&bars[kBarOChunk], (uint32_t)(c & 1), kWaitLimit);
+                if (__shfl_sync(0xffffffffu, (int)(!okc || *serr), 0)) { *serr = 1; break; }
                 tc::fence_after_sync();
 #pragma unroll 1
                 for (int cc = 0; cc < TP / 32; ++cc) {
@@ -446,11 +517,11 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     }
 
     // ------------------------------------------------------------ epilogue
-    double* red = reinterpret_cast<double*>(sP0);         // [4 warps][TP][3], free once O is complete
+    double* red = reinterpret_cast<double*>(sX0);         // [4 warps][TP][3], free once O is complete
     if (warp >= 4 && warp < 8) {
         const int r = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        bool good = !*serr && tc::mbar_wait(&bars[kBarOFull], 0, kWaitLimit);
+        const bool good = !*serr && tc::mbar_wait(&bars[kBarOFull], 0, kWaitLimit);
         const bool ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
         if (!ok) *serr = 1;
         tc::fence_after_sync();

@@ -1,0 +1,97 @@
+// Throughput microbenchmarks for the roofline denominators that the driver
+// does not measure: SFU exp2 (ex2.approx.ftz.f32, the SFU op of every kernel
+// entry), FP32 FMA and FP64 FMA.  Each thread runs 8 independent dependent
+// chains; the grid is 8 CTAs of 256 threads per SM.  Built as its own library
+// (libciq_peaks.so); the solver does not use it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace {
+
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__global__ void ex2_kernel(float* out, int iters) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = -1.0f - 1e-3f * (float)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = -ex2f(a[k]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+__global__ void fma_kernel(T* out, int iters) {
+    T a[8];
+    const T b = (T)0.999999, c = (T)1e-7;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename F>
+int time_kernel(F launch, double* ms_out) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 2;
+    launch();                                   // warm-up
+    cudaEventRecord(e0);
+    launch();
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = ms;
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+}  // namespace
+
+// ops/s of ex2.approx.ftz.f32 over the whole device.
+extern "C" int ciq_peak_sfu_ex2(double* ops_per_s, double* ms) {
+    const int blocks = 8 * sm_count(), threads = 256, iters = 4096;
+    float* out = nullptr;
+    if (cudaMalloc(&out, sizeof(float) * blocks * threads) != cudaSuccess) return 2;
+    int rc = time_kernel([&] { ex2_kernel<<<blocks, threads>>>(out, iters); }, ms);
+    *ops_per_s = (double)blocks * threads * iters * 8 / (*ms * 1e-3);
+    cudaFree(out);
+    return rc;
+}
+
+// FLOP/s (2 per FMA) of FP32 or FP64 FMA over the whole device.
+extern "C" int ciq_peak_fma(int fp64, double* flops, double* ms) {
+    const int blocks = 8 * sm_count(), threads = 256, iters = fp64 ? 256 : 8192;
+    void* out = nullptr;
+    if (cudaMalloc(&out, 8 * (size_t)blocks * threads) != cudaSuccess) return 2;
+    int rc;
+    if (fp64)
+        rc = time_kernel([&] { fma_kernel<double><<<blocks, threads>>>((double*)out, iters); }, ms);
+    else
+        rc = time_kernel([&] { fma_kernel<float><<<blocks, threads>>>((float*)out, iters); }, ms);
+    *flops = 2.0 * blocks * threads * iters * 8 / (*ms * 1e-3);
+    cudaFree(out);
+    return rc;
+}

@@ -224,3 +224,46 @@ def test_stop_rules_report_and_iteration_cap():
     assert info["status"] == 0 and info["errbound_max"] <= 1e-3
     _, info = P.ciq_sqrt(Xd, k, Bd, 8, 1e-4, max_iter=500, stop_rule="residual")
     assert info["status"] == 0 and info["resid_max"] <= 1e-4
+
+
+# ------------------------------------------------------------ stored K ----
+def _npad(n):
+    return (n + 127) // 128 * 128
+
+
+@pytest.mark.parametrize("kind", ["rbf", "matern52"])
+def test_kernel_matrix_matches_oracle_with_zero_padding(kind):
+    n, d = 300, 5
+    X, _, k = problem(n, d, 1, 61, kind, ls=0.3, s=1.7, noise=2e-3)
+    npad = _npad(n)
+    Kd = torch.full((npad, npad + 4), float("nan"), device=DEV)
+    P.ciq_kernel_matrix(torch.from_numpy(X).to(DEV), k, Kd)
+    Km = Kd.cpu().numpy().astype(np.float64)
+    ref = dense_K(X, k)
+    assert rel(Km[:n, :n], ref) < 2e-7
+    assert np.all(Km[n:npad, :npad] == 0) and np.all(Km[:npad, n:npad] == 0)
+
+
+@pytest.mark.parametrize("n,t", [(1, 1), (300, 1), (777, 5), (1000, 17), (1300, 64), (513, 70)])
+def test_stored_mvm_matches_oracle(n, t):
+    X, V, k = problem(n, 4, t, 70 + n + t, "rbf", ls=0.3, s=1.3, noise=1e-3)
+    npad = _npad(n)
+    Kd = torch.empty((npad, npad), device=DEV)
+    P.ciq_kernel_matrix(torch.from_numpy(X).to(DEV), k, Kd)
+    out = P.ciq_stored_mvm(Kd, torch.from_numpy(V).to(DEV), n=n)
+    ref = dense_K(X, k) @ V.T.astype(np.float64)
+    assert rel(out.cpu().numpy().T, ref) < 2e-6
+
+
+@pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
+def test_stored_k_solve_matches_serial_oracle(op):
+    X, B, k = problem(777, 3, 3, 977, "matern52", ls=0.25)
+    K = dense_K(X, k)
+    lam = np.linalg.eigvalsh(K)
+    nodes = O.quad_nodes(k.noise, 1.05 * lam[-1], 8)
+    ref, _ = _oracle(op, X, k, B, 8, 800, nodes)
+    fn = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
+    out, info = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), 8, 0.0, max_iter=800,
+                   nodes=nodes, lmin=k.noise, mvm="stored")
+    assert info["iters"] == 800
+    assert rel(out.cpu().numpy(), ref) < fp32_tol(op, lam[-1] / lam[0])
