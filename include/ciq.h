@@ -55,6 +55,7 @@ typedef struct CUstream_st* ciq_stream_t;
 
 #define CIQ_MAX_DIM 16        /* largest point dimension d */
 #define CIQ_MAX_Q 32          /* largest number of quadrature points Q */
+#define CIQ_MAX_BATCH 65536   /* largest number of problems of one batched call */
 
 typedef enum {
     CIQ_OK = 0,
@@ -216,6 +217,42 @@ ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel*
  * Asynchronous on stream. */
 ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T,
                           float* out, ciq_stream_t stream);
+
+/* One problem of a batch: X (device, N x d), B and out (device, T columns of
+ * N floats).  lmin, lmax > 0 give this problem's spectral bounds and skip its
+ * Lanczos pre-pass (e.g. bounds predicted by a learned model); otherwise the
+ * pre-pass runs as in ciq_sqrt. */
+typedef struct {
+    const float* X;
+    int64_t N;
+    int d;
+    ciq_kernel kern;
+    const float* B;
+    int T;
+    float* out;
+    double lmin, lmax;
+} ciq_problem;
+
+/* K_p^{1/2} B_p / K_p^{-1/2} B_p for P independent problems of uneven N and d
+ * (the batched form of Algorithm "ciq"): one launch per iteration phase
+ * covers every problem that has not stopped (work lists rebuilt on the device
+ * between batches of iterations, finished problems drop out); problems share
+ * Q, tol and the options; all problems must have the same T.  FP32 vectors,
+ * FP64 scalars, on-the-fly MVM on CUDA cores.  Every problem's arithmetic is
+ * that of ciq_sqrt / ciq_invsqrt with the same options, so each output equals
+ * the single-problem call's bit for bit.  1 <= P <= CIQ_MAX_BATCH.
+ * CIQ_ERR_UNSUPPORTED unless opt->precision is CIQ_PREC_FP32, opt->mvm is not
+ * CIQ_MVM_STORED, opt->sqrt_form is CIQ_SQRT_IDENTITY, and quad_w, quad_t,
+ * lanczos_start and workspace are NULL.  The device workspace (the sum of
+ * the problems' ciq_workspace_bytes plus small tables) is allocated on
+ * stream and freed before return; the call returns after the stream work.
+ * infos: NULL or P entries (launches = the call's total).  Returns
+ * CIQ_ERR_NAN / CIQ_NOT_CONVERGED if any problem ended so, CIQ_ERR_ARG on a
+ * bad problem or a host pointer (nothing is computed). */
+ciq_status ciq_sqrt_batched(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                            ciq_info* infos, ciq_stream_t stream);
+ciq_status ciq_invsqrt_batched(const ciq_problem* probs, int P, int Q, double tol,
+                               const ciq_options* opt, ciq_info* infos, ciq_stream_t stream);
 
 /* Device workspace bytes a solve with these sizes and options needs. */
 size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt);

@@ -4,6 +4,6 @@ kernel matrices K = K_XX + sigma^2 I (Pleiss et al., NeurIPS 2020).
 The compute path is the CUDA library ``libciq.so`` (sources in ``csrc/``,
 C ABI in ``include/ciq.h``); this package only marshals arguments to it.
 """
-from ._ciq import (CiqError, Kernel, ciq_invsqrt, ciq_invsqrt_f64, ciq_kernel_matrix,  # noqa: F401
-                   ciq_kernel_mvm, ciq_kernel_mvm_f64, ciq_kernel_mvm_noalloc, ciq_lanczos_bounds, ciq_quad_nodes,
-                   ciq_sqrt, ciq_sqrt_f64, ciq_stored_mvm, ciq_workspace_bytes, lib, LIB_PATH)
+from ._ciq import (CiqError, Kernel, ciq_invsqrt, ciq_invsqrt_batched, ciq_invsqrt_f64,  # noqa: F401
+                   ciq_kernel_matrix, ciq_kernel_mvm, ciq_kernel_mvm_f64, ciq_kernel_mvm_noalloc, ciq_lanczos_bounds, ciq_quad_nodes,
+                   ciq_sqrt, ciq_sqrt_batched, ciq_sqrt_f64, ciq_stored_mvm, ciq_workspace_bytes, lib, LIB_PATH)

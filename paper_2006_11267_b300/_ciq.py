@@ -70,6 +70,12 @@ class _Info(ctypes.Structure):
                 ("mvm_launches", ctypes.c_int), ("step_launches", ctypes.c_int)]
 
 
+class _Problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int), ("kern", _Kernel),
+                ("B", ctypes.c_void_p), ("T", ctypes.c_int), ("out", ctypes.c_void_p),
+                ("lmin", ctypes.c_double), ("lmax", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -101,6 +107,8 @@ def lib() -> ctypes.CDLL:
         "ciq_workspace_bytes": (S, [I64, I, I, I, OP]),
         "ciq_kernel_mvm_noalloc": (I, [P, I64, I, KP, P, I, P, P]),
         "ciq_noalloc_scratch_floats": (S, []),
+        "ciq_sqrt_batched": (I, [ctypes.POINTER(_Problem), I, I, D, OP, IP, P]),
+        "ciq_invsqrt_batched": (I, [ctypes.POINTER(_Problem), I, I, D, OP, IP, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -324,3 +332,46 @@ def ciq_kernel_mvm_noalloc(X, kernel, V, out=None):
     st = lib().ciq_kernel_mvm_noalloc(_ptr(X), N, d, ctypes.byref(k), _ptr(V), T, _ptr(out), _stream(X, V, out))
     _check(st, "ciq_kernel_mvm_noalloc", allow=(CIQ_OK,))
     return out
+
+
+def _solve_batched(name, problems, Q, tol, **opts):
+    """problems: sequence of dicts with X (N, d), kernel (Kernel), B (T, N)
+    device tensors, optional out (T, N) and optional lmin, lmax."""
+    P = len(problems)
+    arr = (_Problem * P)()
+    outs = []
+    for i, pr in enumerate(problems):
+        X, B = pr["X"], pr["B"]
+        N, d = X.shape
+        if B.shape[1] != N:
+            raise ValueError("B must have shape (T, N)")
+        out = pr.get("out")
+        if out is None:
+            out = _empty_like_rhs(B, np.float32)
+        outs.append(out)
+        arr[i].X = _ptr(X).value
+        arr[i].N = N
+        arr[i].d = d
+        arr[i].kern = pr["kernel"].c()
+        arr[i].B = _ptr(B).value
+        arr[i].T = B.shape[0]
+        arr[i].out = _ptr(out).value
+        arr[i].lmin = float(pr.get("lmin") or 0.0)
+        arr[i].lmax = float(pr.get("lmax") or 0.0)
+    o = make_options(**opts)
+    infos = (_Info * P)()
+    first = problems[0]
+    st = getattr(lib(), name)(arr, P, int(Q), float(tol), ctypes.byref(o), infos,
+                              _stream(first["X"], first["B"]))
+    _check(st, name)
+    return outs, [_info_dict(infos[i], st) for i in range(P)]
+
+
+def ciq_sqrt_batched(problems, Q, tol=0.0, **opts):
+    """K_p^{1/2} B_p for every problem of the batch. Returns (outs, infos)."""
+    return _solve_batched("ciq_sqrt_batched", problems, Q, tol, **opts)
+
+
+def ciq_invsqrt_batched(problems, Q, tol=0.0, **opts):
+    """K_p^{-1/2} B_p for every problem of the batch. Returns (outs, infos)."""
+    return _solve_batched("ciq_invsqrt_batched", problems, Q, tol, **opts)

@@ -1,0 +1,86 @@
+// Batched msMINRES-CIQ: one launch per iteration phase over many independent
+// problems of uneven size (the per-problem arithmetic is that of krylov.cu and
+// mvm_simt.cu; only the mapping of blocks to work differs).
+#pragma once
+
+#include "krylov.cuh"
+
+namespace ciq {
+
+// Everything a batched kernel needs about one problem (device array of P).
+struct BatchProblem {
+    KrylovState<float> ks;
+    LanczosState<float> ls;
+    MvmArgs<float> mvm[2];      // main-loop MVM by the parity of j
+    MvmArgs<float> pre[2];      // pre-pass MVM (one column) by the parity of j
+    const float* X;             // caller's points, N x d row-major
+    const float* B;             // caller's right-hand sides, T columns of N
+    float* out;                 // caller's output, T columns of N
+    float* Xp;                  // scaled, padded points (Npad x dp)
+    double* nodes;              // NodeSlot block
+    double inv_ls;              // 1 / lengthscale
+    double noise;               // sigma^2
+    double lmin, lmax;          // given bounds (problems without the pre-pass)
+    int d;
+    int cls;                    // MVM class: kernel type * 4 + dp / 4 - 1
+    int mvm_tiles;              // row tiles of the main MVM (items = tiles x groups)
+    int mvm_items;
+    int pre_tiles;              // row tiles of the pre-pass MVM (= its items)
+};
+
+constexpr int kBatchClasses = 8;            // 2 kernel types x 4 padded dimensions
+constexpr int kSummaryStride = 8 + kNodeCount;
+
+// A work list: problems ids[0..*np) with their first work items prefix[k]
+// (prefix[*np] = total).  Block b of a batched launch takes the item b: the
+// problem is found by binary search over prefix, and blocks past the total
+// return at once, so a grid sized from an older (longer) list is safe.
+struct DevList {
+    int* np;
+    int* ids;
+    int* prefix;
+};
+
+// Main-loop lists rebuilt on the device: one per MVM class, then the
+// recurrence list; kBatchDynLists in all.
+constexpr int kBatchDynLists = kBatchClasses + 1;
+struct DynLists {
+    DevList l[kBatchDynLists];
+};
+
+enum BatchSetupPhase {
+    kBatchPrepare = 0,      // scaled points                   items: ceil(Npad dp / 256)
+    kBatchReset,            // zero the per-problem counters   items: 1
+    kBatchInitRhs,          // copy b, partial ||b||^2         items: chunks x T
+    kBatchInitState,        // q_1, state                      items: chunks x T
+    kBatchPreInitA,         // Lanczos start vector            items: pre-pass chunks
+    kBatchPreInitB,         // normalise it                    items: pre-pass chunks
+    kBatchNodesGiven,       // nodes from given bounds         items: 1
+    kBatchCombine,          // output                          items: ceil(N / 256) x T
+};
+
+// Narrow (one row per lane) or wide (64 x 64 tile) CUDA-core MVM for T
+// columns, and its column-group width; the same choice as the single-problem path.
+bool batch_mvm_wide(int T);
+int batch_mvm_group(int T);
+int64_t batch_mvm_row_tiles(int64_t Npad, int T);
+
+cudaError_t launch_batched_setup(const BatchProblem* probs, int phase, uint64_t seed, int Q, DevList L,
+                                 int blocks, cudaStream_t st);
+cudaError_t launch_batched_mvm(const BatchProblem* probs, int cls, int T, bool prepass, int parity, DevList L,
+                               int blocks, cudaStream_t st);
+cudaError_t launch_batched_lanczos_step(const BatchProblem* probs, int j, DevList L, int blocks, cudaStream_t st);
+cudaError_t launch_batched_bounds_nodes(const BatchProblem* probs, int Q, double lmax_margin, double lmin_div,
+                                        DevList L, int blocks, cudaStream_t st);
+cudaError_t launch_batched_step(const BatchProblem* probs, int j, bool final_pass, DevList L, int blocks,
+                                cudaStream_t st);
+// Summary of every listed problem, gathered with its node block into
+// packed[p * kSummaryStride ...] (summary[8], then the NodeSlot block).
+cudaError_t launch_batched_summary(const BatchProblem* probs, int final_j, double* packed, DevList L, int blocks,
+                                   cudaStream_t st);
+// Rebuild the kBatchDynLists main-loop lists over problems whose columns
+// have not all stopped; totals[l] = the new item total of list l.
+cudaError_t launch_rebuild_lists(const BatchProblem* probs, int P, const DynLists& lists, int* totals,
+                                 cudaStream_t st);
+
+}  // namespace ciq

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <vector>
 
+#include "batched.cuh"
 #include "krylov.cuh"
 #include "mvm_stored.cuh"
 #include "mvm_tc.cuh"
@@ -74,6 +75,15 @@ bool valid_kernel(const ciq_kernel* k) {
     return k && (k->type == CIQ_RBF || k->type == CIQ_MATERN52) && k->lengthscale > 0.0 &&
            std::isfinite(k->lengthscale) && k->outputscale > 0.0 && std::isfinite(k->outputscale) &&
            k->noise >= 0.0 && std::isfinite(k->noise);
+}
+
+bool valid_options(const ciq_options& o) {
+    return !(o.max_iter < 1 || o.max_iter > 1000000 || o.lanczos_iters < 1 || o.lanczos_iters > 512 ||
+             o.check_every < 1 || !(o.lmax_margin >= 1.0) || !(o.lmin_div >= 1.0) ||
+             (o.stop_rule != CIQ_STOP_RESIDUAL && o.stop_rule != CIQ_STOP_ERRBOUND) ||
+             (o.sqrt_form != CIQ_SQRT_IDENTITY && o.sqrt_form != CIQ_SQRT_MVM) ||
+             (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_FP16) ||
+             (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED));
 }
 
 // Pinned host words for the convergence flag, one set per host thread.
@@ -318,13 +328,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     ciq_options o;
     ciq_default_options(&o);
     if (opt) o = *opt;
-    if (o.max_iter < 1 || o.max_iter > 1000000 || o.lanczos_iters < 1 || o.lanczos_iters > 512 ||
-        o.check_every < 1 || !(o.lmax_margin >= 1.0) || !(o.lmin_div >= 1.0) ||
-        (o.stop_rule != CIQ_STOP_RESIDUAL && o.stop_rule != CIQ_STOP_ERRBOUND) ||
-        (o.sqrt_form != CIQ_SQRT_IDENTITY && o.sqrt_form != CIQ_SQRT_MVM) ||
-        (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_FP16) ||
-        (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED))
-        return CIQ_ERR_ARG;
+    if (!valid_options(o)) return CIQ_ERR_ARG;
     if ((o.quad_w == nullptr) != (o.quad_t == nullptr)) return CIQ_ERR_ARG;
     if (o.mvm == CIQ_MVM_STORED && !fp64 && o.precision != CIQ_PREC_FP32) return CIQ_ERR_UNSUPPORTED;
     bool tc = false;
@@ -575,6 +579,306 @@ done:
     return CIQ_OK;
 }
 
+// ---------------------------------------------------------------- batched --
+// Host image of one work list (see DevList): problems and their first items.
+struct HostList {
+    std::vector<int> ids, prefix{0};
+    void add(int p, int64_t items) {
+        ids.push_back(p);
+        prefix.push_back((int)(prefix.back() + items));
+    }
+    int total() const { return prefix.back(); }
+};
+
+// Pinned host words for the list totals (two slots), one set per host thread.
+int* pinned_totals() {
+    thread_local int* p = nullptr;
+    if (!p) {
+        if (cudaHostAlloc(reinterpret_cast<void**>(&p), 2 * kBatchDynLists * sizeof(int), cudaHostAllocDefault) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    return p;
+}
+
+ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                         ciq_info* infos, cudaStream_t st, int op) {
+    if (!probs || P < 1 || P > CIQ_MAX_BATCH || Q < 1 || Q > CIQ_MAX_Q || !(tol >= 0.0)) return CIQ_ERR_ARG;
+    ciq_options o;
+    ciq_default_options(&o);
+    if (opt) o = *opt;
+    if (!valid_options(o)) return CIQ_ERR_ARG;
+    if (o.precision != CIQ_PREC_FP32 || o.mvm == CIQ_MVM_STORED || o.quad_w || o.quad_t || o.lanczos_start ||
+        o.workspace || o.sqrt_form != CIQ_SQRT_IDENTITY)
+        return CIQ_ERR_UNSUPPORTED;
+    const int T = probs[0].T;
+    if (T < 1) return CIQ_ERR_ARG;
+    std::vector<char> given(P);
+    for (int p = 0; p < P; ++p) {
+        const ciq_problem& q = probs[p];
+        if (!q.X || !q.B || !q.out || q.N < 1 || q.d < 1 || q.d > CIQ_MAX_DIM || q.T != T || !valid_kernel(&q.kern))
+            return CIQ_ERR_ARG;
+        given[p] = q.lmin > 0.0 && q.lmax > 0.0;
+        if (given[p] && !(q.lmax >= q.lmin && std::isfinite(q.lmax))) return CIQ_ERR_ARG;
+        if (!device_accessible(q.X) || !device_accessible(q.B) || !device_accessible(q.out)) return CIQ_ERR_ARG;
+    }
+    keep_pool_warm();
+    int* tot_h = pinned_totals();
+    if (!tot_h) return CIQ_ERR_CUDA;
+
+    // Per-problem workspaces (the single-problem layout), then the shared tables.
+    std::vector<Plan<float>> plans;
+    plans.reserve(P);
+    std::vector<size_t> offs(P);
+    size_t off = 0;
+    for (int p = 0; p < P; ++p) {
+        plans.push_back(make_plan<float>(probs[p].N, probs[p].d, T, Q, o, !given[p], false));
+        offs[p] = off;
+        off += round_up((int64_t)plans.back().bytes, kAlign);
+    }
+    const int groups = (T + batch_mvm_group(T) - 1) / batch_mvm_group(T);
+    std::vector<BatchProblem> hp(P);
+    HostList prep, one, init, pre, pre_one, given_one, fin, comb, pre_mvm[kBatchClasses], dyn[kBatchDynLists];
+    int64_t biggest = 0;
+    for (int p = 0; p < P; ++p) {
+        const Plan<float>& pl = plans[p];
+        BatchProblem& b = hp[p];
+        b.mvm_tiles = (int)batch_mvm_row_tiles(pl.Npad, T);
+        b.mvm_items = b.mvm_tiles * groups;
+        b.pre_tiles = (int)(pl.Npad / 32);
+        b.cls = probs[p].kern.type * 4 + pl.dp / 4 - 1;
+        b.d = pl.d;
+        const int64_t prep_items = (pl.Npad * pl.dp + 255) / 256;
+        const int64_t comb_items = (pl.N + 255) / 256 * T;
+        biggest = std::max<int64_t>({biggest, prep_items, comb_items, (int64_t)b.mvm_items,
+                                     (int64_t)pl.nchunks * T});
+        prep.add(p, prep_items);
+        one.add(p, 1);
+        init.add(p, (int64_t)pl.nchunks * T);
+        fin.add(p, T);
+        comb.add(p, comb_items);
+        dyn[b.cls].add(p, b.mvm_items);
+        dyn[kBatchClasses].add(p, (int64_t)pl.nchunks * T);
+        if (given[p]) {
+            given_one.add(p, 1);
+        } else {
+            pre.add(p, pl.nchunks1);
+            pre_one.add(p, 1);
+            pre_mvm[b.cls].add(p, b.pre_tiles);
+        }
+    }
+    // Item totals index blocks as int.
+    {
+        int64_t sums[6] = {0, 0, 0, 0, 0, 0};
+        for (int p = 0; p < P; ++p) {
+            const Plan<float>& pl = plans[p];
+            sums[0] += (pl.Npad * pl.dp + 255) / 256;
+            sums[1] += (pl.N + 255) / 256 * T;
+            sums[2] += (int64_t)hp[p].mvm_items;
+            sums[3] += (int64_t)pl.nchunks * T;
+            sums[4] += hp[p].pre_tiles;
+            sums[5] += pl.nchunks1;
+        }
+        for (int64_t v : sums)
+            if (v >= (int64_t)INT32_MAX) return CIQ_ERR_UNSUPPORTED;
+    }
+    (void)biggest;
+    std::vector<HostList*> all_lists = {&prep, &one, &init, &pre, &pre_one, &given_one, &fin, &comb};
+    for (auto& l : pre_mvm) all_lists.push_back(&l);
+    for (auto& l : dyn) all_lists.push_back(&l);
+    const size_t list_ints = (size_t)2 * P + 2;
+    const size_t tables = round_up((int64_t)(sizeof(BatchProblem) * P), kAlign) +
+                          round_up((int64_t)(sizeof(int) * list_ints * all_lists.size()), kAlign) +
+                          round_up((int64_t)(sizeof(int) * kBatchDynLists), kAlign) +
+                          round_up((int64_t)(sizeof(double) * kSummaryStride * P), kAlign);
+    char* base = nullptr;
+    ciq_status rc = CIQ_OK;
+    int launches = 0;
+    int last_j = 0;
+    std::vector<double> packed((size_t)kSummaryStride * P, 0.0);
+    std::vector<int> list_img(list_ints * all_lists.size(), 0);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), off + tables, st);
+        if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    }
+    {
+        char* tb = base + off;
+        BatchProblem* probs_d = reinterpret_cast<BatchProblem*>(tb);
+        tb += round_up((int64_t)(sizeof(BatchProblem) * P), kAlign);
+        int* lists_d = reinterpret_cast<int*>(tb);
+        tb += round_up((int64_t)(sizeof(int) * list_ints * all_lists.size()), kAlign);
+        int* totals_d = reinterpret_cast<int*>(tb);
+        tb += round_up((int64_t)(sizeof(int) * kBatchDynLists), kAlign);
+        double* packed_d = reinterpret_cast<double*>(tb);
+        // Device lists: [np][ids P][prefix P + 1] each.
+        std::vector<DevList> dl(all_lists.size());
+        for (size_t l = 0; l < all_lists.size(); ++l) {
+            int* img = list_img.data() + l * list_ints;
+            const HostList& h = *all_lists[l];
+            img[0] = (int)h.ids.size();
+            std::copy(h.ids.begin(), h.ids.end(), img + 1);
+            std::copy(h.prefix.begin(), h.prefix.end(), img + 1 + P);
+            int* d = lists_d + l * list_ints;
+            dl[l] = DevList{d, d + 1, d + 1 + P};
+        }
+        auto L = [&](const HostList& h) {
+            for (size_t l = 0; l < all_lists.size(); ++l)
+                if (all_lists[l] == &h) return dl[l];
+            return DevList{};
+        };
+        DynLists dyn_d;
+        for (int l = 0; l < kBatchDynLists; ++l) dyn_d.l[l] = L(dyn[l]);
+        for (int p = 0; p < P; ++p) {
+            Plan<float>& pl = plans[p];
+            pl.layout(base + offs[p]);
+            BatchProblem& b = hp[p];
+            const ciq_kernel& k = probs[p].kern;
+            b.ks = krylov_state(pl, op, o, tol);
+            b.ls = lanczos_state(pl);
+            MvmArgs<float> a = mvm_args(pl, k);
+            for (int par = 0; par < 2; ++par) {
+                MvmArgs<float> m = a;
+                m.T = T;
+                m.mode = kLanczos;
+                m.partials = pl.partials;
+                m.stop = pl.all_done;
+                m.V = par ? pl.QA : pl.QB;
+                m.qprev = par ? pl.QB : pl.QA;
+                m.beta = pl.beta + (size_t)par * T;
+                b.mvm[par] = m;
+                MvmArgs<float> r = a;
+                r.T = 1;
+                r.mode = kLanczos;
+                r.partials = pl.lpart;
+                r.stop = pl.ldone;
+                r.V = par ? pl.LA : pl.LB;
+                r.qprev = par ? pl.LB : pl.LA;
+                r.beta = pl.bpar ? pl.bpar + par : nullptr;
+                b.pre[par] = r;
+            }
+            b.X = probs[p].X;
+            b.B = probs[p].B;
+            b.out = probs[p].out;
+            b.Xp = pl.Xp;
+            b.nodes = pl.nodes;
+            b.inv_ls = 1.0 / k.lengthscale;
+            b.noise = k.noise;
+            b.lmin = probs[p].lmin;
+            b.lmax = probs[p].lmax;
+        }
+        CIQ_TRY(cudaMemcpyAsync(probs_d, hp.data(), sizeof(BatchProblem) * P, cudaMemcpyHostToDevice, st));
+        CIQ_TRY(cudaMemcpyAsync(lists_d, list_img.data(), sizeof(int) * list_img.size(), cudaMemcpyHostToDevice, st));
+        auto setup = [&](int phase, const HostList& h) -> cudaError_t {
+            if (h.total() == 0) return cudaSuccess;
+            ++launches;
+            return launch_batched_setup(probs_d, phase, o.seed, Q, L(h), h.total(), st);
+        };
+        CIQ_TRY(setup(kBatchPrepare, prep));
+        CIQ_TRY(setup(kBatchReset, one));
+        CIQ_TRY(setup(kBatchInitRhs, init));
+        CIQ_TRY(setup(kBatchInitState, init));
+        CIQ_TRY(setup(kBatchNodesGiven, given_one));
+        if (pre.total() > 0) {
+            CIQ_TRY(setup(kBatchPreInitA, pre));
+            CIQ_TRY(setup(kBatchPreInitB, pre));
+            for (int j = 1; j <= o.lanczos_iters; ++j) {
+                for (int c = 0; c < kBatchClasses; ++c) {
+                    if (pre_mvm[c].total() == 0) continue;
+                    CIQ_TRY(launch_batched_mvm(probs_d, c, T, true, j & 1, L(pre_mvm[c]), pre_mvm[c].total(), st));
+                    ++launches;
+                }
+                CIQ_TRY(launch_batched_lanczos_step(probs_d, j, L(pre), pre.total(), st));
+                ++launches;
+            }
+            CIQ_TRY(launch_batched_bounds_nodes(probs_d, Q, o.lmax_margin, o.lmin_div, L(pre_one), pre_one.total(), st));
+            ++launches;
+        }
+        int grid[kBatchDynLists];
+        for (int l = 0; l < kBatchDynLists; ++l) grid[l] = dyn[l].total();
+        CIQ_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        CIQ_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        {
+            int slot = 0;
+            bool pending[2] = {false, false};
+            for (int j = 1; j <= o.max_iter;) {
+                const int jb = std::min(j + o.check_every - 1, o.max_iter);
+                for (int jj = j; jj <= jb; ++jj) {
+                    for (int c = 0; c < kBatchClasses; ++c) {
+                        if (grid[c] == 0) continue;
+                        CIQ_TRY(launch_batched_mvm(probs_d, c, T, false, jj & 1, dyn_d.l[c], grid[c], st));
+                        ++launches;
+                    }
+                    CIQ_TRY(launch_batched_step(probs_d, jj, false, dyn_d.l[kBatchClasses], grid[kBatchClasses], st));
+                    ++launches;
+                }
+                last_j = jb;
+                CIQ_TRY(launch_rebuild_lists(probs_d, P, dyn_d, totals_d, st));
+                ++launches;
+                CIQ_TRY(cudaMemcpyAsync(tot_h + slot * kBatchDynLists, totals_d, sizeof(int) * kBatchDynLists,
+                                        cudaMemcpyDeviceToHost, st));
+                CIQ_TRY(cudaEventRecord(ev[slot], st));
+                bool stop = false;
+                if (pending[slot ^ 1]) {
+                    CIQ_TRY(cudaEventSynchronize(ev[slot ^ 1]));
+                    pending[slot ^ 1] = false;
+                    // Totals of the previous rebuild bound the lists the next
+                    // launches read (lists only shrink).
+                    for (int l = 0; l < kBatchDynLists; ++l) grid[l] = tot_h[(slot ^ 1) * kBatchDynLists + l];
+                    stop = grid[kBatchClasses] == 0;
+                }
+                pending[slot] = true;
+                slot ^= 1;
+                j = jb + 1;
+                if (stop) break;
+            }
+        }
+        CIQ_TRY(launch_batched_step(probs_d, last_j + 1, true, L(fin), fin.total(), st));
+        CIQ_TRY(setup(kBatchCombine, comb));
+        CIQ_TRY(launch_batched_summary(probs_d, last_j, packed_d, L(one), one.total(), st));
+        launches += 2;
+        CIQ_TRY(cudaMemcpyAsync(packed.data(), packed_d, sizeof(double) * packed.size(), cudaMemcpyDeviceToHost, st));
+        CIQ_TRY(cudaStreamSynchronize(st));
+    }
+done:
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    cudaFreeAsync(base, st);
+    if (rc != CIQ_OK) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        return rc;
+    }
+    bool any_nan = false, any_maxit = false;
+    for (int p = 0; p < P; ++p) {
+        const double* sm = packed.data() + (size_t)p * kSummaryStride;
+        const double* nd = sm + 8;
+        if (sm[6] > 0) any_nan = true;
+        if ((int)sm[5] == kColMaxIter) any_maxit = true;
+        if (!infos) continue;
+        ciq_info* info = infos + p;
+        memset(info, 0, sizeof(*info));
+        info->iters = (int)sm[0];
+        info->iters_min = (int)sm[1];
+        info->converged = (int)sm[2];
+        info->resid_max = sm[3];
+        info->errbound_max = sm[4];
+        info->lanczos_iters = (int)nd[kNodeLanczosSteps];
+        info->ritz_min = nd[kNodeRitzMin];
+        info->ritz_max = nd[kNodeRitzMax];
+        info->lmin_used = nd[kNodeLmin];
+        info->lmax_used = nd[kNodeLmax];
+        info->q = Q;
+        for (int q = 0; q < Q; ++q) { info->w[q] = nd[kNodeW + q]; info->t[q] = nd[kNodeT + q]; }
+        info->launches = launches;
+    }
+    if (any_nan) return CIQ_ERR_NAN;
+    if (any_maxit) return CIQ_NOT_CONVERGED;
+    return CIQ_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ C entry points --
@@ -809,6 +1113,16 @@ size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* op
     const bool tc = o.precision != CIQ_PREC_FP32 && tc_supported(o.precision, d) && tc_padded_t(T) > 0;
     Plan<float> p = make_plan<float>(N, d, T, Q, o, prepass, tc);
     return p.bytes;
+}
+
+ciq_status ciq_sqrt_batched(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                            ciq_info* infos, ciq_stream_t stream) {
+    return solve_batched(probs, P, Q, tol, opt, infos, (cudaStream_t)stream, kOpSqrtIdentity);
+}
+
+ciq_status ciq_invsqrt_batched(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                               ciq_info* infos, ciq_stream_t stream) {
+    return solve_batched(probs, P, Q, tol, opt, infos, (cudaStream_t)stream, kOpInvSqrt);
 }
 
 }  // extern "C"

@@ -1,0 +1,472 @@
+// Bodies of the msMINRES recurrence and Lanczos pre-pass kernels (see
+// krylov.cu), written against explicit block coordinates so that the
+// single-problem kernels and the batched kernels (batched.cu) run the same code.
+#pragma once
+
+#include <math.h>
+
+#include "krylov.cuh"
+#include "spectral.cuh"
+
+namespace ciq {
+namespace {
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide FP64 sum (256 threads); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; ++w) r += red[w];
+    return r;
+}
+
+template <typename R>
+__device__ __forceinline__ R split_hi(double a) { return (R)a; }
+
+template <typename R>
+__device__ __forceinline__ void init_rhs_body(KrylovState<R> s, const R* B, int bx, int by) {
+    __shared__ double red[8];
+    const int k = bx, c = by;
+    const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+    const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+    double acc = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) {
+        const R v = i < s.N ? B[(int64_t)c * s.N + i] : (R)0;
+        s.Bw[(int64_t)c * s.Npad + i] = v;
+        acc += (double)v * (double)v;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) s.ynp[(int64_t)k * s.T + c] = acc;
+}
+
+template <typename R>
+__device__ __forceinline__ void init_state_body(KrylovState<R> s, int bx, int by) {
+    __shared__ double sh_inv;
+    const int k = bx, c = by, tid = threadIdx.x;
+    const int T = s.T, Q = s.Q;
+    if (tid < 32) {
+        double b2 = 0.0;
+        for (int kk = tid; kk < s.nchunks; kk += 32) b2 += s.ynp[(int64_t)kk * T + c];
+        b2 = warp_sum(b2);
+        const double b1 = sqrt(b2);
+        if (tid == 0) {
+            sh_inv = b1 > 0.0 ? 1.0 / b1 : 0.0;
+            if (k == 0) {
+                s.beta1[c] = b1;
+                s.beta[c] = 0.0;
+                s.beta[T + c] = 0.0;
+                s.status[c] = b1 > 0.0 ? kColRunning : kColExact;
+                s.iters[c] = 0;
+                s.brk[c] = 0;
+            }
+        }
+        if (k == 0 && tid < Q) {
+            for (int par = 0; par < 2; ++par) {
+                double* g = s.giv + (((int64_t)par * Q + tid) * T + c) * 5;
+                g[0] = 1.0; g[1] = 0.0; g[2] = 1.0; g[3] = 0.0; g[4] = b1;
+            }
+            s.phifinal[(int64_t)tid * T + c] = b1;
+        }
+    }
+    __syncthreads();
+    const R inv = (R)sh_inv;
+    const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+    const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+    const int64_t col = (int64_t)c * s.Npad;
+    for (int64_t i = i0 + tid; i < i1; i += 256) {
+        s.QA[col + i] = s.Bw[col + i] * inv;
+        s.QB[col + i] = (R)0;
+        s.Y[col + i] = (R)0;
+        s.Ylo[col + i] = (R)0;
+    }
+    for (int e = 0; e < 2 * Q; ++e) {
+        R* d = s.D + ((int64_t)e * T + c) * s.Npad;
+        for (int64_t i = i0 + tid; i < i1; i += 256) d[i] = (R)0;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int final_pass, int bx, int by) {
+    if (!final_pass && *s.all_done) return;
+    __shared__ double red[8][3];
+    __shared__ R co_delta[CIQ_MAX_Q], co_eps[CIQ_MAX_Q], co_invg[CIQ_MAX_Q], co_ct[CIQ_MAX_Q];
+    __shared__ R sh_ahi, sh_alo, sh_invb;
+    __shared__ int sh_skip;
+    const int k = bx, c = by, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int T = s.T, Q = s.Q;
+    const int pin = j & 1, pout = (j + 1) & 1;
+    const double* gin = s.giv + (int64_t)pin * Q * T * 5;
+    double* gout = s.giv + (int64_t)pout * Q * T * 5;
+    const double* w = s.nodes + kNodeW;
+    const double* t = s.nodes + kNodeT;
+    const double lmin = s.nodes[kNodeLmin];
+
+    // 1. Decision for step j-1.
+    if (warp == 0) {
+        const int st = s.status[c];
+        int code = kColRunning;
+        if (st == kColRunning && j > 1) {
+            if (s.brk[c]) {
+                code = s.brk[c];
+            } else if (s.tol > 0.0) {
+                const double ph = lane < Q ? fabs(gin[((int64_t)lane * T + c) * 5 + 4]) : 0.0;
+                if (s.stop_rule == CIQ_STOP_RESIDUAL) {
+                    if (warp_max(ph) <= s.tol * s.beta1[c]) code = kColConverged;
+                } else {
+                    const double cq = lane < Q ? (s.op == kOpSqrtIdentity ? w[lane] * t[lane] : w[lane]) : 0.0;
+                    const double bound = warp_sum(lane < Q ? cq * ph / (t[lane] + lmin) : 0.0);
+                    double yn = 0.0;
+                    const double* yp = s.ynp + (int64_t)((j - 1) & 1) * s.nchunks * T;
+                    for (int kk = lane; kk < s.nchunks; kk += 32) yn += yp[(int64_t)kk * T + c];
+                    yn = warp_sum(yn);
+                    if (bound <= s.tol * sqrt(yn)) code = kColConverged;
+                }
+            }
+            if (final_pass && code == kColRunning) code = s.tol > 0.0 ? kColMaxIter : kColFixedIter;
+        }
+        const bool frozen = (st != kColRunning) || (code != kColRunning);
+        if (lane == 0) sh_skip = frozen || final_pass;
+        if (k == 0 && (frozen || final_pass)) {
+            if (st == kColRunning) {
+                if (lane < Q) s.phifinal[(int64_t)lane * T + c] = gin[((int64_t)lane * T + c) * 5 + 4];
+                if (lane == 0) s.status[c] = code != kColRunning ? code : (s.tol > 0.0 ? kColMaxIter : kColFixedIter);
+            }
+            if (lane == 0 && !final_pass) {
+                const int old = atomicAdd(&s.cnt[j], 1);
+                if (old + 1 == T) atomicExch(s.all_done, 1);
+            }
+        }
+    }
+    __syncthreads();
+    if (sh_skip) return;
+
+    // 2. alpha_j, beta_{j+1} from the MVM partial sums.
+    double qp = 0.0, pp = 0.0, qq = 0.0;
+    for (int r = tid; r < s.nparts; r += 256) {
+        const double* src = s.partials + ((int64_t)r * T + c) * 3;
+        qp += src[0]; pp += src[1]; qq += src[2];
+    }
+    qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
+    if (lane == 0) { red[warp][0] = qp; red[warp][1] = pp; red[warp][2] = qq; }
+    __syncthreads();
+    if (warp == 0) {
+        qp = lane < 8 ? red[lane][0] : 0.0;
+        pp = lane < 8 ? red[lane][1] : 0.0;
+        qq = lane < 8 ? red[lane][2] : 0.0;
+        qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
+        const double alpha = qp;
+        const double b2 = pp - 2.0 * alpha * qp + alpha * alpha * qq;
+        const double beta_next = sqrt(fmax(b2, 0.0));
+        const double beta_j = s.beta[pin * T + c];
+        const bool nan = !isfinite(alpha) || !isfinite(beta_next);
+        const bool bd = nan || !(beta_next > s.breakdown_rtol * (fabs(alpha) + beta_j));
+        const double bu = bd ? 0.0 : beta_next;
+        // 3. Givens QR update for every shift (one lane per shift).
+        if (lane < Q) {
+            const double* g = gin + ((int64_t)lane * T + c) * 5;
+            const double c1 = g[0], s1 = g[1], c2 = g[2], s2 = g[3], ph = g[4];
+            const double abar = alpha + t[lane];
+            const double eps = s2 * beta_j;
+            const double dbar = c2 * beta_j;
+            const double delta = c1 * dbar + s1 * abar;
+            const double gbar = -s1 * dbar + c1 * abar;
+            const double gamma = sqrt(gbar * gbar + bu * bu);
+            const double cj = gbar / gamma, sj = bu / gamma;
+            const double tau = cj * ph;
+            const double cq = s.op == kOpSqrtIdentity ? w[lane] * t[lane] : w[lane];
+            co_delta[lane] = (R)delta;
+            co_eps[lane] = (R)eps;
+            co_invg[lane] = (R)(1.0 / gamma);
+            co_ct[lane] = (R)(cq * tau);
+            if (k == 0) {
+                double* go = gout + ((int64_t)lane * T + c) * 5;
+                go[0] = cj; go[1] = sj; go[2] = c1; go[3] = s1; go[4] = -sj * ph;
+            }
+        }
+        if (lane == 0) {
+            const R ahi = (R)alpha;
+            sh_ahi = ahi;
+            sh_alo = (R)(alpha - (double)ahi);
+            sh_invb = bd ? (R)0 : (R)(1.0 / beta_next);
+            sh_skip = nan;
+            if (k == 0) {
+                s.beta[pout * T + c] = bu;
+                s.iters[c] = j;
+                s.brk[c] = nan ? kColNaN : (bd ? kColExact : 0);
+            }
+        }
+    }
+    __syncthreads();
+    if (sh_skip) return;
+
+    // 4. Vector updates for this chunk of rows.
+    const R ahi = sh_ahi, alo = sh_alo, invb = sh_invb;
+    const int64_t col = (int64_t)c * s.Npad;
+    const R* q_j = ((j & 1) ? s.QA : s.QB) + col;
+    R* pbuf = ((j & 1) ? s.QB : s.QA) + col;
+    R* y = s.Y + col;
+    R* ylo = s.Ylo + col;
+    const R* b = s.Bw + col;
+    const R sumw = (R)s.nodes[kNodeSumW];
+    const int64_t dstride = (int64_t)T * s.Npad;
+    R* d_prev = s.D + (int64_t)((j - 1) & 1) * Q * dstride + col;   // d_{j-1}
+    R* d_old = s.D + (int64_t)(j & 1) * Q * dstride + col;          // d_{j-2}, overwritten by d_j
+    const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+    const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+    double ysq = 0.0;
+    for (int64_t i = i0 + tid; i < i1; i += 256) {
+        const R q = q_j[i];
+        R pn = pbuf[i];
+        pn = fma(-ahi, q, pn);
+        pn = fma(-alo, q, pn);
+        pbuf[i] = pn * invb;
+        R acc = (R)0;
+        for (int qq2 = 0; qq2 < Q; ++qq2) {
+            const int64_t off = (int64_t)qq2 * dstride + i;
+            const R dn = (q - co_delta[qq2] * d_prev[off] - co_eps[qq2] * d_old[off]) * co_invg[qq2];
+            d_old[off] = dn;
+            acc = fma(co_ct[qq2], dn, acc);
+        }
+        // y += acc as a (leading, trailing) pair: Knuth's 2Sum error term goes
+        // to the trailing part, so the sum keeps ~2x R's precision.  The K^{1/2}
+        // identity form later subtracts y from (sum w) b, which cancels.
+        const R yh = y[i];
+        const R sum = yh + acc;
+        const R bp = sum - yh;
+        const R err = (yh - (sum - bp)) + (acc - bp);
+        const R yl = ylo[i] + err;
+        y[i] = sum;
+        ylo[i] = yl;
+        const R yv = sum + yl;
+        const R est = s.op == kOpSqrtIdentity ? sumw * b[i] - yv : yv;
+        ysq += (double)est * (double)est;
+    }
+    // 5. Partial ||a_j||^2 for the next decision.
+    ysq = warp_sum(ysq);
+    __shared__ double red2[8];
+    if (lane == 0) red2[warp] = ysq;
+    __syncthreads();
+    if (tid == 0) {
+        double r = 0.0;
+        for (int ww = 0; ww < 8; ++ww) r += red2[ww];
+        s.ynp[((int64_t)(j & 1) * s.nchunks + k) * T + c] = r;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void combine_body(KrylovState<R> s, R* out, int bx, int by) {
+    const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
+    const int c = by;
+    if (i >= s.N) return;
+    const int64_t src = (int64_t)c * s.Npad + i;
+    const double yv = (double)s.Y[src] + (double)s.Ylo[src];
+    double v = yv;
+    if (s.op == kOpSqrtIdentity) v = s.nodes[kNodeSumW] * (double)s.Bw[src] - yv;
+    if (s.op == kOpSqrtMvm) s.Y[src] = (R)yv;      // folded into one vector for the final MVM
+    out[(int64_t)c * s.N + i] = (R)v;
+}
+
+// summary[0] max iters, [1] min iters, [2] converged columns, [3] max |phibar|/||b||,
+// [4] max errbound/||a||, [5] worst status, [6] NaN columns.
+template <typename R>
+__device__ __forceinline__ void summary_body(KrylovState<R> s, int final_j, int bx, int by) {
+    if (threadIdx.x != 0) return;
+    const int T = s.T, Q = s.Q;
+    const double* w = s.nodes + kNodeW;
+    const double* t = s.nodes + kNodeT;
+    const double lmin = s.nodes[kNodeLmin];
+    int itmax = 0, itmin = 1 << 30, conv = 0, nans = 0, worst = 0;
+    double rmax = 0.0, emax = 0.0;
+    const double* yp = s.ynp + (int64_t)(final_j & 1) * s.nchunks * T;
+    for (int c = 0; c < T; ++c) {
+        const int it = s.iters[c];
+        itmax = max(itmax, it);
+        itmin = min(itmin, it);
+        const int st = s.status[c];
+        if (st == kColConverged || st == kColExact) ++conv;
+        if (st == kColNaN) ++nans;
+        worst = max(worst, st);
+        const double b1 = s.beta1[c];
+        double bound = 0.0, rm = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            const double ph = fabs(s.phifinal[(int64_t)q * T + c]);
+            rm = fmax(rm, ph);
+            const double cq = s.op == kOpSqrtIdentity ? w[q] * t[q] : w[q];
+            bound += cq * ph / (t[q] + lmin);
+        }
+        if (b1 > 0.0) rmax = fmax(rmax, rm / b1);
+        double yn = 0.0;
+        for (int kk = 0; kk < s.nchunks; ++kk) yn += yp[(int64_t)kk * T + c];
+        if (yn > 0.0) emax = fmax(emax, bound / sqrt(yn));
+    }
+    s.summary[0] = itmax;
+    s.summary[1] = T > 0 ? itmin : 0;
+    s.summary[2] = conv;
+    s.summary[3] = rmax;
+    s.summary[4] = emax;
+    s.summary[5] = worst;
+    s.summary[6] = nans;
+}
+
+// ---------------------------------------------------------------- pre-pass --
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+template <typename R>
+__device__ __forceinline__ void lanczos_init_a_body(LanczosState<R> s, const R* start, uint64_t seed, int bx, int by) {
+    __shared__ double red[8];
+    const int k = bx;
+    const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+    const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+    double acc = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) {
+        R v = (R)0;
+        if (i < s.N) v = start ? start[i] : (R)(2.0 * splitmix_uniform(seed, (uint64_t)i) - 1.0);
+        s.LA[i] = v;
+        s.LB[i] = (R)0;
+        acc += (double)v * (double)v;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) s.ynp[k] = acc;
+}
+
+template <typename R>
+__device__ __forceinline__ void lanczos_init_b_body(LanczosState<R> s, int bx, int by) {
+    __shared__ double sh_inv;
+    const int k = bx;
+    if (threadIdx.x < 32) {
+        double b2 = 0.0;
+        for (int kk = threadIdx.x; kk < s.nchunks; kk += 32) b2 += s.ynp[kk];
+        b2 = warp_sum(b2);
+        if (threadIdx.x == 0) {
+            const double b1 = sqrt(b2);
+            sh_inv = b1 > 0.0 ? 1.0 / b1 : 0.0;
+            if (k == 0) {
+                s.beta[0] = b1;
+                s.bpar[0] = 0.0;
+                s.bpar[1] = 0.0;
+                *s.jeff = 0;
+                *s.done = b1 > 0.0 ? 0 : 1;
+            }
+        }
+    }
+    __syncthreads();
+    const R inv = (R)sh_inv;
+    const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+    const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) s.LA[i] *= inv;
+}
+
+template <typename R>
+__device__ __forceinline__ void lanczos_step_body(LanczosState<R> s, int j, int bx, int by) {
+    if (*s.done) return;
+    __shared__ double red[8][3];
+    __shared__ R sh_ahi, sh_alo, sh_invb;
+    const int k = bx, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double qp = 0.0, pp = 0.0, qq = 0.0;
+    for (int r = tid; r < s.nparts; r += 256) {
+        qp += s.partials[r * 3 + 0]; pp += s.partials[r * 3 + 1]; qq += s.partials[r * 3 + 2];
+    }
+    qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
+    if (lane == 0) { red[warp][0] = qp; red[warp][1] = pp; red[warp][2] = qq; }
+    __syncthreads();
+    if (tid == 0) {
+        qp = pp = qq = 0.0;
+        for (int w = 0; w < 8; ++w) { qp += red[w][0]; pp += red[w][1]; qq += red[w][2]; }
+        const double alpha = qp;
+        const double beta_next = sqrt(fmax(pp - 2.0 * alpha * qp + alpha * alpha * qq, 0.0));
+        const double beta_j = s.bpar[j & 1];
+        const bool bd = !isfinite(alpha) || !(beta_next > 1e-12 * (fabs(alpha) + beta_j));
+        const R ahi = (R)alpha;
+        sh_ahi = ahi;
+        sh_alo = (R)(alpha - (double)ahi);
+        sh_invb = bd ? (R)0 : (R)(1.0 / beta_next);
+        if (k == 0) {
+            s.alpha[j - 1] = alpha;
+            s.beta[j] = bd ? 0.0 : beta_next;
+            s.bpar[(j + 1) & 1] = bd ? 0.0 : beta_next;
+            *s.jeff = j;
+            if (bd) *s.done = 1;
+        }
+    }
+    __syncthreads();
+    const R ahi = sh_ahi, alo = sh_alo, invb = sh_invb;
+    const R* q_j = (j & 1) ? s.LA : s.LB;
+    R* pbuf = (j & 1) ? s.LB : s.LA;
+    const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+    const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+    for (int64_t i = i0 + tid; i < i1; i += 256) {
+        R pn = pbuf[i];
+        const R q = q_j[i];
+        pn = fma(-ahi, q, pn);
+        pn = fma(-alo, q, pn);
+        pbuf[i] = pn * invb;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void bounds_nodes_body(LanczosState<R> s, double* nodes, int Q, double noise,
+                                    double lmax_margin, double lmin_div, int bx, int by) {
+    if (threadIdx.x != 0 || bx != 0) return;
+    const int J = *s.jeff;
+    double th_min = 0.0, th_max = 0.0;
+    if (J >= 1) {
+        th_min = tridiag_extreme(s.alpha, s.beta, J, false);
+        th_max = tridiag_extreme(s.alpha, s.beta, J, true);
+    }
+    const double lmax = lmax_margin * th_max;
+    double lmin = noise > 0.0 ? noise : th_min / lmin_div;
+    if (!(lmin > 0.0)) lmin = 1e-300;
+    double w[CIQ_MAX_Q], t[CIQ_MAX_Q];
+    const double lmax_u = fmax(lmax, lmin);
+    quad_nodes(lmin, lmax_u, Q, w, t);
+    double sw = 0.0;
+    for (int q = 0; q < CIQ_MAX_Q; ++q) {
+        nodes[kNodeW + q] = q < Q ? w[q] : 0.0;
+        nodes[kNodeT + q] = q < Q ? t[q] : 0.0;
+        if (q < Q) sw += w[q];
+    }
+    nodes[kNodeLmin] = lmin;
+    nodes[kNodeLmax] = lmax_u;
+    nodes[kNodeRitzMin] = th_min;
+    nodes[kNodeRitzMax] = th_max;
+    nodes[kNodeSumW] = sw;
+    nodes[kNodeLanczosSteps] = J;
+}
+
+// Nodes for given bounds (one thread).
+__device__ __forceinline__ void nodes_from_bounds_body(double* nodes, int Q, double lmin, double lmax) {
+    double w[CIQ_MAX_Q], t[CIQ_MAX_Q];
+    quad_nodes(lmin, lmax, Q, w, t);
+    double sw = 0.0;
+    for (int q = 0; q < CIQ_MAX_Q; ++q) {
+        nodes[kNodeW + q] = q < Q ? w[q] : 0.0;
+        nodes[kNodeT + q] = q < Q ? t[q] : 0.0;
+        if (q < Q) sw += w[q];
+    }
+    nodes[kNodeLmin] = lmin;
+    nodes[kNodeLmax] = lmax;
+    nodes[kNodeRitzMin] = 0.0;
+    nodes[kNodeRitzMax] = 0.0;
+    nodes[kNodeSumW] = sw;
+    nodes[kNodeLanczosSteps] = 0.0;
+}
+
+}  // namespace
+}  // namespace ciq

@@ -37,6 +37,8 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_ciq._Options) == 112
     assert ctypes.sizeof(_ciq._Kernel) == 32
     assert ctypes.sizeof(_ciq._Info) == 16 + 6 * 8 + 2 * 32 * 8 + 8 + 4 * 8 + 8
+    # ciq_problem: X, N, d (+pad), kern, B, T (+pad), out, lmin, lmax
+    assert ctypes.sizeof(_ciq._Problem) == 8 + 8 + 8 + 32 + 8 + 8 + 8 + 8 + 8
 
 
 def test_status_strings_and_defaults():
@@ -88,3 +90,30 @@ def test_workspace_bytes_grows_with_problem():
     c = P.ciq_workspace_bytes(1000, 3, 8, 16)
     assert 0 < a < b < c
     assert P.ciq_workspace_bytes(0, 3, 1, 8) == 0
+
+
+def test_batched_validates_before_the_device():
+    lib = P.lib()
+    o = _ciq.make_options()
+    assert lib.ciq_sqrt_batched(None, 1, 8, 1e-4, ctypes.byref(o), None, None) == _ciq.CIQ_ERR_ARG
+    arr = (_ciq._Problem * 1)()
+    assert lib.ciq_sqrt_batched(arr, 0, 8, 1e-4, ctypes.byref(o), None, None) == _ciq.CIQ_ERR_ARG
+    X = np.zeros((10, 3), np.float32)
+    B = np.zeros((2, 10), np.float32)
+    X2 = np.zeros((12, 3), np.float32)
+    B2 = np.zeros((3, 12), np.float32)
+    k = P.Kernel("rbf", 0.5, 1.0, 1e-2)
+    good = dict(X=X, B=B, kernel=k)
+    cases = [
+        ([good], dict(precision="fp16"), _ciq.CIQ_ERR_UNSUPPORTED),                # tensor-core tiles
+        ([good], dict(mvm="stored"), _ciq.CIQ_ERR_UNSUPPORTED),
+        ([good], dict(sqrt_form="mvm"), _ciq.CIQ_ERR_UNSUPPORTED),
+        ([good], dict(max_iter=0), _ciq.CIQ_ERR_ARG),
+        ([good, dict(X=X2, B=B2, kernel=k)], {}, _ciq.CIQ_ERR_ARG),                # T differs
+        ([dict(X=X, B=B, kernel=k, lmin=2.0, lmax=1.0)], {}, _ciq.CIQ_ERR_ARG),   # lmax < lmin
+        ([good], {}, _ciq.CIQ_ERR_ARG),                                            # host pointers
+    ]
+    for probs, kw, want in cases:
+        with pytest.raises(P.CiqError) as e:
+            P.ciq_sqrt_batched(probs, 8, 1e-4, **kw)
+        assert e.value.status == want, (kw, want)
