@@ -143,6 +143,8 @@ typedef struct {
     double t_step_ms;         /* profile: sum over msMINRES recurrence launches */
     int mvm_launches;         /* profile: msMINRES kernel-MVM launches timed */
     int step_launches;        /* profile: recurrence launches timed */
+    double ritz_max_solve;    /* largest Ritz value of column 0's msMINRES tridiagonal
+                                 (ciq_*_batched_learned only; else 0) */
 } ciq_info;
 
 /* Human-readable name of a status code (static string). */
@@ -253,6 +255,72 @@ ciq_status ciq_sqrt_batched(const ciq_problem* probs, int P, int Q, double tol, 
                             ciq_info* infos, ciq_stream_t stream);
 ciq_status ciq_invsqrt_batched(const ciq_problem* probs, int P, int Q, double tol,
                                const ciq_options* opt, ciq_info* infos, ciq_stream_t stream);
+
+/* ---- learned spectral-bound predictor (no counterpart in the paper) ----
+ *
+ * A regression network (CIQ_MLP_INPUTS -> 64 tanh -> 64 tanh ->
+ * CIQ_MLP_OUTPUTS) that predicts, from a problem's description, what the
+ * Lanczos pre-pass and the msMINRES run would report: log theta_min,
+ * log theta_max (the pre-pass's Ritz extremes, App. B.2) and log of the
+ * iteration count.  Used by ciq_*_batched_learned to skip the pre-pass.
+ *
+ * Inputs of a problem (float[CIQ_MLP_INPUTS]): log N, d, kernel type (0 RBF,
+ * 1 Matern-5/2), log lengthscale, log outputscale, log max(sigma^2, 1e-12),
+ * the mean of each of the CIQ_MAX_DIM coordinates of X, then the population
+ * variance of each (0 for coordinates >= d).
+ *
+ * Parameters (float[CIQ_MLP_PARAMS], device): input means [0,38), input
+ * standard deviations [38,76), output means [76,79), output standard
+ * deviations [79,82), then W1 (38 x 64, input-major), b1[64], W2 (64 x 64),
+ * b2[64], W3 (64 x 3), b3[3].  Loss: mean over samples and outputs of the
+ * squared error of the standardised outputs.  All arrays below are device
+ * pointers, row-major (one sample per row); calls are asynchronous on
+ * stream unless stated. */
+#define CIQ_MLP_INPUTS 38
+#define CIQ_MLP_OUTPUTS 3
+#define CIQ_MLP_PARAMS 6933
+
+/* F[p * CIQ_MLP_INPUTS ..] = inputs of problem p (X read from the device). */
+ciq_status ciq_mlp_features(const ciq_problem* probs, int P, float* F, ciq_stream_t stream);
+/* theta[0, 82) = column means and standard deviations of F (n x 38) and
+ * Y (n x 3); a constant column gets standard deviation 1. */
+ciq_status ciq_mlp_normaliser(const float* F, const float* Y, int n, float* theta, ciq_stream_t stream);
+/* Glorot-uniform weights, zero biases: entry k of a weight matrix with fan
+ * in a and fan out b is sqrt(6/(a+b)) (2u_k - 1), u_k the splitmix64 uniform
+ * number k of seed.  theta[0, 82) is left as it is. */
+ciq_status ciq_mlp_init(float* theta, uint64_t seed, ciq_stream_t stream);
+/* Full-batch loss (host double) and its gradient grad[CIQ_MLP_PARAMS]
+ * (device doubles, 0 on the normaliser entries), FP32 arithmetic. */
+ciq_status ciq_mlp_loss_grad(const float* theta, const float* F, const float* Y, int n, double* loss,
+                             double* grad, ciq_stream_t stream);
+/* Adam steps first_step .. first_step + steps - 1 (bias-corrected; moments
+ * 0.9, 0.999, eps 1e-8) on minibatches of `batch` rows drawn with
+ * replacement: row k of step t is floor(u n), u the splitmix64 uniform number
+ * (t-1) batch + k of seed.  adam: 2 x CIQ_MLP_PARAMS floats (first, second
+ * moments), zero before the first step.  losses: NULL or `steps` floats
+ * (the minibatch loss before each step).  One CTA runs all steps. */
+ciq_status ciq_mlp_train(float* theta, float* adam, const float* F, const float* Y, int n, int steps, int batch,
+                         float lr, uint64_t seed, int first_step, float* losses, ciq_stream_t stream);
+/* out (n x 3) = predictions in the output units; bf16 != 0 rounds the
+ * weights and the activations between layers to BF16 (FP32 accumulation). */
+ciq_status ciq_mlp_predict(const float* theta, const float* F, int n, float* out, int bf16, ciq_stream_t stream);
+
+/* The batched solves with bounds from the network instead of the pre-pass.
+ * For problem p with predictions (l0, l1, l2): lmax = opt->lmax_margin
+ * exp(l1 + margin), lmin = sigma^2 if sigma^2 > 0, else exp(l0) /
+ * opt->lmin_div (BF16 inference).  Problems whose own lmin, lmax are set keep
+ * them.  After the solve, the largest Ritz value of each problem's msMINRES
+ * tridiagonal (column 0, all its iterations) is checked against the lmax
+ * used: a problem whose Krylov space shows an eigenvalue above it, or whose
+ * solve produced a non-finite coefficient, is solved again with the Lanczos
+ * pre-pass (fallback[p] = 1, host int array, may be NULL).  infos as in
+ * ciq_sqrt_batched (of the solve whose output is kept); theta: device. */
+ciq_status ciq_sqrt_batched_learned(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                                    const float* theta, double margin, ciq_info* infos, int* fallback,
+                                    ciq_stream_t stream);
+ciq_status ciq_invsqrt_batched_learned(const ciq_problem* probs, int P, int Q, double tol,
+                                       const ciq_options* opt, const float* theta, double margin,
+                                       ciq_info* infos, int* fallback, ciq_stream_t stream);
 
 /* Device workspace bytes a solve with these sizes and options needs. */
 size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt);

@@ -67,7 +67,8 @@ class _Info(ctypes.Structure):
                 ("t", ctypes.c_double * CIQ_MAX_Q), ("q", ctypes.c_int), ("launches", ctypes.c_int),
                 ("t_total_ms", ctypes.c_double), ("t_prepass_ms", ctypes.c_double),
                 ("t_mvm_ms", ctypes.c_double), ("t_step_ms", ctypes.c_double),
-                ("mvm_launches", ctypes.c_int), ("step_launches", ctypes.c_int)]
+                ("mvm_launches", ctypes.c_int), ("step_launches", ctypes.c_int),
+                ("ritz_max_solve", ctypes.c_double)]
 
 
 class _Problem(ctypes.Structure):
@@ -109,6 +110,14 @@ def lib() -> ctypes.CDLL:
         "ciq_noalloc_scratch_floats": (S, []),
         "ciq_sqrt_batched": (I, [ctypes.POINTER(_Problem), I, I, D, OP, IP, P]),
         "ciq_invsqrt_batched": (I, [ctypes.POINTER(_Problem), I, I, D, OP, IP, P]),
+        "ciq_sqrt_batched_learned": (I, [ctypes.POINTER(_Problem), I, I, D, OP, P, D, IP, P, P]),
+        "ciq_invsqrt_batched_learned": (I, [ctypes.POINTER(_Problem), I, I, D, OP, P, D, IP, P, P]),
+        "ciq_mlp_features": (I, [ctypes.POINTER(_Problem), I, P, P]),
+        "ciq_mlp_normaliser": (I, [P, P, I, P, P]),
+        "ciq_mlp_init": (I, [P, U64, P]),
+        "ciq_mlp_loss_grad": (I, [P, P, P, I, DP, P, P]),
+        "ciq_mlp_train": (I, [P, P, P, P, I, I, I, ctypes.c_float, U64, I, P, P]),
+        "ciq_mlp_predict": (I, [P, P, I, P, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -202,7 +211,7 @@ def _info_dict(info: _Info, status: int) -> dict:
                 w=np.array(info.w[:q]), t=np.array(info.t[:q]), launches=info.launches,
                 t_total_ms=info.t_total_ms, t_prepass_ms=info.t_prepass_ms, t_mvm_ms=info.t_mvm_ms,
                 t_step_ms=info.t_step_ms, mvm_launches=info.mvm_launches,
-                step_launches=info.step_launches)
+                step_launches=info.step_launches, ritz_max_solve=info.ritz_max_solve)
 
 
 def _check(status: int, where: str, allow=(CIQ_OK, CIQ_NOT_CONVERGED)):
@@ -334,30 +343,44 @@ def ciq_kernel_mvm_noalloc(X, kernel, V, out=None):
     return out
 
 
-def _solve_batched(name, problems, Q, tol, **opts):
-    """problems: sequence of dicts with X (N, d), kernel (Kernel), B (T, N)
-    device tensors, optional out (T, N) and optional lmin, lmax."""
+CIQ_MLP_INPUTS = 38
+CIQ_MLP_OUTPUTS = 3
+CIQ_MLP_PARAMS = 6933
+
+
+def _problem_array(problems, need_b=True):
     P = len(problems)
     arr = (_Problem * P)()
     outs = []
     for i, pr in enumerate(problems):
-        X, B = pr["X"], pr["B"]
+        X = pr["X"]
         N, d = X.shape
+        arr[i].X = _ptr(X).value
+        arr[i].N = N
+        arr[i].d = d
+        arr[i].kern = pr["kernel"].c()
+        arr[i].lmin = float(pr.get("lmin") or 0.0)
+        arr[i].lmax = float(pr.get("lmax") or 0.0)
+        if not need_b:
+            continue
+        B = pr["B"]
         if B.shape[1] != N:
             raise ValueError("B must have shape (T, N)")
         out = pr.get("out")
         if out is None:
             out = _empty_like_rhs(B, np.float32)
         outs.append(out)
-        arr[i].X = _ptr(X).value
-        arr[i].N = N
-        arr[i].d = d
-        arr[i].kern = pr["kernel"].c()
         arr[i].B = _ptr(B).value
         arr[i].T = B.shape[0]
         arr[i].out = _ptr(out).value
-        arr[i].lmin = float(pr.get("lmin") or 0.0)
-        arr[i].lmax = float(pr.get("lmax") or 0.0)
+    return arr, outs
+
+
+def _solve_batched(name, problems, Q, tol, **opts):
+    """problems: sequence of dicts with X (N, d), kernel (Kernel), B (T, N)
+    device tensors, optional out (T, N) and optional lmin, lmax."""
+    P = len(problems)
+    arr, outs = _problem_array(problems)
     o = make_options(**opts)
     infos = (_Info * P)()
     first = problems[0]
@@ -375,3 +398,83 @@ def ciq_sqrt_batched(problems, Q, tol=0.0, **opts):
 def ciq_invsqrt_batched(problems, Q, tol=0.0, **opts):
     """K_p^{-1/2} B_p for every problem of the batch. Returns (outs, infos)."""
     return _solve_batched("ciq_invsqrt_batched", problems, Q, tol, **opts)
+
+
+def _solve_batched_learned(name, problems, Q, tol, theta, margin=0.0, **opts):
+    P = len(problems)
+    arr, outs = _problem_array(problems)
+    o = make_options(**opts)
+    infos = (_Info * P)()
+    fb = (ctypes.c_int * P)()
+    first = problems[0]
+    st = getattr(lib(), name)(arr, P, int(Q), float(tol), ctypes.byref(o), _ptr(theta), float(margin), infos, fb,
+                              _stream(first["X"], first["B"], theta))
+    _check(st, name)
+    res = [_info_dict(infos[i], st) for i in range(P)]
+    for i in range(P):
+        res[i]["fallback"] = int(fb[i])
+    return outs, res
+
+
+def ciq_sqrt_batched_learned(problems, Q, tol, theta, margin=0.0, **opts):
+    """K_p^{1/2} B_p with bounds from the trained network ``theta`` (device,
+    CIQ_MLP_PARAMS floats); infos carry ``fallback`` per problem."""
+    return _solve_batched_learned("ciq_sqrt_batched_learned", problems, Q, tol, theta, margin, **opts)
+
+
+def ciq_invsqrt_batched_learned(problems, Q, tol, theta, margin=0.0, **opts):
+    """K_p^{-1/2} B_p with bounds from the trained network (see ciq_sqrt_batched_learned)."""
+    return _solve_batched_learned("ciq_invsqrt_batched_learned", problems, Q, tol, theta, margin, **opts)
+
+
+def ciq_mlp_features(problems, out=None):
+    """(P, 38) device tensor of network inputs; problems need X and kernel."""
+    import torch
+    arr, _ = _problem_array(problems, need_b=False)
+    X0 = problems[0]["X"]
+    if out is None:
+        out = torch.empty((len(problems), CIQ_MLP_INPUTS), dtype=torch.float32, device=X0.device)
+    st = lib().ciq_mlp_features(arr, len(problems), _ptr(out), _stream(X0, out))
+    _check(st, "ciq_mlp_features", allow=(CIQ_OK,))
+    return out
+
+
+def ciq_mlp_normaliser(F, Y, theta):
+    st = lib().ciq_mlp_normaliser(_ptr(F), _ptr(Y), int(F.shape[0]), _ptr(theta), _stream(F, Y, theta))
+    _check(st, "ciq_mlp_normaliser", allow=(CIQ_OK,))
+    return theta
+
+
+def ciq_mlp_init(theta, seed):
+    st = lib().ciq_mlp_init(_ptr(theta), int(seed), _stream(theta))
+    _check(st, "ciq_mlp_init", allow=(CIQ_OK,))
+    return theta
+
+
+def ciq_mlp_loss_grad(theta, F, Y, grad=None):
+    """(loss, grad): full-batch loss and its gradient (float64 device tensor)."""
+    import torch
+    if grad is None:
+        grad = torch.empty(CIQ_MLP_PARAMS, dtype=torch.float64, device=theta.device)
+    loss = ctypes.c_double()
+    st = lib().ciq_mlp_loss_grad(_ptr(theta), _ptr(F), _ptr(Y), int(F.shape[0]), ctypes.byref(loss), _ptr(grad),
+                                 _stream(theta, F, Y, grad))
+    _check(st, "ciq_mlp_loss_grad", allow=(CIQ_OK,))
+    return loss.value, grad
+
+
+def ciq_mlp_train(theta, adam, F, Y, steps, batch, lr, seed, first_step=1, losses=None):
+    st = lib().ciq_mlp_train(_ptr(theta), _ptr(adam), _ptr(F), _ptr(Y), int(F.shape[0]), int(steps), int(batch),
+                             float(lr), int(seed), int(first_step), _ptr(losses), _stream(theta, adam, F, Y))
+    _check(st, "ciq_mlp_train", allow=(CIQ_OK,))
+    return theta
+
+
+def ciq_mlp_predict(theta, F, out=None, bf16=True):
+    import torch
+    if out is None:
+        out = torch.empty((F.shape[0], CIQ_MLP_OUTPUTS), dtype=torch.float32, device=F.device)
+    st = lib().ciq_mlp_predict(_ptr(theta), _ptr(F), int(F.shape[0]), _ptr(out), 1 if bf16 else 0,
+                               _stream(theta, F, out))
+    _check(st, "ciq_mlp_predict", allow=(CIQ_OK,))
+    return out

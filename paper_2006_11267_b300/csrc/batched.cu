@@ -147,6 +147,12 @@ __global__ void batched_summary_kernel(const BatchProblem* probs, int final_j, d
     double* dst = packed + (int64_t)p * kSummaryStride;
     for (int k = 0; k < 8; ++k) dst[k] = s.summary[k];
     for (int k = 0; k < kNodeCount; ++k) dst[8 + k] = bp.nodes[k];
+    double th = 0.0;
+    if (s.tri) {
+        const int J = s.iters[0];
+        if (J >= 1) th = tridiag_extreme(s.tri, s.tri + s.jmax + 1, J, true);
+    }
+    dst[8 + kNodeCount] = th;
 }
 
 // Exclusive scan of one int per thread over a 1024-thread block; *total gets the sum.

@@ -16,6 +16,7 @@
 
 #include "batched.cuh"
 #include "krylov.cuh"
+#include "mlp.cuh"
 #include "mvm_stored.cuh"
 #include "mvm_tc.cuh"
 #include "spectral.cuh"
@@ -125,11 +126,12 @@ struct Plan {
     int precision;
     bool stage_x, stage_b, stage_out, stage_start;
     bool prepass;
+    bool tri_on = false;          // record column 0's msMINRES tridiagonal
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB;
     R *sx, *sb, *sout, *sstart;
     float* Kst;
-    double *partials, *ynp, *beta, *beta1, *giv, *phifinal, *nodes, *summary;
+    double *partials, *ynp, *beta, *beta1, *giv, *phifinal, *nodes, *summary, *tri;
     double *lpart, *lynp, *bpar, *lalpha, *lbeta;
     int *status, *iters, *brk, *cnt, *all_done, *jeff, *ldone;
     TcPoints tcp;
@@ -158,6 +160,7 @@ struct Plan {
         brk = a.take<int>(T);
         cnt = a.take<int>((size_t)jmax + 2);
         all_done = a.take<int>(1);
+        tri = tri_on ? a.take<double>(2 * (size_t)jmax + 3) : nullptr;
         if (prepass) {
             LA = a.take<R>((size_t)Npad);
             LB = a.take<R>((size_t)Npad);
@@ -217,7 +220,7 @@ KrylovState<R> krylov_state(const Plan<R>& p, int op, const ciq_options& o, doub
     s.partials = p.partials; s.ynp = p.ynp; s.beta = p.beta; s.beta1 = p.beta1;
     s.giv = p.giv; s.phifinal = p.phifinal; s.status = p.status; s.iters = p.iters;
     s.brk = p.brk; s.cnt = p.cnt; s.all_done = p.all_done; s.nodes = p.nodes;
-    s.summary = p.summary; s.jmax = p.jmax; s.op = op; s.stop_rule = o.stop_rule; s.tol = tol;
+    s.summary = p.summary; s.tri = p.tri; s.jmax = p.jmax; s.op = op; s.stop_rule = o.stop_rule; s.tol = tol;
     s.breakdown_rtol = sizeof(R) == 4 ? 1e-6 : 1e-13;
     return s;
 }
@@ -603,8 +606,11 @@ int* pinned_totals() {
     return p;
 }
 
+// record_tri: keep column 0's msMINRES tridiagonal and report its largest
+// Ritz value; packed_out (optional) receives the packed per-problem results.
 ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
-                         ciq_info* infos, cudaStream_t st, int op) {
+                         ciq_info* infos, cudaStream_t st, int op, bool record_tri = false,
+                         std::vector<double>* packed_out = nullptr) {
     if (!probs || P < 1 || P > CIQ_MAX_BATCH || Q < 1 || Q > CIQ_MAX_Q || !(tol >= 0.0)) return CIQ_ERR_ARG;
     ciq_options o;
     ciq_default_options(&o);
@@ -635,6 +641,10 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     size_t off = 0;
     for (int p = 0; p < P; ++p) {
         plans.push_back(make_plan<float>(probs[p].N, probs[p].d, T, Q, o, !given[p], false));
+        if (record_tri) {
+            plans.back().tri_on = true;
+            plans.back().layout(nullptr);
+        }
         offs[p] = off;
         off += round_up((int64_t)plans.back().bytes, kAlign);
     }
@@ -873,9 +883,108 @@ done:
         info->q = Q;
         for (int q = 0; q < Q; ++q) { info->w[q] = nd[kNodeW + q]; info->t[q] = nd[kNodeT + q]; }
         info->launches = launches;
+        info->ritz_max_solve = sm[8 + kNodeCount];
     }
+    if (packed_out) packed_out->swap(packed);
     if (any_nan) return CIQ_ERR_NAN;
     if (any_maxit) return CIQ_NOT_CONVERGED;
+    return CIQ_OK;
+}
+
+// Batched solve with bounds predicted by the network; fallback to the
+// Lanczos pre-pass for problems whose own Krylov space contradicts them.
+ciq_status solve_batched_learned(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                                 const float* theta, double margin, ciq_info* infos, int* fallback,
+                                 cudaStream_t st, int op) {
+    if (!probs || P < 1 || P > CIQ_MAX_BATCH || !theta || !std::isfinite(margin)) return CIQ_ERR_ARG;
+    if (!device_accessible(theta)) return CIQ_ERR_ARG;
+    ciq_options o;
+    ciq_default_options(&o);
+    if (opt) o = *opt;
+    if (!valid_options(o)) return CIQ_ERR_ARG;
+    for (int p = 0; p < P; ++p)
+        if (!probs[p].X || probs[p].N < 1 || probs[p].d < 1 || probs[p].d > CIQ_MAX_DIM ||
+            !valid_kernel(&probs[p].kern) || !device_accessible(probs[p].X))
+            return CIQ_ERR_ARG;
+    keep_pool_warm();
+    std::vector<float> pred((size_t)P * kMlpOut);
+    {
+        char* base = nullptr;
+        const size_t b0 = round_up((int64_t)(sizeof(ciq_problem) * P), kAlign);
+        const size_t b1 = round_up((int64_t)(sizeof(float) * P * kMlpIn), kAlign);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), b0 + b1 + sizeof(float) * P * kMlpOut, st);
+        if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+        ciq_problem* pd = reinterpret_cast<ciq_problem*>(base);
+        float* F = reinterpret_cast<float*>(base + b0);
+        float* Yp = reinterpret_cast<float*>(base + b0 + b1);
+        e = cudaMemcpyAsync(pd, probs, sizeof(ciq_problem) * P, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_mlp_features(pd, P, F, st);
+        if (e == cudaSuccess) e = launch_mlp_predict(theta, F, P, Yp, 1, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pred.data(), Yp, sizeof(float) * pred.size(), cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(base, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { cudaStreamSynchronize(st); cudaGetLastError(); return from_cuda(e); }
+    }
+    std::vector<ciq_problem> mod(probs, probs + P);
+    std::vector<char> predicted(P, 0);
+    for (int p = 0; p < P; ++p) {
+        if (mod[p].lmin > 0.0 && mod[p].lmax > 0.0) continue;
+        const double noise = mod[p].kern.noise;
+        const double lmax = o.lmax_margin * std::exp((double)pred[(size_t)p * kMlpOut + 1] + margin);
+        const double lmin = noise > 0.0 ? noise : std::exp((double)pred[(size_t)p * kMlpOut]) / o.lmin_div;
+        if (!(lmin > 0.0) || !std::isfinite(lmax)) continue;       // leave this one to the pre-pass
+        mod[p].lmin = lmin;
+        mod[p].lmax = std::max(lmax, lmin);
+        predicted[p] = 1;
+    }
+    std::vector<ciq_info> own;
+    if (!infos) {
+        own.resize(P);
+        infos = own.data();
+    }
+    std::vector<double> packed;
+    ciq_status rc = solve_batched(mod.data(), P, Q, tol, &o, infos, st, op, true, &packed);
+    if (rc != CIQ_OK && rc != CIQ_NOT_CONVERGED && rc != CIQ_ERR_NAN) return rc;
+    std::vector<int> redo;
+    for (int p = 0; p < P; ++p) {
+        const double* sm = packed.data() + (size_t)p * kSummaryStride;
+        const bool nan = sm[6] > 0;
+        const bool above = sm[8 + kNodeCount] > sm[8 + kNodeLmax] * (1.0 + 1e-6);
+        const bool bad = predicted[p] && (nan || above);
+        if (fallback) fallback[p] = bad ? 1 : 0;
+        if (bad) redo.push_back(p);
+    }
+    std::vector<char> nan_p(P), maxit_p(P);
+    for (int p = 0; p < P; ++p) {
+        const double* sm = packed.data() + (size_t)p * kSummaryStride;
+        nan_p[p] = sm[6] > 0;
+        maxit_p[p] = (int)sm[5] == kColMaxIter;
+    }
+    if (!redo.empty()) {
+        std::vector<ciq_problem> sub;
+        for (int p : redo) {
+            ciq_problem q = probs[p];
+            q.lmin = q.lmax = 0.0;
+            sub.push_back(q);
+        }
+        std::vector<ciq_info> sub_infos(redo.size());
+        std::vector<double> packed2;
+        const ciq_status rc2 = solve_batched(sub.data(), (int)sub.size(), Q, tol, &o, sub_infos.data(), st, op, true,
+                                             &packed2);
+        if (rc2 != CIQ_OK && rc2 != CIQ_NOT_CONVERGED && rc2 != CIQ_ERR_NAN) return rc2;
+        for (size_t k = 0; k < redo.size(); ++k) {
+            const int p = redo[k];
+            infos[p] = sub_infos[k];
+            const double* sm = packed2.data() + k * kSummaryStride;
+            nan_p[p] = sm[6] > 0;
+            maxit_p[p] = (int)sm[5] == kColMaxIter;
+        }
+    }
+    for (int p = 0; p < P; ++p)
+        if (nan_p[p]) return CIQ_ERR_NAN;
+    for (int p = 0; p < P; ++p)
+        if (maxit_p[p]) return CIQ_NOT_CONVERGED;
     return CIQ_OK;
 }
 
@@ -1123,6 +1232,85 @@ ciq_status ciq_sqrt_batched(const ciq_problem* probs, int P, int Q, double tol, 
 ciq_status ciq_invsqrt_batched(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
                                ciq_info* infos, ciq_stream_t stream) {
     return solve_batched(probs, P, Q, tol, opt, infos, (cudaStream_t)stream, kOpInvSqrt);
+}
+
+ciq_status ciq_sqrt_batched_learned(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                                    const float* theta, double margin, ciq_info* infos, int* fallback,
+                                    ciq_stream_t stream) {
+    return solve_batched_learned(probs, P, Q, tol, opt, theta, margin, infos, fallback, (cudaStream_t)stream,
+                                 kOpSqrtIdentity);
+}
+
+ciq_status ciq_invsqrt_batched_learned(const ciq_problem* probs, int P, int Q, double tol, const ciq_options* opt,
+                                       const float* theta, double margin, ciq_info* infos, int* fallback,
+                                       ciq_stream_t stream) {
+    return solve_batched_learned(probs, P, Q, tol, opt, theta, margin, infos, fallback, (cudaStream_t)stream,
+                                 kOpInvSqrt);
+}
+
+// ------------------------------------------------------ learned predictor --
+ciq_status ciq_mlp_features(const ciq_problem* probs, int P, float* F, ciq_stream_t stream) {
+    if (!probs || P < 1 || P > CIQ_MAX_BATCH || !F || !device_accessible(F)) return CIQ_ERR_ARG;
+    for (int p = 0; p < P; ++p)
+        if (!probs[p].X || probs[p].N < 1 || probs[p].d < 1 || probs[p].d > CIQ_MAX_DIM ||
+            !valid_kernel(&probs[p].kern) || !device_accessible(probs[p].X))
+            return CIQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ciq_problem* pd = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&pd), sizeof(ciq_problem) * P, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    e = cudaMemcpyAsync(pd, probs, sizeof(ciq_problem) * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_mlp_features(pd, P, F, st);
+    cudaFreeAsync(pd, st);
+    // The host array must stay readable until the copy is done.
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    return CIQ_OK;
+}
+
+ciq_status ciq_mlp_normaliser(const float* F, const float* Y, int n, float* theta, ciq_stream_t stream) {
+    if (!F || !Y || !theta || n < 1 || !device_accessible(F) || !device_accessible(Y) || !device_accessible(theta))
+        return CIQ_ERR_ARG;
+    return from_cuda(launch_mlp_normaliser(F, Y, n, theta, (cudaStream_t)stream));
+}
+
+ciq_status ciq_mlp_init(float* theta, uint64_t seed, ciq_stream_t stream) {
+    if (!theta || !device_accessible(theta)) return CIQ_ERR_ARG;
+    return from_cuda(launch_mlp_init(theta, seed, (cudaStream_t)stream));
+}
+
+ciq_status ciq_mlp_loss_grad(const float* theta, const float* F, const float* Y, int n, double* loss, double* grad,
+                             ciq_stream_t stream) {
+    if (!theta || !F || !Y || !loss || !grad || n < 1 || !device_accessible(theta) || !device_accessible(F) ||
+        !device_accessible(Y) || !device_accessible(grad))
+        return CIQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* dl = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dl), sizeof(double), st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    e = launch_mlp_loss_grad(theta, F, Y, n, dl, grad, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(dl, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    return CIQ_OK;
+}
+
+ciq_status ciq_mlp_train(float* theta, float* adam, const float* F, const float* Y, int n, int steps, int batch,
+                         float lr, uint64_t seed, int first_step, float* losses, ciq_stream_t stream) {
+    if (!theta || !adam || !F || !Y || n < 1 || steps < 0 || batch < 1 || batch > (1 << 20) || first_step < 1 ||
+        !(lr > 0.f) || !device_accessible(theta) || !device_accessible(adam) || !device_accessible(F) ||
+        !device_accessible(Y) || (losses && !device_accessible(losses)))
+        return CIQ_ERR_ARG;
+    if (steps == 0) return CIQ_OK;
+    return from_cuda(launch_mlp_train(theta, adam, F, Y, n, steps, batch, lr, seed, first_step, losses,
+                                      (cudaStream_t)stream));
+}
+
+ciq_status ciq_mlp_predict(const float* theta, const float* F, int n, float* out, int bf16, ciq_stream_t stream) {
+    if (!theta || !F || !out || n < 1 || !device_accessible(theta) || !device_accessible(F) || !device_accessible(out))
+        return CIQ_ERR_ARG;
+    return from_cuda(launch_mlp_predict(theta, F, n, out, bf16 ? 1 : 0, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -62,6 +62,7 @@ struct KrylovState {
     int* all_done;              // 1 once every column is frozen
     const double* nodes;        // NodeSlot block
     double* summary;            // [8] filled by the summary kernel
+    double* tri;                // optional: column 0's T_j, diagonal [jmax + 1] then off-diagonal [jmax + 2]
     int jmax;
     int op;                     // CombineOp
     int stop_rule;              // ciq_stop_rule

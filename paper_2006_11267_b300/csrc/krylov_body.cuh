@@ -204,6 +204,10 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
                 s.beta[pout * T + c] = bu;
                 s.iters[c] = j;
                 s.brk[c] = nan ? kColNaN : (bd ? kColExact : 0);
+                if (s.tri && c == 0) {
+                    s.tri[j - 1] = alpha;
+                    s.tri[s.jmax + 1 + j] = bu;
+                }
             }
         }
     }
