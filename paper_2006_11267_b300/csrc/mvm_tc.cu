@@ -37,7 +37,6 @@ namespace {
 constexpr long long kWaitLimit = 4000000000LL;   // clock cycles, ~2 s at 2 GHz
 constexpr int kUBytes = kTcBM * kTcRowBytes;      // 12 KiB
 constexpr int kXBytes = kTcBN * kTcRowBytes;      // 6 KiB
-constexpr int kPPart = kTcBM * kTcBN * 2;         // 16 KiB per 16-bit part
 
 template <bool HALF>
 __device__ __forceinline__ uint16_t to16(float x) {
@@ -197,56 +196,52 @@ __global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, in
     *reinterpret_cast<uint4*>(base + (int64_t)tpg * 128 + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Separate rings for the point tiles (released when S is computed) and the
-// V tiles (released when the product with P completes), as deep as shared
-// memory allows, so the bulk copies run well ahead of the MMAs.
-constexpr int kTcXStages = 8;
+// The kernel walks K's columns in steps of kTcKN = 128 (two 64-row operand
+// tiles).  Every tcgen05.commit costs about 200 cycles of a serial commit
+// path, so a step carries exactly two: one when its S is complete, one when
+// its product is complete; each completion barrier has several waiters.
+constexpr int kTcKN = 128;
+constexpr int kXStep = 2 * kXBytes;              // points of one step, 12 KiB
+constexpr int kTcXStages = 4;
 template <int TP>
 __host__ __device__ constexpr int tc_vstages() {
-    return TP <= 64 ? 8 : 4;
+    return TP <= 32 ? 6 : 4;
 }
+template <int TP>
+__host__ __device__ constexpr int tc_vstep_bytes() {
+    return 2 * (2 * TP * 128);                   // two 64-row tiles of split V
+}
+constexpr int kRing = 8;                         // completion barriers per kind (>= stages + 2)
 
-// Tiles of K's columns accumulated in TMEM before the partial sum is folded
+// Steps of K's columns accumulated in TMEM before the partial sum is folded
 // into the compensated running sum (keeps the tensor core's FP32 accumulation
-// to 16 x 4 x 3 = 192 steps per partial sum).
-constexpr int kTcChunk = 16;
+// to 8 x 8 x 3 = 192 steps per partial sum).
+constexpr int kTcChunk = 8;
 
-// TMEM: NB S buffers of 64 columns, each overwritten by its P (leading part
-// in the first 32 columns, trailing part in the next 32, two 16-bit values
-// per column); O [64 NB, 64 NB + TP); running sum leading part
-// [64 NB + TP, 64 NB + 2 TP) and trailing part [64 NB + 2 TP, 64 NB + 3 TP).
-// Four S/P buffers when they fit (T <= 64), two otherwise: tile t uses
-// buffer t % NB and exp warpgroup t % 2, so each buffer serves one
-// warpgroup and its barrier phases advance one at a time.
-template <int TP>
-__host__ __device__ constexpr int tc_sbuffers() {
-    return (4 * kTcBN + 3 * TP <= 512) ? 4 : 2;
-}
-
-template <int TP>
-__host__ __device__ constexpr uint32_t tmem_cols() {
-    return (tc_sbuffers<TP>() * kTcBN + 3 * TP <= 256) ? 256u : 512u;
-}
+// TMEM: two S buffers of 128 columns, each overwritten by its P in place,
+// block by block: the 16 values of S in columns [16k, 16k+16) become 8
+// columns of leading parts [16k, 16k+8) and 8 of trailing parts [16k+8,
+// 16k+16) (two 16-bit values per column), the A operand of K-step k of the
+// product; O [256, 256 + TP); running sum leading part [256 + TP, 256 + 2 TP)
+// and trailing part [256 + 2 TP, 256 + 3 TP).  Step t uses buffer t % 2;
+// exp warpgroup g turns columns [64 g, 64 g + 64) of every step into P.
+constexpr uint32_t kTmemCols = 512;
 
 template <int TP>
 __host__ __device__ constexpr int tc_smem_bytes() {
-    return kUBytes + kTcXStages * kXBytes + tc_vstages<TP>() * (2 * TP * 128) + 512;
+    return kUBytes + kTcXStages * kXStep + tc_vstages<TP>() * tc_vstep_bytes<TP>() + 512;
 }
 
 // Barrier slots in shared memory.
 enum TcBar {
     kBarU = 0,             // U tile landed
-    kBarXFull = 1,         // [8] point tile landed
-    kBarXFree = 9,         // [8] point tile consumed by S
-    kBarVFull = 17,        // [8] V tile landed
-    kBarVFree = 25,        // [8] V tile consumed by the product
-    kBarSFull = 33,        // [4] S buffer written by the MMA
-    kBarSFree = 37,        // [4] S/P buffer released by the product that read P
-    kBarPFull = 41,        // [4] P written over S by its exp warpgroup
-    kBarOChunk = 45,       // a chunk of O is complete (to be folded)
-    kBarOFree = 46,        // O folded into the running sum, accumulator free
-    kBarOFull = 47,        // last chunk of O complete
-    kBarCount = 48
+    kBarXFull = 1,         // [4] points of a step landed
+    kBarVFull = 5,         // [6] V of a step landed
+    kBarSDone = 11,        // [8] S of step t complete (ring t % 8): exp may start, point stage free
+    kBarODone = 19,        // [8] product of step t complete: S buffer and V stage free, O readable
+    kBarPFull = 27,        // [2] P written over S in buffer b by both exp warpgroups
+    kBarOFree = 29,        // O folded into the running sum, accumulator free
+    kBarCount = 30
 };
 
 // Kernel value / outputscale from S = -c^2 r^2 / 2 (RBF: S <= 0 up to
@@ -258,237 +253,202 @@ __device__ __forceinline__ float p_of_s(float S) {
     return fmaf(a, fmaf(a, 1.0f / 3.0f, 1.0f), 1.0f) * ex2_approx(a * (float)(-kLog2e));
 }
 
+// 16 values of S (one TMEM block of a row) -> P split into 8 packed leading
+// and 8 packed trailing 16-bit pairs.
+template <int KT, bool HALF>
+__device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi)[8], uint32_t (&lo)[8]) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float pa = p_of_s<KT>(__uint_as_float(s[2 * e]));
+        const float pb = p_of_s<KT>(__uint_as_float(s[2 * e + 1]));
+        split_pair<HALF>(pa, pb, hi[e], lo[e]);
+    }
+}
+
 // --------------------------------------------------------------- kernel --
 // Warp roles (384 threads): warp 0 lane 0 issues the bulk copies, warp 1
-// lane 0 issues the MMAs, warps 4-7 and 8-11 are two exp warpgroups taking
-// even and odd tiles (S and P double-buffered).  Warps 8-11 also fold each
+// lane 0 issues the MMAs, warps 4-7 and 8-11 are two exp warpgroups that
+// split every step's 128 columns between them.  Warps 8-11 also fold each
 // completed chunk of O into the running sum; warps 4-7 run the epilogue.
-// Tensor pipe order: S(t) = U X_t^T, then O += P(t-1) V(t-1), so the exp of
-// one tile overlaps the products of its neighbours.  Columns [c0, c0 + TP)
-// of V (those below a.T) are handled.
+// Tensor pipe order: S(t+1) = U X_{t+1}^T, then O += P(t) V(t): S runs one
+// step ahead, so the exp of step t+1 overlaps the product of step t.
+// Columns [c0, c0 + TP) of V (those below a.T) are handled.
 template <int KT, int TP, bool HALF>
 __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
     if (a.stop && *a.stop) return;
     constexpr int NX = kTcXStages;
     constexpr int NV = tc_vstages<TP>();
-    constexpr int NB = tc_sbuffers<TP>();
-    constexpr int VBYTES = 2 * TP * 128;
+    constexpr int VSTEP = tc_vstep_bytes<TP>();
+    constexpr int VHALF = VSTEP / 2;                     // one 64-row tile of split V
+    static_assert(NX + 2 <= kRing && NV + 2 <= kRing, "completion rings too short");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sU = smem;
     uint8_t* sX0 = sU + kUBytes;
-    uint8_t* sV0 = sX0 + NX * kXBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sV0 + NV * VBYTES);
+    uint8_t* sV0 = sX0 + NX * kXStep;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sV0 + NV * VSTEP);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kBarCount);
     volatile int* serr = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t tile = blockIdx.x;
     const int64_t i0 = tile * kTcBM;
-    const int nt = (int)(a.Npad / kTcBN);
+    const int nt = (int)(a.Npad / kTcKN);
     const int nfold = (nt - 1) / kTcChunk;               // chunks folded before the last one
-    constexpr uint32_t NCOLS = tmem_cols<TP>();
-    constexpr uint32_t IDESC_S = tc::idesc_f16(kTcBM, kTcBN, !HALF);
+    constexpr uint32_t IDESC_S = tc::idesc_f16(kTcBM, kTcKN, !HALF);
     constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
 
     if (tid == 0) {
         tc::mbar_init(&bars[kBarU], 1);
-        for (int s = 0; s < NX; ++s) {
-            tc::mbar_init(&bars[kBarXFull + s], 1);
-            tc::mbar_init(&bars[kBarXFree + s], 1);
+        for (int s = 0; s < NX; ++s) tc::mbar_init(&bars[kBarXFull + s], 1);
+        for (int s = 0; s < NV; ++s) tc::mbar_init(&bars[kBarVFull + s], 1);
+        for (int r = 0; r < kRing; ++r) {
+            tc::mbar_init(&bars[kBarSDone + r], 1);
+            tc::mbar_init(&bars[kBarODone + r], 1);
         }
-        for (int s = 0; s < NV; ++s) {
-            tc::mbar_init(&bars[kBarVFull + s], 1);
-            tc::mbar_init(&bars[kBarVFree + s], 1);
-        }
-        for (int b = 0; b < NB; ++b) {
-            tc::mbar_init(&bars[kBarSFull + b], 1);
-            tc::mbar_init(&bars[kBarSFree + b], 1);
-            tc::mbar_init(&bars[kBarPFull + b], 128);
-        }
-        tc::mbar_init(&bars[kBarOChunk], 1);
+        for (int b = 0; b < 2; ++b) tc::mbar_init(&bars[kBarPFull + b], 256);
         tc::mbar_init(&bars[kBarOFree], 128);
-        tc::mbar_init(&bars[kBarOFull], 1);
         tc::fence_mbarrier_init();
         *serr = 0;
     }
     if (warp == 0) {
-        tc::tmem_alloc(tslot, NCOLS);
+        tc::tmem_alloc(tslot, kTmemCols);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t tO = tmem + NB * kTcBN;
+    const uint32_t tO = tmem + 2 * kTcKN;
     const uint32_t tRh = tO + TP;
     const uint32_t tRl = tO + 2 * TP;
     const uint8_t* vblk = p.vblk;
 
     if (warp == 0) {
         // ---------------------------------------------------------- loader
-        // Two independent rings, polled without blocking: point tile tx
-        // waits for S(tx - NX) to free its stage, V tile tv for the product
-        // of tile tv - NV.  The whole warp runs the loop (uniform control
-        // flow, addresses in uniform registers); one elected lane issues.
-        {
-            const bool leader = tc::elect_one();
-            if (leader) {
-                tc::mbar_expect_tx(&bars[kBarU], kUBytes);
-                tc::bulk_g2s(sU, p.ua + tile * kUBytes, kUBytes, &bars[kBarU]);
-            }
-            __syncwarp();
-            int tx = 0, tv = 0;
-            long long last = clock64();
-            while (tx < nt || tv < nt) {
-                if (__shfl_sync(0xffffffffu, (int)*serr, 0)) break;
-                bool progressed = false;
-                if (tx < nt) {
-                    const int st = tx % NX;
-                    const bool ok = tx < NX || tc::mbar_test(&bars[kBarXFree + st], (uint32_t)((tx / NX - 1) & 1));
-                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
-                        if (tc::elect_one()) {
-                            tc::mbar_expect_tx(&bars[kBarXFull + st], kXBytes);
-                            tc::bulk_g2s(sX0 + st * kXBytes, p.ub + (int64_t)tx * kXBytes, kXBytes,
-                                         &bars[kBarXFull + st]);
-                        }
-                        __syncwarp();
-                        ++tx;
-                        progressed = true;
-                    }
-                }
-                if (tv < nt) {
-                    const int st = tv % NV;
-                    const bool ok = tv < NV || tc::mbar_test(&bars[kBarVFree + st], (uint32_t)((tv / NV - 1) & 1));
-                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
-                        if (tc::elect_one()) {
-                            tc::mbar_expect_tx(&bars[kBarVFull + st], VBYTES);
-                            tc::bulk_g2s(sV0 + st * VBYTES, vblk + (int64_t)tv * VBYTES, VBYTES, &bars[kBarVFull + st]);
-                        }
-                        __syncwarp();
-                        ++tv;
-                        progressed = true;
-                    }
-                }
-                if (progressed) last = clock64();
-                else if (__shfl_sync(0xffffffffu, (int)(clock64() - last > kWaitLimit), 0)) {
-                    if (lane == 0) *serr = 1;
+        // One thread, fixed order: the points of step t, then its V.  The
+        // point stage of step t was read by S(t - NX), the V stage by the
+        // product of step t - NV; each wait is bounded.
+        if (lane == 0) {
+            tc::mbar_expect_tx(&bars[kBarU], kUBytes);
+            tc::bulk_g2s(sU, p.ua + tile * kUBytes, kUBytes, &bars[kBarU]);
+            for (int t = 0; t < nt; ++t) {
+                const int sx = t % NX, sv = t % NV;
+                if (t >= NX && !tc::mbar_wait(&bars[kBarSDone + (t - NX) % kRing], (uint32_t)(((t - NX) / kRing) & 1),
+                                              kWaitLimit)) {
+                    *serr = 1;
                     break;
                 }
+                tc::mbar_expect_tx(&bars[kBarXFull + sx], kXStep);
+                tc::bulk_g2s(sX0 + sx * kXStep, p.ub + (int64_t)t * kXStep, kXStep, &bars[kBarXFull + sx]);
+                if (t >= NV && !tc::mbar_wait(&bars[kBarODone + (t - NV) % kRing], (uint32_t)(((t - NV) / kRing) & 1),
+                                              kWaitLimit)) {
+                    *serr = 1;
+                    break;
+                }
+                tc::mbar_expect_tx(&bars[kBarVFull + sv], VSTEP);
+                tc::bulk_g2s(sV0 + sv * VSTEP, vblk + (int64_t)t * VSTEP, VSTEP, &bars[kBarVFull + sv]);
+                if (*serr) break;
             }
         }
+        __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
-        // Event-driven: S(g1) = U X^T is issued as soon as its S buffer and
-        // point tile are ready, O += P(g2) V(g2) as soon as P(g2) and its V
-        // tile are ready; S is preferred so the in-order tensor pipe never
-        // waits behind a product whose P is late.  Each barrier's next phase
-        // can only complete after this warp issues the matching MMA, so parity
-        // tests are unambiguous; test_wait never suspends the warp.  The whole
-        // warp runs the loop with uniform control flow, so the descriptors
-        // stay in uniform registers; one elected lane issues each MMA.
-        {
-            const uint32_t aU = tc::smem_u32(sU);
+        // One thread, fixed order: S(0); then for each step t, S(t+1) into
+        // the buffer of step t - 1 (once that product is complete), and
+        // O += P(t) V(t) once both exp warpgroups have written P(t) and V(t)
+        // is in (and, at the start of a chunk, the accumulator is folded).
+        // Descriptors are formed once; per MMA only the start address moves.
+        if (lane == 0) {
+            const uint64_t dU = tc::smem_desc(tc::smem_u32(sU), 128, 768);
+            const uint64_t dX = tc::smem_desc(tc::smem_u32(sX0), 128, 768);
+            const uint64_t dV = tc::smem_desc(tc::smem_u32(sV0), 128, 1024);
             bool good = tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
-            good = __shfl_sync(0xffffffffu, (int)good, 0) != 0;
-            int g1 = 0, g2 = 0;
-            long long last = clock64();
-            while (good && g2 < nt) {
-                if (__shfl_sync(0xffffffffu, (int)*serr, 0)) { good = false; break; }
-                bool progressed = false;
-                if (g1 < nt) {
-                    const int st = g1 % NX, b = g1 % NB;
-                    const bool ok = tc::mbar_test(&bars[kBarXFull + st], (uint32_t)((g1 / NX) & 1)) &&
-                                    (g1 < NB || tc::mbar_test(&bars[kBarSFree + b], (uint32_t)((g1 / NB - 1) & 1)));
-                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
-                        tc::fence_after_sync();
-                        const uint32_t aX = tc::smem_u32(sX0 + st * kXBytes);
-                        const uint32_t tS = tmem + b * kTcBN;
-                        if (tc::elect_one()) {
+            auto issue_s = [&](int h) -> bool {
+                const int sx = h % NX;
+                if (h >= 2 && !tc::mbar_wait(&bars[kBarODone + (h - 2) % kRing], (uint32_t)(((h - 2) / kRing) & 1),
+                                             kWaitLimit))
+                    return false;
+                if (!tc::mbar_wait(&bars[kBarXFull + sx], (uint32_t)((h / NX) & 1), kWaitLimit)) return false;
+                tc::fence_after_sync();
+                const uint64_t dx = dX + (uint64_t)((sx * kXStep) >> 4);
+                const uint32_t tS = tmem + (h & 1) * kTcKN;
 #pragma unroll
-                            for (int ch = 0; ch < 3; ++ch)
-                                tc::mma_f16(tS, tc::smem_desc(aU + ch * 256, 128, 768),
-                                            tc::smem_desc(aX + ch * 256, 128, 768), IDESC_S, ch > 0 ? 1u : 0u);
-                            tc::mma_commit(&bars[kBarSFull + b]);
-                            tc::mma_commit(&bars[kBarXFree + st]);
-                        }
-                        __syncwarp();
-                        ++g1;
-                        progressed = true;
-                    }
+                for (int ch = 0; ch < 3; ++ch)
+                    tc::mma_f16(tS, dU + (uint64_t)((ch * 256) >> 4), dx + (uint64_t)((ch * 256) >> 4), IDESC_S,
+                                ch > 0 ? 1u : 0u);
+                tc::mma_commit(&bars[kBarSDone + h % kRing]);
+                return true;
+            };
+            if (good) good = issue_s(0);
+            for (int t = 0; good && t < nt; ++t) {
+                if (t + 1 < nt && !issue_s(t + 1)) { good = false; break; }
+                const int b = t & 1, sv = t % NV;
+                const bool fresh = (t % kTcChunk) == 0;
+                good = tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t >> 1) & 1), kWaitLimit) &&
+                       tc::mbar_wait(&bars[kBarVFull + sv], (uint32_t)((t / NV) & 1), kWaitLimit) &&
+                       (!fresh || t == 0 ||
+                        tc::mbar_wait(&bars[kBarOFree], (uint32_t)((t / kTcChunk - 1) & 1), kWaitLimit));
+                if (!good) break;
+                tc::fence_after_sync();
+                const uint32_t tP = tmem + b * kTcKN;
+                const uint64_t dv = dV + (uint64_t)((sv * VSTEP) >> 4);
+#pragma unroll
+                for (int gg = 0; gg < 3; ++gg) {
+                    const uint32_t pa = tP + (gg == 2 ? 8 : 0);
+                    const uint64_t vb = dv + (uint64_t)(((gg == 1 ? TP * 128 : 0)) >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk)
+                        tc::mma_f16_ts(tO, pa + kk * 16, vb + (uint64_t)(((kk >> 2) * VHALF + (kk & 3) * 256) >> 4),
+                                       IDESC_O, (!fresh || gg > 0 || kk > 0) ? 1u : 0u);
                 }
-                if (!progressed && g2 < g1) {
-                    const int bu = g2 % NB, su = g2 % NV;
-                    const bool fresh = (g2 % kTcChunk) == 0;
-                    const bool ok = tc::mbar_test(&bars[kBarPFull + bu], (uint32_t)((g2 / NB) & 1)) &&
-                                    tc::mbar_test(&bars[kBarVFull + su], (uint32_t)((g2 / NV) & 1)) &&
-                                    (!fresh || g2 == 0 ||
-                                     tc::mbar_test(&bars[kBarOFree], (uint32_t)((g2 / kTcChunk - 1) & 1)));
-                    if (__shfl_sync(0xffffffffu, (int)ok, 0)) {
-                        tc::fence_after_sync();
-                        const uint32_t tP = tmem + bu * kTcBN;     // P over S: hi cols [0,32), lo [32,64)
-                        const uint32_t aV = tc::smem_u32(sV0 + su * VBYTES);
-                        if (tc::elect_one()) {
-#pragma unroll
-                            for (int g = 0; g < 3; ++g) {
-                                const uint32_t pa = tP + (g == 2 ? 32 : 0);
-                                const uint32_t vb = aV + (g == 1 ? TP * 128 : 0);
-#pragma unroll
-                                for (int kk = 0; kk < 4; ++kk)
-                                    tc::mma_f16_ts(tO, pa + kk * 8, tc::smem_desc(vb + kk * 256, 128, 1024), IDESC_O,
-                                                   (!fresh || g > 0 || kk > 0) ? 1u : 0u);
-                            }
-                            tc::mma_commit(&bars[kBarSFree + bu]);
-                            tc::mma_commit(&bars[kBarVFree + su]);
-                            if ((g2 % kTcChunk) == kTcChunk - 1 && g2 != nt - 1) tc::mma_commit(&bars[kBarOChunk]);
-                        }
-                        __syncwarp();
-                        ++g2;
-                        progressed = true;
-                    }
-                }
-                if (progressed) last = clock64();
-                else if (__shfl_sync(0xffffffffu, (int)(clock64() - last > kWaitLimit), 0)) good = false;
+                tc::mma_commit(&bars[kBarODone + t % kRing]);
+                if (*serr) good = false;
             }
-            if (good && tc::elect_one()) tc::mma_commit(&bars[kBarOFull]);
-            __syncwarp();
-            if (!good && lane == 0) *serr = 1;
+            if (!good) *serr = 1;
         }
+        __syncwarp();
     } else if (warp >= 4) {
         // --------------------------------------------------- exp warpgroups
-        const int g = (warp - 4) >> 2;                    // 0: even tiles, 1: odd tiles
-        const int r = 32 * (warp & 3) + lane;             // row in the tile = TMEM lane
+        const int g = (warp - 4) >> 2;                    // columns [64 g, 64 g + 64) of every step
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        for (int t = g; t < nt; t += 2) {
-            const int b = t % NB;
-            const uint32_t tS = tmem + b * kTcBN + lane_base;
-            const bool good = tc::mbar_wait(&bars[kBarSFull + b], (uint32_t)((t / NB) & 1), kWaitLimit);
+        for (int t = 0; t < nt; ++t) {
+            const int b = t & 1;
+            const uint32_t tS = tmem + b * kTcKN + g * 64 + lane_base;
+            const bool good = tc::mbar_wait(&bars[kBarSDone + t % kRing], (uint32_t)((t / kRing) & 1), kWaitLimit);
             if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
             tc::fence_after_sync();
-            uint32_t s0[32], s1[32];
-            tc::tmem_ld32(tS, s0);
-            tc::tmem_ld32(tS + 32, s1);
-            uint32_t hq[32], lq[32];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float pa = p_of_s<KT>(__uint_as_float(s0[2 * e]));
-                const float pb = p_of_s<KT>(__uint_as_float(s0[2 * e + 1]));
-                split_pair<HALF>(pa, pb, hq[e], lq[e]);
-            }
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float pa = p_of_s<KT>(__uint_as_float(s1[2 * e]));
-                const float pb = p_of_s<KT>(__uint_as_float(s1[2 * e + 1]));
-                split_pair<HALF>(pa, pb, hq[16 + e], lq[16 + e]);
-            }
-            // P over S in tensor memory: 64 values per row -> 32 columns per part.
-            tc::tmem_st32(tS, hq);
-            tc::tmem_st32(tS + 32, lq);
+            // S in four 16-column blocks; the load of block k+1 is in flight
+            // while block k is turned into P, written back over the columns
+            // block k was read from.
+            uint32_t A[16], B[16];
+            uint32_t h0[8], l0[8], h1[8], l1[8], h2[8], l2[8], h3[8], l3[8];
+            tc::tmem_ld16(tS, A);
+            tc::tmem_wait_ld16(A);
+            tc::tmem_ld16(tS + 16, B);
+            exp_block<KT, HALF>(A, h0, l0);
+            tc::tmem_st8(tS, h0);
+            tc::tmem_st8(tS + 8, l0);
+            tc::tmem_wait_ld16(B);
+            tc::tmem_ld16(tS + 32, A);
+            exp_block<KT, HALF>(B, h1, l1);
+            tc::tmem_st8(tS + 16, h1);
+            tc::tmem_st8(tS + 24, l1);
+            tc::tmem_wait_ld16(A);
+            tc::tmem_ld16(tS + 48, B);
+            exp_block<KT, HALF>(A, h2, l2);
+            tc::tmem_st8(tS + 32, h2);
+            tc::tmem_st8(tS + 40, l2);
+            tc::tmem_wait_ld16(B);
+            exp_block<KT, HALF>(B, h3, l3);
+            tc::tmem_st8(tS + 48, h3);
+            tc::tmem_st8(tS + 56, l3);
+            tc::tmem_wait_st64(h0, l0, h1, l1, h2, l2, h3, l3);
             tc::fence_before_sync();
             tc::mbar_arrive(&bars[kBarPFull + b]);
-            // Fold a completed chunk of O into the running sum (odd warpgroup).
+            // Fold a completed chunk of O into the running sum (warpgroup 1).
             if (g == 1 && (t % kTcChunk) == kTcChunk - 1 && t != nt - 1) {
                 const int c = t / kTcChunk;
-                const bool okc = tc::mbar_wait(&bars[kBarOChunk], (uint32_t)(c & 1), kWaitLimit);
+                const bool okc = tc::mbar_wait(&bars[kBarODone + t % kRing], (uint32_t)((t / kRing) & 1), kWaitLimit);
                 if (__shfl_sync(0xffffffffu, (int)(!okc || *serr), 0)) { *serr = 1; break; }
                 tc::fence_after_sync();
 #pragma unroll 1
@@ -521,7 +481,8 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     if (warp >= 4 && warp < 8) {
         const int r = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        const bool good = !*serr && tc::mbar_wait(&bars[kBarOFull], 0, kWaitLimit);
+        const bool good = !*serr && tc::mbar_wait(&bars[kBarODone + (nt - 1) % kRing],
+                                                  (uint32_t)(((nt - 1) / kRing) & 1), kWaitLimit);
         const bool ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
         if (!ok) *serr = 1;
         tc::fence_after_sync();
@@ -574,7 +535,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
         }
     }
     if (tid == 0 && *serr) atomicExch(p.err, 1);
-    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 template <int KT, int TP, bool HALF>
@@ -595,7 +556,6 @@ cudaError_t launch_kt_half(const TcPoints& p, const MvmArgs<float>& a, int tpg, 
     switch (tpg) {
         case 32: return launch_tp<KT, 32, HALF>(p, a, c0, st);
         case 64: return launch_tp<KT, 64, HALF>(p, a, c0, st);
-        case 128: return launch_tp<KT, 128, HALF>(p, a, c0, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -606,12 +566,12 @@ bool tc_supported(int precision, int d) {
     return (precision == CIQ_PREC_BF16 || precision == CIQ_PREC_FP16) && d >= 1 && d <= 14;
 }
 
-// Columns of V per MVM launch group (T > 128 runs as groups of 128; the
-// TMEM loads and stores move 32 columns, so a group is at least 32 wide).
+// Columns of V per MVM launch group (T > 64 runs as groups of 64, which
+// with the two 128-column S buffers fill TMEM; the TMEM loads and stores
+// move 32 columns, so a group is at least 32 wide).
 int tc_group_t(int T) {
     if (T <= 32) return 32;
-    if (T <= 64) return 64;
-    return 128;
+    return 64;
 }
 
 int tc_padded_t(int T) {
