@@ -202,10 +202,10 @@ __global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, in
 // its product is complete; each completion barrier has several waiters.
 constexpr int kTcKN = 128;
 constexpr int kXStep = 2 * kXBytes;              // points of one step, 12 KiB
-constexpr int kTcXStages = 4;
+constexpr int kTcXStages = 3;
 template <int TP>
 __host__ __device__ constexpr int tc_vstages() {
-    return TP <= 32 ? 6 : 4;
+    return TP <= 32 ? 4 : 3;
 }
 template <int TP>
 __host__ __device__ constexpr int tc_vstep_bytes() {
@@ -218,18 +218,21 @@ constexpr int kRing = 8;                         // completion barriers per kind
 // to 8 x 8 x 3 = 192 steps per partial sum).
 constexpr int kTcChunk = 8;
 
-// TMEM: two S buffers of 128 columns, each overwritten by its P in place,
+// TMEM: three S buffers of 128 columns, each overwritten by its P in place,
 // block by block: the 16 values of S in columns [16k, 16k+16) become 8
 // columns of leading parts [16k, 16k+8) and 8 of trailing parts [16k+8,
 // 16k+16) (two 16-bit values per column), the A operand of K-step k of the
-// product; O [256, 256 + TP); running sum leading part [256 + TP, 256 + 2 TP)
-// and trailing part [256 + 2 TP, 256 + 3 TP).  Step t uses buffer t % 2;
-// exp warpgroup g turns columns [64 g, 64 g + 64) of every step into P.
+// product; O [384, 384 + TP).  Step t uses buffer t % 3, so S(t+2) can be
+// computed while the products of steps t-1 and t are still queued; exp
+// warpgroup g turns columns [64 g, 64 g + 64) of every step into P.  The
+// compensated running sum (leading and trailing FP32 parts) lives in shared
+// memory, [part][column][row], one row per fold thread.
+constexpr int kNB = 3;
 constexpr uint32_t kTmemCols = 512;
 
 template <int TP>
 __host__ __device__ constexpr int tc_smem_bytes() {
-    return kUBytes + kTcXStages * kXStep + tc_vstages<TP>() * tc_vstep_bytes<TP>() + 512;
+    return kUBytes + kTcXStages * kXStep + tc_vstages<TP>() * tc_vstep_bytes<TP>() + 2 * TP * kTcBM * 4 + 512;
 }
 
 // Barrier slots in shared memory.
@@ -239,9 +242,9 @@ enum TcBar {
     kBarVFull = 5,         // [6] V of a step landed
     kBarSDone = 11,        // [8] S of step t complete (ring t % 8): exp may start, point stage free
     kBarODone = 19,        // [8] product of step t complete: S buffer and V stage free, O readable
-    kBarPFull = 27,        // [2] P written over S in buffer b by both exp warpgroups
-    kBarOFree = 29,        // O folded into the running sum, accumulator free
-    kBarCount = 30
+    kBarPFull = 27,        // [3] P written over S in buffer b by both exp warpgroups
+    kBarOFree = 30,        // O folded into the running sum, accumulator free
+    kBarCount = 31
 };
 
 // Kernel value / outputscale from S = -c^2 r^2 / 2 (RBF: S <= 0 up to
@@ -285,7 +288,8 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     uint8_t* sU = smem;
     uint8_t* sX0 = sU + kUBytes;
     uint8_t* sV0 = sX0 + NX * kXStep;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sV0 + NV * VSTEP);
+    float* sR = reinterpret_cast<float*>(sV0 + NV * VSTEP);   // running sum [2][TP][128]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sR + 2 * TP * kTcBM);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kBarCount);
     volatile int* serr = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
             tc::mbar_init(&bars[kBarSDone + r], 1);
             tc::mbar_init(&bars[kBarODone + r], 1);
         }
-        for (int b = 0; b < 2; ++b) tc::mbar_init(&bars[kBarPFull + b], 256);
+        for (int b = 0; b < kNB; ++b) tc::mbar_init(&bars[kBarPFull + b], 256);
         tc::mbar_init(&bars[kBarOFree], 128);
         tc::fence_mbarrier_init();
         *serr = 0;
@@ -318,45 +322,52 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t tO = tmem + 2 * kTcKN;
-    const uint32_t tRh = tO + TP;
-    const uint32_t tRl = tO + 2 * TP;
+    const uint32_t tO = tmem + kNB * kTcKN;
     const uint8_t* vblk = p.vblk;
 
     if (warp == 0) {
         // ---------------------------------------------------------- loader
-        // One thread, fixed order: the points of step t, then its V.  The
-        // point stage of step t was read by S(t - NX), the V stage by the
-        // product of step t - NV; each wait is bounded.
+        // One thread, fixed order: the points of step t + 2 (S runs two
+        // steps ahead of the product), then the V of step t.  The point
+        // stage of step u was read by S(u - NX), the V stage by the product
+        // of step t - NV; each wait is bounded.
         if (lane == 0) {
             tc::mbar_expect_tx(&bars[kBarU], kUBytes);
             tc::bulk_g2s(sU, p.ua + tile * kUBytes, kUBytes, &bars[kBarU]);
-            for (int t = 0; t < nt; ++t) {
-                const int sx = t % NX, sv = t % NV;
-                if (t >= NX && !tc::mbar_wait(&bars[kBarSDone + (t - NX) % kRing], (uint32_t)(((t - NX) / kRing) & 1),
-                                              kWaitLimit)) {
-                    *serr = 1;
-                    break;
-                }
+            auto load_x = [&](int u) -> bool {
+                const int sx = u % NX;
+                if (u >= NX && !tc::mbar_wait(&bars[kBarSDone + (u - NX) % kRing], (uint32_t)(((u - NX) / kRing) & 1),
+                                              kWaitLimit))
+                    return false;
                 tc::mbar_expect_tx(&bars[kBarXFull + sx], kXStep);
-                tc::bulk_g2s(sX0 + sx * kXStep, p.ub + (int64_t)t * kXStep, kXStep, &bars[kBarXFull + sx]);
+                tc::bulk_g2s(sX0 + sx * kXStep, p.ub + (int64_t)u * kXStep, kXStep, &bars[kBarXFull + sx]);
+                return true;
+            };
+            bool ok = load_x(0) && (nt < 2 || load_x(1));
+            for (int t = 0; ok && t < nt; ++t) {
+                if (t + 2 < nt && !load_x(t + 2)) { ok = false; break; }
+                const int sv = t % NV;
                 if (t >= NV && !tc::mbar_wait(&bars[kBarODone + (t - NV) % kRing], (uint32_t)(((t - NV) / kRing) & 1),
                                               kWaitLimit)) {
-                    *serr = 1;
+                    ok = false;
                     break;
                 }
                 tc::mbar_expect_tx(&bars[kBarVFull + sv], VSTEP);
                 tc::bulk_g2s(sV0 + sv * VSTEP, vblk + (int64_t)t * VSTEP, VSTEP, &bars[kBarVFull + sv]);
                 if (*serr) break;
             }
+            if (!ok) *serr = 1;
         }
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
-        // One thread, fixed order: S(0); then for each step t, S(t+1) into
-        // the buffer of step t - 1 (once that product is complete), and
+        // One thread, fixed order: S(0), S(1); then for each step t,
         // O += P(t) V(t) once both exp warpgroups have written P(t) and V(t)
-        // is in (and, at the start of a chunk, the accumulator is folded).
+        // is in (and, at the start of a chunk, the accumulator is folded),
+        // then S(t+2) into the buffer of step t - 1.  MMA issue blocks while
+        // the tensor pipe's queue is full, so by the time O(t) is issued the
+        // product of step t - 1 has completed and S(t+2) follows O(t) in the
+        // pipe without a gap.
         // Descriptors are formed once; per MMA only the start address moves.
         if (lane == 0) {
             const uint64_t dU = tc::smem_desc(tc::smem_u32(sU), 128, 768);
@@ -365,13 +376,13 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
             bool good = tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
             auto issue_s = [&](int h) -> bool {
                 const int sx = h % NX;
-                if (h >= 2 && !tc::mbar_wait(&bars[kBarODone + (h - 2) % kRing], (uint32_t)(((h - 2) / kRing) & 1),
-                                             kWaitLimit))
+                if (h >= kNB && !tc::mbar_wait(&bars[kBarODone + (h - kNB) % kRing],
+                                               (uint32_t)(((h - kNB) / kRing) & 1), kWaitLimit))
                     return false;
                 if (!tc::mbar_wait(&bars[kBarXFull + sx], (uint32_t)((h / NX) & 1), kWaitLimit)) return false;
                 tc::fence_after_sync();
                 const uint64_t dx = dX + (uint64_t)((sx * kXStep) >> 4);
-                const uint32_t tS = tmem + (h & 1) * kTcKN;
+                const uint32_t tS = tmem + (h % kNB) * kTcKN;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch)
                     tc::mma_f16(tS, dU + (uint64_t)((ch * 256) >> 4), dx + (uint64_t)((ch * 256) >> 4), IDESC_S,
@@ -380,11 +391,11 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                 return true;
             };
             if (good) good = issue_s(0);
+            if (good && nt > 1) good = issue_s(1);
             for (int t = 0; good && t < nt; ++t) {
-                if (t + 1 < nt && !issue_s(t + 1)) { good = false; break; }
-                const int b = t & 1, sv = t % NV;
+                const int b = t % kNB, sv = t % NV;
                 const bool fresh = (t % kTcChunk) == 0;
-                good = tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t >> 1) & 1), kWaitLimit) &&
+                good = tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t / kNB) & 1), kWaitLimit) &&
                        tc::mbar_wait(&bars[kBarVFull + sv], (uint32_t)((t / NV) & 1), kWaitLimit) &&
                        (!fresh || t == 0 ||
                         tc::mbar_wait(&bars[kBarOFree], (uint32_t)((t / kTcChunk - 1) & 1), kWaitLimit));
@@ -402,6 +413,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                                        IDESC_O, (!fresh || gg > 0 || kk > 0) ? 1u : 0u);
                 }
                 tc::mma_commit(&bars[kBarODone + t % kRing]);
+                if (t + 2 < nt && !issue_s(t + 2)) good = false;
                 if (*serr) good = false;
             }
             if (!good) *serr = 1;
@@ -411,8 +423,9 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
         // --------------------------------------------------- exp warpgroups
         const int g = (warp - 4) >> 2;                    // columns [64 g, 64 g + 64) of every step
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int r = 32 * (warp & 3) + lane;             // row of the tile = TMEM lane
         for (int t = 0; t < nt; ++t) {
-            const int b = t & 1;
+            const int b = t % kNB;
             const uint32_t tS = tmem + b * kTcKN + g * 64 + lane_base;
             const bool good = tc::mbar_wait(&bars[kBarSDone + t % kRing], (uint32_t)((t / kRing) & 1), kWaitLimit);
             if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
@@ -453,27 +466,25 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                 tc::fence_after_sync();
 #pragma unroll 1
                 for (int cc = 0; cc < TP / 32; ++cc) {
-                    uint32_t o[32], rh[32], rl[32];
+                    uint32_t o[32];
                     tc::tmem_ld32(tO + lane_base + 32 * cc, o);
-                    if (c > 0) {
-                        tc::tmem_ld32(tRh + lane_base + 32 * cc, rh);
-                        tc::tmem_ld32(tRl + lane_base + 32 * cc, rl);
-                    }
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
-                        float h = c > 0 ? __uint_as_float(rh[e]) : 0.f;
-                        float l = c > 0 ? __uint_as_float(rl[e]) : 0.f;
+                        float* rh = sR + (32 * cc + e) * kTcBM + r;
+                        float* rl = rh + TP * kTcBM;
+                        float h = c > 0 ? *rh : 0.f;
+                        float l = c > 0 ? *rl : 0.f;
                         two_sum_into(h, l, __uint_as_float(o[e]));
-                        rh[e] = __float_as_uint(h);
-                        rl[e] = __float_as_uint(l);
+                        *rh = h;
+                        *rl = l;
                     }
-                    tc::tmem_st32(tRh + lane_base + 32 * cc, rh);
-                    tc::tmem_st32(tRl + lane_base + 32 * cc, rl);
                 }
                 tc::fence_before_sync();
                 tc::mbar_arrive(&bars[kBarOFree]);
             }
         }
+        // The running sum written by warpgroup 1 is read by warpgroup 0's epilogue.
+        asm volatile("bar.sync 1, 256;" ::: "memory");
     }
 
     // ------------------------------------------------------------ epilogue
@@ -491,14 +502,8 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
         const int wl = warp & 3;
 #pragma unroll 1
         for (int cc = 0; cc < TP / 32; ++cc) {
-            uint32_t o[32], rh[32], rl[32];
-            if (ok) {
-                tc::tmem_ld32(tO + lane_base + 32 * cc, o);
-                if (nfold > 0) {
-                    tc::tmem_ld32(tRh + lane_base + 32 * cc, rh);
-                    tc::tmem_ld32(tRl + lane_base + 32 * cc, rl);
-                }
-            }
+            uint32_t o[32];
+            if (ok) tc::tmem_ld32(tO + lane_base + 32 * cc, o);
 #pragma unroll 1
             for (int e = 0; e < 32; ++e) {
                 const int cl = 32 * cc + e;
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                 double qp = 0.0, pp = 0.0, qq = 0.0;
                 if (ok) {
                     double sum = (double)__uint_as_float(o[e]);
-                    if (nfold > 0) sum += (double)__uint_as_float(rh[e]) + (double)__uint_as_float(rl[e]);
+                    if (nfold > 0) sum += (double)sR[cl * kTcBM + r] + (double)sR[(TP + cl) * kTcBM + r];
                     const float val = (float)(sum * (outscale / (double)p.vscale[c]));
                     lanczos_epilogue_value(a, i, c, val, qp, pp, qq);
                 }
