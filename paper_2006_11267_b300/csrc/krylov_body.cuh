@@ -229,32 +229,122 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
     const int64_t i0 = (int64_t)k * s.rows_per_chunk;
     const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
     double ysq = 0.0;
-    for (int64_t i = i0 + tid; i < i1; i += 256) {
-        const R q = q_j[i];
-        R pn = pbuf[i];
-        pn = fma(-ahi, q, pn);
-        pn = fma(-alo, q, pn);
-        pbuf[i] = pn * invb;
-        R acc = (R)0;
-        for (int qq2 = 0; qq2 < Q; ++qq2) {
-            const int64_t off = (int64_t)qq2 * dstride + i;
-            const R dn = (q - co_delta[qq2] * d_prev[off] - co_eps[qq2] * d_old[off]) * co_invg[qq2];
-            d_old[off] = dn;
-            acc = fma(co_ct[qq2], dn, acc);
+    if constexpr (sizeof(R) == 4) {
+        // FP32: four consecutive rows per thread with 16-byte loads and
+        // stores (row chunks and the padded leading dimension are multiples
+        // of 128, so a group of four never straddles either).
+        constexpr int QB = 8;
+        const float4* q4 = reinterpret_cast<const float4*>(q_j);
+        float4* p4 = reinterpret_cast<float4*>(pbuf);
+        float4* y4 = reinterpret_cast<float4*>(y);
+        float4* l4 = reinterpret_cast<float4*>(ylo);
+        const float4* b4 = reinterpret_cast<const float4*>(b);
+        const float4* dp4 = reinterpret_cast<const float4*>(d_prev);
+        float4* do4 = reinterpret_cast<float4*>(d_old);
+        const int64_t ds4 = dstride / 4;
+        for (int64_t i4 = i0 / 4 + tid; i4 < i1 / 4; i4 += 256) {
+            const float4 qv = q4[i4];
+            const float4 pv = p4[i4];
+            const float4 yv4 = y4[i4];
+            const float4 lv4 = l4[i4];
+            const float4 bv4 = s.op == kOpSqrtIdentity ? b4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+            for (int q0 = 0; q0 < Q; q0 += QB) {
+                float4 dpv[QB], dqv[QB];
+                const float4* pp = dp4 + (int64_t)q0 * ds4 + i4;
+                const float4* po = do4 + (int64_t)q0 * ds4 + i4;
+#pragma unroll
+                for (int u = 0; u < QB; ++u) {
+                    dpv[u] = q0 + u < Q ? pp[u * ds4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    dqv[u] = q0 + u < Q ? po[u * ds4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < QB; ++u) {
+                    if (q0 + u >= Q) break;
+                    const int qq2 = q0 + u;
+                    const float de = co_delta[qq2], ep = co_eps[qq2], ig = co_invg[qq2], ct = co_ct[qq2];
+                    const float pa[4] = {dpv[u].x, dpv[u].y, dpv[u].z, dpv[u].w};
+                    const float oa[4] = {dqv[u].x, dqv[u].y, dqv[u].z, dqv[u].w};
+                    float dn[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        dn[e] = (qa[e] - de * pa[e] - ep * oa[e]) * ig;
+                        acc[e] = fmaf(ct, dn[e], acc[e]);
+                    }
+                    do4[(int64_t)qq2 * ds4 + i4] = make_float4(dn[0], dn[1], dn[2], dn[3]);
+                }
+            }
+            const float pa[4] = {pv.x, pv.y, pv.z, pv.w};
+            const float ya[4] = {yv4.x, yv4.y, yv4.z, yv4.w};
+            const float la[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
+            const float ba[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
+            float pn[4], ys[4], yl[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float t = fmaf(-(float)ahi, qa[e], pa[e]);
+                t = fmaf(-(float)alo, qa[e], t);
+                pn[e] = t * (float)invb;
+                // y += acc as a (leading, trailing) pair (Knuth's 2Sum).
+                const float sum = ya[e] + acc[e];
+                const float bp = sum - ya[e];
+                const float err = (ya[e] - (sum - bp)) + (acc[e] - bp);
+                ys[e] = sum;
+                yl[e] = la[e] + err;
+                const float yv = sum + yl[e];
+                const float est = s.op == kOpSqrtIdentity ? (float)sumw * ba[e] - yv : yv;
+                ysq += (double)est * (double)est;
+            }
+            p4[i4] = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            y4[i4] = make_float4(ys[0], ys[1], ys[2], ys[3]);
+            l4[i4] = make_float4(yl[0], yl[1], yl[2], yl[3]);
         }
-        // y += acc as a (leading, trailing) pair: Knuth's 2Sum error term goes
-        // to the trailing part, so the sum keeps ~2x R's precision.  The K^{1/2}
-        // identity form later subtracts y from (sum w) b, which cancels.
-        const R yh = y[i];
-        const R sum = yh + acc;
-        const R bp = sum - yh;
-        const R err = (yh - (sum - bp)) + (acc - bp);
-        const R yl = ylo[i] + err;
-        y[i] = sum;
-        ylo[i] = yl;
-        const R yv = sum + yl;
-        const R est = s.op == kOpSqrtIdentity ? sumw * b[i] - yv : yv;
-        ysq += (double)est * (double)est;
+    } else {
+        constexpr int QB = 8;                  // shifts whose directions are loaded together
+        for (int64_t i = i0 + tid; i < i1; i += 256) {
+            // Every load of the row is issued before any store (the compiler
+            // cannot move a load above a store that may alias it), so the HBM
+            // latency is paid once per block of QB shifts rather than per shift.
+            const R q = q_j[i];
+            R pn = pbuf[i];
+            const R yh = y[i];
+            const R ylo_i = ylo[i];
+            const R b_i = s.op == kOpSqrtIdentity ? b[i] : (R)0;
+            R acc = (R)0;
+            for (int q0 = 0; q0 < Q; q0 += QB) {
+                R dp[QB], dq[QB];
+                const R* pp = d_prev + (int64_t)q0 * dstride + i;
+                const R* po = d_old + (int64_t)q0 * dstride + i;
+    #pragma unroll
+                for (int u = 0; u < QB; ++u) {
+                    dp[u] = q0 + u < Q ? pp[u * dstride] : (R)0;
+                    dq[u] = q0 + u < Q ? po[u * dstride] : (R)0;
+                }
+    #pragma unroll
+                for (int u = 0; u < QB; ++u) {
+                    if (q0 + u >= Q) break;
+                    const int qq2 = q0 + u;
+                    const R dn = (q - co_delta[qq2] * dp[u] - co_eps[qq2] * dq[u]) * co_invg[qq2];
+                    d_old[(int64_t)qq2 * dstride + i] = dn;
+                    acc = fma(co_ct[qq2], dn, acc);
+                }
+            }
+            pn = fma(-ahi, q, pn);
+            pn = fma(-alo, q, pn);
+            pbuf[i] = pn * invb;
+            // y += acc as a (leading, trailing) pair: Knuth's 2Sum error term goes
+            // to the trailing part, so the sum keeps ~2x R's precision.  The K^{1/2}
+            // identity form later subtracts y from (sum w) b, which cancels.
+            const R sum = yh + acc;
+            const R bp = sum - yh;
+            const R err = (yh - (sum - bp)) + (acc - bp);
+            const R yl = ylo_i + err;
+            y[i] = sum;
+            ylo[i] = yl;
+            const R yv = sum + yl;
+            const R est = s.op == kOpSqrtIdentity ? sumw * b_i - yv : yv;
+            ysq += (double)est * (double)est;
+        }
     }
     // 5. Partial ||a_j||^2 for the next decision.
     ysq = warp_sum(ysq);
