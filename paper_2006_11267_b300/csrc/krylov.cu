@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) init_state_kernel(KrylovState<R> s) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) msminres_step_kernel(KrylovState<R> s, int j, int final_pass) {
+__global__ void __launch_bounds__(256, 2) msminres_step_kernel(KrylovState<R> s, int j, int final_pass) {
     msminres_step_body<R>(s, j, final_pass, blockIdx.x, blockIdx.y);
 }
 
