@@ -273,9 +273,13 @@ __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi
 // lane 0 issues the MMAs, warps 4-7 and 8-11 are two exp warpgroups that
 // split every step's 128 columns between them.  Warps 8-11 also fold each
 // completed chunk of O into the running sum; warps 4-7 run the epilogue.
-// Tensor pipe order: S(t+1) = U X_{t+1}^T, then O += P(t) V(t): S runs one
-// step ahead, so the exp of step t+1 overlaps the product of step t.
 // Columns [c0, c0 + TP) of V (those below a.T) are handled.
+//
+// Split K: with p.nsplit = S > 1, CTA b takes row tile b / S and the steps
+// [(b % S) nt / S, (b % S + 1) nt / S) of K's columns, so the grid fills the
+// SMs' waves evenly.  Each CTA writes its FP64 partial O; the last CTA of a
+// row tile to arrive (atomic count) adds the S partials in split order --
+// the result does not depend on which CTA is last -- and runs the epilogue.
 template <int KT, int TP, bool HALF>
 __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
     if (a.stop && *a.stop) return;
@@ -294,9 +298,14 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     volatile int* serr = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t tile = blockIdx.x;
+    const int S = p.nsplit;
+    const int64_t tile = blockIdx.x / S;
+    const int split = blockIdx.x % S;
     const int64_t i0 = tile * kTcBM;
-    const int nt = (int)(a.Npad / kTcKN);
+    const int ntot = (int)(a.Npad / kTcKN);
+    const int st0 = (int)((int64_t)split * ntot / S);
+    const int nt = (int)((int64_t)(split + 1) * ntot / S) - st0;   // steps of this CTA (>= 1)
+    __shared__ int last_arrival;
     const int nfold = (nt - 1) / kTcChunk;               // chunks folded before the last one
     constexpr uint32_t IDESC_S = tc::idesc_f16(kTcBM, kTcKN, !HALF);
     constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                                               kWaitLimit))
                     return false;
                 tc::mbar_expect_tx(&bars[kBarXFull + sx], kXStep);
-                tc::bulk_g2s(sX0 + sx * kXStep, p.ub + (int64_t)u * kXStep, kXStep, &bars[kBarXFull + sx]);
+                tc::bulk_g2s(sX0 + sx * kXStep, p.ub + (int64_t)(st0 + u) * kXStep, kXStep, &bars[kBarXFull + sx]);
                 return true;
             };
             bool ok = load_x(0) && (nt < 2 || load_x(1));
@@ -353,7 +362,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                     break;
                 }
                 tc::mbar_expect_tx(&bars[kBarVFull + sv], VSTEP);
-                tc::bulk_g2s(sV0 + sv * VSTEP, vblk + (int64_t)t * VSTEP, VSTEP, &bars[kBarVFull + sv]);
+                tc::bulk_g2s(sV0 + sv * VSTEP, vblk + (int64_t)(st0 + t) * VSTEP, VSTEP, &bars[kBarVFull + sv]);
                 if (*serr) break;
             }
             if (!ok) *serr = 1;
@@ -488,48 +497,115 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     }
 
     // ------------------------------------------------------------ epilogue
+    // FP64 runs at a few operations per clock per SM on this part, so the
+    // epilogue keeps its sums as unevaluated pairs of floats (Knuth's 2Sum,
+    // exact products by FMA) and converts to FP64 only per warp and column.
     double* red = reinterpret_cast<double*>(sX0);         // [4 warps][TP][3], free once O is complete
+    float2* colsum = reinterpret_cast<float2*>(red + 4 * TP * 3);   // [TP][128] this CTA's sums (S = 1)
+    const int r_e = 32 * ((warp - 4) & 3) + lane;         // row of warpgroup 0's thread
+    float2* part = S > 1 ? reinterpret_cast<float2*>(p.part) + ((int64_t)tile * S) * TP * kTcBM : nullptr;
+    bool ok = true;
     if (warp >= 4 && warp < 8) {
-        const int r = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const bool good = !*serr && tc::mbar_wait(&bars[kBarODone + (nt - 1) % kRing],
                                                   (uint32_t)(((nt - 1) / kRing) & 1), kWaitLimit);
-        const bool ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
+        ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
         if (!ok) *serr = 1;
         tc::fence_after_sync();
-        const int64_t i = i0 + r;
-        const double outscale = a.s;
-        const int wl = warp & 3;
+        // This CTA's column sums over its steps as (leading, trailing) floats.
 #pragma unroll 1
         for (int cc = 0; cc < TP / 32; ++cc) {
             uint32_t o[32];
             if (ok) tc::tmem_ld32(tO + lane_base + 32 * cc, o);
-#pragma unroll 1
+#pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const int cl = 32 * cc + e;
-                const int c = c0 + cl;
-                if (c >= a.T) break;
-                double qp = 0.0, pp = 0.0, qq = 0.0;
-                if (ok) {
-                    double sum = (double)__uint_as_float(o[e]);
-                    if (nfold > 0) sum += (double)sR[cl * kTcBM + r] + (double)sR[(TP + cl) * kTcBM + r];
-                    const float val = (float)(sum * (outscale / (double)p.vscale[c]));
-                    lanczos_epilogue_value(a, i, c, val, qp, pp, qq);
+                float h = ok ? __uint_as_float(o[e]) : 0.f, l = 0.f;
+                if (ok && nfold > 0) {
+                    float rh = sR[cl * kTcBM + r_e];
+                    float rl = sR[(TP + cl) * kTcBM + r_e];
+                    two_sum_into(rh, rl, h);
+                    h = rh;
+                    l = rl;
                 }
-                if (a.mode == kLanczos) {
-                    qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
-                    if (lane == 0) {
-                        red[(wl * TP + cl) * 3 + 0] = qp;
-                        red[(wl * TP + cl) * 3 + 1] = pp;
-                        red[(wl * TP + cl) * 3 + 2] = qq;
-                    }
-                }
+                if (S > 1) part[((int64_t)split * TP + cl) * kTcBM + r_e] = make_float2(h, l);
+                else colsum[cl * kTcBM + r_e] = make_float2(h, l);
             }
+        }
+        if (S > 1) {
+            __threadfence();
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            if (warp == 4 && lane == 0) {
+                const int old = atomicAdd(&p.cnt[tile], 1);
+                last_arrival = old == S - 1;
+                if (old == S - 1) p.cnt[tile] = 0;          // ready for the next launch
+                __threadfence();
+            }
+            asm volatile("bar.sync 2, 128;" ::: "memory");
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (a.mode == kLanczos) {
+    const bool finish = S == 1 || last_arrival;
+    if (finish && warp >= 4 && warp < 8) {
+        const int64_t i = i0 + r_e;
+        const int wl = warp & 3;
+        const bool row_in = i < a.N;
+#pragma unroll 1
+        for (int cl = 0; cl < TP; ++cl) {
+            const int c = c0 + cl;
+            if (c >= a.T) break;
+            float h = 0.f, l = 0.f;
+            if (S > 1) {
+                for (int sp = 0; sp < S; ++sp) {
+                    const float2 v2 = __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r_e]);
+                    two_sum_into(h, l, v2.x);
+                    l += v2.y;
+                }
+            } else {
+                const float2 v2 = colsum[cl * kTcBM + r_e];
+                h = v2.x;
+                l = v2.y;
+            }
+            // O = (h + l) outscale / vscale (a power of two), rounded once.
+            const float sc = (float)((double)a.s / (double)p.vscale[c]);
+            float o = fmaf(h, sc, l * sc);
+            const int64_t idx = (int64_t)c * a.ldv + i;
+            const float v = a.V[idx];
+            o += a.noise * v;
+            if (a.mode == kPlain) {
+                if (row_in) a.out[(int64_t)c * a.ldo + i] = o;
+                continue;
+            }
+            const float pv = row_in ? (float)(o - (float)a.beta[c] * a.qprev[idx]) : 0.f;
+            a.qprev[idx] = pv;
+            // q.p, p.p, q.q of this row: exact products as float pairs,
+            // summed over the warp's 32 rows with 2Sum.
+            float sh[3], sl[3];
+            const float fa[3] = {v, pv, v}, fb[3] = {pv, pv, v};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sh[k] = fa[k] * fb[k];
+                sl[k] = fmaf(fa[k], fb[k], -sh[k]);
+            }
+#pragma unroll
+            for (int ofs = 16; ofs > 0; ofs >>= 1) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, sh[k], ofs);
+                    const float ol = __shfl_xor_sync(0xffffffffu, sl[k], ofs);
+                    two_sum_into(sh[k], sl[k], oh);
+                    sl[k] += ol;
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) red[(wl * TP + cl) * 3 + k] = (double)sh[k] + (double)sl[k];
+            }
+        }
+    }
+    __syncthreads();
+    if (finish && a.mode == kLanczos) {
         const int ncol = min(TP, a.T - c0);
         for (int cl = tid; cl < ncol; cl += blockDim.x) {
             double* dst = a.partials + ((int64_t)tile * a.T + c0 + cl) * 3;
@@ -552,7 +628,7 @@ cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaSt
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    mvm_tc_kernel<KT, TP, HALF><<<(unsigned)(a.Npad / kTcBM), 384, smem, st>>>(p, a, c0);
+    mvm_tc_kernel<KT, TP, HALF><<<(unsigned)(a.Npad / kTcBM * p.nsplit), 384, smem, st>>>(p, a, c0);
     return cudaGetLastError();
 }
 
@@ -587,12 +663,38 @@ int tc_padded_t(int T) {
 
 int64_t tc_row_tiles(int64_t Npad) { return Npad / kTcBM; }
 
+// CTAs per row tile: the S in 1..8 that minimises waves x steps per CTA,
+// with 4 steps charged per CTA for its pipeline start and epilogue.
+int tc_split(int64_t Npad) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0) {
+            cudaGetLastError();
+            sms = 148;
+        }
+    }
+    const int64_t tiles = Npad / kTcBM, steps = Npad / kTcKN;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int S = 1; S <= 8 && S <= steps; ++S) {
+        const double waves = (double)((tiles * S + sms - 1) / sms);
+        const double cost = waves * ((double)steps / S + 4.0);
+        if (cost < best_cost * 0.999) { best_cost = cost; best = S; }
+    }
+    return best;
+}
+
 size_t tc_points_bytes(int64_t Npad, int T) {
     const int TP = tc_padded_t(T);
     if (TP < 0) return 0;
     const size_t pts = (size_t)Npad * kTcRowBytes;
     const size_t vb = (size_t)(Npad / kTcBN) * 2 * TP * 128;
-    return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256;
+    const int S = tc_split(Npad);
+    const size_t part = S > 1 ? (size_t)(Npad / kTcBM) * S * tc_group_t(T) * kTcBM * sizeof(double) + 256 : 0;
+    const size_t cnt = S > 1 ? (size_t)(Npad / kTcBM) * sizeof(int) + 256 : 0;
+    return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256 + part + cnt;
 }
 
 TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision) {
@@ -612,6 +714,12 @@ TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision) {
     p.vscale = reinterpret_cast<float*>(take((size_t)p.TP * sizeof(float)));
     p.mean = reinterpret_cast<double*>(take(16 * sizeof(double)));
     p.err = reinterpret_cast<int*>(take(sizeof(int)));
+    p.nsplit = tc_split(Npad);
+    if (p.nsplit > 1) {
+        p.part = reinterpret_cast<double*>(
+            take((size_t)(Npad / kTcBM) * p.nsplit * tc_group_t(T) * kTcBM * sizeof(double)));
+        p.cnt = reinterpret_cast<int*>(take((size_t)(Npad / kTcBM) * sizeof(int)));
+    }
     return p;
 }
 
@@ -620,6 +728,8 @@ cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int
     cudaError_t e = cudaMemsetAsync(p.mean, 0, 16 * sizeof(double), st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.err, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if (p.nsplit > 1 && (e = cudaMemsetAsync(p.cnt, 0, sizeof(int) * (size_t)(p.Npad / kTcBM), st)) != cudaSuccess)
+        return e;
     tc_mean_kernel<<<148, 256, 0, st>>>(Xp, N, dp, p.mean);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const double c2 = kt == CIQ_RBF ? kLog2e : 1.0;
