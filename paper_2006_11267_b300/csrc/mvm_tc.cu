@@ -222,7 +222,9 @@ constexpr int kTcChunk = 8;
 // block by block: the 16 values of S in columns [16k, 16k+16) become 8
 // columns of leading parts [16k, 16k+8) and 8 of trailing parts [16k+8,
 // 16k+16) (two 16-bit values per column), the A operand of K-step k of the
-// product; O [384, 384 + TP).  Step t uses buffer t % 3, so S(t+2) can be
+// product; two O accumulators [384, 384 + TP) and [384 + TP, 384 + 2 TP)
+// taking alternate chunks, so a chunk is folded while the next one
+// accumulates.  Step t uses buffer t % 3, so S(t+2) can be
 // computed while the products of steps t-1 and t are still queued; exp
 // warpgroup g turns columns [64 g, 64 g + 64) of every step into P.  The
 // compensated running sum (leading and trailing FP32 parts) lives in shared
@@ -243,8 +245,8 @@ enum TcBar {
     kBarSDone = 11,        // [8] S of step t complete (ring t % 8): exp may start, point stage free
     kBarODone = 19,        // [8] product of step t complete: S buffer and V stage free, O readable
     kBarPFull = 27,        // [3] P written over S in buffer b by both exp warpgroups
-    kBarOFree = 30,        // O folded into the running sum, accumulator free
-    kBarCount = 31
+    kBarOFree = 30,        // [2] O accumulator c % 2 folded into the running sum, free again
+    kBarCount = 32
 };
 
 // Kernel value / outputscale from S = -c^2 r^2 / 2 (RBF: S <= 0 up to
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
         }
         for (int b = 0; b < kNB; ++b) tc::mbar_init(&bars[kBarPFull + b], 256);
         tc::mbar_init(&bars[kBarOFree], 128);
+        tc::mbar_init(&bars[kBarOFree + 1], 128);
         tc::fence_mbarrier_init();
         *serr = 0;
     }
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t tO = tmem + kNB * kTcKN;
+    const uint32_t tO0 = tmem + kNB * kTcKN;              // O of even chunks; odd chunks at tO0 + TP
     const uint8_t* vblk = p.vblk;
 
     if (warp == 0) {
@@ -403,11 +406,13 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
             if (good && nt > 1) good = issue_s(1);
             for (int t = 0; good && t < nt; ++t) {
                 const int b = t % kNB, sv = t % NV;
+                const int ch = t / kTcChunk;
                 const bool fresh = (t % kTcChunk) == 0;
+                const uint32_t tO = tO0 + (ch & 1) * TP;
                 good = tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t / kNB) & 1), kWaitLimit) &&
                        tc::mbar_wait(&bars[kBarVFull + sv], (uint32_t)((t / NV) & 1), kWaitLimit) &&
-                       (!fresh || t == 0 ||
-                        tc::mbar_wait(&bars[kBarOFree], (uint32_t)((t / kTcChunk - 1) & 1), kWaitLimit));
+                       (!fresh || ch < 2 ||
+                        tc::mbar_wait(&bars[kBarOFree + (ch & 1)], (uint32_t)((ch / 2 - 1) & 1), kWaitLimit));
                 if (!good) break;
                 tc::fence_after_sync();
                 const uint32_t tP = tmem + b * kTcKN;
@@ -467,12 +472,17 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
             tc::tmem_wait_st64(h0, l0, h1, l1, h2, l2, h3, l3);
             tc::fence_before_sync();
             tc::mbar_arrive(&bars[kBarPFull + b]);
-            // Fold a completed chunk of O into the running sum (warpgroup 1).
-            if (g == 1 && (t % kTcChunk) == kTcChunk - 1 && t != nt - 1) {
-                const int c = t / kTcChunk;
-                const bool okc = tc::mbar_wait(&bars[kBarODone + t % kRing], (uint32_t)((t / kRing) & 1), kWaitLimit);
+            // Fold the previous chunk of O into the running sum (warpgroup 1),
+            // one step after its last product was issued, so the wait for
+            // that product rarely blocks; the accumulator is needed again
+            // two chunks later.
+            if (g == 1 && t >= kTcChunk && (t % kTcChunk) == 0) {
+                const int c = t / kTcChunk - 1;
+                const int te = t - 1;                     // last step of chunk c
+                const bool okc = tc::mbar_wait(&bars[kBarODone + te % kRing], (uint32_t)((te / kRing) & 1), kWaitLimit);
                 if (__shfl_sync(0xffffffffu, (int)(!okc || *serr), 0)) { *serr = 1; break; }
                 tc::fence_after_sync();
+                const uint32_t tO = tO0 + (c & 1) * TP;
 #pragma unroll 1
                 for (int cc = 0; cc < TP / 32; ++cc) {
                     uint32_t o[32];
@@ -489,7 +499,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
                     }
                 }
                 tc::fence_before_sync();
-                tc::mbar_arrive(&bars[kBarOFree]);
+                tc::mbar_arrive(&bars[kBarOFree + (c & 1)]);
             }
         }
         // The running sum written by warpgroup 1 is read by warpgroup 0's epilogue.
@@ -513,6 +523,7 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
         if (!ok) *serr = 1;
         tc::fence_after_sync();
         // This CTA's column sums over its steps as (leading, trailing) floats.
+        const uint32_t tO = tO0 + (((nt - 1) / kTcChunk) & 1) * TP;
 #pragma unroll 1
         for (int cc = 0; cc < TP / 32; ++cc) {
             uint32_t o[32];
