@@ -558,60 +558,82 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
     tc::fence_before_sync();
     __syncthreads();
     const bool finish = S == 1 || last_arrival;
-    if (finish && warp >= 4 && warp < 8) {
+    if (finish && warp >= 4) {
+        // Both warpgroups finish the tile: warpgroup g takes half of the
+        // columns, in batches of 8 whose loads are all issued before any
+        // store (latency is paid once per batch, not per column).
+        constexpr int CB = 8;
+        const int g = (warp - 4) >> 2;
         const int64_t i = i0 + r_e;
         const int wl = warp & 3;
         const bool row_in = i < a.N;
+        const int cbeg = g * (TP / 2), cend = min(cbeg + TP / 2, a.T - c0);
 #pragma unroll 1
-        for (int cl = 0; cl < TP; ++cl) {
-            const int c = c0 + cl;
-            if (c >= a.T) break;
-            float h = 0.f, l = 0.f;
-            if (S > 1) {
-                for (int sp = 0; sp < S; ++sp) {
-                    const float2 v2 = __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r_e]);
-                    two_sum_into(h, l, v2.x);
-                    l += v2.y;
+        for (int cb = cbeg; cb < cend; cb += CB) {
+            float h[CB], l[CB], v[CB], qp[CB], bt[CB], sc[CB];
+#pragma unroll
+            for (int u = 0; u < CB; ++u) {
+                const int cl = cb + u;
+                const bool in = cl < cend;
+                h[u] = 0.f;
+                l[u] = 0.f;
+                if (in) {
+                    if (S > 1) {
+                        for (int sp = 0; sp < S; ++sp) {
+                            const float2 v2 = __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r_e]);
+                            two_sum_into(h[u], l[u], v2.x);
+                            l[u] += v2.y;
+                        }
+                    } else {
+                        const float2 v2 = colsum[cl * kTcBM + r_e];
+                        h[u] = v2.x;
+                        l[u] = v2.y;
+                    }
                 }
-            } else {
-                const float2 v2 = colsum[cl * kTcBM + r_e];
-                h = v2.x;
-                l = v2.y;
-            }
-            // O = (h + l) outscale / vscale (a power of two), rounded once.
-            const float sc = (float)((double)a.s / (double)p.vscale[c]);
-            float o = fmaf(h, sc, l * sc);
-            const int64_t idx = (int64_t)c * a.ldv + i;
-            const float v = a.V[idx];
-            o += a.noise * v;
-            if (a.mode == kPlain) {
-                if (row_in) a.out[(int64_t)c * a.ldo + i] = o;
-                continue;
-            }
-            const float pv = row_in ? (float)(o - (float)a.beta[c] * a.qprev[idx]) : 0.f;
-            a.qprev[idx] = pv;
-            // q.p, p.p, q.q of this row: exact products as float pairs,
-            // summed over the warp's 32 rows with 2Sum.
-            float sh[3], sl[3];
-            const float fa[3] = {v, pv, v}, fb[3] = {pv, pv, v};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                sh[k] = fa[k] * fb[k];
-                sl[k] = fmaf(fa[k], fb[k], -sh[k]);
+                const int64_t idx = (int64_t)(c0 + cl) * a.ldv + i;
+                v[u] = in ? a.V[idx] : 0.f;
+                qp[u] = (in && a.mode == kLanczos) ? a.qprev[idx] : 0.f;
+                bt[u] = (in && a.mode == kLanczos) ? (float)a.beta[c0 + cl] : 0.f;
+                // O = (h + l) outscale / vscale (a power of two), rounded once.
+                sc[u] = in ? (float)((double)a.s / (double)p.vscale[c0 + cl]) : 0.f;
             }
 #pragma unroll
-            for (int ofs = 16; ofs > 0; ofs >>= 1) {
+            for (int u = 0; u < CB; ++u) {
+                const int cl = cb + u;
+                if (cl >= cend) break;
+                const int c = c0 + cl;
+                const int64_t idx = (int64_t)c * a.ldv + i;
+                float o = fmaf(h[u], sc[u], l[u] * sc[u]);
+                o += a.noise * v[u];
+                if (a.mode == kPlain) {
+                    if (row_in) a.out[(int64_t)c * a.ldo + i] = o;
+                    continue;
+                }
+                const float pv = row_in ? (float)(o - bt[u] * qp[u]) : 0.f;
+                a.qprev[idx] = pv;
+                // q.p, p.p, q.q of this row: exact products as float pairs,
+                // summed over the warp's 32 rows with 2Sum.
+                float sh[3], sl[3];
+                const float fa[3] = {v[u], pv, v[u]}, fb[3] = {pv, pv, v[u]};
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, sh[k], ofs);
-                    const float ol = __shfl_xor_sync(0xffffffffu, sl[k], ofs);
-                    two_sum_into(sh[k], sl[k], oh);
-                    sl[k] += ol;
+                    sh[k] = fa[k] * fb[k];
+                    sl[k] = fmaf(fa[k], fb[k], -sh[k]);
                 }
-            }
-            if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) red[(wl * TP + cl) * 3 + k] = (double)sh[k] + (double)sl[k];
+                for (int ofs = 16; ofs > 0; ofs >>= 1) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, sh[k], ofs);
+                        const float ol = __shfl_xor_sync(0xffffffffu, sl[k], ofs);
+                        two_sum_into(sh[k], sl[k], oh);
+                        sl[k] += ol;
+                    }
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) red[(wl * TP + cl) * 3 + k] = (double)sh[k] + (double)sl[k];
+                }
             }
         }
     }
