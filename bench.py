@@ -73,8 +73,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
-    ap.add_argument("--workload", default="thompson50k", choices=["thompson50k", "batched512"],
-                    help="batched512: the uneven 512-problem batch through ciq_sqrt_batched")
+    ap.add_argument("--workload", default="thompson50k", choices=["thompson50k", "batched512", "precision200k"],
+                    help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
+                         "the 200,000-point Matern precision sweep")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
                     help="time only the kernel MVM on the first N points of the workload (for profiling)")
     return ap.parse_args()
@@ -509,12 +510,75 @@ def run_batched(args):
     return 0
 
 
+def run_precision(args):
+    """Precision sweep, 200,000-point Matern-5/2 workload, K^{-1/2}B, Q = 15:
+    per mode (plain FP32, FP16 split, BF16 split) the solve error against the
+    FP64 eigendecomposition on a 4096-point subsample (T = 256), and at full
+    size the MVM time and its difference from the FP32 MVM, and the time per
+    msMINRES iteration (a fixed 10-iteration solve)."""
+    import torch
+
+    import paper_2006_11267_b300 as P
+    from oracle import eig, kernels
+
+    torch.cuda.set_device(0)
+    W = ci.PRECISION_200K
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    modes = ("fp32", "fp16", "bf16")
+    n_sub = 4096
+    Xs = ci.points(W.seed, W.n, W.d)[:n_sub].astype(np.float32)
+    Bs = ci.rhs(W.seed + 1, n_sub, W.t).astype(np.float32)
+    K = kernels.dense_K(Xs.astype(np.float64), W.kernel, W.lengthscale, W.outputscale, W.noise)
+    truth = eig.invsqrt_apply(K, Bs.T.astype(np.float64)).T
+    Xd, Bd = torch.from_numpy(Xs).cuda(), torch.from_numpy(Bs).cuda()
+    sub = {}
+    for m in modes:
+        out, info = P.ciq_invsqrt(Xd, k, Bd, W.q, 1e-4, max_iter=2000, precision=m)
+        torch.cuda.synchronize()
+        err = float(np.linalg.norm(out.cpu().numpy() - truth) / np.linalg.norm(truth))
+        sub[m] = {"rel_err_vs_fp64_eig": err, "iterations": info["iters"], "status": info["status_name"]}
+    X = torch.from_numpy(ci.points(W.seed, W.n, W.d).astype(np.float32)).cuda()
+    B = torch.from_numpy(ci.rhs(W.seed, W.n, W.t).astype(np.float32)).cuda()
+    full = {}
+    ref = None
+    for m in modes:
+        P.ciq_kernel_mvm(X, k, B, precision=m)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = P.ciq_kernel_mvm(X, k, B, precision=m)
+        e1.record()
+        torch.cuda.synchronize()
+        if m == "fp32":
+            ref = out.clone()
+        diff = float(torch.linalg.norm((out - ref).double()) / torch.linalg.norm(ref.double()))
+        # msMINRES iterations timed by the library's profile mode (CUDA
+        # events between consecutive launches): MVM + recurrence.
+        _, info = P.ciq_invsqrt(X, k, B, W.q, 0.0, max_iter=12, lanczos_iters=10, precision=m, profile=1,
+                                check_every=4)
+        it_ms = (info["t_mvm_ms"] / max(1, info["mvm_launches"]) + info["t_step_ms"] / max(1, info["step_launches"]))
+        full[m] = {"mvm_call_ms": e0.elapsed_time(e1), "mvm_rel_diff_vs_fp32": diff, "ms_per_iteration": it_ms,
+                   "mvm_ms_in_solve": info["t_mvm_ms"] / max(1, info["mvm_launches"])}
+    line = {"metric": "K^{-1/2}b precision sweep (error vs FP64 oracle per mode)", "value": full["fp16"]["ms_per_iteration"],
+            "unit": "ms/iteration (FP16 split, N=200000, T=256)", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": False, "dtype": "f32 / fp16x2 / bf16x2 tiles, f64 scalars", "data": "synthetic",
+            "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
+                       "noise": W.noise, "T": W.t, "Q": W.q, "op": "invsqrt", "subsample": n_sub,
+                       "subsample_tol": 1e-4},
+            "subsample": sub, "full_size": full}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched512":
         return run_batched(args)
+    if args.workload == "precision200k":
+        return run_precision(args)
     return run_ours(args)
 
 

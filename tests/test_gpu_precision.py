@@ -1,0 +1,67 @@
+"""Precision sweep on the 200,000-point Matern-5/2 workload (lengthscale 0.1,
+sigma^2 = 1e-2, d = 4): K^{-1/2}B with Q = 15 through the plain FP32 path and
+the FP16 / BF16 hi/lo-split tensor-core tiles, each against the FP64
+eigendecomposition oracle on a 4096-point subsample, and the full-size
+tensor-core MVMs against the FP32 MVM on sampled rows.
+
+Tolerances come from the arithmetic of each mode:
+  * every mode's solve error is dominated by the stop rule (relative residual
+    1e-4 per shift) and the quadrature, so all three must stay within 1e-3
+    of the oracle, and the split modes within 3x the FP32 error plus their
+    own MVM error (FP16 split ~22 significant bits, BF16 split ~16);
+  * full-size MVM: FP16 split 2e-5, BF16 split 2e-4 relative to the FP32
+    MVM (whose own error is ~1e-6).
+"""
+import numpy as np
+import pytest
+import torch
+
+import ciq_inputs as ci
+import paper_2006_11267_b300 as P
+from oracle import eig, kernels
+
+pytestmark = pytest.mark.gpu
+
+W = ci.PRECISION_200K
+DEV = "cuda"
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def subsample():
+    n, t = 4096, 32
+    X = ci.points(W.seed, W.n, W.d)[:n].astype(np.float32)
+    B = ci.rhs(W.seed + 1, n, t).astype(np.float32)
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    K = kernels.dense_K(X.astype(np.float64), W.kernel, W.lengthscale, W.outputscale, W.noise)
+    truth = eig.invsqrt_apply(K, B.T.astype(np.float64)).T
+    return X, B, k, truth
+
+
+def test_invsqrt_each_precision_against_eig_oracle(subsample):
+    X, B, k, truth = subsample
+    Xd, Bd = torch.from_numpy(X).to(DEV), torch.from_numpy(B).to(DEV)
+    errs = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        out, info = P.ciq_invsqrt(Xd, k, Bd, W.q, 1e-4, max_iter=2000, precision=prec)
+        assert info["status"] == 0, (prec, info["status_name"])
+        errs[prec] = rel(out.cpu().numpy(), truth)
+    assert errs["fp32"] < 1e-3, errs
+    assert errs["fp16"] < min(1e-3, 3 * errs["fp32"] + 1e-4), errs
+    assert errs["bf16"] < 1e-3, errs
+
+
+def test_full_size_tensor_core_mvm_against_fp32_mvm():
+    n, t = W.n, 64
+    X = torch.from_numpy(ci.points(W.seed, n, W.d).astype(np.float32)).to(DEV)
+    V = torch.from_numpy(ci.rhs(W.seed + 2, n, t).astype(np.float32)).to(DEV)
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    ref = P.ciq_kernel_mvm(X, k, V, precision="fp32")
+    for prec, tol in (("fp16", 2e-5), ("bf16", 2e-4)):
+        out = P.ciq_kernel_mvm(X, k, V, precision=prec)
+        assert rel(out.cpu().numpy(), ref.cpu().numpy()) < tol, prec
