@@ -240,12 +240,14 @@ typedef struct {
  * covers every problem that has not stopped (work lists rebuilt on the device
  * between batches of iterations, finished problems drop out); problems share
  * Q, tol and the options; all problems must have the same T.  FP32 vectors,
- * FP64 scalars, on-the-fly MVM on CUDA cores.  Every problem's arithmetic is
- * that of ciq_sqrt / ciq_invsqrt with the same options, so each output equals
- * the single-problem call's bit for bit.  1 <= P <= CIQ_MAX_BATCH.
- * CIQ_ERR_UNSUPPORTED unless opt->precision is CIQ_PREC_FP32, opt->mvm is not
- * CIQ_MVM_STORED, opt->sqrt_form is CIQ_SQRT_IDENTITY, and quad_w, quad_t,
- * lanczos_start and workspace are NULL.  The device workspace (the sum of
+ * FP64 scalars; on-the-fly MVM on CUDA cores (CIQ_PREC_FP32) or on tensor
+ * cores with FP16/BF16 split tiles (CIQ_PREC_FP16/BF16; then T <= 64 and
+ * every d <= 14).  Every problem's arithmetic is that of ciq_sqrt /
+ * ciq_invsqrt with the same options, so each output equals the
+ * single-problem call's bit for bit.  1 <= P <= CIQ_MAX_BATCH.
+ * CIQ_ERR_UNSUPPORTED if opt->mvm is CIQ_MVM_STORED, opt->sqrt_form is not
+ * CIQ_SQRT_IDENTITY, quad_w, quad_t, lanczos_start or workspace is set, or a
+ * tensor-core batch breaks its limits.  The device workspace (the sum of
  * the problems' ciq_workspace_bytes plus small tables) is allocated on
  * stream and freed before return; the call returns after the stream work.
  * infos: NULL or P entries (launches = the call's total).  Returns

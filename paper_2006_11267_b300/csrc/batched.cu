@@ -23,21 +23,6 @@ namespace ciq {
 
 namespace {
 
-// Problem and local item of block `item`; false past the list's total.
-__device__ __forceinline__ bool list_item(const DevList& L, int item, int& p, int& local) {
-    const int np = *L.np;
-    if (np <= 0 || item >= L.prefix[np]) return false;
-    int lo = 0, hi = np - 1;              // largest k with prefix[k] <= item
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (L.prefix[mid] <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    p = L.ids[lo];
-    local = item - L.prefix[lo];
-    return true;
-}
-
 __global__ void __launch_bounds__(256) batched_setup_kernel(const BatchProblem* probs, int phase, uint64_t seed,
                                                             int Q, DevList L) {
     int p, local;
@@ -182,9 +167,8 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int* t
     return before + x - v;
 }
 
-// Block l rebuilds dynamic list l: lists 0..kBatchClasses-1 hold the MVM work
-// of problems of that class, the last one the recurrence work (chunks x T).
-// A problem stays listed while *all_done == 0.
+// Block l rebuilds dynamic list l over the problems with list_items[l] > 0
+// whose columns have not all stopped (*all_done == 0).
 __global__ void __launch_bounds__(1024) rebuild_lists_kernel(const BatchProblem* probs, int P, DynLists lists,
                                                              int* totals) {
     __shared__ int warp_tot[32];
@@ -195,13 +179,9 @@ __global__ void __launch_bounds__(1024) rebuild_lists_kernel(const BatchProblem*
     int n = 0, items = 0;
     for (int p = p0; p < p1; ++p) {
         const BatchProblem& bp = probs[p];
-        if (*bp.ks.all_done) continue;
-        if (l < kBatchClasses) {
-            if (bp.cls != l) continue;
-            items += bp.mvm_items;
-        } else {
-            items += bp.ks.nchunks * bp.ks.T;
-        }
+        const int c = bp.list_items[l];
+        if (c <= 0 || *bp.ks.all_done) continue;
+        items += c;
         ++n;
     }
     int n_total, item_total;
@@ -210,14 +190,8 @@ __global__ void __launch_bounds__(1024) rebuild_lists_kernel(const BatchProblem*
     int off = block_exclusive_scan(items, warp_tot, &item_total);
     for (int p = p0; p < p1; ++p) {
         const BatchProblem& bp = probs[p];
-        if (*bp.ks.all_done) continue;
-        int c;
-        if (l < kBatchClasses) {
-            if (bp.cls != l) continue;
-            c = bp.mvm_items;
-        } else {
-            c = bp.ks.nchunks * bp.ks.T;
-        }
+        const int c = bp.list_items[l];
+        if (c <= 0 || *bp.ks.all_done) continue;
         L.ids[pos] = p;
         L.prefix[pos] = off;
         ++pos;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "krylov.cuh"
+#include "mvm_tc.cuh"
 
 namespace ciq {
 
@@ -26,6 +27,8 @@ struct BatchProblem {
     int mvm_tiles;              // row tiles of the main MVM (items = tiles x groups)
     int mvm_items;
     int pre_tiles;              // row tiles of the pre-pass MVM (= its items)
+    TcPoints tcp;               // tensor-core operands (tensor-core batches only)
+    int list_items[9];          // work items of this problem in each main-loop list (0: not a member)
 };
 
 constexpr int kBatchClasses = 8;            // 2 kernel types x 4 padded dimensions
@@ -43,9 +46,28 @@ struct DevList {
     int* prefix;
 };
 
-// Main-loop lists rebuilt on the device: one per MVM class, then the
-// recurrence list; kBatchDynLists in all.
+// Problem and local item of block `item`; false past the list's total.
+__device__ __forceinline__ bool list_item(const DevList& L, int item, int& p, int& local) {
+    const int np = *L.np;
+    if (np <= 0 || item >= L.prefix[np]) return false;
+    int lo = 0, hi = np - 1;              // largest k with prefix[k] <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.prefix[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    p = L.ids[lo];
+    local = item - L.prefix[lo];
+    return true;
+}
+
+// Main-loop lists rebuilt on the device, kBatchDynLists in all.  CUDA-core
+// batches: one per MVM class (kernel type x padded dimension), then the
+// recurrence list.  Tensor-core batches: lists 0 and 1 are the MVM work of
+// RBF and Matern problems, list 2 the V split, the last the recurrence.
 constexpr int kBatchDynLists = kBatchClasses + 1;
+constexpr int kListTcSplit = 2;
+static_assert(kBatchDynLists == 9, "BatchProblem::list_items size");
 struct DynLists {
     DevList l[kBatchDynLists];
 };
@@ -80,6 +102,17 @@ cudaError_t launch_batched_step(const BatchProblem* probs, int j, bool final_pas
 // packed[p * kSummaryStride ...] (summary[8], then the NodeSlot block).
 cudaError_t launch_batched_summary(const BatchProblem* probs, int final_j, double* packed, DevList L, int blocks,
                                    cudaStream_t st);
+// Tensor-core batches (mvm_tc.cu): operand preparation (points centre and
+// split operands; unit V scales; split-K counters), the per-iteration V
+// split, and the MVM over a list of (problem, row tile x split) items.
+cudaError_t launch_batched_tc_mean(const BatchProblem* probs, DevList one, int blocks, cudaStream_t st);
+cudaError_t launch_batched_tc_points(const BatchProblem* probs, DevList rows256, int blocks, bool half,
+                                     cudaStream_t st);
+cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevList L, int blocks, bool half,
+                                    cudaStream_t st);
+cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, DevList L,
+                                  int blocks, cudaStream_t st);
+
 // Rebuild the kBatchDynLists main-loop lists over problems whose columns
 // have not all stopped; totals[l] = the new item total of list l.
 cudaError_t launch_rebuild_lists(const BatchProblem* probs, int P, const DynLists& lists, int* totals,

@@ -616,11 +616,16 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     ciq_default_options(&o);
     if (opt) o = *opt;
     if (!valid_options(o)) return CIQ_ERR_ARG;
-    if (o.precision != CIQ_PREC_FP32 || o.mvm == CIQ_MVM_STORED || o.quad_w || o.quad_t || o.lanczos_start ||
-        o.workspace || o.sqrt_form != CIQ_SQRT_IDENTITY)
+    if (o.mvm == CIQ_MVM_STORED || o.quad_w || o.quad_t || o.lanczos_start || o.workspace ||
+        o.sqrt_form != CIQ_SQRT_IDENTITY)
         return CIQ_ERR_UNSUPPORTED;
     const int T = probs[0].T;
     if (T < 1) return CIQ_ERR_ARG;
+    // Tensor-core batches: FP16/BF16 split tiles, one launch group (T <= 64).
+    const bool tc = o.precision != CIQ_PREC_FP32;
+    const bool half = o.precision == CIQ_PREC_FP16;
+    if (tc && (tc_padded_t(T) < 0 || T > 64)) return CIQ_ERR_UNSUPPORTED;
+    const int TP = tc ? tc_padded_t(T) : 0;
     std::vector<char> given(P);
     for (int p = 0; p < P; ++p) {
         const ciq_problem& q = probs[p];
@@ -628,6 +633,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
             return CIQ_ERR_ARG;
         given[p] = q.lmin > 0.0 && q.lmax > 0.0;
         if (given[p] && !(q.lmax >= q.lmin && std::isfinite(q.lmax))) return CIQ_ERR_ARG;
+        if (tc && !tc_supported(o.precision, q.d)) return CIQ_ERR_UNSUPPORTED;
         if (!device_accessible(q.X) || !device_accessible(q.B) || !device_accessible(q.out)) return CIQ_ERR_ARG;
     }
     keep_pool_warm();
@@ -640,7 +646,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     std::vector<size_t> offs(P);
     size_t off = 0;
     for (int p = 0; p < P; ++p) {
-        plans.push_back(make_plan<float>(probs[p].N, probs[p].d, T, Q, o, !given[p], false));
+        plans.push_back(make_plan<float>(probs[p].N, probs[p].d, T, Q, o, !given[p], tc));
         if (record_tri) {
             plans.back().tri_on = true;
             plans.back().layout(nullptr);
@@ -650,7 +656,8 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     }
     const int groups = (T + batch_mvm_group(T) - 1) / batch_mvm_group(T);
     std::vector<BatchProblem> hp(P);
-    HostList prep, one, init, pre, pre_one, given_one, fin, comb, pre_mvm[kBatchClasses], dyn[kBatchDynLists];
+    HostList prep, one, init, pre, pre_one, given_one, fin, comb, rows256, pre_mvm[kBatchClasses],
+        dyn[kBatchDynLists];
     int64_t biggest = 0;
     for (int p = 0; p < P; ++p) {
         const Plan<float>& pl = plans[p];
@@ -666,11 +673,20 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                                      (int64_t)pl.nchunks * T});
         prep.add(p, prep_items);
         one.add(p, 1);
+        rows256.add(p, (pl.Npad + 255) / 256);
         init.add(p, (int64_t)pl.nchunks * T);
         fin.add(p, T);
         comb.add(p, comb_items);
-        dyn[b.cls].add(p, b.mvm_items);
-        dyn[kBatchClasses].add(p, (int64_t)pl.nchunks * T);
+        for (int l = 0; l < kBatchDynLists; ++l) b.list_items[l] = 0;
+        if (tc) {
+            b.list_items[probs[p].kern.type] = (int)(pl.Npad / kTcBM) * pl.tcp.nsplit;
+            b.list_items[kListTcSplit] = (int)((pl.Npad / 8 * TP + 255) / 256);
+        } else {
+            b.list_items[b.cls] = b.mvm_items;
+        }
+        b.list_items[kBatchClasses] = pl.nchunks * T;
+        for (int l = 0; l < kBatchDynLists; ++l)
+            if (b.list_items[l] > 0) dyn[l].add(p, b.list_items[l]);
         if (given[p]) {
             given_one.add(p, 1);
         } else {
@@ -695,7 +711,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
             if (v >= (int64_t)INT32_MAX) return CIQ_ERR_UNSUPPORTED;
     }
     (void)biggest;
-    std::vector<HostList*> all_lists = {&prep, &one, &init, &pre, &pre_one, &given_one, &fin, &comb};
+    std::vector<HostList*> all_lists = {&prep, &one, &init, &pre, &pre_one, &given_one, &fin, &comb, &rows256};
     for (auto& l : pre_mvm) all_lists.push_back(&l);
     for (auto& l : dyn) all_lists.push_back(&l);
     const size_t list_ints = (size_t)2 * P + 2;
@@ -769,6 +785,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                 r.beta = pl.bpar ? pl.bpar + par : nullptr;
                 b.pre[par] = r;
             }
+            b.tcp = pl.tcp;
             b.X = probs[p].X;
             b.B = probs[p].B;
             b.out = probs[p].out;
@@ -787,6 +804,11 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
             return launch_batched_setup(probs_d, phase, o.seed, Q, L(h), h.total(), st);
         };
         CIQ_TRY(setup(kBatchPrepare, prep));
+        if (tc) {
+            CIQ_TRY(launch_batched_tc_mean(probs_d, L(one), one.total(), st));
+            CIQ_TRY(launch_batched_tc_points(probs_d, L(rows256), rows256.total(), half, st));
+            launches += 2;
+        }
         CIQ_TRY(setup(kBatchReset, one));
         CIQ_TRY(setup(kBatchInitRhs, init));
         CIQ_TRY(setup(kBatchInitState, init));
@@ -816,10 +838,23 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
             for (int j = 1; j <= o.max_iter;) {
                 const int jb = std::min(j + o.check_every - 1, o.max_iter);
                 for (int jj = j; jj <= jb; ++jj) {
-                    for (int c = 0; c < kBatchClasses; ++c) {
-                        if (grid[c] == 0) continue;
-                        CIQ_TRY(launch_batched_mvm(probs_d, c, T, false, jj & 1, dyn_d.l[c], grid[c], st));
-                        ++launches;
+                    if (tc) {
+                        if (grid[kListTcSplit] > 0) {
+                            CIQ_TRY(launch_batched_tc_split(probs_d, jj & 1, dyn_d.l[kListTcSplit], grid[kListTcSplit],
+                                                            half, st));
+                            ++launches;
+                        }
+                        for (int kt = 0; kt < 2; ++kt) {
+                            if (grid[kt] == 0) continue;
+                            CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, TP, half, jj & 1, dyn_d.l[kt], grid[kt], st));
+                            ++launches;
+                        }
+                    } else {
+                        for (int c = 0; c < kBatchClasses; ++c) {
+                            if (grid[c] == 0) continue;
+                            CIQ_TRY(launch_batched_mvm(probs_d, c, T, false, jj & 1, dyn_d.l[c], grid[c], st));
+                            ++launches;
+                        }
                     }
                     CIQ_TRY(launch_batched_step(probs_d, jj, false, dyn_d.l[kBatchClasses], grid[kBatchClasses], st));
                     ++launches;

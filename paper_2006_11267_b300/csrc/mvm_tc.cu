@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "batched.cuh"
 #include "mvm_tc.cuh"
 #include "tc_ptx.cuh"
 
@@ -73,24 +74,38 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
 }
 
 // ---------------------------------------------------------- operand prep --
-__global__ void tc_mean_kernel(const float* Xp, int64_t N, int dp, double* mean) {
+// Centre of the points, one block of 256 threads, in a fixed summation order
+// (so the operands, and every result, are reproducible bit for bit).
+__device__ __forceinline__ void tc_mean_body(const float* Xp, int64_t N, int dp, double* mean) {
+    __shared__ double red[8][kMaxDimPad];
     double acc[kMaxDimPad];
 #pragma unroll
     for (int k = 0; k < kMaxDimPad; ++k) acc[k] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = threadIdx.x; i < N; i += 256)
         for (int k = 0; k < dp; ++k) acc[k] += (double)Xp[i * dp + k];
-    for (int k = 0; k < dp; ++k) {
+#pragma unroll
+    for (int k = 0; k < kMaxDimPad; ++k) {
         const double v = warp_sum(acc[k]);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&mean[k], v / (double)N);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
     }
+    __syncthreads();
+    if (threadIdx.x < kMaxDimPad) {
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += red[w][threadIdx.x];
+        mean[threadIdx.x] = threadIdx.x < dp ? sum / (double)N : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) tc_mean_kernel(const float* Xp, int64_t N, int dp, double* mean) {
+    tc_mean_body(Xp, N, dp, mean);
 }
 
 // One thread per row: u, v augmented and split, written in the operand layout
 // [row/8][chunk 0..2][K-core 0..1][row%8][element%8] (16-bit elements).
 template <bool HALF>
-__global__ void tc_points_kernel(const float* Xp, int64_t N, int64_t Npad, int dp, int d, float c,
-                                 float c2half, const double* mean, uint8_t* ua, uint8_t* ub) {
-    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void tc_points_body(const float* Xp, int64_t N, int64_t Npad, int dp, int d, float c,
+                                               float c2half, const double* mean, uint8_t* ua, uint8_t* ub,
+                                               int64_t row) {
     if (row >= Npad) return;
     float u[16], v[16];
 #pragma unroll
@@ -134,6 +149,12 @@ __global__ void tc_points_kernel(const float* Xp, int64_t N, int64_t Npad, int d
     }
 }
 
+template <bool HALF>
+__global__ void tc_points_kernel(const float* Xp, int64_t N, int64_t Npad, int dp, int d, float c,
+                                 float c2half, const double* mean, uint8_t* ua, uint8_t* ub) {
+    tc_points_body<HALF>(Xp, N, Npad, dp, d, c, c2half, mean, ua, ub, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Power-of-two scale per column so the scaled entries sit near 1.
 __global__ void tc_vscale_kernel(const float* V, int64_t ldv, int64_t N, int T, int TP, float unit_scale,
                                  int unit, float* vscale) {
@@ -166,10 +187,9 @@ __global__ void tc_vscale_kernel(const float* V, int64_t ldv, int64_t N, int T, 
 // B-operand layout.  Columns come in launch groups of tpg; group g holds
 // [tile][part][col/8][K-core][col%8][row%8] at vblk + g * (Npad/64) * 2 tpg 128.
 template <bool HALF>
-__global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
-                                  const float* vscale, uint8_t* vblk) {
+__device__ __forceinline__ void tc_split_v_body(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
+                                                const float* vscale, uint8_t* vblk, int64_t idx) {
     const int64_t groups = Npad / 8;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= groups * TP) return;
     const int c = (int)(idx / groups);
     const int64_t j0 = (idx % groups) * 8;
@@ -194,6 +214,12 @@ __global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, in
     const int64_t off = (int64_t)(cl >> 3) * 1024 + (jj >> 3) * 128 + (cl & 7) * 16;
     *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(base + (int64_t)tpg * 128 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <bool HALF>
+__global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
+                                  const float* vscale, uint8_t* vblk) {
+    tc_split_v_body<HALF>(V, ldv, T, TP, tpg, Npad, vscale, vblk, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // The kernel walks K's columns in steps of kTcKN = 128 (two 64-row operand
@@ -283,7 +309,8 @@ __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi
 // row tile to arrive (atomic count) adds the S partials in split order --
 // the result does not depend on which CTA is last -- and runs the epilogue.
 template <int KT, int TP, bool HALF>
-__global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
+__device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile,
+                                            int split) {
     if (a.stop && *a.stop) return;
     constexpr int NX = kTcXStages;
     constexpr int NV = tc_vstages<TP>();
@@ -301,8 +328,6 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = p.nsplit;
-    const int64_t tile = blockIdx.x / S;
-    const int split = blockIdx.x % S;
     const int64_t i0 = tile * kTcBM;
     const int ntot = (int)(a.Npad / kTcKN);
     const int st0 = (int)((int64_t)split * ntot / S);
@@ -653,6 +678,68 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
 }
 
 template <int KT, int TP, bool HALF>
+__global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
+    mvm_tc_body<KT, TP, HALF>(p, a, c0, blockIdx.x / p.nsplit, blockIdx.x % p.nsplit);
+}
+
+// ------------------------------------------------------ batched problems --
+// Block b takes item b of a work list of (problem, row tile x split); the
+// problem's operands and MVM arguments are copied to shared memory and the
+// same body runs as for one problem.
+template <int KT, int TP, bool HALF>
+__global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProblem* probs, DevList L, int parity) {
+    int pb, local;
+    if (!list_item(L, blockIdx.x, pb, local)) return;
+    __shared__ TcPoints sp;
+    __shared__ MvmArgs<float> sa;
+    if (threadIdx.x == 0) {
+        sp = probs[pb].tcp;
+        sa = probs[pb].mvm[parity];
+    }
+    __syncthreads();
+    mvm_tc_body<KT, TP, HALF>(sp, sa, 0, local / sp.nsplit, local % sp.nsplit);
+}
+
+// One block per problem: centre of the points, unit V scales, cleared
+// error flag and split-K counters.
+__global__ void __launch_bounds__(256) batched_tc_mean_kernel(const BatchProblem* probs, DevList L) {
+    int pb, local;
+    if (!list_item(L, blockIdx.x, pb, local)) return;
+    const BatchProblem& bp = probs[pb];
+    const TcPoints& tp = bp.tcp;
+    const MvmArgs<float>& m = bp.mvm[0];
+    tc_mean_body(m.X, m.N, m.dp, tp.mean);
+    const float unit_scale = ldexpf(1.f, (int)floor(0.5 * log2((double)m.N)));
+    for (int c = threadIdx.x; c < tp.TP; c += 256) tp.vscale[c] = unit_scale;
+    if (tp.nsplit > 1)
+        for (int64_t k = threadIdx.x; k < tp.Npad / kTcBM; k += 256) tp.cnt[k] = 0;
+    if (threadIdx.x == 0) *tp.err = 0;
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(256) batched_tc_points_kernel(const BatchProblem* probs, DevList L) {
+    int pb, local;
+    if (!list_item(L, blockIdx.x, pb, local)) return;
+    const BatchProblem& bp = probs[pb];
+    const MvmArgs<float>& m = bp.mvm[0];
+    const double c2 = m.kt == CIQ_RBF ? kLog2e : 1.0;
+    tc_points_body<HALF>(m.X, m.N, m.Npad, m.dp, bp.d, (float)sqrt(c2), (float)(0.5 * c2), bp.tcp.mean, bp.tcp.ua,
+                         bp.tcp.ub, (int64_t)local * 256 + threadIdx.x);
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(256) batched_tc_split_kernel(const BatchProblem* probs, DevList L, int parity) {
+    int pb, local;
+    if (!list_item(L, blockIdx.x, pb, local)) return;
+    const BatchProblem& bp = probs[pb];
+    const MvmArgs<float>& m = bp.mvm[parity];
+    if (m.stop && *m.stop) return;
+    const TcPoints& tp = bp.tcp;
+    tc_split_v_body<HALF>(m.V, m.ldv, m.T, tp.TP, tp.TP, tp.Npad, tp.vscale, tp.vblk,
+                          (int64_t)local * 256 + threadIdx.x);
+}
+
+template <int KT, int TP, bool HALF>
 cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaStream_t st) {
     constexpr int smem = tc_smem_bytes<TP>();
     static bool configured = false;
@@ -763,7 +850,7 @@ cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int
     if ((e = cudaMemsetAsync(p.err, 0, sizeof(int), st)) != cudaSuccess) return e;
     if (p.nsplit > 1 && (e = cudaMemsetAsync(p.cnt, 0, sizeof(int) * (size_t)(p.Npad / kTcBM), st)) != cudaSuccess)
         return e;
-    tc_mean_kernel<<<148, 256, 0, st>>>(Xp, N, dp, p.mean);
+    tc_mean_kernel<<<1, 256, 0, st>>>(Xp, N, dp, p.mean);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const double c2 = kt == CIQ_RBF ? kLog2e : 1.0;
     const unsigned blocks = (unsigned)((p.Npad + 127) / 128);
@@ -805,6 +892,60 @@ cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_
                        : launch_kt_half<CIQ_MATERN52, false>(pg, a, tpg, c0, st);
     }
     return e;
+}
+
+cudaError_t launch_batched_tc_mean(const BatchProblem* probs, DevList one, int blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    batched_tc_mean_kernel<<<blocks, 256, 0, st>>>(probs, one);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_tc_points(const BatchProblem* probs, DevList rows256, int blocks, bool half,
+                                     cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (half) batched_tc_points_kernel<true><<<blocks, 256, 0, st>>>(probs, rows256);
+    else batched_tc_points_kernel<false><<<blocks, 256, 0, st>>>(probs, rows256);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevList L, int blocks, bool half,
+                                    cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (half) batched_tc_split_kernel<true><<<blocks, 256, 0, st>>>(probs, L, parity);
+    else batched_tc_split_kernel<false><<<blocks, 256, 0, st>>>(probs, L, parity);
+    return cudaGetLastError();
+}
+
+namespace {
+template <int KT, int TP, bool HALF>
+cudaError_t launch_btc(const BatchProblem* probs, int parity, DevList L, int blocks, cudaStream_t st) {
+    constexpr int smem = tc_smem_bytes<TP>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(batched_tc_mvm_kernel<KT, TP, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    batched_tc_mvm_kernel<KT, TP, HALF><<<blocks, 384, smem, st>>>(probs, L, parity);
+    return cudaGetLastError();
+}
+template <int KT, bool HALF>
+cudaError_t launch_btc_tp(const BatchProblem* probs, int TP, int parity, DevList L, int blocks, cudaStream_t st) {
+    return TP == 32 ? launch_btc<KT, 32, HALF>(probs, parity, L, blocks, st)
+                    : launch_btc<KT, 64, HALF>(probs, parity, L, blocks, st);
+}
+}  // namespace
+
+cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, DevList L,
+                                  int blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (TP != 32 && TP != 64) return cudaErrorInvalidValue;
+    if (kt == CIQ_RBF)
+        return half ? launch_btc_tp<CIQ_RBF, true>(probs, TP, parity, L, blocks, st)
+                    : launch_btc_tp<CIQ_RBF, false>(probs, TP, parity, L, blocks, st);
+    return half ? launch_btc_tp<CIQ_MATERN52, true>(probs, TP, parity, L, blocks, st)
+                : launch_btc_tp<CIQ_MATERN52, false>(probs, TP, parity, L, blocks, st);
 }
 
 }  // namespace ciq

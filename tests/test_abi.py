@@ -105,7 +105,10 @@ def test_batched_validates_before_the_device():
     k = P.Kernel("rbf", 0.5, 1.0, 1e-2)
     good = dict(X=X, B=B, kernel=k)
     cases = [
-        ([good], dict(precision="fp16"), _ciq.CIQ_ERR_UNSUPPORTED),                # tensor-core tiles
+        ([dict(X=np.zeros((10, 15), np.float32), B=B, kernel=k)], dict(precision="fp16"),
+         _ciq.CIQ_ERR_UNSUPPORTED),                                                # tensor-core tiles need d <= 14
+        ([dict(X=X, B=np.zeros((65, 10), np.float32), kernel=k)], dict(precision="fp16"),
+         _ciq.CIQ_ERR_UNSUPPORTED),                                                # ... and T <= 64
         ([good], dict(mvm="stored"), _ciq.CIQ_ERR_UNSUPPORTED),
         ([good], dict(sqrt_form="mvm"), _ciq.CIQ_ERR_UNSUPPORTED),
         ([good], dict(max_iter=0), _ciq.CIQ_ERR_ARG),

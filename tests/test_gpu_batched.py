@@ -153,3 +153,26 @@ def test_batched_check_every_does_not_change_results():
         assert torch.equal(x, y)
         assert p["iters"] == q["iters"]
     assert ia[0]["launches"] != ib[0]["launches"]
+
+
+@pytest.mark.parametrize("prec,t", [("fp16", 8), ("bf16", 8), ("fp16", 40)])
+def test_tensor_core_batch_equals_single_tensor_core_calls(prec, t):
+    probs = recipe_problems(34, 7, t=t)
+    probs.append(hand_problem(1, 3, t, 9, "rbf", 0.5, 1e-2))
+    probs.append(hand_problem(300, 14, t, 10, "matern52", 0.8, 1e-2))
+    outs, infos = batched("sqrt", probs, 8, 1e-4, max_iter=600, precision=prec)
+    for pr, out, info in zip(probs, outs, infos):
+        ref, rinfo = single("sqrt", pr, 8, 1e-4, max_iter=600, precision=prec)
+        assert torch.equal(out, ref), (pr["X"].shape, pr["kernel"])
+        assert info["iters"] == rinfo["iters"]
+
+
+def test_tensor_core_batch_limits():
+    too_wide = [hand_problem(200, 15, 4, 1, "rbf", 0.5, 1e-2)]
+    with pytest.raises(P.CiqError) as e:
+        batched("sqrt", too_wide, 8, 1e-4, precision="fp16")
+    assert e.value.status == P._ciq.CIQ_ERR_UNSUPPORTED
+    many = [hand_problem(200, 3, 65, 1, "rbf", 0.5, 1e-2)]
+    with pytest.raises(P.CiqError) as e:
+        batched("sqrt", many, 8, 1e-4, precision="fp16")
+    assert e.value.status == P._ciq.CIQ_ERR_UNSUPPORTED
