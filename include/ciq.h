@@ -122,6 +122,8 @@ typedef struct {
     const double* quad_t;     /* optional Q shifts (host) */
     void* workspace;          /* optional device workspace of workspace_bytes */
     size_t workspace_bytes;
+    int graph;                /* batched solves: capture each batch of check_every iterations as a
+                                 CUDA graph and launch it as one (default 1); single solves ignore it */
 } ciq_options;
 
 typedef struct {

@@ -112,6 +112,8 @@ cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevLi
                                     cudaStream_t st);
 cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, DevList L,
                                   int blocks, cudaStream_t st);
+// Set the kernels' shared-memory attributes (before any stream capture).
+cudaError_t prepare_batched_tc_mvm(int TP, bool half);
 
 // Rebuild the kBatchDynLists main-loop lists over problems whose columns
 // have not all stopped; totals[l] = the new item total of list l.

@@ -593,6 +593,16 @@ struct HostList {
     int total() const { return prefix.back(); }
 };
 
+// Stream used only to record batched iteration graphs, one per host thread.
+cudaStream_t capture_stream() {
+    thread_local cudaStream_t cs = nullptr;
+    if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cs = nullptr;
+    }
+    return cs;
+}
+
 // Pinned host words for the list totals (two slots), one set per host thread.
 int* pinned_totals() {
     thread_local int* p = nullptr;
@@ -726,6 +736,8 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     std::vector<double> packed((size_t)kSummaryStride * P, 0.0);
     std::vector<int> list_img(list_ints * all_lists.size(), 0);
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec = nullptr;
+    bool capturing = false;
     {
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), off + tables, st);
         if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
@@ -835,33 +847,64 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         {
             int slot = 0;
             bool pending[2] = {false, false};
+            if (tc) CIQ_TRY(prepare_batched_tc_mvm(TP, half));   // kernel attributes, outside any capture
             for (int j = 1; j <= o.max_iter;) {
                 const int jb = std::min(j + o.check_every - 1, o.max_iter);
+                // One batch of iterations (and the list rebuild): captured as a
+                // graph and launched as one when o.graph, else launched directly.
+                // The graph keeps its instantiation while only kernel
+                // parameters and grid sizes change between batches.
+                // Captured on a private stream (capture is not allowed on the
+                // legacy default stream); the graph is launched on `st`.
+                cudaStream_t ls = st;
+                if (o.graph) {
+                    ls = capture_stream();
+                    if (!ls) { rc = CIQ_ERR_CUDA; goto done; }
+                    CIQ_TRY(cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal));
+                    capturing = true;
+                }
                 for (int jj = j; jj <= jb; ++jj) {
                     if (tc) {
                         if (grid[kListTcSplit] > 0) {
                             CIQ_TRY(launch_batched_tc_split(probs_d, jj & 1, dyn_d.l[kListTcSplit], grid[kListTcSplit],
-                                                            half, st));
+                                                            half, ls));
                             ++launches;
                         }
                         for (int kt = 0; kt < 2; ++kt) {
                             if (grid[kt] == 0) continue;
-                            CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, TP, half, jj & 1, dyn_d.l[kt], grid[kt], st));
+                            CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, TP, half, jj & 1, dyn_d.l[kt], grid[kt], ls));
                             ++launches;
                         }
                     } else {
                         for (int c = 0; c < kBatchClasses; ++c) {
                             if (grid[c] == 0) continue;
-                            CIQ_TRY(launch_batched_mvm(probs_d, c, T, false, jj & 1, dyn_d.l[c], grid[c], st));
+                            CIQ_TRY(launch_batched_mvm(probs_d, c, T, false, jj & 1, dyn_d.l[c], grid[c], ls));
                             ++launches;
                         }
                     }
-                    CIQ_TRY(launch_batched_step(probs_d, jj, false, dyn_d.l[kBatchClasses], grid[kBatchClasses], st));
+                    CIQ_TRY(launch_batched_step(probs_d, jj, false, dyn_d.l[kBatchClasses], grid[kBatchClasses], ls));
                     ++launches;
                 }
                 last_j = jb;
-                CIQ_TRY(launch_rebuild_lists(probs_d, P, dyn_d, totals_d, st));
+                CIQ_TRY(launch_rebuild_lists(probs_d, P, dyn_d, totals_d, ls));
                 ++launches;
+                if (o.graph) {
+                    cudaGraph_t g = nullptr;
+                    capturing = false;
+                    CIQ_TRY(cudaStreamEndCapture(ls, &g));
+                    if (gexec) {
+                        cudaGraphExecUpdateResultInfo ui;
+                        if (cudaGraphExecUpdate(gexec, g, &ui) != cudaSuccess) {
+                            cudaGetLastError();
+                            cudaGraphExecDestroy(gexec);
+                            gexec = nullptr;
+                        }
+                    }
+                    cudaError_t ge = gexec ? cudaSuccess : cudaGraphInstantiate(&gexec, g, 0);
+                    cudaGraphDestroy(g);
+                    CIQ_TRY(ge);
+                    CIQ_TRY(cudaGraphLaunch(gexec, st));
+                }
                 CIQ_TRY(cudaMemcpyAsync(tot_h + slot * kBatchDynLists, totals_d, sizeof(int) * kBatchDynLists,
                                         cudaMemcpyDeviceToHost, st));
                 CIQ_TRY(cudaEventRecord(ev[slot], st));
@@ -888,6 +931,13 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         CIQ_TRY(cudaStreamSynchronize(st));
     }
 done:
+    if (capturing) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(capture_stream(), &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
     if (ev[0]) cudaEventDestroy(ev[0]);
     if (ev[1]) cudaEventDestroy(ev[1]);
     cudaFreeAsync(base, st);
@@ -1055,6 +1105,7 @@ void ciq_default_options(ciq_options* opt) {
     opt->seed = 0x5eed;
     opt->lmax_margin = 1.05;
     opt->lmin_div = 100.0;
+    opt->graph = 1;
 }
 
 ciq_status ciq_quad_nodes(double lmin, double lmax, int Q, double* w, double* t) {

@@ -918,17 +918,30 @@ cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevLi
 
 namespace {
 template <int KT, int TP, bool HALF>
-cudaError_t launch_btc(const BatchProblem* probs, int parity, DevList L, int blocks, cudaStream_t st) {
-    constexpr int smem = tc_smem_bytes<TP>();
+cudaError_t configure_btc() {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(batched_tc_mvm_kernel<KT, TP, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(batched_tc_mvm_kernel<KT, TP, HALF>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<TP>());
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    batched_tc_mvm_kernel<KT, TP, HALF><<<blocks, 384, smem, st>>>(probs, L, parity);
+    return cudaSuccess;
+}
+
+template <int KT, int TP, bool HALF>
+cudaError_t launch_btc(const BatchProblem* probs, int parity, DevList L, int blocks, cudaStream_t st) {
+    cudaError_t e = configure_btc<KT, TP, HALF>();
+    if (e != cudaSuccess) return e;
+    batched_tc_mvm_kernel<KT, TP, HALF><<<blocks, 384, tc_smem_bytes<TP>(), st>>>(probs, L, parity);
     return cudaGetLastError();
+}
+
+template <bool HALF>
+cudaError_t configure_btc_all(int TP) {
+    cudaError_t e = TP == 32 ? configure_btc<CIQ_RBF, 32, HALF>() : configure_btc<CIQ_RBF, 64, HALF>();
+    if (e != cudaSuccess) return e;
+    return TP == 32 ? configure_btc<CIQ_MATERN52, 32, HALF>() : configure_btc<CIQ_MATERN52, 64, HALF>();
 }
 template <int KT, bool HALF>
 cudaError_t launch_btc_tp(const BatchProblem* probs, int TP, int parity, DevList L, int blocks, cudaStream_t st) {
@@ -936,6 +949,11 @@ cudaError_t launch_btc_tp(const BatchProblem* probs, int TP, int parity, DevList
                     : launch_btc<KT, 64, HALF>(probs, parity, L, blocks, st);
 }
 }  // namespace
+
+cudaError_t prepare_batched_tc_mvm(int TP, bool half) {
+    if (TP != 32 && TP != 64) return cudaErrorInvalidValue;
+    return half ? configure_btc_all<true>(TP) : configure_btc_all<false>(TP);
+}
 
 cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, DevList L,
                                   int blocks, cudaStream_t st) {
