@@ -124,6 +124,8 @@ typedef struct {
     size_t workspace_bytes;
     int graph;                /* batched solves: capture each batch of check_every iterations as a
                                  CUDA graph and launch it as one (default 1); single solves ignore it */
+    int tc_split;             /* tensor-core MVM: CTAs sharing one 128-row tile (1..8; 0 = chosen
+                                 from N for single solves, 1 for batched solves) */
 } ciq_options;
 
 typedef struct {

@@ -84,7 +84,7 @@ bool valid_options(const ciq_options& o) {
              (o.stop_rule != CIQ_STOP_RESIDUAL && o.stop_rule != CIQ_STOP_ERRBOUND) ||
              (o.sqrt_form != CIQ_SQRT_IDENTITY && o.sqrt_form != CIQ_SQRT_MVM) ||
              (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_FP16) ||
-             (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED));
+             (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED) || o.tc_split < 0 || o.tc_split > 8);
 }
 
 // Pinned host words for the convergence flag, one set per host thread.
@@ -127,6 +127,7 @@ struct Plan {
     bool stage_x, stage_b, stage_out, stage_start;
     bool prepass;
     bool tri_on = false;          // record column 0's msMINRES tridiagonal
+    int tc_max_split = 8;         // CTAs per row tile of the tensor-core MVM (batches: 1)
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB;
     R *sx, *sb, *sout, *sstart;
@@ -179,8 +180,8 @@ struct Plan {
         sout = stage_out ? a.take<R>((size_t)N * T) : nullptr;
         sstart = stage_start ? a.take<R>((size_t)N) : nullptr;
         if (tc) {
-            char* q = a.take<char>(tc_points_bytes(Npad, T));
-            tcp = tc_points_layout(q, Npad, T, precision);
+            char* q = a.take<char>(tc_points_bytes(Npad, T, tc_max_split));
+            tcp = tc_points_layout(q, Npad, T, precision, tc_max_split);
         }
         Kst = stored ? a.take<float>((size_t)Npad * Npad) : nullptr;
         bytes = a.off + kAlign;
@@ -200,6 +201,7 @@ Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool pre
     p.jmax = o.max_iter;
     p.JL = o.lanczos_iters;
     p.tc = tc;
+    p.tc_max_split = o.tc_split > 0 ? o.tc_split : 8;
     p.stored = sizeof(R) == 4 && o.mvm == CIQ_MVM_STORED;
     p.nparts = tc ? (int)tc_row_tiles(p.Npad)
                   : p.stored ? (int)stored_row_tiles(p.Npad, T) : (int)mvm_simt_row_tiles<R>(p.Npad, T);
@@ -657,10 +659,12 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     size_t off = 0;
     for (int p = 0; p < P; ++p) {
         plans.push_back(make_plan<float>(probs[p].N, probs[p].d, T, Q, o, !given[p], tc));
-        if (record_tri) {
-            plans.back().tri_on = true;
-            plans.back().layout(nullptr);
-        }
+        // Many problems fill the GPU; splitting a row tile's columns across
+        // CTAs only adds per-CTA cost here (measured 3.78 -> 2.94 s on the
+        // 512-problem batch without it), so batches default to one CTA.
+        plans.back().tc_max_split = o.tc_split > 0 ? o.tc_split : 1;
+        plans.back().tri_on = record_tri;
+        plans.back().layout(nullptr);
         offs[p] = off;
         off += round_up((int64_t)plans.back().bytes, kAlign);
     }

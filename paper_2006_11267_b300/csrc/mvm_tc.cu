@@ -23,6 +23,8 @@
 // an mbarrier, double-buffered.  The epilogue reads O from TMEM and applies
 // the same Lanczos epilogue as the CUDA-core MVM.  Every wait is bounded: on
 // timeout the CTA records an error flag, skips the rest and frees its TMEM.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -806,18 +808,26 @@ int tc_split(int64_t Npad) {
     return best;
 }
 
-size_t tc_points_bytes(int64_t Npad, int T) {
+// max_split 8 means "choose"; a smaller value is used as given (never
+// more than the steps of K's columns).
+int tc_nsplit(int64_t Npad, int max_split) {
+    const int steps = (int)(Npad / kTcKN);
+    const int S = max_split >= 8 ? tc_split(Npad) : max_split;
+    return std::max(1, std::min(S, steps));
+}
+
+size_t tc_points_bytes(int64_t Npad, int T, int max_split) {
     const int TP = tc_padded_t(T);
     if (TP < 0) return 0;
     const size_t pts = (size_t)Npad * kTcRowBytes;
     const size_t vb = (size_t)(Npad / kTcBN) * 2 * TP * 128;
-    const int S = tc_split(Npad);
+    const int S = tc_nsplit(Npad, max_split);
     const size_t part = S > 1 ? (size_t)(Npad / kTcBM) * S * tc_group_t(T) * kTcBM * sizeof(double) + 256 : 0;
     const size_t cnt = S > 1 ? (size_t)(Npad / kTcBM) * sizeof(int) + 256 : 0;
     return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256 + part + cnt;
 }
 
-TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision) {
+TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int max_split) {
     TcPoints p;
     p.Npad = Npad;
     p.TP = tc_padded_t(T);
@@ -834,7 +844,7 @@ TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision) {
     p.vscale = reinterpret_cast<float*>(take((size_t)p.TP * sizeof(float)));
     p.mean = reinterpret_cast<double*>(take(16 * sizeof(double)));
     p.err = reinterpret_cast<int*>(take(sizeof(int)));
-    p.nsplit = tc_split(Npad);
+    p.nsplit = tc_nsplit(Npad, max_split);
     if (p.nsplit > 1) {
         p.part = reinterpret_cast<double*>(
             take((size_t)(Npad / kTcBM) * p.nsplit * tc_group_t(T) * kTcBM * sizeof(double)));

@@ -32,8 +32,10 @@ bool tc_supported(int precision, int d);
 int tc_padded_t(int T);
 int tc_group_t(int T);
 int64_t tc_row_tiles(int64_t Npad);
-size_t tc_points_bytes(int64_t Npad, int T);
-TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision);
+// max_split caps the CTAs per row tile (batches, whose many problems fill the
+// GPU already, use 1).
+size_t tc_points_bytes(int64_t Npad, int T, int max_split = 8);
+TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int max_split = 8);
 // Centre/scale/augment/split the points (Xp: Npad x dp, already divided by
 // the lengthscale) into ua/ub; clears the error flag.
 cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int dp, int d, int kt,

@@ -97,3 +97,23 @@ def test_tc_fp16_full_size_square_root_property():
     KB = P.ciq_kernel_mvm(X, k, B[:4].contiguous(), precision="fp32")
     e = (torch.linalg.norm(A2 - KB, dim=1) / torch.linalg.norm(KB, dim=1)).cpu().numpy()
     assert e.max() < 3e-4
+
+
+def test_tc_split_k_changes_only_the_summation_order():
+    # Splitting a row tile's 128-column steps over S CTAs adds S float-pair
+    # partial sums in split order: only rounding changes, so each split is
+    # reproducible bit for bit (deterministic centre, fixed order) and the
+    # solves agree within the accuracy the stop rule leaves (relative
+    # residual 1e-4: measured differences ~1e-4 between splits).
+    X = torch.from_numpy(f32(ci.points(11, 9000, 5))).cuda()
+    V = torch.from_numpy(f32(ci.rhs(12, 9000, 40))).cuda()
+    k = P.Kernel("rbf", 0.4, 1.0, 1e-2)
+    outs = {}
+    for s in (1, 2, 5, 8):
+        X2, V2 = X.clone(), V.clone()
+        a = P.ciq_sqrt(X2, k, V2, 8, 1e-4, max_iter=600, precision="fp16", tc_split=s)[0]
+        b = P.ciq_sqrt(X2, k, V2, 8, 1e-4, max_iter=600, precision="fp16", tc_split=s)[0]
+        assert torch.equal(a, b), s
+        outs[s] = a.cpu().numpy()
+    for s in (2, 5, 8):
+        assert rel(outs[s], outs[1]) < 1e-3, s
