@@ -73,9 +73,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
-    ap.add_argument("--workload", default="thompson50k", choices=["thompson50k", "batched512", "precision200k"],
+    ap.add_argument("--workload", default="thompson50k", choices=["thompson50k", "batched512", "precision200k", "learned"],
                     help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
-                         "the 200,000-point Matern precision sweep")
+                         "the 200,000-point Matern precision sweep; learned: train the bound predictor on "
+                         "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
                     help="time only the kernel MVM on the first N points of the workload (for profiling)")
     return ap.parse_args()
@@ -440,10 +441,11 @@ def run_batched(args):
     for pr in probs:
         pr["out"] = torch.empty_like(pr["B"])
     opts = dict(max_iter=BATCH_MAX_ITER, lanczos_iters=LANCZOS_ITERS, check_every=8)
+    bopts = dict(opts, precision=args.precision)
     stream = torch.cuda.current_stream()
 
     def step():
-        return P.ciq_sqrt_batched(probs, BATCH_Q, BATCH_TOL, **opts)[1]
+        return P.ciq_sqrt_batched(probs, BATCH_Q, BATCH_TOL, **bopts)[1]
 
     for _ in range(args.warmup):
         infos = step()
@@ -467,13 +469,28 @@ def run_batched(args):
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    same = 0
+    refs = []
     for pr in probs:
         o, _ = P.ciq_sqrt(pr["X"], pr["kernel"], pr["B"], BATCH_Q, BATCH_TOL, **opts)
-        same += int(torch.equal(o, pr["out"]))
+        refs.append(o)
     f1.record(stream)
     torch.cuda.synchronize()
     t_seq = f0.elapsed_time(f1)
+    same = sum(int(torch.equal(o, pr["out"])) for o, pr in zip(refs, probs))
+    diffs = [float(torch.linalg.norm((o - pr["out"]).double()) / torch.linalg.norm(o.double())) for o, pr in
+             zip(refs, probs)]
+    # The batched form with CUDA-core FP32 tiles, for context.
+    b32 = None
+    if args.precision != "fp32":
+        P.ciq_sqrt_batched(probs, BATCH_Q, BATCH_TOL, **opts)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        P.ciq_sqrt_batched(probs, BATCH_Q, BATCH_TOL, **opts)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        b32 = {"value": BATCH_COUNT * BATCH_T / (g0.elapsed_time(g1) * 1e-3), "ms_per_step": g0.elapsed_time(g1)}
     # End to end: pinned host inputs in, outputs back to the host, each step.
     outs_h = [torch.empty_like(h["B"]).pin_memory() for h in host]
     t0 = time.perf_counter()
@@ -490,7 +507,9 @@ def run_batched(args):
     line = {"metric": "K^{1/2}b RHS-solves/s, uneven batch (batched vs plain FP32)", "value": value,
             "unit": "RHS-solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else f"{args.precision}x2-split tiles, f32 vectors, f64 scalars",
+            "data": "synthetic",
             "config": {"workload": f"batched{BATCH_COUNT}_uneven_t{BATCH_T}_q{BATCH_Q}", "problems": BATCH_COUNT,
                        "T": BATCH_T, "Q": BATCH_Q, "tol": BATCH_TOL, "stop_rule": "residual",
                        "max_iter": BATCH_MAX_ITER, "seed": BATCH_SEED,
@@ -500,7 +519,9 @@ def run_batched(args):
                        "l2": "no flush: each step streams every problem's workspace (> 1 GB)"},
             "plain_fp32_gpu_path": {"value": rhs / (t_seq * 1e-3), "ms_per_step": t_seq,
                                     "speedup": t_seq / (elapsed_ms / args.steps),
-                                    "outputs_bitwise_equal": f"{same}/{BATCH_COUNT}"},
+                                    "outputs_bitwise_equal": f"{same}/{BATCH_COUNT}",
+                                    "max_rel_diff": max(diffs), "median_rel_diff": float(np.median(diffs))},
+            "batched_fp32": b32,
             "e2e": {"value": rhs / t_e2e, "unit": "RHS-solves/s",
                     "h2d_bytes_per_step": int(sum(h["X"].nbytes + h["B"].nbytes for h in host)),
                     "d2h_bytes_per_step": int(sum(o.nbytes for o in outs_h))},
@@ -571,6 +592,108 @@ def run_precision(args):
     return 0
 
 
+def run_learned(args):
+    """Learned spectral bounds on the uneven-batch distribution: labels for
+    20,000 instances from the library's batched solve with its Lanczos
+    pre-pass (FP16 split tiles), GPU training of the predictor, then 4096
+    held-out instances solved with predicted bounds (fallback to the
+    pre-pass on a spectral check) and with the pre-pass, both timed; the
+    oracle judges the 64 smallest held-out problems."""
+    import torch
+
+    import paper_2006_11267_b300 as P
+    from paper_2006_11267_b300 import learned
+    from oracle import eig, kernels
+
+    torch.cuda.set_device(0)
+    prec = args.precision
+    opts = dict(max_iter=BATCH_MAX_ITER, lanczos_iters=LANCZOS_ITERS, check_every=8, precision=prec)
+
+    def device_batch(raw):
+        return [dict(X=torch.from_numpy(p["X"].astype(np.float32)).cuda(),
+                     B=torch.from_numpy(p["B"].astype(np.float32)).cuda(),
+                     kernel=P.Kernel(p["kernel"], p["lengthscale"], p["outputscale"], p["noise"])) for p in raw]
+
+    t0 = time.perf_counter()
+    Fs, Ys = [], []
+    n_train = 20000
+    label_opts = dict(opts, max_iter=1000)        # iteration labels saturate at 1000
+    for b0 in range(0, n_train, BATCH_COUNT):
+        raw = ci.batched_problems(BATCH_SEED + 1000 + b0 // BATCH_COUNT, count=min(BATCH_COUNT, n_train - b0),
+                                  t=BATCH_T)
+        F, Y, _ = learned.label_problems(device_batch(raw), BATCH_Q, BATCH_TOL, **label_opts)
+        Fs.append(F)
+        Ys.append(Y)
+    F = torch.cat(Fs)
+    Y = torch.cat(Ys)
+    t_label = time.perf_counter() - t0
+    n_val = 2000
+    t0 = time.perf_counter()
+    theta, losses = learned.train_predictor(F[n_val:].contiguous(), Y[n_val:].contiguous(), steps=8000, batch=256,
+                                            lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    Fv, Yv = F[:n_val].contiguous(), Y[:n_val].contiguous()
+    margin = learned.lmax_margin_from_validation(theta, Fv, Yv, 0.99)
+    pv = P.ciq_mlp_predict(theta, Fv).cpu().numpy()
+    yv = Yv.cpu().numpy()
+    rmse = np.sqrt(np.mean((pv - yv) ** 2, axis=0)).tolist()
+    # Held-out instances.
+    raw_test = ci.batched_problems(BATCH_SEED + 999, count=4096, t=BATCH_T)
+    res = {"prepass": {"ms": 0.0}, "learned": {"ms": 0.0}}
+    outs_all = {"prepass": [], "learned": []}
+    fallbacks = 0
+    work = {"prepass": 0, "learned": 0}
+    for b0 in range(0, len(raw_test), BATCH_COUNT):
+        probs = device_batch(raw_test[b0:b0 + BATCH_COUNT])
+        for mode in ("prepass", "learned"):
+            for pr in probs:
+                pr["out"] = torch.empty_like(pr["B"])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if mode == "prepass":
+                outs, infos = P.ciq_sqrt_batched(probs, BATCH_Q, BATCH_TOL, **opts)
+            else:
+                outs, infos = P.ciq_sqrt_batched_learned(probs, BATCH_Q, BATCH_TOL, theta, margin, **opts)
+                fallbacks += sum(i["fallback"] for i in infos)
+            e1.record()
+            torch.cuda.synchronize()
+            res[mode]["ms"] += e0.elapsed_time(e1)
+            work[mode] += sum(i["iters"] + i["lanczos_iters"] for i in infos)
+            outs_all[mode] += [o.cpu().numpy() for o in outs]
+    # Oracle errors on the 64 smallest held-out problems.
+    small = sorted(range(len(raw_test)), key=lambda i: raw_test[i]["n"])[:64]
+    errs = {"prepass": [], "learned": []}
+    for i in small:
+        p = raw_test[i]
+        X = p["X"].astype(np.float32).astype(np.float64)
+        K = kernels.dense_K(X, p["kernel"], p["lengthscale"], p["outputscale"], p["noise"])
+        truth = eig.sqrt_apply(K, p["B"].astype(np.float32).astype(np.float64).T).T
+        for mode in errs:
+            errs[mode].append(float(np.linalg.norm(outs_all[mode][i] - truth) / np.linalg.norm(truth)))
+    rhs = len(raw_test) * BATCH_T
+    line = {"metric": "K^{1/2}b RHS-solves/s with learned spectral bounds (vs Lanczos pre-pass)",
+            "value": rhs / (res["learned"]["ms"] * 1e-3), "unit": "RHS-solves/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "higher_is_better": True, "dtype": f"{prec}x2-split tiles, f32 vectors, f64 scalars",
+            "data": "synthetic",
+            "config": {"workload": "learned_bounds_uneven_t8_q8", "train": n_train, "validation": n_val,
+                       "held_out": len(raw_test), "network": "38-64-64-3 tanh, FP32 training, BF16 inference",
+                       "label_max_iter": 1000, "tol": BATCH_TOL, "Q": BATCH_Q},
+            "prepass_pipeline": {"value": rhs / (res["prepass"]["ms"] * 1e-3), "ms": res["prepass"]["ms"],
+                                 "mvm_work": work["prepass"]},
+            "learned_pipeline": {"ms": res["learned"]["ms"], "mvm_work": work["learned"], "fallbacks": fallbacks,
+                                 "margin_log": margin},
+            "gain": res["prepass"]["ms"] / res["learned"]["ms"],
+            "validation_rmse_log": {"theta_min": rmse[0], "theta_max": rmse[1], "iterations": rmse[2]},
+            "oracle_rel_err_64_smallest": {m: {"max": max(v), "median": float(np.median(v))} for m, v in errs.items()},
+            "seconds": {"labels": t_label, "training": t_train},
+            "final_minibatch_loss": float(losses[-200:].mean())}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -579,6 +702,8 @@ def main():
         return run_batched(args)
     if args.workload == "precision200k":
         return run_precision(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 
