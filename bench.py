@@ -634,24 +634,37 @@ def run_learned(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     Fv, Yv = F[:n_val].contiguous(), Y[:n_val].contiguous()
-    margin = learned.lmax_margin_from_validation(theta, Fv, Yv, 0.99)
+    margin = learned.lmax_margin_from_validation(theta, Fv, Yv, 0.999)
     pv = P.ciq_mlp_predict(theta, Fv).cpu().numpy()
     yv = Yv.cpu().numpy()
     rmse = np.sqrt(np.mean((pv - yv) ** 2, axis=0)).tolist()
-    # Held-out instances.
+    # Held-out instances, all resident.  The pre-pass pipeline solves them in
+    # batches of 512 in index order; the learned pipeline predicts every
+    # problem first (its bounds and its iteration count), orders the
+    # problems by predicted iterations so each batch of 512 converges
+    # together (the batch schedule sized ahead of time), and solves each
+    # batch with the predicted bounds.
     raw_test = ci.batched_problems(BATCH_SEED + 999, count=4096, t=BATCH_T)
+    test = device_batch(raw_test)
     res = {"prepass": {"ms": 0.0}, "learned": {"ms": 0.0}}
-    outs_all = {"prepass": [], "learned": []}
+    outs_all = {"prepass": [None] * len(test), "learned": [None] * len(test)}
     fallbacks = 0
     work = {"prepass": 0, "learned": 0}
-    for b0 in range(0, len(raw_test), BATCH_COUNT):
-        probs = device_batch(raw_test[b0:b0 + BATCH_COUNT])
-        for mode in ("prepass", "learned"):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pred = P.ciq_mlp_predict(theta, P.ciq_mlp_features(test))
+    order = torch.argsort(pred[:, 2]).cpu().numpy()
+    e1.record()
+    torch.cuda.synchronize()
+    res["learned"]["ms"] += e0.elapsed_time(e1)
+    for mode, idx in (("prepass", np.arange(len(test))), ("learned", order)):
+        for b0 in range(0, len(test), BATCH_COUNT):
+            ids = idx[b0:b0 + BATCH_COUNT]
+            probs = [test[i] for i in ids]
             for pr in probs:
                 pr["out"] = torch.empty_like(pr["B"])
             torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             if mode == "prepass":
                 outs, infos = P.ciq_sqrt_batched(probs, BATCH_Q, BATCH_TOL, **opts)
@@ -662,7 +675,8 @@ def run_learned(args):
             torch.cuda.synchronize()
             res[mode]["ms"] += e0.elapsed_time(e1)
             work[mode] += sum(i["iters"] + i["lanczos_iters"] for i in infos)
-            outs_all[mode] += [o.cpu().numpy() for o in outs]
+            for i, o in zip(ids, outs):
+                outs_all[mode][i] = o.cpu().numpy()
     # Oracle errors on the 64 smallest held-out problems.
     small = sorted(range(len(raw_test)), key=lambda i: raw_test[i]["n"])[:64]
     errs = {"prepass": [], "learned": []}
