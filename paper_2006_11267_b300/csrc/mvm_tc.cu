@@ -77,24 +77,42 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
 
 // ---------------------------------------------------------- operand prep --
 // Centre of the points, one block of 256 threads, in a fixed summation order
-// (so the operands, and every result, are reproducible bit for bit).
+// (so the operands, and every result, are reproducible bit for bit).  Thread
+// s sums rows s, s + 256, ... as a (leading, trailing) float pair (2Sum;
+// FP64 adds run at a few per clock per SM on this part); the 256 pairs are
+// then combined in a fixed tree and converted to FP64 once.
 __device__ __forceinline__ void tc_mean_body(const float* Xp, int64_t N, int dp, double* mean) {
-    __shared__ double red[8][kMaxDimPad];
-    double acc[kMaxDimPad];
+    __shared__ float red_h[8][kMaxDimPad], red_l[8][kMaxDimPad];
+    float h[kMaxDimPad], l[kMaxDimPad];
 #pragma unroll
-    for (int k = 0; k < kMaxDimPad; ++k) acc[k] = 0.0;
+    for (int k = 0; k < kMaxDimPad; ++k) { h[k] = 0.f; l[k] = 0.f; }
     for (int64_t i = threadIdx.x; i < N; i += 256)
-        for (int k = 0; k < dp; ++k) acc[k] += (double)Xp[i * dp + k];
+#pragma unroll
+        for (int k = 0; k < kMaxDimPad; ++k)
+            if (k < dp) two_sum_into(h[k], l[k], Xp[i * dp + k]);
 #pragma unroll
     for (int k = 0; k < kMaxDimPad; ++k) {
-        const double v = warp_sum(acc[k]);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h[k], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, l[k], o);
+            two_sum_into(h[k], l[k], oh);
+            l[k] += ol;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red_h[threadIdx.x >> 5][k] = h[k];
+            red_l[threadIdx.x >> 5][k] = l[k];
+        }
     }
     __syncthreads();
     if (threadIdx.x < kMaxDimPad) {
-        double sum = 0.0;
-        for (int w = 0; w < 8; ++w) sum += red[w][threadIdx.x];
-        mean[threadIdx.x] = threadIdx.x < dp ? sum / (double)N : 0.0;
+        const int k = threadIdx.x;
+        float sh = 0.f, sl = 0.f;
+        for (int w = 0; w < 8; ++w) {
+            two_sum_into(sh, sl, red_h[w][k]);
+            sl += red_l[w][k];
+        }
+        mean[k] = k < dp ? ((double)sh + (double)sl) / (double)N : 0.0;
     }
 }
 
