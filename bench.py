@@ -77,6 +77,8 @@ def parse():
                     help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
                          "the 200,000-point Matern precision sweep; learned: train the bound predictor on "
                          "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones")
+    ap.add_argument("--n", type=int, default=0, metavar="N",
+                    help="run the headline solve on the first N points only (for profiling captures)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
                     help="time only the kernel MVM on the first N points of the workload (for profiling)")
     return ap.parse_args()
@@ -291,6 +293,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     W = WORKLOAD
+    if args.n:
+        import dataclasses
+        W = dataclasses.replace(W, n=args.n, name=f"{W.name}_first{args.n}")
     seed_shift = rank            # independent replica per rank
     X = np.asarray(ci.points(W.seed + seed_shift, W.n, W.d), dtype=np.float32)
     B = np.asarray(ci.rhs(W.seed + seed_shift, W.n, W.t), dtype=np.float32)
