@@ -295,7 +295,8 @@ enum TcBar {
     kBarODone = 19,        // [8] product of step t complete: S buffer and V stage free, O readable
     kBarPFull = 27,        // [3] P written over S in buffer b by both exp warpgroups
     kBarOFree = 30,        // O accumulator read out for folding, free again
-    kBarCount = 32
+    kBarDrain = 31,        // [2] every MMA of an issuing thread complete (teardown)
+    kBarCount = 33
 };
 
 // Kernel value / outputscale from S = -c^2 r^2 / 2 (RBF: S <= 0 up to
@@ -321,9 +322,10 @@ __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi
 
 // --------------------------------------------------------------- kernel --
 // Warp roles (384 threads): warp 0 lane 0 issues the bulk copies, warp 1
-// lane 0 issues the MMAs, warps 4-7 and 8-11 are two exp warpgroups that
-// split every step's 128 columns between them.  Warps 8-11 also fold each
-// completed chunk of O into the running sum; warps 4-7 run the epilogue.
+// lane 0 the products, warp 2 lane 0 the S MMAs; warps 4-7 and 8-11 are two
+// exp warpgroups that split every step's 128 columns between them and fold
+// each completed chunk of O into the running sum; warps 4-7 run the
+// epilogue.
 // Columns [c0, c0 + TP) of V (those below a.T) are handled.
 //
 // Split K: with p.nsplit = S > 1, CTA b takes row tile b / S and the steps
@@ -371,6 +373,8 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
         }
         for (int b = 0; b < kNB; ++b) tc::mbar_init(&bars[kBarPFull + b], 256);
         tc::mbar_init(&bars[kBarOFree], 256);
+        tc::mbar_init(&bars[kBarDrain], 1);
+        tc::mbar_init(&bars[kBarDrain + 1], 1);
         tc::fence_mbarrier_init();
         *serr = 0;
     }
@@ -403,9 +407,15 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                 tc::bulk_g2s(sX0 + sx * kXStep, p.ub + (int64_t)(st0 + u) * kXStep, kXStep, &bars[kBarXFull + sx]);
                 return true;
             };
-            bool ok = load_x(0) && (nt < 2 || load_x(1));
+            int nx = 0, nv = 0;                           // copies issued
+            bool ok = load_x(0);
+            nx += ok;
+            if (ok && nt > 1) nx += (ok = load_x(1));
             for (int t = 0; ok && t < nt; ++t) {
-                if (t + 2 < nt && !load_x(t + 2)) { ok = false; break; }
+                if (t + 2 < nt) {
+                    if (!load_x(t + 2)) { ok = false; break; }
+                    ++nx;
+                }
                 const int sv = t % NV;
                 if (t >= NV && !tc::mbar_wait(&bars[kBarODone + (t - NV) % kRing], (uint32_t)(((t - NV) / kRing) & 1),
                                               kWaitLimit)) {
@@ -414,67 +424,79 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                 }
                 tc::mbar_expect_tx(&bars[kBarVFull + sv], VSTEP);
                 tc::bulk_g2s(sV0 + sv * VSTEP, vblk + (int64_t)(st0 + t) * VSTEP, VSTEP, &bars[kBarVFull + sv]);
+                ++nv;
                 if (*serr) break;
             }
             if (!ok) *serr = 1;
+            // No copy may land in shared memory after the CTA has left: wait
+            // (bounded) for the last copy issued to every stage.
+            tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
+            for (int u = max(nx - NX, 0); u < nx; ++u)
+                tc::mbar_wait(&bars[kBarXFull + u % NX], (uint32_t)((u / NX) & 1), kWaitLimit);
+            for (int u = max(nv - NV, 0); u < nv; ++u)
+                tc::mbar_wait(&bars[kBarVFull + u % NV], (uint32_t)((u / NV) & 1), kWaitLimit);
         }
         __syncwarp();
-    } else if (warp == 1) {
-        // ------------------------------------------------------ MMA issuer
-        // One thread, fixed order: S(0), S(1); then for each step t,
-        // O += P(t) V(t) once both exp warpgroups have written P(t) and V(t)
-        // is in (and, at the start of a chunk, the accumulator is folded),
-        // then S(t+2) into the buffer of step t - 1.  MMA issue blocks while
-        // the tensor pipe's queue is full, so by the time O(t) is issued the
-        // product of step t - 1 has completed and S(t+2) follows O(t) in the
-        // pipe without a gap.
-        // Descriptors are formed once; per MMA only the start address moves.
+    } else if (warp == 1 || warp == 2) {
+        // ----------------------------------------------------- MMA issuers
+        // Two threads feed the tensor pipe, so neither's barrier waits leave
+        // it idle: warp 2 issues S(h) into buffer h % 3 as soon as the
+        // product of step h - 3 (the buffer's last reader) is complete and
+        // the points are in; warp 1 issues O += P(t) V(t) once both exp
+        // warpgroups have written P(t), V(t) is in and, at the start of a
+        // chunk, the accumulator has been folded.  Descriptors are formed
+        // once; per MMA only the start address moves.  Before leaving, each
+        // thread waits (bounded) for all of its MMAs, so tensor memory is
+        // never freed under a running MMA.
         if (lane == 0) {
-            const uint64_t dU = tc::smem_desc(tc::smem_u32(sU), 128, 768);
-            const uint64_t dX = tc::smem_desc(tc::smem_u32(sX0), 128, 768);
-            const uint64_t dV = tc::smem_desc(tc::smem_u32(sV0), 128, 1024);
-            bool good = tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
-            auto issue_s = [&](int h) -> bool {
-                const int sx = h % NX;
-                if (h >= kNB && !tc::mbar_wait(&bars[kBarODone + (h - kNB) % kRing],
-                                               (uint32_t)(((h - kNB) / kRing) & 1), kWaitLimit))
-                    return false;
-                if (!tc::mbar_wait(&bars[kBarXFull + sx], (uint32_t)((h / NX) & 1), kWaitLimit)) return false;
-                tc::fence_after_sync();
-                const uint64_t dx = dX + (uint64_t)((sx * kXStep) >> 4);
-                const uint32_t tS = tmem + (h % kNB) * kTcKN;
+            bool good = true;
+            if (warp == 2) {
+                const uint64_t dU = tc::smem_desc(tc::smem_u32(sU), 128, 768);
+                const uint64_t dX = tc::smem_desc(tc::smem_u32(sX0), 128, 768);
+                good = tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
+                for (int h = 0; good && h < nt; ++h) {
+                    const int sx = h % NX;
+                    good = (h < kNB || tc::mbar_wait(&bars[kBarODone + (h - kNB) % kRing],
+                                                     (uint32_t)(((h - kNB) / kRing) & 1), kWaitLimit)) &&
+                           tc::mbar_wait(&bars[kBarXFull + sx], (uint32_t)((h / NX) & 1), kWaitLimit);
+                    if (!good) break;
+                    tc::fence_after_sync();
+                    const uint64_t dx = dX + (uint64_t)((sx * kXStep) >> 4);
+                    const uint32_t tS = tmem + (h % kNB) * kTcKN;
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch)
-                    tc::mma_f16(tS, dU + (uint64_t)((ch * 256) >> 4), dx + (uint64_t)((ch * 256) >> 4), IDESC_S,
-                                ch > 0 ? 1u : 0u);
-                tc::mma_commit(&bars[kBarSDone + h % kRing]);
-                return true;
-            };
-            if (good) good = issue_s(0);
-            if (good && nt > 1) good = issue_s(1);
-            for (int t = 0; good && t < nt; ++t) {
-                const int b = t % kNB, sv = t % NV;
-                const int ch = t / kTcChunk;
-                const bool fresh = (t % kTcChunk) == 0;
-                good = tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t / kNB) & 1), kWaitLimit) &&
-                       tc::mbar_wait(&bars[kBarVFull + sv], (uint32_t)((t / NV) & 1), kWaitLimit) &&
-                       (!fresh || ch < 1 ||
-                        tc::mbar_wait(&bars[kBarOFree], (uint32_t)((ch - 1) & 1), kWaitLimit));
-                if (!good) break;
-                tc::fence_after_sync();
-                const uint32_t tP = tmem + b * kTcKN;
-                const uint64_t dv = dV + (uint64_t)((sv * VSTEP) >> 4);
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const uint64_t vb = dv + (uint64_t)(((kk >> 2) * VHALF + (kk & 3) * 256) >> 4);
-                    tc::mma_f16_ts(tO0, tP + kk * 16, vb, IDESC_O2, (!fresh || kk > 0) ? 1u : 0u);   // P_hi [V_hi; V_lo]
-                    tc::mma_f16_ts(tO0, tP + kk * 16 + 8, vb, IDESC_O, 1u);                          // P_lo V_hi
+                    for (int ch = 0; ch < 3; ++ch)
+                        tc::mma_f16(tS, dU + (uint64_t)((ch * 256) >> 4), dx + (uint64_t)((ch * 256) >> 4), IDESC_S,
+                                    ch > 0 ? 1u : 0u);
+                    tc::mma_commit(&bars[kBarSDone + h % kRing]);
+                    if (*serr) good = false;
                 }
-                tc::mma_commit(&bars[kBarODone + t % kRing]);
-                if (t + 2 < nt && !issue_s(t + 2)) good = false;
-                if (*serr) good = false;
+            } else {
+                const uint64_t dV = tc::smem_desc(tc::smem_u32(sV0), 128, 1024);
+                for (int t = 0; good && t < nt; ++t) {
+                    const int b = t % kNB, sv = t % NV;
+                    const int ch = t / kTcChunk;
+                    const bool fresh = (t % kTcChunk) == 0;
+                    good = tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t / kNB) & 1), kWaitLimit) &&
+                           tc::mbar_wait(&bars[kBarVFull + sv], (uint32_t)((t / NV) & 1), kWaitLimit) &&
+                           (!fresh || ch < 1 ||
+                            tc::mbar_wait(&bars[kBarOFree], (uint32_t)((ch - 1) & 1), kWaitLimit));
+                    if (!good) break;
+                    tc::fence_after_sync();
+                    const uint32_t tP = tmem + b * kTcKN;
+                    const uint64_t dv = dV + (uint64_t)((sv * VSTEP) >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint64_t vb = dv + (uint64_t)(((kk >> 2) * VHALF + (kk & 3) * 256) >> 4);
+                        tc::mma_f16_ts(tO0, tP + kk * 16, vb, IDESC_O2, (!fresh || kk > 0) ? 1u : 0u);   // P_hi [V_hi; V_lo]
+                        tc::mma_f16_ts(tO0, tP + kk * 16 + 8, vb, IDESC_O, 1u);                          // P_lo V_hi
+                    }
+                    tc::mma_commit(&bars[kBarODone + t % kRing]);
+                    if (*serr) good = false;
+                }
             }
             if (!good) *serr = 1;
+            tc::mma_commit(&bars[kBarDrain + (warp - 1)]);
+            tc::mbar_wait(&bars[kBarDrain + (warp - 1)], 0, kWaitLimit);
         }
         __syncwarp();
     } else if (warp >= 4) {
