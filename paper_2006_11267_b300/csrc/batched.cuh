@@ -64,9 +64,11 @@ __device__ __forceinline__ bool list_item(const DevList& L, int item, int& p, in
 // Main-loop lists rebuilt on the device, kBatchDynLists in all.  CUDA-core
 // batches: one per MVM class (kernel type x padded dimension), then the
 // recurrence list.  Tensor-core batches: lists 0 and 1 are the MVM work of
-// RBF and Matern problems, list 2 the V split, the last the recurrence.
+// RBF and Matern problems, list 2 the V split, list 3 the finishing pass
+// (one item per row tile), the last the recurrence.
 constexpr int kBatchDynLists = kBatchClasses + 1;
 constexpr int kListTcSplit = 2;
+constexpr int kListTcFinish = 3;
 static_assert(kBatchDynLists == 9, "BatchProblem::list_items size");
 struct DynLists {
     DevList l[kBatchDynLists];
@@ -112,6 +114,9 @@ cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevLi
                                     cudaStream_t st);
 cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, DevList L,
                                   int blocks, cudaStream_t st);
+// Sum the split partials of every row tile and apply the MVM epilogue.
+cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, DevList L, int blocks,
+                                     cudaStream_t st);
 // Set the kernels' shared-memory attributes (before any stream capture).
 cudaError_t prepare_batched_tc_mvm(int TP, bool half);
 

@@ -437,8 +437,8 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         a.partials = p.partials;
         a.stop = p.all_done;
         // Kernels per MVM: one on CUDA cores; on tensor cores the V scale,
-        // the V split and one launch per column group.
-        const int mvm_launches = p.tc ? 2 + (T + tc_group_t(T) - 1) / tc_group_t(T) : 1;
+        // the V split and, per column group, the product and the finish.
+        const int mvm_launches = p.tc ? 2 + 2 * ((T + tc_group_t(T) - 1) / tc_group_t(T)) : 1;
         CIQ_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
         CIQ_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         if (prof.on) {
@@ -695,6 +695,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         if (tc) {
             b.list_items[probs[p].kern.type] = (int)(pl.Npad / kTcBM) * pl.tcp.nsplit;
             b.list_items[kListTcSplit] = (int)((pl.Npad / 8 * TP + 255) / 256);
+            b.list_items[kListTcFinish] = (int)(pl.Npad / kTcBM);
         } else {
             b.list_items[b.cls] = b.mvm_items;
         }
@@ -877,6 +878,11 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                         for (int kt = 0; kt < 2; ++kt) {
                             if (grid[kt] == 0) continue;
                             CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, TP, half, jj & 1, dyn_d.l[kt], grid[kt], ls));
+                            ++launches;
+                        }
+                        if (grid[kListTcFinish] > 0) {
+                            CIQ_TRY(launch_batched_tc_finish(probs_d, TP, jj & 1, dyn_d.l[kListTcFinish],
+                                                             grid[kListTcFinish], ls));
                             ++launches;
                         }
                     } else {

@@ -323,16 +323,16 @@ __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi
 // --------------------------------------------------------------- kernel --
 // Warp roles (384 threads): warp 0 lane 0 issues the bulk copies, warp 1
 // lane 0 the products, warp 2 lane 0 the S MMAs; warps 4-7 and 8-11 are two
-// exp warpgroups that split every step's 128 columns between them and fold
-// each completed chunk of O into the running sum; warps 4-7 run the
-// epilogue.
-// Columns [c0, c0 + TP) of V (those below a.T) are handled.
+// exp warpgroups that split every step's 128 columns between them, fold
+// each completed chunk of O into the running sum and write the CTA's column
+// sums.  Columns [c0, c0 + TP) of V (those below a.T) are handled.
 //
-// Split K: with p.nsplit = S > 1, CTA b takes row tile b / S and the steps
+// Split K: with p.nsplit = S, CTA b takes row tile b / S and the steps
 // [(b % S) nt / S, (b % S + 1) nt / S) of K's columns, so the grid fills the
-// SMs' waves evenly.  Each CTA writes its FP64 partial O; the last CTA of a
-// row tile to arrive (atomic count) adds the S partials in split order --
-// the result does not depend on which CTA is last -- and runs the epilogue.
+// SMs' waves evenly.  Every CTA writes its partial O as (leading, trailing)
+// float pairs; tc_finish_body adds a tile's S partials in split order and
+// runs the epilogue, in a kernel of its own (one block per row tile) so
+// this kernel holds only the pipeline.
 template <int KT, int TP, bool HALF>
 __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile,
                                             int split) {
@@ -357,7 +357,6 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
     const int ntot = (int)(a.Npad / kTcKN);
     const int st0 = (int)((int64_t)split * ntot / S);
     const int nt = (int)((int64_t)(split + 1) * ntot / S) - st0;   // steps of this CTA (>= 1)
-    __shared__ int last_arrival;
     const int nfold = (nt - 1) / kTcChunk;               // chunks folded before the last one
     constexpr uint32_t IDESC_S = tc::idesc_f16(kTcBM, kTcKN, !HALF);
     constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
@@ -574,155 +573,49 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
             tc::fence_before_sync();
             tc::mbar_arrive(&bars[kBarPFull + b]);
         }
-        // The running sum written by warpgroup 1 is read by warpgroup 0's epilogue.
-        asm volatile("bar.sync 1, 256;" ::: "memory");
     }
 
-    // ------------------------------------------------------------ epilogue
-    // FP64 runs at a few operations per clock per SM on this part, so the
-    // epilogue keeps its sums as unevaluated pairs of floats (Knuth's 2Sum,
-    // exact products by FMA) and converts to FP64 only per warp and column.
-    double* red = reinterpret_cast<double*>(sX0);         // [4 warps][TP][3], free once O is complete
-    float2* colsum = reinterpret_cast<float2*>(red + 4 * TP * 3);   // [TP][128] this CTA's sums (S = 1)
-    const int r_e = 32 * ((warp - 4) & 3) + lane;         // row of warpgroup 0's thread
-    float2* part = S > 1 ? reinterpret_cast<float2*>(p.part) + ((int64_t)tile * S) * TP * kTcBM : nullptr;
-    bool ok = true;
-    if (warp >= 4 && warp < 8) {
+    // ------------------------------------------------------- partial sums
+    // Warpgroup g writes the columns it folded, [g TP / 2, (g + 1) TP / 2):
+    // running sum + the last chunk's two accumulator halves, as float pairs.
+    if (warp >= 4) {
+        const int g = (warp - 4) >> 2;
+        const int r = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const bool good = !*serr && tc::mbar_wait(&bars[kBarODone + (nt - 1) % kRing],
                                                   (uint32_t)(((nt - 1) / kRing) & 1), kWaitLimit);
-        ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
+        const bool ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
         if (!ok) *serr = 1;
         tc::fence_after_sync();
-        // This CTA's column sums over its steps as (leading, trailing) floats.
+        float2* part = p.part + ((int64_t)tile * S + split) * TP * kTcBM;
 #pragma unroll 1
-        for (int cc = 0; cc < TP / 32; ++cc) {
-            uint32_t oa[32], ob[32];
+        for (int cb = 0; cb < TP / 32; ++cb) {
+            const int col0 = g * (TP / 2) + 16 * cb;
+            uint32_t oa[16], ob[16];
             if (ok) {
-                tc::tmem_ld32(tO0 + lane_base + 32 * cc, oa);
-                tc::tmem_ld32(tO0 + TP + lane_base + 32 * cc, ob);
+                tc::tmem_ld16(tO0 + lane_base + col0, oa);
+                tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
+                tc::tmem_wait_ld16(oa);
+                tc::tmem_wait_ld16(ob);
             }
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                const int cl = 32 * cc + e;
+            for (int e = 0; e < 16; ++e) {
+                const int cl = col0 + e;
                 float h = 0.f, l = 0.f;
                 if (ok && nfold > 0) {
-                    h = sR[cl * kTcBM + r_e];
-                    l = sR[(TP + cl) * kTcBM + r_e];
+                    h = sR[cl * kTcBM + r];
+                    l = sR[(TP + cl) * kTcBM + r];
                 }
                 if (ok) {
                     two_sum_into(h, l, __uint_as_float(oa[e]));
                     two_sum_into(h, l, __uint_as_float(ob[e]));
                 }
-                if (S > 1) part[((int64_t)split * TP + cl) * kTcBM + r_e] = make_float2(h, l);
-                else colsum[cl * kTcBM + r_e] = make_float2(h, l);
+                part[cl * kTcBM + r] = make_float2(h, l);
             }
-        }
-        if (S > 1) {
-            __threadfence();
-            asm volatile("bar.sync 2, 128;" ::: "memory");
-            if (warp == 4 && lane == 0) {
-                const int old = atomicAdd(&p.cnt[tile], 1);
-                last_arrival = old == S - 1;
-                if (old == S - 1) p.cnt[tile] = 0;          // ready for the next launch
-                __threadfence();
-            }
-            asm volatile("bar.sync 2, 128;" ::: "memory");
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    const bool finish = S == 1 || last_arrival;
-    if (finish && warp >= 4) {
-        // Both warpgroups finish the tile: warpgroup g takes half of the
-        // columns, in batches of 8 whose loads are all issued before any
-        // store (latency is paid once per batch, not per column).
-        constexpr int CB = 8;
-        const int g = (warp - 4) >> 2;
-        const int64_t i = i0 + r_e;
-        const int wl = warp & 3;
-        const bool row_in = i < a.N;
-        const int cbeg = g * (TP / 2), cend = min(cbeg + TP / 2, a.T - c0);
-#pragma unroll 1
-        for (int cb = cbeg; cb < cend; cb += CB) {
-            float h[CB], l[CB], v[CB], qp[CB], bt[CB], sc[CB];
-#pragma unroll
-            for (int u = 0; u < CB; ++u) {
-                const int cl = cb + u;
-                const bool in = cl < cend;
-                h[u] = 0.f;
-                l[u] = 0.f;
-                if (in) {
-                    if (S > 1) {
-                        for (int sp = 0; sp < S; ++sp) {
-                            const float2 v2 = __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r_e]);
-                            two_sum_into(h[u], l[u], v2.x);
-                            l[u] += v2.y;
-                        }
-                    } else {
-                        const float2 v2 = colsum[cl * kTcBM + r_e];
-                        h[u] = v2.x;
-                        l[u] = v2.y;
-                    }
-                }
-                const int64_t idx = (int64_t)(c0 + cl) * a.ldv + i;
-                v[u] = in ? a.V[idx] : 0.f;
-                qp[u] = (in && a.mode == kLanczos) ? a.qprev[idx] : 0.f;
-                bt[u] = (in && a.mode == kLanczos) ? (float)a.beta[c0 + cl] : 0.f;
-                // O = (h + l) outscale / vscale (a power of two), rounded once.
-                sc[u] = in ? (float)((double)a.s / (double)p.vscale[c0 + cl]) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < CB; ++u) {
-                const int cl = cb + u;
-                if (cl >= cend) break;
-                const int c = c0 + cl;
-                const int64_t idx = (int64_t)c * a.ldv + i;
-                float o = fmaf(h[u], sc[u], l[u] * sc[u]);
-                o += a.noise * v[u];
-                if (a.mode == kPlain) {
-                    if (row_in) a.out[(int64_t)c * a.ldo + i] = o;
-                    continue;
-                }
-                const float pv = row_in ? (float)(o - bt[u] * qp[u]) : 0.f;
-                a.qprev[idx] = pv;
-                // q.p, p.p, q.q of this row: exact products as float pairs,
-                // summed over the warp's 32 rows with 2Sum.
-                float sh[3], sl[3];
-                const float fa[3] = {v[u], pv, v[u]}, fb[3] = {pv, pv, v[u]};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    sh[k] = fa[k] * fb[k];
-                    sl[k] = fmaf(fa[k], fb[k], -sh[k]);
-                }
-#pragma unroll
-                for (int ofs = 16; ofs > 0; ofs >>= 1) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const float oh = __shfl_xor_sync(0xffffffffu, sh[k], ofs);
-                        const float ol = __shfl_xor_sync(0xffffffffu, sl[k], ofs);
-                        two_sum_into(sh[k], sl[k], oh);
-                        sl[k] += ol;
-                    }
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) red[(wl * TP + cl) * 3 + k] = (double)sh[k] + (double)sl[k];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (finish && a.mode == kLanczos) {
-        const int ncol = min(TP, a.T - c0);
-        for (int cl = tid; cl < ncol; cl += blockDim.x) {
-            double* dst = a.partials + ((int64_t)tile * a.T + c0 + cl) * 3;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                dst[k] = red[(0 * TP + cl) * 3 + k] + red[(1 * TP + cl) * 3 + k] + red[(2 * TP + cl) * 3 + k] +
-                         red[(3 * TP + cl) * 3 + k];
-        }
-    }
     if (tid == 0 && *serr) atomicExch(p.err, 1);
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
@@ -730,6 +623,114 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
 template <int KT, int TP, bool HALF>
 __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
     mvm_tc_body<KT, TP, HALF>(p, a, c0, blockIdx.x / p.nsplit, blockIdx.x % p.nsplit);
+}
+
+// ------------------------------------------------------------- finish --
+// One 128-row tile of O: the S split partials of every column added in split
+// order (2Sum on (leading, trailing) float pairs), scaled by outscale /
+// vscale, plus sigma^2 V, then the epilogue of `a`: kPlain stores O;
+// kLanczos writes p = O - beta q_prev over q_prev and forms the tile's q.p,
+// p.p, q.q per column (exact products by FMA, summed over a warp's rows by
+// shuffles and over the four row warps in order, converted to FP64 once).
+// 256 threads: warpgroup g takes columns [g TP / 2, (g + 1) TP / 2), thread
+// (warp w, lane) row 32 (w % 4) + lane.  FP64 runs at a few operations per
+// clock per SM on this part, so no FP64 arithmetic is done per row.
+template <int TP>
+__device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile) {
+    __shared__ float col_scale[TP], col_beta[TP];
+    __shared__ float2 red[4 * TP * 3];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < TP) {
+        const bool in = tid < a.T - c0;
+        col_scale[tid] = in ? a.s / p.vscale[c0 + tid] : 0.f;    // exact: vscale is a power of two
+        col_beta[tid] = (in && a.mode == kLanczos) ? (float)a.beta[c0 + tid] : 0.f;
+    }
+    __syncthreads();
+    const int S = p.nsplit;
+    const float2* part = p.part + (int64_t)tile * S * TP * kTcBM;
+    constexpr int CB = 8;
+    const int g = warp >> 2, wl = warp & 3, r = 32 * wl + lane;
+    const int64_t i = tile * kTcBM + r;
+    const bool row_in = i < a.N;
+    const int cbeg = g * (TP / 2), cend = min(cbeg + TP / 2, a.T - c0);
+#pragma unroll 1
+    for (int cb = cbeg; cb < cend; cb += CB) {
+        // All loads of a batch of CB columns are issued before any use.
+        float h[CB], l[CB], v[CB], qp[CB];
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const int cl = cb + u;
+            const bool in = cl < cend;
+            h[u] = 0.f;
+            l[u] = 0.f;
+            if (in)
+                for (int sp = 0; sp < S; ++sp) {
+                    const float2 v2 = __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r]);
+                    two_sum_into(h[u], l[u], v2.x);
+                    l[u] += v2.y;
+                }
+            const int64_t idx = (int64_t)(c0 + cl) * a.ldv + i;
+            v[u] = in ? a.V[idx] : 0.f;
+            qp[u] = (in && a.mode == kLanczos) ? a.qprev[idx] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const int cl = cb + u;
+            if (cl >= cend) break;
+            const int c = c0 + cl;
+            const int64_t idx = (int64_t)c * a.ldv + i;
+            const float sc = col_scale[cl];
+            float o = fmaf(h[u], sc, l[u] * sc);
+            o += a.noise * v[u];
+            if (a.mode == kPlain) {
+                if (row_in) a.out[(int64_t)c * a.ldo + i] = o;
+                continue;
+            }
+            const float pv = row_in ? o - col_beta[cl] * qp[u] : 0.f;
+            a.qprev[idx] = pv;
+            float sh[3], sl[3];
+            const float fa[3] = {v[u], pv, v[u]}, fb[3] = {pv, pv, v[u]};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sh[k] = fa[k] * fb[k];
+                sl[k] = fmaf(fa[k], fb[k], -sh[k]);
+            }
+#pragma unroll
+            for (int ofs = 16; ofs > 0; ofs >>= 1) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, sh[k], ofs);
+                    const float ol = __shfl_xor_sync(0xffffffffu, sl[k], ofs);
+                    two_sum_into(sh[k], sl[k], oh);
+                    sl[k] += ol;
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) red[(wl * TP + cl) * 3 + k] = make_float2(sh[k], sl[k]);
+            }
+        }
+    }
+    if (a.mode != kLanczos) return;
+    __syncthreads();
+    const int ncol = min(TP, a.T - c0);
+    for (int q = tid; q < 3 * ncol; q += blockDim.x) {
+        const int cl = q / 3, k = q - 3 * cl;
+        float hs = red[cl * 3 + k].x, ls = red[cl * 3 + k].y;
+#pragma unroll
+        for (int w = 1; w < 4; ++w) {
+            const float2 v2 = red[(w * TP + cl) * 3 + k];
+            two_sum_into(hs, ls, v2.x);
+            ls += v2.y;
+        }
+        a.partials[((int64_t)tile * a.T + c0 + cl) * 3 + k] = (double)hs + (double)ls;
+    }
+}
+
+template <int TP>
+__global__ void __launch_bounds__(256) tc_finish_kernel(TcPoints p, MvmArgs<float> a, int c0) {
+    if (a.stop && *a.stop) return;
+    tc_finish_body<TP>(p, a, c0, blockIdx.x);
 }
 
 // ------------------------------------------------------ batched problems --
@@ -750,8 +751,24 @@ __global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProbl
     mvm_tc_body<KT, TP, HALF>(sp, sa, 0, local / sp.nsplit, local % sp.nsplit);
 }
 
+// Block b finishes row tile `local` of problem pb (item b of the list).
+template <int TP>
+__global__ void __launch_bounds__(256) batched_tc_finish_kernel(const BatchProblem* probs, DevList L, int parity) {
+    int pb, local;
+    if (!list_item(L, blockIdx.x, pb, local)) return;
+    __shared__ TcPoints sp;
+    __shared__ MvmArgs<float> sa;
+    if (threadIdx.x == 0) {
+        sp = probs[pb].tcp;
+        sa = probs[pb].mvm[parity];
+    }
+    __syncthreads();
+    if (sa.stop && *sa.stop) return;
+    tc_finish_body<TP>(sp, sa, 0, local);
+}
+
 // One block per problem: centre of the points, unit V scales, cleared
-// error flag and split-K counters.
+// error flag.
 __global__ void __launch_bounds__(256) batched_tc_mean_kernel(const BatchProblem* probs, DevList L) {
     int pb, local;
     if (!list_item(L, blockIdx.x, pb, local)) return;
@@ -761,8 +778,6 @@ __global__ void __launch_bounds__(256) batched_tc_mean_kernel(const BatchProblem
     tc_mean_body(m.X, m.N, m.dp, tp.mean);
     const float unit_scale = ldexpf(1.f, (int)floor(0.5 * log2((double)m.N)));
     for (int c = threadIdx.x; c < tp.TP; c += 256) tp.vscale[c] = unit_scale;
-    if (tp.nsplit > 1)
-        for (int64_t k = threadIdx.x; k < tp.Npad / kTcBM; k += 256) tp.cnt[k] = 0;
     if (threadIdx.x == 0) *tp.err = 0;
 }
 
@@ -799,6 +814,9 @@ cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaSt
         configured = true;
     }
     mvm_tc_kernel<KT, TP, HALF><<<(unsigned)(a.Npad / kTcBM * p.nsplit), 384, smem, st>>>(p, a, c0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tc_finish_kernel<TP><<<(unsigned)(a.Npad / kTcBM), 256, 0, st>>>(p, a, c0);
     return cudaGetLastError();
 }
 
@@ -870,9 +888,8 @@ size_t tc_points_bytes(int64_t Npad, int T, int max_split) {
     const size_t pts = (size_t)Npad * kTcRowBytes;
     const size_t vb = (size_t)(Npad / kTcBN) * 2 * TP * 128;
     const int S = tc_nsplit(Npad, max_split);
-    const size_t part = S > 1 ? (size_t)(Npad / kTcBM) * S * tc_group_t(T) * kTcBM * sizeof(double) + 256 : 0;
-    const size_t cnt = S > 1 ? (size_t)(Npad / kTcBM) * sizeof(int) + 256 : 0;
-    return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256 + part + cnt;
+    const size_t part = (size_t)(Npad / kTcBM) * S * tc_group_t(T) * kTcBM * 2 * sizeof(float) + 256;
+    return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256 + part;
 }
 
 TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int max_split) {
@@ -893,11 +910,7 @@ TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int ma
     p.mean = reinterpret_cast<double*>(take(16 * sizeof(double)));
     p.err = reinterpret_cast<int*>(take(sizeof(int)));
     p.nsplit = tc_nsplit(Npad, max_split);
-    if (p.nsplit > 1) {
-        p.part = reinterpret_cast<double*>(
-            take((size_t)(Npad / kTcBM) * p.nsplit * tc_group_t(T) * kTcBM * sizeof(double)));
-        p.cnt = reinterpret_cast<int*>(take((size_t)(Npad / kTcBM) * sizeof(int)));
-    }
+    p.part = reinterpret_cast<float2*>(take((size_t)(Npad / kTcBM) * p.nsplit * tc_group_t(T) * kTcBM * sizeof(float2)));
     return p;
 }
 
@@ -906,8 +919,6 @@ cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int
     cudaError_t e = cudaMemsetAsync(p.mean, 0, 16 * sizeof(double), st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.err, 0, sizeof(int), st)) != cudaSuccess) return e;
-    if (p.nsplit > 1 && (e = cudaMemsetAsync(p.cnt, 0, sizeof(int) * (size_t)(p.Npad / kTcBM), st)) != cudaSuccess)
-        return e;
     tc_mean_kernel<<<1, 256, 0, st>>>(Xp, N, dp, p.mean);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const double c2 = kt == CIQ_RBF ? kLog2e : 1.0;
@@ -1022,6 +1033,15 @@ cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, boo
                     : launch_btc_tp<CIQ_RBF, false>(probs, TP, parity, L, blocks, st);
     return half ? launch_btc_tp<CIQ_MATERN52, true>(probs, TP, parity, L, blocks, st)
                 : launch_btc_tp<CIQ_MATERN52, false>(probs, TP, parity, L, blocks, st);
+}
+
+cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, DevList L, int blocks,
+                                     cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (TP == 32) batched_tc_finish_kernel<32><<<blocks, 256, 0, st>>>(probs, L, parity);
+    else if (TP == 64) batched_tc_finish_kernel<64><<<blocks, 256, 0, st>>>(probs, L, parity);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace ciq

@@ -20,8 +20,7 @@ struct TcPoints {
     float* vscale = nullptr;   // power-of-two scale per column of V      [TP]
     double* mean = nullptr;    // centre of the points                    [16]
     int* err = nullptr;        // set to 1 if a bounded wait gave up
-    double* part = nullptr;    // split-K partial sums [row tile][split][TP][128] (nsplit > 1)
-    int* cnt = nullptr;        // split-K arrivals per row tile (nsplit > 1)
+    float2* part = nullptr;    // partial sums as (leading, trailing) pairs [row tile][split][TP][128]
     int nsplit = 1;            // CTAs per row tile, each over a contiguous range of K's columns
     int64_t Npad = 0;
     int TP = 0;                // T rounded up to whole launch groups (32, 64 or k x 128)
