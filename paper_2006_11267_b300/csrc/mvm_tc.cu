@@ -438,51 +438,55 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
         __syncwarp();
     } else if (warp == 1 || warp == 2) {
         // ----------------------------------------------------- MMA issuers
-        // Two threads feed the tensor pipe, so neither's barrier waits leave
-        // it idle: warp 2 issues S(h) into buffer h % 3 as soon as the
-        // product of step h - 3 (the buffer's last reader) is complete and
-        // the points are in; warp 1 issues O += P(t) V(t) once both exp
+        // Two warps feed the tensor pipe, so neither's barrier waits leave it
+        // idle: warp 2 issues S(h) into buffer h % 3 as soon as the product
+        // of step h - 3 (the buffer's last reader) is complete and the
+        // points are in; warp 1 issues O += P(t) V(t) once both exp
         // warpgroups have written P(t), V(t) is in and, at the start of a
-        // chunk, the accumulator has been folded.  Descriptors are formed
-        // once; per MMA only the start address moves.  Before leaving, each
-        // thread waits (bounded) for all of its MMAs, so tensor memory is
-        // never freed under a running MMA.
-        if (lane == 0) {
-            bool good = true;
-            if (warp == 2) {
-                const uint64_t dU = tc::smem_desc(tc::smem_u32(sU), 128, 768);
-                const uint64_t dX = tc::smem_desc(tc::smem_u32(sX0), 128, 768);
-                good = tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
-                for (int h = 0; good && h < nt; ++h) {
-                    const int sx = h % NX;
-                    good = (h < kNB || tc::mbar_wait(&bars[kBarODone + (h - kNB) % kRing],
+        // chunk, the accumulator has been folded.  The whole warp runs the
+        // loop (so the descriptors are warp-uniform values) and one elected
+        // lane issues.  Before leaving, the warp waits (bounded) for all of
+        // its MMAs, so tensor memory is never freed under a running MMA.
+        auto uni = [&](bool b) { return __shfl_sync(0xffffffffu, (int)b, 0) != 0; };
+        bool good = true;
+        if (warp == 2) {
+            const uint64_t dU = tc::smem_desc(tc::smem_u32(sU), 128, 768);
+            const uint64_t dX = tc::smem_desc(tc::smem_u32(sX0), 128, 768);
+            good = uni(tc::mbar_wait(&bars[kBarU], 0, kWaitLimit));
+            for (int h = 0; good && h < nt; ++h) {
+                const int sx = h % NX;
+                good = uni((h < kNB || tc::mbar_wait(&bars[kBarODone + (h - kNB) % kRing],
                                                      (uint32_t)(((h - kNB) / kRing) & 1), kWaitLimit)) &&
-                           tc::mbar_wait(&bars[kBarXFull + sx], (uint32_t)((h / NX) & 1), kWaitLimit);
-                    if (!good) break;
-                    tc::fence_after_sync();
-                    const uint64_t dx = dX + (uint64_t)((sx * kXStep) >> 4);
-                    const uint32_t tS = tmem + (h % kNB) * kTcKN;
+                           tc::mbar_wait(&bars[kBarXFull + sx], (uint32_t)((h / NX) & 1), kWaitLimit));
+                if (!good) break;
+                tc::fence_after_sync();
+                const uint64_t dx = dX + (uint64_t)((sx * kXStep) >> 4);
+                const uint32_t tS = tmem + (h % kNB) * kTcKN;
+                if (tc::elect_one()) {
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch)
                         tc::mma_f16(tS, dU + (uint64_t)((ch * 256) >> 4), dx + (uint64_t)((ch * 256) >> 4), IDESC_S,
                                     ch > 0 ? 1u : 0u);
                     tc::mma_commit(&bars[kBarSDone + h % kRing]);
-                    if (*serr) good = false;
                 }
-            } else {
-                const uint64_t dV = tc::smem_desc(tc::smem_u32(sV0), 128, 1024);
-                for (int t = 0; good && t < nt; ++t) {
-                    const int b = t % kNB, sv = t % NV;
-                    const int ch = t / kTcChunk;
-                    const bool fresh = (t % kTcChunk) == 0;
-                    good = tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t / kNB) & 1), kWaitLimit) &&
+                __syncwarp();
+                good = uni(!*serr);
+            }
+        } else {
+            const uint64_t dV = tc::smem_desc(tc::smem_u32(sV0), 128, 1024);
+            for (int t = 0; good && t < nt; ++t) {
+                const int b = t % kNB, sv = t % NV;
+                const int ch = t / kTcChunk;
+                const bool fresh = (t % kTcChunk) == 0;
+                good = uni(tc::mbar_wait(&bars[kBarPFull + b], (uint32_t)((t / kNB) & 1), kWaitLimit) &&
                            tc::mbar_wait(&bars[kBarVFull + sv], (uint32_t)((t / NV) & 1), kWaitLimit) &&
                            (!fresh || ch < 1 ||
-                            tc::mbar_wait(&bars[kBarOFree], (uint32_t)((ch - 1) & 1), kWaitLimit));
-                    if (!good) break;
-                    tc::fence_after_sync();
-                    const uint32_t tP = tmem + b * kTcKN;
-                    const uint64_t dv = dV + (uint64_t)((sv * VSTEP) >> 4);
+                            tc::mbar_wait(&bars[kBarOFree], (uint32_t)((ch - 1) & 1), kWaitLimit)));
+                if (!good) break;
+                tc::fence_after_sync();
+                const uint32_t tP = tmem + b * kTcKN;
+                const uint64_t dv = dV + (uint64_t)((sv * VSTEP) >> 4);
+                if (tc::elect_one()) {
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
                         const uint64_t vb = dv + (uint64_t)(((kk >> 2) * VHALF + (kk & 3) * 256) >> 4);
@@ -490,13 +494,15 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                         tc::mma_f16_ts(tO0, tP + kk * 16 + 8, vb, IDESC_O, 1u);                          // P_lo V_hi
                     }
                     tc::mma_commit(&bars[kBarODone + t % kRing]);
-                    if (*serr) good = false;
                 }
+                __syncwarp();
+                good = uni(!*serr);
             }
-            if (!good) *serr = 1;
-            tc::mma_commit(&bars[kBarDrain + (warp - 1)]);
-            tc::mbar_wait(&bars[kBarDrain + (warp - 1)], 0, kWaitLimit);
         }
+        if (!good && lane == 0) *serr = 1;
+        if (tc::elect_one()) tc::mma_commit(&bars[kBarDrain + (warp - 1)]);
+        __syncwarp();
+        tc::mbar_wait(&bars[kBarDrain + (warp - 1)], 0, kWaitLimit);
         __syncwarp();
     } else if (warp >= 4) {
         // --------------------------------------------------- exp warpgroups
