@@ -390,51 +390,59 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
 
     if (warp == 0) {
         // ---------------------------------------------------------- loader
-        // One thread, fixed order: the points of step t + 2 (S runs two
+        // Fixed order: the points of step t + 2 (S runs two
         // steps ahead of the product), then the V of step t.  The point
         // stage of step u was read by S(u - NX), the V stage by the product
         // of step t - NV; each wait is bounded.
-        if (lane == 0) {
+        // The whole warp runs the loop; one elected lane issues the copies.
+        auto uni = [&](bool b) { return __shfl_sync(0xffffffffu, (int)b, 0) != 0; };
+        if (tc::elect_one()) {
             tc::mbar_expect_tx(&bars[kBarU], kUBytes);
             tc::bulk_g2s(sU, p.ua + tile * kUBytes, kUBytes, &bars[kBarU]);
-            auto load_x = [&](int u) -> bool {
-                const int sx = u % NX;
-                if (u >= NX && !tc::mbar_wait(&bars[kBarSDone + (u - NX) % kRing], (uint32_t)(((u - NX) / kRing) & 1),
-                                              kWaitLimit))
-                    return false;
+        }
+        auto load_x = [&](int u) -> bool {
+            const int sx = u % NX;
+            if (u >= NX && !uni(tc::mbar_wait(&bars[kBarSDone + (u - NX) % kRing],
+                                              (uint32_t)(((u - NX) / kRing) & 1), kWaitLimit)))
+                return false;
+            if (tc::elect_one()) {
                 tc::mbar_expect_tx(&bars[kBarXFull + sx], kXStep);
                 tc::bulk_g2s(sX0 + sx * kXStep, p.ub + (int64_t)(st0 + u) * kXStep, kXStep, &bars[kBarXFull + sx]);
-                return true;
-            };
-            int nx = 0, nv = 0;                           // copies issued
-            bool ok = load_x(0);
-            nx += ok;
-            if (ok && nt > 1) nx += (ok = load_x(1));
-            for (int t = 0; ok && t < nt; ++t) {
-                if (t + 2 < nt) {
-                    if (!load_x(t + 2)) { ok = false; break; }
-                    ++nx;
-                }
-                const int sv = t % NV;
-                if (t >= NV && !tc::mbar_wait(&bars[kBarODone + (t - NV) % kRing], (uint32_t)(((t - NV) / kRing) & 1),
-                                              kWaitLimit)) {
-                    ok = false;
-                    break;
-                }
+            }
+            __syncwarp();
+            return true;
+        };
+        int nx = 0, nv = 0;                               // copies issued
+        bool ok = load_x(0);
+        nx += ok;
+        if (ok && nt > 1) nx += (ok = load_x(1));
+        for (int t = 0; ok && t < nt; ++t) {
+            if (t + 2 < nt) {
+                if (!load_x(t + 2)) { ok = false; break; }
+                ++nx;
+            }
+            const int sv = t % NV;
+            if (t >= NV && !uni(tc::mbar_wait(&bars[kBarODone + (t - NV) % kRing],
+                                              (uint32_t)(((t - NV) / kRing) & 1), kWaitLimit))) {
+                ok = false;
+                break;
+            }
+            if (tc::elect_one()) {
                 tc::mbar_expect_tx(&bars[kBarVFull + sv], VSTEP);
                 tc::bulk_g2s(sV0 + sv * VSTEP, vblk + (int64_t)(st0 + t) * VSTEP, VSTEP, &bars[kBarVFull + sv]);
-                ++nv;
-                if (*serr) break;
             }
-            if (!ok) *serr = 1;
-            // No copy may land in shared memory after the CTA has left: wait
-            // (bounded) for the last copy issued to every stage.
-            tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
-            for (int u = max(nx - NX, 0); u < nx; ++u)
-                tc::mbar_wait(&bars[kBarXFull + u % NX], (uint32_t)((u / NX) & 1), kWaitLimit);
-            for (int u = max(nv - NV, 0); u < nv; ++u)
-                tc::mbar_wait(&bars[kBarVFull + u % NV], (uint32_t)((u / NV) & 1), kWaitLimit);
+            __syncwarp();
+            ++nv;
+            if (uni(*serr)) break;
         }
+        if (!ok && lane == 0) *serr = 1;
+        // No copy may land in shared memory after the CTA has left: wait
+        // (bounded) for the last copy issued to every stage.
+        tc::mbar_wait(&bars[kBarU], 0, kWaitLimit);
+        for (int u = max(nx - NX, 0); u < nx; ++u)
+            tc::mbar_wait(&bars[kBarXFull + u % NX], (uint32_t)((u / NX) & 1), kWaitLimit);
+        for (int u = max(nv - NV, 0); u < nv; ++u)
+            tc::mbar_wait(&bars[kBarVFull + u % NV], (uint32_t)((u / NV) & 1), kWaitLimit);
         __syncwarp();
     } else if (warp == 1 || warp == 2) {
         // ----------------------------------------------------- MMA issuers
