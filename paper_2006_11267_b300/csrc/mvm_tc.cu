@@ -518,41 +518,6 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int r = 32 * (warp & 3) + lane;             // row of the tile = TMEM lane
         for (int t = 0; t < nt; ++t) {
-            // Fold the previous chunk of O into the running sum, before this
-            // step's exp work; each warpgroup takes half of the columns, and
-            // the accumulator is released as soon as it has been read.
-            if (t >= kTcChunk && (t % kTcChunk) == 0) {
-                const int c = t / kTcChunk - 1;
-                const int te = t - 1;                     // last step of chunk c
-                const bool okc = tc::mbar_wait(&bars[kBarODone + te % kRing], (uint32_t)((te / kRing) & 1), kWaitLimit);
-                if (__shfl_sync(0xffffffffu, (int)(!okc || *serr), 0)) { *serr = 1; break; }
-                tc::fence_after_sync();
-                constexpr int HB = TP / 2 / 16;           // 16-column blocks per warpgroup
-#pragma unroll 1
-                for (int cb = 0; cb < HB; ++cb) {
-                    const int col0 = g * (TP / 2) + 16 * cb;
-                    uint32_t oa[16], ob[16];
-                    tc::tmem_ld16(tO0 + lane_base + col0, oa);
-                    tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
-                    tc::tmem_wait_ld16(oa);
-                    tc::tmem_wait_ld16(ob);
-                    if (cb == HB - 1) {
-                        tc::fence_before_sync();
-                        tc::mbar_arrive(&bars[kBarOFree]);
-                    }
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        float* rh = sR + (col0 + e) * kTcBM + r;
-                        float* rl = rh + TP * kTcBM;
-                        float h = c > 0 ? *rh : 0.f;
-                        float l = c > 0 ? *rl : 0.f;
-                        two_sum_into(h, l, __uint_as_float(oa[e]));
-                        two_sum_into(h, l, __uint_as_float(ob[e]));
-                        *rh = h;
-                        *rl = l;
-                    }
-                }
-            }
             const int b = t % kNB;
             const uint32_t tS = tmem + b * kTcKN + g * 64 + lane_base;
             const bool good = tc::mbar_wait(&bars[kBarSDone + t % kRing], (uint32_t)((t / kRing) & 1), kWaitLimit);
@@ -586,6 +551,44 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
             tc::tmem_wait_st64(h0, l0, h1, l1, h2, l2, h3, l3);
             tc::fence_before_sync();
             tc::mbar_arrive(&bars[kBarPFull + b]);
+            // At the start of a chunk, fold the previous chunk of O into the
+            // running sum after this step's P is written, so the product of
+            // this step waits only for the accumulator to be read, not for
+            // the exp work as well; each warpgroup takes half of the
+            // columns, and the accumulator is released as soon as it has
+            // been read.
+            if (t >= kTcChunk && (t % kTcChunk) == 0) {
+                const int c = t / kTcChunk - 1;
+                const int te = t - 1;                     // last step of chunk c
+                const bool okc = tc::mbar_wait(&bars[kBarODone + te % kRing], (uint32_t)((te / kRing) & 1), kWaitLimit);
+                if (__shfl_sync(0xffffffffu, (int)(!okc || *serr), 0)) { *serr = 1; break; }
+                tc::fence_after_sync();
+                constexpr int HB = TP / 2 / 16;           // 16-column blocks per warpgroup
+#pragma unroll 1
+                for (int cb = 0; cb < HB; ++cb) {
+                    const int col0 = g * (TP / 2) + 16 * cb;
+                    uint32_t oa[16], ob[16];
+                    tc::tmem_ld16(tO0 + lane_base + col0, oa);
+                    tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
+                    tc::tmem_wait_ld16(oa);
+                    tc::tmem_wait_ld16(ob);
+                    if (cb == HB - 1) {
+                        tc::fence_before_sync();
+                        tc::mbar_arrive(&bars[kBarOFree]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        float* rh = sR + (col0 + e) * kTcBM + r;
+                        float* rl = rh + TP * kTcBM;
+                        float h = c > 0 ? *rh : 0.f;
+                        float l = c > 0 ? *rl : 0.f;
+                        two_sum_into(h, l, __uint_as_float(oa[e]));
+                        two_sum_into(h, l, __uint_as_float(ob[e]));
+                        *rh = h;
+                        *rl = l;
+                    }
+                }
+            }
         }
     }
 
