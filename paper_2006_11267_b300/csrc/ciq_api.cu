@@ -181,7 +181,7 @@ struct Plan {
         sstart = stage_start ? a.take<R>((size_t)N) : nullptr;
         if (tc) {
             char* q = a.take<char>(tc_points_bytes(Npad, T, tc_max_split));
-            tcp = tc_points_layout(q, Npad, T, precision, tc_max_split);
+            tcp = tc_points_layout(q, Npad, T, precision, tc_max_split, d);
         }
         Kst = stored ? a.take<float>((size_t)Npad * Npad) : nullptr;
         bytes = a.off + kAlign;

@@ -8,8 +8,9 @@
 //         -c^2 |x - m|^2 / 2], so S = -c^2 r^2 / 2 directly (norm expansion of
 //         the distance; m is the centre of the points).  Each operand is split
 //         into a 16-bit leading part and a 16-bit trailing part and S =
-//         U_h V_h + U_h V_l + U_l V_h (three K-chunks of one MMA sequence):
-//         about 22 significant bits with FP16 parts.
+//         U_h V_h + U_h V_l + U_l V_h (three K-chunks of one MMA sequence;
+//         two MMAs for d <= 6, whose 8 augmented features fill half a
+//         chunk): about 22 significant bits with FP16 parts.
 //   P   = k(r) / s from S on the SFU (RBF: ex2(S) with c^2 = log2 e; Matern-5/2:
 //         a = sqrt(-10 S), (1 + a + a^2/3) ex2(-a log2 e)), split again into
 //         leading/trailing 16-bit parts and written back over S in tensor
@@ -460,6 +461,12 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
         if (warp == 2) {
             const uint64_t dU = tc::smem_desc(tc::smem_u32(sU), 128, 768);
             const uint64_t dX = tc::smem_desc(tc::smem_u32(sX0), 128, 768);
+            // With at most 8 features only K-core 0 of each chunk is
+            // non-zero: a K-core stride of one chunk (256 bytes) makes one
+            // K16 MMA read core 0 of chunks 0 and 1, U_h [X_h; X_l].
+            const uint64_t dU2 = tc::smem_desc(tc::smem_u32(sU), 256, 768);
+            const uint64_t dX2 = tc::smem_desc(tc::smem_u32(sX0), 256, 768);
+            const bool narrow = p.narrow != 0;
             good = uni(tc::mbar_wait(&bars[kBarU], 0, kWaitLimit));
             for (int h = 0; good && h < nt; ++h) {
                 const int sx = h % NX;
@@ -471,10 +478,15 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                 const uint64_t dx = dX + (uint64_t)((sx * kXStep) >> 4);
                 const uint32_t tS = tmem + (h % kNB) * kTcKN;
                 if (tc::elect_one()) {
+                    if (narrow) {
+                        tc::mma_f16(tS, dU2, dX2 + (uint64_t)((sx * kXStep) >> 4), IDESC_S, 0u);
+                        tc::mma_f16(tS, dU + (uint64_t)(512 >> 4), dx + (uint64_t)(512 >> 4), IDESC_S, 1u);
+                    } else {
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch)
-                        tc::mma_f16(tS, dU + (uint64_t)((ch * 256) >> 4), dx + (uint64_t)((ch * 256) >> 4), IDESC_S,
-                                    ch > 0 ? 1u : 0u);
+                        for (int ch = 0; ch < 3; ++ch)
+                            tc::mma_f16(tS, dU + (uint64_t)((ch * 256) >> 4), dx + (uint64_t)((ch * 256) >> 4),
+                                        IDESC_S, ch > 0 ? 1u : 0u);
+                    }
                     tc::mma_commit(&bars[kBarSDone + h % kRing]);
                 }
                 __syncwarp();
@@ -909,8 +921,9 @@ size_t tc_points_bytes(int64_t Npad, int T, int max_split) {
     return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256 + part;
 }
 
-TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int max_split) {
+TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int max_split, int d) {
     TcPoints p;
+    p.narrow = d + 2 <= 8 ? 1 : 0;
     p.Npad = Npad;
     p.TP = tc_padded_t(T);
     p.half = precision == CIQ_PREC_FP16 ? 1 : 0;

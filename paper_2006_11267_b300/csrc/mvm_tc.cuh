@@ -22,6 +22,8 @@ struct TcPoints {
     int* err = nullptr;        // set to 1 if a bounded wait gave up
     float2* part = nullptr;    // partial sums as (leading, trailing) pairs [row tile][split][TP][128]
     int nsplit = 1;            // CTAs per row tile, each over a contiguous range of K's columns
+    int narrow = 0;            // 1: at most 8 augmented features (d <= 6), so only the first K-core
+                               // of every chunk is non-zero and S takes two MMAs instead of three
     int64_t Npad = 0;
     int TP = 0;                // T rounded up to whole launch groups (32, 64 or k x 128)
     int half = 0;              // 1: FP16 operands; 0: BF16
@@ -34,7 +36,7 @@ int64_t tc_row_tiles(int64_t Npad);
 // max_split caps the CTAs per row tile (batches, whose many problems fill the
 // GPU already, use 1).
 size_t tc_points_bytes(int64_t Npad, int T, int max_split = 8);
-TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int max_split = 8);
+TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int max_split, int d);
 // Centre/scale/augment/split the points (Xp: Npad x dp, already divided by
 // the lengthscale) into ua/ub; clears the error flag.
 cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int dp, int d, int kt,
