@@ -65,7 +65,7 @@ __device__ __forceinline__ bool list_item(const DevList& L, int item, int& p, in
 // batches: one per MVM class (kernel type x padded dimension), then the
 // recurrence list.  Tensor-core batches: lists 0 and 1 are the MVM work of
 // RBF and Matern problems, list 2 the V split, list 3 the finishing pass
-// (one item per row tile), the last the recurrence.
+// (one item per row tile and 16 columns), the last the recurrence.
 constexpr int kBatchDynLists = kBatchClasses + 1;
 constexpr int kListTcSplit = 2;
 constexpr int kListTcFinish = 3;

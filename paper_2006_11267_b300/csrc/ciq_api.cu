@@ -695,7 +695,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         if (tc) {
             b.list_items[probs[p].kern.type] = (int)(pl.Npad / kTcBM) * pl.tcp.nsplit;
             b.list_items[kListTcSplit] = (int)((pl.Npad / 8 * TP + 255) / 256);
-            b.list_items[kListTcFinish] = (int)(pl.Npad / kTcBM);
+            b.list_items[kListTcFinish] = (int)(pl.Npad / kTcBM) * (TP / 16);   // row tile x 16 columns
         } else {
             b.list_items[b.cls] = b.mvm_items;
         }

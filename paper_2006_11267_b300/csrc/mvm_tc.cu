@@ -606,7 +606,9 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
 
     // ------------------------------------------------------- partial sums
     // Warpgroup g writes the columns it folded, [g TP / 2, (g + 1) TP / 2):
-    // running sum + the last chunk's two accumulator halves, as float pairs.
+    // running sum + the last chunk's two accumulator halves, formed as a
+    // float pair and rounded once to a float (2^-24 relative, far below the
+    // error of the 16-bit split operands; halves the finishing traffic).
     if (warp >= 4) {
         const int g = (warp - 4) >> 2;
         const int r = 32 * (warp & 3) + lane;
@@ -616,7 +618,7 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
         const bool ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
         if (!ok) *serr = 1;
         tc::fence_after_sync();
-        float2* part = p.part + ((int64_t)tile * S + split) * TP * kTcBM;
+        float* part = p.part + ((int64_t)tile * S + split) * TP * kTcBM;
 #pragma unroll 1
         for (int cb = 0; cb < TP / 32; ++cb) {
             const int col0 = g * (TP / 2) + 16 * cb;
@@ -639,7 +641,7 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                     two_sum_into(h, l, __uint_as_float(oa[e]));
                     two_sum_into(h, l, __uint_as_float(ob[e]));
                 }
-                part[cl * kTcBM + r] = make_float2(h, l);
+                part[cl * kTcBM + r] = h + l;
             }
         }
     }
@@ -655,33 +657,38 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
 }
 
 // ------------------------------------------------------------- finish --
-// One 128-row tile of O: the S split partials of every column added in split
-// order (2Sum on (leading, trailing) float pairs), scaled by outscale /
-// vscale, plus sigma^2 V, then the epilogue of `a`: kPlain stores O;
-// kLanczos writes p = O - beta q_prev over q_prev and forms the tile's q.p,
-// p.p, q.q per column (exact products by FMA, summed over a warp's rows by
-// shuffles and over the four row warps in order, converted to FP64 once).
-// 256 threads: warpgroup g takes columns [g TP / 2, (g + 1) TP / 2), thread
-// (warp w, lane) row 32 (w % 4) + lane.  FP64 runs at a few operations per
-// clock per SM on this part, so no FP64 arithmetic is done per row.
+// Rows [128 tile, 128 tile + 128) and columns [16 cg, 16 cg + 16) of O: the
+// S split partials of every entry added in split order (2Sum into a
+// (leading, trailing) float pair), scaled by outscale / vscale, plus
+// sigma^2 V, then
+// the epilogue of `a`: kPlain stores O; kLanczos writes p = O - beta q_prev
+// over q_prev and forms the tile's q.p, p.p, q.q per column (exact products
+// by FMA, summed over a warp's rows by shuffles and over the four row warps
+// in order, converted to FP64 once).  128 threads, one row each.  FP64 runs
+// at a few operations per clock per SM on this part, so no FP64 arithmetic
+// is done per row.
+constexpr int kFinCols = 16;
 template <int TP>
-__device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile) {
-    __shared__ float col_scale[TP], col_beta[TP];
-    __shared__ float2 red[4 * TP * 3];
+__device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile,
+                                               int cg) {
+    __shared__ float col_scale[kFinCols], col_beta[kFinCols];
+    __shared__ float2 red[4 * kFinCols * 3];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid < TP) {
-        const bool in = tid < a.T - c0;
-        col_scale[tid] = in ? a.s / p.vscale[c0 + tid] : 0.f;    // exact: vscale is a power of two
-        col_beta[tid] = (in && a.mode == kLanczos) ? (float)a.beta[c0 + tid] : 0.f;
+    const int cbeg = cg * kFinCols, cend = min(cbeg + kFinCols, a.T - c0);
+    if (cbeg >= cend) return;                             // columns past T: nothing to do
+    if (tid < kFinCols) {
+        const int cl = cbeg + tid;
+        const bool in = cl < cend;
+        col_scale[tid] = in ? a.s / p.vscale[c0 + cl] : 0.f;    // exact: vscale is a power of two
+        col_beta[tid] = (in && a.mode == kLanczos) ? (float)a.beta[c0 + cl] : 0.f;
     }
     __syncthreads();
     const int S = p.nsplit;
-    const float2* part = p.part + (int64_t)tile * S * TP * kTcBM;
+    const float* part = p.part + (int64_t)tile * S * TP * kTcBM;
     constexpr int CB = 8;
-    const int g = warp >> 2, wl = warp & 3, r = 32 * wl + lane;
+    const int r = tid;
     const int64_t i = tile * kTcBM + r;
     const bool row_in = i < a.N;
-    const int cbeg = g * (TP / 2), cend = min(cbeg + TP / 2, a.T - c0);
 #pragma unroll 1
     for (int cb = cbeg; cb < cend; cb += CB) {
         // All loads of a batch of CB columns are issued before any use.
@@ -693,11 +700,7 @@ __device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<
             h[u] = 0.f;
             l[u] = 0.f;
             if (in)
-                for (int sp = 0; sp < S; ++sp) {
-                    const float2 v2 = __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r]);
-                    two_sum_into(h[u], l[u], v2.x);
-                    l[u] += v2.y;
-                }
+                for (int sp = 0; sp < S; ++sp) two_sum_into(h[u], l[u], __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r]));
             const int64_t idx = (int64_t)(c0 + cl) * a.ldv + i;
             v[u] = in ? a.V[idx] : 0.f;
             qp[u] = (in && a.mode == kLanczos) ? a.qprev[idx] : 0.f;
@@ -708,14 +711,14 @@ __device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<
             if (cl >= cend) break;
             const int c = c0 + cl;
             const int64_t idx = (int64_t)c * a.ldv + i;
-            const float sc = col_scale[cl];
+            const float sc = col_scale[cl - cbeg];
             float o = fmaf(h[u], sc, l[u] * sc);
             o += a.noise * v[u];
             if (a.mode == kPlain) {
                 if (row_in) a.out[(int64_t)c * a.ldo + i] = o;
                 continue;
             }
-            const float pv = row_in ? o - col_beta[cl] * qp[u] : 0.f;
+            const float pv = row_in ? o - col_beta[cl - cbeg] * qp[u] : 0.f;
             a.qprev[idx] = pv;
             float sh[3], sl[3];
             const float fa[3] = {v[u], pv, v[u]}, fb[3] = {pv, pv, v[u]};
@@ -736,30 +739,30 @@ __device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<
             }
             if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) red[(wl * TP + cl) * 3 + k] = make_float2(sh[k], sl[k]);
+                for (int k = 0; k < 3; ++k) red[(warp * kFinCols + cl - cbeg) * 3 + k] = make_float2(sh[k], sl[k]);
             }
         }
     }
     if (a.mode != kLanczos) return;
     __syncthreads();
-    const int ncol = min(TP, a.T - c0);
+    const int ncol = cend - cbeg;
     for (int q = tid; q < 3 * ncol; q += blockDim.x) {
         const int cl = q / 3, k = q - 3 * cl;
         float hs = red[cl * 3 + k].x, ls = red[cl * 3 + k].y;
 #pragma unroll
         for (int w = 1; w < 4; ++w) {
-            const float2 v2 = red[(w * TP + cl) * 3 + k];
+            const float2 v2 = red[(w * kFinCols + cl) * 3 + k];
             two_sum_into(hs, ls, v2.x);
             ls += v2.y;
         }
-        a.partials[((int64_t)tile * a.T + c0 + cl) * 3 + k] = (double)hs + (double)ls;
+        a.partials[((int64_t)tile * a.T + c0 + cbeg + cl) * 3 + k] = (double)hs + (double)ls;
     }
 }
 
 template <int TP>
-__global__ void __launch_bounds__(256) tc_finish_kernel(TcPoints p, MvmArgs<float> a, int c0) {
+__global__ void __launch_bounds__(128) tc_finish_kernel(TcPoints p, MvmArgs<float> a, int c0) {
     if (a.stop && *a.stop) return;
-    tc_finish_body<TP>(p, a, c0, blockIdx.x);
+    tc_finish_body<TP>(p, a, c0, blockIdx.x / (TP / kFinCols), blockIdx.x % (TP / kFinCols));
 }
 
 // ------------------------------------------------------ batched problems --
@@ -780,9 +783,9 @@ __global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProbl
     mvm_tc_body<KT, TP, HALF>(sp, sa, 0, local / sp.nsplit, local % sp.nsplit);
 }
 
-// Block b finishes row tile `local` of problem pb (item b of the list).
+// Block b finishes item `local` (row tile x 16-column group) of problem pb.
 template <int TP>
-__global__ void __launch_bounds__(256) batched_tc_finish_kernel(const BatchProblem* probs, DevList L, int parity) {
+__global__ void __launch_bounds__(128) batched_tc_finish_kernel(const BatchProblem* probs, DevList L, int parity) {
     int pb, local;
     if (!list_item(L, blockIdx.x, pb, local)) return;
     __shared__ TcPoints sp;
@@ -793,7 +796,7 @@ __global__ void __launch_bounds__(256) batched_tc_finish_kernel(const BatchProbl
     }
     __syncthreads();
     if (sa.stop && *sa.stop) return;
-    tc_finish_body<TP>(sp, sa, 0, local);
+    tc_finish_body<TP>(sp, sa, 0, local / (TP / kFinCols), local % (TP / kFinCols));
 }
 
 // One block per problem: centre of the points, unit V scales, cleared
@@ -845,7 +848,7 @@ cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaSt
     mvm_tc_kernel<KT, TP, HALF><<<(unsigned)(a.Npad / kTcBM * p.nsplit), 384, smem, st>>>(p, a, c0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    tc_finish_kernel<TP><<<(unsigned)(a.Npad / kTcBM), 256, 0, st>>>(p, a, c0);
+    tc_finish_kernel<TP><<<(unsigned)(a.Npad / kTcBM * (TP / kFinCols)), 128, 0, st>>>(p, a, c0);
     return cudaGetLastError();
 }
 
@@ -917,7 +920,7 @@ size_t tc_points_bytes(int64_t Npad, int T, int max_split) {
     const size_t pts = (size_t)Npad * kTcRowBytes;
     const size_t vb = (size_t)(Npad / kTcBN) * 2 * TP * 128;
     const int S = tc_nsplit(Npad, max_split);
-    const size_t part = (size_t)(Npad / kTcBM) * S * tc_group_t(T) * kTcBM * 2 * sizeof(float) + 256;
+    const size_t part = (size_t)(Npad / kTcBM) * S * tc_group_t(T) * kTcBM * sizeof(float) + 256;
     return 2 * pts + vb + 256 * 4 + (size_t)TP * sizeof(float) + 16 * sizeof(double) + 256 + part;
 }
 
@@ -940,7 +943,7 @@ TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int ma
     p.mean = reinterpret_cast<double*>(take(16 * sizeof(double)));
     p.err = reinterpret_cast<int*>(take(sizeof(int)));
     p.nsplit = tc_nsplit(Npad, max_split);
-    p.part = reinterpret_cast<float2*>(take((size_t)(Npad / kTcBM) * p.nsplit * tc_group_t(T) * kTcBM * sizeof(float2)));
+    p.part = reinterpret_cast<float*>(take((size_t)(Npad / kTcBM) * p.nsplit * tc_group_t(T) * kTcBM * sizeof(float)));
     return p;
 }
 
@@ -1068,8 +1071,8 @@ cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, boo
 cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, DevList L, int blocks,
                                      cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    if (TP == 32) batched_tc_finish_kernel<32><<<blocks, 256, 0, st>>>(probs, L, parity);
-    else if (TP == 64) batched_tc_finish_kernel<64><<<blocks, 256, 0, st>>>(probs, L, parity);
+    if (TP == 32) batched_tc_finish_kernel<32><<<blocks, 128, 0, st>>>(probs, L, parity);
+    else if (TP == 64) batched_tc_finish_kernel<64><<<blocks, 128, 0, st>>>(probs, L, parity);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -20,7 +20,7 @@ struct TcPoints {
     float* vscale = nullptr;   // power-of-two scale per column of V      [TP]
     double* mean = nullptr;    // centre of the points                    [16]
     int* err = nullptr;        // set to 1 if a bounded wait gave up
-    float2* part = nullptr;    // partial sums as (leading, trailing) pairs [row tile][split][TP][128]
+    float* part = nullptr;     // per-CTA column sums, rounded to float   [row tile][split][TP][128]
     int nsplit = 1;            // CTAs per row tile, each over a contiguous range of K's columns
     int narrow = 0;            // 1: at most 8 augmented features (d <= 6), so only the first K-core
                                // of every chunk is non-zero and S takes two MMAs instead of three
