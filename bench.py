@@ -203,17 +203,18 @@ def roofline_tc(W, t_launch_ms, dev, pk):
     # One kernel MVM on tensor cores.  Algorithmic work per kernel entry:
     # 2T flops of the product with V plus 2(d+2) flops of the augmented
     # distance (norm expansion), 1 SFU exp2 (RBF; + sqrt for Matern-5/2).
-    # The FP16 hi/lo operand split executes three products for each: per
-    # entry 3 (2 TP + 2 * 16) tensor flops with TP = T rounded to the launch
-    # group and K = 16 for the distance.  The tensor pipe is the binding
-    # resource (the SFU rate is 2.6x higher), so the line reports the tensor
+    # The FP16 hi/lo operand split executes three products for the product
+    # with V (3 x 2 TP flops per entry, TP = T rounded to the launch group)
+    # and two (d <= 6: 8 augmented features fill half of a K = 16 chunk) or
+    # three K = 16 products for the distance.  The line reports the tensor
     # roofline; the executed-flop and SFU fractions are given beside it.
     N, T, d = W.n, W.t, W.d
     entries = float(N) * N
     secs = t_launch_ms * 1e-3
     alg = entries * (2 * T + 2 * (d + 2)) / secs / 1e12
     tp = 32 if T <= 32 else -(-T // 64) * 64
-    executed = entries * 3 * (2 * tp + 2 * 16) / secs / 1e12
+    s_products = 2 if d + 2 <= 8 else 3
+    executed = entries * (3 * 2 * tp + s_products * 2 * 16) / secs / 1e12
     # The MVM is timed inside a seconds-long solve: the sustained measured
     # BF16 rate is the denominator (the burst rate is reported beside it).
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
