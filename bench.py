@@ -199,6 +199,12 @@ def device_peaks():
     return res
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one in-solve
+# launch of mvm_tc_kernel, from one single-pass ncu capture of the default
+# command on this workload; kept only while the kernel is unchanged since.
+MVM_TC_DRAM_BYTES = {"rbf_n50000_d6_t64_q12": 22.48e6 + 0.136e6}
+
+
 def roofline_tc(W, t_launch_ms, dev, pk):
     # One kernel MVM on tensor cores.  Algorithmic work per kernel entry:
     # 2T flops of the product with V plus 2(d+2) flops of the augmented
@@ -223,7 +229,8 @@ def roofline_tc(W, t_launch_ms, dev, pk):
     sfu_rate = entries * sfu_per_entry / secs
     sfu_peak = dev.get("sfu_ex2_per_s")
     return {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s",
-            "frac": alg / peak if peak else None, "traffic": None,
+            "frac": alg / peak if peak else None, "traffic": MVM_TC_DRAM_BYTES.get(W.name),
+            "traffic_unit": "bytes per launch",
             "kernel": "mvm_tc_kernel (tcgen05 on-the-fly kernel MVM, FP16 hi/lo split operands)",
             "peak_source": "measured cuBLAS BF16 dense rate, sustained (MEASURED_PEAKS.json), taken for FP16 "
                            "(same nominal rate)",
