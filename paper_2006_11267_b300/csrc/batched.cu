@@ -113,7 +113,7 @@ __global__ void batched_bounds_nodes_kernel(const BatchProblem* probs, int Q, do
     bounds_nodes_body<float>(s, bp.nodes, Q, bp.noise, lmax_margin, lmin_div, 0, 0);
 }
 
-__global__ void __launch_bounds__(256, 2) batched_step_kernel(const BatchProblem* probs, int j, int final_pass,
+__global__ void __launch_bounds__(256, 3) batched_step_kernel(const BatchProblem* probs, int j, int final_pass,
                                                            DevList L) {
     int p, local;
     if (!list_item(L, blockIdx.x, p, local)) return;

@@ -51,10 +51,22 @@ bool device_accessible(const void* p) {
 
 int dim_pad(int d) { return (d + 3) / 4 * 4; }
 
+// Row chunks per column of the recurrence (its grid is chunks x T blocks):
+// the grid should fill whole waves of resident blocks, so among one to three
+// waves the chunk count with the best fill is taken (a further wave only for
+// at least 2 % more fill; every block also re-reads its column's partial
+// sums), at most Npad / 1024 chunks.
 void choose_chunks(int64_t Npad, int T, int* nchunks, int64_t* rpc) {
     const int64_t max_chunks = std::max<int64_t>(1, Npad / 1024);
-    const int64_t target = (4 * 148 + T - 1) / T;
-    const int64_t ch = std::min<int64_t>(std::max<int64_t>(1, target), max_chunks);
+    const int64_t W = step_blocks_per_wave();
+    int64_t ch = 1;
+    double best_fill = -1.0;
+    for (int64_t m = 1; m <= 3; ++m) {
+        const int64_t c = std::min<int64_t>(std::max<int64_t>(1, m * W / T), max_chunks);
+        const int64_t blocks = c * T;
+        const double fill = (double)blocks / (double)(((blocks + W - 1) / W) * W);
+        if (fill > best_fill + 0.02) { best_fill = fill; ch = c; }
+    }
     const int64_t r = round_up((Npad + ch - 1) / ch, kRowPad);
     *rpc = r;
     *nchunks = (int)((Npad + r - 1) / r);

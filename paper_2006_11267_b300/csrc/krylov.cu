@@ -39,8 +39,10 @@ __global__ void __launch_bounds__(256) init_state_kernel(KrylovState<R> s) {
     init_state_body<R>(s, blockIdx.x, blockIdx.y);
 }
 
+// Three blocks per SM (at most 85 registers): the vector update is HBM-bound
+// and needs the resident threads more than registers.
 template <typename R>
-__global__ void __launch_bounds__(256, 2) msminres_step_kernel(KrylovState<R> s, int j, int final_pass) {
+__global__ void __launch_bounds__(256, 3) msminres_step_kernel(KrylovState<R> s, int j, int final_pass) {
     msminres_step_body<R>(s, j, final_pass, blockIdx.x, blockIdx.y);
 }
 
@@ -91,6 +93,23 @@ cudaError_t launch_init_state(const KrylovState<R>& s, cudaStream_t st) {
     init_state_kernel<R><<<dim3(s.nchunks, s.T), 256, 0, st>>>(s);
     return cudaGetLastError();
 }
+// Resident recurrence blocks on the whole GPU (row chunks are sized to it).
+int step_blocks_per_wave() {
+    static int w = 0;
+    if (w == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msminres_step_kernel<float>, 256, 0) != cudaSuccess ||
+            sms <= 0 || per_sm <= 0) {
+            cudaGetLastError();
+            return 148 * 3;
+        }
+        w = sms * per_sm;
+    }
+    return w;
+}
+
 template <typename R>
 cudaError_t launch_msminres_step(const KrylovState<R>& s, int j, bool final_pass, cudaStream_t st) {
     msminres_step_kernel<R><<<dim3(final_pass ? 1 : s.nchunks, s.T), 256, 0, st>>>(s, j, final_pass ? 1 : 0);

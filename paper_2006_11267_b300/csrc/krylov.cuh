@@ -93,6 +93,8 @@ template <typename R>
 cudaError_t launch_init_state(const KrylovState<R>& s, cudaStream_t st);
 template <typename R>
 cudaError_t launch_msminres_step(const KrylovState<R>& s, int j, bool final_pass, cudaStream_t st);
+// Recurrence blocks resident at once on the device (SMs x blocks per SM).
+int step_blocks_per_wave();
 template <typename R>
 cudaError_t launch_combine(const KrylovState<R>& s, R* out, cudaStream_t st);
 template <typename R>

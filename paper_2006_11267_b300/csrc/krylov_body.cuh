@@ -233,7 +233,7 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
         // FP32: four consecutive rows per thread with 16-byte loads and
         // stores (row chunks and the padded leading dimension are multiples
         // of 128, so a group of four never straddles either).
-        constexpr int QB = 8;
+        constexpr int QB = 4;                  // shifts whose directions are loaded together
         const float4* q4 = reinterpret_cast<const float4*>(q_j);
         float4* p4 = reinterpret_cast<float4*>(pbuf);
         float4* y4 = reinterpret_cast<float4*>(y);
@@ -242,6 +242,10 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
         const float4* dp4 = reinterpret_cast<const float4*>(d_prev);
         float4* do4 = reinterpret_cast<float4*>(d_old);
         const int64_t ds4 = dstride / 4;
+        // ||a_j||^2 of this thread's rows in FP32 (a few dozen terms; the
+        // stopping rule needs a few digits), converted to FP64 once: FP64
+        // runs at a few operations per clock per SM on this part.
+        float ysqf = 0.f;
         for (int64_t i4 = i0 / 4 + tid; i4 < i1 / 4; i4 += 256) {
             const float4 qv = q4[i4];
             const float4 pv = p4[i4];
@@ -293,12 +297,13 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
                 yl[e] = la[e] + err;
                 const float yv = sum + yl[e];
                 const float est = s.op == kOpSqrtIdentity ? (float)sumw * ba[e] - yv : yv;
-                ysq += (double)est * (double)est;
+                ysqf = fmaf(est, est, ysqf);
             }
             p4[i4] = make_float4(pn[0], pn[1], pn[2], pn[3]);
             y4[i4] = make_float4(ys[0], ys[1], ys[2], ys[3]);
             l4[i4] = make_float4(yl[0], yl[1], yl[2], yl[3]);
         }
+        ysq = (double)ysqf;
     } else {
         constexpr int QB = 8;                  // shifts whose directions are loaded together
         for (int64_t i = i0 + tid; i < i1; i += 256) {
