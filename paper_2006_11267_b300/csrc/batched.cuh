@@ -105,17 +105,19 @@ cudaError_t launch_batched_step(const BatchProblem* probs, int j, bool final_pas
 cudaError_t launch_batched_summary(const BatchProblem* probs, int final_j, double* packed, DevList L, int blocks,
                                    cudaStream_t st);
 // Tensor-core batches (mvm_tc.cu): operand preparation (points centre and
-// split operands; unit V scales; split-K counters), the per-iteration V
-// split, and the MVM over a list of (problem, row tile x split) items.
+// split operands; unit V scales), the per-iteration V split, and the MVM
+// over a list of (problem, row tile x split) items.  `pre` selects the
+// pre-pass arguments (one column, a 32-column group) instead of the
+// main-loop ones.
 cudaError_t launch_batched_tc_mean(const BatchProblem* probs, DevList one, int blocks, cudaStream_t st);
 cudaError_t launch_batched_tc_points(const BatchProblem* probs, DevList rows256, int blocks, bool half,
                                      cudaStream_t st);
 cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevList L, int blocks, bool half,
-                                    cudaStream_t st);
-cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, DevList L,
-                                  int blocks, cudaStream_t st);
+                                    bool pre, cudaStream_t st);
+cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, bool pre,
+                                  DevList L, int blocks, cudaStream_t st);
 // Sum the split partials of every row tile and apply the MVM epilogue.
-cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, DevList L, int blocks,
+cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, bool pre, DevList L, int blocks,
                                      cudaStream_t st);
 // Set the kernels' shared-memory attributes (before any stream capture).
 cudaError_t prepare_batched_tc_mvm(int TP, bool half);

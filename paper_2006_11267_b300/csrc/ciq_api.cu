@@ -217,7 +217,10 @@ Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool pre
     p.stored = sizeof(R) == 4 && o.mvm == CIQ_MVM_STORED;
     p.nparts = tc ? (int)tc_row_tiles(p.Npad)
                   : p.stored ? (int)stored_row_tiles(p.Npad, T) : (int)mvm_simt_row_tiles<R>(p.Npad, T);
-    p.nparts1 = p.stored ? (int)stored_row_tiles(p.Npad, 1) : (int)mvm_simt_row_tiles<R>(p.Npad, 1);
+    // The pre-pass (one column) runs on the solve's MVM path: tensor cores,
+    // stored K or CUDA cores.
+    p.nparts1 = tc ? (int)tc_row_tiles(p.Npad)
+                   : p.stored ? (int)stored_row_tiles(p.Npad, 1) : (int)mvm_simt_row_tiles<R>(p.Npad, 1);
     choose_chunks(p.Npad, T, &p.nchunks, &p.rpc);
     choose_chunks(p.Npad, 1, &p.nchunks1, &p.rpc1);
     p.prepass = prepass;
@@ -273,7 +276,7 @@ cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options
         a.V = (j & 1) ? p.LA : p.LB;
         a.qprev = (j & 1) ? p.LB : p.LA;
         a.beta = p.bpar + (j & 1);
-        if ((e = p.stored ? launch_mvm(p, a, true, st) : launch_mvm_simt(a, st)) != cudaSuccess) return e;
+        if ((e = (p.stored || p.tc) ? launch_mvm(p, a, true, st) : launch_mvm_simt(a, st)) != cudaSuccess) return e;
         if ((e = launch_lanczos_step(ls, j, st)) != cudaSuccess) return e;
     }
     return launch_bounds_nodes(ls, p.nodes, Q, k.noise, o.lmax_margin, o.lmin_div, st);
@@ -440,7 +443,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             launches += 1;
         } else {
             CIQ_TRY(run_prepass(p, *kern, o, Q, startd, st));
-            launches += 3 + 2 * p.JL;
+            launches += 3 + p.JL * (1 + (p.tc ? 4 : 1));   // tensor cores: V scale, V split, product, finish
         }
         if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_pre1, st));
         MvmArgs<R> a = mvm_args(p, *kern);
@@ -682,6 +685,8 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     }
     const int groups = (T + batch_mvm_group(T) - 1) / batch_mvm_group(T);
     std::vector<BatchProblem> hp(P);
+    // Tensor-core pre-pass: MVM items per kernel type, V split and finish.
+    HostList pre_tc[2], pre_tc_split, pre_tc_fin;
     HostList prep, one, init, pre, pre_one, given_one, fin, comb, rows256, pre_mvm[kBatchClasses],
         dyn[kBatchDynLists];
     int64_t biggest = 0;
@@ -719,12 +724,18 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         } else {
             pre.add(p, pl.nchunks1);
             pre_one.add(p, 1);
-            pre_mvm[b.cls].add(p, b.pre_tiles);
+            if (tc) {
+                pre_tc[probs[p].kern.type].add(p, (int64_t)(pl.Npad / kTcBM) * pl.tcp.nsplit);
+                pre_tc_split.add(p, (pl.Npad / 8 * 32 + 255) / 256);
+                pre_tc_fin.add(p, (pl.Npad / kTcBM) * (32 / 16));
+            } else {
+                pre_mvm[b.cls].add(p, b.pre_tiles);
+            }
         }
     }
     // Item totals index blocks as int.
     {
-        int64_t sums[6] = {0, 0, 0, 0, 0, 0};
+        int64_t sums[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int p = 0; p < P; ++p) {
             const Plan<float>& pl = plans[p];
             sums[0] += (pl.Npad * pl.dp + 255) / 256;
@@ -733,6 +744,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
             sums[3] += (int64_t)pl.nchunks * T;
             sums[4] += hp[p].pre_tiles;
             sums[5] += pl.nchunks1;
+            sums[6] += (pl.Npad / kTcBM) * std::max(pl.tcp.nsplit, 2);
         }
         for (int64_t v : sums)
             if (v >= (int64_t)INT32_MAX) return CIQ_ERR_UNSUPPORTED;
@@ -740,6 +752,9 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     (void)biggest;
     std::vector<HostList*> all_lists = {&prep, &one, &init, &pre, &pre_one, &given_one, &fin, &comb, &rows256};
     for (auto& l : pre_mvm) all_lists.push_back(&l);
+    for (auto& l : pre_tc) all_lists.push_back(&l);
+    all_lists.push_back(&pre_tc_split);
+    all_lists.push_back(&pre_tc_fin);
     for (auto& l : dyn) all_lists.push_back(&l);
     const size_t list_ints = (size_t)2 * P + 2;
     const size_t tables = round_up((int64_t)(sizeof(BatchProblem) * P), kAlign) +
@@ -845,7 +860,19 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         if (pre.total() > 0) {
             CIQ_TRY(setup(kBatchPreInitA, pre));
             CIQ_TRY(setup(kBatchPreInitB, pre));
+            // Tensor-core batches run the pre-pass MVM on tensor cores too, as
+            // a single solve does (one column in a 32-column group).
+            if (tc) CIQ_TRY(prepare_batched_tc_mvm(32, half));
             for (int j = 1; j <= o.lanczos_iters; ++j) {
+                if (tc) {
+                    CIQ_TRY(launch_batched_tc_split(probs_d, j & 1, L(pre_tc_split), pre_tc_split.total(), half, true,
+                                                    st));
+                    for (int kt = 0; kt < 2; ++kt)
+                        CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, 32, half, j & 1, true, L(pre_tc[kt]),
+                                                      pre_tc[kt].total(), st));
+                    CIQ_TRY(launch_batched_tc_finish(probs_d, 32, j & 1, true, L(pre_tc_fin), pre_tc_fin.total(), st));
+                    launches += 2 + (pre_tc[0].total() > 0) + (pre_tc[1].total() > 0);
+                }
                 for (int c = 0; c < kBatchClasses; ++c) {
                     if (pre_mvm[c].total() == 0) continue;
                     CIQ_TRY(launch_batched_mvm(probs_d, c, T, true, j & 1, L(pre_mvm[c]), pre_mvm[c].total(), st));
@@ -884,16 +911,17 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                     if (tc) {
                         if (grid[kListTcSplit] > 0) {
                             CIQ_TRY(launch_batched_tc_split(probs_d, jj & 1, dyn_d.l[kListTcSplit], grid[kListTcSplit],
-                                                            half, ls));
+                                                            half, false, ls));
                             ++launches;
                         }
                         for (int kt = 0; kt < 2; ++kt) {
                             if (grid[kt] == 0) continue;
-                            CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, TP, half, jj & 1, dyn_d.l[kt], grid[kt], ls));
+                            CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, TP, half, jj & 1, false, dyn_d.l[kt], grid[kt],
+                                                          ls));
                             ++launches;
                         }
                         if (grid[kListTcFinish] > 0) {
-                            CIQ_TRY(launch_batched_tc_finish(probs_d, TP, jj & 1, dyn_d.l[kListTcFinish],
+                            CIQ_TRY(launch_batched_tc_finish(probs_d, TP, jj & 1, false, dyn_d.l[kListTcFinish],
                                                              grid[kListTcFinish], ls));
                             ++launches;
                         }

@@ -770,14 +770,15 @@ __global__ void __launch_bounds__(128) tc_finish_kernel(TcPoints p, MvmArgs<floa
 // problem's operands and MVM arguments are copied to shared memory and the
 // same body runs as for one problem.
 template <int KT, int TP, bool HALF>
-__global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProblem* probs, DevList L, int parity) {
+__global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProblem* probs, DevList L, int parity,
+                                                                 int pre) {
     int pb, local;
     if (!list_item(L, blockIdx.x, pb, local)) return;
     __shared__ TcPoints sp;
     __shared__ MvmArgs<float> sa;
     if (threadIdx.x == 0) {
         sp = probs[pb].tcp;
-        sa = probs[pb].mvm[parity];
+        sa = pre ? probs[pb].pre[parity] : probs[pb].mvm[parity];
     }
     __syncthreads();
     mvm_tc_body<KT, TP, HALF>(sp, sa, 0, local / sp.nsplit, local % sp.nsplit);
@@ -785,14 +786,15 @@ __global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProbl
 
 // Block b finishes item `local` (row tile x 16-column group) of problem pb.
 template <int TP>
-__global__ void __launch_bounds__(128) batched_tc_finish_kernel(const BatchProblem* probs, DevList L, int parity) {
+__global__ void __launch_bounds__(128) batched_tc_finish_kernel(const BatchProblem* probs, DevList L, int parity,
+                                                                int pre) {
     int pb, local;
     if (!list_item(L, blockIdx.x, pb, local)) return;
     __shared__ TcPoints sp;
     __shared__ MvmArgs<float> sa;
     if (threadIdx.x == 0) {
         sp = probs[pb].tcp;
-        sa = probs[pb].mvm[parity];
+        sa = pre ? probs[pb].pre[parity] : probs[pb].mvm[parity];
     }
     __syncthreads();
     if (sa.stop && *sa.stop) return;
@@ -824,16 +826,18 @@ __global__ void __launch_bounds__(256) batched_tc_points_kernel(const BatchProbl
                          bp.tcp.ub, (int64_t)local * 256 + threadIdx.x);
 }
 
+// The pre-pass (one column) uses a 32-column group, as a single solve does.
 template <bool HALF>
-__global__ void __launch_bounds__(256) batched_tc_split_kernel(const BatchProblem* probs, DevList L, int parity) {
+__global__ void __launch_bounds__(256) batched_tc_split_kernel(const BatchProblem* probs, DevList L, int parity,
+                                                               int pre) {
     int pb, local;
     if (!list_item(L, blockIdx.x, pb, local)) return;
     const BatchProblem& bp = probs[pb];
-    const MvmArgs<float>& m = bp.mvm[parity];
+    const MvmArgs<float>& m = pre ? bp.pre[parity] : bp.mvm[parity];
     if (m.stop && *m.stop) return;
     const TcPoints& tp = bp.tcp;
-    tc_split_v_body<HALF>(m.V, m.ldv, m.T, tp.TP, tp.TP, tp.Npad, tp.vscale, tp.vblk,
-                          (int64_t)local * 256 + threadIdx.x);
+    const int tpw = pre ? 32 : tp.TP;
+    tc_split_v_body<HALF>(m.V, m.ldv, m.T, tpw, tpw, tp.Npad, tp.vscale, tp.vblk, (int64_t)local * 256 + threadIdx.x);
 }
 
 template <int KT, int TP, bool HALF>
@@ -1011,10 +1015,10 @@ cudaError_t launch_batched_tc_points(const BatchProblem* probs, DevList rows256,
 }
 
 cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevList L, int blocks, bool half,
-                                    cudaStream_t st) {
+                                    bool pre, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    if (half) batched_tc_split_kernel<true><<<blocks, 256, 0, st>>>(probs, L, parity);
-    else batched_tc_split_kernel<false><<<blocks, 256, 0, st>>>(probs, L, parity);
+    if (half) batched_tc_split_kernel<true><<<blocks, 256, 0, st>>>(probs, L, parity, pre ? 1 : 0);
+    else batched_tc_split_kernel<false><<<blocks, 256, 0, st>>>(probs, L, parity, pre ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1032,10 +1036,10 @@ cudaError_t configure_btc() {
 }
 
 template <int KT, int TP, bool HALF>
-cudaError_t launch_btc(const BatchProblem* probs, int parity, DevList L, int blocks, cudaStream_t st) {
+cudaError_t launch_btc(const BatchProblem* probs, int parity, int pre, DevList L, int blocks, cudaStream_t st) {
     cudaError_t e = configure_btc<KT, TP, HALF>();
     if (e != cudaSuccess) return e;
-    batched_tc_mvm_kernel<KT, TP, HALF><<<blocks, 384, tc_smem_bytes<TP>(), st>>>(probs, L, parity);
+    batched_tc_mvm_kernel<KT, TP, HALF><<<blocks, 384, tc_smem_bytes<TP>(), st>>>(probs, L, parity, pre);
     return cudaGetLastError();
 }
 
@@ -1046,9 +1050,10 @@ cudaError_t configure_btc_all(int TP) {
     return TP == 32 ? configure_btc<CIQ_MATERN52, 32, HALF>() : configure_btc<CIQ_MATERN52, 64, HALF>();
 }
 template <int KT, bool HALF>
-cudaError_t launch_btc_tp(const BatchProblem* probs, int TP, int parity, DevList L, int blocks, cudaStream_t st) {
-    return TP == 32 ? launch_btc<KT, 32, HALF>(probs, parity, L, blocks, st)
-                    : launch_btc<KT, 64, HALF>(probs, parity, L, blocks, st);
+cudaError_t launch_btc_tp(const BatchProblem* probs, int TP, int parity, int pre, DevList L, int blocks,
+                         cudaStream_t st) {
+    return TP == 32 ? launch_btc<KT, 32, HALF>(probs, parity, pre, L, blocks, st)
+                    : launch_btc<KT, 64, HALF>(probs, parity, pre, L, blocks, st);
 }
 }  // namespace
 
@@ -1057,22 +1062,24 @@ cudaError_t prepare_batched_tc_mvm(int TP, bool half) {
     return half ? configure_btc_all<true>(TP) : configure_btc_all<false>(TP);
 }
 
-cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, DevList L,
-                                  int blocks, cudaStream_t st) {
+cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, bool pre,
+                                  DevList L, int blocks, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
     if (TP != 32 && TP != 64) return cudaErrorInvalidValue;
+    const int pr = pre ? 1 : 0;
     if (kt == CIQ_RBF)
-        return half ? launch_btc_tp<CIQ_RBF, true>(probs, TP, parity, L, blocks, st)
-                    : launch_btc_tp<CIQ_RBF, false>(probs, TP, parity, L, blocks, st);
-    return half ? launch_btc_tp<CIQ_MATERN52, true>(probs, TP, parity, L, blocks, st)
-                : launch_btc_tp<CIQ_MATERN52, false>(probs, TP, parity, L, blocks, st);
+        return half ? launch_btc_tp<CIQ_RBF, true>(probs, TP, parity, pr, L, blocks, st)
+                    : launch_btc_tp<CIQ_RBF, false>(probs, TP, parity, pr, L, blocks, st);
+    return half ? launch_btc_tp<CIQ_MATERN52, true>(probs, TP, parity, pr, L, blocks, st)
+                : launch_btc_tp<CIQ_MATERN52, false>(probs, TP, parity, pr, L, blocks, st);
 }
 
-cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, DevList L, int blocks,
+cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, bool pre, DevList L, int blocks,
                                      cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    if (TP == 32) batched_tc_finish_kernel<32><<<blocks, 128, 0, st>>>(probs, L, parity);
-    else if (TP == 64) batched_tc_finish_kernel<64><<<blocks, 128, 0, st>>>(probs, L, parity);
+    const int pr = pre ? 1 : 0;
+    if (TP == 32) batched_tc_finish_kernel<32><<<blocks, 128, 0, st>>>(probs, L, parity, pr);
+    else if (TP == 64) batched_tc_finish_kernel<64><<<blocks, 128, 0, st>>>(probs, L, parity, pr);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
