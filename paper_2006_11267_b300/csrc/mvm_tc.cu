@@ -660,102 +660,105 @@ __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<floa
 // Rows [128 tile, 128 tile + 128) and columns [16 cg, 16 cg + 16) of O: the
 // S split partials of every entry added in split order (2Sum into a
 // (leading, trailing) float pair), scaled by outscale / vscale, plus
-// sigma^2 V, then
-// the epilogue of `a`: kPlain stores O; kLanczos writes p = O - beta q_prev
-// over q_prev and forms the tile's q.p, p.p, q.q per column (exact products
-// by FMA, summed over a warp's rows by shuffles and over the four row warps
-// in order, converted to FP64 once).  128 threads, one row each.  FP64 runs
-// at a few operations per clock per SM on this part, so no FP64 arithmetic
-// is done per row.
+// sigma^2 V, then the epilogue of `a`: kPlain stores O; kLanczos writes
+// p = O - beta q_prev over q_prev and forms the tile's q.p, p.p, q.q per
+// column.  128 threads: thread t takes column t / 8 and the 16 consecutive
+// rows 16 (t % 8) ..., loads them as float4s, sums its products (exact by
+// FMA) as float pairs and meets the other 7 threads of its column in three
+// shuffles; the pair is converted to FP64 once (FP64 runs at a few
+// operations per clock per SM on this part).
 constexpr int kFinCols = 16;
 template <int TP>
 __device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile,
                                                int cg) {
-    __shared__ float col_scale[kFinCols], col_beta[kFinCols];
-    __shared__ float2 red[4 * kFinCols * 3];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int cbeg = cg * kFinCols, cend = min(cbeg + kFinCols, a.T - c0);
     if (cbeg >= cend) return;                             // columns past T: nothing to do
-    if (tid < kFinCols) {
-        const int cl = cbeg + tid;
-        const bool in = cl < cend;
-        col_scale[tid] = in ? a.s / p.vscale[c0 + cl] : 0.f;    // exact: vscale is a power of two
-        col_beta[tid] = (in && a.mode == kLanczos) ? (float)a.beta[c0 + cl] : 0.f;
-    }
-    __syncthreads();
+    // Threads of columns past T keep their lanes in the shuffles but touch
+    // no memory (whole 8-thread groups, never a partial one).
+    const bool active = cbeg + (tid >> 3) < cend;
+    const int cl = active ? cbeg + (tid >> 3) : cbeg;    // column of the group
+    const int r0 = 16 * (tid & 7);                        // first of this thread's rows
+    const int c = c0 + cl;
+    const float sc = a.s / p.vscale[c];                   // exact: vscale is a power of two
+    const bool lanczos = a.mode == kLanczos;
+    const float bt = lanczos ? (float)a.beta[c] : 0.f;
     const int S = p.nsplit;
-    const float* part = p.part + (int64_t)tile * S * TP * kTcBM;
-    constexpr int CB = 8;
-    const int r = tid;
-    const int64_t i = tile * kTcBM + r;
-    const bool row_in = i < a.N;
-#pragma unroll 1
-    for (int cb = cbeg; cb < cend; cb += CB) {
-        // All loads of a batch of CB columns are issued before any use.
-        float h[CB], l[CB], v[CB], qp[CB];
+    const float* part = p.part + (int64_t)tile * S * TP * kTcBM + (int64_t)cl * kTcBM + r0;
+    const int64_t i0 = tile * kTcBM + r0;
+    const int64_t base = (int64_t)c * a.ldv + i0;
+    float* pdst = a.qprev;                                // p is written over q_{j-1}
+    float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
-            const int cl = cb + u;
-            const bool in = cl < cend;
-            h[u] = 0.f;
-            l[u] = 0.f;
-            if (in)
-                for (int sp = 0; sp < S; ++sp) two_sum_into(h[u], l[u], __ldcg(&part[((int64_t)sp * TP + cl) * kTcBM + r]));
-            const int64_t idx = (int64_t)(c0 + cl) * a.ldv + i;
-            v[u] = in ? a.V[idx] : 0.f;
-            qp[u] = (in && a.mode == kLanczos) ? a.qprev[idx] : 0.f;
+    for (int half = 0; half < 2 && active; ++half) {
+        // 8 rows: every load issued before any use.
+        float h[8], l[8], v[8], qp[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) { h[e] = 0.f; l[e] = 0.f; }
+        for (int sp = 0; sp < S; ++sp) {
+            const float4* src = reinterpret_cast<const float4*>(part + (int64_t)sp * TP * kTcBM + 8 * half);
+            const float4 x0 = __ldcg(src), x1 = __ldcg(src + 1);
+            const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) two_sum_into(h[e], l[e], xs[e]);
         }
+        {
+            const float4* vs = reinterpret_cast<const float4*>(a.V + base + 8 * half);
+            const float4 v0 = vs[0], v1 = vs[1];
+            v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w; v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
+        }
+        if (lanczos) {
+            const float4* qs = reinterpret_cast<const float4*>(a.qprev + base + 8 * half);
+            const float4 q0 = qs[0], q1 = qs[1];
+            qp[0] = q0.x; qp[1] = q0.y; qp[2] = q0.z; qp[3] = q0.w; qp[4] = q1.x; qp[5] = q1.y; qp[6] = q1.z; qp[7] = q1.w;
+        }
+        float o[8];
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
-            const int cl = cb + u;
-            if (cl >= cend) break;
-            const int c = c0 + cl;
-            const int64_t idx = (int64_t)c * a.ldv + i;
-            const float sc = col_scale[cl - cbeg];
-            float o = fmaf(h[u], sc, l[u] * sc);
-            o += a.noise * v[u];
-            if (a.mode == kPlain) {
-                if (row_in) a.out[(int64_t)c * a.ldo + i] = o;
-                continue;
+        for (int e = 0; e < 8; ++e) {
+            o[e] = fmaf(h[e], sc, l[e] * sc);
+            o[e] += a.noise * v[e];
+        }
+        if (!lanczos) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t i = i0 + 8 * half + e;
+                if (i < a.N) a.out[(int64_t)c * a.ldo + i] = o[e];
             }
-            const float pv = row_in ? o - col_beta[cl - cbeg] * qp[u] : 0.f;
-            a.qprev[idx] = pv;
-            float sh[3], sl[3];
-            const float fa[3] = {v[u], pv, v[u]}, fb[3] = {pv, pv, v[u]};
+            continue;
+        }
+        float pv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const bool row_in = i0 + 8 * half + e < a.N;
+            pv[e] = row_in ? o[e] - bt * qp[e] : 0.f;
+            const float fa[3] = {v[e], pv[e], v[e]}, fb[3] = {pv[e], pv[e], v[e]};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                sh[k] = fa[k] * fb[k];
-                sl[k] = fmaf(fa[k], fb[k], -sh[k]);
+                const float pr = fa[k] * fb[k];
+                two_sum_into(sh[k], sl[k], pr);
+                sl[k] += fmaf(fa[k], fb[k], -pr);
             }
+        }
+        float4* pd = reinterpret_cast<float4*>(pdst + base + 8 * half);
+        pd[0] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        pd[1] = make_float4(pv[4], pv[5], pv[6], pv[7]);
+    }
+    if (!lanczos) return;
+    // The 8 threads of a column are consecutive lanes of one warp.
 #pragma unroll
-            for (int ofs = 16; ofs > 0; ofs >>= 1) {
+    for (int ofs = 1; ofs < 8; ofs <<= 1) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, sh[k], ofs);
-                    const float ol = __shfl_xor_sync(0xffffffffu, sl[k], ofs);
-                    two_sum_into(sh[k], sl[k], oh);
-                    sl[k] += ol;
-                }
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) red[(warp * kFinCols + cl - cbeg) * 3 + k] = make_float2(sh[k], sl[k]);
-            }
+        for (int k = 0; k < 3; ++k) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh[k], ofs);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl[k], ofs);
+            two_sum_into(sh[k], sl[k], oh);
+            sl[k] += ol;
         }
     }
-    if (a.mode != kLanczos) return;
-    __syncthreads();
-    const int ncol = cend - cbeg;
-    for (int q = tid; q < 3 * ncol; q += blockDim.x) {
-        const int cl = q / 3, k = q - 3 * cl;
-        float hs = red[cl * 3 + k].x, ls = red[cl * 3 + k].y;
+    if (active && (tid & 7) == 0) {
 #pragma unroll
-        for (int w = 1; w < 4; ++w) {
-            const float2 v2 = red[(w * kFinCols + cl) * 3 + k];
-            two_sum_into(hs, ls, v2.x);
-            ls += v2.y;
-        }
-        a.partials[((int64_t)tile * a.T + c0 + cbeg + cl) * 3 + k] = (double)hs + (double)ls;
+        for (int k = 0; k < 3; ++k)
+            a.partials[((int64_t)tile * a.T + c) * 3 + k] = (double)sh[k] + (double)sl[k];
     }
 }
 
