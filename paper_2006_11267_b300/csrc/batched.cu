@@ -122,21 +122,58 @@ __global__ void __launch_bounds__(256, 3) batched_step_kernel(const BatchProblem
     msminres_step_body<float>(s, j, final_pass, local % nbx, local / nbx);
 }
 
+// Largest eigenvalue of the symmetric tridiagonal (diag[0..J), off[1..J))
+// by multisection over one warp: each round the 32 lanes take Sturm counts
+// at 32 interior points of the bracket, which shrinks 33-fold, until it
+// stops shrinking (FP64 resolution), about 11 rounds instead of the ~60
+// serial bisection steps of tridiag_extreme (each step a pass of J FP64
+// divisions; J reaches the solve's iteration count).
+__device__ double tridiag_max_warp(const double* diag, const double* off, int J) {
+    const int lane = threadIdx.x & 31;
+    double lo = 1e300, hi = -1e300;
+    for (int k = lane; k < J; k += 32) {
+        const double r = (k > 0 ? fabs(off[k]) : 0.0) + (k + 1 < J ? fabs(off[k + 1]) : 0.0);
+        lo = fmin(lo, diag[k] - r);
+        hi = fmax(hi, diag[k] + r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    for (int round = 0; round < 24; ++round) {
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const unsigned above = __ballot_sync(0xffffffffu, sturm_count(diag, off, J, x) == J);
+        const int first = above ? __ffs(above) - 1 : 32;        // first point above every eigenvalue
+        const double nhi = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
+        const double nlo = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
+        const double new_hi = first < 32 ? nhi : hi;
+        const double new_lo = first > 0 ? nlo : lo;
+        if (!(new_hi < hi || new_lo > lo)) break;
+        lo = new_lo;
+        hi = new_hi;
+    }
+    return 0.5 * (lo + hi);
+}
+
 __global__ void batched_summary_kernel(const BatchProblem* probs, int final_j, double* packed, DevList L) {
     int p, local;
     if (!list_item(L, blockIdx.x, p, local)) return;
     const BatchProblem& bp = probs[p];
     const KrylovState<float> s = bp.ks;
     summary_body<float>(s, final_j, 0, 0);
+    // The largest Ritz value of column 0's msMINRES tridiagonal (the
+    // spectral check of learned bounds), by the whole warp.
+    double th = 0.0;
+    if (s.tri) {
+        __syncwarp();
+        const int J = s.iters[0];
+        if (J >= 1) th = tridiag_max_warp(s.tri, s.tri + s.jmax + 1, J);
+    }
     if (threadIdx.x != 0) return;
     double* dst = packed + (int64_t)p * kSummaryStride;
     for (int k = 0; k < 8; ++k) dst[k] = s.summary[k];
     for (int k = 0; k < kNodeCount; ++k) dst[8 + k] = bp.nodes[k];
-    double th = 0.0;
-    if (s.tri) {
-        const int J = s.iters[0];
-        if (J >= 1) th = tridiag_extreme(s.tri, s.tri + s.jmax + 1, J, true);
-    }
     dst[8 + kNodeCount] = th;
 }
 
