@@ -152,3 +152,33 @@ def test_learned_batch_matches_prepass_batch_and_saves_work():
         ep = np.linalg.norm(op.cpu().numpy() - truth) / np.linalg.norm(truth)
         worst_l, worst_p = max(worst_l, el), max(worst_p, ep)
     assert worst_l <= max(2.0 * worst_p, 1e-3)
+
+
+def test_learned_spectral_check_value_is_the_largest_ritz_value():
+    # With learned bounds the solve records column 0's msMINRES tridiagonal
+    # and reports its largest eigenvalue (warp multisection over Sturm
+    # counts), which the spectral check compares with the lambda_max used.
+    # After ~100 Lanczos steps the largest Ritz value equals lambda_max(K) to
+    # within the FP16-split MVM's accuracy, so it is judged by the FP64
+    # eigendecomposition of K.  An untrained network with a wide margin
+    # (e^4) keeps the predicted bounds valid, so no problem falls back.
+    probs = small_batch(55, 5, nmax=700)
+    F, Y, _ = learned.label_problems(probs, 8, 1e-6, max_iter=1000)
+    theta = torch.zeros(P.CIQ_MLP_PARAMS, device=DEV)
+    P.ciq_mlp_normaliser(F, Y, theta)
+    P.ciq_mlp_init(theta, 5)
+    _, infos = P.ciq_sqrt_batched_learned(probs, 8, 1e-6, theta, 4.0, max_iter=1000)
+    long_runs = 0
+    for pr, info in zip(probs, infos):
+        assert not info["fallback"]
+        k = pr["kernel"]
+        K = kernels.dense_K(pr["X"].cpu().numpy().astype(np.float64), k.type, k.lengthscale, k.outputscale, k.noise)
+        lam = np.linalg.eigvalsh(K)[-1]
+        # Ritz values lie in the spectrum; a short run (a well-conditioned
+        # problem) need not have reached lambda_max yet.
+        assert info["ritz_max_solve"] <= lam * (1 + 1e-5)
+        assert info["ritz_max_solve"] <= info["lmax_used"]
+        if info["iters"] >= 30:
+            long_runs += 1
+            assert abs(info["ritz_max_solve"] - lam) <= 1e-4 * lam, (info["ritz_max_solve"], lam)
+    assert long_runs >= 2
