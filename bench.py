@@ -73,7 +73,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
-    ap.add_argument("--workload", default="thompson50k", choices=["thompson50k", "batched512", "precision200k", "learned"],
+    ap.add_argument("--workload", default="thompson50k",
+                    choices=["thompson50k", "batched512", "precision200k", "learned", "stored"],
                     help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
                          "the 200,000-point Matern precision sweep; learned: train the bound predictor on "
                          "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones")
@@ -544,6 +545,87 @@ def run_batched(args):
     return 0
 
 
+def run_stored(args):
+    """Stored-K MVM (the explicit-matrix case of Sec. 3.3): K = K_XX + sigma^2 I
+    of the 50,000-point RBF workload and of its 80,000-point extension formed
+    once in HBM (FP32: 10.0 and 25.6 GB), then streamed by every MVM.  A
+    column group of T <= 8 reads K once per MVM with float4 loads and is
+    HBM-bound: 4 Npad^2 bytes against the measured copy rate.  T = 64 runs
+    the register-tiled FP32 product (32 flops per byte of K: FP32-FMA-bound,
+    reported against the derived FP32 rate).  Beside it the headline solve
+    with the stored MVM (FP32) for comparison with the on-the-fly paths."""
+    import torch
+
+    import paper_2006_11267_b300 as P
+
+    torch.cuda.set_device(0)
+    pk, pk_kind = peaks()
+    W = WORKLOAD
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sizes = {}
+    for n in (50000, 80000):
+        npad = -(-n // 128) * 128
+        X = torch.from_numpy(ci.points(W.seed, n, W.d).astype(np.float32)).cuda()
+        K = torch.empty((npad, npad), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        e0.record()
+        P.ciq_kernel_matrix(X, k, K)
+        e1.record()
+        torch.cuda.synchronize()
+        form_ms = e0.elapsed_time(e1)
+        res = {"form_ms": form_ms, "K_GB": 4.0 * npad * npad / 1e9}
+        for t in (1, 8, 64):
+            V = torch.from_numpy(ci.rhs(W.seed + 3, n, t).astype(np.float32)).cuda()
+            out = torch.empty_like(V)
+            for _ in range(2):
+                P.ciq_stored_mvm(K, V, out)
+            torch.cuda.synchronize()
+            reps = 5
+            e0.record()
+            for _ in range(reps):
+                P.ciq_stored_mvm(K, V, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            nbytes = 4.0 * npad * npad + 4.0 * 2 * t * n
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            flops = 2.0 * npad * npad * t
+            res[f"t{t}"] = {"ms": ms, "GB_s": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
+                            "TFLOP_s": flops / (ms * 1e-3) / 1e12}
+        sizes[str(n)] = res
+        del K
+        torch.cuda.empty_cache()
+    # The headline solve with the stored MVM (K of 10 GB formed inside the call).
+    n = W.n
+    X = torch.from_numpy(ci.points(W.seed, n, W.d).astype(np.float32)).cuda()
+    B = torch.from_numpy(ci.rhs(W.seed, n, W.t).astype(np.float32)).cuda()
+    P.ciq_sqrt(X, k, B, W.q, 1e-3, stop_rule="errbound", max_iter=4000, mvm="stored")
+    torch.cuda.synchronize()
+    e0.record()
+    _, info = P.ciq_sqrt(X, k, B, W.q, 1e-3, stop_rule="errbound", max_iter=4000, mvm="stored")
+    e1.record()
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    fp32_rate = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    head = sizes["50000"]["t8"]
+    line = {"metric": "stored-K MVM HBM GB/s (T=8 column group, N=50,000)", "value": head["GB_s"], "unit": "GB/s",
+            "n_gpus": 1, "steps": 5, "warmup": 2, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"stored_{W.name}", "N": [50000, 80000], "T": [1, 8, 64], "d": W.d,
+                       "kernel": W.kernel, "l2": "no flush: K (10 / 25.6 GB) is far larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": head["GB_s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": head["frac_hbm"], "traffic": None,
+                         "kernel": "stored_narrow (one warp per row, float4 loads of K)",
+                         "peak_source": f"{pk_kind} copy rate (MEASURED_PEAKS.json)",
+                         "t64_alu_peak_tflops": fp32_rate},
+            "sizes": sizes,
+            "stored_solve": {"RHS_solves_per_s": W.t / (solve_ms * 1e-3), "ms": solve_ms, "iterations": info["iters"],
+                             "errbound_max": info["errbound_max"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_precision(args):
     """Precision sweep, 200,000-point Matern-5/2 workload, K^{-1/2}B, Q = 15:
     per mode (plain FP32, FP16 split, BF16 split) the solve error against the
@@ -729,6 +811,8 @@ def main():
         return run_batched(args)
     if args.workload == "precision200k":
         return run_precision(args)
+    if args.workload == "stored":
+        return run_stored(args)
     if args.workload == "learned":
         return run_learned(args)
     return run_ours(args)

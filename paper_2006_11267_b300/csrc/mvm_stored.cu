@@ -7,8 +7,9 @@
 //  * stored_wide (T >= 17): 64 x 64 tile of K loaded with float4 reads into
 //    shared memory, register-tiled 64 x 64 x TC product with V, compensated
 //    accumulation over tiles, Lanczos epilogue (same as the on-the-fly MVM).
-//  * stored_narrow (T <= 8 per column group): one warp per row, float4 reads
-//    along the row, the T-column group of V read from L2; HBM-bound.
+//  * stored_narrow (T <= 16, column groups of up to 8): a warp takes 1, 2 or
+//    4 rows with float4 reads along them, each V float4 from L2 shared by the
+//    warp's rows; HBM-bound.
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -136,46 +137,59 @@ __global__ void __launch_bounds__(256) stored_wide(const float* Kmat, int64_t ld
     }
 }
 
-// One warp per row, 8 rows per block; TC columns of V per launch column group.
-template <int TC>
+// R rows per warp, 8 warps per block; TC columns of V per launch column
+// group.  Each float4 of V feeds the warp's R rows, so V is read from L2 TC / R
+// times per float4 of K (R = TC / 2, at least 1), which keeps the kernel on
+// the HBM stream of K.  Per (row, column) the sum order is the same for any R.
+template <int TC, int R>
 __global__ void __launch_bounds__(256) stored_narrow(const float* Kmat, int64_t ldk, MvmArgs<float> a) {
     if (a.stop && *a.stop) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    const int64_t i0 = ((int64_t)blockIdx.x * 8 + warp) * R;
     const int c0 = blockIdx.y * TC;
-    const float* krow = Kmat + i * ldk;
-    float hi[TC], lo[TC];
+    float hi[R][TC], lo[R][TC];
 #pragma unroll
-    for (int c = 0; c < TC; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < TC; ++c) { hi[r][c] = 0.f; lo[r][c] = 0.f; }
     for (int64_t j0 = 0; j0 < a.Npad; j0 += 1024) {
-        float acc[TC];
+        float acc[R][TC];
 #pragma unroll
-        for (int c = 0; c < TC; ++c) acc[c] = 0.f;
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) acc[r][c] = 0.f;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t j = j0 + q * 128 + lane * 4;
             if (j < a.Npad) {
-                const float4 k4 = *reinterpret_cast<const float4*>(krow + j);
+                float4 v4[TC];
 #pragma unroll
-                for (int c = 0; c < TC; ++c) {
-                    if (c0 + c < a.T) {
-                        const float4 v4 = *reinterpret_cast<const float4*>(a.V + (int64_t)(c0 + c) * a.ldv + j);
-                        acc[c] = fmaf(k4.x, v4.x, fmaf(k4.y, v4.y, fmaf(k4.z, v4.z, fmaf(k4.w, v4.w, acc[c]))));
-                    }
+                for (int c = 0; c < TC; ++c)
+                    v4[c] = c0 + c < a.T ? *reinterpret_cast<const float4*>(a.V + (int64_t)(c0 + c) * a.ldv + j)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float4 k4 = *reinterpret_cast<const float4*>(Kmat + (i0 + r) * ldk + j);
+#pragma unroll
+                    for (int c = 0; c < TC; ++c)
+                        acc[r][c] = fmaf(k4.x, v4[c].x, fmaf(k4.y, v4[c].y, fmaf(k4.z, v4[c].z, fmaf(k4.w, v4[c].w, acc[r][c]))));
                 }
             }
         }
 #pragma unroll
-        for (int c = 0; c < TC; ++c) two_sum_into(hi[c], lo[c], acc[c]);
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) two_sum_into(hi[r][c], lo[r][c], acc[r][c]);
     }
     __shared__ double red[8][TC][3];
 #pragma unroll
     for (int c = 0; c < TC; ++c) {
         const int col = c0 + c;
-        double o = warp_sum((double)hi[c] + (double)lo[c]);
         double qp = 0, pp = 0, qq = 0;
-        if (lane == 0 && col < a.T) {
-            lanczos_epilogue_value(a, i, col, (float)o, qp, pp, qq);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const double o = warp_sum((double)hi[r][c] + (double)lo[r][c]);
+            if (lane == 0 && col < a.T) lanczos_epilogue_value(a, i0 + r, col, (float)o, qp, pp, qq);
         }
         if (lane == 0) { red[warp][c][0] = qp; red[warp][c][1] = pp; red[warp][c][2] = qq; }
     }
@@ -207,7 +221,11 @@ cudaError_t km_dp(const float* Xp, int64_t N, int64_t Npad, int dp, float s, flo
 
 }  // namespace
 
-int64_t stored_row_tiles(int64_t Npad, int T) { return T >= 17 ? Npad / 64 : Npad / 8; }
+// Column group of the narrow kernel for T <= 16 columns and its rows per warp.
+static int narrow_tc(int T) { return T <= 1 ? 1 : T <= 2 ? 2 : T <= 4 ? 4 : 8; }
+static int narrow_rows(int T) { return narrow_tc(T) <= 2 ? 1 : narrow_tc(T) / 2; }
+
+int64_t stored_row_tiles(int64_t Npad, int T) { return T >= 17 ? Npad / 64 : Npad / (8 * narrow_rows(T)); }
 
 cudaError_t launch_kernel_matrix(const float* Xp, int64_t N, int64_t Npad, int dp, int kt, float s, float noise,
                                  float* Kmat, int64_t ldk, int64_t ncols, cudaStream_t st) {
@@ -227,13 +245,13 @@ cudaError_t launch_stored_mvm(const float* Kmat, int64_t ldk, const MvmArgs<floa
         if (TC == 64) stored_wide<64><<<grid, 256, 0, st>>>(Kmat, ldk, a);
         else stored_wide<32><<<grid, 256, 0, st>>>(Kmat, ldk, a);
     } else {
-        const int TC = a.T <= 1 ? 1 : a.T <= 2 ? 2 : a.T <= 4 ? 4 : 8;
-        dim3 grid((unsigned)(a.Npad / 8), (unsigned)((a.T + TC - 1) / TC));
+        const int TC = narrow_tc(a.T);
+        dim3 grid((unsigned)(a.Npad / (8 * narrow_rows(a.T))), (unsigned)((a.T + TC - 1) / TC));
         switch (TC) {
-            case 1: stored_narrow<1><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
-            case 2: stored_narrow<2><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
-            case 4: stored_narrow<4><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
-            default: stored_narrow<8><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
+            case 1: stored_narrow<1, 1><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
+            case 2: stored_narrow<2, 1><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
+            case 4: stored_narrow<4, 2><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
+            default: stored_narrow<8, 4><<<grid, 256, 0, st>>>(Kmat, ldk, a); break;
         }
     }
     return cudaGetLastError();
