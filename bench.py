@@ -548,9 +548,10 @@ def run_batched(args):
 def run_stored(args):
     """Stored-K MVM (the explicit-matrix case of Sec. 3.3): K = K_XX + sigma^2 I
     of the 50,000-point RBF workload and of its 80,000-point extension formed
-    once in HBM (FP32: 10.0 and 25.6 GB), then streamed by every MVM.  A
-    column group of T <= 8 reads K once per MVM with float4 loads and is
-    HBM-bound: 4 Npad^2 bytes against the measured copy rate.  T = 64 runs
+    once in HBM (FP32: 10.0 and 25.6 GB), then streamed by every MVM.  One
+    column reads K once per MVM with float4 loads and is HBM-bound: 4 Npad^2
+    bytes against the measured copy rate (T = 8 reads it once too, four rows
+    per warp sharing each V load).  T = 64 runs
     the register-tiled FP32 product (32 flops per byte of K: FP32-FMA-bound,
     reported against the derived FP32 rate).  Beside it the headline solve
     with the stored MVM (FP32) for comparison with the on-the-fly paths."""
@@ -609,14 +610,15 @@ def run_stored(args):
     torch.cuda.synchronize()
     solve_ms = e0.elapsed_time(e1)
     fp32_rate = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-    head = sizes["50000"]["t8"]
-    line = {"metric": "stored-K MVM HBM GB/s (T=8 column group, N=50,000)", "value": head["GB_s"], "unit": "GB/s",
+    head = sizes["50000"]["t1"]
+    line = {"metric": "stored-K MVM HBM GB/s (one column, N=50,000)", "value": head["GB_s"], "unit": "GB/s",
             "n_gpus": 1, "steps": 5, "warmup": 2, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"stored_{W.name}", "N": [50000, 80000], "T": [1, 8, 64], "d": W.d,
                        "kernel": W.kernel, "l2": "no flush: K (10 / 25.6 GB) is far larger than L2"},
             "roofline": {"bound": "hbm", "achieved": head["GB_s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": head["frac_hbm"], "traffic": None,
-                         "kernel": "stored_narrow (one warp per row, float4 loads of K)",
+                         "kernel": "stored_narrow<1, 1> (one warp per row, float4 loads of K); T = 8 runs "
+                                   "stored_narrow<8, 4> (4 rows per warp), T = 64 stored_wide (FP32 FMA-bound)",
                          "peak_source": f"{pk_kind} copy rate (MEASURED_PEAKS.json)",
                          "t64_alu_peak_tflops": fp32_rate},
             "sizes": sizes,
