@@ -566,7 +566,8 @@ def run_stored(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     sizes = {}
-    for n in (50000, 80000):
+    ns = (args.n,) if args.n else (50000, 80000)
+    for n in ns:
         npad = -(-n // 128) * 128
         X = torch.from_numpy(ci.points(W.seed, n, W.d).astype(np.float32)).cuda()
         K = torch.empty((npad, npad), dtype=torch.float32, device="cuda")
@@ -610,6 +611,9 @@ def run_stored(args):
     torch.cuda.synchronize()
     solve_ms = e0.elapsed_time(e1)
     fp32_rate = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    if args.n:                    # a profiling case: the MVMs only
+        print(json.dumps({"stored_only": args.n, "sizes": sizes}), flush=True)
+        return 0
     head = sizes["50000"]["t1"]
     line = {"metric": "stored-K MVM HBM GB/s (one column, N=50,000)", "value": head["GB_s"], "unit": "GB/s",
             "n_gpus": 1, "steps": 5, "warmup": 2, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -737,10 +741,10 @@ def run_learned(args):
     rmse = np.sqrt(np.mean((pv - yv) ** 2, axis=0)).tolist()
     # Held-out instances, all resident.  The pre-pass pipeline solves them in
     # batches of 512 in index order; the learned pipeline predicts every
-    # problem first (its bounds and its iteration count), orders the
-    # problems by predicted iterations so each batch of 512 converges
-    # together (the batch schedule sized ahead of time), and solves each
-    # batch with the predicted bounds.
+    # problem first (its bounds and its iteration count) and sizes its batch
+    # schedule ahead of time: the problems predicted to need >= 500
+    # iterations in one batch, the rest in batches of 512 in order of
+    # predicted iterations, each solved with the predicted bounds.
     raw_test = ci.batched_problems(BATCH_SEED + 999, count=4096, t=BATCH_T)
     test = device_batch(raw_test)
     res = {"prepass": {"ms": 0.0}, "learned": {"ms": 0.0}}
@@ -751,13 +755,13 @@ def run_learned(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     pred = P.ciq_mlp_predict(theta, P.ciq_mlp_features(test))
-    order = torch.argsort(pred[:, 2]).cpu().numpy()
+    schedule = learned.batch_schedule(pred[:, 2].cpu().numpy(), batch=BATCH_COUNT, long_iters=500)
     e1.record()
     torch.cuda.synchronize()
     res["learned"]["ms"] += e0.elapsed_time(e1)
-    for mode, idx in (("prepass", np.arange(len(test))), ("learned", order)):
-        for b0 in range(0, len(test), BATCH_COUNT):
-            ids = idx[b0:b0 + BATCH_COUNT]
+    index_batches = [list(range(b0, min(b0 + BATCH_COUNT, len(test)))) for b0 in range(0, len(test), BATCH_COUNT)]
+    for mode, batches in (("prepass", index_batches), ("learned", schedule)):
+        for ids in batches:
             probs = [test[i] for i in ids]
             for pr in probs:
                 pr["out"] = torch.empty_like(pr["B"])
@@ -795,7 +799,7 @@ def run_learned(args):
             "prepass_pipeline": {"value": rhs / (res["prepass"]["ms"] * 1e-3), "ms": res["prepass"]["ms"],
                                  "mvm_work": work["prepass"]},
             "learned_pipeline": {"ms": res["learned"]["ms"], "mvm_work": work["learned"], "fallbacks": fallbacks,
-                                 "margin_log": margin},
+                                 "margin_log": margin, "batches": [len(b) for b in schedule]},
             "gain": res["prepass"]["ms"] / res["learned"]["ms"],
             "validation_rmse_log": {"theta_min": rmse[0], "theta_max": rmse[1], "iterations": rmse[2]},
             "oracle_rel_err_64_smallest": {m: {"max": max(v), "median": float(np.median(v))} for m, v in errs.items()},

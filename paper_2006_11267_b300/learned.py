@@ -45,3 +45,23 @@ def lmax_margin_from_validation(theta, F, Y, quantile=0.99):
     pred = _ciq.ciq_mlp_predict(theta, F, bf16=True)
     under = (Y[:, 1] - pred[:, 1]).double().cpu()
     return max(0.0, float(torch.quantile(under, quantile)))
+
+
+def batch_schedule(pred_log_iters, batch=512, long_iters=500):
+    """Batches of problem indices sized ahead of time from the predicted log
+    iteration counts (column 2 of ciq_mlp_predict): the problems predicted
+    to need at least `long_iters` iterations form one batch of their own
+    (a batch runs as long as its slowest problem, so they are kept out of
+    the others), and the rest run in batches of `batch` in order of
+    predicted iterations, shortest first."""
+    import numpy as np
+    pred = np.asarray(pred_log_iters, dtype=np.float64).reshape(-1)
+    order = np.argsort(pred, kind="stable")
+    cut = math.log(long_iters)
+    short = [int(i) for i in order if pred[i] < cut]
+    long = [int(i) for i in order if pred[i] >= cut]
+    batches = [short[b:b + batch] for b in range(0, len(short), batch)]
+    if long:
+        batches.append(long)
+    return batches
+

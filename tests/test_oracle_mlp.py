@@ -118,3 +118,4 @@ def test_training_fits_a_smooth_function():
     theta, _, _, losses = mlp.train(theta, F, Y, steps=1500, batch=64, lr=3e-3, seed=8)
     loss1 = mlp.loss_and_grad(theta, F, Y)[0]
     assert loss1 < 0.1 * loss0
+
