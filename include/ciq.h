@@ -248,7 +248,9 @@ typedef struct {
  * cores with FP16/BF16 split tiles (CIQ_PREC_FP16/BF16; then T <= 64 and
  * every d <= 14).  Every problem's arithmetic is that of ciq_sqrt /
  * ciq_invsqrt with the same options, so each output equals the
- * single-problem call's bit for bit.  1 <= P <= CIQ_MAX_BATCH.
+ * single-problem call's bit for bit (tensor-core batches run one CTA per
+ * row tile unless opt->tc_split says otherwise, so the single call is
+ * compared with the same tc_split).  1 <= P <= CIQ_MAX_BATCH.
  * CIQ_ERR_UNSUPPORTED if opt->mvm is CIQ_MVM_STORED, opt->sqrt_form is not
  * CIQ_SQRT_IDENTITY, quad_w, quad_t, lanczos_start or workspace is set, or a
  * tensor-core batch breaks its limits.  The device workspace (the sum of

@@ -1,7 +1,8 @@
 // On-the-fly kernel MVM on the tcgen05 tensor cores (sm_103a).
 //
 // O = (K_XX + sigma^2 I) V without storing K (the map-reduce MVM of Sec. 3.3).
-// One CTA owns 128 rows of K and streams the points and V in tiles of 64:
+// One CTA owns 128 rows of K and streams the points and V in steps of 128
+// columns (two 64-row operand tiles):
 //
 //   S   = U_i V_j^T on tensor cores, kind::f16, accumulator in TMEM.  Rows are
 //         augmented, u = [c(x - m), -c^2 |x - m|^2 / 2, 1] and v = [c(x - m), 1,
@@ -20,10 +21,13 @@
 //         with Vt = V times a power of two per column, split like U.
 //
 // The operands are pre-arranged in global memory in the shared-memory layout
-// of the MMA, so every tile is one bulk copy (cp.async.bulk) completing on
-// an mbarrier, double-buffered.  The epilogue reads O from TMEM and applies
-// the same Lanczos epilogue as the CUDA-core MVM.  Every wait is bounded: on
-// timeout the CTA records an error flag, skips the rest and frees its TMEM.
+// of the MMA, so every step's tile is one bulk copy (cp.async.bulk)
+// completing on an mbarrier, in three-stage rings.  Each CTA writes its
+// column sums (a contiguous range of K's columns of one row tile); the
+// finish kernel adds a tile's partial sums in split order and applies the
+// same plain or Lanczos epilogue as the CUDA-core MVM.  Every wait is
+// bounded: on timeout the CTA records an error flag, stops issuing, waits
+// (bounded) for its own copies and MMAs in flight and frees its TMEM.
 #include <algorithm>
 
 #include <cuda_bf16.h>
