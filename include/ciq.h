@@ -65,7 +65,12 @@ typedef enum {
     CIQ_NOT_CONVERGED = 4,    /* max_iter reached before every column met the stop rule */
     CIQ_ERR_NAN = 5,          /* a non-finite Lanczos coefficient appeared */
     CIQ_ERR_UNSUPPORTED = 6,  /* valid request this build does not implement */
-    CIQ_ERR_SCRATCH_TOO_SMALL = 7 /* problem larger than the static scratch of ciq_kernel_mvm_noalloc */
+    CIQ_ERR_SCRATCH_TOO_SMALL = 7, /* problem larger than the static scratch of ciq_kernel_mvm_noalloc */
+    CIQ_ERR_TIMEOUT = 8       /* a bounded wait of the tensor-core MVM gave up (about 2 s); the
+                                 kernel stopped cleanly, later MVMs of the call were skipped and the
+                                 results are invalid; the device stays usable.  Reported by the
+                                 solves (which wait for their stream); ciq_kernel_mvm returns
+                                 before its kernels finish and does not report it */
 } ciq_status;
 
 typedef enum { CIQ_RBF = 0, CIQ_MATERN52 = 1 } ciq_kernel_type;
@@ -126,6 +131,9 @@ typedef struct {
                                  CUDA graph and launch it as one (default 1); single solves ignore it */
     int tc_split;             /* tensor-core MVM: CTAs sharing one 128-row tile (1..8; 0 = chosen
                                  from N for single solves, 1 for batched solves) */
+    int fault_inject;         /* testing only (default 0): 1 makes CTA 0 of the first tensor-core MVM
+                                 skip its first point copy, so its bounded waits run out and the
+                                 call returns CIQ_ERR_TIMEOUT (the failure-detection path) */
 } ciq_options;
 
 typedef struct {

@@ -25,9 +25,10 @@ CIQ_MAX_Q = 32
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
           4: "not converged within max_iter", 5: "non-finite Lanczos coefficient",
-          6: "unsupported option", 7: "problem exceeds the static scratch of the allocation-free entry point"}
+          6: "unsupported option", 7: "problem exceeds the static scratch of the allocation-free entry point",
+          8: "a bounded wait of the tensor-core MVM gave up"}
 (CIQ_OK, CIQ_ERR_ARG, CIQ_ERR_CUDA, CIQ_ERR_NOMEM, CIQ_NOT_CONVERGED, CIQ_ERR_NAN, CIQ_ERR_UNSUPPORTED,
- CIQ_ERR_SCRATCH_TOO_SMALL) = range(8)
+ CIQ_ERR_SCRATCH_TOO_SMALL, CIQ_ERR_TIMEOUT) = range(9)
 
 KERNELS = {"rbf": 0, "matern52": 1}
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16": 3}
@@ -56,7 +57,7 @@ class _Options(ctypes.Structure):
                 ("lmin_div", ctypes.c_double), ("lmin", ctypes.c_double), ("lmax", ctypes.c_double),
                 ("quad_w", ctypes.c_void_p), ("quad_t", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("graph", ctypes.c_int),
-                ("tc_split", ctypes.c_int)]
+                ("tc_split", ctypes.c_int), ("fault_inject", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):

@@ -175,6 +175,7 @@ __global__ void batched_summary_kernel(const BatchProblem* probs, int final_j, d
     for (int k = 0; k < 8; ++k) dst[k] = s.summary[k];
     for (int k = 0; k < kNodeCount; ++k) dst[8 + k] = bp.nodes[k];
     dst[8 + kNodeCount] = th;
+    dst[9 + kNodeCount] = (bp.tcp.err && *bp.tcp.err) ? 1.0 : 0.0;
 }
 
 // Exclusive scan of one int per thread over a 1024-thread block; *total gets the sum.

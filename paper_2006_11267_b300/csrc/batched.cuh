@@ -34,7 +34,7 @@ struct BatchProblem {
 constexpr int kBatchClasses = 8;            // 2 kernel types x 4 padded dimensions
 // Packed per-problem results: summary[8], the NodeSlot block, then the
 // largest Ritz value of column 0's msMINRES tridiagonal (0 unless recorded).
-constexpr int kSummaryStride = 9 + kNodeCount;
+constexpr int kSummaryStride = 10 + kNodeCount;   // ..., Ritz maximum, tensor-core timeout flag
 
 // A work list: problems ids[0..*np) with their first work items prefix[k]
 // (prefix[*np] = total).  Block b of a batched launch takes the item b: the

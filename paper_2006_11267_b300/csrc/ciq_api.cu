@@ -96,7 +96,8 @@ bool valid_options(const ciq_options& o) {
              (o.stop_rule != CIQ_STOP_RESIDUAL && o.stop_rule != CIQ_STOP_ERRBOUND) ||
              (o.sqrt_form != CIQ_SQRT_IDENTITY && o.sqrt_form != CIQ_SQRT_MVM) ||
              (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_FP16) ||
-             (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED) || o.tc_split < 0 || o.tc_split > 8);
+             (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED) || o.tc_split < 0 || o.tc_split > 8 ||
+             o.fault_inject < 0 || o.fault_inject > 1);
 }
 
 // Pinned host words for the convergence flag, one set per host thread.
@@ -140,6 +141,7 @@ struct Plan {
     bool prepass;
     bool tri_on = false;          // record column 0's msMINRES tridiagonal
     int tc_max_split = 8;         // CTAs per row tile of the tensor-core MVM (batches: 1)
+    int fault_inject = 0;         // ciq_options.fault_inject (testing the bounded-wait path)
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB;
     R *sx, *sb, *sout, *sstart;
@@ -194,6 +196,7 @@ struct Plan {
         if (tc) {
             char* q = a.take<char>(tc_points_bytes(Npad, T, tc_max_split));
             tcp = tc_points_layout(q, Npad, T, precision, tc_max_split, d);
+            tcp.inject = fault_inject;
         }
         Kst = stored ? a.take<float>((size_t)Npad * Npad) : nullptr;
         bytes = a.off + kAlign;
@@ -214,6 +217,7 @@ Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool pre
     p.JL = o.lanczos_iters;
     p.tc = tc;
     p.tc_max_split = o.tc_split > 0 ? o.tc_split : 8;
+    p.fault_inject = o.fault_inject;
     p.stored = sizeof(R) == 4 && o.mvm == CIQ_MVM_STORED;
     p.nparts = tc ? (int)tc_row_tiles(p.Npad)
                   : p.stored ? (int)stored_row_tiles(p.Npad, T) : (int)mvm_simt_row_tiles<R>(p.Npad, T);
@@ -383,6 +387,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     ciq_status rc = CIQ_OK;
     int* flags = pinned_flags();
     double summary[8] = {0};
+    int tc_timeout = 0;                // the tensor-core MVM's error flag (a bounded wait gave up)
     double nodes[kNodeCount] = {0};
     int last_j = 0;
     int launches = 0;
@@ -542,6 +547,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             CIQ_TRY(cudaMemcpyAsync(out, p.sout, sizeof(R) * (size_t)N * T, cudaMemcpyDeviceToHost, st));
         CIQ_TRY(cudaMemcpyAsync(summary, p.summary, sizeof(summary), cudaMemcpyDeviceToHost, st));
         CIQ_TRY(cudaMemcpyAsync(nodes, p.nodes, sizeof(nodes), cudaMemcpyDeviceToHost, st));
+        if (p.tc) CIQ_TRY(cudaMemcpyAsync(&tc_timeout, p.tcp.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CIQ_TRY(cudaStreamSynchronize(st));
     }
 done:
@@ -594,6 +600,7 @@ done:
         info->mvm_launches = n_mvm;
         info->step_launches = n_step;
     }
+    if (tc_timeout) return CIQ_ERR_TIMEOUT;
     if (summary[6] > 0) return CIQ_ERR_NAN;
     if ((int)summary[5] == kColMaxIter) return CIQ_NOT_CONVERGED;
     return CIQ_OK;
@@ -996,10 +1003,11 @@ done:
         cudaGetLastError();
         return rc;
     }
-    bool any_nan = false, any_maxit = false;
+    bool any_nan = false, any_maxit = false, any_timeout = false;
     for (int p = 0; p < P; ++p) {
         const double* sm = packed.data() + (size_t)p * kSummaryStride;
         const double* nd = sm + 8;
+        if (sm[9 + kNodeCount] != 0.0) any_timeout = true;
         if (sm[6] > 0) any_nan = true;
         if ((int)sm[5] == kColMaxIter) any_maxit = true;
         if (!infos) continue;
@@ -1021,6 +1029,7 @@ done:
         info->ritz_max_solve = sm[8 + kNodeCount];
     }
     if (packed_out) packed_out->swap(packed);
+    if (any_timeout) return CIQ_ERR_TIMEOUT;
     if (any_nan) return CIQ_ERR_NAN;
     if (any_maxit) return CIQ_NOT_CONVERGED;
     return CIQ_OK;
@@ -1138,6 +1147,7 @@ const char* ciq_status_string(int status) {
         case CIQ_ERR_NAN: return "non-finite Lanczos coefficient";
         case CIQ_ERR_UNSUPPORTED: return "unsupported option";
         case CIQ_ERR_SCRATCH_TOO_SMALL: return "problem exceeds the static scratch of the allocation-free entry point";
+        case CIQ_ERR_TIMEOUT: return "a bounded wait of the tensor-core MVM gave up";
         default: return "unknown status";
     }
 }

@@ -341,7 +341,13 @@ __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi
 template <int KT, int TP, bool HALF>
 __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile,
                                             int split) {
-    if (a.stop && *a.stop) return;
+    // Stopped columns, or an earlier MVM of this call gave up a bounded wait
+    // (its results are invalid; the call reports CIQ_ERR_TIMEOUT): no work.
+    // One thread reads the flags so the whole CTA takes the same branch.
+    __shared__ int skip_all;
+    if (threadIdx.x == 0) skip_all = (a.stop && *a.stop) || *p.err;
+    __syncthreads();
+    if (skip_all) return;
     constexpr int NX = kTcXStages;
     constexpr int NV = tc_vstages<TP>();
     constexpr int VSTEP = tc_vstep_bytes<TP>();
@@ -407,6 +413,7 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
         }
         auto load_x = [&](int u) -> bool {
             const int sx = u % NX;
+            if (p.inject && u == 0 && blockIdx.x == 0) return false;   // testing: the copy never comes
             if (u >= NX && !uni(tc::mbar_wait(&bars[kBarSDone + (u - NX) % kRing],
                                               (uint32_t)(((u - NX) / kRing) & 1), kWaitLimit)))
                 return false;
@@ -768,7 +775,7 @@ __device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<
 
 template <int TP>
 __global__ void __launch_bounds__(128) tc_finish_kernel(TcPoints p, MvmArgs<float> a, int c0) {
-    if (a.stop && *a.stop) return;
+    if ((a.stop && *a.stop) || *p.err) return;      // the product launch before it is complete
     tc_finish_body<TP>(p, a, c0, blockIdx.x / (TP / kFinCols), blockIdx.x % (TP / kFinCols));
 }
 
@@ -804,7 +811,7 @@ __global__ void __launch_bounds__(128) batched_tc_finish_kernel(const BatchProbl
         sa = pre ? probs[pb].pre[parity] : probs[pb].mvm[parity];
     }
     __syncthreads();
-    if (sa.stop && *sa.stop) return;
+    if ((sa.stop && *sa.stop) || *sp.err) return;
     tc_finish_body<TP>(sp, sa, 0, local / (TP / kFinCols), local % (TP / kFinCols));
 }
 

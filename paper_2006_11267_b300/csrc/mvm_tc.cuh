@@ -22,6 +22,7 @@ struct TcPoints {
     int* err = nullptr;        // set to 1 if a bounded wait gave up
     float* part = nullptr;     // per-CTA column sums, rounded to float   [row tile][split][TP][128]
     int nsplit = 1;            // CTAs per row tile, each over a contiguous range of K's columns
+    int inject = 0;            // testing only: CTA 0 skips its first point copy (its waits run out)
     int narrow = 0;            // 1: at most 8 augmented features (d <= 6), so only the first K-core
                                // of every chunk is non-zero and S takes two MMAs instead of three
     int64_t Npad = 0;

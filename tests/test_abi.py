@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_sizes_match_header_layout():
-    assert ctypes.sizeof(_ciq._Options) == 120
+    assert ctypes.sizeof(_ciq._Options) == 128
     assert ctypes.sizeof(_ciq._Kernel) == 32
     assert ctypes.sizeof(_ciq._Info) == 16 + 6 * 8 + 2 * 32 * 8 + 8 + 4 * 8 + 8 + 8
     # ciq_problem: X, N, d (+pad), kern, B, T (+pad), out, lmin, lmax
@@ -45,8 +45,10 @@ def test_status_strings_and_defaults():
     lib = P.lib()
     assert lib.ciq_status_string(0) == b"ok"
     assert lib.ciq_status_string(4).startswith(b"not converged")
+    assert lib.ciq_status_string(_ciq.CIQ_ERR_TIMEOUT).startswith(b"a bounded wait")
     o = _ciq.make_options()
     assert (o.max_iter, o.lanczos_iters, o.lmax_margin, o.lmin_div) == (200, 10, 1.05, 100.0)
+    assert o.fault_inject == 0
 
 
 @pytest.mark.parametrize("kappa,Q", [(1.0, 5), (1e3, 8), (1e8, 15), (1e12, 32)])
@@ -76,6 +78,7 @@ def test_solve_validates_before_the_device():
         dict(X=X, B=B, kernel=P.Kernel("rbf", 1.0, 1.0, -0.1), Q=4),          # noise < 0
         dict(X=X, B=B, kernel=k, Q=4, max_iter=0),
         dict(X=X, B=B, kernel=k, Q=4, stop_rule=7),
+        dict(X=X, B=B, kernel=k, Q=4, fault_inject=2),
     ]
     for case in bad:
         kw = {kk: v for kk, v in case.items() if kk not in ("X", "B", "kernel", "Q")}

@@ -117,3 +117,27 @@ def test_tc_split_k_changes_only_the_summation_order():
         outs[s] = a.cpu().numpy()
     for s in (2, 5, 8):
         assert rel(outs[s], outs[1]) < 1e-3, s
+
+
+def test_tc_bounded_wait_runs_out_and_the_host_reads_the_status():
+    # Failure detection without a fault: with fault_inject = 1, CTA 0 of the
+    # first tensor-core MVM never receives its first point tile, so its
+    # bounded waits (about 2 s) run out; the kernel records the error,
+    # frees its tensor memory and returns, later MVMs of the call do no
+    # work, and the call returns CIQ_ERR_TIMEOUT.  The device stays usable:
+    # the same solve right after is correct.
+    X = torch.from_numpy(f32(ci.points(31, 700, 3))).cuda()
+    B = torch.from_numpy(f32(ci.rhs(32, 700, 4))).cuda()
+    k = P.Kernel("rbf", 0.3, 1.0, 1e-2)
+    with pytest.raises(P.CiqError) as e:
+        P.ciq_sqrt(X, k, B, 8, 1e-4, max_iter=50, precision="fp16", fault_inject=1)
+    assert e.value.status == P._ciq.CIQ_ERR_TIMEOUT
+    probs = [dict(X=X, B=B, kernel=k), dict(X=X[:300].contiguous(), B=B[:, :300].contiguous(), kernel=k)]
+    with pytest.raises(P.CiqError) as e:
+        P.ciq_sqrt_batched(probs, 8, 1e-4, max_iter=50, precision="fp16", fault_inject=1)
+    assert e.value.status == P._ciq.CIQ_ERR_TIMEOUT
+    out, info = P.ciq_sqrt(X, k, B, 8, 1e-4, max_iter=500, precision="fp16")
+    assert info["status"] == 0
+    K = kernels.dense_K(X.cpu().numpy().astype(np.float64), "rbf", 0.3, 1.0, 1e-2)
+    truth = eig.sqrt_apply(K, B.cpu().numpy().astype(np.float64).T).T
+    assert rel(out.cpu().numpy(), truth) < 1e-3
