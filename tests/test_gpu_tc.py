@@ -141,3 +141,18 @@ def test_tc_bounded_wait_runs_out_and_the_host_reads_the_status():
     K = kernels.dense_K(X.cpu().numpy().astype(np.float64), "rbf", 0.3, 1.0, 1e-2)
     truth = eig.sqrt_apply(K, B.cpu().numpy().astype(np.float64).T).T
     assert rel(out.cpu().numpy(), truth) < 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_nan_in_the_points_is_reported(prec):
+    # A non-finite point makes a row and a column of K non-finite; the first
+    # Lanczos coefficients are then NaN and the solve reports CIQ_ERR_NAN
+    # (per column: status NaN) instead of returning numbers.
+    X = f32(ci.points(41, 500, 3))
+    X[17, 1] = np.nan
+    Xd = torch.from_numpy(X).cuda()
+    B = torch.from_numpy(f32(ci.rhs(42, 500, 4))).cuda()
+    k = P.Kernel("rbf", 0.3, 1.0, 1e-2)
+    with pytest.raises(P.CiqError) as e:
+        P.ciq_sqrt(Xd, k, B, 8, 1e-4, max_iter=100, precision=prec, lmin=1e-2, lmax=400.0)
+    assert e.value.status == P._ciq.CIQ_ERR_NAN
