@@ -617,14 +617,21 @@ struct HostList {
     int total() const { return prefix.back(); }
 };
 
-// Stream used only to record batched iteration graphs, one per host thread.
+// Stream used only to record batched iteration graphs, one per host thread
+// and device (a stream belongs to the device current at its creation).
 cudaStream_t capture_stream() {
-    thread_local cudaStream_t cs = nullptr;
-    if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    constexpr int kMaxDev = 64;
+    thread_local cudaStream_t cs[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
         cudaGetLastError();
-        cs = nullptr;
+        return nullptr;
     }
-    return cs;
+    if (!cs[dev] && cudaStreamCreateWithFlags(&cs[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cs[dev] = nullptr;
+    }
+    return cs[dev];
 }
 
 // Pinned host words for the list totals (two slots), one set per host thread.

@@ -29,6 +29,7 @@
 // bounded: on timeout the CTA records an error flag, stops issuing, waits
 // (bounded) for its own copies and MMAs in flight and frees its TMEM.
 #include <algorithm>
+#include <atomic>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -854,15 +855,27 @@ __global__ void __launch_bounds__(256) batched_tc_split_kernel(const BatchProble
     tc_split_v_body<HALF>(m.V, m.ldv, m.T, tpw, tpw, tp.Npad, tp.vscale, tp.vblk, (int64_t)local * 256 + threadIdx.x);
 }
 
+// A kernel's shared-memory attribute is set once per device (the attribute
+// belongs to the device that is current when it is set); `done` holds one
+// bit per device id.
+template <typename F>
+cudaError_t set_smem_once(std::atomic<uint64_t>& done, F kernel, int smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? uint64_t(1) << dev : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
 template <int KT, int TP, bool HALF>
 cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaStream_t st) {
     constexpr int smem = tc_smem_bytes<TP>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(mvm_tc_kernel<KT, TP, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    cudaError_t e0 = set_smem_once(configured, mvm_tc_kernel<KT, TP, HALF>, smem);
+    if (e0 != cudaSuccess) return e0;
     mvm_tc_kernel<KT, TP, HALF><<<(unsigned)(a.Npad / kTcBM * p.nsplit), 384, smem, st>>>(p, a, c0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1039,14 +1052,8 @@ cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevLi
 namespace {
 template <int KT, int TP, bool HALF>
 cudaError_t configure_btc() {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(batched_tc_mvm_kernel<KT, TP, HALF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<TP>());
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    return cudaSuccess;
+    static std::atomic<uint64_t> configured{0};
+    return set_smem_once(configured, batched_tc_mvm_kernel<KT, TP, HALF>, tc_smem_bytes<TP>());
 }
 
 template <int KT, int TP, bool HALF>
