@@ -63,8 +63,8 @@ __device__ __forceinline__ bool list_item(const DevList& L, int item, int& p, in
 
 // Main-loop lists rebuilt on the device, kBatchDynLists in all.  CUDA-core
 // batches: one per MVM class (kernel type x padded dimension), then the
-// recurrence list.  Tensor-core batches: lists 0 and 1 are the MVM work of
-// RBF and Matern problems, list 2 the V split, list 3 the finishing pass
+// recurrence list.  Tensor-core batches: list 0 is the MVM work of every
+// problem (both kernel types), list 2 the V split, list 3 the finishing pass
 // (one item per row tile and 16 columns), the last the recurrence.
 constexpr int kBatchDynLists = kBatchClasses + 1;
 constexpr int kListTcSplit = 2;
@@ -114,8 +114,9 @@ cudaError_t launch_batched_tc_points(const BatchProblem* probs, DevList rows256,
                                      cudaStream_t st);
 cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevList L, int blocks, bool half,
                                     bool pre, cudaStream_t st);
-cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, bool pre,
-                                  DevList L, int blocks, cudaStream_t st);
+// Both kernel types in one launch (the problem selects the body).
+cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int TP, bool half, int parity, bool pre, DevList L,
+                                  int blocks, cudaStream_t st);
 // Sum the split partials of every row tile and apply the MVM epilogue.
 cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, bool pre, DevList L, int blocks,
                                      cudaStream_t st);

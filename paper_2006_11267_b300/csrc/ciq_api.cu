@@ -700,7 +700,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     const int groups = (T + batch_mvm_group(T) - 1) / batch_mvm_group(T);
     std::vector<BatchProblem> hp(P);
     // Tensor-core pre-pass: MVM items per kernel type, V split and finish.
-    HostList pre_tc[2], pre_tc_split, pre_tc_fin;
+    HostList pre_tc, pre_tc_split, pre_tc_fin;
     HostList prep, one, init, pre, pre_one, given_one, fin, comb, rows256, pre_mvm[kBatchClasses],
         dyn[kBatchDynLists];
     int64_t biggest = 0;
@@ -724,7 +724,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         comb.add(p, comb_items);
         for (int l = 0; l < kBatchDynLists; ++l) b.list_items[l] = 0;
         if (tc) {
-            b.list_items[probs[p].kern.type] = (int)(pl.Npad / kTcBM) * pl.tcp.nsplit;
+            b.list_items[0] = (int)(pl.Npad / kTcBM) * pl.tcp.nsplit;     // both kernel types in one list
             b.list_items[kListTcSplit] = (int)((pl.Npad / 8 * TP + 255) / 256);
             b.list_items[kListTcFinish] = (int)(pl.Npad / kTcBM) * (TP / 16);   // row tile x 16 columns
         } else {
@@ -739,7 +739,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
             pre.add(p, pl.nchunks1);
             pre_one.add(p, 1);
             if (tc) {
-                pre_tc[probs[p].kern.type].add(p, (int64_t)(pl.Npad / kTcBM) * pl.tcp.nsplit);
+                pre_tc.add(p, (int64_t)(pl.Npad / kTcBM) * pl.tcp.nsplit);
                 pre_tc_split.add(p, (pl.Npad / 8 * 32 + 255) / 256);
                 pre_tc_fin.add(p, (pl.Npad / kTcBM) * (32 / 16));
             } else {
@@ -766,7 +766,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     (void)biggest;
     std::vector<HostList*> all_lists = {&prep, &one, &init, &pre, &pre_one, &given_one, &fin, &comb, &rows256};
     for (auto& l : pre_mvm) all_lists.push_back(&l);
-    for (auto& l : pre_tc) all_lists.push_back(&l);
+    all_lists.push_back(&pre_tc);
     all_lists.push_back(&pre_tc_split);
     all_lists.push_back(&pre_tc_fin);
     for (auto& l : dyn) all_lists.push_back(&l);
@@ -881,11 +881,9 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                 if (tc) {
                     CIQ_TRY(launch_batched_tc_split(probs_d, j & 1, L(pre_tc_split), pre_tc_split.total(), half, true,
                                                     st));
-                    for (int kt = 0; kt < 2; ++kt)
-                        CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, 32, half, j & 1, true, L(pre_tc[kt]),
-                                                      pre_tc[kt].total(), st));
+                    CIQ_TRY(launch_batched_tc_mvm(probs_d, 32, half, j & 1, true, L(pre_tc), pre_tc.total(), st));
                     CIQ_TRY(launch_batched_tc_finish(probs_d, 32, j & 1, true, L(pre_tc_fin), pre_tc_fin.total(), st));
-                    launches += 2 + (pre_tc[0].total() > 0) + (pre_tc[1].total() > 0);
+                    launches += 3;
                 }
                 for (int c = 0; c < kBatchClasses; ++c) {
                     if (pre_mvm[c].total() == 0) continue;
@@ -928,10 +926,8 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                                                             half, false, ls));
                             ++launches;
                         }
-                        for (int kt = 0; kt < 2; ++kt) {
-                            if (grid[kt] == 0) continue;
-                            CIQ_TRY(launch_batched_tc_mvm(probs_d, kt, TP, half, jj & 1, false, dyn_d.l[kt], grid[kt],
-                                                          ls));
+                        if (grid[0] > 0) {
+                            CIQ_TRY(launch_batched_tc_mvm(probs_d, TP, half, jj & 1, false, dyn_d.l[0], grid[0], ls));
                             ++launches;
                         }
                         if (grid[kListTcFinish] > 0) {

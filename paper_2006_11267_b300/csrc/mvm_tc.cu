@@ -783,8 +783,10 @@ __global__ void __launch_bounds__(128) tc_finish_kernel(TcPoints p, MvmArgs<floa
 // ------------------------------------------------------ batched problems --
 // Block b takes item b of a work list of (problem, row tile x split); the
 // problem's operands and MVM arguments are copied to shared memory and the
-// same body runs as for one problem.
-template <int KT, int TP, bool HALF>
+// same body runs as for one problem.  One launch covers both kernel types:
+// the CTA's problem selects the body (a branch uniform over the CTA), so RBF
+// and Matern problems share one work list and fill the same waves.
+template <int TP, bool HALF>
 __global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProblem* probs, DevList L, int parity,
                                                                  int pre) {
     int pb, local;
@@ -796,7 +798,8 @@ __global__ void __launch_bounds__(384, 1) batched_tc_mvm_kernel(const BatchProbl
         sa = pre ? probs[pb].pre[parity] : probs[pb].mvm[parity];
     }
     __syncthreads();
-    mvm_tc_body<KT, TP, HALF>(sp, sa, 0, local / sp.nsplit, local % sp.nsplit);
+    if (sa.kt == CIQ_RBF) mvm_tc_body<CIQ_RBF, TP, HALF>(sp, sa, 0, local / sp.nsplit, local % sp.nsplit);
+    else mvm_tc_body<CIQ_MATERN52, TP, HALF>(sp, sa, 0, local / sp.nsplit, local % sp.nsplit);
 }
 
 // Block b finishes item `local` (row tile x 16-column group) of problem pb.
@@ -1050,31 +1053,29 @@ cudaError_t launch_batched_tc_split(const BatchProblem* probs, int parity, DevLi
 }
 
 namespace {
-template <int KT, int TP, bool HALF>
+template <int TP, bool HALF>
 cudaError_t configure_btc() {
     static std::atomic<uint64_t> configured{0};
-    return set_smem_once(configured, batched_tc_mvm_kernel<KT, TP, HALF>, tc_smem_bytes<TP>());
+    return set_smem_once(configured, batched_tc_mvm_kernel<TP, HALF>, tc_smem_bytes<TP>());
 }
 
-template <int KT, int TP, bool HALF>
+template <int TP, bool HALF>
 cudaError_t launch_btc(const BatchProblem* probs, int parity, int pre, DevList L, int blocks, cudaStream_t st) {
-    cudaError_t e = configure_btc<KT, TP, HALF>();
+    cudaError_t e = configure_btc<TP, HALF>();
     if (e != cudaSuccess) return e;
-    batched_tc_mvm_kernel<KT, TP, HALF><<<blocks, 384, tc_smem_bytes<TP>(), st>>>(probs, L, parity, pre);
+    batched_tc_mvm_kernel<TP, HALF><<<blocks, 384, tc_smem_bytes<TP>(), st>>>(probs, L, parity, pre);
     return cudaGetLastError();
 }
 
 template <bool HALF>
 cudaError_t configure_btc_all(int TP) {
-    cudaError_t e = TP == 32 ? configure_btc<CIQ_RBF, 32, HALF>() : configure_btc<CIQ_RBF, 64, HALF>();
-    if (e != cudaSuccess) return e;
-    return TP == 32 ? configure_btc<CIQ_MATERN52, 32, HALF>() : configure_btc<CIQ_MATERN52, 64, HALF>();
+    return TP == 32 ? configure_btc<32, HALF>() : configure_btc<64, HALF>();
 }
-template <int KT, bool HALF>
+template <bool HALF>
 cudaError_t launch_btc_tp(const BatchProblem* probs, int TP, int parity, int pre, DevList L, int blocks,
                          cudaStream_t st) {
-    return TP == 32 ? launch_btc<KT, 32, HALF>(probs, parity, pre, L, blocks, st)
-                    : launch_btc<KT, 64, HALF>(probs, parity, pre, L, blocks, st);
+    return TP == 32 ? launch_btc<32, HALF>(probs, parity, pre, L, blocks, st)
+                    : launch_btc<64, HALF>(probs, parity, pre, L, blocks, st);
 }
 }  // namespace
 
@@ -1083,16 +1084,13 @@ cudaError_t prepare_batched_tc_mvm(int TP, bool half) {
     return half ? configure_btc_all<true>(TP) : configure_btc_all<false>(TP);
 }
 
-cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int kt, int TP, bool half, int parity, bool pre,
-                                  DevList L, int blocks, cudaStream_t st) {
+cudaError_t launch_batched_tc_mvm(const BatchProblem* probs, int TP, bool half, int parity, bool pre, DevList L,
+                                  int blocks, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
     if (TP != 32 && TP != 64) return cudaErrorInvalidValue;
     const int pr = pre ? 1 : 0;
-    if (kt == CIQ_RBF)
-        return half ? launch_btc_tp<CIQ_RBF, true>(probs, TP, parity, pr, L, blocks, st)
-                    : launch_btc_tp<CIQ_RBF, false>(probs, TP, parity, pr, L, blocks, st);
-    return half ? launch_btc_tp<CIQ_MATERN52, true>(probs, TP, parity, pr, L, blocks, st)
-                : launch_btc_tp<CIQ_MATERN52, false>(probs, TP, parity, pr, L, blocks, st);
+    return half ? launch_btc_tp<true>(probs, TP, parity, pr, L, blocks, st)
+                : launch_btc_tp<false>(probs, TP, parity, pr, L, blocks, st);
 }
 
 cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int parity, bool pre, DevList L, int blocks,
