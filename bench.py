@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--krylov", default="auto", choices=["auto", "recurrence", "basis"],
+                    help="how the solves form their iterates (stored Lanczos basis or Q direction recurrences)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
@@ -313,6 +315,7 @@ def run_ours(args):
     out = torch.empty_like(Bd)
     k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
     opts = dict(stop_rule="errbound", max_iter=MAX_ITER, lanczos_iters=LANCZOS_ITERS, precision=args.precision,
+                krylov=args.krylov,
                 check_every=16)
 
     def step(profile=0):
@@ -419,7 +422,7 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
                            "noise": W.noise, "T": W.t, "Q": W.q, "op": "sqrt", "tol": TOL,
-                           "stop_rule": "errbound", "precision": args.precision, "iterations": it,
+                           "stop_rule": "errbound", "precision": args.precision, "krylov": infos[0].get("krylov"), "iterations": it,
                            "lanczos_iters": LANCZOS_ITERS, "errbound_max": max(i["errbound_max"] for i in infos),
                            "parallelism": f"replicas{world}",
                            "l2": "no flush: every step streams > 100 GB through a > 126 MB workspace"},

@@ -104,6 +104,24 @@ typedef enum {
     CIQ_STOP_ERRBOUND = 1     /* per column: sum_q c_q |phibar_q| / (t_q + lmin) <= tol ||a_j|| */
 } ciq_stop_rule;
 
+/* How the iterates are formed (single solves; batched solves always recur).
+ * RECURRENCE is App. C as written: Q search directions per column, updated every
+ * step, O(QNT) memory.  BASIS keeps every Lanczos vector in the workspace
+ * ((max_iter + 2) T Npad floats) and forms the Q solutions once at the end,
+ * x_q = V_J R_q^{-1} tau_q, from the FP64 Givens factors recorded every step:
+ * the same MINRES iterates with (3Q + 4) fewer vector passes per iteration.
+ * Under CIQ_STOP_ERRBOUND, BASIS compares the bound with tol (1 - 2 tol)
+ * times ||K^{1/2}b|| = ||b|| sqrt(alpha_1) (square root; the CIQ_SQRT_MVM
+ * form's bound is multiplied by lmax_used) or times the Gauss-quadrature lower
+ * bound of ||K^{-1/2}b|| from T_j (inverse root), instead of tol times the
+ * running estimate's norm; the bound is then <= tol ||a_j|| as well.  AUTO: BASIS for FP32 solves whose basis takes at
+ * most a quarter of the device memory, else RECURRENCE. */
+typedef enum {
+    CIQ_KRYLOV_AUTO = 0,
+    CIQ_KRYLOV_RECURRENCE = 1,
+    CIQ_KRYLOV_BASIS = 2
+} ciq_krylov_form;
+
 typedef enum {
     CIQ_SQRT_IDENTITY = 0,    /* K^{1/2}b = (sum w_q) b - sum w_q t_q x_q   (no extra MVM) */
     CIQ_SQRT_MVM = 1          /* K^{1/2}b = K (sum w_q x_q)                 (one extra MVM) */
@@ -134,6 +152,7 @@ typedef struct {
     int fault_inject;         /* testing only (default 0): 1 makes CTA 0 of the first tensor-core MVM
                                  skip its first point copy, so its bounded waits run out and the
                                  call returns CIQ_ERR_TIMEOUT (the failure-detection path) */
+    int krylov;               /* ciq_krylov_form (default CIQ_KRYLOV_AUTO) */
 } ciq_options;
 
 typedef struct {
@@ -157,6 +176,8 @@ typedef struct {
     int step_launches;        /* profile: recurrence launches timed */
     double ritz_max_solve;    /* largest Ritz value of column 0's msMINRES tridiagonal
                                  (ciq_*_batched_learned only; else 0) */
+    int krylov;               /* ciq_krylov_form the solve ran (RECURRENCE or BASIS) */
+    int reserved;
 } ciq_info;
 
 /* Human-readable name of a status code (static string). */

@@ -17,10 +17,19 @@ Stopping rules (the paper's "relative residual" is not defined further):
                with c_q = w_q (K^{-1/2}) or w_q t_q (K^{1/2}), because
                ||x_q - x_q*|| <= ||r_q|| / lambda_min(K + t_q I).
 Both are evaluated after the update of step j, on a_j, the estimate at step j.
+
+``errbound_norm="scalar"`` replaces ||a_j|| by a norm that needs no vector:
+  K^{1/2}:  ||K^{1/2} b|| = sqrt(b^T K b)  (one extra MVM here; a Lanczos
+            implementation has it as ||b|| sqrt(alpha_1));
+  K^{-1/2}: sqrt(||b||^2 e_1^T T_j^{-1} e_1) <= ||K^{-1/2} b||, the Gauss
+            quadrature rule of the Lanczos tridiagonal T_j (from below);
+both times (1 - 2 tol), so that the bound is <= tol ||a_j|| at the stop as
+well (||a_j|| >= ||a*|| - bound).
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg
 
 from . import kernels
 from .lanczos import lanczos, ritz_extremes, spectral_bounds
@@ -44,9 +53,29 @@ def lanczos_bounds(mvm, start, iters, noise, lmax_margin=1.05, lmin_div=100.0):
     return dict(ritz_min=th_min, ritz_max=th_max, lmin=lmin, lmax=lmax, alpha=alpha, beta=beta)
 
 
+def gauss_invsqrt_norm(alpha, beta):
+    """||b|| sqrt(e_1^T T_j^{-1} e_1), the Gauss quadrature rule for b^T K^{-1} b.
+
+    ``alpha`` (j entries) and ``beta`` (beta[0] = ||b||, then beta_2.. as the
+    msMINRES info lists them) give the Lanczos tridiagonal T_j, solved here
+    with a banded LAPACK solve.  For SPD K this is a lower bound of ||K^{-1/2} b|| that grows
+    with j and is exact once the Krylov space is invariant.
+    """
+    jn = len(alpha)
+    if jn == 0:
+        return 0.0
+    ab = np.zeros((3, jn))                   # T_j in banded storage (super, main, sub)
+    ab[0, 1:] = beta[1:jn]
+    ab[1] = alpha
+    ab[2, :-1] = beta[1:jn]
+    e1 = np.zeros(jn)
+    e1[0] = 1.0
+    return beta[0] * np.sqrt(max(scipy.linalg.solve_banded((1, 1), ab, e1)[0], 0.0))
+
+
 def ciq_apply(mvm, B, Q, op, tol=0.0, max_iter=200, stop_rule="residual", noise=0.0,
               start=None, lanczos_iters=10, lmin=None, lmax=None, nodes=None,
-              sqrt_form="identity", lmax_margin=1.05, lmin_div=100.0):
+              sqrt_form="identity", lmax_margin=1.05, lmin_div=100.0, errbound_norm="estimate"):
     """K^{1/2} B (op="sqrt") or K^{-1/2} B (op="invsqrt") for B of shape (T, n).
 
     Returns (A, info) with A of shape (T, n).
@@ -76,7 +105,14 @@ def ciq_apply(mvm, B, Q, op, tol=0.0, max_iter=200, stop_rule="residual", noise=
             return np.einsum("q,qic->ic", w, Xs)
         return w.sum() * Bc - np.einsum("q,qic->ic", w * t, Xs)
 
-    def stop(j, phibar, Xs):
+    sqrt_norm = None
+    if errbound_norm == "scalar" and op == "sqrt":
+        sqrt_norm = np.sqrt(np.einsum("ic,ic->c", Bc, mvm(Bc)))          # ||K^{1/2} b||
+
+    def gauss_norm(alphas, betas):
+        return np.array([gauss_invsqrt_norm(a, b) for a, b in zip(alphas, betas)])
+
+    def stop(j, phibar, Xs, alphas, betas):
         if tol <= 0.0:
             return np.zeros(phibar.shape[1], dtype=bool)
         if stop_rule == "residual":
@@ -85,6 +121,9 @@ def ciq_apply(mvm, B, Q, op, tol=0.0, max_iter=200, stop_rule="residual", noise=
         bound = np.sum(coef[:, None] * np.abs(phibar) / (t[:, None] + lmin_b), axis=0)
         if op == "sqrt" and sqrt_form == "mvm":
             bound = bound * (info.get("lmax") or 1.0)
+        if errbound_norm == "scalar":
+            den = sqrt_norm if op == "sqrt" else gauss_norm(alphas, betas)
+            return bound <= tol * (1.0 - 2.0 * tol) * den
         return bound <= tol * np.linalg.norm(estimate(Xs), axis=0)
 
     Xs, minfo = msminres(mvm, Bc, t, max_iter, stop)

@@ -35,10 +35,11 @@ BREAKDOWN_RTOL = 1e-13
 def msminres(mvm, B: np.ndarray, shifts: np.ndarray, max_iter: int, stop=None):
     """Solve (K + t_q I) x = b for every shift and every column of ``B``.
 
-    ``B``: (n, T).  ``stop(j, phibar, X) -> bool[T]`` is called after each
-    step with the per-shift residual estimates ``phibar`` (Q, T) and the
-    current solutions ``X`` (Q, n, T); columns for which it returns True
-    freeze.  Returns (X, info) with info holding the iteration count per
+    ``B``: (n, T).  ``stop(j, phibar, X, alphas, betas) -> bool[T]`` is
+    called after each step with the per-shift residual estimates ``phibar``
+    (Q, T), the current solutions ``X`` (Q, n, T) and each column's Lanczos
+    coefficients so far (lists as in the returned info); columns for which it
+    returns True freeze.  Returns (X, info) with info holding the iteration count per
     column, |phibar|, and the Lanczos coefficients per column.
     """
     B = np.asarray(B, dtype=np.float64)
@@ -99,7 +100,7 @@ def msminres(mvm, B: np.ndarray, shifts: np.ndarray, max_iter: int, stop=None):
         beta_j = np.where(m, beta_next, beta_j)
         done = breakdown.copy()
         if stop is not None:
-            done |= stop(j, phibar, X)
+            done |= stop(j, phibar, X, alphas, betas)
         active = active & ~done
     info = dict(iters=iters, phibar=phibar, alpha=[np.array(a) for a in alphas],
                 beta=[np.array(b) for b in betas], beta1=beta1)

@@ -35,6 +35,7 @@ PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16": 3}
 MVM_MODES = {"auto": 0, "onthefly": 1, "stored": 2}
 STOP_RULES = {"residual": 0, "errbound": 1}
 SQRT_FORMS = {"identity": 0, "mvm": 1}
+KRYLOV_FORMS = {"auto": 0, "recurrence": 1, "basis": 2}
 
 
 class CiqError(RuntimeError):
@@ -57,7 +58,7 @@ class _Options(ctypes.Structure):
                 ("lmin_div", ctypes.c_double), ("lmin", ctypes.c_double), ("lmax", ctypes.c_double),
                 ("quad_w", ctypes.c_void_p), ("quad_t", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("graph", ctypes.c_int),
-                ("tc_split", ctypes.c_int), ("fault_inject", ctypes.c_int)]
+                ("tc_split", ctypes.c_int), ("fault_inject", ctypes.c_int), ("krylov", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -70,7 +71,7 @@ class _Info(ctypes.Structure):
                 ("t_total_ms", ctypes.c_double), ("t_prepass_ms", ctypes.c_double),
                 ("t_mvm_ms", ctypes.c_double), ("t_step_ms", ctypes.c_double),
                 ("mvm_launches", ctypes.c_int), ("step_launches", ctypes.c_int),
-                ("ritz_max_solve", ctypes.c_double)]
+                ("ritz_max_solve", ctypes.c_double), ("krylov", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -189,6 +190,8 @@ def make_options(**kw) -> _Options:
             o.stop_rule = STOP_RULES[v] if isinstance(v, str) else int(v)
         elif k == "sqrt_form":
             o.sqrt_form = SQRT_FORMS[v] if isinstance(v, str) else int(v)
+        elif k == "krylov":
+            o.krylov = KRYLOV_FORMS[v] if isinstance(v, str) else int(v)
         elif k in ("lanczos_start", "workspace"):
             setattr(o, k, _ptr(v))
             keep.append(v)
@@ -213,7 +216,8 @@ def _info_dict(info: _Info, status: int) -> dict:
                 w=np.array(info.w[:q]), t=np.array(info.t[:q]), launches=info.launches,
                 t_total_ms=info.t_total_ms, t_prepass_ms=info.t_prepass_ms, t_mvm_ms=info.t_mvm_ms,
                 t_step_ms=info.t_step_ms, mvm_launches=info.mvm_launches,
-                step_launches=info.step_launches, ritz_max_solve=info.ritz_max_solve)
+                step_launches=info.step_launches, ritz_max_solve=info.ritz_max_solve,
+                krylov={v: k for k, v in KRYLOV_FORMS.items()}.get(info.krylov))
 
 
 def _check(status: int, where: str, allow=(CIQ_OK, CIQ_NOT_CONVERGED)):

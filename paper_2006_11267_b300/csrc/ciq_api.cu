@@ -97,7 +97,8 @@ bool valid_options(const ciq_options& o) {
              (o.sqrt_form != CIQ_SQRT_IDENTITY && o.sqrt_form != CIQ_SQRT_MVM) ||
              (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_FP16) ||
              (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED) || o.tc_split < 0 || o.tc_split > 8 ||
-             o.fault_inject < 0 || o.fault_inject > 1);
+             o.fault_inject < 0 || o.fault_inject > 1 || o.krylov < CIQ_KRYLOV_AUTO ||
+             o.krylov > CIQ_KRYLOV_BASIS);
 }
 
 // Pinned host words for the convergence flag, one set per host thread.
@@ -142,8 +143,10 @@ struct Plan {
     bool tri_on = false;          // record column 0's msMINRES tridiagonal
     int tc_max_split = 8;         // CTAs per row tile of the tensor-core MVM (batches: 1)
     int fault_inject = 0;         // ciq_options.fault_inject (testing the bounded-wait path)
+    bool basis = false;           // stored-basis form (CIQ_KRYLOV_BASIS)
     // pointers (valid once an arena base is set)
-    R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB;
+    R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB, *V, *sco;
+    double *rcoef, *gauss, *bco;
     R *sx, *sb, *sout, *sstart;
     float* Kst;
     double *partials, *ynp, *beta, *beta1, *giv, *phifinal, *nodes, *summary, *tri;
@@ -156,12 +159,24 @@ struct Plan {
         Arena a;
         a.base = base;
         Xp = a.take<R>((size_t)Npad * dp);
-        QA = a.take<R>((size_t)T * Npad);
-        QB = a.take<R>((size_t)T * Npad);
+        if (basis) {
+            // q_0 = 0 in slot 0, q_1 in slot 1: the first two slots double as QB, QA.
+            V = a.take<R>(((size_t)jmax + 2) * T * Npad);
+            QB = V;
+            QA = base ? V + (size_t)T * Npad : nullptr;
+        } else {
+            V = nullptr;
+            QA = a.take<R>((size_t)T * Npad);
+            QB = a.take<R>((size_t)T * Npad);
+        }
         Y = a.take<R>((size_t)T * Npad);
         Ylo = a.take<R>((size_t)T * Npad);
         Bw = a.take<R>((size_t)T * Npad);
-        D = a.take<R>((size_t)2 * Q * T * Npad);
+        D = basis ? nullptr : a.take<R>((size_t)2 * Q * T * Npad);
+        rcoef = basis ? a.take<double>((size_t)jmax * Q * T * 4) : nullptr;
+        gauss = basis ? a.take<double>((size_t)2 * T * 4) : nullptr;
+        bco = basis ? a.take<double>(((size_t)jmax + 1) * T) : nullptr;
+        sco = a.take<R>((size_t)T * kScoStride);
         partials = a.take<double>((size_t)nparts * T * 3);
         ynp = a.take<double>((size_t)2 * nchunks * T);
         beta = a.take<double>((size_t)2 * T);
@@ -203,8 +218,26 @@ struct Plan {
     }
 };
 
+// Largest stored basis the AUTO form takes: a quarter of the device memory,
+// at most 64 GiB (64 GiB when no device answers).
+size_t basis_cap_bytes() {
+    const size_t cap = (size_t)64 << 30;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return cap; }
+    return std::min(cap, tot / 4);
+}
+
+// Stored-basis form of a single solve (batched solves always recur).
+bool use_basis(const ciq_options& o, size_t elem, int64_t Npad, int T) {
+    if (o.krylov == CIQ_KRYLOV_RECURRENCE) return false;
+    if (o.krylov == CIQ_KRYLOV_BASIS) return true;
+    const size_t bytes = ((size_t)o.max_iter + 2) * (size_t)T * (size_t)Npad * elem;
+    return elem == 4 && bytes <= basis_cap_bytes();
+}
+
 template <typename R>
-Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool prepass, bool tc) {
+Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool prepass, bool tc,
+                  bool allow_basis = false) {
     Plan<R> p{};
     p.precision = o.precision;
     p.N = N;
@@ -228,6 +261,7 @@ Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool pre
     choose_chunks(p.Npad, T, &p.nchunks, &p.rpc);
     choose_chunks(p.Npad, 1, &p.nchunks1, &p.rpc1);
     p.prepass = prepass;
+    p.basis = allow_basis && use_basis(o, sizeof(R), p.Npad, T);
     p.layout(nullptr);
     return p;
 }
@@ -242,6 +276,7 @@ KrylovState<R> krylov_state(const Plan<R>& p, int op, const ciq_options& o, doub
     s.giv = p.giv; s.phifinal = p.phifinal; s.status = p.status; s.iters = p.iters;
     s.brk = p.brk; s.cnt = p.cnt; s.all_done = p.all_done; s.nodes = p.nodes;
     s.summary = p.summary; s.tri = p.tri; s.jmax = p.jmax; s.op = op; s.stop_rule = o.stop_rule; s.tol = tol;
+    s.basis = p.V; s.rcoef = p.rcoef; s.gauss = p.gauss; s.bco = p.bco; s.sco = p.sco;
     s.breakdown_rtol = sizeof(R) == 4 ? 1e-6 : 1e-13;
     return s;
 }
@@ -375,7 +410,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     const bool prepass = !given_nodes && !given_bounds;
     keep_pool_warm();
 
-    Plan<R> p = make_plan<R>(N, d, T, Q, o, prepass, tc);
+    Plan<R> p = make_plan<R>(N, d, T, Q, o, prepass, tc, true);
     p.stage_x = !device_accessible(X);
     p.stage_b = !device_accessible(B);
     p.stage_out = !device_accessible(out);
@@ -425,6 +460,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         }
         CIQ_TRY(cudaMemsetAsync(p.cnt, 0, sizeof(int) * ((size_t)p.jmax + 2), st));
         CIQ_TRY(cudaMemsetAsync(p.all_done, 0, sizeof(int), st));
+        if (p.basis) CIQ_TRY(cudaMemsetAsync(p.gauss, 0, sizeof(double) * 2 * 4 * (size_t)T, st));
         if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_start, st));
         CIQ_TRY(launch_prepare_points<R, R>(Xd, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
         CIQ_TRY(tc_prepare(p, kern->type, st));
@@ -491,14 +527,21 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                 const int jb = std::min(j + o.check_every - 1, p.jmax);
                 if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][0], st));
                 for (int jj = j; jj <= jb; ++jj) {
-                    a.V = (jj & 1) ? p.QA : p.QB;
-                    a.qprev = (jj & 1) ? p.QB : p.QA;
+                    if (p.basis) {
+                        const size_t vs = (size_t)T * p.Npad;
+                        a.V = p.V + (size_t)jj * vs;
+                        a.qprev = p.V + (size_t)(jj - 1) * vs;
+                        a.pout = p.V + (size_t)(jj + 1) * vs;
+                    } else {
+                        a.V = (jj & 1) ? p.QA : p.QB;
+                        a.qprev = (jj & 1) ? p.QB : p.QA;
+                    }
                     a.beta = p.beta + (size_t)(jj & 1) * T;
                     CIQ_TRY(launch_mvm(p, a, true, st));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
                     CIQ_TRY(launch_msminres_step(s, jj, false, st));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 2], st));
-                    launches += 1 + mvm_launches;
+                    launches += 2 + mvm_launches;
                 }
                 first_j[slot] = j;
                 count[slot] = jb - j + 1;
@@ -526,8 +569,12 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         }
         CIQ_TRY(launch_msminres_step(s, last_j + 1, true, st));
         launches += 1;
+        if (p.basis) {
+            CIQ_TRY(launch_basis_combine(s, outd, last_j, st));   // kOpSqrtMvm: the sum goes to Y
+            launches += 2;
+        }
         if (op == kOpSqrtMvm) {
-            CIQ_TRY(launch_combine(s, outd, st));      // folds the trailing part into Y
+            if (!p.basis) CIQ_TRY(launch_combine(s, outd, st));      // folds the trailing part into Y
             MvmArgs<R> m = mvm_args(p, *kern);
             m.T = T;
             m.mode = kPlain;
@@ -535,8 +582,8 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             m.out = outd;
             m.ldo = N;
             CIQ_TRY(launch_mvm(p, m, false, st));
-            launches += 2;
-        } else {
+            launches += p.basis ? 1 : 2;
+        } else if (!p.basis) {
             CIQ_TRY(launch_combine(s, outd, st));
             launches += 1;
         }
@@ -599,6 +646,7 @@ done:
         info->t_step_ms = t_step;
         info->mvm_launches = n_mvm;
         info->step_launches = n_step;
+        info->krylov = p.basis ? CIQ_KRYLOV_BASIS : CIQ_KRYLOV_RECURRENCE;
     }
     if (tc_timeout) return CIQ_ERR_TIMEOUT;
     if (summary[6] > 0) return CIQ_ERR_NAN;
@@ -1369,7 +1417,7 @@ size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* op
     if (opt) o = *opt;
     const bool prepass = !(o.quad_w && o.quad_t) && !(o.lmin > 0.0 && o.lmax > 0.0);
     const bool tc = o.precision != CIQ_PREC_FP32 && tc_supported(o.precision, d) && tc_padded_t(T) > 0;
-    Plan<float> p = make_plan<float>(N, d, T, Q, o, prepass, tc);
+    Plan<float> p = make_plan<float>(N, d, T, Q, o, prepass, tc, true);
     return p.bytes;
 }
 

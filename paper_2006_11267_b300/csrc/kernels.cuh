@@ -28,6 +28,7 @@ struct MvmArgs {
     R* out;                // kPlain
     int64_t ldo;
     R* qprev;              // kLanczos
+    R* pout;               // kLanczos: where p goes (nullptr: over q_prev)
     const double* beta;    // kLanczos: beta_j per column
     double* partials;      // kLanczos: [ntiles][T][3]
     const int* stop;       // optional: skip the launch when *stop != 0
@@ -35,7 +36,8 @@ struct MvmArgs {
 
 // Epilogue of one output entry O[i][col] (before the noise term): kPlain
 // stores O + sigma^2 v; kLanczos forms p = O + sigma^2 v - beta q_prev (0 on
-// padded rows), writes it over q_prev and accumulates q.p, p.p, q.q in FP64.
+// padded rows), writes it to pout (over q_prev when pout is null) and
+// accumulates q.p, p.p, q.q in FP64.
 template <typename R>
 __device__ __forceinline__ void lanczos_epilogue_value(const MvmArgs<R>& a, int64_t i, int col, R o,
                                                        double& qp, double& pp, double& qq) {
@@ -47,7 +49,7 @@ __device__ __forceinline__ void lanczos_epilogue_value(const MvmArgs<R>& a, int6
         return;
     }
     R p = (i < a.N) ? (R)(o - (R)a.beta[col] * a.qprev[idx]) : (R)0;
-    a.qprev[idx] = p;
+    (a.pout ? a.pout : a.qprev)[idx] = p;
     qp += (double)v * (double)p;
     pp += (double)p * (double)p;
     qq += (double)v * (double)v;

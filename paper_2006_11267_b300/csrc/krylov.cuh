@@ -36,6 +36,10 @@ enum CombineOp {
     kOpSqrtMvm = 2          // y = sum_q w_q x_q, a = K y (MVM launched by the caller)
 };
 
+// Per-column scalars the split recurrence step publishes (skip flag, alpha
+// in two parts, 1/beta_{j+1}, then delta, eps, 1/gamma, c_q tau per shift).
+constexpr int kScoStride = 4 + 4 * CIQ_MAX_Q;
+
 template <typename R>
 struct KrylovState {
     int64_t N, Npad;
@@ -63,6 +67,12 @@ struct KrylovState {
     const double* nodes;        // NodeSlot block
     double* summary;            // [8] filled by the summary kernel
     double* tri;                // optional: column 0's T_j, diagonal [jmax + 1] then off-diagonal [jmax + 2]
+    // Stored-basis form (basis != nullptr): no directions, no Y updates per step.
+    R* basis;                   // [jmax + 2][T][Npad]; slot 0 = q_0 = 0, slot j = q_j (slot j + 1 holds p first)
+    double* rcoef;              // [jmax][Q][T][4]: 1/gamma_j, delta_j, eps_j, tau_j of shift q at step j
+    double* gauss;              // [2][T][4]: LDL^T pivot d_j, u_j^2, sum_k u_k^2/d_k, alpha_1 (parity of j)
+    double* bco;                // [jmax + 1][T]: sum_q c_q y_q(j), the coefficient of q_j
+    R* sco;                     // [T][kScoStride]: scalars of the split step (single solves)
     int jmax;
     int op;                     // CombineOp
     int stop_rule;              // ciq_stop_rule
@@ -99,6 +109,11 @@ template <typename R>
 cudaError_t launch_combine(const KrylovState<R>& s, R* out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_summary(const KrylovState<R>& s, int final_j, cudaStream_t st);
+// Stored-basis form: back-substitution R_q y_q = tau_q per column and shift,
+// then one pass over the basis forming the output (and ||a||^2 partials for
+// the summary in the parity slot of final_j).  kOpSqrtMvm leaves the sum in Y.
+template <typename R>
+cudaError_t launch_basis_combine(const KrylovState<R>& s, R* out, int final_j, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_lanczos_init(const LanczosState<R>& s, const R* start, uint64_t seed,

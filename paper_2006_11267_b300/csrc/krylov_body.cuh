@@ -89,20 +89,30 @@ __device__ __forceinline__ void init_state_body(KrylovState<R> s, int bx, int by
         s.Y[col + i] = (R)0;
         s.Ylo[col + i] = (R)0;
     }
-    for (int e = 0; e < 2 * Q; ++e) {
+    for (int e = 0; s.D && e < 2 * Q; ++e) {
         R* d = s.D + ((int64_t)e * T + c) * s.Npad;
         for (int64_t i = i0 + tid; i < i1; i += 256) d[i] = (R)0;
     }
 }
 
+// BASIS: the stored-basis form (s.basis set).  Steps 1-3 are shared; the
+// Givens factors of every shift are recorded instead of updating Q
+// directions, and the vector work is q_{j+1} = (p - alpha q_j) / beta_{j+1}.
 template <typename R>
-__device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int final_pass, int bx, int by) {
-    if (!final_pass && *s.all_done) return;
-    __shared__ double red[8][3];
-    __shared__ R co_delta[CIQ_MAX_Q], co_eps[CIQ_MAX_Q], co_invg[CIQ_MAX_Q], co_ct[CIQ_MAX_Q];
-    __shared__ R sh_ahi, sh_alo, sh_invb;
-    __shared__ int sh_skip;
-    const int k = bx, c = by, tid = threadIdx.x;
+struct StepShared {
+    double red[8][3];
+    R co_delta[CIQ_MAX_Q], co_eps[CIQ_MAX_Q], co_invg[CIQ_MAX_Q], co_ct[CIQ_MAX_Q];
+    R ahi, alo, invb;
+    int skip;
+};
+
+// Steps 1-3 by one block of 256 threads for column c (k: the block's row
+// chunk; chunk 0 writes the column's scalars).  Returns false when the
+// column does no vector work this step.
+template <typename R, bool BASIS>
+__device__ __forceinline__ bool step_scalars(const KrylovState<R>& s, int j, int final_pass, int k, int c,
+                                             StepShared<R>& sh) {
+    const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int T = s.T, Q = s.Q;
     const int pin = j & 1, pout = (j + 1) & 1;
@@ -124,19 +134,34 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
                 if (s.stop_rule == CIQ_STOP_RESIDUAL) {
                     if (warp_max(ph) <= s.tol * s.beta1[c]) code = kColConverged;
                 } else {
-                    const double cq = lane < Q ? (s.op == kOpSqrtIdentity ? w[lane] * t[lane] : w[lane]) : 0.0;
+                    // Both square-root forms of the stored-basis rule weigh by w_q t_q.
+                    const bool wt = BASIS ? s.op != kOpInvSqrt : s.op == kOpSqrtIdentity;
+                    const double cq = lane < Q ? (wt ? w[lane] * t[lane] : w[lane]) : 0.0;
                     const double bound = warp_sum(lane < Q ? cq * ph / (t[lane] + lmin) : 0.0);
-                    double yn = 0.0;
-                    const double* yp = s.ynp + (int64_t)((j - 1) & 1) * s.nchunks * T;
-                    for (int kk = lane; kk < s.nchunks; kk += 32) yn += yp[(int64_t)kk * T + c];
-                    yn = warp_sum(yn);
-                    if (bound <= s.tol * sqrt(yn)) code = kColConverged;
+                    if constexpr (BASIS) {
+                        // ||K^{1/2} b||^2 = b^T K b = ||b||^2 alpha_1; ||K^{-1/2} b||^2 >=
+                        // ||b||^2 e_1^T T_{j-1}^{-1} e_1 (Gauss rule, from below).  With the
+                        // (1 - 2 tol) factor the bound is also <= tol ||a_j|| at the stop.
+                        // K (sum w_q x_q) is scaled by lambda_max, as in the oracle's reading.
+                        const double* gs = s.gauss + ((int64_t)pin * T + c) * 4;
+                        const double den2 = s.op == kOpInvSqrt ? gs[2] : gs[3];
+                        const double den = (1.0 - 2.0 * s.tol) * s.beta1[c] * sqrt(fmax(den2, 0.0));
+                        const double lm = s.nodes[kNodeLmax];
+                        const double scale = s.op == kOpSqrtMvm && lm > 0.0 ? lm : 1.0;
+                        if (bound * scale <= s.tol * den) code = kColConverged;
+                    } else {
+                        double yn = 0.0;
+                        const double* yp = s.ynp + (int64_t)((j - 1) & 1) * s.nchunks * T;
+                        for (int kk = lane; kk < s.nchunks; kk += 32) yn += yp[(int64_t)kk * T + c];
+                        yn = warp_sum(yn);
+                        if (bound <= s.tol * sqrt(yn)) code = kColConverged;
+                    }
                 }
             }
             if (final_pass && code == kColRunning) code = s.tol > 0.0 ? kColMaxIter : kColFixedIter;
         }
         const bool frozen = (st != kColRunning) || (code != kColRunning);
-        if (lane == 0) sh_skip = frozen || final_pass;
+        if (lane == 0) sh.skip = frozen || final_pass;
         if (k == 0 && (frozen || final_pass)) {
             if (st == kColRunning) {
                 if (lane < Q) s.phifinal[(int64_t)lane * T + c] = gin[((int64_t)lane * T + c) * 5 + 4];
@@ -149,7 +174,7 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
         }
     }
     __syncthreads();
-    if (sh_skip) return;
+    if (sh.skip) return false;
 
     // 2. alpha_j, beta_{j+1} from the MVM partial sums.
     double qp = 0.0, pp = 0.0, qq = 0.0;
@@ -158,12 +183,12 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
         qp += src[0]; pp += src[1]; qq += src[2];
     }
     qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
-    if (lane == 0) { red[warp][0] = qp; red[warp][1] = pp; red[warp][2] = qq; }
+    if (lane == 0) { sh.red[warp][0] = qp; sh.red[warp][1] = pp; sh.red[warp][2] = qq; }
     __syncthreads();
     if (warp == 0) {
-        qp = lane < 8 ? red[lane][0] : 0.0;
-        pp = lane < 8 ? red[lane][1] : 0.0;
-        qq = lane < 8 ? red[lane][2] : 0.0;
+        qp = lane < 8 ? sh.red[lane][0] : 0.0;
+        pp = lane < 8 ? sh.red[lane][1] : 0.0;
+        qq = lane < 8 ? sh.red[lane][2] : 0.0;
         qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
         const double alpha = qp;
         const double b2 = pp - 2.0 * alpha * qp + alpha * alpha * qq;
@@ -185,21 +210,51 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
             const double cj = gbar / gamma, sj = bu / gamma;
             const double tau = cj * ph;
             const double cq = s.op == kOpSqrtIdentity ? w[lane] * t[lane] : w[lane];
-            co_delta[lane] = (R)delta;
-            co_eps[lane] = (R)eps;
-            co_invg[lane] = (R)(1.0 / gamma);
-            co_ct[lane] = (R)(cq * tau);
+            sh.co_delta[lane] = (R)delta;
+            sh.co_eps[lane] = (R)eps;
+            sh.co_invg[lane] = (R)(1.0 / gamma);
+            sh.co_ct[lane] = (R)(cq * tau);
             if (k == 0) {
                 double* go = gout + ((int64_t)lane * T + c) * 5;
                 go[0] = cj; go[1] = sj; go[2] = c1; go[3] = s1; go[4] = -sj * ph;
+                if constexpr (BASIS) {
+                    // Column j of R_q (V_j = D_j R_q) and tau_j: x_q = V_J R_q^{-1} tau.
+                    double* rc = s.rcoef + (((int64_t)(j - 1) * Q + lane) * T + c) * 4;
+                    rc[0] = 1.0 / gamma; rc[1] = delta; rc[2] = eps; rc[3] = tau;
+                }
+            }
+        }
+        if constexpr (BASIS) {
+            // e_1^T T_j^{-1} e_1 by T_j = L D L^T: d_1 = alpha_1, d_k = alpha_k -
+            // beta_k^2 / d_{k-1}, u_k^2 = u_{k-1}^2 beta_k^2 / d_{k-1}^2, sum u_k^2 / d_k.
+            // A non-positive pivot (T_j not numerically SPD) ends the growth.
+            if (k == 0 && lane == 0) {
+                const double* gi = s.gauss + ((int64_t)pin * T + c) * 4;
+                double* go = s.gauss + ((int64_t)pout * T + c) * 4;
+                double dk, u2, S, a1;
+                if (j == 1) {
+                    dk = alpha; u2 = 1.0; S = 0.0; a1 = alpha;
+                } else {
+                    const double dp = gi[0];
+                    S = gi[2]; a1 = gi[3];
+                    if (dp > 0.0) {
+                        u2 = gi[1] * (beta_j / dp) * (beta_j / dp);
+                        dk = alpha - beta_j * (beta_j / dp);
+                    } else {
+                        u2 = 0.0; dk = -1.0;
+                    }
+                }
+                if (dk > 0.0 && isfinite(dk) && isfinite(u2)) S += u2 / dk;
+                else dk = -1.0;
+                go[0] = dk; go[1] = u2; go[2] = S; go[3] = a1;
             }
         }
         if (lane == 0) {
             const R ahi = (R)alpha;
-            sh_ahi = ahi;
-            sh_alo = (R)(alpha - (double)ahi);
-            sh_invb = bd ? (R)0 : (R)(1.0 / beta_next);
-            sh_skip = nan;
+            sh.ahi = ahi;
+            sh.alo = (R)(alpha - (double)ahi);
+            sh.invb = bd ? (R)0 : (R)(1.0 / beta_next);
+            sh.skip = nan;
             if (k == 0) {
                 s.beta[pout * T + c] = bu;
                 s.iters[c] = j;
@@ -212,11 +267,50 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
         }
     }
     __syncthreads();
-    if (sh_skip) return;
+    if (sh.skip) return false;
+    return true;
+}
 
+// Steps 4-5 for row chunk k of column c with the scalars of step_scalars.
+template <typename R, bool BASIS>
+__device__ __forceinline__ void step_vectors(const KrylovState<R>& s, int j, int k, int c, const StepShared<R>& sh) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int T = s.T, Q = s.Q;
     // 4. Vector updates for this chunk of rows.
-    const R ahi = sh_ahi, alo = sh_alo, invb = sh_invb;
+    const R ahi = sh.ahi, alo = sh.alo, invb = sh.invb;
     const int64_t col = (int64_t)c * s.Npad;
+    if constexpr (BASIS) {
+        const int64_t vs = (int64_t)T * s.Npad;
+        const R* qj = s.basis + (int64_t)j * vs + col;
+        R* pn = s.basis + (int64_t)(j + 1) * vs + col;      // p in, q_{j+1} out
+        const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+        const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+        if constexpr (sizeof(R) == 4) {
+            const float4* q4 = reinterpret_cast<const float4*>(qj);
+            float4* p4 = reinterpret_cast<float4*>(pn);
+            for (int64_t i4 = i0 / 4 + tid; i4 < i1 / 4; i4 += 256) {
+                const float4 qv = q4[i4];
+                const float4 pv = p4[i4];
+                const float qa[4] = {qv.x, qv.y, qv.z, qv.w}, pa[4] = {pv.x, pv.y, pv.z, pv.w};
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float t = fmaf(-(float)ahi, qa[e], pa[e]);
+                    t = fmaf(-(float)alo, qa[e], t);
+                    o[e] = t * (float)invb;
+                }
+                p4[i4] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        } else {
+            for (int64_t i = i0 + tid; i < i1; i += 256) {
+                R t = fma(-ahi, qj[i], pn[i]);
+                t = fma(-alo, qj[i], t);
+                pn[i] = t * invb;
+            }
+        }
+        return;
+    }
     const R* q_j = ((j & 1) ? s.QA : s.QB) + col;
     R* pbuf = ((j & 1) ? s.QB : s.QA) + col;
     R* y = s.Y + col;
@@ -267,7 +361,7 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
                 for (int u = 0; u < QB; ++u) {
                     if (q0 + u >= Q) break;
                     const int qq2 = q0 + u;
-                    const float de = co_delta[qq2], ep = co_eps[qq2], ig = co_invg[qq2], ct = co_ct[qq2];
+                    const float de = sh.co_delta[qq2], ep = sh.co_eps[qq2], ig = sh.co_invg[qq2], ct = sh.co_ct[qq2];
                     const float pa[4] = {dpv[u].x, dpv[u].y, dpv[u].z, dpv[u].w};
                     const float oa[4] = {dqv[u].x, dqv[u].y, dqv[u].z, dqv[u].w};
                     float dn[4];
@@ -329,9 +423,9 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
                 for (int u = 0; u < QB; ++u) {
                     if (q0 + u >= Q) break;
                     const int qq2 = q0 + u;
-                    const R dn = (q - co_delta[qq2] * dp[u] - co_eps[qq2] * dq[u]) * co_invg[qq2];
+                    const R dn = (q - sh.co_delta[qq2] * dp[u] - sh.co_eps[qq2] * dq[u]) * sh.co_invg[qq2];
                     d_old[(int64_t)qq2 * dstride + i] = dn;
-                    acc = fma(co_ct[qq2], dn, acc);
+                    acc = fma(sh.co_ct[qq2], dn, acc);
                 }
             }
             pn = fma(-ahi, q, pn);
@@ -363,6 +457,58 @@ __device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int 
     }
 }
 
+// Fused step (batched solves): every block computes the scalars of its
+// column itself, in the same order as the single-solve scalar kernel.
+template <typename R, bool BASIS = false>
+__device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int final_pass, int bx, int by) {
+    if (!final_pass && *s.all_done) return;
+    __shared__ StepShared<R> sh;
+    if (!step_scalars<R, BASIS>(s, j, final_pass, bx, by, sh)) return;
+    step_vectors<R, BASIS>(s, j, bx, by, sh);
+}
+
+// Split step (single solves): one block per column computes the scalars
+// once and publishes them (sco); the row-chunk blocks only read them.  The
+// FP64 work is then done once per column instead of once per row chunk,
+// where the chunks of one SM would queue on its FP64 pipe.
+template <typename R, bool BASIS>
+__device__ __forceinline__ void step_scalar_body(KrylovState<R> s, int j, int final_pass, int c) {
+    if (!final_pass && *s.all_done) return;
+    __shared__ StepShared<R> sh;
+    const bool go = step_scalars<R, BASIS>(s, j, final_pass, 0, c, sh);
+    if (final_pass) return;
+    R* dst = s.sco + (int64_t)c * kScoStride;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        dst[0] = go ? (R)0 : (R)1;
+        dst[1] = sh.ahi; dst[2] = sh.alo; dst[3] = sh.invb;
+    }
+    if (go && !BASIS && tid < s.Q) {
+        dst[4 + tid] = sh.co_delta[tid];
+        dst[4 + CIQ_MAX_Q + tid] = sh.co_eps[tid];
+        dst[4 + 2 * CIQ_MAX_Q + tid] = sh.co_invg[tid];
+        dst[4 + 3 * CIQ_MAX_Q + tid] = sh.co_ct[tid];
+    }
+}
+
+template <typename R, bool BASIS>
+__device__ __forceinline__ void step_vector_body(KrylovState<R> s, int j, int k, int c) {
+    if (*s.all_done) return;
+    const R* src = s.sco + (int64_t)c * kScoStride;
+    if (src[0] != (R)0) return;
+    __shared__ StepShared<R> sh;
+    const int tid = threadIdx.x;
+    if (tid == 0) { sh.ahi = src[1]; sh.alo = src[2]; sh.invb = src[3]; }
+    if (!BASIS && tid < s.Q) {
+        sh.co_delta[tid] = src[4 + tid];
+        sh.co_eps[tid] = src[4 + CIQ_MAX_Q + tid];
+        sh.co_invg[tid] = src[4 + 2 * CIQ_MAX_Q + tid];
+        sh.co_ct[tid] = src[4 + 3 * CIQ_MAX_Q + tid];
+    }
+    __syncthreads();
+    step_vectors<R, BASIS>(s, j, k, c, sh);
+}
+
 template <typename R>
 __device__ __forceinline__ void combine_body(KrylovState<R> s, R* out, int bx, int by) {
     const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
@@ -374,6 +520,127 @@ __device__ __forceinline__ void combine_body(KrylovState<R> s, R* out, int bx, i
     if (s.op == kOpSqrtIdentity) v = s.nodes[kNodeSumW] * (double)s.Bw[src] - yv;
     if (s.op == kOpSqrtMvm) s.Y[src] = (R)yv;      // folded into one vector for the final MVM
     out[(int64_t)c * s.N + i] = (R)v;
+}
+
+// Stored-basis form, part 1: one warp per column, one lane per shift.  Back
+// substitution R_q y_q = tau_q (R_q upper triangular with gamma_j, delta_{j+1},
+// eps_{j+2} on its three diagonals) from the last step down, in FP64, and the
+// CIQ combination sum_q c_q y_q(j) of every basis vector's coefficient.  The
+// factors come through shared memory 32 steps at a time and the sums over
+// shifts are taken after each group, so the FP64 chain carries only
+// y_j = ((tau_j - eps_{j+2} y_{j+2}) - delta_{j+1} y_{j+1}) / gamma_j.
+template <typename R>
+__device__ __forceinline__ void basis_backsub_body(KrylovState<R> s, int c) {
+    constexpr int CH = 32;
+    __shared__ double co[CH][CIQ_MAX_Q][4];
+    __shared__ double cy[CH][CIQ_MAX_Q + 1];
+    const int lane = threadIdx.x & 31, T = s.T, Q = s.Q;
+    const int J = s.iters[c];
+    const double* w = s.nodes + kNodeW;
+    const double* t = s.nodes + kNodeT;
+    const bool on = lane < Q;
+    const double cq = on ? (s.op == kOpSqrtIdentity ? w[lane] * t[lane] : w[lane]) : 0.0;
+    double y1 = 0.0, y2 = 0.0, dl1 = 0.0, ep1 = 0.0, ep2 = 0.0;   // y_{j+1}, y_{j+2}, delta_{j+1}, eps_{j+1}, eps_{j+2}
+    for (int jt = J; jt >= 1; jt -= CH) {                // steps jt, jt - 1, ..., jt - n + 1
+        const int n = min(CH, jt);
+        __syncwarp();
+        for (int idx = lane; idx < n * Q * 4; idx += 32) {
+            const int u = idx / (Q * 4), q = (idx / 4) % Q, e = idx % 4;
+            co[u][q][e] = s.rcoef[(((int64_t)(jt - u - 1) * Q + q) * T + c) * 4 + e];
+        }
+        __syncwarp();
+        if (on) {
+            for (int u = 0; u < n; ++u) {
+                const double invg = co[u][lane][0], de = co[u][lane][1], ep = co[u][lane][2], tau = co[u][lane][3];
+                const double y = fma(-dl1, y1, fma(-ep2, y2, tau)) * invg;
+                ep2 = ep1; ep1 = ep; dl1 = de; y2 = y1; y1 = y;
+                cy[u][lane] = cq * y;
+            }
+        }
+        __syncwarp();
+        if (lane < n) {
+            double tot = 0.0;
+            for (int q = 0; q < Q; ++q) tot += cy[lane][q];
+            s.bco[(int64_t)(jt - lane) * T + c] = tot;
+        }
+    }
+}
+
+// Stored-basis form, part 2: one block per (row chunk, column).  The sum
+// sum_j coef_j q_j runs over the basis once, in FP32 with the coefficient split
+// in two floats, the exact product error (FMA) and Knuth's 2Sum, so that the
+// K^{1/2} identity form's cancellation against (sum w) b keeps FP32 accuracy.
+template <typename R>
+__device__ __forceinline__ void basis_combine_body(KrylovState<R> s, R* out, int final_j, int k, int c) {
+    __shared__ float2 cof[256];
+    __shared__ double cod[256];
+    __shared__ double red[8];
+    const int tid = threadIdx.x, T = s.T;
+    const int J = s.iters[c];
+    const int64_t vs = (int64_t)T * s.Npad;
+    const int64_t col = (int64_t)c * s.Npad;
+    const int64_t i0 = (int64_t)k * s.rows_per_chunk;
+    const int64_t i1 = min(i0 + s.rows_per_chunk, s.Npad);
+    const double sumw = s.nodes[kNodeSumW];
+    constexpr int RPT = sizeof(R) == 4 ? 4 : 1;           // rows per thread
+    double ysq = 0.0;
+    for (int64_t base = i0; base < i1; base += 256 * RPT) {
+        const int64_t i = base + (int64_t)RPT * tid;
+        const bool act = i < i1;
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        double acc = 0.0;
+        for (int jb = 1; jb <= J; jb += 256) {
+            const int nj = min(256, J - jb + 1);
+            __syncthreads();
+            if (tid < nj) {
+                const double cf = s.bco[(int64_t)(jb + tid) * T + c];
+                const float h = (float)cf;
+                cof[tid] = make_float2(h, (float)(cf - (double)h));
+                cod[tid] = cf;
+            }
+            __syncthreads();
+            if (!act) continue;
+            const R* vp = s.basis + (int64_t)jb * vs + col + i;
+            if constexpr (sizeof(R) == 4) {
+#pragma unroll 4
+                for (int u = 0; u < nj; ++u) {
+                    const float2 cf = cof[u];
+                    const float4 v4 = *reinterpret_cast<const float4*>(vp + (int64_t)u * vs);
+                    const float va[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float pr = cf.x * va[e];
+                        const float pe = fmaf(cf.x, va[e], -pr) + cf.y * va[e];
+                        const float sm = hi[e] + pr;
+                        const float bp = sm - hi[e];
+                        lo[e] += ((hi[e] - (sm - bp)) + (pr - bp)) + pe;
+                        hi[e] = sm;
+                    }
+                }
+            } else {
+                for (int u = 0; u < nj; ++u) acc = fma(cod[u], (double)vp[(int64_t)u * vs], acc);
+            }
+        }
+        if (!act) continue;
+#pragma unroll
+        for (int e = 0; e < RPT; ++e) {
+            const int64_t r = i + e;
+            const double sv = sizeof(R) == 4 ? (double)hi[e] + (double)lo[e] : acc;
+            double v = sv;
+            if (s.op == kOpSqrtIdentity) v = sumw * (double)s.Bw[col + r] - sv;
+            if (s.op == kOpSqrtMvm) s.Y[col + r] = (R)sv;
+            else if (r < s.N) out[(int64_t)c * s.N + r] = (R)v;
+            ysq += v * v;
+        }
+    }
+    ysq = warp_sum(ysq);
+    if ((tid & 31) == 0) red[tid >> 5] = ysq;
+    __syncthreads();
+    if (tid == 0) {
+        double r = 0.0;
+        for (int ww = 0; ww < 8; ++ww) r += red[ww];
+        s.ynp[((int64_t)(final_j & 1) * s.nchunks + k) * T + c] = r;
+    }
 }
 
 // summary[0] max iters, [1] min iters, [2] converged columns, [3] max |phibar|/||b||,

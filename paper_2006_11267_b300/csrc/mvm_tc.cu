@@ -699,7 +699,7 @@ __device__ __forceinline__ void tc_finish_body(const TcPoints& p, const MvmArgs<
     const float* part = p.part + (int64_t)tile * S * TP * kTcBM + (int64_t)cl * kTcBM + r0;
     const int64_t i0 = tile * kTcBM + r0;
     const int64_t base = (int64_t)c * a.ldv + i0;
-    float* pdst = a.qprev;                                // p is written over q_{j-1}
+    float* pdst = a.pout ? a.pout : a.qprev;              // p: over q_{j-1} unless pout is set
     float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int half = 0; half < 2 && active; ++half) {

@@ -43,6 +43,8 @@ def hand_problem(n, d, t, seed, kind, ls, noise):
 
 
 def single(op, pr, Q, tol, **opts):
+    # batched solves run the direction recurrence; the single call is asked for it
+    opts = dict(opts, krylov="recurrence")
     fn = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
     if pr.get("lmin"):
         opts = dict(opts, lmin=pr["lmin"], lmax=pr["lmax"])

@@ -103,10 +103,11 @@ def fp32_tol(op, kappa):
     return 1e-5 if op == "sqrt" else max(1e-5, 20 * U32 * np.sqrt(kappa))
 
 
+@pytest.mark.parametrize("krylov", ["recurrence", "basis"])
 @pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
 @pytest.mark.parametrize("kind,n,d,t,Q,J", [("matern52", 777, 3, 3, 8, 800), ("rbf", 1025, 6, 17, 12, 600),
                                              ("matern52", 300, 2, 64, 15, 600), ("rbf", 2000, 4, 8, 10, 900)])
-def test_fp32_solve_matches_serial_oracle_at_equal_nodes_and_J(op, kind, n, d, t, Q, J):
+def test_fp32_solve_matches_serial_oracle_at_equal_nodes_and_J(op, kind, n, d, t, Q, J, krylov):
     X, B, k = problem(n, d, t, 200 + n, kind, ls=0.25)
     K = dense_K(X, k)
     lam = np.linalg.eigvalsh(K)
@@ -115,9 +116,39 @@ def test_fp32_solve_matches_serial_oracle_at_equal_nodes_and_J(op, kind, n, d, t
     assert np.max(info_o["errbound"] / np.linalg.norm(ref, axis=1)) < 1e-9      # oracle converged
     fn = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
     out, info = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), Q, 0.0,
-                   max_iter=J, nodes=nodes, lmin=k.noise)
-    assert info["iters"] == J
+                   max_iter=J, nodes=nodes, lmin=k.noise, krylov=krylov)
+    assert info["iters"] == J and info["krylov"] == krylov
     assert rel(out.cpu().numpy(), ref) < fp32_tol(op, lam[-1] / lam[0])
+
+
+@pytest.mark.parametrize("op,form", [("sqrt", "identity"), ("sqrt", "mvm"), ("invsqrt", "identity")])
+def test_basis_errbound_stop_matches_oracle_scalar_norm_rule(op, form):
+    # The stored-basis error-bound rule (||b|| sqrt(alpha_1), Gauss rule) at equal
+    # nodes: the true error stays <= tol, the result agrees with the oracle's
+    # errbound_norm="scalar" run, and the stop comes within a few steps of the
+    # direction recurrence's (same FP32 Lanczos; FP32 needs more steps than the
+    # FP64 oracle, whose stop is therefore not compared).
+    X, B, k = problem(1500, 3, 8, 31, "matern52", ls=0.25)
+    K = dense_K(X, k)
+    lam = np.linalg.eigvalsh(K)
+    nodes = O.quad_nodes(k.noise, 1.05 * lam[-1], 12)
+    tol = 1e-4
+    ref, info_o = O.ciq_apply(O.dense_mvm(K), B.astype(np.float64), 12, op, tol=tol, max_iter=1500,
+                              stop_rule="errbound", nodes=nodes, lmin=k.noise, lmax=1.05 * lam[-1],
+                              sqrt_form=form, errbound_norm="scalar")
+    fn = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
+    out, info = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), 12, tol, max_iter=1500,
+                   nodes=nodes, lmin=k.noise, lmax=1.05 * lam[-1], stop_rule="errbound", sqrt_form=form)
+    assert info["status"] == 0 and info["krylov"] == "basis"              # the default for FP32
+    if form == "identity":                 # the MVM form's recurrence rule is on y, not on K y
+        _, info_r = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), 12, tol, max_iter=1500,
+                       nodes=nodes, lmin=k.noise, lmax=1.05 * lam[-1], stop_rule="errbound",
+                       krylov="recurrence")
+        assert abs(info["iters"] - info_r["iters"]) <= max(3, int(0.02 * info["iters"]))
+    exact = (eig.sqrt_apply if op == "sqrt" else eig.invsqrt_apply)(K, B.T.astype(np.float64)).T
+    err = np.linalg.norm(out.cpu().numpy() - exact, axis=1) / np.linalg.norm(exact, axis=1)
+    assert err.max() <= 1.05 * tol
+    assert rel(out.cpu().numpy(), ref) < 10 * tol
 
 
 @pytest.mark.parametrize("op", ["sqrt", "invsqrt"])

@@ -70,8 +70,9 @@ def test_tc_mvm_accumulation_at_50k_points_sampled_rows():
     assert rel(out.cpu().numpy().T[rows], ref) < 2e-5
 
 
+@pytest.mark.parametrize("krylov", ["recurrence", "basis"])
 @pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
-def test_tc_fp16_solve_against_eig_oracle(op):
+def test_tc_fp16_solve_against_eig_oracle(op, krylov):
     X = f32(ci.points(20201106, 2048, 3))
     B = f32(ci.rhs(20201106, 2048, 40))
     k = P.Kernel("matern52", 0.2, 1.0, 1e-2)
@@ -79,8 +80,8 @@ def test_tc_fp16_solve_against_eig_oracle(op):
     ref = (eig.sqrt_apply if op == "sqrt" else eig.invsqrt_apply)(K, B.T.astype(np.float64)).T
     fn = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
     out, info = fn(torch.from_numpy(X).cuda(), k, torch.from_numpy(B).cuda(), 15, 1e-4, stop_rule="errbound",
-                   max_iter=2000, precision="fp16")
-    assert info["status"] == 0
+                   max_iter=2000, precision="fp16", krylov=krylov)
+    assert info["status"] == 0 and info["krylov"] == krylov
     err = np.linalg.norm(out.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() < 1e-3
 
@@ -92,7 +93,7 @@ def test_tc_fp16_full_size_square_root_property():
     B = torch.from_numpy(f32(ci.rhs(W.seed, W.n, W.t))).cuda()
     k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
     A, info = P.ciq_sqrt(X, k, B, W.q, 1e-3, stop_rule="errbound", max_iter=4000, precision="fp16")
-    assert info["status"] == 0
+    assert info["status"] == 0 and info["krylov"] == "basis"          # the stored basis (47.7 GiB) by default
     A2, _ = P.ciq_sqrt(X, k, A[:4].contiguous(), W.q, 1e-4, stop_rule="errbound", max_iter=4000, precision="fp16")
     KB = P.ciq_kernel_mvm(X, k, B[:4].contiguous(), precision="fp32")
     e = (torch.linalg.norm(A2 - KB, dim=1) / torch.linalg.norm(KB, dim=1)).cpu().numpy()

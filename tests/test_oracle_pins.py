@@ -378,3 +378,38 @@ def test_errbound_stop_rule_bounds_true_error():
     err = np.linalg.norm(A - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert (err <= 1.05e-3).all()
     assert (info["iters"] < 500).all()
+
+
+def test_scalar_norms_of_the_basis_stop_rule():
+    """||K^{1/2} b||^2 = ||b||^2 alpha_1, and the Gauss rule ||b||^2 e_1^T T_j^{-1} e_1
+    approaches ||K^{-1/2} b||^2 from below, reaching it when the Krylov space is
+    the whole space (both against the eigendecomposition)."""
+    X, K, B = _matern_problem(120, 5)
+    b = B[0]
+    half = eig.sqrt_apply(K, b[:, None])[:, 0]
+    ihalf = eig.invsqrt_apply(K, b[:, None])[:, 0]
+    _, info = msminres(lambda V: K @ V, b[:, None], np.array([0.5]), 120)
+    alpha, beta = info["alpha"][0], info["beta"][0]
+    assert abs(beta[0] ** 2 * alpha[0] - half @ half) < 1e-12 * (half @ half)
+    g = [ciq.gauss_invsqrt_norm(alpha[:j], beta[:j + 1]) for j in range(1, len(alpha) + 1)]
+    exact = np.linalg.norm(ihalf)
+    assert all(v <= exact * (1 + 1e-10) for v in g)
+    assert all(g2 >= g1 * (1 - 1e-12) for g1, g2 in zip(g, g[1:]))
+    assert g[0] < 0.9 * exact
+    assert abs(g[-1] - exact) < 1e-8 * exact
+
+
+@pytest.mark.parametrize("op,form", [("sqrt", "identity"), ("sqrt", "mvm"), ("invsqrt", "identity")])
+def test_errbound_with_scalar_norm_bounds_true_error(op, form):
+    X, K, B = _matern_problem(300, 21)
+    lam = np.linalg.eigvalsh(K)
+    w, t = quad_nodes(lam[0], lam[-1], 15)
+    ref = (eig.sqrt_apply if op == "sqrt" else eig.invsqrt_apply)(K, B.T).T
+    A, info = ciq.ciq_apply(ciq.dense_mvm(K), B, 15, op, nodes=(w, t), tol=1e-3, stop_rule="errbound",
+                            max_iter=500, lmin=lam[0], lmax=lam[-1], sqrt_form=form, errbound_norm="scalar")
+    err = np.linalg.norm(A - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert (err <= 1.05e-3).all()
+    assert (info["iters"] < 500).all()
+    # the bound also holds against the returned estimate's own norm
+    if form == "identity":
+        assert (info["errbound"] <= 1e-3 * np.linalg.norm(A, axis=1)).all()
