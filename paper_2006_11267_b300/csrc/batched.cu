@@ -113,13 +113,18 @@ __global__ void batched_bounds_nodes_kernel(const BatchProblem* probs, int Q, do
     bounds_nodes_body<float>(s, bp.nodes, Q, bp.noise, lmax_margin, lmin_div, 0, 0);
 }
 
-__global__ void __launch_bounds__(256, 3) batched_step_kernel(const BatchProblem* probs, int j, int final_pass,
-                                                           DevList L) {
+__global__ void __launch_bounds__(256) batched_step_scalar_kernel(const BatchProblem* probs, int j, int final_pass,
+                                                                  DevList L) {
+    int p, local;
+    if (!list_item(L, blockIdx.x, p, local)) return;
+    step_scalar_body<float, false>(probs[p].ks, j, final_pass, local);
+}
+
+__global__ void __launch_bounds__(256, 3) batched_step_vector_kernel(const BatchProblem* probs, int j, DevList L) {
     int p, local;
     if (!list_item(L, blockIdx.x, p, local)) return;
     const KrylovState<float> s = probs[p].ks;
-    const int nbx = final_pass ? 1 : s.nchunks;
-    msminres_step_body<float>(s, j, final_pass, local % nbx, local / nbx);
+    step_vector_body<float, false>(s, j, local % s.nchunks, local / s.nchunks);
 }
 
 // Largest eigenvalue of the symmetric tridiagonal (diag[0..J), off[1..J))
@@ -310,10 +315,16 @@ cudaError_t launch_batched_bounds_nodes(const BatchProblem* probs, int Q, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_batched_step(const BatchProblem* probs, int j, bool final_pass, DevList L, int blocks,
-                                cudaStream_t st) {
+cudaError_t launch_batched_step_scalar(const BatchProblem* probs, int j, bool final_pass, DevList L, int blocks,
+                                       cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    batched_step_kernel<<<blocks, 256, 0, st>>>(probs, j, final_pass ? 1 : 0, L);
+    batched_step_scalar_kernel<<<blocks, 256, 0, st>>>(probs, j, final_pass ? 1 : 0, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_step_vector(const BatchProblem* probs, int j, DevList L, int blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    batched_step_vector_kernel<<<blocks, 256, 0, st>>>(probs, j, L);
     return cudaGetLastError();
 }
 

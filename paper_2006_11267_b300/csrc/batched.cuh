@@ -28,7 +28,7 @@ struct BatchProblem {
     int mvm_items;
     int pre_tiles;              // row tiles of the pre-pass MVM (= its items)
     TcPoints tcp;               // tensor-core operands (tensor-core batches only)
-    int list_items[9];          // work items of this problem in each main-loop list (0: not a member)
+    int list_items[10];         // work items of this problem in each main-loop list (0: not a member)
 };
 
 constexpr int kBatchClasses = 8;            // 2 kernel types x 4 padded dimensions
@@ -63,13 +63,15 @@ __device__ __forceinline__ bool list_item(const DevList& L, int item, int& p, in
 
 // Main-loop lists rebuilt on the device, kBatchDynLists in all.  CUDA-core
 // batches: one per MVM class (kernel type x padded dimension), then the
-// recurrence list.  Tensor-core batches: list 0 is the MVM work of every
+// recurrence lists.  Tensor-core batches: list 0 is the MVM work of every
 // problem (both kernel types), list 2 the V split, list 3 the finishing pass
-// (one item per row tile and 16 columns), the last the recurrence.
-constexpr int kBatchDynLists = kBatchClasses + 1;
+// (one item per row tile and 16 columns).  The last two are the recurrence
+// step's vector part (row chunk x column) and scalar part (one per column).
+constexpr int kBatchDynLists = kBatchClasses + 2;
 constexpr int kListTcSplit = 2;
 constexpr int kListTcFinish = 3;
-static_assert(kBatchDynLists == 9, "BatchProblem::list_items size");
+constexpr int kListStepScalar = kBatchClasses + 1;
+static_assert(kBatchDynLists == 10, "BatchProblem::list_items size");
 struct DynLists {
     DevList l[kBatchDynLists];
 };
@@ -98,8 +100,12 @@ cudaError_t launch_batched_mvm(const BatchProblem* probs, int cls, int T, bool p
 cudaError_t launch_batched_lanczos_step(const BatchProblem* probs, int j, DevList L, int blocks, cudaStream_t st);
 cudaError_t launch_batched_bounds_nodes(const BatchProblem* probs, int Q, double lmax_margin, double lmin_div,
                                         DevList L, int blocks, cudaStream_t st);
-cudaError_t launch_batched_step(const BatchProblem* probs, int j, bool final_pass, DevList L, int blocks,
-                                cudaStream_t st);
+// The recurrence step in two launches, as for single solves: the scalars of
+// every listed column (one item per column; the final decision pass is this
+// launch alone), then the vector work (one item per row chunk and column).
+cudaError_t launch_batched_step_scalar(const BatchProblem* probs, int j, bool final_pass, DevList L, int blocks,
+                                       cudaStream_t st);
+cudaError_t launch_batched_step_vector(const BatchProblem* probs, int j, DevList L, int blocks, cudaStream_t st);
 // Summary of every listed problem, gathered with its node block into
 // packed[p * kSummaryStride ...] (summary[8], then the NodeSlot block).
 cudaError_t launch_batched_summary(const BatchProblem* probs, int final_j, double* packed, DevList L, int blocks,

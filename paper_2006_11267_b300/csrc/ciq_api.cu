@@ -779,6 +779,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
             b.list_items[b.cls] = b.mvm_items;
         }
         b.list_items[kBatchClasses] = pl.nchunks * T;
+        b.list_items[kListStepScalar] = T;
         for (int l = 0; l < kBatchDynLists; ++l)
             if (b.list_items[l] > 0) dyn[l].add(p, b.list_items[l]);
         if (given[p]) {
@@ -990,8 +991,10 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                             ++launches;
                         }
                     }
-                    CIQ_TRY(launch_batched_step(probs_d, jj, false, dyn_d.l[kBatchClasses], grid[kBatchClasses], ls));
-                    ++launches;
+                    CIQ_TRY(launch_batched_step_scalar(probs_d, jj, false, dyn_d.l[kListStepScalar],
+                                                       grid[kListStepScalar], ls));
+                    CIQ_TRY(launch_batched_step_vector(probs_d, jj, dyn_d.l[kBatchClasses], grid[kBatchClasses], ls));
+                    launches += 2;
                 }
                 last_j = jb;
                 CIQ_TRY(launch_rebuild_lists(probs_d, P, dyn_d, totals_d, ls));
@@ -1031,7 +1034,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                 if (stop) break;
             }
         }
-        CIQ_TRY(launch_batched_step(probs_d, last_j + 1, true, L(fin), fin.total(), st));
+        CIQ_TRY(launch_batched_step_scalar(probs_d, last_j + 1, true, L(fin), fin.total(), st));
         CIQ_TRY(setup(kBatchCombine, comb));
         CIQ_TRY(launch_batched_summary(probs_d, last_j, packed_d, L(one), one.total(), st));
         launches += 2;

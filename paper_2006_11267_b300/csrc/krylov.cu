@@ -4,9 +4,8 @@
 // (p = K q_j - beta_j q_{j-1} and FP64 partial sums of q.p, p.p, q.q) and
 // the recurrence step, split in two launches: step_scalar (one block per
 // column: steps 1-3) and step_vector (one block per row chunk and column:
-// steps 4-5).  Batched solves run both parts in one launch per block
-// (msminres_step_body), in the same arithmetic order, so that their results
-// equal single solves bit for bit.
+// steps 4-5).  Batched solves launch the same two bodies over their work
+// lists, so their results equal single solves bit for bit.
 //
 //  1. decide whether the column stopped after step j-1 (stop rule, breakdown);
 //  2. alpha_j = q.p and beta_{j+1}^2 = p.p - 2 alpha q.p + alpha^2 q.q in FP64

@@ -98,6 +98,8 @@ __device__ __forceinline__ void init_state_body(KrylovState<R> s, int bx, int by
 // BASIS: the stored-basis form (s.basis set).  Steps 1-3 are shared; the
 // Givens factors of every shift are recorded instead of updating Q
 // directions, and the vector work is q_{j+1} = (p - alpha q_j) / beta_{j+1}.
+// The bodies take explicit block coordinates so that single solves and
+// batched solves (batched.cu) run the same code.
 template <typename R>
 struct StepShared {
     double red[8][3];
@@ -457,20 +459,10 @@ __device__ __forceinline__ void step_vectors(const KrylovState<R>& s, int j, int
     }
 }
 
-// Fused step (batched solves): every block computes the scalars of its
-// column itself, in the same order as the single-solve scalar kernel.
-template <typename R, bool BASIS = false>
-__device__ __forceinline__ void msminres_step_body(KrylovState<R> s, int j, int final_pass, int bx, int by) {
-    if (!final_pass && *s.all_done) return;
-    __shared__ StepShared<R> sh;
-    if (!step_scalars<R, BASIS>(s, j, final_pass, bx, by, sh)) return;
-    step_vectors<R, BASIS>(s, j, bx, by, sh);
-}
-
-// Split step (single solves): one block per column computes the scalars
-// once and publishes them (sco); the row-chunk blocks only read them.  The
-// FP64 work is then done once per column instead of once per row chunk,
-// where the chunks of one SM would queue on its FP64 pipe.
+// The step in two launches: one block per column computes the scalars once
+// and publishes them (sco); the row-chunk blocks only read them.  The FP64
+// work is then done once per column instead of once per row chunk, where
+// the chunks of one SM would queue on its FP64 pipe.
 template <typename R, bool BASIS>
 __device__ __forceinline__ void step_scalar_body(KrylovState<R> s, int j, int final_pass, int c) {
     if (!final_pass && *s.all_done) return;
