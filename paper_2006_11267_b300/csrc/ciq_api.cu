@@ -332,9 +332,10 @@ cudaError_t tc_prepare(const Plan<R>& p, int kt, cudaStream_t st) {
 // unit_columns: V's columns have norm 1 (Lanczos vectors), which fixes the
 // power-of-two operand scale of the tensor-core MVM.
 template <typename R>
-cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns, cudaStream_t st) {
+cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns, cudaStream_t st,
+                       bool scale_ready = false) {
     if constexpr (sizeof(R) == 4) {
-        if (p.tc) return launch_mvm_tc(p.tcp, a, unit_columns, st);
+        if (p.tc) return launch_mvm_tc(p.tcp, a, unit_columns, st, scale_ready);
         if (p.stored) return launch_stored_mvm(p.Kst, p.Npad, a, st);
     }
     return launch_mvm_simt(a, st);
@@ -492,9 +493,13 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         a.mode = kLanczos;
         a.partials = p.partials;
         a.stop = p.all_done;
-        // Kernels per MVM: one on CUDA cores; on tensor cores the V scale,
-        // the V split and, per column group, the product and the finish.
-        const int mvm_launches = p.tc ? 2 + 2 * ((T + tc_group_t(T) - 1) / tc_group_t(T)) : 1;
+        // Kernels per MVM: one on CUDA cores; on tensor cores the V split
+        // and, per column group, the product and the finish (the V scale of
+        // unit columns is set by the first MVM only).
+        const int mvm_launches = p.tc ? 1 + 2 * ((T + tc_group_t(T) - 1) / tc_group_t(T)) : 1;
+        // Stored basis on tensor cores: the V split of MVM j + 1 finishes
+        // step j's vector update (q_{j+1} from p and the published scalars).
+        const bool lz = p.basis && p.tc;
         CIQ_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
         CIQ_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         if (prof.on) {
@@ -532,16 +537,18 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                         a.V = p.V + (size_t)jj * vs;
                         a.qprev = p.V + (size_t)(jj - 1) * vs;
                         a.pout = p.V + (size_t)(jj + 1) * vs;
+                        a.lz_q = lz && jj > 1 ? a.qprev : nullptr;
+                        a.lz_sco = lz && jj > 1 ? p.sco : nullptr;
                     } else {
                         a.V = (jj & 1) ? p.QA : p.QB;
                         a.qprev = (jj & 1) ? p.QB : p.QA;
                     }
                     a.beta = p.beta + (size_t)(jj & 1) * T;
-                    CIQ_TRY(launch_mvm(p, a, true, st));
+                    CIQ_TRY(launch_mvm(p, a, true, st, jj > 1));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
-                    CIQ_TRY(launch_msminres_step(s, jj, false, st));
+                    CIQ_TRY(launch_msminres_step(s, jj, false, st, !lz));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 2], st));
-                    launches += 2 + mvm_launches;
+                    launches += (lz ? 1 : 2) + mvm_launches + (p.tc && jj == 1 ? 1 : 0);
                 }
                 first_j[slot] = j;
                 count[slot] = jb - j + 1;

@@ -29,6 +29,12 @@ struct MvmArgs {
     int64_t ldo;
     R* qprev;              // kLanczos
     R* pout;               // kLanczos: where p goes (nullptr: over q_prev)
+    // Optional (tensor-core MVM only): V holds p of the previous step and the
+    // V split first finishes that step's Lanczos update in place, V = (V -
+    // alpha q) / beta per column from lz_sco rows [skip, alpha_hi, alpha_lo,
+    // 1/beta] (kScoStride apart; skip != 0 leaves the column as it is).
+    const R* lz_q;
+    const R* lz_sco;
     const double* beta;    // kLanczos: beta_j per column
     double* partials;      // kLanczos: [ntiles][T][3]
     const int* stop;       // optional: skip the launch when *stop != 0

@@ -136,13 +136,13 @@ int step_blocks_per_wave() {
 }
 
 template <typename R>
-cudaError_t launch_msminres_step(const KrylovState<R>& s, int j, bool final_pass, cudaStream_t st) {
+cudaError_t launch_msminres_step(const KrylovState<R>& s, int j, bool final_pass, cudaStream_t st, bool vector_part) {
     // One block per column for the scalars, then the row chunks (none after
     // the final decision pass).
     const int fp = final_pass ? 1 : 0;
     if (s.basis) step_scalar_kernel<R, true><<<s.T, 256, 0, st>>>(s, j, fp);
     else step_scalar_kernel<R, false><<<s.T, 256, 0, st>>>(s, j, fp);
-    if (!final_pass) {
+    if (!final_pass && vector_part) {
         const dim3 grid(s.nchunks, s.T);
         if (s.basis) step_vector_kernel<R, true><<<grid, 256, 0, st>>>(s, j);
         else step_vector_kernel<R, false><<<grid, 256, 0, st>>>(s, j);
@@ -190,7 +190,7 @@ cudaError_t launch_nodes_from_bounds(double* nodes, int Q, double lmin, double l
 #define CIQ_INSTANTIATE(R)                                                                          \
     template cudaError_t launch_init_rhs<R>(const KrylovState<R>&, const R*, cudaStream_t);           \
     template cudaError_t launch_init_state<R>(const KrylovState<R>&, cudaStream_t);                   \
-    template cudaError_t launch_msminres_step<R>(const KrylovState<R>&, int, bool, cudaStream_t);     \
+    template cudaError_t launch_msminres_step<R>(const KrylovState<R>&, int, bool, cudaStream_t, bool); \
     template cudaError_t launch_combine<R>(const KrylovState<R>&, R*, cudaStream_t);                  \
     template cudaError_t launch_basis_combine<R>(const KrylovState<R>&, R*, int, cudaStream_t);       \
     template cudaError_t launch_summary<R>(const KrylovState<R>&, int, cudaStream_t);                 \

@@ -101,8 +101,11 @@ template <typename R>
 cudaError_t launch_init_rhs(const KrylovState<R>& s, const R* B, cudaStream_t st);
 template <typename R>
 cudaError_t launch_init_state(const KrylovState<R>& s, cudaStream_t st);
+// vector_part = false leaves step 4 to the next MVM (the tensor-core V split
+// of the stored-basis form finishes q_{j+1} from the published scalars).
 template <typename R>
-cudaError_t launch_msminres_step(const KrylovState<R>& s, int j, bool final_pass, cudaStream_t st);
+cudaError_t launch_msminres_step(const KrylovState<R>& s, int j, bool final_pass, cudaStream_t st,
+                                 bool vector_part = true);
 // Recurrence blocks resident at once on the device (SMs x blocks per SM).
 int step_blocks_per_wave();
 template <typename R>

@@ -214,15 +214,33 @@ __global__ void tc_vscale_kernel(const float* V, int64_t ldv, int64_t N, int T, 
 // [tile][part][col/8][K-core][col%8][row%8] at vblk + g * (Npad/64) * 2 tpg 128.
 template <bool HALF>
 __device__ __forceinline__ void tc_split_v_body(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
-                                                const float* vscale, uint8_t* vblk, int64_t idx) {
+                                                const float* vscale, uint8_t* vblk, int64_t idx,
+                                                const float* lz_q = nullptr, const float* lz_sco = nullptr) {
     const int64_t groups = Npad / 8;
     if (idx >= groups * TP) return;
     const int c = (int)(idx / groups);
     const int64_t j0 = (idx % groups) * 8;
     float x[8];
     if (c < T) {
-        const float4 a = *reinterpret_cast<const float4*>(V + (int64_t)c * ldv + j0);
-        const float4 b = *reinterpret_cast<const float4*>(V + (int64_t)c * ldv + j0 + 4);
+        float4 a = *reinterpret_cast<const float4*>(V + (int64_t)c * ldv + j0);
+        float4 b = *reinterpret_cast<const float4*>(V + (int64_t)c * ldv + j0 + 4);
+        if (lz_sco && lz_sco[(int64_t)c * kScoStride] == 0.f) {
+            // The previous step's q_{j+1} = (p - alpha q_j) / beta_{j+1}, in the
+            // recurrence step's operation order, stored over p.
+            const float* sc = lz_sco + (int64_t)c * kScoStride;
+            const float ah = sc[1], al = sc[2], ib = sc[3];
+            const float4 qa = *reinterpret_cast<const float4*>(lz_q + (int64_t)c * ldv + j0);
+            const float4 qb = *reinterpret_cast<const float4*>(lz_q + (int64_t)c * ldv + j0 + 4);
+            float pv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) pv[e] = fmaf(-al, qv[e], fmaf(-ah, qv[e], pv[e])) * ib;
+            a = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            b = make_float4(pv[4], pv[5], pv[6], pv[7]);
+            float4* dst = reinterpret_cast<float4*>(const_cast<float*>(V) + (int64_t)c * ldv + j0);
+            dst[0] = a;
+            dst[1] = b;
+        }
         const float s = vscale[c];
         x[0] = a.x * s; x[1] = a.y * s; x[2] = a.z * s; x[3] = a.w * s;
         x[4] = b.x * s; x[5] = b.y * s; x[6] = b.z * s; x[7] = b.w * s;
@@ -244,8 +262,9 @@ __device__ __forceinline__ void tc_split_v_body(const float* V, int64_t ldv, int
 
 template <bool HALF>
 __global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
-                                  const float* vscale, uint8_t* vblk) {
-    tc_split_v_body<HALF>(V, ldv, T, TP, tpg, Npad, vscale, vblk, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+                                  const float* vscale, uint8_t* vblk, const float* lz_q, const float* lz_sco) {
+    tc_split_v_body<HALF>(V, ldv, T, TP, tpg, Npad, vscale, vblk, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                          lz_q, lz_sco);
 }
 
 // The kernel walks K's columns in steps of kTcKN = 128 (two 64-row operand
@@ -999,21 +1018,25 @@ cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_columns, cudaStream_t st) {
+cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_columns, cudaStream_t st,
+                          bool scale_ready) {
     if (p.TP < 0 || a.T > p.TP || a.Npad != p.Npad || a.ldv != a.Npad) return cudaErrorInvalidValue;
-    const float unit_scale = ldexpf(1.f, (int)floor(0.5 * log2((double)a.N)));
-    tc_vscale_kernel<<<p.TP, 256, 0, st>>>(a.V, a.ldv, a.N, a.T, p.TP, unit_scale, unit_columns ? 1 : 0, p.vscale);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!(unit_columns && scale_ready)) {
+        const float unit_scale = ldexpf(1.f, (int)floor(0.5 * log2((double)a.N)));
+        tc_vscale_kernel<<<p.TP, 256, 0, st>>>(a.V, a.ldv, a.N, a.T, p.TP, unit_scale, unit_columns ? 1 : 0,
+                                               p.vscale);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const int64_t work = (a.Npad / 8) * p.TP;
     if (p.half)
         tc_split_v_kernel<true><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a.V, a.ldv, a.T, p.TP,
                                                                                  tc_group_t(a.T), a.Npad,
-                                                                                 p.vscale, p.vblk);
+                                                                                 p.vscale, p.vblk, a.lz_q, a.lz_sco);
     else
         tc_split_v_kernel<false><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a.V, a.ldv, a.T, p.TP,
                                                                                   tc_group_t(a.T), a.Npad,
-                                                                                  p.vscale, p.vblk);
+                                                                                  p.vscale, p.vblk, a.lz_q, a.lz_sco);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // V is split into groups of tpg columns; group g's tiles start at
     // vblk + g * (Npad / 64) * 2 * tpg * 128.

@@ -45,6 +45,9 @@ cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int
 // Split V into vblk (unit_columns: every column has norm 1, so one fixed
 // power-of-two scale is used; otherwise per-column scales from the norms)
 // and run the tensor-core MVM with the epilogue of `a`.
-cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_columns, cudaStream_t st);
+// unit_columns: V's columns have norm 1 (one power-of-two scale for all);
+// scale_ready: that scale is already in p.vscale (the V-scale launch is skipped).
+cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_columns, cudaStream_t st,
+                          bool scale_ready = false);
 
 }  // namespace ciq
