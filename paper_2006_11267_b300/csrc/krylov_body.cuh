@@ -178,7 +178,24 @@ __device__ __forceinline__ bool step_scalars(const KrylovState<R>& s, int j, int
     __syncthreads();
     if (sh.skip) return false;
 
-    // 2. alpha_j, beta_{j+1} from the MVM partial sums.
+    // 2. alpha_j, beta_{j+1} from the MVM partial sums.  Every operand of
+    // step 3 that does not depend on them is loaded first: the chain below is
+    // FP64 (about 65 cycles per FMA, 430 per division, 670 per square root on
+    // this part), and loads issued after its stores could not move above them.
+    double c1 = 1.0, s1 = 0.0, c2 = 1.0, s2 = 0.0, ph = 0.0, tq = 0.0, cq = 0.0, beta_j = 0.0;
+    double g_dp = 0.0, g_u2 = 0.0, g_S = 0.0, g_a1 = 0.0;
+    if (warp == 0) {
+        const int ql = lane < Q ? lane : 0;
+        const double* g = gin + ((int64_t)ql * T + c) * 5;
+        c1 = g[0]; s1 = g[1]; c2 = g[2]; s2 = g[3]; ph = g[4];
+        tq = t[ql];
+        cq = s.op == kOpSqrtIdentity ? w[ql] * tq : w[ql];
+        beta_j = s.beta[pin * T + c];
+        if constexpr (BASIS) {
+            const double* gi = s.gauss + ((int64_t)pin * T + c) * 4;
+            g_dp = gi[0]; g_u2 = gi[1]; g_S = gi[2]; g_a1 = gi[3];
+        }
+    }
     double qp = 0.0, pp = 0.0, qq = 0.0;
     for (int r = tid; r < s.nparts; r += 256) {
         const double* src = s.partials + ((int64_t)r * T + c) * 3;
@@ -195,26 +212,25 @@ __device__ __forceinline__ bool step_scalars(const KrylovState<R>& s, int j, int
         const double alpha = qp;
         const double b2 = pp - 2.0 * alpha * qp + alpha * alpha * qq;
         const double beta_next = sqrt(fmax(b2, 0.0));
-        const double beta_j = s.beta[pin * T + c];
         const bool nan = !isfinite(alpha) || !isfinite(beta_next);
         const bool bd = nan || !(beta_next > s.breakdown_rtol * (fabs(alpha) + beta_j));
         const double bu = bd ? 0.0 : beta_next;
-        // 3. Givens QR update for every shift (one lane per shift).
+        const double inv_beta = bd ? 0.0 : 1.0 / beta_next;
+        // 3. Givens QR update for every shift (one lane per shift; every lane
+        // computes, lanes >= Q on shift 0's data and store nothing).
+        const double abar = alpha + tq;
+        const double eps = s2 * beta_j;
+        const double dbar = c2 * beta_j;
+        const double delta = c1 * dbar + s1 * abar;
+        const double gbar = -s1 * dbar + c1 * abar;
+        const double gamma = sqrt(gbar * gbar + bu * bu);
+        const double ig = 1.0 / gamma;
+        const double cj = gbar * ig, sj = bu * ig;
+        const double tau = cj * ph;
         if (lane < Q) {
-            const double* g = gin + ((int64_t)lane * T + c) * 5;
-            const double c1 = g[0], s1 = g[1], c2 = g[2], s2 = g[3], ph = g[4];
-            const double abar = alpha + t[lane];
-            const double eps = s2 * beta_j;
-            const double dbar = c2 * beta_j;
-            const double delta = c1 * dbar + s1 * abar;
-            const double gbar = -s1 * dbar + c1 * abar;
-            const double gamma = sqrt(gbar * gbar + bu * bu);
-            const double cj = gbar / gamma, sj = bu / gamma;
-            const double tau = cj * ph;
-            const double cq = s.op == kOpSqrtIdentity ? w[lane] * t[lane] : w[lane];
             sh.co_delta[lane] = (R)delta;
             sh.co_eps[lane] = (R)eps;
-            sh.co_invg[lane] = (R)(1.0 / gamma);
+            sh.co_invg[lane] = (R)ig;
             sh.co_ct[lane] = (R)(cq * tau);
             if (k == 0) {
                 double* go = gout + ((int64_t)lane * T + c) * 5;
@@ -222,7 +238,7 @@ __device__ __forceinline__ bool step_scalars(const KrylovState<R>& s, int j, int
                 if constexpr (BASIS) {
                     // Column j of R_q (V_j = D_j R_q) and tau_j: x_q = V_J R_q^{-1} tau.
                     double* rc = s.rcoef + (((int64_t)(j - 1) * Q + lane) * T + c) * 4;
-                    rc[0] = 1.0 / gamma; rc[1] = delta; rc[2] = eps; rc[3] = tau;
+                    rc[0] = ig; rc[1] = delta; rc[2] = eps; rc[3] = tau;
                 }
             }
         }
@@ -230,24 +246,19 @@ __device__ __forceinline__ bool step_scalars(const KrylovState<R>& s, int j, int
             // e_1^T T_j^{-1} e_1 by T_j = L D L^T: d_1 = alpha_1, d_k = alpha_k -
             // beta_k^2 / d_{k-1}, u_k^2 = u_{k-1}^2 beta_k^2 / d_{k-1}^2, sum u_k^2 / d_k.
             // A non-positive pivot (T_j not numerically SPD) ends the growth.
+            double dk, u2, S, a1;
+            if (j == 1) {
+                dk = alpha; u2 = 1.0; S = 0.0; a1 = alpha;
+            } else {
+                S = g_S; a1 = g_a1;
+                const double r = beta_j / g_dp;
+                u2 = g_dp > 0.0 ? g_u2 * r * r : 0.0;
+                dk = g_dp > 0.0 ? alpha - beta_j * r : -1.0;
+            }
+            if (dk > 0.0 && isfinite(dk) && isfinite(u2)) S += u2 / dk;
+            else dk = -1.0;
             if (k == 0 && lane == 0) {
-                const double* gi = s.gauss + ((int64_t)pin * T + c) * 4;
                 double* go = s.gauss + ((int64_t)pout * T + c) * 4;
-                double dk, u2, S, a1;
-                if (j == 1) {
-                    dk = alpha; u2 = 1.0; S = 0.0; a1 = alpha;
-                } else {
-                    const double dp = gi[0];
-                    S = gi[2]; a1 = gi[3];
-                    if (dp > 0.0) {
-                        u2 = gi[1] * (beta_j / dp) * (beta_j / dp);
-                        dk = alpha - beta_j * (beta_j / dp);
-                    } else {
-                        u2 = 0.0; dk = -1.0;
-                    }
-                }
-                if (dk > 0.0 && isfinite(dk) && isfinite(u2)) S += u2 / dk;
-                else dk = -1.0;
                 go[0] = dk; go[1] = u2; go[2] = S; go[3] = a1;
             }
         }
@@ -255,7 +266,7 @@ __device__ __forceinline__ bool step_scalars(const KrylovState<R>& s, int j, int
             const R ahi = (R)alpha;
             sh.ahi = ahi;
             sh.alo = (R)(alpha - (double)ahi);
-            sh.invb = bd ? (R)0 : (R)(1.0 / beta_next);
+            sh.invb = (R)inv_beta;
             sh.skip = nan;
             if (k == 0) {
                 s.beta[pout * T + c] = bu;
