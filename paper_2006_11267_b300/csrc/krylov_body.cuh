@@ -547,9 +547,16 @@ __device__ __forceinline__ void basis_backsub_body(KrylovState<R> s, int c) {
     for (int jt = J; jt >= 1; jt -= CH) {                // steps jt, jt - 1, ..., jt - n + 1
         const int n = min(CH, jt);
         __syncwarp();
-        for (int idx = lane; idx < n * Q * 4; idx += 32) {
-            const int u = idx / (Q * 4), q = (idx / 4) % Q, e = idx % 4;
-            co[u][q][e] = s.rcoef[(((int64_t)(jt - u - 1) * Q + q) * T + c) * 4 + e];
+        if (on) {
+            // Lane q copies its own factors; unrolled so that eight steps' loads
+            // are in flight at once (the shared stores cannot alias them).
+#pragma unroll 8
+            for (int u = 0; u < n; ++u) {
+                const double2* src =
+                    reinterpret_cast<const double2*>(s.rcoef + (((int64_t)(jt - u - 1) * Q + lane) * T + c) * 4);
+                const double2 a = src[0], b = src[1];
+                co[u][lane][0] = a.x; co[u][lane][1] = a.y; co[u][lane][2] = b.x; co[u][lane][3] = b.y;
+            }
         }
         __syncwarp();
         if (on) {
