@@ -264,6 +264,22 @@ def dist_env():
     return world, rank, local
 
 
+def whole_job_rate(elapsed_ms, units_per_rank, dist=None, device="cpu"):
+    """The slowest rank's timed region and the whole-job rate over it.
+
+    Every rank passes its own elapsed time (ms) and the units it processed;
+    with a process group the times are reduced with MAX, so the rate is the
+    units all ranks processed divided by the slowest rank's time.
+    """
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    if world > 1:
+        import torch
+        t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, units_per_rank * world / (elapsed_ms * 1e-3)
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -358,13 +374,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    elapsed_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms, value = whole_job_rate(e0.elapsed_time(e1), W.t * args.steps, dist if world > 1 else None, dev)
     ms_per_step = elapsed_ms / args.steps
-    value = W.t * args.steps * world / (elapsed_ms * 1e-3)
     launches = sum(i["launches"] for i in infos)
     # One profiled solve: per-launch CUDA events on the library's stream.
     pinfo = step(profile=1)
@@ -372,12 +383,12 @@ def run_ours(args):
     t_mvm = pinfo["t_mvm_ms"] / max(1, pinfo["mvm_launches"])
     t_rec = pinfo["t_step_ms"] / max(1, pinfo["step_launches"])
     pk, pk_kind = peaks()
-    dev = device_peaks()
+    devpk = device_peaks()
     if args.precision == "fp32":
         roof = roofline_fp32(W.n, W.t, W.d, t_mvm, pk)
         roof["peak_source"] = pk_kind
     else:
-        roof = roofline_tc(W, t_mvm, dev, pk)
+        roof = roofline_tc(W, t_mvm, devpk, pk)
     fp32 = None
     if not args.no_fp32_compare and args.precision != "fp32":
         o32 = dict(opts, precision="fp32")
@@ -398,11 +409,14 @@ def run_ours(args):
         out_h = np.empty_like(B)
         for _ in range(1):
             P.ciq_sqrt(X, k, B, W.q, TOL, out=out_h, **opts)
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             P.ciq_sqrt(X, k, B, W.q, TOL, out=out_h, **opts)
-        t_e2e = (time.perf_counter() - t0) / args.steps
-        e2e = {"value": W.t * world / t_e2e, "unit": "RHS-solves/s",
+        _, e2e_rate = whole_job_rate((time.perf_counter() - t0) * 1e3, W.t * args.steps,
+                                     dist if world > 1 else None, dev)
+        e2e = {"value": e2e_rate, "unit": "RHS-solves/s",
                "h2d_bytes_per_step": int(X.nbytes + B.nbytes), "d2h_bytes_per_step": int(out_h.nbytes)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -432,7 +446,7 @@ def run_ours(args):
                             "recurrence_share": pinfo["t_step_ms"] / max(pinfo["t_total_ms"], 1e-9),
                             "prepass_ms": pinfo["t_prepass_ms"], "total_ms": pinfo["t_total_ms"]},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-                "plain_fp32_gpu_path": fp32, "device_peaks": dev}
+                "plain_fp32_gpu_path": fp32, "device_peaks": devpk}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
