@@ -76,10 +76,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--workload", default="thompson50k",
-                    choices=["thompson50k", "batched512", "precision200k", "learned", "stored"],
+                    choices=["thompson50k", "batched512", "precision200k", "learned", "stored", "spectrum"],
                     help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
                          "the 200,000-point Matern precision sweep; learned: train the bound predictor on "
-                         "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones")
+                         "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones; "
+                         "spectrum: K^{1/2}b error against Q on matrices with prescribed spectra")
     ap.add_argument("--n", type=int, default=0, metavar="N",
                     help="run the headline solve on the first N points only (for profiling captures)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
@@ -826,6 +827,65 @@ def run_learned(args):
     return 0
 
 
+def run_spectrum(args):
+    """The Q sweep of Sec. 5 (Fig. quad_error) on explicit matrices through
+    ciq_sqrt_dense: spectra lambda_t = 1/sqrt(t) and 1/t^2 (K = U diag(lambda)
+    U^T, U Haar-orthogonal) and a one-dimensional Matern-5/2 matrix on random
+    points (l = 0.2, sigma^2 = 1e-4, formed by the library), N = 1024 and 4096,
+    8 right-hand sides, Lanczos bounds, relative residual 1e-4 or J = 400 as
+    in the study.  Error: relative 2-norm against the eigendecomposition of
+    the FP32 matrix the solve sees (FP64 eigh on the host)."""
+    import torch
+
+    import paper_2006_11267_b300 as P
+
+    torch.cuda.set_device(0)
+    T, qs, kinds = 8, (2, 4, 6, 8, 12, 16), ("inv_sqrt", "inv_square", "matern1d")
+    table = {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    worst8 = 0.0
+    for kind in kinds:
+        table[kind] = {}
+        for n in (1024, 4096):
+            if kind == "matern1d":
+                npad = -(-n // 128) * 128
+                X = torch.from_numpy(ci.points(20201109, n, 1).astype(np.float32)).cuda()
+                Kd = torch.empty((npad, npad), dtype=torch.float32, device="cuda")
+                P.ciq_kernel_matrix(X, P.Kernel("matern52", 0.2, 1.0, 1e-4), Kd)
+                K32 = Kd[:n, :n].cpu().numpy()
+                Kd = Kd[:n].contiguous()
+            else:
+                K32 = ci.spectrum_matrix(20201109, n, kind)[0].astype(np.float32)
+                Kd = torch.from_numpy(K32).cuda()
+            B = ci.rhs(20201110, n, T).astype(np.float32)
+            w, V = np.linalg.eigh(K32.astype(np.float64))
+            exact = (V * np.sqrt(np.clip(w, 0.0, None))[None, :]) @ (V.T @ B.T.astype(np.float64))
+            Bd = torch.from_numpy(B).cuda()
+            row = {"kappa": float(w[-1] / w[0]) if w[0] > 0 else None}
+            for q in qs:
+                P.ciq_sqrt_dense(Kd, Bd, q, 1e-4, max_iter=400, stop_rule="residual")
+                torch.cuda.synchronize()
+                e0.record()
+                out, info = P.ciq_sqrt_dense(Kd, Bd, q, 1e-4, max_iter=400, stop_rule="residual")
+                e1.record()
+                torch.cuda.synchronize()
+                A = out.cpu().numpy().T.astype(np.float64)
+                err = float(np.max(np.linalg.norm(A - exact, axis=0) / np.linalg.norm(exact, axis=0)))
+                row[str(q)] = {"rel_err": err, "iters": info["iters"], "ms": e0.elapsed_time(e1)}
+                if q == 8:
+                    worst8 = max(worst8, err)
+            table[kind][str(n)] = row
+    line = {"metric": "K^{1/2}b relative error against Q (synthetic spectra, explicit K)", "value": worst8,
+            "unit": "max relative error at Q = 8", "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False,
+            "dtype": "f32 stored K, f32 vectors, f64 scalars", "data": "synthetic",
+            "config": {"workload": "spectrum_sweep_t8", "T": T, "Q": list(qs), "N": [1024, 4096],
+                       "stop_rule": "residual", "tol": 1e-4, "max_iter": 400, "spectra": list(kinds)},
+            "table": table}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -838,6 +898,8 @@ def main():
         return run_stored(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "spectrum":
+        return run_spectrum(args)
     return run_ours(args)
 
 

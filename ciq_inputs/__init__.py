@@ -82,6 +82,39 @@ def rhs(seed: int, n: int, t: int) -> np.ndarray:
     return normal(stream_seed(seed, STREAM_B), n * t).reshape(t, n)
 
 
+STREAM_ORTHO = 4
+
+
+def orthogonal(seed: int, n: int) -> np.ndarray:
+    """A Haar-distributed n x n orthogonal matrix (FP64): the Q factor of a
+    seeded Gaussian matrix with the signs of R's diagonal moved into Q."""
+    G = normal(stream_seed(seed, STREAM_ORTHO), n * n).reshape(n, n)
+    Qm, R = np.linalg.qr(G)
+    return Qm * np.sign(np.diag(R))[None, :]
+
+
+SPECTRA = ("inv_sqrt", "inv_square")
+
+
+def spectrum(kind: str, n: int) -> np.ndarray:
+    """Eigenvalues of the synthetic matrices of the Q-sweep study (Sec. 5,
+    Fig. quad_error): lambda_t = 1/sqrt(t) or 1/t^2, t = 1..n, descending."""
+    t = np.arange(1, n + 1, dtype=np.float64)
+    if kind == "inv_sqrt":
+        return 1.0 / np.sqrt(t)
+    if kind == "inv_square":
+        return 1.0 / t ** 2
+    raise ValueError(kind)
+
+
+def spectrum_matrix(seed: int, n: int, kind: str):
+    """(K, lam, U): K = U diag(lam) U^T in FP64 with U = orthogonal(seed, n)."""
+    lam = spectrum(kind, n)
+    U = orthogonal(seed, n)
+    K = (U * lam[None, :]) @ U.T
+    return 0.5 * (K + K.T), lam, U
+
+
 def start_vector(seed: int, n: int) -> np.ndarray:
     """Lanczos start vector with entries ``2u - 1`` (float64).
 

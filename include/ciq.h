@@ -253,6 +253,23 @@ ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel*
 ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T,
                           float* out, ciq_stream_t stream);
 
+/* K^{1/2} B and K^{-1/2} B for a caller's explicit symmetric positive
+ * definite K: the general-matrix case of Sec. 3.3 (any K with an MVM; here
+ * the stored-K MVM, O(J N^2) per solve), used e.g. for matrices with a
+ * prescribed spectrum (Sec. 5, Fig. quad_error).  K: N x N row-major floats
+ * with leading dimension ldk >= N, host or device (copied once into the
+ * workspace's zero-padded Npad x Npad layout; only the FP32 path exists, so
+ * opt->precision must be CIQ_PREC_FP32, else CIQ_ERR_UNSUPPORTED).  B, out,
+ * opt, info and the return codes are those of ciq_sqrt.  There is no noise
+ * term: without opt->lmin/lmax the pre-pass bounds are lambda_max =
+ * lmax_margin theta_max and lambda_min = theta_min / lmin_div (reading R4 for
+ * sigma^2 = 0).  Workspace: ciq_workspace_bytes(N, 1, T, Q, opt with mvm =
+ * CIQ_MVM_STORED). */
+ciq_status ciq_sqrt_dense(const float* K, int64_t N, int64_t ldk, const float* B, int T, int Q, double tol,
+                          const ciq_options* opt, float* out, ciq_info* info, ciq_stream_t stream);
+ciq_status ciq_invsqrt_dense(const float* K, int64_t N, int64_t ldk, const float* B, int T, int Q, double tol,
+                             const ciq_options* opt, float* out, ciq_info* info, ciq_stream_t stream);
+
 /* One problem of a batch: X (device, N x d), B and out (device, T columns of
  * N floats).  lmin, lmax > 0 give this problem's spectral bounds and skip its
  * Lanczos pre-pass (e.g. bounds predicted by a learned model); otherwise the

@@ -108,6 +108,8 @@ def lib() -> ctypes.CDLL:
         "ciq_kernel_mvm_f64": (I, [P, I64, I, KP, P, I, P, P]),
         "ciq_kernel_matrix": (I, [P, I64, I, KP, P, I64, P]),
         "ciq_stored_mvm": (I, [P, I64, I64, P, I, P, P]),
+        "ciq_sqrt_dense": (I, [P, I64, I64, P, I, I, D, OP, P, IP, P]),
+        "ciq_invsqrt_dense": (I, [P, I64, I64, P, I, I, D, OP, P, IP, P]),
         "ciq_workspace_bytes": (S, [I64, I, I, I, OP]),
         "ciq_kernel_mvm_noalloc": (I, [P, I64, I, KP, P, I, P, P]),
         "ciq_noalloc_scratch_floats": (S, []),
@@ -325,6 +327,33 @@ def ciq_stored_mvm(Kmat, V, out=None, n=None):
     st = lib().ciq_stored_mvm(_ptr(Kmat), N, Kmat.shape[1], _ptr(V), T, _ptr(out), _stream(Kmat, V, out))
     _check(st, "ciq_stored_mvm", allow=(CIQ_OK,))
     return out
+
+
+def _solve_dense(name, K, B, Q, tol, out=None, **opts):
+    N = K.shape[0]
+    if K.ndim != 2 or K.shape[1] < N:
+        raise ValueError("K must have shape (N, ldk) with ldk >= N")
+    T = B.shape[0]
+    if B.shape[1] != N:
+        raise ValueError("B must have shape (T, N)")
+    if out is None:
+        out = _empty_like_rhs(B, np.float32)
+    o = make_options(**opts)
+    info = _Info()
+    st = getattr(lib(), name)(_ptr(K), N, K.shape[1], _ptr(B), T, int(Q), float(tol), ctypes.byref(o), _ptr(out),
+                              ctypes.byref(info), _stream(K, B, out))
+    _check(st, name)
+    return out, _info_dict(info, st)
+
+
+def ciq_sqrt_dense(K, B, Q, tol=0.0, out=None, **opts):
+    """K^{1/2} B for an explicit SPD matrix K (N x N, FP32, row-major). Returns (out, info)."""
+    return _solve_dense("ciq_sqrt_dense", K, B, Q, tol, out, **opts)
+
+
+def ciq_invsqrt_dense(K, B, Q, tol=0.0, out=None, **opts):
+    """K^{-1/2} B for an explicit SPD matrix K (N x N, FP32, row-major). Returns (out, info)."""
+    return _solve_dense("ciq_invsqrt_dense", K, B, Q, tol, out, **opts)
 
 
 def ciq_workspace_bytes(N, d, T, Q, **opts):

@@ -378,17 +378,24 @@ struct Profile {
     }
 };
 
+// Kd: a caller's explicit matrix (N x N, leading dimension ldk) instead of X
+// and a kernel; the solve then runs on the stored-K MVM with no noise term.
 template <typename R>
 ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* B, int T, int Q,
                  double tol, const ciq_options* opt, R* out, ciq_info* info, cudaStream_t st,
-                 int op, bool fp64) {
-    if (!X || !B || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q ||
-        !(tol >= 0.0) || !valid_kernel(kern))
+                 int op, bool fp64, const float* Kd = nullptr, int64_t ldk = 0) {
+    const bool dense = Kd != nullptr;
+    if ((!dense && !X) || !B || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q ||
+        !(tol >= 0.0) || !valid_kernel(kern) || (dense && (ldk < N || fp64)))
         return CIQ_ERR_ARG;
     ciq_options o;
     ciq_default_options(&o);
     if (opt) o = *opt;
     if (!valid_options(o)) return CIQ_ERR_ARG;
+    if (dense) {
+        if (o.precision != CIQ_PREC_FP32) return CIQ_ERR_UNSUPPORTED;
+        o.mvm = CIQ_MVM_STORED;
+    }
     if ((o.quad_w == nullptr) != (o.quad_t == nullptr)) return CIQ_ERR_ARG;
     if (o.mvm == CIQ_MVM_STORED && !fp64 && o.precision != CIQ_PREC_FP32) return CIQ_ERR_UNSUPPORTED;
     bool tc = false;
@@ -412,7 +419,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     keep_pool_warm();
 
     Plan<R> p = make_plan<R>(N, d, T, Q, o, prepass, tc, true);
-    p.stage_x = !device_accessible(X);
+    p.stage_x = !dense && !device_accessible(X);
     p.stage_b = !device_accessible(B);
     p.stage_out = !device_accessible(out);
     p.stage_start = prepass && o.lanczos_start && !device_accessible(o.lanczos_start);
@@ -463,10 +470,18 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         CIQ_TRY(cudaMemsetAsync(p.all_done, 0, sizeof(int), st));
         if (p.basis) CIQ_TRY(cudaMemsetAsync(p.gauss, 0, sizeof(double) * 2 * 4 * (size_t)T, st));
         if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_start, st));
-        CIQ_TRY(launch_prepare_points<R, R>(Xd, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
-        CIQ_TRY(tc_prepare(p, kern->type, st));
-        CIQ_TRY(form_stored(p, *kern, st));
-        launches += p.stored ? 1 : 0;
+        if (dense) {
+            // The caller's matrix into the zero-padded Npad x Npad layout.
+            CIQ_TRY(cudaMemsetAsync(p.Kst, 0, sizeof(float) * (size_t)p.Npad * p.Npad, st));
+            CIQ_TRY(cudaMemcpy2DAsync(p.Kst, sizeof(float) * p.Npad, Kd, sizeof(float) * ldk, sizeof(float) * N, N,
+                                      cudaMemcpyDefault, st));
+            CIQ_TRY(cudaMemsetAsync(p.Xp, 0, sizeof(R) * (size_t)p.Npad * p.dp, st));
+        } else {
+            CIQ_TRY(launch_prepare_points<R, R>(Xd, N, d, p.Npad, p.dp, 1.0 / kern->lengthscale, p.Xp, st));
+            CIQ_TRY(tc_prepare(p, kern->type, st));
+            CIQ_TRY(form_stored(p, *kern, st));
+            launches += p.stored ? 1 : 0;
+        }
         KrylovState<R> s = krylov_state(p, op, o, tol);
         CIQ_TRY(launch_init_rhs(s, Bd, st));
         CIQ_TRY(launch_init_state(s, st));
@@ -1240,6 +1255,23 @@ ciq_status ciq_sqrt(const float* X, int64_t N, int d, const ciq_kernel* kern, co
                     ciq_stream_t stream) {
     return solve<float>(X, N, d, kern, B, T, Q, tol, opt, out, info, (cudaStream_t)stream,
                         kOpSqrtIdentity, false);
+}
+
+// An explicit matrix: the kernel here only carries the absent noise term.
+static const ciq_kernel kDenseKernel = {CIQ_RBF, 1.0, 1.0, 0.0};
+
+ciq_status ciq_sqrt_dense(const float* K, int64_t N, int64_t ldk, const float* B, int T, int Q, double tol,
+                          const ciq_options* opt, float* out, ciq_info* info, ciq_stream_t stream) {
+    if (!K) return CIQ_ERR_ARG;
+    return solve<float>(nullptr, N, 1, &kDenseKernel, B, T, Q, tol, opt, out, info, (cudaStream_t)stream,
+                        kOpSqrtIdentity, false, K, ldk);
+}
+
+ciq_status ciq_invsqrt_dense(const float* K, int64_t N, int64_t ldk, const float* B, int T, int Q, double tol,
+                             const ciq_options* opt, float* out, ciq_info* info, ciq_stream_t stream) {
+    if (!K) return CIQ_ERR_ARG;
+    return solve<float>(nullptr, N, 1, &kDenseKernel, B, T, Q, tol, opt, out, info, (cudaStream_t)stream,
+                        kOpInvSqrt, false, K, ldk);
 }
 
 ciq_status ciq_invsqrt(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, int T,

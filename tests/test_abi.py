@@ -123,3 +123,21 @@ def test_batched_validates_before_the_device():
         with pytest.raises(P.CiqError) as e:
             P.ciq_sqrt_batched(probs, 8, 1e-4, **kw)
         assert e.value.status == want, (kw, want)
+
+
+def test_dense_validates_before_the_device():
+    lib = P.lib()
+    o = _ciq.make_options()
+    K = np.eye(8, dtype=np.float32)
+    B = np.ones((1, 8), np.float32)
+    out = np.empty_like(B)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert lib.ciq_sqrt_dense(ptr(K), 8, 4, ptr(B), 1, 4, 1e-4, ctypes.byref(o), ptr(out), None, None) == \
+        _ciq.CIQ_ERR_ARG                                                            # ldk < N
+    assert lib.ciq_sqrt_dense(None, 8, 8, ptr(B), 1, 4, 1e-4, ctypes.byref(o), ptr(out), None, None) == \
+        _ciq.CIQ_ERR_ARG
+    o16 = _ciq.make_options(precision="fp16")
+    assert lib.ciq_invsqrt_dense(ptr(K), 8, 8, ptr(B), 1, 4, 1e-4, ctypes.byref(o16), ptr(out), None, None) == \
+        _ciq.CIQ_ERR_UNSUPPORTED
+    with pytest.raises(ValueError):
+        P.ciq_sqrt_dense(K[:, :4].copy(), B, 4, 1e-4)

@@ -413,3 +413,15 @@ def test_errbound_with_scalar_norm_bounds_true_error(op, form):
     # the bound also holds against the returned estimate's own norm
     if form == "identity":
         assert (info["errbound"] <= 1e-3 * np.linalg.norm(A, axis=1)).all()
+
+
+@pytest.mark.parametrize("kind", ci.SPECTRA)
+def test_spectrum_matrix_has_the_prescribed_eigenvalues(kind):
+    # Inputs of the Q-sweep study: U orthogonal, K = U diag(lam) U^T symmetric
+    # with lam_t = 1/sqrt(t) or 1/t^2.
+    K, lam, U = ci.spectrum_matrix(9, 257, kind)
+    assert np.abs(U.T @ U - np.eye(257)).max() < 1e-13
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(K))[::-1], lam, rtol=0, atol=1e-14)
+    assert lam[0] == 1.0 and (np.diff(lam) < 0).all()
+    expect = 1.0 / np.sqrt(257) if kind == "inv_sqrt" else 1.0 / 257 ** 2
+    assert lam[-1] == pytest.approx(expect, rel=1e-15)
