@@ -425,3 +425,66 @@ def test_spectrum_matrix_has_the_prescribed_eigenvalues(kind):
     assert lam[0] == 1.0 and (np.diff(lam) < 0).all()
     expect = 1.0 / np.sqrt(257) if kind == "inv_sqrt" else 1.0 / 257 ** 2
     assert lam[-1] == pytest.approx(expect, rel=1e-15)
+
+
+# ----------------------------------------------------------- backward pass --
+from oracle import vjp as VJP  # noqa: E402
+
+
+def _vjp_case(kind, op, Q=12, n=140, T=2, seed=31, ls=0.35, s=1.3, noise=0.05):
+    X = ci.points(seed, n, 2)
+    B = ci.rhs(seed, n, T)
+    G = ci.rhs(seed + 1, n, T)
+    K = kernels.dense_K(X, kind, ls, s, noise)
+    lam = np.linalg.eigvalsh(K)
+    w, t = quad_nodes(lam[0], lam[-1], Q)
+    return X, B, G, K, w, t
+
+
+@pytest.mark.parametrize("kind", ["rbf", "matern52"])
+@pytest.mark.parametrize("op", ["invsqrt", "sqrt"])
+def test_vjp_matches_finite_differences_of_the_quadrature(kind, op):
+    # Eq. ciq_deriv is the exact derivative of the quadrature approximant with
+    # the nodes fixed: central differences of L(theta) = sum g . CIQ(b; theta)
+    # (converged FP64 solves, same nodes) must agree.
+    ls, s, noise = 0.35, 1.3, 0.05
+    X, B, G, K, w, t = _vjp_case(kind, op, ls=ls, s=s, noise=noise)
+    dKs = VJP.dK_dtheta(X, kind, ls, s)
+    A, gB, gth = VJP.ciq_vjp(K, dKs, B, G, w, t, op, max_iter=400)
+
+    def loss(l_, s_, n_):
+        Kp = kernels.dense_K(X, kind, l_, s_, n_)
+        Ap, _, _ = VJP.ciq_vjp(Kp, [], B, G, w, t, op, max_iter=400)
+        return float(np.sum(G * Ap))
+    h = 1e-5
+    fd = [(loss(ls + h, s, noise) - loss(ls - h, s, noise)) / (2 * h),
+          (loss(ls, s + h, noise) - loss(ls, s - h, noise)) / (2 * h),
+          (loss(ls, s, noise + h) - loss(ls, s, noise - h)) / (2 * h)]
+    np.testing.assert_allclose(gth, fd, rtol=2e-6, atol=1e-9 * np.abs(fd).max())
+    # dL/db: L is linear in b, so the gradient is exact against a difference too
+    e = np.zeros_like(B); e[0, 7] = 1.0
+    Ap, _, _ = VJP.ciq_vjp(K, [], B + e, G, w, t, op, max_iter=400)
+    assert abs(np.sum(G * (Ap - A)) - gB[0, 7]) < 1e-10 * np.abs(gB).max()
+
+
+@pytest.mark.parametrize("op", ["invsqrt", "sqrt"])
+def test_vjp_approaches_the_exact_derivative_of_the_matrix_root(op):
+    # Daleckii-Krein: for K = V diag(lam) V^T and f = lam^{-1/2} (or lam^{1/2}),
+    # d f(K) = V (F o (V^T dK V)) V^T with F_ij = (f_i - f_j)/(lam_i - lam_j)
+    # (f'(lam_i) on ties).  The quadrature's derivative converges to it with Q.
+    X, B, G, K, w, t = _vjp_case("matern52", op, Q=24)
+    dKs = VJP.dK_dtheta(X, "matern52", 0.35, 1.3)
+    _, gB, gth = VJP.ciq_vjp(K, dKs, B, G, w, t, op, max_iter=400)
+    lam, V = np.linalg.eigh(K)
+    p = -0.5 if op == "invsqrt" else 0.5
+    f = lam ** p
+    dl = lam[:, None] - lam[None, :]
+    same = np.abs(dl) < 1e-12 * lam.max()
+    F = np.where(same, p * lam[:, None] ** (p - 1), (f[:, None] - f[None, :]) / np.where(same, 1.0, dl))
+    exact = []
+    for D in dKs:
+        dF = V @ (F * (V.T @ D @ V)) @ V.T
+        exact.append(float(np.sum(G.T * (dF @ B.T))))
+    np.testing.assert_allclose(gth, exact, rtol=1e-5)
+    ref_gB = (eig.invsqrt_apply if op == "invsqrt" else eig.sqrt_apply)(K, G.T).T
+    assert np.linalg.norm(gB - ref_gB) / np.linalg.norm(ref_gB) < 1e-5
