@@ -76,11 +76,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--workload", default="thompson50k",
-                    choices=["thompson50k", "batched512", "precision200k", "learned", "stored", "spectrum"],
+                    choices=["thompson50k", "batched512", "precision200k", "learned", "stored", "spectrum", "vjp"],
                     help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
                          "the 200,000-point Matern precision sweep; learned: train the bound predictor on "
                          "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones; "
-                         "spectrum: K^{1/2}b error against Q on matrices with prescribed spectra")
+                         "spectrum: K^{1/2}b error against Q on matrices with prescribed spectra; "
+                         "vjp: forward and backward pass of K^{-1/2}B on the 50,000-point problem")
     ap.add_argument("--n", type=int, default=0, metavar="N",
                     help="run the headline solve on the first N points only (for profiling captures)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
@@ -886,6 +887,65 @@ def run_spectrum(args):
     return 0
 
 
+def run_vjp(args):
+    """Backward pass (Sec. 3.4, Eq. ciq_deriv) on the 50,000-point RBF problem
+    with T = 8 right-hand sides (a whitening / SVGP-sized block), Q = 12,
+    error bound 1e-3, FP16 split tiles: the forward solve alone against the
+    forward-and-backward call (one solve over [B | G], then the gradient
+    contractions), and the contractions alone (the VJP call minus a forward
+    solve over the same 2T columns).  The contraction pass is CUDA-core FP32:
+    algorithmic work N^2 (2 Q T + 30) flops against the derived FP32 rate."""
+    import torch
+
+    import paper_2006_11267_b300 as P
+
+    torch.cuda.set_device(0)
+    W = WORKLOAD
+    T = 8
+    X = torch.from_numpy(ci.points(W.seed, W.n, W.d).astype(np.float32)).cuda()
+    B = torch.from_numpy(ci.rhs(W.seed, W.n, T).astype(np.float32)).cuda()
+    G = torch.from_numpy(ci.rhs(W.seed + 7, W.n, T).astype(np.float32)).cuda()
+    BG = torch.cat([B, G], 0).contiguous()
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    opts = dict(stop_rule="errbound", max_iter=MAX_ITER, lanczos_iters=LANCZOS_ITERS, precision=args.precision)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    reps = max(1, args.steps)
+    t_fwd, (_, i_fwd) = timed(lambda: P.ciq_invsqrt(X, k, B, W.q, TOL, **opts), reps)
+    t_fwd2, (_, i_fwd2) = timed(lambda: P.ciq_invsqrt(X, k, BG, W.q, TOL, **opts), reps)
+    t_vjp, (_, _, gth, i_vjp) = timed(lambda: P.ciq_invsqrt_vjp(X, k, B, G, W.q, TOL, **opts), reps)
+    t_con = max(t_vjp - t_fwd2, 1e-6)
+    flops = float(W.n) ** 2 * (2 * W.q * T + 30)
+    pk, _ = peaks()
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    achieved = flops / (t_con * 1e-3) / 1e12
+    line = {"metric": "K^{-1/2}B forward + backward (VJP) time", "value": t_vjp, "unit": "ms per call",
+            "n_gpus": 1, "steps": reps, "warmup": 1, "higher_is_better": False,
+            "dtype": f"{args.precision}x2-split tiles, f32 vectors, f64 scalars; f32 contractions", "data": "synthetic",
+            "config": {"workload": "vjp_rbf_n50000_d6_t8_q12", "N": W.n, "d": W.d, "T": T, "Q": W.q, "tol": TOL,
+                       "stop_rule": "errbound", "op": "invsqrt", "krylov": i_vjp.get("krylov")},
+            "forward_ms": t_fwd, "forward_2T_ms": t_fwd2, "backward_over_forward": t_vjp / t_fwd,
+            "iterations": {"forward": i_fwd["iters"], "forward_2T": i_fwd2["iters"], "vjp": i_vjp["iters"]},
+            "contractions_ms": t_con, "grad_theta": [float(g) for g in gth],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None,
+                         "kernel": "vjp_bilinear_kernel (32 x 32 tiles of K, rank-QT form, kernel and dk/dl values)",
+                         "peak_note": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived, not measured)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -900,6 +960,8 @@ def main():
         return run_learned(args)
     if args.workload == "spectrum":
         return run_spectrum(args)
+    if args.workload == "vjp":
+        return run_vjp(args)
     return run_ours(args)
 
 

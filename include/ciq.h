@@ -270,6 +270,26 @@ ciq_status ciq_sqrt_dense(const float* K, int64_t N, int64_t ldk, const float* B
 ciq_status ciq_invsqrt_dense(const float* K, int64_t N, int64_t ldk, const float* B, int T, int Q, double tol,
                              const ciq_options* opt, float* out, ciq_info* info, ciq_stream_t stream);
 
+/* Backward pass (Sec. 3.4, Eq. ciq_deriv): the forward result out = K^{-1/2}B
+ * (ciq_invsqrt_vjp) or K^{1/2}B (ciq_sqrt_vjp, identity form), and for the loss
+ * L = sum_c G_c . out_c its gradients grad_B = dL/dB (T x N like B) and
+ * grad_theta[0..2] = dL/d lengthscale, dL/d outputscale, dL/d noise (host, summed
+ * over the T columns).  The quadrature is differentiated term by term with its
+ * nodes held fixed: dL/dtheta = sum_q c_q y_q^T (dK/dtheta) x_q with x_q, y_q the
+ * shifted solves of b and g (c_q = -w_q, or w_q t_q for the square root), and
+ * dL/dB is the same root applied to G.  One solve runs over the 2T columns
+ * [B | G] in the stored-basis form (opt->krylov RECURRENCE or opt->sqrt_form
+ * CIQ_SQRT_MVM: CIQ_ERR_UNSUPPORTED); the contractions then run on CUDA cores
+ * over all N^2 kernel entries (O(N^2 Q T) work).  X, B, G, out, grad_B: host or
+ * device; precision, stop rule and bounds as in ciq_sqrt, applied to all 2T
+ * columns.  Returns after the stream work. */
+ciq_status ciq_invsqrt_vjp(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, const float* G,
+                           int T, int Q, double tol, const ciq_options* opt, float* out, float* grad_B,
+                           double* grad_theta, ciq_info* info, ciq_stream_t stream);
+ciq_status ciq_sqrt_vjp(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, const float* G,
+                        int T, int Q, double tol, const ciq_options* opt, float* out, float* grad_B,
+                        double* grad_theta, ciq_info* info, ciq_stream_t stream);
+
 /* One problem of a batch: X (device, N x d), B and out (device, T columns of
  * N floats).  lmin, lmax > 0 give this problem's spectral bounds and skip its
  * Lanczos pre-pass (e.g. bounds predicted by a learned model); otherwise the

@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         "ciq_kernel_matrix": (I, [P, I64, I, KP, P, I64, P]),
         "ciq_stored_mvm": (I, [P, I64, I64, P, I, P, P]),
         "ciq_sqrt_dense": (I, [P, I64, I64, P, I, I, D, OP, P, IP, P]),
+        "ciq_invsqrt_vjp": (I, [P, I64, I, KP, P, P, I, I, D, OP, P, P, DP, IP, P]),
+        "ciq_sqrt_vjp": (I, [P, I64, I, KP, P, P, I, I, D, OP, P, P, DP, IP, P]),
         "ciq_invsqrt_dense": (I, [P, I64, I64, P, I, I, D, OP, P, IP, P]),
         "ciq_workspace_bytes": (S, [I64, I, I, I, OP]),
         "ciq_kernel_mvm_noalloc": (I, [P, I64, I, KP, P, I, P, P]),
@@ -354,6 +356,36 @@ def ciq_sqrt_dense(K, B, Q, tol=0.0, out=None, **opts):
 def ciq_invsqrt_dense(K, B, Q, tol=0.0, out=None, **opts):
     """K^{-1/2} B for an explicit SPD matrix K (N x N, FP32, row-major). Returns (out, info)."""
     return _solve_dense("ciq_invsqrt_dense", K, B, Q, tol, out, **opts)
+
+
+def _vjp(name, X, kernel, B, G, Q, tol, **opts):
+    N, d = X.shape
+    T = B.shape[0]
+    if B.shape != (T, N) or G.shape != (T, N):
+        raise ValueError("B and G must have shape (T, N)")
+    out = _empty_like_rhs(B, np.float32)
+    grad_B = _empty_like_rhs(B, np.float32)
+    grad = (ctypes.c_double * 3)()
+    o = make_options(**opts)
+    info = _Info()
+    k = kernel.c()
+    st = getattr(lib(), name)(_ptr(X), N, d, ctypes.byref(k), _ptr(B), _ptr(G), T, int(Q), float(tol),
+                              ctypes.byref(o), _ptr(out), _ptr(grad_B), grad, ctypes.byref(info),
+                              _stream(X, B, G))
+    _check(st, name)
+    return out, grad_B, np.array(grad[:]), _info_dict(info, st)
+
+
+def ciq_invsqrt_vjp(X, kernel, B, G, Q, tol=0.0, **opts):
+    """K^{-1/2} B and the gradients of sum(G * K^{-1/2} B) w.r.t. B and
+    (lengthscale, outputscale, noise).  Returns (out, grad_B, grad_theta, info)."""
+    return _vjp("ciq_invsqrt_vjp", X, kernel, B, G, Q, tol, **opts)
+
+
+def ciq_sqrt_vjp(X, kernel, B, G, Q, tol=0.0, **opts):
+    """K^{1/2} B and the gradients of sum(G * K^{1/2} B) w.r.t. B and
+    (lengthscale, outputscale, noise).  Returns (out, grad_B, grad_theta, info)."""
+    return _vjp("ciq_sqrt_vjp", X, kernel, B, G, Q, tol, **opts)
 
 
 def ciq_workspace_bytes(N, d, T, Q, **opts):

@@ -144,9 +144,11 @@ struct Plan {
     int tc_max_split = 8;         // CTAs per row tile of the tensor-core MVM (batches: 1)
     int fault_inject = 0;         // ciq_options.fault_inject (testing the bounded-wait path)
     bool basis = false;           // stored-basis form (CIQ_KRYLOV_BASIS)
+    bool vjp = false;             // backward pass: T = 2 T_B columns [B | G], basis form
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB, *V, *sco;
-    double *rcoef, *gauss, *bco;
+    double *rcoef, *gauss, *bco, *ycoef, *vpart, *vgrad;
+    float* Xq;
     R *sx, *sb, *sout, *sstart;
     float* Kst;
     double *partials, *ynp, *beta, *beta1, *giv, *phifinal, *nodes, *summary, *tri;
@@ -177,6 +179,10 @@ struct Plan {
         gauss = basis ? a.take<double>((size_t)2 * T * 4) : nullptr;
         bco = basis ? a.take<double>(((size_t)jmax + 1) * T) : nullptr;
         sco = a.take<R>((size_t)T * kScoStride);
+        ycoef = vjp ? a.take<double>(((size_t)jmax + 1) * Q * T) : nullptr;
+        Xq = vjp ? a.take<float>((size_t)Q * T * Npad) : nullptr;
+        vpart = vjp ? a.take<double>((size_t)vjp_partials(Npad, T / 2, Q)) : nullptr;
+        vgrad = vjp ? a.take<double>(3) : nullptr;
         partials = a.take<double>((size_t)nparts * T * 3);
         ynp = a.take<double>((size_t)2 * nchunks * T);
         beta = a.take<double>((size_t)2 * T);
@@ -276,7 +282,7 @@ KrylovState<R> krylov_state(const Plan<R>& p, int op, const ciq_options& o, doub
     s.giv = p.giv; s.phifinal = p.phifinal; s.status = p.status; s.iters = p.iters;
     s.brk = p.brk; s.cnt = p.cnt; s.all_done = p.all_done; s.nodes = p.nodes;
     s.summary = p.summary; s.tri = p.tri; s.jmax = p.jmax; s.op = op; s.stop_rule = o.stop_rule; s.tol = tol;
-    s.basis = p.V; s.rcoef = p.rcoef; s.gauss = p.gauss; s.bco = p.bco; s.sco = p.sco;
+    s.basis = p.V; s.rcoef = p.rcoef; s.gauss = p.gauss; s.bco = p.bco; s.sco = p.sco; s.ycoef = p.ycoef;
     s.breakdown_rtol = sizeof(R) == 4 ? 1e-6 : 1e-13;
     return s;
 }
@@ -383,8 +389,9 @@ struct Profile {
 template <typename R>
 ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* B, int T, int Q,
                  double tol, const ciq_options* opt, R* out, ciq_info* info, cudaStream_t st,
-                 int op, bool fp64, const float* Kd = nullptr, int64_t ldk = 0) {
+                 int op, bool fp64, const float* Kd = nullptr, int64_t ldk = 0, double* vjp_grad = nullptr) {
     const bool dense = Kd != nullptr;
+    const bool vjp = vjp_grad != nullptr;
     if ((!dense && !X) || !B || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q ||
         !(tol >= 0.0) || !valid_kernel(kern) || (dense && (ldk < N || fp64)))
         return CIQ_ERR_ARG;
@@ -395,6 +402,13 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     if (dense) {
         if (o.precision != CIQ_PREC_FP32) return CIQ_ERR_UNSUPPORTED;
         o.mvm = CIQ_MVM_STORED;
+    }
+    if (vjp) {
+        // The backward pass needs every shift's solution: the stored-basis form.
+        if (fp64 || dense || T % 2 != 0 || o.krylov == CIQ_KRYLOV_RECURRENCE ||
+            (op == kOpSqrtIdentity && o.sqrt_form == CIQ_SQRT_MVM))
+            return CIQ_ERR_UNSUPPORTED;
+        o.krylov = CIQ_KRYLOV_BASIS;
     }
     if ((o.quad_w == nullptr) != (o.quad_t == nullptr)) return CIQ_ERR_ARG;
     if (o.mvm == CIQ_MVM_STORED && !fp64 && o.precision != CIQ_PREC_FP32) return CIQ_ERR_UNSUPPORTED;
@@ -419,6 +433,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     keep_pool_warm();
 
     Plan<R> p = make_plan<R>(N, d, T, Q, o, prepass, tc, true);
+    p.vjp = vjp;
     p.stage_x = !dense && !device_accessible(X);
     p.stage_b = !device_accessible(B);
     p.stage_out = !device_accessible(out);
@@ -595,6 +610,13 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             CIQ_TRY(launch_basis_combine(s, outd, last_j, st));   // kOpSqrtMvm: the sum goes to Y
             launches += 2;
         }
+        if constexpr (sizeof(R) == 4) {
+            if (vjp) {
+                CIQ_TRY(launch_vjp(s, p.Xp, p.dp, kern->type, kern->lengthscale, kern->outputscale, p.Xq, p.vpart,
+                                   p.vgrad, st));
+                launches += 3 + (Q + 3) / 4;
+            }
+        }
         if (op == kOpSqrtMvm) {
             if (!p.basis) CIQ_TRY(launch_combine(s, outd, st));      // folds the trailing part into Y
             MvmArgs<R> m = mvm_args(p, *kern);
@@ -617,6 +639,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         CIQ_TRY(cudaMemcpyAsync(summary, p.summary, sizeof(summary), cudaMemcpyDeviceToHost, st));
         CIQ_TRY(cudaMemcpyAsync(nodes, p.nodes, sizeof(nodes), cudaMemcpyDeviceToHost, st));
         if (p.tc) CIQ_TRY(cudaMemcpyAsync(&tc_timeout, p.tcp.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (vjp) CIQ_TRY(cudaMemcpyAsync(vjp_grad, p.vgrad, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CIQ_TRY(cudaStreamSynchronize(st));
     }
 done:
@@ -1257,6 +1280,39 @@ ciq_status ciq_sqrt(const float* X, int64_t N, int d, const ciq_kernel* kern, co
                         kOpSqrtIdentity, false);
 }
 
+// Backward pass: one solve over [B | G] (2T columns), then the contractions.
+static ciq_status solve_vjp(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, const float* G,
+                     int T, int Q, double tol, const ciq_options* opt, float* out, float* grad_B, double* grad_theta,
+                     ciq_info* info, cudaStream_t st, int op) {
+    if (!X || !B || !G || !out || !grad_B || !grad_theta || N < 1 || T < 1 || T > (1 << 20)) return CIQ_ERR_ARG;
+    ciq_options o;
+    ciq_default_options(&o);
+    if (opt) o = *opt;
+    if (!valid_options(o)) return CIQ_ERR_ARG;
+    if (o.krylov == CIQ_KRYLOV_RECURRENCE || o.sqrt_form == CIQ_SQRT_MVM) return CIQ_ERR_UNSUPPORTED;
+    keep_pool_warm();
+    const size_t cols = sizeof(float) * (size_t)N * T;
+    float *BG = nullptr, *OG = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&BG), 2 * cols, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&OG), 2 * cols, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(BG, B, cols, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(BG + (size_t)N * T, G, cols, cudaMemcpyDefault, st);
+    ciq_status rc = from_cuda(e);
+    if (rc == CIQ_OK) {
+        rc = solve<float>(X, N, d, kern, BG, 2 * T, Q, tol, &o, OG, info, st, op, false, nullptr, 0, grad_theta);
+        if (rc == CIQ_OK || rc == CIQ_NOT_CONVERGED) {
+            e = cudaMemcpyAsync(out, OG, cols, cudaMemcpyDefault, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(grad_B, OG + (size_t)N * T, cols, cudaMemcpyDefault, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = from_cuda(e);
+        }
+    }
+    if (BG) cudaFreeAsync(BG, st);
+    if (OG) cudaFreeAsync(OG, st);
+    if (rc != CIQ_OK && rc != CIQ_NOT_CONVERGED) cudaGetLastError();
+    return rc;
+}
+
 // An explicit matrix: the kernel here only carries the absent noise term.
 static const ciq_kernel kDenseKernel = {CIQ_RBF, 1.0, 1.0, 0.0};
 
@@ -1550,6 +1606,20 @@ ciq_status ciq_mlp_predict(const float* theta, const float* F, int n, float* out
     if (!theta || !F || !out || n < 1 || !device_accessible(theta) || !device_accessible(F) || !device_accessible(out))
         return CIQ_ERR_ARG;
     return from_cuda(launch_mlp_predict(theta, F, n, out, bf16 ? 1 : 0, (cudaStream_t)stream));
+}
+
+ciq_status ciq_invsqrt_vjp(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, const float* G,
+                           int T, int Q, double tol, const ciq_options* opt, float* out, float* grad_B,
+                           double* grad_theta, ciq_info* info, ciq_stream_t stream) {
+    return solve_vjp(X, N, d, kern, B, G, T, Q, tol, opt, out, grad_B, grad_theta, info, (cudaStream_t)stream,
+                     kOpInvSqrt);
+}
+
+ciq_status ciq_sqrt_vjp(const float* X, int64_t N, int d, const ciq_kernel* kern, const float* B, const float* G,
+                        int T, int Q, double tol, const ciq_options* opt, float* out, float* grad_B,
+                        double* grad_theta, ciq_info* info, ciq_stream_t stream) {
+    return solve_vjp(X, N, d, kern, B, G, T, Q, tol, opt, out, grad_B, grad_theta, info, (cudaStream_t)stream,
+                     kOpSqrtIdentity);
 }
 
 }  // extern "C"

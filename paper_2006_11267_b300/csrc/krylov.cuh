@@ -73,6 +73,7 @@ struct KrylovState {
     double* gauss;              // [2][T][4]: LDL^T pivot d_j, u_j^2, sum_k u_k^2/d_k, alpha_1 (parity of j)
     double* bco;                // [jmax + 1][T]: sum_q c_q y_q(j), the coefficient of q_j
     R* sco;                     // [T][kScoStride]: scalars of the split step (single solves)
+    double* ycoef;              // optional [jmax + 1][Q][T]: y_q(j) of every shift (backward pass)
     int jmax;
     int op;                     // CombineOp
     int stop_rule;              // ciq_stop_rule
@@ -117,6 +118,17 @@ cudaError_t launch_summary(const KrylovState<R>& s, int final_j, cudaStream_t st
 // the summary in the parity slot of final_j).  kOpSqrtMvm leaves the sum in Y.
 template <typename R>
 cudaError_t launch_basis_combine(const KrylovState<R>& s, R* out, int final_j, cudaStream_t st);
+
+// Backward pass (Eq. ciq_deriv), stored-basis form, FP32 solves over 2T
+// columns [B | G] (s.T = 2T; s.ycoef filled by launch_basis_combine).
+// Per-shift solutions Xq[q][c][Npad] = V_c y_q for every column, then
+// grad[0] = sum_c sum_q c_q y_qc^T (dK/dl) x_qc, grad[1] the same with
+// dK/ds = K_XX / s, grad[2] with dK/dsigma^2 = I (device doubles), c_q = -w_q
+// (op kOpInvSqrt) or w_q t_q (kOpSqrtIdentity); x_qc from column c, y_qc
+// from column T + c.  part: >= vjp_partials(Npad, T, Q) doubles of scratch.
+int64_t vjp_partials(int64_t Npad, int T, int Q);
+cudaError_t launch_vjp(const KrylovState<float>& s, const float* Xp, int dp, int kt, double lengthscale,
+                       double outputscale, float* Xq, double* part, double* grad, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_lanczos_init(const LanczosState<R>& s, const R* start, uint64_t seed,

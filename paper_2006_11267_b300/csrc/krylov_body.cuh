@@ -565,6 +565,7 @@ __device__ __forceinline__ void basis_backsub_body(KrylovState<R> s, int c) {
                 const double y = fma(-dl1, y1, fma(-ep2, y2, tau)) * invg;
                 ep2 = ep1; ep1 = ep; dl1 = de; y2 = y1; y1 = y;
                 cy[u][lane] = cq * y;
+                if (s.ycoef) s.ycoef[((int64_t)(jt - u) * Q + lane) * T + c] = y;
             }
         }
         __syncwarp();

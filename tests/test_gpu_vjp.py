@@ -1,0 +1,66 @@
+"""Backward pass (Eq. ciq_deriv) through the C ABI against the FP64 oracle
+(oracle/vjp.py, pinned by finite differences) at equal nodes and J."""
+import numpy as np
+import pytest
+import torch
+
+import ciq_inputs as ci
+import paper_2006_11267_b300 as P
+from oracle import ciq as O
+from oracle import kernels
+from oracle import vjp as VJP
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("kind", ["rbf", "matern52"])
+@pytest.mark.parametrize("op", ["invsqrt", "sqrt"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_vjp_matches_oracle_at_equal_nodes_and_J(kind, op, precision):
+    n, d, T, Q, J = 1100, 3, 3, 10, 250
+    ls, s, noise = 0.3, 1.2, 2e-2
+    X = ci.points(41, n, d).astype(np.float32)
+    B = ci.rhs(42, n, T).astype(np.float32)
+    G = ci.rhs(43, n, T).astype(np.float32)
+    X64 = X.astype(np.float64)
+    K = kernels.dense_K(X64, kind, ls, s, noise)
+    lam = np.linalg.eigvalsh(K)
+    w, t = O.quad_nodes(noise, 1.05 * lam[-1], Q)
+    A_o, gB_o, gth_o = VJP.ciq_vjp(K, VJP.dK_dtheta(X64, kind, ls, s), B, G, w, t, op, max_iter=J)
+    fn = P.ciq_invsqrt_vjp if op == "invsqrt" else P.ciq_sqrt_vjp
+    k = P.Kernel(kind, ls, s, noise)
+    out, gB, gth, info = fn(torch.from_numpy(X).cuda(), k, torch.from_numpy(B).cuda(), torch.from_numpy(G).cuda(),
+                            Q, 0.0, max_iter=J, nodes=(w, t), lmin=noise, precision=precision)
+    assert info["iters"] == J and info["krylov"] == "basis"
+    # FP32 Lanczos vectors: K^{-1/2} b is attainable to about 20 u sqrt(kappa)
+    # (the convention of the forward parity tests); FP16-split tiles add 1e-4.
+    u = 2.0 ** -24
+    tol = 2e-5 if op == "sqrt" else max(2e-5, 20 * u * np.sqrt(lam[-1] / lam[0]))
+    if precision == "fp16":
+        tol = max(tol, 1e-4)
+    assert rel(out.cpu().numpy(), A_o) < tol
+    assert rel(gB.cpu().numpy(), gB_o) < tol
+    np.testing.assert_allclose(gth, gth_o, rtol=10 * tol, atol=10 * tol * np.abs(gth_o).max())
+
+
+def test_vjp_host_arrays_and_unsupported_forms():
+    n, T = 300, 2
+    X = ci.points(5, n, 2).astype(np.float32)
+    B = ci.rhs(6, n, T).astype(np.float32)
+    G = ci.rhs(7, n, T).astype(np.float32)
+    k = P.Kernel("rbf", 0.4, 1.0, 1e-2)
+    out, gB, gth, info = P.ciq_invsqrt_vjp(X, k, B, G, 8, 1e-6, max_iter=400)          # host arrays
+    ref, _ = P.ciq_invsqrt(X, k, B, 8, 1e-6, max_iter=400)
+    assert rel(out, ref) < 1e-5 and np.isfinite(gth).all()
+    gref, _ = P.ciq_invsqrt(X, k, G, 8, 1e-6, max_iter=400)                              # dL/dB = K^{-1/2} G
+    assert rel(gB, gref) < 1e-5
+    for bad in (dict(krylov="recurrence"), dict(sqrt_form="mvm")):
+        with pytest.raises(P.CiqError) as e:
+            (P.ciq_sqrt_vjp if "sqrt_form" in bad else P.ciq_invsqrt_vjp)(X, k, B, G, 8, 1e-6, **bad)
+        assert e.value.status == 6
