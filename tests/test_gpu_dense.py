@@ -83,3 +83,16 @@ def test_dense_identity_and_scaled_identity():
     out, _ = P.ciq_invsqrt_dense(torch.from_numpy(K).cuda(), torch.from_numpy(B).cuda(), 8, 1e-6,
                                  lmin=4.0, lmax=4.0)
     assert rel(out.cpu().numpy(), 0.5 * B) < 1e-6
+
+
+def test_dense_wide_block_and_tiny_matrix():
+    # T = 70 (two column groups) and N = 1
+    K32 = matrix("inv_sqrt", 600, 5).astype(np.float32)
+    B = ci.rhs(6, 600, 70).astype(np.float32)
+    exact = eig.invsqrt_apply(K32.astype(np.float64), B.T.astype(np.float64)).T
+    out, info = P.ciq_invsqrt_dense(torch.from_numpy(K32).cuda(), torch.from_numpy(B).cuda(), 10, 1e-7,
+                                    max_iter=300)
+    assert rel(out.cpu().numpy(), exact) < 1e-4
+    one = np.array([[2.25]], np.float32)
+    out, _ = P.ciq_sqrt_dense(one, np.array([[3.0]], np.float32), 6, 1e-8, lmin=2.25, lmax=2.25)
+    assert abs(out[0, 0] - 4.5) < 1e-5

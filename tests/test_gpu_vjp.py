@@ -64,3 +64,24 @@ def test_vjp_host_arrays_and_unsupported_forms():
         with pytest.raises(P.CiqError) as e:
             (P.ciq_sqrt_vjp if "sqrt_form" in bad else P.ciq_invsqrt_vjp)(X, k, B, G, 8, 1e-6, **bad)
         assert e.value.status == 6
+
+
+@pytest.mark.parametrize("T,Q", [(1, 1), (40, 6)])
+def test_vjp_edge_shapes(T, Q):
+    # one column and one shift; and 2T = 80 columns (two tensor-core groups)
+    n = 500
+    X = ci.points(8, n, 4).astype(np.float32)
+    B = ci.rhs(9, n, T).astype(np.float32)
+    G = ci.rhs(10, n, T).astype(np.float32)
+    ls, s, noise = 0.5, 0.9, 5e-2
+    K = kernels.dense_K(X.astype(np.float64), "matern52", ls, s, noise)
+    lam = np.linalg.eigvalsh(K)
+    w, t = O.quad_nodes(noise, 1.05 * lam[-1], Q)
+    J = 150
+    A_o, gB_o, gth_o = VJP.ciq_vjp(K, VJP.dK_dtheta(X.astype(np.float64), "matern52", ls, s), B, G, w, t, "sqrt",
+                                   max_iter=J)
+    out, gB, gth, info = P.ciq_sqrt_vjp(torch.from_numpy(X).cuda(), P.Kernel("matern52", ls, s, noise),
+                                        torch.from_numpy(B).cuda(), torch.from_numpy(G).cuda(), Q, 0.0,
+                                        max_iter=J, nodes=(w, t), lmin=noise, precision="fp16")
+    assert rel(out.cpu().numpy(), A_o) < 1e-4 and rel(gB.cpu().numpy(), gB_o) < 1e-4
+    np.testing.assert_allclose(gth, gth_o, rtol=1e-3, atol=1e-3 * np.abs(gth_o).max())
