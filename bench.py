@@ -940,7 +940,8 @@ def run_vjp(args):
             "contractions_ms": t_con, "grad_theta": [float(g) for g in gth],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None,
-                         "kernel": "vjp_bilinear_kernel (32 x 32 tiles of K, rank-QT form, kernel and dk/dl values)",
+                         "kernel": "the contraction launches together (basis_solutions, vjp_bilinear on 64 x 64 tiles "
+                                   "of K with 4 x 4 register blocks, vjp_dots); work counted is the bilinear pass's",
                          "peak_note": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived, not measured)"}}
     print(json.dumps(line), flush=True)
     return 0

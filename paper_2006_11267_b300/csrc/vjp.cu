@@ -9,7 +9,7 @@
 // records; this file forms them and the three contractions:
 //   * basis_solutions: Xq[q][c] = sum_j y_q(j) q_j of column c, four shifts
 //     per pass over the basis;
-//   * vjp_bilinear: sum over 32 x 32 tiles (i, j) of K of
+//   * vjp_bilinear: sum over 64 x 64 tiles (i, j) of K of
 //     A_ij = sum_{c<T,q} c_q y_qc[i] x_qc[j] times dk/dl (scaled by s) and
 //     times k/s, with kernel values from coordinate differences of the
 //     scaled points (RBF dk/dl = k r~^2 / l, Matern-5/2 dk/dl = s (z^2 / 3l)
@@ -23,7 +23,7 @@
 namespace ciq {
 namespace {
 
-constexpr int kVT = 32;          // tile edge of the bilinear pass
+constexpr int kVT = 64;          // tile edge of the bilinear pass
 constexpr int kQG = 4;           // shifts per pass of basis_solutions
 
 __device__ __forceinline__ double vjp_coef(const KrylovState<float>& s, int q) {
@@ -67,18 +67,20 @@ __global__ void __launch_bounds__(256) basis_solutions_kernel(KrylovState<float>
     }
 }
 
-// One block per 32 x 32 tile of K; 256 threads, four entries each.
+// One block per 64 x 64 tile of K; 256 threads, a 4 x 4 block of entries
+// each (register-tiled rank-R update, two 16-byte shared loads per 16 FMAs).
 __global__ void __launch_bounds__(256) vjp_bilinear_kernel(KrylovState<float> s, const float* Xp, int dp, int kt,
                                                            float inv_l, float sc, const float* Xq, int Tb,
                                                            double* part) {
-    __shared__ float Ys[kVT][kVT + 1];
-    __shared__ float Xs[kVT][kVT + 1];
+    constexpr int RC = 16;                                // (shift, column) pairs per shared-memory panel
+    __shared__ __align__(16) float Ys[RC][kVT];
+    __shared__ __align__(16) float Xs[RC][kVT];
     __shared__ float Pi[kVT][17], Pj[kVT][17];
     __shared__ double red[8][2];
     __shared__ float cqs[CIQ_MAX_Q];
     const int nt = (int)(s.Npad / kVT);
     const int bi = blockIdx.x % nt, bj = blockIdx.x / nt;
-    const int tid = threadIdx.x, ti = tid >> 3, tj0 = (tid & 7) * 4;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int64_t i0 = (int64_t)bi * kVT, j0 = (int64_t)bj * kVT;
     const int Q = s.Q, T2 = s.T;
     for (int e = tid; e < kVT * dp; e += 256) {
@@ -87,11 +89,15 @@ __global__ void __launch_bounds__(256) vjp_bilinear_kernel(KrylovState<float> s,
         Pj[r][k] = Xp[(j0 + r) * dp + k];
     }
     if (tid < Q) cqs[tid] = (float)vjp_coef(s, tid);
-    float A[4] = {0.f, 0.f, 0.f, 0.f};
+    float A[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) A[a][b] = 0.f;
     const int R = Q * Tb;                                 // (shift, column) pairs
-    for (int r0 = 0; r0 < R; r0 += kVT) {
+    for (int r0 = 0; r0 < R; r0 += RC) {
         __syncthreads();
-        for (int e = tid; e < kVT * kVT; e += 256) {
+        for (int e = tid; e < RC * kVT; e += 256) {
             const int rr = e / kVT, row = e % kVT, r = r0 + rr;     // consecutive threads: consecutive rows
             float yv = 0.f, xv = 0.f;
             if (r < R) {
@@ -99,42 +105,48 @@ __global__ void __launch_bounds__(256) vjp_bilinear_kernel(KrylovState<float> s,
                 yv = cqs[q] * Xq[((int64_t)q * T2 + Tb + c) * s.Npad + i0 + row];
                 xv = Xq[((int64_t)q * T2 + c) * s.Npad + j0 + row];
             }
-            Ys[row][rr] = yv;
-            Xs[row][rr] = xv;
+            Ys[rr][row] = yv;
+            Xs[rr][row] = xv;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int rr = 0; rr < kVT; ++rr) {
-            const float y = Ys[ti][rr];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) A[e] = fmaf(y, Xs[tj0 + e][rr], A[e]);
+        for (int rr = 0; rr < RC; ++rr) {
+            const float4 y = *reinterpret_cast<const float4*>(&Ys[rr][4 * ty]);
+            const float4 x = *reinterpret_cast<const float4*>(&Xs[rr][4 * tx]);
+            const float ya[4] = {y.x, y.y, y.z, y.w}, xa[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) A[a][b] = fmaf(ya[a], xa[b], A[a][b]);
         }
     }
-    // Kernel values of this thread's four entries, from coordinate differences.
-    double gl = 0.0, gs = 0.0;
+    // Kernel values of this thread's 16 entries, from coordinate differences.
+    float gl = 0.f, gs = 0.f;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        float r2 = 0.f;
-        for (int k = 0; k < dp; ++k) {
-            const float df = Pi[ti][k] - Pj[tj0 + e][k];
-            r2 = fmaf(df, df, r2);
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float r2 = 0.f;
+            for (int k = 0; k < dp; ++k) {
+                const float df = Pi[4 * ty + a][k] - Pj[4 * tx + b][k];
+                r2 = fmaf(df, df, r2);
+            }
+            float kv, dl;
+            if (kt == CIQ_RBF) {
+                kv = expf(-0.5f * r2);
+                dl = sc * kv * r2 * inv_l;
+            } else {
+                const float z = sqrtf(5.f * r2);
+                const float ez = expf(-z);
+                kv = (1.f + z + z * z * (1.f / 3.f)) * ez;
+                dl = sc * (z * z * (1.f / 3.f) * inv_l) * (1.f + z) * ez;
+            }
+            gl = fmaf(dl, A[a][b], gl);
+            gs = fmaf(kv, A[a][b], gs);
         }
-        float kv, dl;
-        if (kt == CIQ_RBF) {
-            kv = expf(-0.5f * r2);
-            dl = sc * kv * r2 * inv_l;
-        } else {
-            const float z = sqrtf(5.f * r2);
-            const float ez = expf(-z);
-            kv = (1.f + z + z * z * (1.f / 3.f)) * ez;
-            dl = sc * (z * z * (1.f / 3.f) * inv_l) * (1.f + z) * ez;
-        }
-        gl += (double)(dl * A[e]);
-        gs += (double)(kv * A[e]);
     }
-    gl = warp_sum(gl);
-    gs = warp_sum(gs);
-    if ((tid & 31) == 0) { red[tid >> 5][0] = gl; red[tid >> 5][1] = gs; }
+    double dgl = warp_sum((double)gl), dgs = warp_sum((double)gs);
+    if ((tid & 31) == 0) { red[tid >> 5][0] = dgl; red[tid >> 5][1] = dgs; }
     __syncthreads();
     if (tid == 0) {
         double a = 0.0, b = 0.0;
