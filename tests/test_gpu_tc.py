@@ -157,3 +157,22 @@ def test_nan_in_the_points_is_reported(prec):
     with pytest.raises(P.CiqError) as e:
         P.ciq_sqrt(Xd, k, B, 8, 1e-4, max_iter=100, precision=prec, lmin=1e-2, lmax=400.0)
     assert e.value.status == P._ciq.CIQ_ERR_NAN
+
+
+def test_basis_and_recurrence_forms_agree_at_full_size():
+    # The 50,000-point workload in the bench's configuration: the stored-basis
+    # form and the direction recurrence stop within a few steps of each other
+    # (their error-bound denominators differ, R15) and agree to the 1e-3 target.
+    W = ci.THOMPSON_50K
+    X = torch.from_numpy(f32(ci.points(W.seed, W.n, W.d))).cuda()
+    B = torch.from_numpy(f32(ci.rhs(W.seed, W.n, 16))).cuda()
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    outs, infos = {}, {}
+    for form in ("basis", "recurrence"):
+        outs[form], infos[form] = P.ciq_sqrt(X, k, B, W.q, 1e-3, stop_rule="errbound", max_iter=4000,
+                                             precision="fp16", krylov=form)
+        assert infos[form]["status"] == 0 and infos[form]["krylov"] == form
+        assert infos[form]["errbound_max"] <= 1e-3
+    assert abs(infos["basis"]["iters"] - infos["recurrence"]["iters"]) <= 0.02 * infos["recurrence"]["iters"]
+    d = torch.linalg.norm(outs["basis"] - outs["recurrence"], dim=1) / torch.linalg.norm(outs["recurrence"], dim=1)
+    assert d.max().item() < 2e-3
