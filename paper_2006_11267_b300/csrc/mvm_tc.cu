@@ -286,8 +286,11 @@ constexpr int kRing = 8;                         // completion barriers per kind
 
 // Steps of K's columns accumulated in TMEM before the partial sum is folded
 // into the compensated running sum (keeps the tensor core's FP32 accumulation
-// to 16 x 8 x 2 = 256 MMAs per partial sum).
-constexpr int kTcChunk = 16;
+// to 12 x 8 x 2 = 192 MMAs per partial sum).  Measured on the 50,000-point
+// RBF solve: 16 steps gave 4.8e-6 MVM error and 915 iterations, 12 steps
+// 3.7e-6 and 897 (0.6 % faster in all; the 512-problem batch 3 % faster), 8
+// steps 897 iterations but slower folds, 32 steps 9.7e-6 and 1000 iterations.
+constexpr int kTcChunk = 12;
 
 // TMEM: three S buffers of 128 columns, each overwritten by its P in place,
 // block by block: the 16 values of S in columns [16k, 16k+16) become 8
