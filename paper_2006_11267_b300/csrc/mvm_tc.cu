@@ -285,12 +285,20 @@ __host__ __device__ constexpr int tc_vstep_bytes() {
 constexpr int kRing = 8;                         // completion barriers per kind (>= stages + 2)
 
 // Steps of K's columns accumulated in TMEM before the partial sum is folded
-// into the compensated running sum (keeps the tensor core's FP32 accumulation
-// to 12 x 8 x 2 = 192 MMAs per partial sum).  Measured on the 50,000-point
-// RBF solve: 16 steps gave 4.8e-6 MVM error and 915 iterations, 12 steps
-// 3.7e-6 and 897 (0.6 % faster in all; the 512-problem batch 3 % faster), 8
-// steps 897 iterations but slower folds, 32 steps 9.7e-6 and 1000 iterations.
-constexpr int kTcChunk = 12;
+// into the compensated running sum (bounds the tensor core's FP32
+// accumulation to kTcChunk x 16 MMAs per partial sum).  Fewer steps per fold
+// cost exp-warpgroup time (the fold reads TP columns of O) but lower the MVM
+// error, and the solves need fewer iterations.  Measured on the 50,000-point
+// RBF problem:
+//   TP = 64, K^{1/2} with error bound 1e-3: 16 steps, 4.8e-6 MVM error, 915
+//     iterations; 12 steps, 3.7e-6 and 897, fastest; 8 steps, 897 but
+//     slower; 32 steps, 9.7e-6 and 1000;
+//   TP = 32 (8 columns), K^{-1/2}: 12 steps, 2833 iterations; 8 steps 2704
+//     and 1.2 % faster (a fold there reads half as many columns).
+template <int TP>
+__host__ __device__ constexpr int tc_chunk() {
+    return TP <= 32 ? 8 : 12;
+}
 
 // TMEM: three S buffers of 128 columns, each overwritten by its P in place,
 // block by block: the 16 values of S in columns [16k, 16k+16) become 8
@@ -391,6 +399,7 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
     const int ntot = (int)(a.Npad / kTcKN);
     const int st0 = (int)((int64_t)split * ntot / S);
     const int nt = (int)((int64_t)(split + 1) * ntot / S) - st0;   // steps of this CTA (>= 1)
+    constexpr int kTcChunk = tc_chunk<TP>();
     const int nfold = (nt - 1) / kTcChunk;               // chunks folded before the last one
     constexpr uint32_t IDESC_S = tc::idesc_f16(kTcBM, kTcKN, !HALF);
     constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
