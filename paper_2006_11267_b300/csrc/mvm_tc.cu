@@ -293,11 +293,15 @@ constexpr int kRing = 8;                         // completion barriers per kind
 //   TP = 64, K^{1/2} with error bound 1e-3: 16 steps, 4.8e-6 MVM error, 915
 //     iterations; 12 steps, 3.7e-6 and 897, fastest; 8 steps, 897 but
 //     slower; 32 steps, 9.7e-6 and 1000;
-//   TP = 32 (8 columns), K^{-1/2}: 12 steps, 2833 iterations; 8 steps 2704
-//     and 1.2 % faster (a fold there reads half as many columns).
+//   TP = 32 (a fold reads half as many columns), the 512-problem batch with
+//     residual 1e-4: 12 steps, 108 columns left at the iteration cap; 8
+//     steps, 77 and 4 % faster; 6, 67 and 4 % faster again; 4 steps, 34 at
+//     the same speed as 6.  The 8-column K^{-1/2} solve: 2833, 2704, 2650 and
+//     2581 iterations, 2249, 2223, 2235 and 2306 ms.  Batched and single
+//     solves share the interval (their results are equal bit for bit).
 template <int TP>
 __host__ __device__ constexpr int tc_chunk() {
-    return TP <= 32 ? 8 : 12;
+    return TP <= 32 ? 4 : 12;
 }
 
 // TMEM: three S buffers of 128 columns, each overwritten by its P in place,
