@@ -412,7 +412,8 @@ size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* op
  * more.  X, V, out: device pointers (layouts as above), else CIQ_ERR_ARG.
  * The first call on a device looks up the scratch's device address (once
  * per device, with that device current); make that first call before any
- * stream capture.  All calls share the one array and it keeps the last
+ * stream capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset of a device, do not call this entry point on it again.  All calls share the one array and it keeps the last
  * call's contents (the call clears what must start at zero): calls that
  * overlap on the GPU, e.g. on two streams, race on it.  Allocates nothing
  * (no cudaMalloc, cudaFree or allocating library routine).  Asynchronous on

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "batched.cuh"
+#include "host_checks.cuh"
 #include "krylov.cuh"
 #include "mlp.cuh"
 #include "mvm_stored.cuh"
@@ -38,18 +39,6 @@ struct Arena {
         return p;
     }
 };
-
-bool device_accessible(const void* p) {
-    if (p == nullptr) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-int dim_pad(int d) { return (d + 3) / 4 * 4; }
 
 // Row chunks per column of the recurrence (its grid is chunks x T blocks):
 // the grid should fill whole waves of resident blocks, so among one to three
@@ -83,12 +72,6 @@ ciq_status from_cuda(cudaError_t e) {
         cudaError_t _e = (__VA_ARGS__);                 \
         if (_e != cudaSuccess) { rc = from_cuda(_e); goto done; } \
     } while (0)
-
-bool valid_kernel(const ciq_kernel* k) {
-    return k && (k->type == CIQ_RBF || k->type == CIQ_MATERN52) && k->lengthscale > 0.0 &&
-           std::isfinite(k->lengthscale) && k->outputscale > 0.0 && std::isfinite(k->outputscale) &&
-           k->noise >= 0.0 && std::isfinite(k->noise);
-}
 
 bool valid_options(const ciq_options& o) {
     return !(o.max_iter < 1 || o.max_iter > 1000000 || o.lanczos_iters < 1 || o.lanczos_iters > 512 ||

@@ -10,6 +10,7 @@
 // library and stays until the process exits.
 #include <mutex>
 
+#include "host_checks.cuh"
 #include "kernels.cuh"
 
 namespace {
@@ -28,7 +29,11 @@ float* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  In host code
 // the symbol g_noalloc_scratch names a host-side stand-in, not device memory,
-// so the address is looked up once per device with that device current.
+// so the address is looked up once per device with that device current and
+// kept for the life of the process.  The cache does not survive a reset of
+// the device's primary context (cudaDeviceReset): the module is loaded again
+// after one and the array may move, so a process that resets a device must
+// not call this entry point on it afterwards.
 cudaError_t scratch_on_current_device(float** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -45,31 +50,20 @@ cudaError_t scratch_on_current_device(float** out) {
     return cudaSuccess;
 }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (p == nullptr || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 extern "C" size_t ciq_noalloc_scratch_floats(void) { return kNoAllocScratchFloats; }
 
 extern "C" ciq_status ciq_kernel_mvm_noalloc(const float* X, int64_t N, int d, const ciq_kernel* kern,
                                              const float* V, int T, float* out, ciq_stream_t stream) {
-    if (!X || !V || !out || !kern || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 ||
-        (kern->type != CIQ_RBF && kern->type != CIQ_MATERN52) || !(kern->lengthscale > 0.0) ||
-        !(kern->outputscale > 0.0) || !(kern->noise >= 0.0))
+    if (!X || !V || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || !valid_kernel(kern))
         return CIQ_ERR_ARG;
     const int64_t Npad = round_up(N, kRowPad);
-    const int dp = (d + 3) / 4 * 4;
+    const int dp = dim_pad(d);
     const int64_t x_floats = round_up(Npad * dp, 64);
     const double need = (double)x_floats + (double)T * (double)Npad;
     if (need > (double)kNoAllocScratchFloats) return CIQ_ERR_SCRATCH_TOO_SMALL;
-    if (!on_device(X) || !on_device(V) || !on_device(out)) return CIQ_ERR_ARG;
+    if (!device_accessible(X) || !device_accessible(V) || !device_accessible(out)) return CIQ_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     float* scratch = nullptr;
     cudaError_t e = scratch_on_current_device(&scratch);

@@ -141,3 +141,26 @@ def test_dense_validates_before_the_device():
         _ciq.CIQ_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         P.ciq_sqrt_dense(K[:, :4].copy(), B, 4, 1e-4)
+
+
+@pytest.mark.parametrize("field,value", [("lengthscale", float("inf")), ("lengthscale", float("nan")),
+                                         ("outputscale", float("inf")), ("outputscale", float("nan")),
+                                         ("noise", float("inf")), ("noise", float("nan"))])
+def test_kernel_mvm_entry_points_reject_non_finite_hyperparameters(field, value):
+    # Both MVM entry points share one kernel check.  The valid kernel is sent
+    # down a path that fails later for another reason (tensor-core tiles with
+    # d = 16; a problem beyond the static scratch), so on a machine without a
+    # GPU the two status codes still tell the checks apart.
+    lib = P.lib()
+    buf = np.zeros(64, np.float32)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    good = P.Kernel("rbf", 0.5, 1.0, 1e-2).c()
+    bad = P.Kernel("rbf", 0.5, 1.0, 1e-2).c()
+    setattr(bad, field, value)
+    fp16 = _ciq.PRECISIONS["fp16"]
+    assert lib.ciq_kernel_mvm(ptr, 4, 16, ctypes.byref(good), ptr, 1, ptr, fp16, None) == _ciq.CIQ_ERR_UNSUPPORTED
+    assert lib.ciq_kernel_mvm(ptr, 4, 16, ctypes.byref(bad), ptr, 1, ptr, fp16, None) == _ciq.CIQ_ERR_ARG
+    huge = 1 << 30
+    assert lib.ciq_kernel_mvm_noalloc(ptr, huge, 3, ctypes.byref(good), ptr, 1, ptr, None) == \
+        _ciq.CIQ_ERR_SCRATCH_TOO_SMALL
+    assert lib.ciq_kernel_mvm_noalloc(ptr, huge, 3, ctypes.byref(bad), ptr, 1, ptr, None) == _ciq.CIQ_ERR_ARG
