@@ -19,7 +19,8 @@ Two parts:
 
 Every function cites the passage it follows.  Pins (tests marked
 ``not gpu``) tie each part to closed forms, library routines (SciPy, LAPACK)
-and brute force rather than to the oracle itself.  Parity unpinned: the
-lambda_min reading for sigma^2 = 0 (theta_min / 100), which the paper leaves
-open.
+and brute force rather than to the oracle itself.  The lambda_min reading
+for sigma^2 = 0 (theta_min / 100), which the paper leaves open, is pinned on
+the matrices it is used for (it lies below LAPACK's smallest eigenvalue there);
+it is not a bound in general.
 """

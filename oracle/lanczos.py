@@ -20,7 +20,9 @@ extremes and gives no margin).  Reading:
   lambda_max_used = 1.05 theta_max(T_J)
   lambda_min_used = sigma^2                  if sigma^2 > 0 (K_XX is PSD, so
                                              lambda_min(K) >= sigma^2 exactly)
-                  = theta_min(T_J) / 100     otherwise (parity unpinned).
+                  = theta_min(T_J) / 100     otherwise (a heuristic: pinned
+                                             against LAPACK's lambda_min on the
+                                             Q-sweep matrices, not a bound).
 """
 from __future__ import annotations
 

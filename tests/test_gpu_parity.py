@@ -1,15 +1,17 @@
 """Parity of the CUDA path against the FP64 oracle, through the C ABI.
 
 Inputs are seeded (ciq_inputs) and rounded to FP32 before both sides see
-them, so differences come from arithmetic only.  Tolerances:
-  * FP32 kernel MVM: 2e-6 relative (Frobenius) -- FP32 rounding of d-term
+them, so differences come from arithmetic only.  Every error is a relative
+2-norm per right-hand side, gated on the largest (tests/relerr.py).
+Tolerances:
+  * FP32 kernel MVM: 2e-6 relative -- FP32 rounding of d-term
     distances, expf/sqrtf (<= 2 ulp) and compensated N-term sums;
   * FP32 solves vs the serial FP64 oracle at equal nodes and J, once both
-    have converged: K^{1/2}b within 1e-5; K^{-1/2}b within
-    max(1e-5, 20 u sqrt(kappa)), u = 2^-24.  FP32 Lanczos vectors perturb
-    the Krylov recurrence by O(u) per step, which limits the attainable
-    accuracy of K^{-1/2}b (whose sensitivity grows like sqrt(kappa));
-    measured constants were 4-11 (CPU emulation and GPU agree);
+    have converged: K^{1/2}b within 1e-5; K^{-1/2}b within 1e-5, or within
+    8 times the oracle's own change when K's entries are rounded to FP32
+    if that is larger (relerr.fp32_gate: at kappa ~ 1e4 the rounding of the
+    entries alone moves K^{-1/2}b by 4e-6 to 7e-6, so 1e-5 is out of reach
+    of any FP32 kernel evaluation there);
   * FP64 solves: 1e-11 once converged.  Before convergence two correct FP64
     implementations differ by far more than rounding (finite-precision
     Lanczos is chaotic there: a 1e-16 change of K moves the J = 200 iterate
@@ -25,6 +27,7 @@ import paper_2006_11267_b300 as P
 from oracle import ciq as O
 from oracle import eig, kernels
 from oracle.lanczos import lanczos, ritz_extremes
+from relerr import fp32_gate, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -33,12 +36,6 @@ DEV = "cuda"
 
 def f32(a):
     return np.asarray(a, dtype=np.float32)
-
-
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def problem(n, d, t, seed, kind="matern52", ls=0.2, s=1.0, noise=1e-2):
@@ -59,7 +56,7 @@ def test_kernel_mvm_fp32_matches_oracle(kind, n, d, t):
     X, V, k = problem(n, d, t, 100 + n + d + t, kind, ls=0.3, s=1.3, noise=1e-3)
     out = P.ciq_kernel_mvm(torch.from_numpy(X).to(DEV), k, torch.from_numpy(V).to(DEV))
     ref = dense_K(X, k) @ V.T.astype(np.float64)
-    assert rel(out.cpu().numpy().T, ref) < 2e-6
+    assert rel(out.cpu().numpy(), ref.T) < 2e-6
 
 
 @pytest.mark.parametrize("kind", ["rbf", "matern52"])
@@ -69,7 +66,7 @@ def test_kernel_mvm_fp64_matches_oracle(kind):
     V = V.astype(np.float64)
     out = P.ciq_kernel_mvm_f64(torch.from_numpy(X).to(DEV), k, torch.from_numpy(V).to(DEV))
     ref = dense_K(X, k) @ V.T
-    assert rel(out.cpu().numpy().T, ref) < 1e-13
+    assert rel(out.cpu().numpy(), ref.T) < 1e-13
 
 
 # ------------------------------------------------------------ pre-pass ----
@@ -96,11 +93,12 @@ def _oracle(op, X, k, B, Q, J, nodes, tol=0.0, stop_rule="residual"):
                        stop_rule=stop_rule, nodes=nodes, lmin=k.noise, lmax=None)
 
 
-U32 = 2.0 ** -24
-
-
-def fp32_tol(op, kappa):
-    return 1e-5 if op == "sqrt" else max(1e-5, 20 * U32 * np.sqrt(kappa))
+def fp32_tol(op, K, ref, run):
+    """K^{1/2}b: 1e-5.  K^{-1/2}b: 1e-5, or 8 times the error that rounding
+    K's entries to FP32 alone causes when that is larger (relerr.fp32_gate)."""
+    if op == "sqrt":
+        return 1e-5, None
+    return fp32_gate(run, K, ref)
 
 
 @pytest.mark.parametrize("krylov", ["recurrence", "basis"])
@@ -118,7 +116,10 @@ def test_fp32_solve_matches_serial_oracle_at_equal_nodes_and_J(op, kind, n, d, t
     out, info = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), Q, 0.0,
                    max_iter=J, nodes=nodes, lmin=k.noise, krylov=krylov)
     assert info["iters"] == J and info["krylov"] == krylov
-    assert rel(out.cpu().numpy(), ref) < fp32_tol(op, lam[-1] / lam[0])
+    tol, floor = fp32_tol(op, K, ref, lambda Km: O.ciq_apply(O.dense_mvm(Km), B.astype(np.float64), Q, op,
+                                                             max_iter=J, nodes=nodes, lmin=k.noise)[0])
+    err = rel(out.cpu().numpy(), ref)
+    assert err < tol, (err, tol, floor)
 
 
 @pytest.mark.parametrize("op,form", [("sqrt", "identity"), ("sqrt", "mvm"), ("invsqrt", "identity")])
@@ -283,7 +284,7 @@ def test_stored_mvm_matches_oracle(n, t):
     P.ciq_kernel_matrix(torch.from_numpy(X).to(DEV), k, Kd)
     out = P.ciq_stored_mvm(Kd, torch.from_numpy(V).to(DEV), n=n)
     ref = dense_K(X, k) @ V.T.astype(np.float64)
-    assert rel(out.cpu().numpy().T, ref) < 2e-6
+    assert rel(out.cpu().numpy(), ref.T) < 2e-6
 
 
 @pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
@@ -297,4 +298,7 @@ def test_stored_k_solve_matches_serial_oracle(op):
     out, info = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), 8, 0.0, max_iter=800,
                    nodes=nodes, lmin=k.noise, mvm="stored")
     assert info["iters"] == 800
-    assert rel(out.cpu().numpy(), ref) < fp32_tol(op, lam[-1] / lam[0])
+    tol, floor = fp32_tol(op, K, ref, lambda Km: O.ciq_apply(O.dense_mvm(Km), B.astype(np.float64), 8, op,
+                                                             max_iter=800, nodes=nodes, lmin=k.noise)[0])
+    err = rel(out.cpu().numpy(), ref)
+    assert err < tol, (err, tol, floor)

@@ -23,17 +23,12 @@ import torch
 import ciq_inputs as ci
 import paper_2006_11267_b300 as P
 from oracle import eig, kernels
+from relerr import rel
 
 pytestmark = pytest.mark.gpu
 
 W = ci.PRECISION_200K
 DEV = "cuda"
-
-
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.fixture(scope="module")
