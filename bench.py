@@ -42,11 +42,22 @@ WORKLOAD = ci.THOMPSON_50K
 TOL = 1e-3
 MAX_ITER = 4000
 LANCZOS_ITERS = 10
-# Iterations this workload needs to reach the error bound 1e-3 (measured: 876
-# for the library's compensated FP32 solve, which tracks the FP64 recurrence;
-# 897 with FP16-split tiles).  Only the reference arm uses it, to scale its
-# per-iteration time to a solve.
-J_WORKLOAD = 875
+# msMINRES iterations this workload needs to reach the error bound 1e-3 in
+# exact-K arithmetic.  A full FP64 oracle solve at N = 50,000 takes hours on
+# the host, so the count is the one measured for the library's FP32 path (876),
+# whose compensated MVM and FP64 scalars track the FP64 recurrence; the
+# FP16-split tiles need 897 because their MVM carries ~4e-6 relative error.
+# Only the reference arm uses it, to scale its per-iteration time to a solve.
+J_WORKLOAD = 876
+# Rows of K per bounded sample of the oracle's kernel MVM: one step of the
+# reference arm (about 5 s of host work) and the CPU leg of our arm (8192).
+REF_SAMPLE_ROWS = 2048
+CPU_SAMPLE_ROWS = 8192
+# The headline configuration is checked against the FP64 eigendecomposition
+# on the workload's first ORACLE_CHECK_N points (O1 is affordable there), with
+# the tensor-core split of three CTAs per row tile that the full-size solve runs.
+ORACLE_CHECK_N = 16384
+ORACLE_CHECK_TC_SPLIT = 3
 
 # Uneven batch: 512 independent GPs (N log-uniform in [256, 8192], d in 2..12,
 # RBF or Matern-5/2, lengthscale log-uniform in [0.05, 1], sigma^2 log-uniform
@@ -140,7 +151,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- CPU baseline --
-def oracle_iteration_seconds(X, B, Q, rows=8192):
+def oracle_iteration_seconds(X, B, Q, rows=CPU_SAMPLE_ROWS):
     """FP64 oracle, bounded sample of one full-size msMINRES iteration.
 
     The O(N^2) part is timed on `rows` of the N rows of K (the oracle's own
@@ -156,7 +167,7 @@ def oracle_iteration_seconds(X, B, Q, rows=8192):
     V = np.ascontiguousarray(B.T)
     t0 = time.perf_counter()
     for r0 in range(0, rows, 2048):
-        kernels.kernel_matrix(X[r0:r0 + 2048], X, W.kernel, W.lengthscale, W.outputscale) @ V
+        kernels.kernel_matrix(X[r0:min(rows, r0 + 2048)], X, W.kernel, W.lengthscale, W.outputscale) @ V
     t_rows = time.perf_counter() - t0
     w, t = quad_nodes(W.noise, 2100.0, Q)
     t0 = time.perf_counter()
@@ -174,6 +185,35 @@ def cpu_threads():
     except Exception:
         pass
     return os.cpu_count() or 1
+
+
+def headline_oracle_check(P, torch, dev, opts):
+    """CPU leg, second part: the headline configuration's delivered columns
+    against the FP64 eigendecomposition (O1, K^{1/2}b = V diag(lambda^{1/2})
+    V^T b) on the workload's first ORACLE_CHECK_N points, per right-hand side
+    (relative 2-norm).  The solve runs with the bench's options and the
+    full-size solve's tensor-core split; only the O(N^3) reference is on the
+    host."""
+    from oracle import eig, kernels
+
+    W = WORKLOAD
+    X, B = W.make(ORACLE_CHECK_N)
+    X = X.astype(np.float32)
+    B = B.astype(np.float32)
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    out, info = P.ciq_sqrt(torch.from_numpy(X).to(dev), k, torch.from_numpy(B).to(dev), W.q, TOL,
+                           **dict(opts, tc_split=ORACLE_CHECK_TC_SPLIT))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    K = kernels.dense_K(X.astype(np.float64), W.kernel, W.lengthscale, W.outputscale, W.noise)
+    truth = eig.sqrt_apply(K, B.T.astype(np.float64)).T
+    del K
+    A = out.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(A - truth, axis=1) / np.linalg.norm(truth, axis=1)
+    return {"n": ORACLE_CHECK_N, "columns": int(err.size), "max": float(err.max()),
+            "median": float(np.median(err)), "iterations": info["iters"], "errbound_max": info["errbound_max"],
+            "tc_split": ORACLE_CHECK_TC_SPLIT, "oracle": "O1: FP64 eigendecomposition (LAPACK dsyevd)",
+            "oracle_seconds": time.perf_counter() - t0}
 
 
 # --------------------------------------------------------------- roofline --
@@ -194,9 +234,13 @@ def device_peaks():
     out, ms = ctypes.c_double(), ctypes.c_double()
     L.ciq_peak_sfu_ex2.argtypes = [ctypes.POINTER(ctypes.c_double)] * 2
     L.ciq_peak_fma.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 2
+    L.ciq_peak_sfu_ex2_clock.argtypes = [ctypes.POINTER(ctypes.c_double)] * 4
     res = {}
-    if L.ciq_peak_sfu_ex2(ctypes.byref(out), ctypes.byref(ms)) == 0:
+    per_clk, mhz = ctypes.c_double(), ctypes.c_double()
+    if L.ciq_peak_sfu_ex2_clock(ctypes.byref(out), ctypes.byref(ms), ctypes.byref(per_clk), ctypes.byref(mhz)) == 0:
         res["sfu_ex2_per_s"] = out.value
+        res["sfu_ex2_per_sm_per_clk"] = per_clk.value
+        res["sfu_sm_mhz"] = mhz.value
     if L.ciq_peak_fma(0, ctypes.byref(out), ctypes.byref(ms)) == 0:
         res["fp32_flops"] = out.value
     if L.ciq_peak_fma(1, ctypes.byref(out), ctypes.byref(ms)) == 0:
@@ -210,15 +254,19 @@ def device_peaks():
 MVM_TC_DRAM_BYTES = {"rbf_n50000_d6_t64_q12": 22.47e6 + 0.211e6}
 
 
-def roofline_tc(W, t_launch_ms, dev, pk):
+def roofline_tc(W, t_launch_ms, dev, pk, sm_mhz=None):
     # One kernel MVM on tensor cores.  Algorithmic work per kernel entry:
     # 2T flops of the product with V plus 2(d+2) flops of the augmented
     # distance (norm expansion), 1 SFU exp2 (RBF; + sqrt for Matern-5/2).
     # The FP16 hi/lo operand split executes three products for the product
     # with V (3 x 2 TP flops per entry, TP = T rounded to the launch group)
     # and two (d <= 6: 8 augmented features fill half of a K = 16 chunk) or
-    # three K = 16 products for the distance.  The line reports the tensor
-    # roofline; the executed-flop and SFU fractions are given beside it.
+    # three K = 16 products for the distance.
+    # Roofline of an on-the-fly tile (the slower of the two pipes): kernel
+    # entries per second the tensor pipe allows at the sustained measured
+    # BF16 rate, against entries per second the SFU allows at the measured
+    # ex2 rate per SM and clock, scaled to the SM clock sampled during the
+    # timed solves.  The line reports the binding one; both are given.
     N, T, d = W.n, W.t, W.d
     entries = float(N) * N
     secs = t_launch_ms * 1e-3
@@ -232,18 +280,30 @@ def roofline_tc(W, t_launch_ms, dev, pk):
     burst = pk.get("bf16_tflops")
     sfu_per_entry = 1 if W.kernel == "rbf" else 2
     sfu_rate = entries * sfu_per_entry / secs
-    sfu_peak = dev.get("sfu_ex2_per_s")
-    return {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s",
-            "frac": alg / peak if peak else None, "traffic": MVM_TC_DRAM_BYTES.get(W.name),
-            "traffic_unit": "bytes per launch",
+    per_clk = dev.get("sfu_ex2_per_sm_per_clk")
+    mhz = sm_mhz or dev.get("sfu_sm_mhz")
+    sfu_peak = per_clk * SM_COUNT * mhz * 1e6 if per_clk and mhz else dev.get("sfu_ex2_per_s")
+    entry_rate = entries / secs / 1e9                                    # G entries/s
+    tensor_roof = peak * 1e12 / (2 * T + 2 * (d + 2)) / 1e9 if peak else None
+    sfu_roof = sfu_peak / sfu_per_entry / 1e9 if sfu_peak else None
+    roofs = {k: v for k, v in (("tensor", tensor_roof), ("sfu", sfu_roof)) if v}
+    bound = min(roofs, key=roofs.get) if roofs else "tensor"
+    return {"bound": bound, "achieved": entry_rate, "peak": roofs.get(bound), "unit": "Gentries/s",
+            "frac": entry_rate / roofs[bound] if roofs else None,
+            "traffic": MVM_TC_DRAM_BYTES.get(W.name), "traffic_unit": "bytes per launch",
             "kernel": "mvm_tc_kernel (tcgen05 on-the-fly kernel MVM, FP16 hi/lo split operands)",
-            "peak_source": "measured cuBLAS BF16 dense rate, sustained (MEASURED_PEAKS.json), taken for FP16 "
-                           "(same nominal rate)",
-            "peak_burst": burst, "frac_burst": alg / burst if burst else None,
-            "executed_tflops": executed, "frac_executed": executed / peak if peak else None,
+            "peak_source": "min(tensor roof: measured cuBLAS BF16 sustained rate (MEASURED_PEAKS.json) / "
+                           "(2T + 2(d+2)) flops per entry; SFU roof: measured ex2 per SM per clock "
+                           "(libciq_peaks) x 148 SMs x the SM clock sampled during the timed solves)",
+            "tensor": {"achieved_tflops": alg, "peak_tflops": peak, "frac": alg / peak if peak else None,
+                       "peak_burst_tflops": burst, "frac_burst": alg / burst if burst else None,
+                       "executed_tflops": executed, "frac_executed": executed / peak if peak else None,
+                       "roof_gentries_per_s": tensor_roof},
             "sfu": {"achieved_ex2_per_s": sfu_rate, "peak_ex2_per_s": sfu_peak,
                     "frac": sfu_rate / sfu_peak if sfu_peak else None,
-                    "peak_source": "measured by libciq_peaks (ex2.approx throughput)"}}
+                    "ex2_per_sm_per_clk": per_clk, "sm_mhz": mhz,
+                    "peak_measured_at_mhz": dev.get("sfu_sm_mhz"),
+                    "roof_gentries_per_s": sfu_roof}}
 
 
 def roofline_fp32(N, T, d, t_launch_ms, pk):
@@ -288,10 +348,14 @@ def run_reference(args):
         return 0
     W = WORKLOAD
     X, B = W.make()
+    X = X.astype(np.float32).astype(np.float64)       # the FP32 inputs our arm solves
+    B = B.astype(np.float32).astype(np.float64)
     Q = W.q
+    for _ in range(args.warmup):                       # untimed warm-up samples
+        oracle_iteration_seconds(X, B, Q, rows=REF_SAMPLE_ROWS)
     steps = []
-    for _ in range(max(1, args.warmup and 0) + args.steps):
-        t_iter, t_spent, rows = oracle_iteration_seconds(X, B, Q)
+    for _ in range(args.steps):
+        t_iter, t_spent, rows = oracle_iteration_seconds(X, B, Q, rows=REF_SAMPLE_ROWS)
         steps.append(t_iter)
     t_iter = statistics.median(steps)
     t_solve = t_iter * (LANCZOS_ITERS + J_WORKLOAD)
@@ -300,8 +364,11 @@ def run_reference(args):
             "unit": "RHS-solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "T": W.t, "Q": Q,
-                       "tol": TOL, "stop_rule": "errbound", "iterations": LANCZOS_ITERS + J_WORKLOAD},
+            "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
+                       "noise": W.noise, "T": W.t, "Q": Q, "op": "sqrt", "tol": TOL, "stop_rule": "errbound",
+                       "precision": "fp64", "krylov": "recurrence", "iterations": [J_WORKLOAD] * args.steps,
+                       "lanczos_iters": LANCZOS_ITERS, "parallelism": "replicas1",
+                       "l2": "host oracle (no device)"},
             "cpu_baseline": {"value": value, "unit": "RHS-solves/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": f"per step: oracle kernel MVM on {rows} of {W.n} rows (scaled x{W.n / rows:.2f}) "
                                        f"+ one full-size oracle msMINRES vector step; x{LANCZOS_ITERS + J_WORKLOAD} iterations"},
@@ -390,7 +457,7 @@ def run_ours(args):
         roof = roofline_fp32(W.n, W.t, W.d, t_mvm, pk)
         roof["peak_source"] = pk_kind
     else:
-        roof = roofline_tc(W, t_mvm, devpk, pk)
+        roof = roofline_tc(W, t_mvm, devpk, pk, clocks.get("sm_mhz"))
     fp32 = None
     if not args.no_fp32_compare and args.precision != "fp32":
         o32 = dict(opts, precision="fp32")
@@ -421,6 +488,9 @@ def run_ours(args):
         e2e = {"value": e2e_rate, "unit": "RHS-solves/s",
                "h2d_bytes_per_step": int(X.nbytes + B.nbytes), "d2h_bytes_per_step": int(out_h.nbytes)}
     cpu = None
+    oracle_err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.n:
+        oracle_err = headline_oracle_check(P, torch, dev, opts)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         J = int(statistics.median(i["iters"] for i in infos))
         t_iter, t_spent, rows = oracle_iteration_seconds(X.astype(np.float64), B.astype(np.float64), W.q)
@@ -447,6 +517,7 @@ def run_ours(args):
                             "mvm_share": pinfo["t_mvm_ms"] / max(pinfo["t_total_ms"], 1e-9),
                             "recurrence_share": pinfo["t_step_ms"] / max(pinfo["t_total_ms"], 1e-9),
                             "prepass_ms": pinfo["t_prepass_ms"], "total_ms": pinfo["t_total_ms"]},
+                "oracle_err": oracle_err,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "plain_fp32_gpu_path": fp32, "device_peaks": devpk}
         print(json.dumps(line), flush=True)

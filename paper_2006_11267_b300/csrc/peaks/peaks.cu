@@ -14,7 +14,20 @@ __device__ __forceinline__ float ex2f(float x) {
     return y;
 }
 
-__global__ void ex2_kernel(float* out, int iters) {
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// clk (optional): thread 0 of block 0 writes the SM clock count and the
+// global timer (ns) at its start and end, so the run's own SM clock is known.
+__global__ void ex2_kernel(float* out, int iters, unsigned long long* clk) {
+    unsigned long long c0 = 0, t0 = 0;
+    if (clk && blockIdx.x == 0 && threadIdx.x == 0) {
+        c0 = clock64();
+        t0 = globaltimer_ns();
+    }
     float a[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) a[k] = -1.0f - 1e-3f * (float)(threadIdx.x + k);
@@ -26,6 +39,10 @@ __global__ void ex2_kernel(float* out, int iters) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += a[k];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (clk && blockIdx.x == 0 && threadIdx.x == 0) {
+        clk[0] = clock64() - c0;
+        clk[1] = globaltimer_ns() - t0;
+    }
 }
 
 template <typename T>
@@ -75,9 +92,32 @@ extern "C" int ciq_peak_sfu_ex2(double* ops_per_s, double* ms) {
     const int blocks = 8 * sm_count(), threads = 256, iters = 4096;
     float* out = nullptr;
     if (cudaMalloc(&out, sizeof(float) * blocks * threads) != cudaSuccess) return 2;
-    int rc = time_kernel([&] { ex2_kernel<<<blocks, threads>>>(out, iters); }, ms);
+    int rc = time_kernel([&] { ex2_kernel<<<blocks, threads>>>(out, iters, nullptr); }, ms);
     *ops_per_s = (double)blocks * threads * iters * 8 / (*ms * 1e-3);
     cudaFree(out);
+    return rc;
+}
+
+// The same ex2 throughput over a longer run (about 20 ms), with the SM clock
+// the run itself saw: ops/s, ex2 per SM per clock cycle, and SM MHz (clock64
+// cycles over global-timer ns of one thread that lives for the whole launch).
+extern "C" int ciq_peak_sfu_ex2_clock(double* ops_per_s, double* ms, double* per_sm_per_clk, double* sm_mhz) {
+    const int sms = sm_count(), blocks = 8 * sms, threads = 256, iters = 65536;
+    float* out = nullptr;
+    unsigned long long* clk = nullptr;
+    if (cudaMalloc(&out, sizeof(float) * blocks * threads) != cudaSuccess) return 2;
+    if (cudaMalloc(&clk, 2 * sizeof(unsigned long long)) != cudaSuccess) { cudaFree(out); return 2; }
+    int rc = time_kernel([&] { ex2_kernel<<<blocks, threads>>>(out, iters, clk); }, ms);
+    unsigned long long h[2] = {0, 0};
+    if (cudaMemcpy(h, clk, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) rc = 2;
+    const double ops = (double)blocks * threads * iters * 8;
+    *ops_per_s = ops / (*ms * 1e-3);
+    *sm_mhz = h[1] ? (double)h[0] / (double)h[1] * 1e3 : 0.0;
+    // Cycles of the whole launch at that clock.
+    const double cycles = (*ms * 1e-3) * (*sm_mhz * 1e6);
+    *per_sm_per_clk = cycles > 0 ? ops / (cycles * sms) : 0.0;
+    cudaFree(out);
+    cudaFree(clk);
     return rc;
 }
 
