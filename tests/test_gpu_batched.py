@@ -104,7 +104,7 @@ def test_batched_matches_serial_oracle_at_equal_nodes_and_J(op):
         assert np.max(info_o["errbound"] / np.linalg.norm(ref, axis=1)) < 1e-9
         probs.append(pr)
         refs.append(ref)
-        gates.append((1e-5, None) if op == "sqrt" else fp32_gate(run, K, ref))
+        gates.append(fp32_gate(run, K, ref))
     outs, infos = batched(op, probs, Q, 0.0, max_iter=J)
     for out, ref, info, (tol, floor) in zip(outs, refs, infos, gates):
         assert info["iters"] == J

@@ -40,9 +40,9 @@ def test_dense_solve_matches_oracle_at_equal_nodes_and_J(op, krylov):
                    nodes=nodes, lmin=lam[0], lmax=lam[-1], krylov=krylov)
     assert info["iters"] == J and info["krylov"] == krylov
     # The matrix is given in FP32, so the oracle already sees the rounded
-    # entries: the gate is 1e-5, or 8 times the change that rounding them
+    # entries: the gate is 1e-5, or 15 times the change that rounding them
     # once more would cause (relerr.fp32_gate) when that is larger.
-    tol, floor = (1e-5, None) if op == "sqrt" else fp32_gate(
+    tol, floor = fp32_gate(
         lambda Km: O.ciq_apply(O.dense_mvm(Km), B.astype(np.float64), Q, op, max_iter=J, nodes=nodes,
                                lmin=lam[0], lmax=lam[-1])[0], K, ref)
     err = rel(out.cpu().numpy(), ref)

@@ -33,15 +33,13 @@ def test_vjp_matches_oracle_at_equal_nodes_and_J(kind, op, precision):
     out, gB, gth, info = fn(torch.from_numpy(X).cuda(), k, torch.from_numpy(B).cuda(), torch.from_numpy(G).cuda(),
                             Q, 0.0, max_iter=J, nodes=(w, t), lmin=noise, precision=precision)
     assert info["iters"] == J and info["krylov"] == "basis"
-    # FP32 kernel entries: K^{-1/2} b within 8 times the oracle's own change
-    # when K's entries are rounded to FP32 (relerr.fp32_gate; the forward
-    # parity tests' convention), at least 2e-5; FP16-split tiles add 1e-4.
-    tol, floor = 2e-5, None
-    if op == "invsqrt":
-        BG = np.concatenate([B, G]).astype(np.float64)
-        ref = np.concatenate([A_o, gB_o])
-        tol, floor = fp32_gate(lambda Km: O.ciq_apply(O.dense_mvm(Km), BG, Q, op, max_iter=J, nodes=(w, t),
-                                                      lmin=noise)[0], K, ref, least=2e-5)
+    # FP32 kernel entries: within 15 times the oracle's own change when K's
+    # entries are rounded to FP32 (relerr.fp32_gate; the forward parity tests'
+    # convention), at least 2e-5; FP16-split tiles add 1e-4.
+    BG = np.concatenate([B, G]).astype(np.float64)
+    ref = np.concatenate([A_o, gB_o])
+    tol, floor = fp32_gate(lambda Km: O.ciq_apply(O.dense_mvm(Km), BG, Q, op, max_iter=J, nodes=(w, t),
+                                                  lmin=noise)[0], K, ref, least=2e-5)
     if precision == "fp16":
         tol = max(tol, 1e-4)
     e_out, e_gb = rel(out.cpu().numpy(), A_o), rel(gB.cpu().numpy(), gB_o)
