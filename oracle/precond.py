@@ -75,11 +75,12 @@ def pivoted_cholesky(diag, column, rank):
         if d[i] <= 0.0:
             L = L[:, :k]
             break
-        piv.append(i)
         col = np.asarray(column(i), dtype=np.float64) - L[:, :k] @ L[i, :k]
+        col[piv] = 0.0                        # earlier pivot rows of the Schur complement are exactly 0
+        piv.append(i)
         L[:, k] = col / np.sqrt(d[i])
         d = d - L[:, k] ** 2
-        d[piv] = 0.0                          # pivot rows are exact: no rounding residue
+        d[piv] = 0.0                          # and so is the diagonal at every pivot
     return L, np.array(piv, dtype=np.int64)
 
 
