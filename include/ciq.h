@@ -177,7 +177,7 @@ typedef struct {
     double ritz_max_solve;    /* largest Ritz value of column 0's msMINRES tridiagonal
                                  (ciq_*_batched_learned only; else 0) */
     int krylov;               /* ciq_krylov_form the solve ran (RECURRENCE or BASIS) */
-    int reserved;
+    int precond_rank;         /* ciq_*_precond: directions of the preconditioner kept (else 0) */
 } ciq_info;
 
 /* Human-readable name of a status code (static string). */
@@ -395,6 +395,57 @@ ciq_status ciq_sqrt_batched_learned(const ciq_problem* probs, int P, int Q, doub
 ciq_status ciq_invsqrt_batched_learned(const ciq_problem* probs, int P, int Q, double tol,
                                        const ciq_options* opt, const float* theta, double margin,
                                        ciq_info* infos, int* fallback, ciq_stream_t stream);
+
+/* ---- preconditioned solves (Sec. 3 "Preconditioning"; App. "Preconditioning
+ * msMINRES-CIQ", Eq. precond_sqrt and Eq. precond_sqrt_inverse) ----
+ *
+ * Preconditioner: P = L L^T + sigma^2 I with L the rank-`rank` partial
+ * pivoted Cholesky factor of K_XX (greedy pivot: the largest residual
+ * diagonal entry, the first index on ties).  msMINRES-CIQ then runs on
+ * A = P^{-1/2} K P^{-1/2}, whose spectrum lies in [1, lambda_max(P^{-1}K)]
+ * (K_XX - L L^T is positive semidefinite), with the nodes for lambda_min = 1
+ * and lambda_max = lmax_margin times the largest Ritz value of a pre-pass on
+ * A (or opt->lmin/lmax, opt->quad_w/quad_t for A), and returns
+ *     ciq_invsqrt_precond:  out = R' B = P^{-1/2} A^{-1/2} B,  R' R'^T = K^{-1},
+ *     ciq_sqrt_precond:     out = R  B = P^{1/2}  A^{1/2}  B,  R  R^T  = K,
+ * square roots of K^{-1} and K that equal the principal ones up to an
+ * orthogonal rotation (Eq. precond_sqrt_inverse with P^{1/2} b as the start
+ * vector; R = K P^{-1/2} A^{-1/2} of Eq. precond_sqrt).  Convergence follows
+ * the conditioning of P^{-1}K instead of K.  The stop rules apply to the
+ * estimate in the space of A (relative error of A^{+-1/2} b).  P^{+-1/2}
+ * come in closed form from the eigendecomposition of L^T L (host, FP64): with
+ * L^T L = U diag(s) U^T and Qh = L U diag(s)^{-1/2},
+ * P^{+-1/2} = sigma^{+-1} I + Qh diag((s + sigma^2)^{+-1/2} - sigma^{+-1}) Qh^T,
+ * applied in FP32 around every kernel MVM; directions with s <= 1e-10 max(s)
+ * are dropped.
+ * L: NULL (the factor is computed on the device, rank columns or fewer when
+ * the residual diagonal vanishes) or the caller's N x rank factor, column m
+ * at L + m * ldl (ldl >= N), host or device, used as given.  1 <= rank <=
+ * min(N, 1024); sigma^2 (kern->noise) > 0.  Every other argument, option and
+ * return code is that of ciq_sqrt / ciq_invsqrt; opt->sqrt_form CIQ_SQRT_MVM
+ * gives CIQ_ERR_UNSUPPORTED.  The setup reads L^T L on the host, so these
+ * calls synchronise the stream before the iterations as well.
+ * info->precond_rank: the directions kept. */
+ciq_status ciq_sqrt_precond(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, const float* L,
+                            int64_t ldl, const float* B, int T, int Q, double tol, const ciq_options* opt, float* out,
+                            ciq_info* info, ciq_stream_t stream);
+ciq_status ciq_invsqrt_precond(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, const float* L,
+                               int64_t ldl, const float* B, int T, int Q, double tol, const ciq_options* opt,
+                               float* out, ciq_info* info, ciq_stream_t stream);
+
+/* The partial pivoted Cholesky factor the preconditioned solves build: L
+ * (N x rank, column m at L + m * ldl, ldl >= N; host or device) and the
+ * pivots piv[0 .. rank-1] (host or device int64, may be NULL); *rank_out
+ * (host, may be NULL) = the columns formed (fewer than rank when the residual
+ * diagonal of K_XX - L L^T vanishes first; later columns are 0).  K_XX is
+ * evaluated in FP32 (the accurate expf), the residual diagonal and the dot
+ * products with earlier columns in FP64.  Synchronous. */
+ciq_status ciq_pivoted_cholesky(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, float* L,
+                                int64_t ldl, int64_t* piv, int* rank_out, ciq_stream_t stream);
+
+/* Device workspace bytes a preconditioned solve of this rank needs (for
+ * opt->workspace). */
+size_t ciq_precond_workspace_bytes(int64_t N, int d, int T, int Q, int rank, const ciq_options* opt);
 
 /* Device workspace bytes a solve with these sizes and options needs. */
 size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt);

@@ -71,7 +71,7 @@ class _Info(ctypes.Structure):
                 ("t_total_ms", ctypes.c_double), ("t_prepass_ms", ctypes.c_double),
                 ("t_mvm_ms", ctypes.c_double), ("t_step_ms", ctypes.c_double),
                 ("mvm_launches", ctypes.c_int), ("step_launches", ctypes.c_int),
-                ("ritz_max_solve", ctypes.c_double), ("krylov", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("ritz_max_solve", ctypes.c_double), ("krylov", ctypes.c_int), ("precond_rank", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -125,6 +125,10 @@ def lib() -> ctypes.CDLL:
         "ciq_mlp_loss_grad": (I, [P, P, P, I, DP, P, P]),
         "ciq_mlp_train": (I, [P, P, P, P, I, I, I, ctypes.c_float, U64, I, P, P]),
         "ciq_mlp_predict": (I, [P, P, I, P, I, P]),
+        "ciq_sqrt_precond": (I, [P, I64, I, KP, I, P, I64, P, I, I, D, OP, P, IP, P]),
+        "ciq_invsqrt_precond": (I, [P, I64, I, KP, I, P, I64, P, I, I, D, OP, P, IP, P]),
+        "ciq_pivoted_cholesky": (I, [P, I64, I, KP, I, P, I64, P, ctypes.POINTER(I), P]),
+        "ciq_precond_workspace_bytes": (S, [I64, I, I, I, I, OP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -221,7 +225,8 @@ def _info_dict(info: _Info, status: int) -> dict:
                 t_total_ms=info.t_total_ms, t_prepass_ms=info.t_prepass_ms, t_mvm_ms=info.t_mvm_ms,
                 t_step_ms=info.t_step_ms, mvm_launches=info.mvm_launches,
                 step_launches=info.step_launches, ritz_max_solve=info.ritz_max_solve,
-                krylov={v: k for k, v in KRYLOV_FORMS.items()}.get(info.krylov))
+                krylov={v: k for k, v in KRYLOV_FORMS.items()}.get(info.krylov),
+                precond_rank=info.precond_rank)
 
 
 def _check(status: int, where: str, allow=(CIQ_OK, CIQ_NOT_CONVERGED)):
@@ -329,6 +334,63 @@ def ciq_stored_mvm(Kmat, V, out=None, n=None):
     st = lib().ciq_stored_mvm(_ptr(Kmat), N, Kmat.shape[1], _ptr(V), T, _ptr(out), _stream(Kmat, V, out))
     _check(st, "ciq_stored_mvm", allow=(CIQ_OK,))
     return out
+
+
+def _solve_precond(name, X, kernel, B, Q, tol, rank, L, out, **opts):
+    N, d = X.shape
+    T = B.shape[0]
+    if B.shape[1] != N:
+        raise ValueError("B must have shape (T, N)")
+    ldl = N
+    if L is not None:
+        if L.ndim != 2 or L.shape[1] < N:
+            raise ValueError("L must have shape (rank, ldl) with ldl >= N (row m is column m of the factor)")
+        rank, ldl = L.shape
+    if out is None:
+        out = _empty_like_rhs(B, np.float32)
+    o = make_options(**opts)
+    info = _Info()
+    k = kernel.c()
+    st = getattr(lib(), name)(_ptr(X), N, d, ctypes.byref(k), int(rank), _ptr(L), int(ldl), _ptr(B), T, int(Q),
+                              float(tol), ctypes.byref(o), _ptr(out), ctypes.byref(info), _stream(X, B, out, L))
+    _check(st, name)
+    return out, _info_dict(info, st)
+
+
+def ciq_sqrt_precond(X, kernel, B, Q, tol=0.0, rank=100, L=None, out=None, **opts):
+    """R B with R R^T = K (pivoted-Cholesky preconditioner of the given rank,
+    or the caller's factor L of shape (rank, N)). Returns (out, info)."""
+    return _solve_precond("ciq_sqrt_precond", X, kernel, B, Q, tol, rank, L, out, **opts)
+
+
+def ciq_invsqrt_precond(X, kernel, B, Q, tol=0.0, rank=100, L=None, out=None, **opts):
+    """R' B with R' R'^T = K^{-1} (see ciq_sqrt_precond). Returns (out, info)."""
+    return _solve_precond("ciq_invsqrt_precond", X, kernel, B, Q, tol, rank, L, out, **opts)
+
+
+def ciq_pivoted_cholesky(X, kernel, rank):
+    """Partial pivoted Cholesky factor of K_XX: (L of shape (rank, N), pivots
+    (int64, rank), columns formed).  Host arrays are returned for host X,
+    device tensors for a device X."""
+    N, d = X.shape
+    if _is_torch(X):
+        import torch
+        L = torch.empty((rank, N), dtype=torch.float32, device=X.device)
+        piv = torch.empty(rank, dtype=torch.int64, device=X.device)
+    else:
+        L = np.empty((rank, N), np.float32)
+        piv = np.empty(rank, np.int64)
+    got = ctypes.c_int()
+    k = kernel.c()
+    st = lib().ciq_pivoted_cholesky(_ptr(X), N, d, ctypes.byref(k), int(rank), _ptr(L), N, _ptr(piv),
+                                    ctypes.byref(got), _stream(X, L, piv))
+    _check(st, "ciq_pivoted_cholesky", allow=(CIQ_OK,))
+    return L, piv, got.value
+
+
+def ciq_precond_workspace_bytes(N, d, T, Q, rank, **opts):
+    o = make_options(**opts)
+    return int(lib().ciq_precond_workspace_bytes(int(N), int(d), int(T), int(Q), int(rank), ctypes.byref(o)))
 
 
 def _solve_dense(name, K, B, Q, tol, out=None, **opts):

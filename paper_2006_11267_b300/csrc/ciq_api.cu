@@ -20,7 +20,9 @@
 #include "mlp.cuh"
 #include "mvm_stored.cuh"
 #include "mvm_tc.cuh"
+#include "precond.cuh"
 #include "spectral.cuh"
+#include "symeig.h"
 
 using namespace ciq;
 
@@ -128,6 +130,8 @@ struct Plan {
     int fault_inject = 0;         // ciq_options.fault_inject (testing the bounded-wait path)
     bool basis = false;           // stored-basis form (CIQ_KRYLOV_BASIS)
     bool vjp = false;             // backward pass: T = 2 T_B columns [B | G], basis form
+    int pc_rank = 0;              // pivoted-Cholesky preconditioner rank (0: none)
+    bool stage_l = false;         // the caller's factor L is on the host
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB, *V, *sco;
     double *rcoef, *gauss, *bco, *ycoef, *vpart, *vgrad;
@@ -138,6 +142,14 @@ struct Plan {
     double *lpart, *lynp, *bpar, *lalpha, *lbeta;
     int *status, *iters, *brk, *cnt, *all_done, *jeff, *ldone;
     TcPoints tcp;
+    // Preconditioner: factor L and basis Qh [pc_rank][Npad], g^-/g^+, the
+    // scratch of its applications, the MVM's input P^{-1/2} q and raw output
+    // K P^{-1/2} q, the A-space result, and the setup scratch.
+    float *Lf = nullptr, *Qh = nullptr, *pc_g = nullptr, *pcs = nullptr, *Up = nullptr, *Op = nullptr,
+          *Apre = nullptr, *sL = nullptr;
+    double *dres = nullptr, *Gm = nullptr, *gpart = nullptr, *Wm = nullptr;
+    int *piv = nullptr, *rank_out = nullptr;
+    void* cwork = nullptr;
     size_t bytes;
 
     void layout(char* base) {
@@ -203,6 +215,24 @@ struct Plan {
             tcp.inject = fault_inject;
         }
         Kst = stored ? a.take<float>((size_t)Npad * Npad) : nullptr;
+        if (pc_rank > 0) {
+            const size_t RK = (size_t)pc_rank;
+            Lf = a.take<float>(RK * Npad);
+            Qh = a.take<float>(RK * Npad);
+            pc_g = a.take<float>(2 * RK);
+            pcs = a.take<float>(pc_scratch_floats(Npad, pc_rank, T));
+            Up = a.take<float>((size_t)T * Npad);
+            Op = a.take<float>((size_t)T * Npad);
+            Apre = a.take<float>((size_t)T * Npad);
+            dres = a.take<double>((size_t)Npad);
+            Gm = a.take<double>(RK * RK);
+            gpart = a.take<double>((size_t)pc_gram_scratch(Npad, pc_rank));
+            Wm = a.take<double>(RK * RK);
+            piv = a.take<int>(RK + 1);
+            rank_out = a.take<int>(1);
+            cwork = a.take<char>(pc_cholesky_work_bytes(Npad));
+            sL = stage_l ? a.take<float>(RK * (size_t)N) : nullptr;
+        }
         bytes = a.off + kAlign;
     }
 };
@@ -288,10 +318,37 @@ MvmArgs<R> mvm_args(const Plan<R>& p, const ciq_kernel& k) {
     return a;
 }
 
-// Lanczos pre-pass on the device; leaves nodes in p.nodes.
+template <typename R>
+cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns, cudaStream_t st,
+                       bool scale_ready = false);
+
+// The MVM of the preconditioned operator A = P^{-1/2} K P^{-1/2} with the
+// Lanczos epilogue of `a`: U = P^{-1/2} q, O' = K U (plain MVM), then
+// p = P^{-1/2} O' - beta q_prev and the partial sums.
+template <typename R>
+cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<R>& a, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        cudaError_t e = launch_pc_apply(pc, a.V, p.Npad, a.T, true, p.Up, p.Npad, a.stop, st);
+        if (e != cudaSuccess) return e;
+        MvmArgs<R> m = a;
+        m.mode = kPlain;
+        m.V = p.Up;
+        m.out = p.Op;
+        m.ldo = p.Npad;
+        m.lz_q = nullptr;
+        m.lz_sco = nullptr;
+        e = launch_mvm(p, m, false, st, false);
+        if (e != cudaSuccess) return e;
+        return launch_pc_lanczos(pc, p.Op, a.V, a.qprev, a.pout, a.beta, a.partials, a.T, a.stop, st);
+    }
+    return cudaErrorNotSupported;
+}
+
+// Lanczos pre-pass on the device; leaves nodes in p.nodes.  With a
+// preconditioner the pre-pass runs on A and lambda_min = 1 (P <= K).
 template <typename R>
 cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options& o, int Q,
-                        const R* start_dev, cudaStream_t st) {
+                        const R* start_dev, cudaStream_t st, const PrecondState* pc = nullptr) {
     LanczosState<R> ls = lanczos_state(p);
     cudaError_t e = launch_lanczos_init(ls, start_dev, o.seed, st);
     if (e != cudaSuccess) return e;
@@ -304,10 +361,12 @@ cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options
         a.V = (j & 1) ? p.LA : p.LB;
         a.qprev = (j & 1) ? p.LB : p.LA;
         a.beta = p.bpar + (j & 1);
-        if ((e = (p.stored || p.tc) ? launch_mvm(p, a, true, st) : launch_mvm_simt(a, st)) != cudaSuccess) return e;
+        if (pc) e = precond_mvm(p, *pc, a, st);
+        else e = (p.stored || p.tc) ? launch_mvm(p, a, true, st) : launch_mvm_simt(a, st);
+        if (e != cudaSuccess) return e;
         if ((e = launch_lanczos_step(ls, j, st)) != cudaSuccess) return e;
     }
-    return launch_bounds_nodes(ls, p.nodes, Q, k.noise, o.lmax_margin, o.lmin_div, st);
+    return launch_bounds_nodes(ls, p.nodes, Q, pc ? 1.0 : k.noise, o.lmax_margin, o.lmin_div, st);
 }
 
 template <typename R>
@@ -322,7 +381,7 @@ cudaError_t tc_prepare(const Plan<R>& p, int kt, cudaStream_t st) {
 // power-of-two operand scale of the tensor-core MVM.
 template <typename R>
 cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns, cudaStream_t st,
-                       bool scale_ready = false) {
+                       bool scale_ready) {
     if constexpr (sizeof(R) == 4) {
         if (p.tc) return launch_mvm_tc(p.tcp, a, unit_columns, st, scale_ready);
         if (p.stored) return launch_stored_mvm(p.Kst, p.Npad, a, st);
@@ -367,14 +426,106 @@ struct Profile {
     }
 };
 
+// A preconditioned solve's factor: the caller's L (N x rank, column m at
+// L + m * ldl, host or device) or, when L is null, the pivoted Cholesky of
+// K_XX computed here.
+struct PcSpec {
+    const float* L;
+    int64_t ldl;
+    int rank;
+};
+
+// Preconditioner setup (App. "Preconditioning msMINRES-CIQ"): the factor,
+// G = L^T L on the device, its eigendecomposition on the host, the basis
+// Qh = L U diag(s)^{-1/2} of the directions with s > 1e-10 max(s) and the
+// coefficients of P^{+-1/2}.  Synchronises the stream (the host reads G).
+ciq_status build_precond(const Plan<float>& p, const ciq_kernel& k, const PcSpec& spec, const float* Ld,
+                         cudaStream_t st, PrecondState* pc, int* launches) {
+    int R = spec.rank;
+    cudaError_t e = cudaSuccess;
+    if (Ld) {
+        e = cudaMemsetAsync(p.Lf, 0, sizeof(float) * (size_t)R * p.Npad, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(p.Lf, sizeof(float) * p.Npad, Ld, sizeof(float) * spec.ldl, sizeof(float) * p.N, R,
+                                  cudaMemcpyDeviceToDevice, st);
+    } else {
+        e = launch_pivoted_cholesky(p.Xp, p.N, p.Npad, p.dp, k.type, (float)k.outputscale, R, p.Lf, p.piv, p.dres,
+                                    p.cwork, p.rank_out, st);
+        *launches += R + 1;
+        int rr = R;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&rr, p.rank_out, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        R = std::min(R, std::max(0, rr));
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    const double sig2 = k.noise, sig = std::sqrt(k.noise);
+    std::vector<double> G((size_t)R * R), w(R), Z((size_t)R * R), W;
+    std::vector<float> g;
+    int Rk = 0;
+    if (R > 0) {
+        e = launch_gram(p.Lf, p.Npad, R, p.gpart, p.Gm, st);
+        *launches += 2;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(G.data(), p.Gm, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return from_cuda(e);
+        for (double x : G)
+            if (!std::isfinite(x)) return CIQ_ERR_NAN;
+        if (!symeig::eigh(R, G.data(), w.data(), Z.data())) return CIQ_ERR_NAN;
+        const double smax = w[R - 1];
+        std::vector<int> keep;
+        for (int c = 0; c < R; ++c)
+            if (w[c] > 1e-10 * smax && w[c] > 0.0) keep.push_back(c);
+        Rk = (int)keep.size();
+        W.assign((size_t)R * std::max(Rk, 1), 0.0);
+        g.assign(2 * (size_t)std::max(Rk, 1), 0.f);
+        for (int c = 0; c < Rk; ++c) {
+            const double sv = w[keep[c]], inv = 1.0 / std::sqrt(sv), root = std::sqrt(sv + sig2);
+            for (int m = 0; m < R; ++m) W[(size_t)m + (size_t)c * R] = Z[(size_t)m + (size_t)keep[c] * R] * inv;
+            g[c] = (float)(1.0 / root - 1.0 / sig);                  // g^-
+            g[Rk + c] = (float)(root - sig);                         // g^+
+        }
+        if (Rk > 0) {
+            e = cudaMemcpyAsync(p.Wm, W.data(), sizeof(double) * (size_t)R * Rk, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(p.pc_g, g.data(), sizeof(float) * 2 * (size_t)Rk, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = launch_basis_from_factor(p.Lf, p.Npad, R, p.Wm, Rk, p.Qh, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);     // the host vectors go out of scope
+            *launches += 1;
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+    }
+    PrecondState s;
+    s.N = p.N;
+    s.Npad = p.Npad;
+    s.rank = Rk;
+    s.Qh = p.Qh;
+    s.gm = p.pc_g;
+    s.gp = p.pc_g + Rk;
+    s.sigma = (float)sig;
+    s.inv_sigma = (float)(1.0 / sig);
+    s.cpart = p.pcs;
+    s.coef = p.pcs + (pc_scratch_floats(p.Npad, p.pc_rank, p.T) - (size_t)Rk * p.T);
+    s.T = p.T;
+    *pc = s;
+    return CIQ_OK;
+}
+
 // Kd: a caller's explicit matrix (N x N, leading dimension ldk) instead of X
 // and a kernel; the solve then runs on the stored-K MVM with no noise term.
 template <typename R>
 ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* B, int T, int Q,
                  double tol, const ciq_options* opt, R* out, ciq_info* info, cudaStream_t st,
-                 int op, bool fp64, const float* Kd = nullptr, int64_t ldk = 0, double* vjp_grad = nullptr) {
+                 int op, bool fp64, const float* Kd = nullptr, int64_t ldk = 0, double* vjp_grad = nullptr,
+                 const PcSpec* pcs = nullptr) {
     const bool dense = Kd != nullptr;
     const bool vjp = vjp_grad != nullptr;
+    if (pcs) {
+        // Preconditioned solves: FP32 vectors, kernel MVMs, identity forms only.
+        if (fp64 || dense || vjp || pcs->rank < 1 || pcs->rank > kPcMaxRank || pcs->rank > N ||
+            (pcs->L && pcs->ldl < N) || !kern || !(kern->noise > 0.0))
+            return CIQ_ERR_ARG;
+        if (opt && opt->sqrt_form == CIQ_SQRT_MVM) return CIQ_ERR_UNSUPPORTED;
+    }
     if ((!dense && !X) || !B || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q ||
         !(tol >= 0.0) || !valid_kernel(kern) || (dense && (ldk < N || fp64)))
         return CIQ_ERR_ARG;
@@ -417,6 +568,11 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
 
     Plan<R> p = make_plan<R>(N, d, T, Q, o, prepass, tc, true);
     p.vjp = vjp;
+    if (pcs) {
+        p.pc_rank = pcs->rank;
+        p.stage_l = pcs->L && !device_accessible(pcs->L);
+        p.nparts = p.nparts1 = (int)pc_row_tiles(p.Npad);    // the preconditioned epilogue's row tiles
+    }
     p.stage_x = !dense && !device_accessible(X);
     p.stage_b = !device_accessible(B);
     p.stage_out = !device_accessible(out);
@@ -432,6 +588,8 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     double nodes[kNodeCount] = {0};
     int last_j = 0;
     int launches = 0;
+    PrecondState pcst;
+    bool pc_on = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     Profile prof;
     prof.on = o.profile != 0;
@@ -480,6 +638,21 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             CIQ_TRY(form_stored(p, *kern, st));
             launches += p.stored ? 1 : 0;
         }
+        if constexpr (sizeof(R) == 4) {
+            if (p.pc_rank > 0) {
+                const float* Ld = pcs->L;
+                if (p.stage_l) {
+                    CIQ_TRY(cudaMemcpy2DAsync(p.sL, sizeof(float) * N, pcs->L, sizeof(float) * pcs->ldl,
+                                              sizeof(float) * N, pcs->rank, cudaMemcpyHostToDevice, st));
+                    Ld = p.sL;
+                }
+                PcSpec spec = *pcs;
+                if (p.stage_l) spec.ldl = N;
+                rc = build_precond(p, *kern, spec, Ld, st, &pcst, &launches);
+                if (rc != CIQ_OK) goto done;
+                pc_on = true;
+            }
+        }
         KrylovState<R> s = krylov_state(p, op, o, tol);
         CIQ_TRY(launch_init_rhs(s, Bd, st));
         CIQ_TRY(launch_init_state(s, st));
@@ -497,8 +670,9 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             CIQ_TRY(launch_nodes_from_bounds(p.nodes, Q, o.lmin, o.lmax, st));
             launches += 1;
         } else {
-            CIQ_TRY(run_prepass(p, *kern, o, Q, startd, st));
-            launches += 3 + p.JL * (1 + (p.tc ? 4 : 1));   // tensor cores: V scale, V split, product, finish
+            CIQ_TRY(run_prepass(p, *kern, o, Q, startd, st, pc_on ? &pcst : nullptr));
+            launches += 3 + p.JL * (1 + (p.tc ? 4 : 1) + (pc_on ? 6 : 0));   // tensor cores: V scale, V split,
+                                                                             // product, finish
         }
         if (prof.on) CIQ_TRY(cudaEventRecord(prof.t_pre1, st));
         MvmArgs<R> a = mvm_args(p, *kern);
@@ -512,7 +686,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         const int mvm_launches = p.tc ? 1 + 2 * ((T + tc_group_t(T) - 1) / tc_group_t(T)) : 1;
         // Stored basis on tensor cores: the V split of MVM j + 1 finishes
         // step j's vector update (q_{j+1} from p and the published scalars).
-        const bool lz = p.basis && p.tc;
+        const bool lz = p.basis && p.tc && !pc_on;
         CIQ_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
         CIQ_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         if (prof.on) {
@@ -557,11 +731,13 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                         a.qprev = (jj & 1) ? p.QB : p.QA;
                     }
                     a.beta = p.beta + (size_t)(jj & 1) * T;
-                    CIQ_TRY(launch_mvm(p, a, true, st, jj > 1));
+                    if (pc_on) CIQ_TRY(precond_mvm(p, pcst, a, st));
+                    else CIQ_TRY(launch_mvm(p, a, true, st, jj > 1));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
                     CIQ_TRY(launch_msminres_step(s, jj, false, st, !lz));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 2], st));
-                    launches += (lz ? 1 : 2) + mvm_launches + (p.tc && jj == 1 ? 1 : 0);
+                    launches += (lz ? 1 : 2) + mvm_launches + (p.tc && (jj == 1 || pc_on) ? 1 : 0) +
+                                (pc_on ? 6 : 0);
                 }
                 first_j[slot] = j;
                 count[slot] = jb - j + 1;
@@ -589,8 +765,14 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         }
         CIQ_TRY(launch_msminres_step(s, last_j + 1, true, st));
         launches += 1;
+        // Preconditioned: the combine forms the estimate in the space of A,
+        // then P^{-1/2} (R' b) or P^{1/2} (R b) maps it back.
+        R* comb = outd;
+        if constexpr (sizeof(R) == 4) {
+            if (pc_on) comb = p.Apre;
+        }
         if (p.basis) {
-            CIQ_TRY(launch_basis_combine(s, outd, last_j, st));   // kOpSqrtMvm: the sum goes to Y
+            CIQ_TRY(launch_basis_combine(s, comb, last_j, st));   // kOpSqrtMvm: the sum goes to Y
             launches += 2;
         }
         if constexpr (sizeof(R) == 4) {
@@ -611,8 +793,14 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             CIQ_TRY(launch_mvm(p, m, false, st));
             launches += p.basis ? 1 : 2;
         } else if (!p.basis) {
-            CIQ_TRY(launch_combine(s, outd, st));
+            CIQ_TRY(launch_combine(s, comb, st));
             launches += 1;
+        }
+        if constexpr (sizeof(R) == 4) {
+            if (pc_on) {
+                CIQ_TRY(launch_pc_apply(pcst, p.Apre, N, T, op == kOpInvSqrt, outd, N, nullptr, st));
+                launches += pcst.rank > 0 ? 3 : 1;
+            }
         }
         CIQ_TRY(launch_summary(s, last_j, st));
         launches += 1;
@@ -675,6 +863,7 @@ done:
         info->mvm_launches = n_mvm;
         info->step_launches = n_step;
         info->krylov = p.basis ? CIQ_KRYLOV_BASIS : CIQ_KRYLOV_RECURRENCE;
+        info->precond_rank = pc_on ? pcst.rank : 0;
     }
     if (tc_timeout) return CIQ_ERR_TIMEOUT;
     if (summary[6] > 0) return CIQ_ERR_NAN;
@@ -1489,6 +1678,98 @@ ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float
     cudaFreeAsync(Vp, st);
     if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
     return CIQ_OK;
+}
+
+ciq_status ciq_sqrt_precond(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, const float* L,
+                            int64_t ldl, const float* B, int T, int Q, double tol, const ciq_options* opt, float* out,
+                            ciq_info* info, ciq_stream_t stream) {
+    const PcSpec spec{L, ldl, rank};
+    return solve<float>(X, N, d, kern, B, T, Q, tol, opt, out, info, (cudaStream_t)stream, kOpSqrtIdentity, false,
+                        nullptr, 0, nullptr, &spec);
+}
+
+ciq_status ciq_invsqrt_precond(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, const float* L,
+                               int64_t ldl, const float* B, int T, int Q, double tol, const ciq_options* opt,
+                               float* out, ciq_info* info, ciq_stream_t stream) {
+    const PcSpec spec{L, ldl, rank};
+    return solve<float>(X, N, d, kern, B, T, Q, tol, opt, out, info, (cudaStream_t)stream, kOpInvSqrt, false,
+                        nullptr, 0, nullptr, &spec);
+}
+
+ciq_status ciq_pivoted_cholesky(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, float* L,
+                                int64_t ldl, int64_t* piv, int* rank_out, ciq_stream_t stream) {
+    if (!X || !L || N < 1 || d < 1 || d > CIQ_MAX_DIM || rank < 1 || rank > kPcMaxRank || rank > N || ldl < N ||
+        !valid_kernel(kern))
+        return CIQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_warm();
+    const int64_t Npad = round_up(N, kRowPad);
+    const int dp = dim_pad(d);
+    const bool stage_x = !device_accessible(X);
+    Arena ar;
+    auto lay = [&](char* base) {
+        ar = Arena{};
+        ar.base = base;
+        struct { float *Xs, *Xp, *Lf; double* dres; int *piv, *rk; void* work; } b;
+        b.Xs = stage_x ? ar.take<float>((size_t)N * d) : nullptr;
+        b.Xp = ar.take<float>((size_t)Npad * dp);
+        b.Lf = ar.take<float>((size_t)rank * Npad);
+        b.dres = ar.take<double>((size_t)Npad);
+        b.piv = ar.take<int>((size_t)rank + 1);
+        b.rk = ar.take<int>(1);
+        b.work = ar.take<char>(pc_cholesky_work_bytes(Npad));
+        return b;
+    };
+    lay(nullptr);
+    const size_t need = ar.off + kAlign;
+    char* base = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), need, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    auto b = lay(base);
+    std::vector<int> hp((size_t)rank + 1, 0);
+    int got = 0;
+    const float* Xd = X;
+    if (stage_x) {
+        e = cudaMemcpyAsync(b.Xs, X, sizeof(float) * (size_t)N * d, cudaMemcpyHostToDevice, st);
+        Xd = b.Xs;
+    }
+    if (e == cudaSuccess)
+        e = launch_prepare_points<float, float>(Xd, N, d, Npad, dp, 1.0 / kern->lengthscale, b.Xp, st);
+    if (e == cudaSuccess)
+        e = launch_pivoted_cholesky(b.Xp, N, Npad, dp, kern->type, (float)kern->outputscale, rank, b.Lf, b.piv,
+                                    b.dres, b.work, b.rk, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(L, sizeof(float) * ldl, b.Lf, sizeof(float) * Npad, sizeof(float) * N, rank,
+                              cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), b.piv, sizeof(int) * rank, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&got, b.rk, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && piv) {
+        std::vector<int64_t> p64(rank);
+        for (int k = 0; k < rank; ++k) p64[k] = k < got ? hp[k] : -1;
+        e = cudaMemcpy(piv, p64.data(), sizeof(int64_t) * rank, cudaMemcpyDefault);
+    }
+    cudaFreeAsync(base, st);
+    cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    if (rank_out) *rank_out = got;
+    return CIQ_OK;
+}
+
+size_t ciq_precond_workspace_bytes(int64_t N, int d, int T, int Q, int rank, const ciq_options* opt) {
+    if (N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q || rank < 1 || rank > kPcMaxRank ||
+        rank > N)
+        return 0;
+    ciq_options o;
+    ciq_default_options(&o);
+    if (opt) o = *opt;
+    const bool prepass = !(o.quad_w && o.quad_t) && !(o.lmin > 0.0 && o.lmax > 0.0);
+    const bool tc = o.precision != CIQ_PREC_FP32 && tc_supported(o.precision, d) && tc_padded_t(T) > 0;
+    Plan<float> p = make_plan<float>(N, d, T, Q, o, prepass, tc, true);
+    p.pc_rank = rank;
+    p.nparts = p.nparts1 = (int)pc_row_tiles(p.Npad);
+    p.layout(nullptr);
+    return p.bytes;
 }
 
 size_t ciq_workspace_bytes(int64_t N, int d, int T, int Q, const ciq_options* opt) {

@@ -1,0 +1,492 @@
+// Pivoted-Cholesky preconditioner of msMINRES-CIQ (App. "Preconditioning
+// msMINRES-CIQ"): the factor, its orthonormal basis and the FP32 applications
+// of P^{+-1/2}.  See precond.cuh for the formulas.
+//
+//  * pc_cholesky_step: one greedy step of the partial pivoted Cholesky of
+//    K_XX (Harbrecht, Peters and Schneider 2012): the pivot's kernel column,
+//    minus the previous columns (FP64 dot), divided by the root of the
+//    pivot's residual diagonal; the residual diagonal (FP64) is updated and
+//    the next pivot (largest residual, first index on ties) is chosen by the
+//    last block to finish.  One launch per column.
+//  * gram_part / gram_reduce: G = L^T L in FP64 (exact FP32 products).
+//  * basis_from_factor: Qh = L W with W = U diag(s)^{-1/2} (FP64 accumulation).
+//  * pc_reduce / pc_coef: C = diag(g) Qh^T X, a 64 x 64 register-tiled product
+//    over row chunks (FP32 within a chunk, FP64 across chunks).
+//  * pc_expand: out = sigma^{+-1} X + Qh C over 128-row tiles, with the
+//    Lanczos epilogue (p = O - beta q_prev, FP64 q.p, p.p, q.q per tile) for
+//    the preconditioned MVM.
+#include <climits>
+
+#include <algorithm>
+
+#include "precond.cuh"
+
+namespace ciq {
+
+namespace {
+
+constexpr int kRedRT = 64;      // r (basis column) tile of the reduction
+constexpr int kRedTT = 64;      // t (right-hand side) tile
+constexpr int kRedSub = 32;     // rows per shared-memory stage
+constexpr int kRedLd = 68;      // padded row of the shared tiles (16-byte aligned)
+
+int64_t chunk_rows(int64_t Npad, int R, int T) {
+    // Enough row chunks for about two blocks per SM, each at least 256 rows.
+    const int64_t tiles = (int64_t)((R + kRedRT - 1) / kRedRT) * ((T + kRedTT - 1) / kRedTT);
+    int64_t ch = std::max<int64_t>(1, (296 + tiles - 1) / tiles);
+    ch = std::min<int64_t>(ch, std::max<int64_t>(1, Npad / 256));
+    return round_up((Npad + ch - 1) / ch, kRedSub);
+}
+
+// cpart[chunk][r][t] = sum over the chunk's rows of Qh[r][i] X[t][i].
+__global__ void __launch_bounds__(256) pc_reduce(PrecondState pc, const float* X, int64_t ldx, int T,
+                                                 int64_t rows_per_chunk, const int* stop) {
+    if (stop && *stop) return;
+    __shared__ __align__(16) float As[kRedSub][kRedLd];
+    __shared__ __align__(16) float Bs[kRedSub][kRedLd];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int r0 = blockIdx.x * kRedRT, t0 = blockIdx.y * kRedTT;
+    const int64_t i_begin = (int64_t)blockIdx.z * rows_per_chunk;
+    const int64_t i_end = min(i_begin + rows_per_chunk, pc.Npad);
+    float acc[4][4] = {};
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += kRedSub) {
+#pragma unroll
+        for (int m = 0; m < (kRedRT * kRedSub) / 256; ++m) {
+            const int e = tid + 256 * m;
+            const int ii = e & (kRedSub - 1), rr = e / kRedSub;
+            const int64_t i = i0 + ii;
+            const int r = r0 + rr, t = t0 + rr;
+            As[ii][rr] = (r < pc.rank && i < i_end) ? pc.Qh[(int64_t)r * pc.Npad + i] : 0.f;
+            Bs[ii][rr] = (t < T && i < pc.N) ? X[(int64_t)t * ldx + i] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int ii = 0; ii < kRedSub; ++ii) {
+            const float4 a = *reinterpret_cast<const float4*>(&As[ii][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[ii][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+    float* dst = pc.cpart + (int64_t)blockIdx.z * pc.rank * T;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = r0 + ty * 4 + u;
+        if (r >= pc.rank) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int t = t0 + tx * 4 + v;
+            if (t < T) dst[(int64_t)r * T + t] = acc[u][v];
+        }
+    }
+}
+
+// coef[r][t] = g[r] * sum over chunks (FP64, fixed order).
+__global__ void pc_coef(PrecondState pc, int T, int nchunks, bool inverse_root, const int* stop) {
+    if (stop && *stop) return;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)pc.rank * T) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += (double)pc.cpart[(int64_t)c * pc.rank * T + e];
+    const int r = (int)(e / T);
+    pc.coef[e] = (float)(s * (double)(inverse_root ? pc.gm[r] : pc.gp[r]));
+}
+
+// out[t][i] = alpha X[t][i] + sum_r Qh[r][i] coef[r][t] over a 128-row tile
+// and 64 columns; LANCZOS: p = out - beta_t qprev[t][i] with partial sums.
+template <bool LANCZOS>
+__global__ void __launch_bounds__(256) pc_expand(PrecondState pc, const float* X, int64_t ldx, int T, float alpha,
+                                                 float* out, int64_t ldo, const float* q, float* qprev,
+                                                 float* pout, const double* beta, double* partials,
+                                                 const int* stop) {
+    if (stop && *stop) return;
+    constexpr int RT = 32;
+    __shared__ __align__(16) float Qs[RT][128];
+    __shared__ __align__(16) float Cs[RT][64];
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * 128;
+    const int t0 = blockIdx.y * 64;
+    float acc[4][8] = {};
+    for (int r0 = 0; r0 < pc.rank; r0 += RT) {
+#pragma unroll
+        for (int m = 0; m < (RT * 128) / 256; ++m) {
+            const int e = tid + 256 * m;
+            const int ii = e & 127, rr = e >> 7;
+            const int r = r0 + rr;
+            Qs[rr][ii] = r < pc.rank ? pc.Qh[(int64_t)r * pc.Npad + i0 + ii] : 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < (RT * 64) / 256; ++m) {
+            const int e = tid + 256 * m;
+            const int tt = e & 63, rr = e >> 6;
+            const int r = r0 + rr, t = t0 + tt;
+            Cs[rr][tt] = (r < pc.rank && t < T) ? pc.coef[(int64_t)r * T + t] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < RT; ++rr) {
+            float qv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) qv[u] = Qs[rr][tx + 32 * u];
+            const float4 c0 = *reinterpret_cast<const float4*>(&Cs[rr][ty * 8]);
+            const float4 c1 = *reinterpret_cast<const float4*>(&Cs[rr][ty * 8 + 4]);
+            const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(qv[u], cv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const int t = t0 + ty * 8 + v;
+        if (t >= T) break;                       // warp-uniform: every lane has the same ty
+        double qp = 0.0, pp = 0.0, qq = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + tx + 32 * u;
+            const float x = i < pc.N ? X[(int64_t)t * ldx + i] : 0.f;
+            const float o = fmaf(alpha, x, acc[u][v]);
+            if (!LANCZOS) {
+                if (i < pc.N) out[(int64_t)t * ldo + i] = o;
+                else if (ldo >= pc.Npad) out[(int64_t)t * ldo + i] = 0.f;
+            } else {
+                const int64_t idx = (int64_t)t * pc.Npad + i;
+                const float p = i < pc.N ? o - (float)beta[t] * qprev[idx] : 0.f;
+                (pout ? pout : qprev)[idx] = p;
+                const double qd = (double)q[idx], pd = (double)p;
+                qp += qd * pd;
+                pp += pd * pd;
+                qq += qd * qd;
+            }
+        }
+        if (LANCZOS) {
+            qp = warp_sum(qp);
+            pp = warp_sum(pp);
+            qq = warp_sum(qq);
+            if (tx == 0) {
+                double* dst = partials + ((int64_t)blockIdx.x * T + t) * 3;
+                dst[0] = qp;
+                dst[1] = pp;
+                dst[2] = qq;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- setup ----
+struct CholWork {
+    int* ispiv;          // [Npad]
+    double* dmax;        // [rank + 1] residual diagonal of each pivot when chosen
+    double* bval;        // [blocks]
+    int* bidx;           // [blocks]
+    unsigned* counter;
+};
+
+CholWork chol_work(void* base, int64_t Npad) {
+    CholWork w;
+    char* p = static_cast<char*>(base);
+    const int64_t blocks = Npad / 256 + 1;
+    w.ispiv = reinterpret_cast<int*>(p);
+    p += round_up(Npad * sizeof(int), 256);
+    w.dmax = reinterpret_cast<double*>(p);
+    p += round_up((kPcMaxRank + 1) * sizeof(double), 256);
+    w.bval = reinterpret_cast<double*>(p);
+    p += round_up(blocks * sizeof(double), 256);
+    w.bidx = reinterpret_cast<int*>(p);
+    p += round_up(blocks * sizeof(int), 256);
+    w.counter = reinterpret_cast<unsigned*>(p);
+    return w;
+}
+
+__global__ void pc_cholesky_init(int64_t N, int64_t Npad, double s, double* dres, CholWork w, int* piv,
+                                 int* rank_out, int rank) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < Npad) {
+        dres[i] = i < N ? s : -1.0;
+        w.ispiv[i] = 0;
+    }
+    if (i == 0) {
+        piv[0] = 0;                   // every diagonal entry of K_XX is s: the first index wins
+        w.dmax[0] = s;
+        *w.counter = 0u;
+        *rank_out = rank;
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(256) pc_cholesky_step(const float* Xp, int64_t N, int64_t Npad, int dp, float s,
+                                                        int k, float* L, int* piv, double* dres, CholWork w,
+                                                        int* rank_out) {
+    __shared__ float Lp[kPcMaxRank];
+    __shared__ float xp[kMaxDimPad];
+    __shared__ double rv[8];
+    __shared__ int ri[8];
+    __shared__ bool last;
+    const double dpiv = w.dmax[k];
+    if (!(dpiv > 0.0)) {                       // residual exhausted: the factor has k columns
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicMin(rank_out, k);
+            w.dmax[k + 1] = 0.0;               // and every later step returns here too
+        }
+        return;
+    }
+    const int ip = piv[k];
+    const int tid = threadIdx.x;
+    for (int m = tid; m < k; m += 256) Lp[m] = L[(int64_t)m * Npad + ip];
+    if (tid < dp) xp[tid] = Xp[(int64_t)ip * dp + tid];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    double dnew = -1.0;
+    if (i < N) {
+        float r2 = 0.f;
+        for (int c = 0; c < dp; ++c) {
+            const float df = Xp[i * dp + c] - xp[c];
+            r2 = fmaf(df, df, r2);
+        }
+        double col = (double)kernel_value<KT>(r2, s);
+        for (int m = 0; m < k; ++m) col -= (double)L[(int64_t)m * Npad + i] * (double)Lp[m];
+        const bool was_pivot = w.ispiv[i] != 0;
+        if (was_pivot) col = 0.0;              // earlier pivot rows of the Schur complement are 0
+        const float l = (float)(col / sqrt(dpiv));
+        L[(int64_t)k * Npad + i] = l;
+        if (was_pivot || i == ip) {
+            dnew = 0.0;
+            if (i == ip) w.ispiv[i] = 1;
+        } else {
+            dnew = dres[i] - (double)l * (double)l;
+        }
+        dres[i] = dnew;
+    } else if (i < Npad) {
+        L[(int64_t)k * Npad + i] = 0.f;
+    }
+    // Block argmax (largest value, then smallest index).
+    double bv = dnew;
+    int bi = i < N ? (int)i : INT_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { rv[tid >> 5] = bv; ri[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+        bv = rv[0];
+        bi = ri[0];
+        for (int q = 1; q < 8; ++q)
+            if (rv[q] > bv || (rv[q] == bv && ri[q] < bi)) { bv = rv[q]; bi = ri[q]; }
+        w.bval[blockIdx.x] = bv;
+        w.bidx[blockIdx.x] = bi;
+        __threadfence();
+        last = atomicAdd(w.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // Last block: argmax over the blocks, the next pivot.
+    __threadfence();
+    bv = -2.0;
+    bi = INT_MAX;
+    for (int b = tid; b < (int)gridDim.x; b += 256) {
+        const double ov = ((volatile double*)w.bval)[b];
+        const int oi = ((volatile int*)w.bidx)[b];
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) { rv[tid >> 5] = bv; ri[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+        bv = rv[0];
+        bi = ri[0];
+        for (int q = 1; q < 8; ++q)
+            if (rv[q] > bv || (rv[q] == bv && ri[q] < bi)) { bv = rv[q]; bi = ri[q]; }
+        piv[k + 1] = bi == INT_MAX ? 0 : bi;
+        w.dmax[k + 1] = bv;
+        *w.counter = 0u;
+    }
+}
+
+// gpart[chunk][a][b] = sum over the chunk's rows of L[a][i] L[b][i] (32 x 32
+// tiles with a-tile <= b-tile).
+__global__ void __launch_bounds__(256) gram_part(const float* L, int64_t Npad, int R, int64_t rows_per_chunk,
+                                                 double* gpart) {
+    if (blockIdx.x > blockIdx.y) return;
+    __shared__ float As[64][33];
+    __shared__ float Bs[64][33];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int a0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    const int64_t i_begin = (int64_t)blockIdx.z * rows_per_chunk;
+    const int64_t i_end = min(i_begin + rows_per_chunk, Npad);
+    double acc[2][2] = {};
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += 64) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int ii = e & 63, cc = e >> 6;
+            const int64_t i = i0 + ii;
+            As[ii][cc] = (a0 + cc < R && i < i_end) ? L[(int64_t)(a0 + cc) * Npad + i] : 0.f;
+            Bs[ii][cc] = (b0 + cc < R && i < i_end) ? L[(int64_t)(b0 + cc) * Npad + i] : 0.f;
+        }
+        __syncthreads();
+        for (int ii = 0; ii < 64; ++ii) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v)
+                    acc[u][v] = fma((double)As[ii][ty * 2 + u], (double)Bs[ii][tx * 2 + v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int a = a0 + ty * 2 + u, b = b0 + tx * 2 + v;
+            if (a < R && b < R) gpart[((int64_t)blockIdx.z * R + a) * R + b] = acc[u][v];
+        }
+}
+
+__global__ void gram_reduce(const double* gpart, int R, int nchunks, double* G) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)R * R) return;
+    const int a = (int)(e / R), b = (int)(e % R);
+    if (a / 32 > b / 32) return;                 // written from the transposed entry
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += gpart[((int64_t)c * R + a) * R + b];
+    G[a + (int64_t)b * R] = s;
+    G[b + (int64_t)a * R] = s;
+}
+
+// Qh[c][i] = sum_m L[m][i] W[m][c], 32 columns per block, one row per thread.
+__global__ void __launch_bounds__(128) basis_from_factor(const float* L, int64_t Npad, int R, const double* W,
+                                                         int Rk, float* Qh) {
+    __shared__ double Ws[32][32];
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int c0 = blockIdx.y * 32;
+    double acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+    for (int m0 = 0; m0 < R; m0 += 32) {
+        for (int e = threadIdx.x; e < 32 * 32; e += 128) {
+            const int mm = e >> 5, cc = e & 31;
+            Ws[mm][cc] = (m0 + mm < R && c0 + cc < Rk) ? W[(m0 + mm) + (int64_t)(c0 + cc) * R] : 0.0;
+        }
+        __syncthreads();
+        const int mend = min(32, R - m0);
+        for (int mm = 0; mm < mend; ++mm) {
+            const double l = (double)L[(int64_t)(m0 + mm) * Npad + i];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = fma(l, Ws[mm][c], acc[c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        if (c0 + c < Rk) Qh[(int64_t)(c0 + c) * Npad + i] = (float)acc[c];
+}
+
+}  // namespace
+
+int64_t pc_chunks(int64_t Npad) {
+    // Worst case over rank and T (chunk_rows is at least kRedSub rows).
+    return (Npad + kRedSub - 1) / kRedSub;
+}
+
+size_t pc_scratch_floats(int64_t Npad, int rank, int T) {
+    const int64_t rows = chunk_rows(Npad, rank, T);
+    const int64_t nch = (Npad + rows - 1) / rows;
+    return (size_t)nch * rank * T + (size_t)rank * T;
+}
+
+cudaError_t launch_pc_apply(const PrecondState& pc, const float* X, int64_t ldx, int T, bool inverse_root,
+                            float* out, int64_t ldo, const int* stop, cudaStream_t st) {
+    if (pc.rank > 0) {
+        const int64_t rows = chunk_rows(pc.Npad, pc.rank, T);
+        const int nch = (int)((pc.Npad + rows - 1) / rows);
+        dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
+        pc_reduce<<<g1, 256, 0, st>>>(pc, X, ldx, T, rows, stop);
+        const int64_t n = (int64_t)pc.rank * T;
+        pc_coef<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pc, T, nch, inverse_root, stop);
+    }
+    dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
+    pc_expand<false><<<g2, 256, 0, st>>>(pc, X, ldx, T, inverse_root ? pc.inv_sigma : pc.sigma, out, ldo, nullptr,
+                                         nullptr, nullptr, nullptr, nullptr, stop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pc_lanczos(const PrecondState& pc, const float* Oraw, const float* q, float* qprev, float* pout,
+                              const double* beta, double* partials, int T, const int* stop, cudaStream_t st) {
+    if (pc.rank > 0) {
+        const int64_t rows = chunk_rows(pc.Npad, pc.rank, T);
+        const int nch = (int)((pc.Npad + rows - 1) / rows);
+        dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
+        pc_reduce<<<g1, 256, 0, st>>>(pc, Oraw, pc.Npad, T, rows, stop);
+        const int64_t n = (int64_t)pc.rank * T;
+        pc_coef<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pc, T, nch, true, stop);
+    }
+    dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
+    pc_expand<true><<<g2, 256, 0, st>>>(pc, Oraw, pc.Npad, T, pc.inv_sigma, nullptr, 0, q, qprev, pout, beta,
+                                        partials, stop);
+    return cudaGetLastError();
+}
+
+size_t pc_cholesky_work_bytes(int64_t Npad) {
+    const int64_t blocks = Npad / 256 + 1;
+    return round_up(Npad * sizeof(int), 256) + round_up((kPcMaxRank + 1) * sizeof(double), 256) +
+           round_up(blocks * sizeof(double), 256) + round_up(blocks * sizeof(int), 256) + 256;
+}
+
+cudaError_t launch_pivoted_cholesky(const float* Xp, int64_t N, int64_t Npad, int dp, int kt, float outputscale,
+                                    int rank, float* L, int* piv, double* dres, void* work, int* rank_out,
+                                    cudaStream_t st) {
+    if (rank < 1 || rank > kPcMaxRank) return cudaErrorInvalidValue;
+    CholWork w = chol_work(work, Npad);
+    cudaError_t e = cudaMemsetAsync(L, 0, sizeof(float) * (size_t)rank * Npad, st);
+    if (e != cudaSuccess) return e;
+    pc_cholesky_init<<<(unsigned)((Npad + 255) / 256), 256, 0, st>>>(N, Npad, (double)outputscale, dres, w, piv,
+                                                                      rank_out, rank);
+    const unsigned blocks = (unsigned)((Npad + 255) / 256);
+    for (int k = 0; k < rank; ++k) {
+        if (kt == CIQ_RBF)
+            pc_cholesky_step<CIQ_RBF><<<blocks, 256, 0, st>>>(Xp, N, Npad, dp, outputscale, k, L, piv, dres, w,
+                                                               rank_out);
+        else
+            pc_cholesky_step<CIQ_MATERN52><<<blocks, 256, 0, st>>>(Xp, N, Npad, dp, outputscale, k, L, piv, dres,
+                                                                    w, rank_out);
+    }
+    return cudaGetLastError();
+}
+
+int64_t pc_gram_scratch(int64_t Npad, int R) {
+    const int64_t rows = 4096;
+    const int64_t nch = (Npad + rows - 1) / rows;
+    return nch * R * R;
+}
+
+cudaError_t launch_gram(const float* L, int64_t Npad, int R, double* gpart, double* G, cudaStream_t st) {
+    const int64_t rows = 4096;
+    const int nch = (int)((Npad + rows - 1) / rows);
+    const int rt = (R + 31) / 32;
+    gram_part<<<dim3(rt, rt, nch), 256, 0, st>>>(L, Npad, R, rows, gpart);
+    const int64_t n = (int64_t)R * R;
+    gram_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gpart, R, nch, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_basis_from_factor(const float* L, int64_t Npad, int R, const double* W, int Rk, float* Qh,
+                                     cudaStream_t st) {
+    if (Rk < 1) return cudaSuccess;
+    basis_from_factor<<<dim3((unsigned)(Npad / 128), (Rk + 31) / 32), 128, 0, st>>>(L, Npad, R, W, Rk, Qh);
+    return cudaGetLastError();
+}
+
+}  // namespace ciq

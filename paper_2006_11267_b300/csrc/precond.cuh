@@ -1,0 +1,77 @@
+// Partial pivoted Cholesky preconditioner of msMINRES-CIQ (App.
+// "Preconditioning msMINRES-CIQ"): P = L L^T + sigma^2 I with L the rank-R
+// pivoted Cholesky factor of K_XX.
+//
+// The solve runs msMINRES on the preconditioned operator A = P^{-1/2} K P^{-1/2}
+// (whose shifted solves are P^{1/2} (K + t P)^{-1} P^{1/2}) and maps its result
+// back with P^{-1/2} (R' b, Eq. precond_sqrt_inverse) or P^{1/2} (R b,
+// Eq. precond_sqrt).  The roots of P come in closed form from the
+// eigendecomposition L^T L = U diag(s) U^T:
+//     Qh = L U diag(s)^{-1/2}      (orthonormal basis of range(L), N x R')
+//     P^{+-1/2} = sigma^{+-1} I + Qh diag(g^{+-}) Qh^T,
+//     g^- = (s + sigma^2)^{-1/2} - 1/sigma,  g^+ = (s + sigma^2)^{1/2} - sigma.
+// Both applications lose at most about sqrt(kappa(P)) digits to cancellation,
+// so they run in FP32; P^{-1} alone (the paper's matrix-inversion-lemma form)
+// cancels like kappa(P) and does not survive FP32 at sigma^2 = 1e-3.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace ciq {
+
+constexpr int kPcMaxRank = 1024;    // largest preconditioner rank
+
+struct PrecondState {
+    int64_t N = 0, Npad = 0;
+    int rank = 0;                   // R' kept directions (columns of Qh)
+    const float* Qh = nullptr;      // [R'][Npad], zero rows past N
+    const float* gm = nullptr;      // [R'] g^-
+    const float* gp = nullptr;      // [R'] g^+
+    float sigma = 0.f, inv_sigma = 0.f;
+    float* cpart = nullptr;         // [pc_chunks(Npad)][R'][T] partial sums of Qh^T X
+    float* coef = nullptr;          // [R'][T]
+    int T = 0;                      // columns the scratch is sized for
+};
+
+int64_t pc_chunks(int64_t Npad);
+size_t pc_scratch_floats(int64_t Npad, int rank, int T);
+
+// out = sigma^{e} X + Qh diag(g) Qh^T X with e = -1, g = g^- (inverse root)
+// or e = +1, g = g^+ (root).  X: T columns, leading dimension ldx, rows >=
+// N read as 0; out: leading dimension ldo, rows >= N written as 0 when
+// ldo >= Npad.  stop: skip when *stop != 0 (may be null).
+cudaError_t launch_pc_apply(const PrecondState& pc, const float* X, int64_t ldx, int T, bool inverse_root,
+                            float* out, int64_t ldo, const int* stop, cudaStream_t st);
+
+// Lanczos epilogue of the preconditioned MVM: with O' = K U (U = P^{-1/2} q),
+// O = P^{-1/2} O' and p = O - beta q_prev (0 on rows >= N) written to pout
+// (over qprev when null); per 128-row tile and column the FP64 sums (q.p,
+// p.p, q.q) go to partials[(tile * T + c) * 3 + k].
+cudaError_t launch_pc_lanczos(const PrecondState& pc, const float* Oraw, const float* q, float* qprev, float* pout,
+                              const double* beta, double* partials, int T, const int* stop, cudaStream_t st);
+
+// Rows of 128 of the epilogue's partial sums.
+inline int64_t pc_row_tiles(int64_t Npad) { return Npad / 128; }
+
+// ---- setup ----
+// Pivoted Cholesky of K_XX from the scaled points (Npad x dp, divided by the
+// lengthscale): L [rank][Npad] (column m contiguous), piv [rank] pivots,
+// dres [Npad] (FP64 scratch, left holding the residual diagonal), and
+// `work` of pc_cholesky_work_bytes(Npad) bytes.  *rank_out (device int) is
+// the number of columns formed (smaller when the residual diagonal vanishes).
+size_t pc_cholesky_work_bytes(int64_t Npad);
+cudaError_t launch_pivoted_cholesky(const float* Xp, int64_t N, int64_t Npad, int dp, int kt, float outputscale,
+                                    int rank, float* L, int* piv, double* dres, void* work, int* rank_out,
+                                    cudaStream_t st);
+
+// G = L^T L (FP64, R x R, column-major) from L [R][Npad]; gpart: scratch of
+// pc_gram_scratch(Npad, R) doubles.
+int64_t pc_gram_scratch(int64_t Npad, int R);
+cudaError_t launch_gram(const float* L, int64_t Npad, int R, double* gpart, double* G, cudaStream_t st);
+
+// Qh[c][i] = sum_m L[m][i] W[m][c] (FP64 accumulation, rounded once):
+// W is R x Rk column-major FP64 (device).
+cudaError_t launch_basis_from_factor(const float* L, int64_t Npad, int R, const double* W, int Rk, float* Qh,
+                                     cudaStream_t st);
+
+}  // namespace ciq

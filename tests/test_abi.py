@@ -164,3 +164,31 @@ def test_kernel_mvm_entry_points_reject_non_finite_hyperparameters(field, value)
     assert lib.ciq_kernel_mvm_noalloc(ptr, huge, 3, ctypes.byref(good), ptr, 1, ptr, None) == \
         _ciq.CIQ_ERR_SCRATCH_TOO_SMALL
     assert lib.ciq_kernel_mvm_noalloc(ptr, huge, 3, ctypes.byref(bad), ptr, 1, ptr, None) == _ciq.CIQ_ERR_ARG
+
+
+def test_precond_entry_points_validate_before_the_device():
+    X = np.zeros((10, 3), np.float32)
+    B = np.zeros((2, 10), np.float32)
+    k = P.Kernel("rbf", 0.5, 1.0, 1e-2)
+    cases = [
+        (dict(kernel=P.Kernel("rbf", 0.5, 1.0, 0.0), rank=4), _ciq.CIQ_ERR_ARG),   # sigma^2 = 0: P singular
+        (dict(kernel=k, rank=11), _ciq.CIQ_ERR_ARG),                               # rank > N
+        (dict(kernel=k, rank=0), _ciq.CIQ_ERR_ARG),
+        (dict(kernel=k, rank=1025), _ciq.CIQ_ERR_ARG),                             # rank > 1024
+        (dict(kernel=k, rank=4, L=np.zeros((4, 9), np.float32)), ValueError),      # ldl < N
+        (dict(kernel=k, rank=4, sqrt_form="mvm"), _ciq.CIQ_ERR_UNSUPPORTED),
+    ]
+    for kw, want in cases:
+        kernel = kw.pop("kernel")
+        if want is ValueError:
+            with pytest.raises(ValueError):
+                P.ciq_sqrt_precond(X, kernel, B, 8, 1e-4, **kw)
+            continue
+        with pytest.raises(P.CiqError) as e:
+            P.ciq_sqrt_precond(X, kernel, B, 8, 1e-4, **kw)
+        assert e.value.status == want, kw
+    with pytest.raises(P.CiqError) as e:
+        P.ciq_pivoted_cholesky(X, k, 11)
+    assert e.value.status == _ciq.CIQ_ERR_ARG
+    assert P.ciq_precond_workspace_bytes(1000, 3, 8, 8, 50) > P.ciq_workspace_bytes(1000, 3, 8, 8)
+    assert P.ciq_precond_workspace_bytes(1000, 3, 8, 8, 0) == 0
