@@ -87,12 +87,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--workload", default="thompson50k",
-                    choices=["thompson50k", "batched512", "precision200k", "learned", "stored", "spectrum", "vjp"],
+                    choices=["thompson50k", "batched512", "precision200k", "learned", "stored", "spectrum", "vjp",
+                             "precond"],
                     help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
                          "the 200,000-point Matern precision sweep; learned: train the bound predictor on "
                          "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones; "
                          "spectrum: K^{1/2}b error against Q on matrices with prescribed spectra; "
-                         "vjp: forward and backward pass of K^{-1/2}B on the 50,000-point problem")
+                         "vjp: forward and backward pass of K^{-1/2}B on the 50,000-point problem; "
+                         "precond: pivoted-Cholesky preconditioned roots of ranks 100-400 on the 50,000-point problem")
     ap.add_argument("--n", type=int, default=0, metavar="N",
                     help="run the headline solve on the first N points only (for profiling captures)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
@@ -1018,6 +1020,132 @@ def run_vjp(args):
     return 0
 
 
+PRECOND_RANKS = (100, 200, 400)
+PRECOND_CHECK_N = 8192
+
+
+def run_precond(args):
+    """Preconditioned msMINRES-CIQ (App. "Preconditioning msMINRES-CIQ",
+    Eq. precond_sqrt, Eq. precond_sqrt_inverse) on the 50,000-point RBF
+    workload, against the unpreconditioned solve: for K^{1/2}-like (R b,
+    R R^T = K) and K^{-1/2}-like (R' b, R' R'^T = K^{-1}) roots and pivoted
+    Cholesky ranks 100, 200 and 400, the iterations, the time of a whole call
+    (factor, eigendecomposition and basis included) and the RHS-solves/s at
+    the error bound 1e-3 in the space msMINRES runs in (that of
+    A = P^{-1/2} K P^{-1/2}).  CPU leg: the columns' relative error against
+    the exact rotated roots (FP64 eigendecompositions of P and of A) on the
+    workload's first PRECOND_CHECK_N points with the oracle's own factor, and
+    of the unpreconditioned solve against the principal roots."""
+    import torch
+
+    import paper_2006_11267_b300 as P
+
+    torch.cuda.set_device(0)
+    W = WORKLOAD
+    X = torch.from_numpy(ci.points(W.seed, W.n, W.d).astype(np.float32)).cuda()
+    B = torch.from_numpy(ci.rhs(W.seed, W.n, W.t).astype(np.float32)).cuda()
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    opts = dict(stop_rule="errbound", max_iter=MAX_ITER, lanczos_iters=LANCZOS_ITERS, precision=args.precision,
+                check_every=16)
+    reps = max(1, args.steps)
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    table = {}
+    for op in ("sqrt", "invsqrt"):
+        base = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
+        pre = P.ciq_sqrt_precond if op == "sqrt" else P.ciq_invsqrt_precond
+        ms, (_, inf) = timed(lambda: base(X, k, B, W.q, TOL, **opts))
+        rows = {"0": {"iters": inf["iters"], "ms": ms, "rhs_solves_per_s": W.t / (ms * 1e-3)}}
+        for r in PRECOND_RANKS:
+            ms, (_, inf) = timed(lambda: pre(X, k, B, W.q, TOL, rank=r, **opts))
+            _, pinf = pre(X, k, B, W.q, TOL, rank=r, profile=1, **opts)
+            mvm = pinf["t_mvm_ms"] / max(1, pinf["mvm_launches"])
+            setup = pinf["t_total_ms"] - pinf["t_mvm_ms"] - pinf["t_step_ms"] - pinf["t_prepass_ms"]
+            rows[str(r)] = {"iters": inf["iters"], "ms": ms, "rhs_solves_per_s": W.t / (ms * 1e-3),
+                            "speedup": rows["0"]["ms"] / ms, "lmax_used": inf["lmax_used"],
+                            "precond_rank": inf["precond_rank"], "ms_per_iteration": mvm,
+                            "prepass_ms": pinf["t_prepass_ms"], "setup_and_combine_ms": setup}
+        table[op] = rows
+    clocks = sampler.stop()
+    check = None
+    if not args.no_cpu_baseline:
+        check = precond_oracle_check(P, torch, opts)
+    best = max(PRECOND_RANKS, key=lambda r: table["sqrt"][str(r)]["rhs_solves_per_s"])
+    line = {"metric": "rotated K^{1/2}b (R b, R R^T = K) RHS-solves/s at A-space error bound 1e-3, pivoted-Cholesky "
+                      "preconditioner", "value": table["sqrt"][str(best)]["rhs_solves_per_s"], "unit": "RHS-solves/s",
+            "n_gpus": 1, "steps": reps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f"{args.precision}x2-split tiles, f32 vectors and P^(+-1/2), f64 scalars",
+            "data": "synthetic",
+            "config": {"workload": "precond_" + W.name, "N": W.n, "d": W.d, "kernel": W.kernel,
+                       "lengthscale": W.lengthscale, "noise": W.noise, "T": W.t, "Q": W.q, "tol": TOL,
+                       "stop_rule": "errbound (space of A)", "ranks": list(PRECOND_RANKS), "best_rank": best,
+                       "precision": args.precision},
+            "table": table, "oracle_check": check, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def precond_oracle_check(P, torch, opts):
+    """Per-column relative errors of the preconditioned roots on the first
+    PRECOND_CHECK_N points, with the oracle's pivoted Cholesky factor (FP64,
+    rounded to FP32) passed to the library, against the exact rotated roots
+    R b = K P^{-1/2} A^{-1/2} b and R' b = P^{-1/2} A^{-1/2} b; rank 0 is the
+    unpreconditioned solve against the principal roots."""
+    from oracle import eig, kernels
+    from oracle import precond as PC
+
+    W = WORKLOAD
+    n = PRECOND_CHECK_N
+    X, B = W.make(n)
+    X = X.astype(np.float32)
+    B = B.astype(np.float32)
+    X64, B64 = X.astype(np.float64), B.astype(np.float64)
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    Kxx = kernels.kernel_matrix(X64, X64, W.kernel, W.lengthscale, W.outputscale)
+    K = Kxx + W.noise * np.eye(n)
+    Xd, Bd = torch.from_numpy(X).cuda(), torch.from_numpy(B).cuda()
+
+    def errs(A, exact):
+        e = np.linalg.norm(A - exact, axis=1) / np.linalg.norm(exact, axis=1)
+        return {"max": float(e.max()), "median": float(np.median(e))}
+
+    res = {"n": n}
+    t0 = time.perf_counter()
+    row = {}
+    for op, base, f in (("sqrt", P.ciq_sqrt, eig.sqrt_apply), ("invsqrt", P.ciq_invsqrt, eig.invsqrt_apply)):
+        A, inf = base(Xd, k, Bd, W.q, TOL, **opts)
+        row[op] = dict(errs(A.cpu().numpy().astype(np.float64), f(K, B64.T).T), iters=inf["iters"])
+    res["0"] = row
+    for r in PRECOND_RANKS:
+        L, _ = PC.pivoted_cholesky(np.diag(Kxx), lambda i: Kxx[:, i], r)
+        L32 = L.astype(np.float32)
+        Pm = PC.Preconditioner(L32.astype(np.float64), W.noise).dense()
+        Rb, Rpb = PC.rotated_roots_exact(K, Pm, B64)
+        Ld = torch.from_numpy(np.ascontiguousarray(L32.T)).cuda()
+        row = {}
+        for op, fn, exact in (("sqrt", P.ciq_sqrt_precond, Rb), ("invsqrt", P.ciq_invsqrt_precond, Rpb)):
+            A, inf = fn(Xd, k, Bd, W.q, TOL, L=Ld, **opts)
+            row[op] = dict(errs(A.cpu().numpy().astype(np.float64), exact), iters=inf["iters"])
+        res[str(r)] = row
+    res["oracle"] = "O1 of the preconditioned problem: FP64 eigendecompositions of P and A (LAPACK dsyevd)"
+    res["oracle_seconds"] = time.perf_counter() - t0
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1034,6 +1162,8 @@ def main():
         return run_spectrum(args)
     if args.workload == "vjp":
         return run_vjp(args)
+    if args.workload == "precond":
+        return run_precond(args)
     return run_ours(args)
 
 
