@@ -407,12 +407,19 @@ ciq_status ciq_invsqrt_batched_learned(const ciq_problem* probs, int P, int Q, d
  * and lambda_max = lmax_margin times the largest Ritz value of a pre-pass on
  * A (or opt->lmin/lmax, opt->quad_w/quad_t for A), and returns
  *     ciq_invsqrt_precond:  out = R' B = P^{-1/2} A^{-1/2} B,  R' R'^T = K^{-1},
- *     ciq_sqrt_precond:     out = R  B = P^{1/2}  A^{1/2}  B,  R  R^T  = K,
+ *     ciq_sqrt_precond:     out = R  B = K R' B = P^{1/2} A^{1/2} B,  R R^T = K,
  * square roots of K^{-1} and K that equal the principal ones up to an
  * orthogonal rotation (Eq. precond_sqrt_inverse with P^{1/2} b as the start
  * vector; R = K P^{-1/2} A^{-1/2} of Eq. precond_sqrt).  Convergence follows
  * the conditioning of P^{-1}K instead of K.  The stop rules apply to the
- * estimate in the space of A (relative error of A^{+-1/2} b).  P^{+-1/2}
+ * estimate in the space of A (relative error of A^{+-1/2} b).  R b has two
+ * forms: opt->sqrt_form CIQ_SQRT_MVM is Eq. precond_sqrt as printed, K (R' b)
+ * with R' b's solve and stop rule and one more kernel MVM; CIQ_SQRT_IDENTITY
+ * (the default) maps A^{1/2} b = (sum w) b - sum_q w_q t_q (A + t_q)^{-1} b
+ * with P^{1/2} and needs fewer iterations, but its error in the space of K can
+ * be up to sqrt(kappa(P)) times the one the stop rule bounds (measured at
+ * N = 8192, sigma^2 = 1e-3: 2e-2 at tol 1e-3, against 2e-4 to 4e-4 for the
+ * MVM form at the same tol).  P^{+-1/2}
  * come in closed form from the eigendecomposition of L^T L (host, FP64): with
  * L^T L = U diag(s) U^T and Qh = L U diag(s)^{-1/2},
  * P^{+-1/2} = sigma^{+-1} I + Qh diag((s + sigma^2)^{+-1/2} - sigma^{+-1}) Qh^T,
@@ -422,8 +429,7 @@ ciq_status ciq_invsqrt_batched_learned(const ciq_problem* probs, int P, int Q, d
  * the residual diagonal vanishes) or the caller's N x rank factor, column m
  * at L + m * ldl (ldl >= N), host or device, used as given.  1 <= rank <=
  * min(N, 1024); sigma^2 (kern->noise) > 0.  Every other argument, option and
- * return code is that of ciq_sqrt / ciq_invsqrt; opt->sqrt_form CIQ_SQRT_MVM
- * gives CIQ_ERR_UNSUPPORTED.  The setup reads L^T L on the host, so these
+ * return code is that of ciq_sqrt / ciq_invsqrt.  The setup reads L^T L on the host, so these
  * calls synchronise the stream before the iterations as well.
  * info->precond_rank: the directions kept. */
 ciq_status ciq_sqrt_precond(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, const float* L,

@@ -36,8 +36,11 @@ silent:
     reading without a preconditioner), lambda_max = 1.05 theta_max of a
     preconditioned Lanczos pre-pass;
   * K^{1/2}: the identity form K (K + tP)^{-1} = I - t P (K + tP)^{-1}, i.e.
-    R b = (sum w) z - P sum_q w_q t_q x_q (no extra kernel MVM); the literal
-    K sum_q w_q x_q is sqrt_form="mvm";
+    R b = (sum w) z - P sum_q w_q t_q x_q (no extra kernel MVM), or
+    sqrt_form="mvm": Eq. precond_sqrt as printed, R b = K (R' b), where R' b
+    is solved and stopped exactly as for op="invsqrt" (the identity form's
+    error in the space of K can exceed the bound its stop rule uses by up to
+    sqrt(kappa(P)); the printed form's does not, at one more kernel MVM);
   * stopping: the rules of the unpreconditioned solve evaluated in the space
     msMINRES works in (that of A): |phibar_q| there is the P^{-1}-norm of the
     residual of (K + t_q P) x = z, the estimate's norm is its A-space norm
@@ -272,21 +275,23 @@ def ciq_precond_apply(mvm, pre: Preconditioner, B, Q, op, tol=0.0, max_iter=200,
             info.update(lmin=lmin, lmax=lmax)
         w, t = quad_nodes(lmin, lmax, Q)
     info.update(w=w, t=t)
-    coef = w if op == "invsqrt" else w * t
+    literal = op == "sqrt" and sqrt_form == "mvm"
+    solve_op = "invsqrt" if literal else op           # R b = K (R' b): R' b's solve and rule
+    coef = w if solve_op == "invsqrt" else w * t
     lmin_b = info.get("lmin") or 0.0
 
     def estimate(Xs):
-        if op == "invsqrt":
+        if solve_op == "invsqrt":
             return np.einsum("q,qic->ic", w, Xs)
         return w.sum() * Z - pre.matvec(np.einsum("q,qic->ic", w * t, Xs))
 
     def a_norm(E):
         # Norm in the space of A: R'b = P^{-1/2} a_A, R b = P^{1/2} a_A.
-        M = pre.matvec(E) if op == "invsqrt" else pre.solve(E)
+        M = pre.matvec(E) if solve_op == "invsqrt" else pre.solve(E)
         return np.sqrt(np.maximum(np.einsum("ic,ic->c", E, M), 0.0))
 
     sqrt_norm = None
-    if errbound_norm == "scalar" and op == "sqrt":
+    if errbound_norm == "scalar" and solve_op == "sqrt":
         # ||A^{1/2} b|| = sqrt(b^T A b) with P^{-1/2} b = P^{-1} z (one extra MVM
         # here; the device has it as ||b|| sqrt(alpha_1)).
         Y = pre.solve(Z)
@@ -299,20 +304,17 @@ def ciq_precond_apply(mvm, pre: Preconditioner, B, Q, op, tol=0.0, max_iter=200,
             beta1 = np.linalg.norm(Bc, axis=0)
             return np.max(np.abs(phibar), axis=0) <= tol * beta1
         bound = np.sum(coef[:, None] * np.abs(phibar) / (t[:, None] + lmin_b), axis=0)
-        if op == "sqrt" and sqrt_form == "mvm":
-            bound = bound * (info.get("lmax") or 1.0)
         if errbound_norm == "scalar":
-            den = sqrt_norm if op == "sqrt" else np.array(
+            den = sqrt_norm if solve_op == "sqrt" else np.array(
                 [gauss_invsqrt_norm(a, b) for a, b in zip(alphas, betas)])
             return bound <= tol * (1.0 - 2.0 * tol) * den
         return bound <= tol * a_norm(estimate(Xs))
 
     Xs, minfo = precond_msminres(mvm, pre.solve, Z, t, max_iter, stop)
     info.update(minfo)
-    if op == "sqrt" and sqrt_form == "mvm":
-        A = mvm(np.einsum("q,qic->ic", w, Xs))
-    else:
-        A = estimate(Xs)
+    A = estimate(Xs)
+    if literal:
+        A = mvm(A)
     info["errbound"] = np.sum(coef[:, None] * np.abs(minfo["phibar"]) / (t[:, None] + lmin_b), axis=0)
     return A.T, info
 

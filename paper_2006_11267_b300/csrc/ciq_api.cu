@@ -524,7 +524,6 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         if (fp64 || dense || vjp || pcs->rank < 1 || pcs->rank > kPcMaxRank || pcs->rank > N ||
             (pcs->L && pcs->ldl < N) || !kern || !(kern->noise > 0.0))
             return CIQ_ERR_ARG;
-        if (opt && opt->sqrt_form == CIQ_SQRT_MVM) return CIQ_ERR_UNSUPPORTED;
     }
     if ((!dense && !X) || !B || !out || N < 1 || d < 1 || d > CIQ_MAX_DIM || T < 1 || Q < 1 || Q > CIQ_MAX_Q ||
         !(tol >= 0.0) || !valid_kernel(kern) || (dense && (ldk < N || fp64)))
@@ -552,6 +551,10 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         tc = true;
     }
     if (op == kOpSqrtIdentity && o.sqrt_form == CIQ_SQRT_MVM) op = kOpSqrtMvm;
+    // Preconditioned literal form R b = K (R' b) (Eq. precond_sqrt as printed):
+    // the solve, its stop rule and its combine are those of R' b.
+    const bool pc_literal = pcs && op == kOpSqrtMvm;
+    if (pc_literal) op = kOpInvSqrt;
     const bool given_nodes = o.quad_w != nullptr;
     const bool given_bounds = !given_nodes && o.lmin > 0.0 && o.lmax > 0.0;
     if (given_bounds && !(o.lmax >= o.lmin)) return CIQ_ERR_ARG;
@@ -798,7 +801,20 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         }
         if constexpr (sizeof(R) == 4) {
             if (pc_on) {
-                CIQ_TRY(launch_pc_apply(pcst, p.Apre, N, T, op == kOpInvSqrt, outd, N, nullptr, st));
+                if (pc_literal) {
+                    // R' b into the MVM's input buffer, then R b = K (R' b).
+                    CIQ_TRY(launch_pc_apply(pcst, p.Apre, N, T, true, p.Up, p.Npad, nullptr, st));
+                    MvmArgs<R> m = mvm_args(p, *kern);
+                    m.T = T;
+                    m.mode = kPlain;
+                    m.V = p.Up;
+                    m.out = outd;
+                    m.ldo = N;
+                    CIQ_TRY(launch_mvm(p, m, false, st));
+                    launches += mvm_launches + 1;
+                } else {
+                    CIQ_TRY(launch_pc_apply(pcst, p.Apre, N, T, op == kOpInvSqrt, outd, N, nullptr, st));
+                }
                 launches += pcst.rank > 0 ? 3 : 1;
             }
         }

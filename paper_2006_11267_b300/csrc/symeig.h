@@ -125,30 +125,52 @@ inline bool eigh(int n, double* A, double* w, double* Z) {
             rots.push_back({k, c, s});
         }
     }
+    // Row-major copy: a row of Z stays in cache while the whole rotation
+    // sequence passes over it, four rows at a time.
+    std::vector<double> Zr((size_t)n * n);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) Zr[(size_t)i * n + j] = z(i, j);
     auto apply_rows = [&](int r0, int r1) {
-        for (const Rot& g : rots) {
-            double* zk = Z + (size_t)g.k * n;
-            double* zk1 = zk + n;
-            for (int i = r0; i < r1; ++i) {
-                const double t1 = zk[i], t2 = zk1[i];
-                zk[i] = g.c * t1 - g.s * t2;
-                zk1[i] = g.s * t1 + g.c * t2;
+        int i = r0;
+        for (; i + 4 <= r1; i += 4) {
+            double* z0 = &Zr[(size_t)i * n];
+            double* z1 = z0 + n;
+            double* z2 = z1 + n;
+            double* z3 = z2 + n;
+            for (const Rot& g : rots) {
+                const int k = g.k;
+                const double a0 = z0[k], b0 = z0[k + 1], a1 = z1[k], b1 = z1[k + 1];
+                const double a2 = z2[k], b2 = z2[k + 1], a3 = z3[k], b3 = z3[k + 1];
+                z0[k] = g.c * a0 - g.s * b0; z0[k + 1] = g.s * a0 + g.c * b0;
+                z1[k] = g.c * a1 - g.s * b1; z1[k + 1] = g.s * a1 + g.c * b1;
+                z2[k] = g.c * a2 - g.s * b2; z2[k + 1] = g.s * a2 + g.c * b2;
+                z3[k] = g.c * a3 - g.s * b3; z3[k + 1] = g.s * a3 + g.c * b3;
+            }
+        }
+        for (; i < r1; ++i) {
+            double* z0 = &Zr[(size_t)i * n];
+            for (const Rot& g : rots) {
+                const double a0 = z0[g.k], b0 = z0[g.k + 1];
+                z0[g.k] = g.c * a0 - g.s * b0;
+                z0[g.k + 1] = g.s * a0 + g.c * b0;
             }
         }
     };
     const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const int nth = n >= 128 ? std::min(hw, n / 32) : 1;
+    const int nth = n >= 128 ? std::min(hw, n / 16) : 1;
     if (nth <= 1) {
         apply_rows(0, n);
     } else {
         std::vector<std::thread> pool;
-        const int per = (n + nth - 1) / nth;
+        const int per = ((n + nth - 1) / nth + 3) / 4 * 4;
         for (int t = 0; t < nth; ++t) {
             const int r0 = t * per, r1 = std::min(n, r0 + per);
             if (r0 < r1) pool.emplace_back(apply_rows, r0, r1);
         }
         for (auto& th : pool) th.join();
     }
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) z(i, j) = Zr[(size_t)i * n + j];
     // Ascending order (selection sort of the pairs; n is small).
     for (int i = 0; i < n; ++i) w[i] = d[i];
     for (int i = 0; i < n; ++i) {

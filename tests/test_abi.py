@@ -176,7 +176,6 @@ def test_precond_entry_points_validate_before_the_device():
         (dict(kernel=k, rank=0), _ciq.CIQ_ERR_ARG),
         (dict(kernel=k, rank=1025), _ciq.CIQ_ERR_ARG),                             # rank > 1024
         (dict(kernel=k, rank=4, L=np.zeros((4, 9), np.float32)), ValueError),      # ldl < N
-        (dict(kernel=k, rank=4, sqrt_form="mvm"), _ciq.CIQ_ERR_UNSUPPORTED),
     ]
     for kw, want in cases:
         kernel = kw.pop("kernel")

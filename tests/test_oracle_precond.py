@@ -173,3 +173,22 @@ def test_preconditioned_ciq_sqrt_forms_and_scalar_stop_rule(op):
         A4, _ = PC.ciq_precond_apply(lambda V: K @ V, pre, B, 12, op, tol=0.0, max_iter=300,
                                      start=ci.start_vector(3, n))
         assert (np.linalg.norm(A3 - A4, axis=1) / np.linalg.norm(A4, axis=1)).max() < 1e-6
+
+
+def test_literal_sqrt_form_is_accurate_in_the_space_of_K():
+    # Eq. precond_sqrt as printed, R b = K (R' b) with R' b's solve and stop
+    # rule, against the identity form whose error in the space of K can exceed
+    # the bound its A-space stop rule uses (kernel matrix with sigma^2 = 1e-3).
+    X = ci.points(13, 600, 4)
+    Kxx = kernels.kernel_matrix(X, X, "rbf", 0.3, 1.0)
+    K = Kxx + 1e-3 * np.eye(600)
+    pre, _ = _pre(Kxx, 1e-3, 30)
+    B = ci.rhs(14, 600, 4)
+    Rb, _ = PC.rotated_roots_exact(K, pre.dense(), B)
+    kw = dict(tol=1e-3, max_iter=3000, stop_rule="errbound", start=ci.start_vector(5, 600))
+    A_lit, i_lit = PC.ciq_precond_apply(lambda V: K @ V, pre, B, 12, "sqrt", sqrt_form="mvm", **kw)
+    A_id, i_id = PC.ciq_precond_apply(lambda V: K @ V, pre, B, 12, "sqrt", **kw)
+    e_lit = (np.linalg.norm(A_lit - Rb, axis=1) / np.linalg.norm(Rb, axis=1)).max()
+    e_id = (np.linalg.norm(A_id - Rb, axis=1) / np.linalg.norm(Rb, axis=1)).max()
+    assert e_lit < 1e-3 < e_id, (e_lit, e_id)
+    assert i_lit["iters"].max() > i_id["iters"].max()
