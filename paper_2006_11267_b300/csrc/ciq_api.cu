@@ -328,7 +328,10 @@ cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns,
 template <typename R>
 cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<R>& a, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        cudaError_t e = launch_pc_apply(pc, a.V, p.Npad, a.T, true, p.Up, p.Npad, a.stop, st);
+        // On tensor cores the operand scales of U come from the reduction of
+        // P^{-1/2} (the columns of q have norm 1), so the MVM skips its own pass.
+        cudaError_t e = launch_pc_apply(pc, a.V, p.Npad, a.T, true, p.Up, p.Npad, a.stop, st,
+                                        p.tc ? p.tcp.vscale : nullptr, p.tc ? p.tcp.TP : 0);
         if (e != cudaSuccess) return e;
         MvmArgs<R> m = a;
         m.mode = kPlain;
@@ -337,7 +340,7 @@ cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<
         m.ldo = p.Npad;
         m.lz_q = nullptr;
         m.lz_sco = nullptr;
-        e = launch_mvm(p, m, false, st, false);
+        e = launch_mvm(p, m, p.tc, st, p.tc);
         if (e != cudaSuccess) return e;
         return launch_pc_lanczos(pc, p.Op, a.V, a.qprev, a.pout, a.beta, a.partials, a.T, a.stop, st);
     }

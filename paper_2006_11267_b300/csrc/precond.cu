@@ -31,17 +31,19 @@ constexpr int kRedSub = 32;     // rows per shared-memory stage
 constexpr int kRedLd = 68;      // padded row of the shared tiles (16-byte aligned)
 
 int64_t chunk_rows(int64_t Npad, int R, int T) {
-    // Enough row chunks for about two blocks per SM, each at least 256 rows.
+    // Row chunks for one wave of three blocks per SM (148 SMs), each chunk at
+    // least 256 rows.
     const int64_t tiles = (int64_t)((R + kRedRT - 1) / kRedRT) * ((T + kRedTT - 1) / kRedTT);
-    int64_t ch = std::max<int64_t>(1, (296 + tiles - 1) / tiles);
+    int64_t ch = std::max<int64_t>(1, 444 / tiles);
     ch = std::min<int64_t>(ch, std::max<int64_t>(1, Npad / 256));
     return round_up((Npad + ch - 1) / ch, kRedSub);
 }
 
 // cpart[chunk][r][t] = sum over the chunk's rows of Qh[r][i] X[t][i].
-__global__ void __launch_bounds__(256) pc_reduce(PrecondState pc, const float* X, int64_t ldx, int T,
-                                                 int64_t rows_per_chunk, const int* stop) {
+__global__ void __launch_bounds__(256, 3) pc_reduce(PrecondState pc, const float* X, int64_t ldx, int T,
+                                                    int64_t rows_per_chunk, const int* stop) {
     if (stop && *stop) return;
+    constexpr int M = (kRedRT * kRedSub) / 256;           // elements per thread and stage, per operand
     __shared__ __align__(16) float As[kRedSub][kRedLd];
     __shared__ __align__(16) float Bs[kRedSub][kRedLd];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -49,17 +51,30 @@ __global__ void __launch_bounds__(256) pc_reduce(PrecondState pc, const float* X
     const int64_t i_begin = (int64_t)blockIdx.z * rows_per_chunk;
     const int64_t i_end = min(i_begin + rows_per_chunk, pc.Npad);
     float acc[4][4] = {};
-    for (int64_t i0 = i_begin; i0 < i_end; i0 += kRedSub) {
+    // Stage s + 1 is loaded into registers while stage s is multiplied.
+    float na[M], nb[M];
+    auto load = [&](int64_t i0) {
 #pragma unroll
-        for (int m = 0; m < (kRedRT * kRedSub) / 256; ++m) {
+        for (int m = 0; m < M; ++m) {
             const int e = tid + 256 * m;
             const int ii = e & (kRedSub - 1), rr = e / kRedSub;
             const int64_t i = i0 + ii;
             const int r = r0 + rr, t = t0 + rr;
-            As[ii][rr] = (r < pc.rank && i < i_end) ? pc.Qh[(int64_t)r * pc.Npad + i] : 0.f;
-            Bs[ii][rr] = (t < T && i < pc.N) ? X[(int64_t)t * ldx + i] : 0.f;
+            na[m] = (r < pc.rank && i < i_end) ? pc.Qh[(int64_t)r * pc.Npad + i] : 0.f;
+            nb[m] = (t < T && i < pc.N) ? X[(int64_t)t * ldx + i] : 0.f;
+        }
+    };
+    if (i_begin < i_end) load(i_begin);
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += kRedSub) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int e = tid + 256 * m;
+            const int ii = e & (kRedSub - 1), rr = e / kRedSub;
+            As[ii][rr] = na[m];
+            Bs[ii][rr] = nb[m];
         }
         __syncthreads();
+        if (i0 + kRedSub < i_end) load(i0 + kRedSub);
 #pragma unroll 8
         for (int ii = 0; ii < kRedSub; ++ii) {
             const float4 a = *reinterpret_cast<const float4*>(&As[ii][ty * 4]);
@@ -85,21 +100,54 @@ __global__ void __launch_bounds__(256) pc_reduce(PrecondState pc, const float* X
     }
 }
 
-// coef[r][t] = g[r] * sum over chunks (FP64, fixed order).
-__global__ void pc_coef(PrecondState pc, int T, int nchunks, bool inverse_root, const int* stop) {
+// coef[r][t] = g[r] * sum over chunks (FP64, fixed order); one block per
+// column t.  vscale (optional, inverse root of a unit column v only): the
+// power-of-two operand scale the tensor-core MVM takes for U = P^{-1/2} v,
+// from ||U||^2 = sigma^{-2} + sum_r (g_r^2 + 2 g_r / sigma) (Qh^T v)_r^2 (the
+// formula of its own scale kernel, without another pass over U); columns
+// [T, TP) get the scale of a unit column.
+__global__ void __launch_bounds__(256) pc_coef(PrecondState pc, int T, int nchunks, bool inverse_root,
+                                               float* vscale, int TP, const int* stop) {
     if (stop && *stop) return;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)pc.rank * T) return;
-    double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += (double)pc.cpart[(int64_t)c * pc.rank * T + e];
-    const int r = (int)(e / T);
-    pc.coef[e] = (float)(s * (double)(inverse_root ? pc.gm[r] : pc.gp[r]));
+    const int t = blockIdx.x;
+    double nrm2 = 0.0;
+    const double is = 1.0 / (double)pc.sigma;
+    for (int r = threadIdx.x; r < pc.rank; r += blockDim.x) {
+        const int64_t e = (int64_t)r * T + t;
+        double s = 0.0;
+        for (int c = 0; c < nchunks; ++c) s += (double)pc.cpart[(int64_t)c * pc.rank * T + e];
+        const double g = (double)(inverse_root ? pc.gm[r] : pc.gp[r]);
+        pc.coef[e] = (float)(s * g);
+        nrm2 += (g * g + 2.0 * g * is) * s * s;
+    }
+    if (!vscale) return;
+    __shared__ double red[8];
+    nrm2 = warp_sum(nrm2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = is * is;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        const double nrm = sqrt(fmax(s, 0.0));
+        vscale[t] = nrm > 0.0 ? ldexpf(1.f, (int)floor(log2(sqrt((double)pc.N) / nrm))) : 1.f;
+        if (t == 0)
+            for (int c = T; c < TP; ++c) vscale[c] = ldexpf(1.f, (int)floor(0.5 * log2((double)pc.N)));
+    }
+}
+
+// The operand scale of U = v / sigma when P has no low-rank part.
+__global__ void pc_unit_scale(PrecondState pc, int T, int TP, float* vscale, const int* stop) {
+    if (stop && *stop) return;
+    for (int c = threadIdx.x; c < TP; c += blockDim.x) {
+        const double nrm = c < T ? 1.0 / (double)pc.sigma : 1.0;
+        vscale[c] = ldexpf(1.f, (int)floor(log2(sqrt((double)pc.N) / nrm)));
+    }
 }
 
 // out[t][i] = alpha X[t][i] + sum_r Qh[r][i] coef[r][t] over a 128-row tile
 // and 64 columns; LANCZOS: p = out - beta_t qprev[t][i] with partial sums.
 template <bool LANCZOS>
-__global__ void __launch_bounds__(256) pc_expand(PrecondState pc, const float* X, int64_t ldx, int T, float alpha,
+__global__ void __launch_bounds__(256, 3) pc_expand(PrecondState pc, const float* X, int64_t ldx, int T, float alpha,
                                                  float* out, int64_t ldo, const float* q, float* qprev,
                                                  float* pout, const double* beta, double* partials,
                                                  const int* stop) {
@@ -408,14 +456,15 @@ size_t pc_scratch_floats(int64_t Npad, int rank, int T) {
 }
 
 cudaError_t launch_pc_apply(const PrecondState& pc, const float* X, int64_t ldx, int T, bool inverse_root,
-                            float* out, int64_t ldo, const int* stop, cudaStream_t st) {
+                            float* out, int64_t ldo, const int* stop, cudaStream_t st, float* vscale, int TP) {
     if (pc.rank > 0) {
         const int64_t rows = chunk_rows(pc.Npad, pc.rank, T);
         const int nch = (int)((pc.Npad + rows - 1) / rows);
         dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
         pc_reduce<<<g1, 256, 0, st>>>(pc, X, ldx, T, rows, stop);
-        const int64_t n = (int64_t)pc.rank * T;
-        pc_coef<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pc, T, nch, inverse_root, stop);
+        pc_coef<<<T, 256, 0, st>>>(pc, T, nch, inverse_root, vscale, TP, stop);
+    } else if (vscale) {
+        pc_unit_scale<<<1, 256, 0, st>>>(pc, T, TP, vscale, stop);
     }
     dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
     pc_expand<false><<<g2, 256, 0, st>>>(pc, X, ldx, T, inverse_root ? pc.inv_sigma : pc.sigma, out, ldo, nullptr,
@@ -430,8 +479,7 @@ cudaError_t launch_pc_lanczos(const PrecondState& pc, const float* Oraw, const f
         const int nch = (int)((pc.Npad + rows - 1) / rows);
         dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
         pc_reduce<<<g1, 256, 0, st>>>(pc, Oraw, pc.Npad, T, rows, stop);
-        const int64_t n = (int64_t)pc.rank * T;
-        pc_coef<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pc, T, nch, true, stop);
+        pc_coef<<<T, 256, 0, st>>>(pc, T, nch, true, nullptr, 0, stop);
     }
     dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
     pc_expand<true><<<g2, 256, 0, st>>>(pc, Oraw, pc.Npad, T, pc.inv_sigma, nullptr, 0, q, qprev, pout, beta,

@@ -40,8 +40,11 @@ size_t pc_scratch_floats(int64_t Npad, int rank, int T);
 // or e = +1, g = g^+ (root).  X: T columns, leading dimension ldx, rows >=
 // N read as 0; out: leading dimension ldo, rows >= N written as 0 when
 // ldo >= Npad.  stop: skip when *stop != 0 (may be null).
+// vscale (optional, with inverse_root and unit columns X): also write the
+// tensor-core MVM's power-of-two operand scales of out for TP columns.
 cudaError_t launch_pc_apply(const PrecondState& pc, const float* X, int64_t ldx, int T, bool inverse_root,
-                            float* out, int64_t ldo, const int* stop, cudaStream_t st);
+                            float* out, int64_t ldo, const int* stop, cudaStream_t st, float* vscale = nullptr,
+                            int TP = 0);
 
 // Lanczos epilogue of the preconditioned MVM: with O' = K U (U = P^{-1/2} q),
 // O = P^{-1/2} O' and p = O - beta q_prev (0 on rows >= N) written to pout
