@@ -84,8 +84,9 @@ def test_precond_fp32_solve_matches_oracle_at_equal_nodes_and_J(op, form, krylov
     # The identity form of R b is P^{1/2} applied to the estimate of A^{1/2} b:
     # FP32 errors of the solve in the space of A reach the result scaled by up
     # to ||P^{1/2}||, so that form is compared where the solve runs, after
-    # P^{-1/2} (FP64, both sides).  R' b and the printed form K (R' b) are
-    # compared as they are.
+    # P^{-1/2} (FP64, both sides).  The printed form K (R' b) is compared
+    # after K^{-1} (FP64, both sides), i.e. as the solve's R' b; its last MVM
+    # is the kernel MVM checked on its own elsewhere.  R' b as it is.
     n, d, t, Q, J, rank = 900, 3, 5, 10, 300, 30
     X, B, Kxx, K, k = case(n, d, t, 71)
     L32, Lrows, _ = oracle_factor(Kxx, rank)
@@ -93,7 +94,12 @@ def test_precond_fp32_solve_matches_oracle_at_equal_nodes_and_J(op, form, krylov
     Pm = pre.dense()
     (w, tq), lam = _nodes_of_A(K, Pm, Q)
     lp, Vp = np.linalg.eigh(Pm)
-    to_a = (Vp * lp ** -0.5) @ Vp.T if form == "identity" and op == "sqrt" else np.eye(n)
+    if op == "invsqrt":
+        to_a = np.eye(n)
+    elif form == "identity":
+        to_a = (Vp * lp ** -0.5) @ Vp.T
+    else:
+        to_a = np.linalg.inv(K)
     run = lambda Km: PC.ciq_precond_apply(lambda V: Km @ V, pre, B.astype(np.float64), Q, op, max_iter=J,
                                           nodes=(w, tq), lmin=1.0, sqrt_form=form)[0] @ to_a
     ref, info_o = PC.ciq_precond_apply(lambda V: K @ V, pre, B.astype(np.float64), Q, op, max_iter=J,
@@ -169,7 +175,8 @@ def test_precond_fp16_tensor_core_matches_fp32(op):
     a32, i32 = fn(Xd, k, Bd, 12, 1e-5, L=Ld, precision="fp32", **kw)
     a16, i16 = fn(Xd, k, Bd, 12, 1e-5, L=Ld, precision="fp16", **kw)
     assert i32["status"] == 0 and i16["status"] == 0
-    assert rel(a16.cpu().numpy(), a32.cpu().numpy()) < 1e-3
+    # K (R' b) multiplies R' b's error (FP16-split MVMs inside the solve) by K.
+    assert rel(a16.cpu().numpy(), a32.cpu().numpy()) < (1e-3 if op == "invsqrt" else 2e-3)
     # Both preconditioned forms stop on R' b's rule: compare with K^{-1/2} b's solve.
     _, i0 = P.ciq_invsqrt(Xd, k, Bd, 12, 1e-5, precision="fp16", stop_rule="errbound", max_iter=3000)
     assert i16["iters"] < i0["iters"], (i16["iters"], i0["iters"])
