@@ -56,6 +56,7 @@ typedef struct CUstream_st* ciq_stream_t;
 #define CIQ_MAX_DIM 16        /* largest point dimension d */
 #define CIQ_MAX_Q 32          /* largest number of quadrature points Q */
 #define CIQ_MAX_BATCH 65536   /* largest number of problems of one batched call */
+#define CIQ_MAX_TRAIN 2048    /* largest training set of ciq_posterior_sample */
 
 typedef enum {
     CIQ_OK = 0,
@@ -448,6 +449,34 @@ ciq_status ciq_invsqrt_precond(const float* X, int64_t N, int d, const ciq_kerne
  * products with earlier columns in FP64.  Synchronous. */
 ciq_status ciq_pivoted_cholesky(const float* X, int64_t N, int d, const ciq_kernel* kern, int rank, float* L,
                                 int64_t ldl, int64_t* piv, int* rank_out, ciq_stream_t stream);
+
+/* Posterior Thompson draws (Sec. 5 "Posterior Sampling for Bayesian
+ * Optimization", Eq. thompson_sample): out = mu* + COV*^{1/2} eps at the
+ * candidate set Xc (Nc points) given training points Xtr (n points, values
+ * y), where
+ *     mu*  = m + K*X (K_XX + sigma^2 I)^{-1} (y - m),
+ *     COV* = K** - K*X (K_XX + sigma^2 I)^{-1} K_X* + jitter I,
+ * for the kernel_type (ciq_kernel_type) with ARD lengthscales
+ * (lengthscales[0..d-1], host doubles: coordinate c is divided by
+ * lengthscales[c]), outputscale s, noise sigma^2 >= 0 on the training
+ * diagonal, jitter > 0 on the candidate diagonal (the paper adds 1e-4) and
+ * constant mean m.  COV*^{1/2} is the principal root, by msMINRES-CIQ on COV*
+ * (Algorithm "ciq" as in ciq_sqrt, same options, nodes and stop rules; the
+ * pre-pass bounds use lambda_min = jitter, a lower bound since
+ * K** - K*X M^{-1} K_X* is positive semidefinite).  Every MVM is
+ * (K** + jitter I) V on the candidates (on the fly, the opt->precision path)
+ * minus C (C^T V) with C = K*X W, W = U diag(lambda^{-1/2}) from the
+ * eigendecomposition M = U diag(lambda) U^T of M = K_XX + sigma^2 I (FP64 on the
+ * host, directions with lambda <= 1e-13 max(lambda) dropped) and K*X in FP64;
+ * C is kept in FP32 (n x round_up(Nc, 128) floats).  Layouts: Xtr n x d,
+ * Xc Nc x d row-major; y n floats; eps, out Nc x T as B and out of ciq_sqrt.
+ * Host or device pointers.  0 <= n <= CIQ_MAX_TRAIN (n = 0: prior draws,
+ * mu* = m); the setup costs O(n^3) on the host and O(n^2 Nc) FP64 on the device.
+ * Returns the codes of ciq_sqrt; synchronous. */
+ciq_status ciq_posterior_sample(const float* Xtr, int64_t n, const float* y, const float* Xc, int64_t Nc, int d,
+                                int kernel_type, const double* lengthscales, double outputscale, double noise,
+                                double jitter, double mean, const float* eps, int T, int Q, double tol,
+                                const ciq_options* opt, float* out, ciq_info* info, ciq_stream_t stream);
 
 /* Device workspace bytes a preconditioned solve of this rank needs (for
  * opt->workspace). */

@@ -10,4 +10,5 @@ from ._ciq import (CiqError, Kernel, ciq_invsqrt, ciq_invsqrt_batched, ciq_invsq
                    ciq_sqrt_dense, ciq_invsqrt_dense, ciq_sqrt_vjp, ciq_invsqrt_vjp,
                    ciq_sqrt_batched_learned, ciq_invsqrt_batched_learned, ciq_mlp_features, ciq_mlp_normaliser,
                    ciq_mlp_init, ciq_mlp_loss_grad, ciq_mlp_train, ciq_mlp_predict, CIQ_MLP_PARAMS,
-                   ciq_sqrt_precond, ciq_invsqrt_precond, ciq_pivoted_cholesky, ciq_precond_workspace_bytes)
+                   ciq_sqrt_precond, ciq_invsqrt_precond, ciq_pivoted_cholesky, ciq_precond_workspace_bytes,
+                   ciq_posterior_sample)

@@ -129,6 +129,7 @@ def lib() -> ctypes.CDLL:
         "ciq_invsqrt_precond": (I, [P, I64, I, KP, I, P, I64, P, I, I, D, OP, P, IP, P]),
         "ciq_pivoted_cholesky": (I, [P, I64, I, KP, I, P, I64, P, ctypes.POINTER(I), P]),
         "ciq_precond_workspace_bytes": (S, [I64, I, I, I, I, OP]),
+        "ciq_posterior_sample": (I, [P, I64, P, P, I64, I, I, DP, D, D, D, D, P, I, I, D, OP, P, IP, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -386,6 +387,29 @@ def ciq_pivoted_cholesky(X, kernel, rank):
                                     ctypes.byref(got), _stream(X, L, piv))
     _check(st, "ciq_pivoted_cholesky", allow=(CIQ_OK,))
     return L, piv, got.value
+
+
+def ciq_posterior_sample(Xtr, y, Xc, kind, lengthscales, outputscale, noise, jitter, mean, eps, Q, tol=0.0,
+                         out=None, **opts):
+    """Posterior draws mu* + COV*^{1/2} eps at the candidates Xc (Nc, d) given
+    training data Xtr (n, d), y (n,); eps and out are (T, Nc).  ARD
+    lengthscales (d values). Returns (out, info)."""
+    Nc, d = Xc.shape
+    n = 0 if Xtr is None else Xtr.shape[0]
+    T = eps.shape[0]
+    if eps.shape[1] != Nc:
+        raise ValueError("eps must have shape (T, Nc)")
+    ls = np.ascontiguousarray(np.broadcast_to(np.asarray(lengthscales, dtype=np.float64), (d,)))
+    if out is None:
+        out = _empty_like_rhs(eps, np.float32)
+    o = make_options(**opts)
+    info = _Info()
+    st = lib().ciq_posterior_sample(_ptr(Xtr), int(n), _ptr(y), _ptr(Xc), int(Nc), int(d), KERNELS[kind],
+                                    ls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(outputscale),
+                                    float(noise), float(jitter), float(mean), _ptr(eps), int(T), int(Q), float(tol),
+                                    ctypes.byref(o), _ptr(out), ctypes.byref(info), _stream(Xtr, Xc, eps, out))
+    _check(st, "ciq_posterior_sample")
+    return out, _info_dict(info, st)
 
 
 def ciq_precond_workspace_bytes(N, d, T, Q, rank, **opts):

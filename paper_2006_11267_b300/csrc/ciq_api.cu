@@ -20,6 +20,7 @@
 #include "mlp.cuh"
 #include "mvm_stored.cuh"
 #include "mvm_tc.cuh"
+#include "posterior.cuh"
 #include "precond.cuh"
 #include "spectral.cuh"
 #include "symeig.h"
@@ -131,6 +132,7 @@ struct Plan {
     bool basis = false;           // stored-basis form (CIQ_KRYLOV_BASIS)
     bool vjp = false;             // backward pass: T = 2 T_B columns [B | G], basis form
     int pc_rank = 0;              // pivoted-Cholesky preconditioner rank (0: none)
+    int lr_rank = -1;             // low-rank correction -C C^T of the MVM (>= 0: on)
     bool stage_l = false;         // the caller's factor L is on the host
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB, *V, *sco;
@@ -215,6 +217,12 @@ struct Plan {
             tcp.inject = fault_inject;
         }
         Kst = stored ? a.take<float>((size_t)Npad * Npad) : nullptr;
+        if (lr_rank >= 0) {
+            const int rk = std::max(lr_rank, 1);
+            pc_g = a.take<float>((size_t)rk);
+            pcs = a.take<float>(pc_scratch_floats(Npad, rk, T));
+            Op = a.take<float>((size_t)T * Npad);
+        }
         if (pc_rank > 0) {
             const size_t RK = (size_t)pc_rank;
             Lf = a.take<float>(RK * Npad);
@@ -326,8 +334,22 @@ cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns,
 // Lanczos epilogue of `a`: U = P^{-1/2} q, O' = K U (plain MVM), then
 // p = P^{-1/2} O' - beta q_prev and the partial sums.
 template <typename R>
-cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<R>& a, cudaStream_t st) {
+cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<R>& a, cudaStream_t st,
+                        bool scale_ready = false) {
     if constexpr (sizeof(R) == 4) {
+        if (pc.lowrank) {
+            // (K - C C^T) q: the plain MVM of the unit columns q, then the
+            // correction and the Lanczos epilogue.
+            MvmArgs<R> m = a;
+            m.mode = kPlain;
+            m.out = p.Op;
+            m.ldo = p.Npad;
+            m.lz_q = nullptr;
+            m.lz_sco = nullptr;
+            cudaError_t e = launch_mvm(p, m, true, st, scale_ready);
+            if (e != cudaSuccess) return e;
+            return launch_lowrank_lanczos(pc, a.V, p.Op, a.V, a.qprev, a.pout, a.beta, a.partials, a.T, a.stop, st);
+        }
         // On tensor cores the operand scales of U come from the reduction of
         // P^{-1/2} (the columns of q have norm 1), so the MVM skips its own pass.
         cudaError_t e = launch_pc_apply(pc, a.V, p.Npad, a.T, true, p.Up, p.Npad, a.stop, st,
@@ -369,7 +391,7 @@ cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options
         if (e != cudaSuccess) return e;
         if ((e = launch_lanczos_step(ls, j, st)) != cudaSuccess) return e;
     }
-    return launch_bounds_nodes(ls, p.nodes, Q, pc ? 1.0 : k.noise, o.lmax_margin, o.lmin_div, st);
+    return launch_bounds_nodes(ls, p.nodes, Q, pc && !pc->lowrank ? 1.0 : k.noise, o.lmax_margin, o.lmin_div, st);
 }
 
 template <typename R>
@@ -436,6 +458,16 @@ struct PcSpec {
     const float* L;
     int64_t ldl;
     int rank;
+};
+
+// A low-rank correction of the MVM, (K - C C^T) V, with C^T given on the
+// device as [rank][Npad] (the posterior covariance K** - K*X M^{-1} K_X* of
+// a draw, C = K*X M^{-1/2}); mu (device, Npad floats, may be null) is added
+// to every output column.
+struct LrSpec {
+    const float* Ct;
+    int rank;
+    const float* mu;
 };
 
 // Preconditioner setup (App. "Preconditioning msMINRES-CIQ"): the factor,
@@ -519,7 +551,9 @@ template <typename R>
 ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* B, int T, int Q,
                  double tol, const ciq_options* opt, R* out, ciq_info* info, cudaStream_t st,
                  int op, bool fp64, const float* Kd = nullptr, int64_t ldk = 0, double* vjp_grad = nullptr,
-                 const PcSpec* pcs = nullptr) {
+                 const PcSpec* pcs = nullptr, const LrSpec* lrs = nullptr) {
+    if (lrs && (fp64 || Kd || vjp_grad || pcs || lrs->rank < 0 || (lrs->rank > 0 && !lrs->Ct)))
+        return CIQ_ERR_ARG;
     const bool dense = Kd != nullptr;
     const bool vjp = vjp_grad != nullptr;
     if (pcs) {
@@ -578,6 +612,10 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         p.pc_rank = pcs->rank;
         p.stage_l = pcs->L && !device_accessible(pcs->L);
         p.nparts = p.nparts1 = (int)pc_row_tiles(p.Npad);    // the preconditioned epilogue's row tiles
+    }
+    if (lrs) {
+        p.lr_rank = lrs->rank;
+        p.nparts = p.nparts1 = (int)pc_row_tiles(p.Npad);
     }
     p.stage_x = !dense && !device_accessible(X);
     p.stage_b = !device_accessible(B);
@@ -645,6 +683,26 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             launches += p.stored ? 1 : 0;
         }
         if constexpr (sizeof(R) == 4) {
+            if (lrs) {
+                std::vector<float> neg((size_t)std::max(lrs->rank, 1), -1.f);
+                CIQ_TRY(cudaMemcpyAsync(p.pc_g, neg.data(), sizeof(float) * neg.size(), cudaMemcpyHostToDevice, st));
+                CIQ_TRY(cudaStreamSynchronize(st));
+                pcst.N = N;
+                pcst.Npad = p.Npad;
+                pcst.rank = lrs->rank;
+                pcst.Qh = lrs->Ct;
+                pcst.gm = p.pc_g;
+                pcst.gp = p.pc_g;
+                pcst.sigma = 1.f;
+                pcst.inv_sigma = 1.f;
+                pcst.cpart = p.pcs;
+                pcst.coef = p.pcs + (pc_scratch_floats(p.Npad, std::max(lrs->rank, 1), T) -
+                                     (size_t)std::max(lrs->rank, 1) * T);
+                pcst.T = T;
+                pcst.lowrank = true;
+                pcst.mu = lrs->mu;
+                pc_on = true;
+            }
             if (p.pc_rank > 0) {
                 const float* Ld = pcs->L;
                 if (p.stage_l) {
@@ -693,6 +751,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         // Stored basis on tensor cores: the V split of MVM j + 1 finishes
         // step j's vector update (q_{j+1} from p and the published scalars).
         const bool lz = p.basis && p.tc && !pc_on;
+        const bool pc_map = pc_on && !pcst.lowrank;        // the result maps back through P^{+-1/2}
         CIQ_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
         CIQ_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         if (prof.on) {
@@ -737,7 +796,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                         a.qprev = (jj & 1) ? p.QB : p.QA;
                     }
                     a.beta = p.beta + (size_t)(jj & 1) * T;
-                    if (pc_on) CIQ_TRY(precond_mvm(p, pcst, a, st));
+                    if (pc_on) CIQ_TRY(precond_mvm(p, pcst, a, st, jj > 1));
                     else CIQ_TRY(launch_mvm(p, a, true, st, jj > 1));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
                     CIQ_TRY(launch_msminres_step(s, jj, false, st, !lz));
@@ -775,7 +834,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         // then P^{-1/2} (R' b) or P^{1/2} (R b) maps it back.
         R* comb = outd;
         if constexpr (sizeof(R) == 4) {
-            if (pc_on) comb = p.Apre;
+            if (pc_map) comb = p.Apre;
         }
         if (p.basis) {
             CIQ_TRY(launch_basis_combine(s, comb, last_j, st));   // kOpSqrtMvm: the sum goes to Y
@@ -803,7 +862,11 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             launches += 1;
         }
         if constexpr (sizeof(R) == 4) {
-            if (pc_on) {
+            if (pc_on && pcst.lowrank && pcst.mu) {
+                CIQ_TRY(launch_add_mean(outd, N, N, T, pcst.mu, st));
+                launches += 1;
+            }
+            if (pc_map) {
                 if (pc_literal) {
                     // R' b into the MVM's input buffer, then R b = K (R' b).
                     CIQ_TRY(launch_pc_apply(pcst, p.Apre, N, T, true, p.Up, p.Npad, nullptr, st));
@@ -882,7 +945,7 @@ done:
         info->mvm_launches = n_mvm;
         info->step_launches = n_step;
         info->krylov = p.basis ? CIQ_KRYLOV_BASIS : CIQ_KRYLOV_RECURRENCE;
-        info->precond_rank = pc_on ? pcst.rank : 0;
+        info->precond_rank = pc_on && !pcst.lowrank ? pcst.rank : 0;
     }
     if (tc_timeout) return CIQ_ERR_TIMEOUT;
     if (summary[6] > 0) return CIQ_ERR_NAN;
@@ -1773,6 +1836,115 @@ ciq_status ciq_pivoted_cholesky(const float* X, int64_t N, int d, const ciq_kern
     if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
     if (rank_out) *rank_out = got;
     return CIQ_OK;
+}
+
+ciq_status ciq_posterior_sample(const float* Xtr, int64_t n, const float* y, const float* Xc, int64_t Nc, int d,
+                                int kernel_type, const double* lengthscales, double outputscale, double noise,
+                                double jitter, double mean, const float* eps, int T, int Q, double tol,
+                                const ciq_options* opt, float* out, ciq_info* info, ciq_stream_t stream) {
+    if (n < 0 || n > CIQ_MAX_TRAIN || (n > 0 && (!Xtr || !y)) || !Xc || Nc < 1 || d < 1 || d > CIQ_MAX_DIM ||
+        !lengthscales || !eps || !out || T < 1 || (kernel_type != CIQ_RBF && kernel_type != CIQ_MATERN52) ||
+        !(outputscale > 0.0) || !std::isfinite(outputscale) || !(noise >= 0.0) || !std::isfinite(noise) ||
+        !(jitter > 0.0) || !std::isfinite(jitter) || !std::isfinite(mean))
+        return CIQ_ERR_ARG;
+    for (int c = 0; c < d; ++c)
+        if (!(lengthscales[c] > 0.0) || !std::isfinite(lengthscales[c])) return CIQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_warm();
+    const int64_t Npad = round_up(Nc, kRowPad);
+    const int nn = (int)n;
+    Arena ar;
+    struct Buf {
+        float *Xt, *Xc, *Xts, *Xcs, *Ct, *mu;
+        double *ls, *M, *Kcx, *W, *a;
+    };
+    auto lay = [&](char* base) {
+        ar = Arena{};
+        ar.base = base;
+        Buf b;
+        b.Xt = ar.take<float>((size_t)std::max<int64_t>(n, 1) * d);
+        b.Xc = ar.take<float>((size_t)Nc * d);
+        b.Xts = ar.take<float>((size_t)std::max<int64_t>(n, 1) * d);
+        b.Xcs = ar.take<float>((size_t)Nc * d);
+        b.Ct = ar.take<float>((size_t)std::max(nn, 1) * Npad);
+        b.mu = ar.take<float>((size_t)Npad);
+        b.ls = ar.take<double>((size_t)d);
+        b.M = ar.take<double>((size_t)std::max(nn, 1) * std::max(nn, 1));
+        b.Kcx = ar.take<double>((size_t)std::max(nn, 1) * Npad);
+        b.W = ar.take<double>((size_t)std::max(nn, 1) * std::max(nn, 1));
+        b.a = ar.take<double>((size_t)std::max(nn, 1));
+        return b;
+    };
+    lay(nullptr);
+    const size_t need = ar.off + kAlign;
+    char* base = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), need, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    const Buf b = lay(base);
+    ciq_status rc = CIQ_OK;
+    std::vector<double> M((size_t)nn * nn), lam(nn), U((size_t)nn * nn), W((size_t)nn * nn, 0.0), a(nn), yh(nn);
+    int rk = 0;
+    e = cudaMemcpyAsync(b.Xc, Xc, sizeof(float) * (size_t)Nc * d, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.ls, lengthscales, sizeof(double) * d, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_ard_scale(b.Xc, Nc, d, b.ls, b.Xcs, st);
+    if (nn > 0) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b.Xt, Xtr, sizeof(float) * (size_t)n * d, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = launch_ard_scale(b.Xt, n, d, b.ls, b.Xts, st);
+        // M = K_XX + sigma^2 I (FP64), to the host for its eigendecomposition.
+        if (e == cudaSuccess)
+            e = launch_kernel_block_f64(b.Xts, n, b.Xts, n, d, kernel_type, outputscale, noise, b.M, n, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(M.data(), b.M, sizeof(double) * M.size(), cudaMemcpyDeviceToHost, st);
+        std::vector<float> yf(nn);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(yf.data(), y, sizeof(float) * nn, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        for (int i = 0; i < nn; ++i) yh[i] = (double)yf[i] - mean;
+        if (e == cudaSuccess) {
+            if (!symeig::eigh(nn, M.data(), lam.data(), U.data())) rc = CIQ_ERR_NAN;
+        }
+        if (e == cudaSuccess && rc == CIQ_OK) {
+            // M = U diag(lambda) U^T; over the directions with lambda > 1e-13
+            // max(lambda), W = U diag(lambda^{-1/2}) (n x rk) and C = K*X W, so
+            // C C^T = K*X M^{-1} K_X*; a = W^T (y - m), so C a = K*X M^{-1} (y - m).
+            const double lmax = lam[nn - 1];
+            if (!(lmax > 0.0) || !std::isfinite(lmax)) rc = CIQ_ERR_NAN;
+            for (int i = 0; rc == CIQ_OK && i < nn; ++i) {
+                if (!(lam[i] > 1e-13 * lmax)) continue;
+                const double f = 1.0 / std::sqrt(lam[i]);
+                double sa = 0.0;
+                for (int r = 0; r < nn; ++r) {
+                    const double u = U[(size_t)r + (size_t)i * nn];
+                    W[(size_t)r + (size_t)rk * nn] = u * f;
+                    sa += u * yh[r];
+                }
+                a[rk] = sa * f;
+                ++rk;
+            }
+        }
+        if (e == cudaSuccess && rc == CIQ_OK && rk > 0) {
+            e = cudaMemcpyAsync(b.W, W.data(), sizeof(double) * (size_t)nn * rk, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(b.a, a.data(), sizeof(double) * rk, cudaMemcpyHostToDevice, st);
+            // K*X in FP64 ([n][Npad], column m = training point m over the
+            // candidates), then C^T = (K*X W)^T rounded once to FP32.
+            if (e == cudaSuccess)
+                e = launch_kernel_block_f64(b.Xcs, Nc, b.Xts, n, d, kernel_type, outputscale, 0.0, b.Kcx, Npad, st);
+            if (e == cudaSuccess) e = launch_product_f64(b.Kcx, Npad, nn, b.W, rk, b.Ct, st);
+            if (e == cudaSuccess) e = launch_posterior_mean(b.Ct, rk, Nc, Npad, b.a, mean, b.mu, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);       // the host vectors go out of scope
+        }
+    } else {
+        if (e == cudaSuccess) e = launch_posterior_mean(b.Ct, 0, Nc, Npad, b.a, mean, b.mu, st);
+    }
+    if (e != cudaSuccess) rc = from_cuda(e);
+    if (rc == CIQ_OK) {
+        const ciq_kernel kc{kernel_type, 1.0, outputscale, jitter};       // candidates already divided by l_d
+        const LrSpec lr{b.Ct, rk, b.mu};
+        rc = solve<float>(b.Xcs, Nc, d, &kc, eps, T, Q, tol, opt, out, info, st, kOpSqrtIdentity, false, nullptr, 0,
+                          nullptr, nullptr, &lr);
+    }
+    cudaFreeAsync(base, st);
+    cudaStreamSynchronize(st);
+    if (rc != CIQ_OK && rc != CIQ_NOT_CONVERGED) cudaGetLastError();
+    return rc;
 }
 
 size_t ciq_precond_workspace_bytes(int64_t N, int d, int T, int Q, int rank, const ciq_options* opt) {

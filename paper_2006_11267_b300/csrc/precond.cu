@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256, 3) pc_reduce(PrecondState pc, const float
         }
         __syncthreads();
     }
-    float* dst = pc.cpart + (int64_t)blockIdx.z * pc.rank * T;
+    float* dst = pc.cpart + (int64_t)blockIdx.z * pc.rank * T;      // [chunk][t][r]
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int r = r0 + ty * 4 + u;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256, 3) pc_reduce(PrecondState pc, const float
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int t = t0 + tx * 4 + v;
-            if (t < T) dst[(int64_t)r * T + t] = acc[u][v];
+            if (t < T) dst[(int64_t)t * pc.rank + r] = acc[u][v];
         }
     }
 }
@@ -113,11 +113,10 @@ __global__ void __launch_bounds__(256) pc_coef(PrecondState pc, int T, int nchun
     double nrm2 = 0.0;
     const double is = 1.0 / (double)pc.sigma;
     for (int r = threadIdx.x; r < pc.rank; r += blockDim.x) {
-        const int64_t e = (int64_t)r * T + t;
         double s = 0.0;
-        for (int c = 0; c < nchunks; ++c) s += (double)pc.cpart[(int64_t)c * pc.rank * T + e];
+        for (int c = 0; c < nchunks; ++c) s += (double)pc.cpart[((int64_t)c * T + t) * pc.rank + r];
         const double g = (double)(inverse_root ? pc.gm[r] : pc.gp[r]);
-        pc.coef[e] = (float)(s * g);
+        pc.coef[(int64_t)r * T + t] = (float)(s * g);
         nrm2 += (g * g + 2.0 * g * is) * s * s;
     }
     if (!vscale) return;
@@ -415,7 +414,8 @@ __global__ void gram_reduce(const double* gpart, int R, int nchunks, double* G) 
 }
 
 // Qh[c][i] = sum_m L[m][i] W[m][c], 32 columns per block, one row per thread.
-__global__ void __launch_bounds__(128) basis_from_factor(const float* L, int64_t Npad, int R, const double* W,
+template <typename TIn>
+__global__ void __launch_bounds__(128) basis_from_factor(const TIn* L, int64_t Npad, int R, const double* W,
                                                          int Rk, float* Qh) {
     __shared__ double Ws[32][32];
     const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
@@ -450,7 +450,10 @@ int64_t pc_chunks(int64_t Npad) {
 }
 
 size_t pc_scratch_floats(int64_t Npad, int rank, int T) {
-    const int64_t rows = chunk_rows(Npad, rank, T);
+    // Partial sums for the most row chunks any rank up to `rank` uses (the
+    // chunk count only falls as the rank needs more tiles, so rank 1 has the
+    // most), then the coefficients.
+    const int64_t rows = chunk_rows(Npad, 1, T);
     const int64_t nch = (Npad + rows - 1) / rows;
     return (size_t)nch * rank * T + (size_t)rank * T;
 }
@@ -533,7 +536,29 @@ cudaError_t launch_gram(const float* L, int64_t Npad, int R, double* gpart, doub
 cudaError_t launch_basis_from_factor(const float* L, int64_t Npad, int R, const double* W, int Rk, float* Qh,
                                      cudaStream_t st) {
     if (Rk < 1) return cudaSuccess;
-    basis_from_factor<<<dim3((unsigned)(Npad / 128), (Rk + 31) / 32), 128, 0, st>>>(L, Npad, R, W, Rk, Qh);
+    basis_from_factor<float><<<dim3((unsigned)(Npad / 128), (Rk + 31) / 32), 128, 0, st>>>(L, Npad, R, W, Rk, Qh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_product_f64(const double* A, int64_t Npad, int R, const double* W, int Rk, float* out,
+                               cudaStream_t st) {
+    if (Rk < 1) return cudaSuccess;
+    basis_from_factor<double><<<dim3((unsigned)(Npad / 128), (Rk + 31) / 32), 128, 0, st>>>(A, Npad, R, W, Rk, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lowrank_lanczos(const PrecondState& pc, const float* V, const float* Oraw, const float* q,
+                                   float* qprev, float* pout, const double* beta, double* partials, int T,
+                                   const int* stop, cudaStream_t st) {
+    if (pc.rank > 0) {
+        const int64_t rows = chunk_rows(pc.Npad, pc.rank, T);
+        const int nch = (int)((pc.Npad + rows - 1) / rows);
+        dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
+        pc_reduce<<<g1, 256, 0, st>>>(pc, V, pc.Npad, T, rows, stop);
+        pc_coef<<<T, 256, 0, st>>>(pc, T, nch, true, nullptr, 0, stop);
+    }
+    dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
+    pc_expand<true><<<g2, 256, 0, st>>>(pc, Oraw, pc.Npad, T, 1.f, nullptr, 0, q, qprev, pout, beta, partials, stop);
     return cudaGetLastError();
 }
 

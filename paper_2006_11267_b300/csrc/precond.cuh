@@ -28,9 +28,13 @@ struct PrecondState {
     const float* gm = nullptr;      // [R'] g^-
     const float* gp = nullptr;      // [R'] g^+
     float sigma = 0.f, inv_sigma = 0.f;
-    float* cpart = nullptr;         // [pc_chunks(Npad)][R'][T] partial sums of Qh^T X
+    float* cpart = nullptr;         // [chunks][T][R'] partial sums of Qh^T X
     float* coef = nullptr;          // [R'][T]
     int T = 0;                      // columns the scratch is sized for
+    // Low-rank correction instead of a preconditioner: the MVM is K V + Qh
+    // diag(gm) Qh^T V (gm = -1: K - C C^T with C = Qh), no P^{+-1/2}.
+    bool lowrank = false;
+    const float* mu = nullptr;      // low-rank mode: added to every output column (may be null)
 };
 
 int64_t pc_chunks(int64_t Npad);
@@ -76,5 +80,18 @@ cudaError_t launch_gram(const float* L, int64_t Npad, int R, double* gpart, doub
 // W is R x Rk column-major FP64 (device).
 cudaError_t launch_basis_from_factor(const float* L, int64_t Npad, int R, const double* W, int Rk, float* Qh,
                                      cudaStream_t st);
+
+// out[c][i] = sum_m A[m][i] W[m][c] with FP64 A [R][Npad] (FP64 accumulation,
+// rounded once to FP32).
+cudaError_t launch_product_f64(const double* A, int64_t Npad, int R, const double* W, int Rk, float* out,
+                               cudaStream_t st);
+
+// Lanczos epilogue of an MVM with a low-rank correction, O = O' + Qh diag(gm)
+// Qh^T V (V: the MVM's input, O': its plain output, both leading dimension
+// Npad), then p = O - beta q_prev and the partial sums as launch_pc_lanczos.
+// With gm = -1 this is (K - C C^T) V for C = Qh.
+cudaError_t launch_lowrank_lanczos(const PrecondState& pc, const float* V, const float* Oraw, const float* q,
+                                   float* qprev, float* pout, const double* beta, double* partials, int T,
+                                   const int* stop, cudaStream_t st);
 
 }  // namespace ciq

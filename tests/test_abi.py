@@ -191,3 +191,21 @@ def test_precond_entry_points_validate_before_the_device():
     assert e.value.status == _ciq.CIQ_ERR_ARG
     assert P.ciq_precond_workspace_bytes(1000, 3, 8, 8, 50) > P.ciq_workspace_bytes(1000, 3, 8, 8)
     assert P.ciq_precond_workspace_bytes(1000, 3, 8, 8, 0) == 0
+
+
+def test_posterior_sample_validates_before_the_device():
+    Xtr = np.zeros((5, 2), np.float32)
+    y = np.zeros(5, np.float32)
+    Xc = np.zeros((10, 2), np.float32)
+    eps = np.zeros((1, 10), np.float32)
+    good = dict(kind="matern52", lengthscales=[0.3, 0.3], outputscale=1.0, noise=1e-4, jitter=1e-4, mean=0.0)
+    bad = [dict(good, jitter=0.0), dict(good, lengthscales=[0.3, -1.0]), dict(good, noise=-1.0),
+           dict(good, outputscale=float("inf")), dict(good, lengthscales=[0.3, float("nan")])]
+    for kw in bad:
+        with pytest.raises(P.CiqError) as e:
+            P.ciq_posterior_sample(Xtr, y, Xc, eps=eps, Q=8, **kw)
+        assert e.value.status == _ciq.CIQ_ERR_ARG, kw
+    big = np.zeros((2049, 2), np.float32)
+    with pytest.raises(P.CiqError) as e:
+        P.ciq_posterior_sample(big, np.zeros(2049, np.float32), Xc, eps=eps, Q=8, **good)
+    assert e.value.status == _ciq.CIQ_ERR_ARG

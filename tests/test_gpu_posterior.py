@@ -1,0 +1,91 @@
+"""Posterior Thompson draws (Sec. 5, Eq. thompson_sample) through the C ABI
+against the FP64 oracle (oracle/posterior.py, pinned in
+tests/test_oracle_posterior.py): the draw against the eigendecomposition of
+the dense posterior covariance (O1), and msMINRES-CIQ on that dense matrix
+(O2) at equal nodes and J.  Errors are relative 2-norms per draw
+(tests/relerr.py)."""
+import numpy as np
+import pytest
+import torch
+
+import ciq_inputs as ci
+import paper_2006_11267_b300 as P
+from oracle import ciq as O
+from oracle import posterior as PO
+from relerr import fp32_gate, rel
+
+pytestmark = pytest.mark.gpu
+
+LS = np.array([0.3, 0.2, 0.4, 0.25])
+S, NOISE, JITTER, MEAN = 1.2, 1e-4, 1e-4, 0.1
+
+
+def data(n, nc, t, seed, d=4):
+    Xtr = ci.points(seed, n, d).astype(np.float32)
+    Xc = ci.points(seed + 1, nc, d).astype(np.float32)
+    y = np.sin(5.0 * Xtr.astype(np.float64) @ np.arange(1, d + 1) / d).astype(np.float32)
+    eps = ci.rhs(seed + 2, nc, t).astype(np.float32)
+    return Xtr, y, Xc, eps
+
+
+def oracle(kind, Xtr, y, Xc):
+    return PO.posterior(Xtr.astype(np.float64), y.astype(np.float64), Xc.astype(np.float64), kind, LS, S, NOISE,
+                        JITTER, MEAN)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("kind", ["matern52", "rbf"])
+def test_posterior_draws_against_eigendecomposition(kind, prec):
+    Xtr, y, Xc, eps = data(150, 3000, 8, 11)
+    mu, cov = oracle(kind, Xtr, y, Xc)
+    exact = PO.thompson_draws(mu, cov, eps)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    out, info = P.ciq_posterior_sample(dev(Xtr), dev(y), dev(Xc), kind, LS, S, NOISE, JITTER, MEAN, dev(eps), 15,
+                                       1e-5, stop_rule="errbound", max_iter=3000, precision=prec)
+    assert info["status"] == 0 and info["lmin_used"] == JITTER
+    got = out.cpu().numpy().astype(np.float64)
+    assert rel(got, exact) < 1e-3
+    assert rel(got - mu[None, :], exact - mu[None, :]) < 1e-3          # the fluctuation part itself
+    # eps = 0: the posterior mean alone
+    zero = np.zeros((1, Xc.shape[0]), np.float32)
+    m0, _ = P.ciq_posterior_sample(dev(Xtr), dev(y), dev(Xc), kind, LS, S, NOISE, JITTER, MEAN, dev(zero), 15, 1e-5,
+                                   stop_rule="errbound", max_iter=3000)
+    assert rel(m0.cpu().numpy()[0], mu) < 1e-5
+
+
+@pytest.mark.parametrize("krylov", ["basis", "recurrence"])
+def test_posterior_fp32_matches_serial_oracle_at_equal_nodes_and_J(krylov):
+    Xtr, y, Xc, eps = data(100, 1500, 5, 21)
+    mu, cov = oracle("matern52", Xtr, y, Xc)
+    lam = np.linalg.eigvalsh(cov)
+    Q, J = 12, 400
+    nodes = O.quad_nodes(JITTER, 1.05 * lam[-1], Q)
+    run = lambda C: O.ciq_apply(O.dense_mvm(C), eps.astype(np.float64), Q, "sqrt", max_iter=J, nodes=nodes,
+                                lmin=JITTER)[0]
+    ref, info_o = O.ciq_apply(O.dense_mvm(cov), eps.astype(np.float64), Q, "sqrt", max_iter=J, nodes=nodes,
+                              lmin=JITTER)
+    assert np.max(info_o["errbound"] / np.linalg.norm(ref, axis=1)) < 1e-8            # converged
+    out, info = P.ciq_posterior_sample(Xtr, y, Xc, "matern52", LS, S, NOISE, JITTER, MEAN, eps, Q, 0.0,
+                                       max_iter=J, nodes=nodes, lmin=JITTER, krylov=krylov)
+    assert info["iters"] == J and info["krylov"] == krylov
+    tol, floor = fp32_gate(run, cov, ref)
+    err = rel(out - mu[None, :].astype(np.float32), ref)
+    assert err < tol, (err, tol, floor)
+
+
+def test_prior_draws_without_training_data_and_interpolation():
+    _, _, Xc, eps = data(1, 800, 3, 31)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    out, info = P.ciq_posterior_sample(None, None, dev(Xc), "matern52", LS, S, NOISE, JITTER, MEAN, dev(eps), 15,
+                                       1e-6, stop_rule="errbound", max_iter=2000)
+    mu, cov = PO.posterior(np.zeros((0, 4)), np.zeros(0), Xc.astype(np.float64), "matern52", LS, S, NOISE, JITTER,
+                           MEAN)
+    assert rel(out.cpu().numpy(), PO.thompson_draws(mu, cov, eps)) < 1e-3
+    # Candidates at the training points with nearly noise-free data: every
+    # draw passes within a few sqrt(jitter) of the observations there.
+    Xtr, y, Xc2, _ = data(60, 500, 1, 41)
+    Xc2 = np.vstack([Xtr, Xc2]).astype(np.float32)
+    eps2 = ci.rhs(42, Xc2.shape[0], 4).astype(np.float32)
+    out, _ = P.ciq_posterior_sample(Xtr, y, Xc2, "matern52", LS, S, 1e-8, JITTER, MEAN, eps2, 15, 1e-6,
+                                    stop_rule="errbound", max_iter=3000)
+    assert np.abs(out[:, :60] - y[None, :]).max() < 6 * np.sqrt(JITTER)
