@@ -88,13 +88,14 @@ def parse():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--workload", default="thompson50k",
                     choices=["thompson50k", "batched512", "precision200k", "learned", "stored", "spectrum", "vjp",
-                             "precond"],
+                             "precond", "posterior"],
                     help="batched512: the uneven 512-problem batch through ciq_sqrt_batched; precision200k: "
                          "the 200,000-point Matern precision sweep; learned: train the bound predictor on "
                          "20,000 instances and compare it with the Lanczos pre-pass on 4096 held-out ones; "
                          "spectrum: K^{1/2}b error against Q on matrices with prescribed spectra; "
                          "vjp: forward and backward pass of K^{-1/2}B on the 50,000-point problem; "
-                         "precond: pivoted-Cholesky preconditioned roots of ranks 100-400 on the 50,000-point problem")
+                         "precond: pivoted-Cholesky preconditioned roots of ranks 100-400 on the 50,000-point problem; "
+                         "posterior: Thompson draws at 50,000 candidates given 256 observations")
     ap.add_argument("--n", type=int, default=0, metavar="N",
                     help="run the headline solve on the first N points only (for profiling captures)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
@@ -1153,6 +1154,96 @@ def precond_oracle_check(P, torch, opts):
     return res
 
 
+POSTERIOR = dict(n_train=256, n_cand=50_000, d=6, kind="matern52", ls=(0.2, 0.25, 0.3, 0.35, 0.4, 0.45),
+                 s=1.0, noise=1e-4, jitter=1e-4, mean=0.0, t=64, q=12, seed=20201112, check_n=4096)
+
+
+def posterior_inputs(n_cand):
+    """Synthetic Bayesian-optimisation state: training points and candidates
+    uniform in [0,1]^6, observations of a smooth test function (a sum of
+    sines; the paper's Hartmann and Lunar Lander runs are not reproduced),
+    standard-normal eps."""
+    c = POSTERIOR
+    Xtr = ci.points(c["seed"], c["n_train"], c["d"]).astype(np.float32)
+    Xc = ci.points(c["seed"] + 1, c["n_cand"], c["d"])[:n_cand].astype(np.float32)
+    y = np.sin(2.0 * np.pi * Xtr.astype(np.float64) @ np.linspace(0.5, 1.5, c["d"])).astype(np.float32)
+    eps = ci.rhs(c["seed"] + 2, c["n_cand"], c["t"])[:, :n_cand].astype(np.float32)
+    return Xtr, y, Xc, np.ascontiguousarray(eps)
+
+
+def run_posterior(args):
+    """Posterior Thompson draws (Sec. 5, Eq. thompson_sample): 64 draws at
+    50,000 candidates given 256 observations, Matern-5/2 with ARD
+    lengthscales, sigma^2 = 1e-4, jitter 1e-4 (the paper's), Q = 12, error
+    bound 1e-3 on COV*^{1/2} eps.  One step = one ciq_posterior_sample call
+    (setup of the correction, pre-pass, solve, mean).  CPU leg: the draws on
+    the first check_n candidates against the FP64 eigendecomposition of the
+    dense posterior covariance (O1)."""
+    import torch
+
+    import paper_2006_11267_b300 as P
+
+    torch.cuda.set_device(0)
+    c = POSTERIOR
+    Xtr, y, Xc, eps = posterior_inputs(c["n_cand"])
+    dev = lambda a: torch.from_numpy(a).cuda()
+    Xtr_d, y_d, Xc_d, eps_d = dev(Xtr), dev(y), dev(Xc), dev(eps)
+    opts = dict(stop_rule="errbound", max_iter=MAX_ITER, lanczos_iters=LANCZOS_ITERS, precision=args.precision,
+                check_every=16)
+    call = lambda: P.ciq_posterior_sample(Xtr_d, y_d, Xc_d, c["kind"], c["ls"], c["s"], c["noise"], c["jitter"],
+                                          c["mean"], eps_d, c["q"], TOL, **opts)
+    for _ in range(max(1, args.warmup)):
+        call()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps)
+    e0.record()
+    infos = [call()[1] for _ in range(reps)]
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / reps
+    _, pinf = P.ciq_posterior_sample(Xtr_d, y_d, Xc_d, c["kind"], c["ls"], c["s"], c["noise"], c["jitter"], c["mean"],
+                                     eps_d, c["q"], TOL, profile=1, **opts)
+    check = None
+    if not args.no_cpu_baseline:
+        from oracle import posterior as PO
+        n = c["check_n"]
+        Xtr2, y2, Xc2, eps2 = posterior_inputs(n)
+        out, inf = P.ciq_posterior_sample(Xtr2, y2, Xc2, c["kind"], c["ls"], c["s"], c["noise"], c["jitter"],
+                                          c["mean"], eps2, c["q"], TOL, **opts)
+        t0 = time.perf_counter()
+        mu, cov = PO.posterior(Xtr2.astype(np.float64), y2.astype(np.float64), Xc2.astype(np.float64), c["kind"],
+                               np.array(c["ls"]), c["s"], c["noise"], c["jitter"], c["mean"])
+        exact = PO.thompson_draws(mu, cov, eps2)
+        fl = out.astype(np.float64) - mu[None, :]
+        ex = exact - mu[None, :]
+        e_draw = np.linalg.norm(out - exact, axis=1) / np.linalg.norm(exact, axis=1)
+        e_fl = np.linalg.norm(fl - ex, axis=1) / np.linalg.norm(ex, axis=1)
+        check = {"n_cand": n, "draw": {"max": float(e_draw.max()), "median": float(np.median(e_draw))},
+                 "fluctuation": {"max": float(e_fl.max()), "median": float(np.median(e_fl))},
+                 "iterations": inf["iters"], "oracle": "O1: FP64 eigendecomposition of the dense posterior covariance",
+                 "oracle_seconds": time.perf_counter() - t0}
+    line = {"metric": "posterior Thompson draws/s (mu* + COV*^{1/2} eps) at error bound 1e-3",
+            "value": c["t"] / (ms * 1e-3), "unit": "draws/s", "n_gpus": 1, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"{args.precision}x2-split tiles, f32 vectors and correction, f64 scalars and setup",
+            "data": "synthetic",
+            "config": {"workload": f"posterior_{c['kind']}_ard_ncand{c['n_cand']}_ntrain{c['n_train']}_d{c['d']}_t{c['t']}",
+                       "n_train": c["n_train"], "n_cand": c["n_cand"], "d": c["d"], "kernel": c["kind"] + " ARD",
+                       "lengthscales": list(c["ls"]), "noise": c["noise"], "jitter": c["jitter"], "T": c["t"],
+                       "Q": c["q"], "tol": TOL, "stop_rule": "errbound", "precision": args.precision},
+            "iterations": [i["iters"] for i in infos], "profile": {k: pinf[k] for k in
+                                                                   ("t_total_ms", "t_prepass_ms", "t_mvm_ms",
+                                                                    "t_step_ms", "mvm_launches")},
+            "oracle_check": check, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1171,6 +1262,8 @@ def main():
         return run_vjp(args)
     if args.workload == "precond":
         return run_precond(args)
+    if args.workload == "posterior":
+        return run_posterior(args)
     return run_ours(args)
 
 
