@@ -96,6 +96,8 @@ def parse():
                          "vjp: forward and backward pass of K^{-1/2}B on the 50,000-point problem; "
                          "precond: pivoted-Cholesky preconditioned roots of ranks 100-400 on the 50,000-point problem; "
                          "posterior: Thompson draws at 50,000 candidates given 256 observations")
+    ap.add_argument("--full-fp32", action="store_true",
+                    help="precision200k: run the plain FP32 solve to the stop rule too (about 10 minutes)")
     ap.add_argument("--n", type=int, default=0, metavar="N",
                     help="run the headline solve on the first N points only (for profiling captures)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
@@ -611,6 +613,23 @@ def run_batched(args):
         torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t0) / args.steps
     its = [i["iters"] for i in infos]
+    # Roofline of the batch: kernel entries evaluated over every live
+    # problem (each MVM of problem p, pre-pass included, covers N_p^2
+    # entries), against the SFU roof (1 ex2 per RBF entry, sqrt + ex2 per
+    # Matern entry; T = 8 leaves the tensor pipe far from binding), at the
+    # measured ex2 rate per SM and clock and the clock sampled while timing.
+    ent = [float(i["iters"] + i["lanczos_iters"]) * p["n"] ** 2 for i, p in zip(infos, raw)]
+    sfu_ops = sum(e * (1 if p["kernel"] == "rbf" else 2) for e, p in zip(ent, raw))
+    secs = elapsed_ms / args.steps * 1e-3
+    devpk = device_peaks()
+    per_clk = devpk.get("sfu_ex2_per_sm_per_clk")
+    mhz = clocks.get("sm_mhz") or devpk.get("sfu_sm_mhz")
+    sfu_peak = per_clk * SM_COUNT * mhz * 1e6 if per_clk and mhz else None
+    roof = {"bound": "sfu", "achieved": sfu_ops / secs / 1e9, "peak": sfu_peak / 1e9 if sfu_peak else None,
+            "unit": "G ex2/s", "frac": sfu_ops / secs / sfu_peak if sfu_peak else None, "traffic": None,
+            "entries_per_s": sum(ent) / secs,
+            "kernel": "the whole batched solve (tensor-core MVM over every live problem, recurrence, pre-pass)",
+            "peak_source": "measured ex2 per SM per clock (libciq_peaks) x 148 SMs x the sampled SM clock"}
     line = {"metric": "K^{1/2}b RHS-solves/s, uneven batch (batched vs plain FP32)", "value": value,
             "unit": "RHS-solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -632,7 +651,7 @@ def run_batched(args):
             "e2e": {"value": rhs / t_e2e, "unit": "RHS-solves/s",
                     "h2d_bytes_per_step": int(sum(h["X"].nbytes + h["B"].nbytes for h in host)),
                     "d2h_bytes_per_step": int(sum(o.nbytes for o in outs_h))},
-            "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None}
+            "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None, "roofline": roof}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -750,8 +769,9 @@ def run_precision(args):
     for m in modes:
         out, info = P.ciq_invsqrt(Xd, k, Bd, W.q, 1e-4, max_iter=2000, precision=m)
         torch.cuda.synchronize()
-        err = float(np.linalg.norm(out.cpu().numpy() - truth) / np.linalg.norm(truth))
-        sub[m] = {"rel_err_vs_fp64_eig": err, "iterations": info["iters"], "status": info["status_name"]}
+        col = np.linalg.norm(out.cpu().numpy() - truth, axis=1) / np.linalg.norm(truth, axis=1)
+        sub[m] = {"rel_err_vs_fp64_eig": float(col.max()), "median_col_err": float(np.median(col)),
+                  "iterations": info["iters"], "status": info["status_name"]}
     X = torch.from_numpy(ci.points(W.seed, W.n, W.d).astype(np.float32)).cuda()
     B = torch.from_numpy(ci.rhs(W.seed, W.n, W.t).astype(np.float32)).cuda()
     full = {}
@@ -775,13 +795,36 @@ def run_precision(args):
         it_ms = (info["t_mvm_ms"] / max(1, info["mvm_launches"]) + info["t_step_ms"] / max(1, info["step_launches"]))
         full[m] = {"mvm_call_ms": e0.elapsed_time(e1), "mvm_rel_diff_vs_fp32": diff, "ms_per_iteration": it_ms,
                    "mvm_ms_in_solve": info["t_mvm_ms"] / max(1, info["mvm_launches"])}
+    # Whole solves at the workload's stop rule (relative residual 1e-4):
+    # RHS-solves/s and the iterations each mode needs.  The FP32 solve (about
+    # 0.75 s per iteration) runs in full only with --full-fp32; otherwise its
+    # time is the FP16 solve's iteration count times its measured
+    # per-iteration time (labelled as such).
+    solves = {}
+    for m in modes:
+        if m == "fp32" and not args.full_fp32:
+            continue
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record()
+        _, info = P.ciq_invsqrt(X, k, B, W.q, W.tol, max_iter=3000, lanczos_iters=10, precision=m, check_every=16)
+        g1.record()
+        torch.cuda.synchronize()
+        ms = g0.elapsed_time(g1)
+        solves[m] = {"rhs_solves_per_s": W.t / (ms * 1e-3), "ms": ms, "iterations": info["iters"],
+                     "status": info["status_name"], "resid_max": info["resid_max"], "measured": "full solve"}
+    if "fp32" not in solves and "fp16" in solves:
+        J = solves["fp16"]["iterations"] + 10
+        ms = J * full["fp32"]["ms_per_iteration"]
+        solves["fp32"] = {"rhs_solves_per_s": W.t / (ms * 1e-3), "ms": ms, "iterations": None,
+                          "measured": f"extrapolated: the FP16 solve's {J} MVMs x the measured FP32 ms/iteration"}
     line = {"metric": "K^{-1/2}b precision sweep (error vs FP64 oracle per mode)", "value": full["fp16"]["ms_per_iteration"],
             "unit": "ms/iteration (FP16 split, N=200000, T=256)", "n_gpus": 1, "steps": 1, "warmup": 1,
             "higher_is_better": False, "dtype": "f32 / fp16x2 / bf16x2 tiles, f64 scalars", "data": "synthetic",
             "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
                        "noise": W.noise, "T": W.t, "Q": W.q, "op": "invsqrt", "subsample": n_sub,
                        "subsample_tol": 1e-4},
-            "subsample": sub, "full_size": full}
+            "subsample": sub, "full_size": full, "solves": solves}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -58,7 +58,7 @@ def test_posterior_fp32_matches_serial_oracle_at_equal_nodes_and_J(krylov):
     Xtr, y, Xc, eps = data(100, 1500, 5, 21)
     mu, cov = oracle("matern52", Xtr, y, Xc)
     lam = np.linalg.eigvalsh(cov)
-    Q, J = 12, 400
+    Q, J = 12, 1500                     # kappa(COV*) ~ 1e5: converged well before J
     nodes = O.quad_nodes(JITTER, 1.05 * lam[-1], Q)
     run = lambda C: O.ciq_apply(O.dense_mvm(C), eps.astype(np.float64), Q, "sqrt", max_iter=J, nodes=nodes,
                                 lmin=JITTER)[0]
