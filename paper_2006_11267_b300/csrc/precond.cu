@@ -8,7 +8,8 @@
 //    pivot's residual diagonal; the residual diagonal (FP64) is updated and
 //    the next pivot (largest residual, first index on ties) is chosen by the
 //    last block to finish.  One launch per column.
-//  * gram_part / gram_reduce: G = L^T L in FP64 (exact FP32 products).
+//  * gram_part / gram_reduce: G = L^T L with exact FP32 products summed as
+//    float pairs within a row chunk and in FP64 across chunks.
 //  * basis_from_factor: Qh = L W with W = U diag(s)^{-1/2} (FP64 accumulation).
 //  * pc_reduce / pc_coef: C = diag(g) Qh^T X, a 64 x 64 register-tiled product
 //    over row chunks (FP32 within a chunk, FP64 across chunks).
@@ -375,7 +376,10 @@ __global__ void __launch_bounds__(256) gram_part(const float* L, int64_t Npad, i
     const int a0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
     const int64_t i_begin = (int64_t)blockIdx.z * rows_per_chunk;
     const int64_t i_end = min(i_begin + rows_per_chunk, Npad);
-    double acc[2][2] = {};
+    // Float-pair accumulation of exact products (the product's error from an
+    // FMA, Knuth's 2Sum for the sum; intrinsics, so nothing is contracted):
+    // about twice FP32's precision at the FP32 pipe's rate.
+    float hi[2][2] = {}, lo[2][2] = {};
     for (int64_t i0 = i_begin; i0 < i_end; i0 += 64) {
         for (int e = tid; e < 64 * 32; e += 256) {
             const int ii = e & 63, cc = e >> 6;
@@ -388,8 +392,16 @@ __global__ void __launch_bounds__(256) gram_part(const float* L, int64_t Npad, i
 #pragma unroll
             for (int u = 0; u < 2; ++u)
 #pragma unroll
-                for (int v = 0; v < 2; ++v)
-                    acc[u][v] = fma((double)As[ii][ty * 2 + u], (double)Bs[ii][tx * 2 + v], acc[u][v]);
+                for (int v = 0; v < 2; ++v) {
+                    const float x = As[ii][ty * 2 + u], y = Bs[ii][tx * 2 + v];
+                    const float p = __fmul_rn(x, y);
+                    const float pe = __fmaf_rn(x, y, -p);
+                    const float s = __fadd_rn(hi[u][v], p);
+                    const float bp = __fsub_rn(s, hi[u][v]);
+                    const float err = __fadd_rn(__fsub_rn(hi[u][v], __fsub_rn(s, bp)), __fsub_rn(p, bp));
+                    hi[u][v] = s;
+                    lo[u][v] = __fadd_rn(lo[u][v], __fadd_rn(err, pe));
+                }
         }
         __syncthreads();
     }
@@ -398,7 +410,7 @@ __global__ void __launch_bounds__(256) gram_part(const float* L, int64_t Npad, i
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
             const int a = a0 + ty * 2 + u, b = b0 + tx * 2 + v;
-            if (a < R && b < R) gpart[((int64_t)blockIdx.z * R + a) * R + b] = acc[u][v];
+            if (a < R && b < R) gpart[((int64_t)blockIdx.z * R + a) * R + b] = (double)hi[u][v] + (double)lo[u][v];
         }
 }
 
