@@ -96,6 +96,9 @@ def parse():
                          "vjp: forward and backward pass of K^{-1/2}B on the 50,000-point problem; "
                          "precond: pivoted-Cholesky preconditioned roots of ranks 100-400 on the 50,000-point problem; "
                          "posterior: Thompson draws at 50,000 candidates given 256 observations")
+    ap.add_argument("--profile-rank", type=int, default=0, metavar="R",
+                    help="precond: only run two 40-iteration R' b solves with a rank-R preconditioner "
+                         "(a short, fixed launch sequence for profiling)")
     ap.add_argument("--full-fp32", action="store_true",
                     help="precision200k: run the plain FP32 solve to the stop rule too (about 10 minutes)")
     ap.add_argument("--n", type=int, default=0, metavar="N",
@@ -1089,6 +1092,13 @@ def run_precond(args):
     X = torch.from_numpy(ci.points(W.seed, W.n, W.d).astype(np.float32)).cuda()
     B = torch.from_numpy(ci.rhs(W.seed, W.n, W.t).astype(np.float32)).cuda()
     k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    if args.profile_rank:
+        for _ in range(2):
+            _, inf = P.ciq_invsqrt_precond(X, k, B, W.q, 0.0, rank=args.profile_rank, max_iter=40,
+                                           precision=args.precision, lmin=1.0, lmax=1e5)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_rank": args.profile_rank, "iters": inf["iters"], "launches": inf["launches"]}))
+        return 0
     opts = dict(stop_rule="errbound", max_iter=MAX_ITER, lanczos_iters=LANCZOS_ITERS, precision=args.precision,
                 check_every=16)
     reps = max(1, args.steps)
