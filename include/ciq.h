@@ -154,6 +154,9 @@ typedef struct {
                                  skip its first point copy, so its bounded waits run out and the
                                  call returns CIQ_ERR_TIMEOUT (the failure-detection path) */
     int krylov;               /* ciq_krylov_form (default CIQ_KRYLOV_AUTO) */
+    int batch_split_rows;     /* tensor-core batches: problems of at least this many 128-row tiles
+                                 run batch_split CTAs per row tile (0 = off, the default) */
+    int batch_split;          /* 1..8 (used when batch_split_rows > 0) */
 } ciq_options;
 
 typedef struct {

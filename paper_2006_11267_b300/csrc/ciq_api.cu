@@ -84,7 +84,8 @@ bool valid_options(const ciq_options& o) {
              (o.precision < CIQ_PREC_FP32 || o.precision > CIQ_PREC_FP16) ||
              (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED) || o.tc_split < 0 || o.tc_split > 8 ||
              o.fault_inject < 0 || o.fault_inject > 1 || o.krylov < CIQ_KRYLOV_AUTO ||
-             o.krylov > CIQ_KRYLOV_BASIS);
+             o.krylov > CIQ_KRYLOV_BASIS || o.batch_split_rows < 0 ||
+             (o.batch_split_rows > 0 && (o.batch_split < 1 || o.batch_split > 8)));
 }
 
 // Pinned host words for the convergence flag, one set per host thread.
@@ -1039,6 +1040,10 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         // CTAs only adds per-CTA cost here (measured 3.78 -> 2.94 s on the
         // 512-problem batch without it), so batches default to one CTA.
         plans.back().tc_max_split = o.tc_split > 0 ? o.tc_split : 1;
+        // A tuned policy: large problems (the ones left in a batch's tail, when
+        // few row tiles are live) split their row tiles over more CTAs.
+        if (o.batch_split_rows > 0 && plans.back().Npad / kTcBM >= o.batch_split_rows)
+            plans.back().tc_max_split = o.batch_split;
         plans.back().tri_on = record_tri;
         plans.back().layout(nullptr);
         offs[p] = off;

@@ -175,3 +175,25 @@ def test_tensor_core_batch_limits():
     with pytest.raises(P.CiqError) as e:
         batched("sqrt", many, 8, 1e-4, precision="fp16")
     assert e.value.status == P._ciq.CIQ_ERR_UNSUPPORTED
+
+
+def test_split_policy_and_autotuner_change_only_the_summation_order(tmp_path):
+    # Large problems split their row tiles over more CTAs (batch_split_rows /
+    # batch_split): each problem's result stays within the stop rule's
+    # accuracy of the default launch shape; the autotuner measures its
+    # candidates once, stores the fastest and reuses it.
+    from paper_2006_11267_b300 import autotune
+    specs = [(300, 3, "rbf", 0.3, 1e-2), (2100, 4, "matern52", 0.4, 1e-2), (4200, 5, "rbf", 0.5, 1e-2)]
+    probs = [hand_problem(n, d, 8, 700 + n, kind, ls, noise) for n, d, kind, ls, noise in specs]
+    outs0, infos0 = batched("sqrt", probs, 8, 1e-5, max_iter=1000, precision="fp16")
+    ref = [o.clone() for o in outs0]
+    outs1, infos1 = batched("sqrt", probs, 8, 1e-5, max_iter=1000, precision="fp16", batch_split_rows=16,
+                            batch_split=4)
+    for a, b, i in zip(outs1, ref, infos1):
+        assert i["status"] == 0
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-4
+    path = str(tmp_path / "tune.json")
+    best, timings = autotune.tune(probs, 8, 1e-5, path=path, max_iter=1000, precision="fp16")
+    assert len(timings) == len(autotune.CANDIDATES) and best in autotune.CANDIDATES
+    _, infos2 = autotune.solve_batched_tuned(probs, 8, 1e-5, path=path, max_iter=1000, precision="fp16")
+    assert all(i["status"] == 0 for i in infos2)
