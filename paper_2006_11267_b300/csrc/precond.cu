@@ -4,7 +4,7 @@
 //
 //  * pc_cholesky_step: one greedy step of the partial pivoted Cholesky of
 //    K_XX (Harbrecht, Peters and Schneider 2012): the pivot's kernel column,
-//    minus the previous columns (FP64 dot), divided by the root of the
+//    minus the previous columns (float-pair dot), divided by the root of the
 //    pivot's residual diagonal; the residual diagonal (FP64) is updated and
 //    the next pivot (largest residual, first index on ties) is chosen by the
 //    last block to finish.  One launch per column.
@@ -12,10 +12,10 @@
 //    float pairs within a row chunk and in FP64 across chunks.
 //  * basis_from_factor: Qh = L W with W = U diag(s)^{-1/2} (FP64 accumulation).
 //  * pc_reduce / pc_coef: C = diag(g) Qh^T X, a 64 x 64 register-tiled product
-//    over row chunks (FP32 within a chunk, FP64 across chunks).
+//    over row chunks (FP32 within a chunk, float pairs across chunks).
 //  * pc_expand: out = sigma^{+-1} X + Qh C over 128-row tiles, with the
-//    Lanczos epilogue (p = O - beta q_prev, FP64 q.p, p.p, q.q per tile) for
-//    the preconditioned MVM.
+//    Lanczos epilogue (p = O - beta q_prev; q.p, p.p, q.q per tile as float
+//    pairs of exact products, stored as FP64) for the preconditioned MVM.
 #include <climits>
 
 #include <algorithm>
@@ -38,6 +38,42 @@ int64_t chunk_rows(int64_t Npad, int R, int T) {
     int64_t ch = std::max<int64_t>(1, 444 / tiles);
     ch = std::min<int64_t>(ch, std::max<int64_t>(1, Npad / 256));
     return round_up((Npad + ch - 1) / ch, kRedSub);
+}
+
+// Float pairs (hi + lo, about twice FP32's precision): FP64 runs at about
+// 1/64 of FP32's rate on this part, and the Lanczos sums of the epilogue
+// would otherwise dominate it.  Intrinsics keep every operation rounded as
+// written (no contraction into FMAs).
+struct FPair {
+    float hi = 0.f, lo = 0.f;
+};
+
+__device__ __forceinline__ void pair_add(FPair& a, float x) {
+    const float s = __fadd_rn(a.hi, x);
+    const float bp = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, err);
+}
+
+// a += x * y with the product's rounding error kept (FMA), so the pair holds
+// the exact product sum to about 2^-48 relative.
+__device__ __forceinline__ void pair_fma(FPair& a, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    pair_add(a, p);
+    a.lo = __fadd_rn(a.lo, e);
+}
+
+__device__ __forceinline__ FPair pair_warp_sum(FPair a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        const float l = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        pair_add(a, h);
+        a.lo = __fadd_rn(a.lo, l);
+    }
+    return a;
 }
 
 // cpart[chunk][r][t] = sum over the chunk's rows of Qh[r][i] X[t][i].
@@ -114,8 +150,9 @@ __global__ void __launch_bounds__(256) pc_coef(PrecondState pc, int T, int nchun
     double nrm2 = 0.0;
     const double is = 1.0 / (double)pc.sigma;
     for (int r = threadIdx.x; r < pc.rank; r += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < nchunks; ++c) s += (double)pc.cpart[((int64_t)c * T + t) * pc.rank + r];
+        FPair acc;
+        for (int c = 0; c < nchunks; ++c) pair_add(acc, pc.cpart[((int64_t)c * T + t) * pc.rank + r]);
+        const double s = (double)acc.hi + (double)acc.lo;
         const double g = (double)(inverse_root ? pc.gm[r] : pc.gp[r]);
         pc.coef[(int64_t)r * T + t] = (float)(s * g);
         nrm2 += (g * g + 2.0 * g * is) * s * s;
@@ -194,7 +231,7 @@ __global__ void __launch_bounds__(256, 3) pc_expand(PrecondState pc, const float
     for (int v = 0; v < 8; ++v) {
         const int t = t0 + ty * 8 + v;
         if (t >= T) break;                       // warp-uniform: every lane has the same ty
-        double qp = 0.0, pp = 0.0, qq = 0.0;
+        FPair qp, pp, qq;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t i = i0 + tx + 32 * u;
@@ -207,21 +244,21 @@ __global__ void __launch_bounds__(256, 3) pc_expand(PrecondState pc, const float
                 const int64_t idx = (int64_t)t * pc.Npad + i;
                 const float p = i < pc.N ? o - (float)beta[t] * qprev[idx] : 0.f;
                 (pout ? pout : qprev)[idx] = p;
-                const double qd = (double)q[idx], pd = (double)p;
-                qp += qd * pd;
-                pp += pd * pd;
-                qq += qd * qd;
+                const float qv = q[idx];
+                pair_fma(qp, qv, p);
+                pair_fma(pp, p, p);
+                pair_fma(qq, qv, qv);
             }
         }
         if (LANCZOS) {
-            qp = warp_sum(qp);
-            pp = warp_sum(pp);
-            qq = warp_sum(qq);
+            qp = pair_warp_sum(qp);
+            pp = pair_warp_sum(pp);
+            qq = pair_warp_sum(qq);
             if (tx == 0) {
                 double* dst = partials + ((int64_t)blockIdx.x * T + t) * 3;
-                dst[0] = qp;
-                dst[1] = pp;
-                dst[2] = qq;
+                dst[0] = (double)qp.hi + (double)qp.lo;
+                dst[1] = (double)pp.hi + (double)pp.lo;
+                dst[2] = (double)qq.hi + (double)qq.lo;
             }
         }
     }
@@ -297,8 +334,11 @@ __global__ void __launch_bounds__(256) pc_cholesky_step(const float* Xp, int64_t
             const float df = Xp[i * dp + c] - xp[c];
             r2 = fmaf(df, df, r2);
         }
-        double col = (double)kernel_value<KT>(r2, s);
-        for (int m = 0; m < k; ++m) col -= (double)L[(int64_t)m * Npad + i] * (double)Lp[m];
+        // The kernel value minus the earlier columns' contributions, summed as
+        // a float pair of exact products (FP64 is slow here; see FPair).
+        FPair dot;
+        for (int m = 0; m < k; ++m) pair_fma(dot, L[(int64_t)m * Npad + i], Lp[m]);
+        double col = (double)kernel_value<KT>(r2, s) - ((double)dot.hi + (double)dot.lo);
         const bool was_pivot = w.ispiv[i] != 0;
         if (was_pivot) col = 0.0;              // earlier pivot rows of the Schur complement are 0
         const float l = (float)(col / sqrt(dpiv));
