@@ -773,7 +773,7 @@ def run_stored(args):
 
 def run_precision(args):
     """Precision sweep, 200,000-point Matern-5/2 workload, K^{-1/2}B, Q = 15:
-    per mode (plain FP32, FP16 split, BF16 split) the solve error against the
+    per mode (plain FP32, FP16 split, BF16 split, TF32 tiles) the solve error against the
     FP64 eigendecomposition on a 4096-point subsample (T = 256), and at full
     size the MVM time and its difference from the FP32 MVM, and the time per
     msMINRES iteration (a fixed 10-iteration solve)."""
@@ -785,7 +785,7 @@ def run_precision(args):
     torch.cuda.set_device(0)
     W = ci.PRECISION_200K
     k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
-    modes = ("fp32", "fp16", "bf16")
+    modes = ("fp32", "fp16", "bf16", "tf32")
     n_sub = 4096
     Xs = ci.points(W.seed, W.n, W.d)[:n_sub].astype(np.float32)
     Bs = ci.rhs(W.seed + 1, n_sub, W.t).astype(np.float32)
@@ -829,7 +829,9 @@ def run_precision(args):
     # per-iteration time (labelled as such).
     solves = {}
     for m in modes:
-        if m == "fp32" and not args.full_fp32:
+        # TF32 tiles (11 significant bits): the residual stalls above the 1e-4
+        # stop (see the subsample), so no whole solve is timed for it.
+        if m == "tf32" or (m == "fp32" and not args.full_fp32):
             continue
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
@@ -847,7 +849,7 @@ def run_precision(args):
                           "measured": f"extrapolated: the FP16 solve's {J} MVMs x the measured FP32 ms/iteration"}
     line = {"metric": "K^{-1/2}b precision sweep (error vs FP64 oracle per mode)", "value": full["fp16"]["ms_per_iteration"],
             "unit": "ms/iteration (FP16 split, N=200000, T=256)", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "higher_is_better": False, "dtype": "f32 / fp16x2 / bf16x2 tiles, f64 scalars", "data": "synthetic",
+            "higher_is_better": False, "dtype": "f32 / fp16x2 / bf16x2 / tf32 tiles, f64 scalars", "data": "synthetic",
             "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
                        "noise": W.noise, "T": W.t, "Q": W.q, "op": "invsqrt", "subsample": n_sub,
                        "subsample_tol": 1e-4},

@@ -88,7 +88,9 @@ typedef struct {
  * Lanczos/Givens scalars stay FP64 in every mode). */
 typedef enum {
     CIQ_PREC_FP32 = 0,        /* plain FP32 on CUDA cores */
-    CIQ_PREC_TF32 = 1,        /* reserved: tensor cores with TF32 operands (not built) */
+    CIQ_PREC_TF32 = 1,        /* tensor cores (tcgen05, kind::tf32): P and V rounded to TF32, one
+                                 product, no split (the distance tile keeps the FP16 split);
+                                 single problems only (batches: CIQ_ERR_UNSUPPORTED) */
     CIQ_PREC_BF16 = 2,        /* tensor cores (tcgen05): every operand split into two BF16 parts */
     CIQ_PREC_FP16 = 3         /* tensor cores (tcgen05): every operand split into two FP16 parts */
 } ciq_precision;
@@ -316,7 +318,7 @@ typedef struct {
  * Q, tol and the options; all problems must have the same T.  FP32 vectors,
  * FP64 scalars; on-the-fly MVM on CUDA cores (CIQ_PREC_FP32) or on tensor
  * cores with FP16/BF16 split tiles (CIQ_PREC_FP16/BF16; then T <= 64 and
- * every d <= 14).  Every problem's arithmetic is that of ciq_sqrt /
+ * every d <= 14; CIQ_PREC_TF32: CIQ_ERR_UNSUPPORTED).  Every problem's arithmetic is that of ciq_sqrt /
  * ciq_invsqrt with the same options, so each output equals the
  * single-problem call's bit for bit (tensor-core batches run one CTA per
  * row tile unless opt->tc_split says otherwise, so the single call is

@@ -1006,7 +1006,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     if (opt) o = *opt;
     if (!valid_options(o)) return CIQ_ERR_ARG;
     if (o.mvm == CIQ_MVM_STORED || o.quad_w || o.quad_t || o.lanczos_start || o.workspace ||
-        o.sqrt_form != CIQ_SQRT_IDENTITY)
+        o.sqrt_form != CIQ_SQRT_IDENTITY || o.precision == CIQ_PREC_TF32)
         return CIQ_ERR_UNSUPPORTED;
     const int T = probs[0].T;
     if (T < 1) return CIQ_ERR_ARG;

@@ -81,6 +81,14 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
     }
 }
 
+// Round to TF32 (10 stored mantissa bits), to nearest with ties away from
+// zero; the result is a float whose 13 low mantissa bits are zero.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return u;
+}
+
 // ---------------------------------------------------------- operand prep --
 // Centre of the points, one block of 256 threads, in a fixed summation order
 // (so the operands, and every result, are reproducible bit for bit).  Thread
@@ -212,7 +220,9 @@ __global__ void tc_vscale_kernel(const float* V, int64_t ldv, int64_t N, int T, 
 // One thread per (column, 8 consecutive rows): scaled V split into the
 // B-operand layout.  Columns come in launch groups of tpg; group g holds
 // [tile][part][col/8][K-core][col%8][row%8] at vblk + g * (Npad/64) * 2 tpg 128.
-template <bool HALF>
+// TF32: V rounded to TF32, one part, [tile][col/8][K-core of 4 rows][col%8]
+// [row%4] (core matrices of 8 columns x 16 bytes; same tile size).
+template <bool HALF, bool TF32 = false>
 __device__ __forceinline__ void tc_split_v_body(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
                                                 const float* vscale, uint8_t* vblk, int64_t idx,
                                                 const float* lz_q = nullptr, const float* lz_sco = nullptr) {
@@ -248,23 +258,30 @@ __device__ __forceinline__ void tc_split_v_body(const float* V, int64_t ldv, int
 #pragma unroll
         for (int e = 0; e < 8; ++e) x[e] = 0.f;
     }
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) split_pair<HALF>(x[2 * e], x[2 * e + 1], h[e], l[e]);
     const int g = c / tpg, cl = c % tpg;
     const int64_t tile_bytes = 2 * (int64_t)tpg * 128;
     uint8_t* base = vblk + (int64_t)g * (Npad / kTcBN) * tile_bytes + (j0 / kTcBN) * tile_bytes;
     const int jj = (int)(j0 % kTcBN);
+    if (TF32) {
+        const int64_t o = (int64_t)(cl >> 3) * 2048 + (jj >> 2) * 128 + (cl & 7) * 16;
+        *reinterpret_cast<uint4*>(base + o) = make_uint4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
+        *reinterpret_cast<uint4*>(base + o + 128) =
+            make_uint4(to_tf32(x[4]), to_tf32(x[5]), to_tf32(x[6]), to_tf32(x[7]));
+        return;
+    }
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) split_pair<HALF>(x[2 * e], x[2 * e + 1], h[e], l[e]);
     const int64_t off = (int64_t)(cl >> 3) * 1024 + (jj >> 3) * 128 + (cl & 7) * 16;
     *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(base + (int64_t)tpg * 128 + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-template <bool HALF>
+template <bool HALF, bool TF32>
 __global__ void tc_split_v_kernel(const float* V, int64_t ldv, int T, int TP, int tpg, int64_t Npad,
                                   const float* vscale, uint8_t* vblk, const float* lz_q, const float* lz_sco) {
-    tc_split_v_body<HALF>(V, ldv, T, TP, tpg, Npad, vscale, vblk, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                          lz_q, lz_sco);
+    tc_split_v_body<HALF, TF32>(V, ldv, T, TP, tpg, Npad, vscale, vblk,
+                                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, lz_q, lz_sco);
 }
 
 // The kernel walks K's columns in steps of kTcKN = 128 (two 64-row operand
@@ -349,9 +366,19 @@ __device__ __forceinline__ float p_of_s(float S) {
 }
 
 // 16 values of S (one TMEM block of a row) -> P split into 8 packed leading
-// and 8 packed trailing 16-bit pairs.
-template <int KT, bool HALF>
+// and 8 packed trailing 16-bit pairs (TF32: the 16 values of P rounded to
+// TF32, the first 8 in hi and the last 8 in lo, so the block keeps its
+// column order).
+template <int KT, bool HALF, bool TF32 = false>
 __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi)[8], uint32_t (&lo)[8]) {
+    if (TF32) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            hi[e] = to_tf32(p_of_s<KT>(__uint_as_float(s[e])));
+            lo[e] = to_tf32(p_of_s<KT>(__uint_as_float(s[8 + e])));
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const float pa = p_of_s<KT>(__uint_as_float(s[2 * e]));
@@ -373,7 +400,7 @@ __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi
 // float pairs; tc_finish_body adds a tile's S partials in split order and
 // runs the epilogue, in a kernel of its own (one block per row tile) so
 // this kernel holds only the pipeline.
-template <int KT, int TP, bool HALF>
+template <int KT, int TP, bool HALF, bool TF32 = false>
 __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<float>& a, int c0, int64_t tile,
                                             int split) {
     // Stopped columns, or an earlier MVM of this call gave up a bounded wait
@@ -408,6 +435,7 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
     constexpr uint32_t IDESC_S = tc::idesc_f16(kTcBM, kTcKN, !HALF);
     constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
     constexpr uint32_t IDESC_O2 = tc::idesc_f16(kTcBM, 2 * TP, !HALF);
+    constexpr uint32_t IDESC_T = tc::idesc_tf32(kTcBM, TP);
 
     if (tid == 0) {
         tc::mbar_init(&bars[kBarU], 1);
@@ -540,7 +568,9 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                 good = uni(!*serr);
             }
         } else {
-            const uint64_t dV = tc::smem_desc(tc::smem_u32(sV0), 128, 1024);
+            // TF32: V's core matrices are 8 columns x 4 rows; 16 K-cores per
+            // group of 8 columns of a 64-row tile.
+            const uint64_t dV = tc::smem_desc(tc::smem_u32(sV0), 128, TF32 ? 2048 : 1024);
             for (int t = 0; good && t < nt; ++t) {
                 const int b = t % kNB, sv = t % NV;
                 const int ch = t / kTcChunk;
@@ -554,11 +584,19 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                 const uint32_t tP = tmem + b * kTcKN;
                 const uint64_t dv = dV + (uint64_t)((sv * VSTEP) >> 4);
                 if (tc::elect_one()) {
+                    if (TF32) {
 #pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const uint64_t vb = dv + (uint64_t)(((kk >> 2) * VHALF + (kk & 3) * 256) >> 4);
-                        tc::mma_f16_ts(tO0, tP + kk * 16, vb, IDESC_O2, (!fresh || kk > 0) ? 1u : 0u);   // P_hi [V_hi; V_lo]
-                        tc::mma_f16_ts(tO0, tP + kk * 16 + 8, vb, IDESC_O, 1u);                          // P_lo V_hi
+                        for (int kk = 0; kk < 16; ++kk) {   // K = 8 columns of P per MMA
+                            const uint64_t vb = dv + (uint64_t)(((kk >> 3) * VHALF + (kk & 7) * 256) >> 4);
+                            tc::mma_tf32_ts(tO0, tP + kk * 8, vb, IDESC_T, (!fresh || kk > 0) ? 1u : 0u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint64_t vb = dv + (uint64_t)(((kk >> 2) * VHALF + (kk & 3) * 256) >> 4);
+                            tc::mma_f16_ts(tO0, tP + kk * 16, vb, IDESC_O2, (!fresh || kk > 0) ? 1u : 0u);   // P_hi [V_hi; V_lo]
+                            tc::mma_f16_ts(tO0, tP + kk * 16 + 8, vb, IDESC_O, 1u);                          // P_lo V_hi
+                        }
                     }
                     tc::mma_commit(&bars[kBarODone + t % kRing]);
                 }
@@ -590,21 +628,21 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
             tc::tmem_ld16(tS, A);
             tc::tmem_wait_ld16(A);
             tc::tmem_ld16(tS + 16, B);
-            exp_block<KT, HALF>(A, h0, l0);
+            exp_block<KT, HALF, TF32>(A, h0, l0);
             tc::tmem_st8(tS, h0);
             tc::tmem_st8(tS + 8, l0);
             tc::tmem_wait_ld16(B);
             tc::tmem_ld16(tS + 32, A);
-            exp_block<KT, HALF>(B, h1, l1);
+            exp_block<KT, HALF, TF32>(B, h1, l1);
             tc::tmem_st8(tS + 16, h1);
             tc::tmem_st8(tS + 24, l1);
             tc::tmem_wait_ld16(A);
             tc::tmem_ld16(tS + 48, B);
-            exp_block<KT, HALF>(A, h2, l2);
+            exp_block<KT, HALF, TF32>(A, h2, l2);
             tc::tmem_st8(tS + 32, h2);
             tc::tmem_st8(tS + 40, l2);
             tc::tmem_wait_ld16(B);
-            exp_block<KT, HALF>(B, h3, l3);
+            exp_block<KT, HALF, TF32>(B, h3, l3);
             tc::tmem_st8(tS + 48, h3);
             tc::tmem_st8(tS + 56, l3);
             tc::tmem_wait_st64(h0, l0, h1, l1, h2, l2, h3, l3);
@@ -628,9 +666,9 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                     const int col0 = g * (TP / 2) + 16 * cb;
                     uint32_t oa[16], ob[16];
                     tc::tmem_ld16(tO0 + lane_base + col0, oa);
-                    tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
+                    if (!TF32) tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
                     tc::tmem_wait_ld16(oa);
-                    tc::tmem_wait_ld16(ob);
+                    if (!TF32) tc::tmem_wait_ld16(ob);
                     if (cb == HB - 1) {
                         tc::fence_before_sync();
                         tc::mbar_arrive(&bars[kBarOFree]);
@@ -642,7 +680,7 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                         float h = c > 0 ? *rh : 0.f;
                         float l = c > 0 ? *rl : 0.f;
                         two_sum_into(h, l, __uint_as_float(oa[e]));
-                        two_sum_into(h, l, __uint_as_float(ob[e]));
+                        if (!TF32) two_sum_into(h, l, __uint_as_float(ob[e]));
                         *rh = h;
                         *rl = l;
                     }
@@ -672,9 +710,9 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
             uint32_t oa[16], ob[16];
             if (ok) {
                 tc::tmem_ld16(tO0 + lane_base + col0, oa);
-                tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
+                if (!TF32) tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
                 tc::tmem_wait_ld16(oa);
-                tc::tmem_wait_ld16(ob);
+                if (!TF32) tc::tmem_wait_ld16(ob);
             }
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -686,7 +724,7 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
                 }
                 if (ok) {
                     two_sum_into(h, l, __uint_as_float(oa[e]));
-                    two_sum_into(h, l, __uint_as_float(ob[e]));
+                    if (!TF32) two_sum_into(h, l, __uint_as_float(ob[e]));
                 }
                 part[cl * kTcBM + r] = h + l;
             }
@@ -698,9 +736,9 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int KT, int TP, bool HALF>
+template <int KT, int TP, bool HALF, bool TF32>
 __global__ void __launch_bounds__(384, 1) mvm_tc_kernel(TcPoints p, MvmArgs<float> a, int c0) {
-    mvm_tc_body<KT, TP, HALF>(p, a, c0, blockIdx.x / p.nsplit, blockIdx.x % p.nsplit);
+    mvm_tc_body<KT, TP, HALF, TF32>(p, a, c0, blockIdx.x / p.nsplit, blockIdx.x % p.nsplit);
 }
 
 // ------------------------------------------------------------- finish --
@@ -908,13 +946,13 @@ cudaError_t set_smem_once(std::atomic<uint64_t>& done, F kernel, int smem) {
     return e;
 }
 
-template <int KT, int TP, bool HALF>
+template <int KT, int TP, bool HALF, bool TF32>
 cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaStream_t st) {
     constexpr int smem = tc_smem_bytes<TP>();
     static std::atomic<uint64_t> configured{0};
-    cudaError_t e0 = set_smem_once(configured, mvm_tc_kernel<KT, TP, HALF>, smem);
+    cudaError_t e0 = set_smem_once(configured, mvm_tc_kernel<KT, TP, HALF, TF32>, smem);
     if (e0 != cudaSuccess) return e0;
-    mvm_tc_kernel<KT, TP, HALF><<<(unsigned)(a.Npad / kTcBM * p.nsplit), 384, smem, st>>>(p, a, c0);
+    mvm_tc_kernel<KT, TP, HALF, TF32><<<(unsigned)(a.Npad / kTcBM * p.nsplit), 384, smem, st>>>(p, a, c0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     tc_finish_kernel<TP><<<(unsigned)(a.Npad / kTcBM * (TP / kFinCols)), 128, 0, st>>>(p, a, c0);
@@ -923,9 +961,17 @@ cudaError_t launch_tp(const TcPoints& p, const MvmArgs<float>& a, int c0, cudaSt
 
 template <int KT, bool HALF>
 cudaError_t launch_kt_half(const TcPoints& p, const MvmArgs<float>& a, int tpg, int c0, cudaStream_t st) {
+    if (p.tf32) {
+        if (!HALF) return cudaErrorInvalidValue;   // TF32 pairs with the FP16 point split
+        switch (tpg) {
+            case 32: return launch_tp<KT, 32, true, true>(p, a, c0, st);
+            case 64: return launch_tp<KT, 64, true, true>(p, a, c0, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (tpg) {
-        case 32: return launch_tp<KT, 32, HALF>(p, a, c0, st);
-        case 64: return launch_tp<KT, 64, HALF>(p, a, c0, st);
+        case 32: return launch_tp<KT, 32, HALF, false>(p, a, c0, st);
+        case 64: return launch_tp<KT, 64, HALF, false>(p, a, c0, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -933,7 +979,8 @@ cudaError_t launch_kt_half(const TcPoints& p, const MvmArgs<float>& a, int tpg, 
 }  // namespace
 
 bool tc_supported(int precision, int d) {
-    return (precision == CIQ_PREC_BF16 || precision == CIQ_PREC_FP16) && d >= 1 && d <= 14;
+    return (precision == CIQ_PREC_BF16 || precision == CIQ_PREC_FP16 || precision == CIQ_PREC_TF32) && d >= 1 &&
+           d <= 14;
 }
 
 // Columns of V per MVM launch group (T > 64 runs as groups of 64, which
@@ -998,7 +1045,8 @@ TcPoints tc_points_layout(char* base, int64_t Npad, int T, int precision, int ma
     p.narrow = d + 2 <= 8 ? 1 : 0;
     p.Npad = Npad;
     p.TP = tc_padded_t(T);
-    p.half = precision == CIQ_PREC_FP16 ? 1 : 0;
+    p.half = (precision == CIQ_PREC_FP16 || precision == CIQ_PREC_TF32) ? 1 : 0;
+    p.tf32 = precision == CIQ_PREC_TF32 ? 1 : 0;
     auto take = [&](size_t bytes) {
         char* q = base;
         base += (bytes + 255) / 256 * 256;
@@ -1045,14 +1093,16 @@ cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t work = (a.Npad / 8) * p.TP;
-    if (p.half)
-        tc_split_v_kernel<true><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a.V, a.ldv, a.T, p.TP,
-                                                                                 tc_group_t(a.T), a.Npad,
-                                                                                 p.vscale, p.vblk, a.lz_q, a.lz_sco);
+    const unsigned vblocks = (unsigned)((work + 255) / 256);
+    if (p.tf32)
+        tc_split_v_kernel<true, true><<<vblocks, 256, 0, st>>>(a.V, a.ldv, a.T, p.TP, tc_group_t(a.T), a.Npad,
+                                                               p.vscale, p.vblk, a.lz_q, a.lz_sco);
+    else if (p.half)
+        tc_split_v_kernel<true, false><<<vblocks, 256, 0, st>>>(a.V, a.ldv, a.T, p.TP, tc_group_t(a.T), a.Npad,
+                                                                p.vscale, p.vblk, a.lz_q, a.lz_sco);
     else
-        tc_split_v_kernel<false><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a.V, a.ldv, a.T, p.TP,
-                                                                                  tc_group_t(a.T), a.Npad,
-                                                                                  p.vscale, p.vblk, a.lz_q, a.lz_sco);
+        tc_split_v_kernel<false, false><<<vblocks, 256, 0, st>>>(a.V, a.ldv, a.T, p.TP, tc_group_t(a.T), a.Npad,
+                                                                 p.vscale, p.vblk, a.lz_q, a.lz_sco);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // V is split into groups of tpg columns; group g's tiles start at
     // vblk + g * (Npad / 64) * 2 * tpg * 128.

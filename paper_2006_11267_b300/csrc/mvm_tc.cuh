@@ -17,6 +17,7 @@ struct TcPoints {
     uint8_t* ua = nullptr;     // points as the M operand of S = U V^T   [Npad/8][3][2][8][8] 16-bit
     uint8_t* ub = nullptr;     // points as the N operand                 same layout
     uint8_t* vblk = nullptr;   // V split hi/lo, per 64-row tile          [Npad/64][2][TP/8][8][8][8]
+                               // (TF32: V rounded to TF32, per 64-row tile [Npad/64][TP/8][16][8][4])
     float* vscale = nullptr;   // power-of-two scale per column of V      [TP]
     double* mean = nullptr;    // centre of the points                    [16]
     int* err = nullptr;        // set to 1 if a bounded wait gave up
@@ -28,6 +29,7 @@ struct TcPoints {
     int64_t Npad = 0;
     int TP = 0;                // T rounded up to whole launch groups (32, 64 or k x 128)
     int half = 0;              // 1: FP16 operands; 0: BF16
+    int tf32 = 0;              // 1: the product P V on TF32 operands (no split; points still FP16 split)
 };
 
 bool tc_supported(int precision, int d);

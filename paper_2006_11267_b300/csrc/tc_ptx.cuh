@@ -10,7 +10,8 @@
 // matrices adjacent in K, SBO between core matrices adjacent in M/N.
 //
 // Instruction descriptor (kind::f16): [4,6) D format (1 = F32), [7,10) A
-// format, [10,13) B format (0 = F16, 1 = BF16), [15] A major, [16] B major
+// format, [10,13) B format (kind::f16: 0 = F16, 1 = BF16; kind::tf32: 2 =
+// TF32), [15] A major, [16] B major
 // (0 = K-major), [17,23) N >> 3, [24,29) M >> 4.
 #pragma once
 
@@ -132,6 +133,11 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
            ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::tf32 (A and B format 2 = TF32, D = F32,
+// both operands K-major).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 // D[tmem] (+)= A[smem desc] * B[smem desc]^T, one thread issues.
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
@@ -153,6 +159,16 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
         : "memory");
 }
 
+// D[tmem] (+)= A[tmem] * B[smem desc]^T with TF32 operands: A is M = 128
+// lanes by K = 8 32-bit columns of tensor memory.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // Arrive on `bar` once every tcgen05 operation issued so far by this thread completes.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

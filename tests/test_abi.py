@@ -114,6 +114,7 @@ def test_batched_validates_before_the_device():
          _ciq.CIQ_ERR_UNSUPPORTED),                                                # ... and T <= 64
         ([good], dict(mvm="stored"), _ciq.CIQ_ERR_UNSUPPORTED),
         ([good], dict(sqrt_form="mvm"), _ciq.CIQ_ERR_UNSUPPORTED),
+        ([good], dict(precision="tf32"), _ciq.CIQ_ERR_UNSUPPORTED),                # TF32 tiles: single problems only
         ([good], dict(max_iter=0), _ciq.CIQ_ERR_ARG),
         ([good, dict(X=X2, B=B2, kernel=k)], {}, _ciq.CIQ_ERR_ARG),                # T differs
         ([dict(X=X, B=B, kernel=k, lmin=2.0, lmax=1.0)], {}, _ciq.CIQ_ERR_ARG),   # lmax < lmin

@@ -20,7 +20,7 @@ import torch
 import ciq_inputs as ci
 import paper_2006_11267_b300 as P
 from oracle import eig, kernels
-from relerr import rel
+from relerr import colrel, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +41,31 @@ def test_tc_mvm_matches_oracle(prec, tol, n, d, t, kind, ls):
     ref = kernels.dense_K(X.astype(np.float64), kind, ls, 1.3, 1e-3) @ V.T.astype(np.float64)
     out = P.ciq_kernel_mvm(torch.from_numpy(X).cuda(), k, torch.from_numpy(V).cuda(), precision=prec)
     assert rel(out.cpu().numpy(), ref.T) < tol
+
+
+@pytest.mark.parametrize("n,d,t,kind,ls", [(1000, 3, 8, "rbf", 0.3), (1300, 6, 64, "rbf", 0.3),
+                                           (2000, 12, 33, "matern52", 0.5), (3001, 6, 100, "matern52", 0.2),
+                                           (129, 14, 1, "rbf", 1.0)])
+def test_tc_mvm_tf32_matches_oracle_within_the_rounding_bound(n, d, t, kind, ls):
+    # TF32 tiles: P and V rounded to TF32 (unit roundoff u = 2^-11), one
+    # product, FP32 accumulation.  Each term P_ij V_j carries a relative error
+    # of at most 2u + u^2, so row i of O is off by at most 2^-10 sum_j |K_ij| |V_j|
+    # (the sigma^2 V term is added unrounded): per column, ||err|| <= 2^-10
+    # || |K| |V| ||.  The distance tile (FP16 split, ~22 bits) and the FP32
+    # accumulation add about 1e-5 (the FP16-split mode's gate).
+    X = f32(ci.points(n + d + 7, n, d))
+    V = f32(ci.rhs(n + t + 7, n, t))
+    k = P.Kernel(kind, ls, 1.3, 1e-3)
+    K = kernels.dense_K(X.astype(np.float64), kind, ls, 1.3, 1e-3)
+    V64 = V.T.astype(np.float64)
+    ref = K @ V64
+    bound = 2.0 ** -10 * np.linalg.norm(np.abs(K) @ np.abs(V64), axis=0) / np.linalg.norm(ref, axis=0) + 1e-5
+    out = P.ciq_kernel_mvm(torch.from_numpy(X).cuda(), k, torch.from_numpy(V).cuda(), precision="tf32")
+    err = colrel(out.cpu().numpy(), ref.T)
+    assert np.all(err < bound), (err.max(), bound.min())
+    # TF32 is coarser than the FP16 split but far from noise: the error is
+    # at least a few times the FP16-split mode's.
+    assert err.max() > 1e-5
 
 
 def test_tc_mvm_fp16_small_lengthscale():
