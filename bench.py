@@ -717,24 +717,25 @@ def run_stored(args):
         torch.cuda.synchronize()
         form_ms = e0.elapsed_time(e1)
         res = {"form_ms": form_ms, "K_GB": 4.0 * npad * npad / 1e9}
-        for t in (1, 8, 64):
+        for t, prec in ((1, "fp32"), (8, "fp32"), (64, "fp32"), (1, "fp16"), (8, "fp16"), (64, "fp16")):
             V = torch.from_numpy(ci.rhs(W.seed + 3, n, t).astype(np.float32)).cuda()
             out = torch.empty_like(V)
             for _ in range(2):
-                P.ciq_stored_mvm(K, V, out)
+                P.ciq_stored_mvm(K, V, out, precision=prec)
             torch.cuda.synchronize()
             reps = 5
             e0.record()
             for _ in range(reps):
-                P.ciq_stored_mvm(K, V, out)
+                P.ciq_stored_mvm(K, V, out, precision=prec)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             nbytes = 4.0 * npad * npad + 4.0 * 2 * t * n
             gbs = nbytes / (ms * 1e-3) / 1e9
             flops = 2.0 * npad * npad * t
-            res[f"t{t}"] = {"ms": ms, "GB_s": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
-                            "TFLOP_s": flops / (ms * 1e-3) / 1e12}
+            key = f"t{t}" if prec == "fp32" else f"t{t}_fp16"
+            res[key] = {"ms": ms, "GB_s": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
+                        "TFLOP_s": flops / (ms * 1e-3) / 1e12}
         sizes[str(n)] = res
         del K
         torch.cuda.empty_cache()
@@ -749,24 +750,44 @@ def run_stored(args):
     e1.record()
     torch.cuda.synchronize()
     solve_ms = e0.elapsed_time(e1)
+    # The same solve with the stored K on tensor cores (FP16 split of K and
+    # V), and its MVM time per launch from the library's profile mode.
+    P.ciq_sqrt(X, k, B, W.q, 1e-3, stop_rule="errbound", max_iter=4000, mvm="stored", precision="fp16")
+    torch.cuda.synchronize()
+    e0.record()
+    _, info16 = P.ciq_sqrt(X, k, B, W.q, 1e-3, stop_rule="errbound", max_iter=4000, mvm="stored",
+                           precision="fp16")
+    e1.record()
+    torch.cuda.synchronize()
+    solve16_ms = e0.elapsed_time(e1)
+    _, infop = P.ciq_sqrt(X, k, B, W.q, 0.0, max_iter=40, lanczos_iters=10, mvm="stored", precision="fp16",
+                          profile=1)
+    mvm16_ms = infop["t_mvm_ms"] / max(1, infop["mvm_launches"])
     fp32_rate = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     if args.n:                    # a profiling case: the MVMs only
         print(json.dumps({"stored_only": args.n, "sizes": sizes}), flush=True)
         return 0
-    head = sizes["50000"]["t1"]
-    line = {"metric": "stored-K MVM HBM GB/s (one column, N=50,000)", "value": head["GB_s"], "unit": "GB/s",
-            "n_gpus": 1, "steps": 5, "warmup": 2, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    head = sizes["50000"]["t64_fp16"]
+    npad50 = -(-50000 // 128) * 128
+    line = {"metric": "stored-K MVM HBM GB/s (64 columns, N=50,000, tensor cores)", "value": head["GB_s"],
+            "unit": "GB/s", "n_gpus": 1, "steps": 5, "warmup": 2, "higher_is_better": True,
+            "dtype": "fp16x2 split K and V, f32 accumulation (the fp32 entries: f32 CUDA cores)", "data": "synthetic",
             "config": {"workload": f"stored_{W.name}", "N": [50000, 80000], "T": [1, 8, 64], "d": W.d,
                        "kernel": W.kernel, "l2": "no flush: K (10 / 25.6 GB) is far larger than L2"},
             "roofline": {"bound": "hbm", "achieved": head["GB_s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": head["frac_hbm"], "traffic": None,
-                         "kernel": "stored_narrow<1, 1> (one warp per row, float4 loads of K); T = 8 runs "
-                                   "stored_narrow<8, 4> (4 rows per warp), T = 64 stored_wide (FP32 FMA-bound)",
+                         "kernel": "stored_tc_kernel<64, FP16> (TMA boxes of K, split in TMEM, tcgen05 products); "
+                                   "the call also reads K's diagonal and synchronises once. In the solve: "
+                                   f"{mvm16_ms:.3f} ms per MVM = "
+                                   f"{4.0 * npad50 * npad50 / (mvm16_ms * 1e-3) / 1e9:.0f} GB/s of K",
                          "peak_source": f"{pk_kind} copy rate (MEASURED_PEAKS.json)",
-                         "t64_alu_peak_tflops": fp32_rate},
+                         "t64_fp32_alu_peak_tflops": fp32_rate},
             "sizes": sizes,
             "stored_solve": {"RHS_solves_per_s": W.t / (solve_ms * 1e-3), "ms": solve_ms, "iterations": info["iters"],
-                             "errbound_max": info["errbound_max"]}}
+                             "errbound_max": info["errbound_max"], "precision": "fp32"},
+            "stored_solve_fp16": {"RHS_solves_per_s": W.t / (solve16_ms * 1e-3), "ms": solve16_ms,
+                                  "iterations": info16["iters"], "errbound_max": info16["errbound_max"],
+                                  "mvm_ms_in_solve": mvm16_ms}}
     print(json.dumps(line), flush=True)
     return 0
 

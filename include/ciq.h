@@ -254,10 +254,16 @@ ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel*
 
 /* out = Kmat V for a matrix in the layout ciq_kernel_matrix writes (Npad
  * rows of ldk floats, zero padding).  V, out: device, T columns of N floats.
- * FP32 on CUDA cores, compensated accumulation; HBM-bound for T <= 16.
- * Asynchronous on stream. */
+ * precision CIQ_PREC_FP32: CUDA cores, compensated accumulation, HBM-bound
+ * for T <= 16.  CIQ_PREC_FP16 / BF16: tensor cores; K (read once by TMA,
+ * Kmat 16-byte aligned) is scaled by a power of two taken from its largest
+ * diagonal entry (which bounds every entry of a positive semidefinite K;
+ * entries beyond 2^15 times it overflow) and split into two 16-bit parts, V
+ * likewise (about 22 significant bits with FP16 parts); this call reads the
+ * diagonal maximum back to the host (it synchronises the stream once).
+ * CIQ_PREC_TF32: CIQ_ERR_UNSUPPORTED.  Asynchronous on stream otherwise. */
 ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T,
-                          float* out, ciq_stream_t stream);
+                          float* out, int precision, ciq_stream_t stream);
 
 /* K^{1/2} B and K^{-1/2} B for a caller's explicit symmetric positive
  * definite K: the general-matrix case of Sec. 3.3 (any K with an MVM; here

@@ -108,7 +108,7 @@ def lib() -> ctypes.CDLL:
         "ciq_kernel_mvm": (I, [P, I64, I, KP, P, I, P, I, P]),
         "ciq_kernel_mvm_f64": (I, [P, I64, I, KP, P, I, P, P]),
         "ciq_kernel_matrix": (I, [P, I64, I, KP, P, I64, P]),
-        "ciq_stored_mvm": (I, [P, I64, I64, P, I, P, P]),
+        "ciq_stored_mvm": (I, [P, I64, I64, P, I, P, I, P]),
         "ciq_sqrt_dense": (I, [P, I64, I64, P, I, I, D, OP, P, IP, P]),
         "ciq_invsqrt_vjp": (I, [P, I64, I, KP, P, P, I, I, D, OP, P, P, DP, IP, P]),
         "ciq_sqrt_vjp": (I, [P, I64, I, KP, P, P, I, I, D, OP, P, P, DP, IP, P]),
@@ -326,14 +326,16 @@ def ciq_kernel_matrix(X, kernel, Kmat):
     return Kmat
 
 
-def ciq_stored_mvm(Kmat, V, out=None, n=None):
+def ciq_stored_mvm(Kmat, V, out=None, n=None, precision="fp32"):
     """Kmat V for a matrix in the layout ciq_kernel_matrix writes
-    (round_up(N,128) rows of ldk floats); V and out are (T, N)."""
+    (round_up(N,128) rows of ldk floats); V and out are (T, N).  precision
+    "fp16"/"bf16": tensor cores (split operands)."""
     N = V.shape[1] if n is None else n
     T = V.shape[0]
     if out is None:
         out = V.new_empty(V.shape)
-    st = lib().ciq_stored_mvm(_ptr(Kmat), N, Kmat.shape[1], _ptr(V), T, _ptr(out), _stream(Kmat, V, out))
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    st = lib().ciq_stored_mvm(_ptr(Kmat), N, Kmat.shape[1], _ptr(V), T, _ptr(out), prec, _stream(Kmat, V, out))
     _check(st, "ciq_stored_mvm", allow=(CIQ_OK,))
     return out
 

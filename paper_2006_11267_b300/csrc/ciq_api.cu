@@ -124,6 +124,7 @@ struct Plan {
     int64_t rpc, rpc1;
     bool tc;                      // tensor-core MVM
     bool stored;                  // stored-K MVM (K formed once, Npad x Npad)
+    float kscale = 1.f;           // stored K on tensor cores: power-of-two scale of K
     int precision;
     bool stage_x, stage_b, stage_out, stage_start;
     bool prepass;
@@ -409,6 +410,8 @@ template <typename R>
 cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns, cudaStream_t st,
                        bool scale_ready) {
     if constexpr (sizeof(R) == 4) {
+        if (p.stored && p.tc)
+            return launch_stored_mvm_tc(p.Kst, p.Npad, p.tcp, a, p.kscale, unit_columns, st, scale_ready);
         if (p.tc) return launch_mvm_tc(p.tcp, a, unit_columns, st, scale_ready);
         if (p.stored) return launch_stored_mvm(p.Kst, p.Npad, a, st);
     }
@@ -582,7 +585,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         o.krylov = CIQ_KRYLOV_BASIS;
     }
     if ((o.quad_w == nullptr) != (o.quad_t == nullptr)) return CIQ_ERR_ARG;
-    if (o.mvm == CIQ_MVM_STORED && !fp64 && o.precision != CIQ_PREC_FP32) return CIQ_ERR_UNSUPPORTED;
+    if (o.mvm == CIQ_MVM_STORED && !fp64 && o.precision == CIQ_PREC_TF32) return CIQ_ERR_UNSUPPORTED;
     bool tc = false;
     if (!fp64 && o.precision != CIQ_PREC_FP32) {
         if (!tc_supported(o.precision, d) || tc_padded_t(T) < 0) return CIQ_ERR_UNSUPPORTED;
@@ -609,6 +612,8 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
 
     Plan<R> p = make_plan<R>(N, d, T, Q, o, prepass, tc, true);
     p.vjp = vjp;
+    // Stored K on tensor cores: max_i K_ii = outputscale + sigma^2 sets K's scale.
+    if (p.stored && p.tc) p.kscale = stored_tc_scale(kern->outputscale + kern->noise);
     if (pcs) {
         p.pc_rank = pcs->rank;
         p.stage_l = pcs->L && !device_accessible(pcs->L);
@@ -1737,15 +1742,25 @@ ciq_status ciq_kernel_matrix(const float* X, int64_t N, int d, const ciq_kernel*
 }
 
 ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float* V, int T, float* out,
-                          ciq_stream_t stream) {
+                          int precision, ciq_stream_t stream) {
     const int64_t Npad = round_up(N, kRowPad);
-    if (!Kmat || !V || !out || N < 1 || T < 1 || ldk < Npad || ldk % 4 != 0) return CIQ_ERR_ARG;
+    if (!Kmat || !V || !out || N < 1 || T < 1 || ldk < Npad || ldk % 4 != 0 || precision < CIQ_PREC_FP32 ||
+        precision > CIQ_PREC_FP16)
+        return CIQ_ERR_ARG;
+    const bool tc = precision != CIQ_PREC_FP32;
+    if (tc && (precision == CIQ_PREC_TF32 || tc_padded_t(T) < 0 || (reinterpret_cast<uintptr_t>(Kmat) & 15) != 0))
+        return CIQ_ERR_UNSUPPORTED;
     if (!device_accessible(Kmat) || !device_accessible(V) || !device_accessible(out)) return CIQ_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     keep_pool_warm();
-    float* Vp = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&Vp), sizeof(float) * (size_t)T * Npad, st);
+    // Zero-padded copy of V, and for the tensor cores the split-operand
+    // buffers and the largest diagonal entry (it sets K's power-of-two scale).
+    const size_t vbytes = round_up(sizeof(float) * (size_t)T * Npad, (size_t)kAlign);
+    const size_t tbytes = tc ? tc_points_bytes(Npad, T) + kAlign : 0;
+    char* base = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), vbytes + tbytes + kAlign, st);
     if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+    float* Vp = reinterpret_cast<float*>(base);
     e = cudaMemsetAsync(Vp, 0, sizeof(float) * (size_t)T * Npad, st);
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(Vp, sizeof(float) * Npad, V, sizeof(float) * N, sizeof(float) * N, T,
@@ -1760,9 +1775,20 @@ ciq_status ciq_stored_mvm(const float* Kmat, int64_t N, int64_t ldk, const float
         a.mode = kPlain;
         a.out = out;
         a.ldo = N;
-        e = launch_stored_mvm(Kmat, ldk, a, st);
+        if (!tc) {
+            e = launch_stored_mvm(Kmat, ldk, a, st);
+        } else {
+            TcPoints tp = tc_points_layout(base + vbytes, Npad, T, precision, 8, 1);
+            float* dmax = reinterpret_cast<float*>(base + vbytes + tbytes);
+            float hmax = 0.f;
+            e = cudaMemsetAsync(tp.err, 0, sizeof(int), st);
+            if (e == cudaSuccess) e = launch_stored_diag_max(Kmat, ldk, N, dmax, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hmax, dmax, sizeof(float), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) e = launch_stored_mvm_tc(Kmat, ldk, tp, a, stored_tc_scale(hmax), false, st);
+        }
     }
-    cudaFreeAsync(Vp, st);
+    cudaFreeAsync(base, st);
     if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
     return CIQ_OK;
 }

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <atomic>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -931,6 +932,311 @@ __global__ void __launch_bounds__(256) batched_tc_split_kernel(const BatchProble
     tc_split_v_body<HALF>(m.V, m.ldv, m.T, tpw, tpw, tp.Npad, tp.vscale, tp.vblk, (int64_t)local * 256 + threadIdx.x);
 }
 
+// ------------------------------------------------ stored K on tensor cores --
+// O = K V for a K held in device memory (FP32, row-major, leading dimension
+// ldk, padded rows and columns zero) on the product pipeline of the
+// on-the-fly MVM, with K's tile in place of P.  Every step's 128 x 64 tile
+// arrives by TMA as two 32-column boxes with the 128-byte swizzle (the
+// split warps read rows, which then fall in different banks); the split
+// warpgroups scale it by a power of two (so max_i K_ii, which bounds every
+// |K_ij| of a positive semidefinite K, sits at 2^14), split it into 16-bit
+// leading and trailing parts in a TMEM buffer and release the stage; the
+// product warp multiplies the buffer with the split V.  K is read from
+// device memory once per MVM.
+constexpr int kStKN = 64;                          // columns of K per step
+constexpr int kStKStages = 3;
+constexpr int kStKBytes = kTcBM * kStKN * 4;       // 32 KiB: two 16 KiB boxes
+constexpr int kStNB = 4;                           // P buffers of 64 TMEM columns
+constexpr int kStVStages = 3;
+template <int TP>
+__host__ __device__ constexpr int st_vstep_bytes() {
+    return 2 * TP * 128;                           // one 64-row tile of split V
+}
+// Steps per fold: the same 1,536 (TP = 64) or 512 columns as the on-the-fly kernel.
+template <int TP>
+__host__ __device__ constexpr int st_chunk() {
+    return TP <= 32 ? 8 : 24;
+}
+template <int TP>
+__host__ __device__ constexpr int st_smem_bytes() {
+    return 1024 + kStKStages * kStKBytes + kStVStages * st_vstep_bytes<TP>() + 2 * TP * kTcBM * 4 + 512;
+}
+enum StBar {
+    kSbKFull = 0,      // [3] tile of K landed
+    kSbKEmpty = 3,     // [3] the split warps have read the stage
+    kSbVFull = 6,      // [3] V of a step landed
+    kSbPFull = 9,      // [4] split K written to buffer b
+    kSbODone = 17,     // [8] product of step t complete
+    kSbOFree = 25,     // O accumulator read out for folding
+    kSbDrain = 26,     // every MMA complete (teardown)
+    kSbCount = 27
+};
+
+template <int TP, bool HALF>
+__global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcPoints p,
+                                                           MvmArgs<float> a, int c0, float kscale) {
+    __shared__ int skip_all;
+    if (threadIdx.x == 0) skip_all = (a.stop && *a.stop) || *p.err;
+    __syncthreads();
+    if (skip_all) return;
+    constexpr int VSTEP = st_vstep_bytes<TP>();
+    constexpr int C = st_chunk<TP>();
+    extern __shared__ __align__(1024) uint8_t st_smem[];
+    // The swizzled boxes need 1024-byte aligned stages (1024 bytes reserved).
+    uint8_t* sK = st_smem + ((1024u - (tc::smem_u32(st_smem) & 1023u)) & 1023u);
+    uint8_t* sV = sK + kStKStages * kStKBytes;
+    float* sR = reinterpret_cast<float*>(sV + kStVStages * VSTEP);   // running sum [2][TP][128]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sR + 2 * TP * kTcBM);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kSbCount);
+    volatile int* serr = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = p.nsplit;
+    const int64_t tile = blockIdx.x / S;
+    const int split = blockIdx.x % S;
+    const int64_t i0 = tile * kTcBM;
+    const int ntot = (int)(a.Npad / kStKN);
+    const int st0 = (int)((int64_t)split * ntot / S);
+    const int nt = (int)((int64_t)(split + 1) * ntot / S) - st0;   // steps of this CTA (>= 1)
+    const int nfold = (nt - 1) / C;
+    constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
+    constexpr uint32_t IDESC_O2 = tc::idesc_f16(kTcBM, 2 * TP, !HALF);
+
+    if (tid == 0) {
+        for (int s = 0; s < kStKStages; ++s) {
+            tc::mbar_init(&bars[kSbKFull + s], 1);
+            tc::mbar_init(&bars[kSbKEmpty + s], 256);
+        }
+        for (int s = 0; s < kStVStages; ++s) tc::mbar_init(&bars[kSbVFull + s], 1);
+        for (int b = 0; b < kStNB; ++b) tc::mbar_init(&bars[kSbPFull + b], 256);
+        for (int r = 0; r < kRing; ++r) tc::mbar_init(&bars[kSbODone + r], 1);
+        tc::mbar_init(&bars[kSbOFree], 256);
+        tc::mbar_init(&bars[kSbDrain], 1);
+        tc::fence_mbarrier_init();
+        *serr = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tO0 = tmem + kStNB * kStKN;            // O accumulator, 2 TP columns
+    auto uni = [&](bool b) { return __shfl_sync(0xffffffffu, (int)b, 0) != 0; };
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- loader
+        // The tile of step t goes to stage t % 3 once the split warps have
+        // read step t - 3; the V of step t once the product of t - 3 is done.
+        int nk = 0, nv = 0;
+        bool ok = true;
+        for (int t = 0; t < nt; ++t) {
+            const int sk = t % kStKStages, sv = t % kStVStages;
+            if (t >= kStKStages &&
+                !uni(tc::mbar_wait(&bars[kSbKEmpty + sk], (uint32_t)(((t - kStKStages) / kStKStages) & 1), kWaitLimit))) {
+                ok = false;
+                break;
+            }
+            const int x = (st0 + t) * kStKN;              // a multiple of 64 columns: 16-byte aligned
+            if (tc::elect_one()) {
+                tc::mbar_expect_tx(&bars[kSbKFull + sk], kStKBytes);
+                tc::tma_load_2d(sK + sk * kStKBytes, &tmap, x, (int)i0, &bars[kSbKFull + sk]);
+                tc::tma_load_2d(sK + sk * kStKBytes + kStKBytes / 2, &tmap, x + 32, (int)i0, &bars[kSbKFull + sk]);
+            }
+            __syncwarp();
+            ++nk;
+            if (t >= kStVStages &&
+                !uni(tc::mbar_wait(&bars[kSbODone + (t - kStVStages) % kRing],
+                                   (uint32_t)(((t - kStVStages) / kRing) & 1), kWaitLimit))) {
+                ok = false;
+                break;
+            }
+            if (tc::elect_one()) {
+                tc::mbar_expect_tx(&bars[kSbVFull + sv], VSTEP);
+                tc::bulk_g2s(sV + sv * VSTEP, p.vblk + (int64_t)(st0 + t) * VSTEP, VSTEP, &bars[kSbVFull + sv]);
+            }
+            __syncwarp();
+            ++nv;
+            if (uni(*serr)) break;
+        }
+        if (!ok && lane == 0) *serr = 1;
+        // No copy may land in shared memory after the CTA has left.
+        for (int u = max(nk - kStKStages, 0); u < nk; ++u)
+            tc::mbar_wait(&bars[kSbKFull + u % kStKStages], (uint32_t)((u / kStKStages) & 1), kWaitLimit);
+        for (int u = max(nv - kStVStages, 0); u < nv; ++u)
+            tc::mbar_wait(&bars[kSbVFull + u % kStVStages], (uint32_t)((u / kStVStages) & 1), kWaitLimit);
+        __syncwarp();
+    } else if (warp == 1) {
+        // --------------------------------------------------- product issuer
+        bool good = true;
+        const uint64_t dV = tc::smem_desc(tc::smem_u32(sV), 128, 1024);
+        for (int t = 0; good && t < nt; ++t) {
+            const int b = t % kStNB, sv = t % kStVStages;
+            const int ch = t / C;
+            const bool fresh = (t % C) == 0;
+            good = uni(tc::mbar_wait(&bars[kSbPFull + b], (uint32_t)((t / kStNB) & 1), kWaitLimit) &&
+                       tc::mbar_wait(&bars[kSbVFull + sv], (uint32_t)((t / kStVStages) & 1), kWaitLimit) &&
+                       (!fresh || ch < 1 || tc::mbar_wait(&bars[kSbOFree], (uint32_t)((ch - 1) & 1), kWaitLimit)));
+            if (!good) break;
+            tc::fence_after_sync();
+            const uint32_t tP = tmem + b * kStKN;
+            const uint64_t dv = dV + (uint64_t)((sv * VSTEP) >> 4);
+            if (tc::elect_one()) {
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t vb = dv + (uint64_t)((kk * 256) >> 4);
+                    tc::mma_f16_ts(tO0, tP + kk * 16, vb, IDESC_O2, (!fresh || kk > 0) ? 1u : 0u);   // K_hi [V_hi; V_lo]
+                    tc::mma_f16_ts(tO0, tP + kk * 16 + 8, vb, IDESC_O, 1u);                          // K_lo V_hi
+                }
+                tc::mma_commit(&bars[kSbODone + t % kRing]);
+            }
+            __syncwarp();
+            good = uni(!*serr);
+        }
+        if (!good && lane == 0) *serr = 1;
+        if (tc::elect_one()) tc::mma_commit(&bars[kSbDrain]);
+        __syncwarp();
+        tc::mbar_wait(&bars[kSbDrain], 0, kWaitLimit);
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ------------------------------------------------ split warpgroups
+        // Warpgroup g takes columns [32 g, 32 g + 32) of every step (box g);
+        // thread r takes row r of the tile (TMEM lane r).
+        const int g = (warp - 4) >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int r = 32 * (warp & 3) + lane;
+        for (int t = 0; t < nt; ++t) {
+            const int sk = t % kStKStages, b = t % kStNB;
+            bool good = tc::mbar_wait(&bars[kSbKFull + sk], (uint32_t)((t / kStKStages) & 1), kWaitLimit);
+            // Buffer b was last read by the product of step t - 4.
+            if (good && t >= kStNB)
+                good = tc::mbar_wait(&bars[kSbODone + (t - kStNB) % kRing], (uint32_t)(((t - kStNB) / kRing) & 1),
+                                     kWaitLimit);
+            if (__shfl_sync(0xffffffffu, (int)(!good || *serr), 0)) { *serr = 1; break; }
+            tc::fence_after_sync();
+            // Row r of box g: 16-byte chunk j of the row sits at chunk j ^ (r % 8).
+            const uint8_t* row = sK + sk * kStKBytes + g * (kStKBytes / 2) + r * 128;
+            float x[32];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 v = *reinterpret_cast<const float4*>(row + ((j ^ (r & 7)) << 4));
+                x[4 * j] = v.x * kscale;
+                x[4 * j + 1] = v.y * kscale;
+                x[4 * j + 2] = v.z * kscale;
+                x[4 * j + 3] = v.w * kscale;
+            }
+            tc::mbar_arrive(&bars[kSbKEmpty + sk]);
+            uint32_t h0[8], l0[8], h1[8], l1[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                split_pair<HALF>(x[2 * e], x[2 * e + 1], h0[e], l0[e]);
+                split_pair<HALF>(x[16 + 2 * e], x[17 + 2 * e], h1[e], l1[e]);
+            }
+            const uint32_t tS = tmem + b * kStKN + g * 32 + lane_base;
+            tc::tmem_st8(tS, h0);
+            tc::tmem_st8(tS + 8, l0);
+            tc::tmem_st8(tS + 16, h1);
+            tc::tmem_st8(tS + 24, l1);
+            tc::tmem_wait_st32(h0, l0, h1, l1);
+            tc::fence_before_sync();
+            tc::mbar_arrive(&bars[kSbPFull + b]);
+            // At the start of a chunk, fold the previous chunk of O into the
+            // running sum (half of the columns per warpgroup).
+            if (t >= C && (t % C) == 0) {
+                const int c = t / C - 1;
+                const int te = t - 1;
+                const bool okc = tc::mbar_wait(&bars[kSbODone + te % kRing], (uint32_t)((te / kRing) & 1), kWaitLimit);
+                if (__shfl_sync(0xffffffffu, (int)(!okc || *serr), 0)) { *serr = 1; break; }
+                tc::fence_after_sync();
+                constexpr int HB = TP / 2 / 16;
+#pragma unroll 1
+                for (int cb = 0; cb < HB; ++cb) {
+                    const int col0 = g * (TP / 2) + 16 * cb;
+                    uint32_t oa[16], ob[16];
+                    tc::tmem_ld16(tO0 + lane_base + col0, oa);
+                    tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
+                    tc::tmem_wait_ld16(oa);
+                    tc::tmem_wait_ld16(ob);
+                    if (cb == HB - 1) {
+                        tc::fence_before_sync();
+                        tc::mbar_arrive(&bars[kSbOFree]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        float* rh = sR + (col0 + e) * kTcBM + r;
+                        float* rl = rh + TP * kTcBM;
+                        float h = c > 0 ? *rh : 0.f;
+                        float l = c > 0 ? *rl : 0.f;
+                        two_sum_into(h, l, __uint_as_float(oa[e]));
+                        two_sum_into(h, l, __uint_as_float(ob[e]));
+                        *rh = h;
+                        *rl = l;
+                    }
+                }
+            }
+        }
+    }
+
+    // ------------------------------------------------------- partial sums
+    if (warp >= 4) {
+        const int g = (warp - 4) >> 2;
+        const int r = 32 * (warp & 3) + lane;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const bool good = !*serr && tc::mbar_wait(&bars[kSbODone + (nt - 1) % kRing],
+                                                  (uint32_t)(((nt - 1) / kRing) & 1), kWaitLimit);
+        const bool ok = !__shfl_sync(0xffffffffu, (int)(!good || *serr), 0);
+        if (!ok) *serr = 1;
+        tc::fence_after_sync();
+        float* part = p.part + ((int64_t)tile * S + split) * TP * kTcBM;
+#pragma unroll 1
+        for (int cb = 0; cb < TP / 32; ++cb) {
+            const int col0 = g * (TP / 2) + 16 * cb;
+            uint32_t oa[16], ob[16];
+            if (ok) {
+                tc::tmem_ld16(tO0 + lane_base + col0, oa);
+                tc::tmem_ld16(tO0 + TP + lane_base + col0, ob);
+                tc::tmem_wait_ld16(oa);
+                tc::tmem_wait_ld16(ob);
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int cl = col0 + e;
+                float h = 0.f, l = 0.f;
+                if (ok && nfold > 0) {
+                    h = sR[cl * kTcBM + r];
+                    l = sR[(TP + cl) * kTcBM + r];
+                }
+                if (ok) {
+                    two_sum_into(h, l, __uint_as_float(oa[e]));
+                    two_sum_into(h, l, __uint_as_float(ob[e]));
+                }
+                part[cl * kTcBM + r] = h + l;
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && *serr) atomicExch(p.err, 1);
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// Largest diagonal entry of K (bounds every |K_ij| of a PSD matrix), one block.
+__global__ void stored_diag_max_kernel(const float* Kmat, int64_t ldk, int64_t N, float* out) {
+    __shared__ float red[8];
+    float m = 0.f;
+    for (int64_t i = threadIdx.x; i < N; i += 256) m = fmaxf(m, fabsf(Kmat[i * ldk + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+        out[0] = fmaxf(m, red[0]);
+    }
+}
+
 // A kernel's shared-memory attribute is set once per device (the attribute
 // belongs to the device that is current when it is set); `done` holds one
 // bit per device id.
@@ -1115,6 +1421,97 @@ cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_
         else
             e = p.half ? launch_kt_half<CIQ_MATERN52, true>(pg, a, tpg, c0, st)
                        : launch_kt_half<CIQ_MATERN52, false>(pg, a, tpg, c0, st);
+    }
+    return e;
+}
+
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+template <int TP, bool HALF>
+cudaError_t launch_st_tp(const CUtensorMap& tmap, const TcPoints& p, const MvmArgs<float>& a, int c0, float kscale,
+                         cudaStream_t st) {
+    constexpr int smem = st_smem_bytes<TP>();
+    static std::atomic<uint64_t> configured{0};
+    cudaError_t e0 = set_smem_once(configured, stored_tc_kernel<TP, HALF>, smem);
+    if (e0 != cudaSuccess) return e0;
+    stored_tc_kernel<TP, HALF><<<(unsigned)(a.Npad / kTcBM * p.nsplit), 384, smem, st>>>(tmap, p, a, c0, kscale);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tc_finish_kernel<TP><<<(unsigned)(a.Npad / kTcBM * (TP / kFinCols)), 128, 0, st>>>(p, a, c0);
+    return cudaGetLastError();
+}
+}  // namespace
+
+float stored_tc_scale(double max_diag) {
+    if (!(max_diag > 0.0) || !std::isfinite(max_diag)) return 1.f;
+    return ldexpf(1.f, 14 - (int)ceil(log2(max_diag)));
+}
+
+cudaError_t launch_stored_diag_max(const float* Kmat, int64_t ldk, int64_t N, float* out, cudaStream_t st) {
+    stored_diag_max_kernel<<<1, 256, 0, st>>>(Kmat, ldk, N, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stored_mvm_tc(const float* Kmat, int64_t ldk, const TcPoints& p, const MvmArgs<float>& args,
+                                 float kscale, bool unit_columns, cudaStream_t st, bool scale_ready) {
+    if (p.TP < 0 || p.tf32 || args.T > p.TP || args.Npad != p.Npad || args.ldv != args.Npad || ldk % 4 != 0 ||
+        ldk < args.Npad || args.Npad % kTcBM != 0 || (reinterpret_cast<uintptr_t>(Kmat) & 15) != 0 || !(kscale > 0.f))
+        return cudaErrorInvalidValue;
+    MvmArgs<float> a = args;
+    a.noise = 0.f;              // the stored matrix holds sigma^2 on its diagonal
+    a.s = 1.f / kscale;         // exact: kscale is a power of two
+    cudaError_t e = cudaSuccess;
+    if (!(unit_columns && scale_ready)) {
+        const float unit_scale = ldexpf(1.f, (int)floor(0.5 * log2((double)a.N)));
+        tc_vscale_kernel<<<p.TP, 256, 0, st>>>(a.V, a.ldv, a.N, a.T, p.TP, unit_scale, unit_columns ? 1 : 0,
+                                               p.vscale);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int64_t work = (a.Npad / 8) * p.TP;
+    const unsigned vblocks = (unsigned)((work + 255) / 256);
+    if (p.half)
+        tc_split_v_kernel<true, false><<<vblocks, 256, 0, st>>>(a.V, a.ldv, a.T, p.TP, tc_group_t(a.T), a.Npad,
+                                                                p.vscale, p.vblk, a.lz_q, a.lz_sco);
+    else
+        tc_split_v_kernel<false, false><<<vblocks, 256, 0, st>>>(a.V, a.ldv, a.T, p.TP, tc_group_t(a.T), a.Npad,
+                                                                 p.vscale, p.vblk, a.lz_q, a.lz_sco);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // K as a 2-D tensor of Npad x Npad floats, row pitch ldk floats; boxes of
+    // 32 columns x 128 rows with the 128-byte swizzle.
+    // The driver's encoder is reached through the runtime (the library does
+    // not link the driver library).
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return cudaErrorNotSupported;
+        }
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    CUtensorMap tmap;
+    const cuuint64_t dims[2] = {(cuuint64_t)a.Npad, (cuuint64_t)a.Npad};
+    const cuuint64_t pitch[1] = {(cuuint64_t)ldk * sizeof(float)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)kTcBM};
+    const cuuint32_t estride[2] = {1, 1};
+    if (encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Kmat), dims, pitch, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const int tpg = tc_group_t(a.T);
+    for (int c0 = 0; c0 < a.T && e == cudaSuccess; c0 += tpg) {
+        TcPoints pg = p;
+        pg.vblk = p.vblk + (size_t)(c0 / tpg) * (size_t)(a.Npad / kTcBN) * 2 * tpg * 128;
+        if (tpg == 32) e = p.half ? launch_st_tp<32, true>(tmap, pg, a, c0, kscale, st)
+                                  : launch_st_tp<32, false>(tmap, pg, a, c0, kscale, st);
+        else e = p.half ? launch_st_tp<64, true>(tmap, pg, a, c0, kscale, st)
+                        : launch_st_tp<64, false>(tmap, pg, a, c0, kscale, st);
     }
     return e;
 }

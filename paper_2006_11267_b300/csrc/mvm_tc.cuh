@@ -52,4 +52,16 @@ cudaError_t launch_tc_prepare(const TcPoints& p, const float* Xp, int64_t N, int
 cudaError_t launch_mvm_tc(const TcPoints& p, const MvmArgs<float>& a, bool unit_columns, cudaStream_t st,
                           bool scale_ready = false);
 
+// Stored K on tensor cores: O = K V with K (Npad x Npad floats, row pitch ldk,
+// ldk % 4 == 0, 16-byte aligned, padded rows and columns 0) streamed by TMA,
+// scaled by kscale (a power of two from stored_tc_scale(max_i K_ii), which
+// bounds |K_ij| for a positive semidefinite K) and split into FP16 (p.half)
+// or BF16 parts, V split as for launch_mvm_tc; p from tc_points_layout (the
+// points are not used; p.err must be clear).  The epilogue of `a`, its noise
+// term ignored (the stored matrix holds sigma^2).
+float stored_tc_scale(double max_diag);
+cudaError_t launch_stored_diag_max(const float* Kmat, int64_t ldk, int64_t N, float* out, cudaStream_t st);
+cudaError_t launch_stored_mvm_tc(const float* Kmat, int64_t ldk, const TcPoints& p, const MvmArgs<float>& a,
+                                 float kscale, bool unit_columns, cudaStream_t st, bool scale_ready = false);
+
 }  // namespace ciq

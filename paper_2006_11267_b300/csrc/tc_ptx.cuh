@@ -93,6 +93,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Tiled 2-D tensor copy global -> shared (TMA) completing on an mbarrier:
+// the box at element coordinates (x, y) of the tensor map `tmap` (a kernel
+// parameter in the constant bank).  x times the element size must be a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -242,6 +253,16 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
 // Wait for this thread's outstanding TMEM stores.  The 64 source words of
 // the stores are in-out operands, so the compiler keeps their registers
 // untouched until every store has completed.
+__device__ __forceinline__ void tmem_wait_st32(uint32_t (&a)[8], uint32_t (&b)[8], uint32_t (&c)[8],
+                                               uint32_t (&d)[8]) {
+    asm volatile("tcgen05.wait::st.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                   "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]),
+                   "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7])
+                 :
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st64(uint32_t (&a)[8], uint32_t (&b)[8], uint32_t (&c)[8], uint32_t (&d)[8],
                                                uint32_t (&e)[8], uint32_t (&f)[8], uint32_t (&g)[8],
                                                uint32_t (&h)[8]) {

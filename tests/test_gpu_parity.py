@@ -27,7 +27,7 @@ import paper_2006_11267_b300 as P
 from oracle import ciq as O
 from oracle import eig, kernels
 from oracle.lanczos import lanczos, ritz_extremes
-from relerr import fp32_gate, rel
+from relerr import colrel, fp32_gate, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -283,6 +283,66 @@ def test_stored_mvm_matches_oracle(n, t):
     out = P.ciq_stored_mvm(Kd, torch.from_numpy(V).to(DEV), n=n)
     ref = dense_K(X, k) @ V.T.astype(np.float64)
     assert rel(out.cpu().numpy(), ref.T) < 2e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 2e-5), ("bf16", 1e-4)])
+@pytest.mark.parametrize("n,t", [(1, 1), (300, 8), (777, 5), (1000, 17), (3001, 64), (513, 70), (2000, 128)])
+def test_stored_mvm_tensor_cores_matches_oracle(prec, tol, n, t):
+    # K streamed by TMA (ragged edges are the stored matrix's zero padding),
+    # scaled by a power of two and split into two 16-bit parts, as is V:
+    # per column the FP16 split keeps about 22 significant bits (the on-the-fly
+    # tensor-core MVM's 2e-5 gate), BF16 about 16 (1e-4).
+    X, V, k = problem(n, 4, t, 170 + n + t, "rbf", ls=0.3, s=1.3, noise=1e-3)
+    npad = _npad(n)
+    Kd = torch.empty((npad, npad), device=DEV)
+    P.ciq_kernel_matrix(torch.from_numpy(X).to(DEV), k, Kd)
+    out = P.ciq_stored_mvm(Kd, torch.from_numpy(V).to(DEV), n=n, precision=prec)
+    ref = dense_K(X, k) @ V.T.astype(np.float64)
+    assert rel(out.cpu().numpy(), ref.T) < tol
+
+
+def test_stored_mvm_tensor_cores_general_psd_matrix_and_pitch():
+    # A caller's positive definite matrix with a prescribed spectrum (not a
+    # kernel matrix: entries of both signs, diagonal far from 1) in a pitched
+    # layout (ldk > Npad): the scale taken from the diagonal keeps every
+    # entry in range.
+    n, t = 1500, 24
+    rng = np.random.default_rng(5)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.geomspace(1e-2, 3e3, n)
+    K = (Qm * lam) @ Qm.T
+    npad = _npad(n)
+    Kp = np.zeros((npad, npad + 8), np.float32)
+    Kp[:n, :n] = K
+    V = rng.standard_normal((t, n)).astype(np.float32)
+    out = P.ciq_stored_mvm(torch.from_numpy(Kp).to(DEV), torch.from_numpy(V).to(DEV), n=n, precision="fp16")
+    K32 = K.astype(np.float32).astype(np.float64)
+    V64 = V.T.astype(np.float64)
+    ref = K32 @ V64
+    # Each split entry is within 2^-22 of the FP32 value and the three
+    # products are exact in FP32: per column the error is a few 2^-22
+    # || |K| |V| || (entries of both signs cancel in K V) plus the FP32
+    # accumulation (about 1e-6 of the result, folded every 1,536 columns).
+    bound = 8 * 2.0 ** -22 * np.linalg.norm(np.abs(K32) @ np.abs(V64), axis=0) / np.linalg.norm(ref, axis=0) + 2e-6
+    err = colrel(out.cpu().numpy(), ref.T)
+    assert np.all(err < bound), (err.max(), bound.min())
+
+
+@pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
+def test_stored_k_tensor_core_solve_matches_on_the_fly_tensor_core_solve(op):
+    # The same FP16-split arithmetic on K's entries either way (stored K is
+    # formed with the accurate exponential, the on-the-fly tile from the
+    # split distances): both solves agree within the FP16-split MVM error.
+    X, B, k = problem(2500, 3, 16, 991, "matern52", ls=0.25)
+    fn = P.ciq_sqrt if op == "sqrt" else P.ciq_invsqrt
+    Xd, Bd = torch.from_numpy(X).to(DEV), torch.from_numpy(B).to(DEV)
+    a, ia = fn(Xd, k, Bd, 10, 1e-6, max_iter=1500, precision="fp16", mvm="stored", stop_rule="errbound")
+    b, ib = fn(Xd, k, Bd, 10, 1e-6, max_iter=1500, precision="fp16", stop_rule="errbound")
+    assert ia["status"] == 0 and ib["status"] == 0
+    # Both are within the FP16-split mode's 1e-3 of the exact root; their
+    # MVMs differ by a few 1e-6 (accurate expf against ex2.approx of the
+    # split distances), amplified by the root's conditioning.
+    assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-3
 
 
 @pytest.mark.parametrize("op", ["sqrt", "invsqrt"])
