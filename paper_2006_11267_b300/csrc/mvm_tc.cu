@@ -263,19 +263,19 @@ __device__ __forceinline__ void tc_split_v_body(const float* V, int64_t ldv, int
     const int64_t tile_bytes = 2 * (int64_t)tpg * 128;
     uint8_t* base = vblk + (int64_t)g * (Npad / kTcBN) * tile_bytes + (j0 / kTcBN) * tile_bytes;
     const int jj = (int)(j0 % kTcBN);
-    if (TF32) {
+    if constexpr (TF32) {
         const int64_t o = (int64_t)(cl >> 3) * 2048 + (jj >> 2) * 128 + (cl & 7) * 16;
         *reinterpret_cast<uint4*>(base + o) = make_uint4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
         *reinterpret_cast<uint4*>(base + o + 128) =
             make_uint4(to_tf32(x[4]), to_tf32(x[5]), to_tf32(x[6]), to_tf32(x[7]));
-        return;
-    }
-    uint32_t h[4], l[4];
+    } else {
+        uint32_t h[4], l[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) split_pair<HALF>(x[2 * e], x[2 * e + 1], h[e], l[e]);
-    const int64_t off = (int64_t)(cl >> 3) * 1024 + (jj >> 3) * 128 + (cl & 7) * 16;
-    *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(base + (int64_t)tpg * 128 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        for (int e = 0; e < 4; ++e) split_pair<HALF>(x[2 * e], x[2 * e + 1], h[e], l[e]);
+        const int64_t off = (int64_t)(cl >> 3) * 1024 + (jj >> 3) * 128 + (cl & 7) * 16;
+        *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(base + (int64_t)tpg * 128 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
 }
 
 template <bool HALF, bool TF32>
@@ -372,19 +372,19 @@ __device__ __forceinline__ float p_of_s(float S) {
 // column order).
 template <int KT, bool HALF, bool TF32 = false>
 __device__ __forceinline__ void exp_block(const uint32_t (&s)[16], uint32_t (&hi)[8], uint32_t (&lo)[8]) {
-    if (TF32) {
+    if constexpr (TF32) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             hi[e] = to_tf32(p_of_s<KT>(__uint_as_float(s[e])));
             lo[e] = to_tf32(p_of_s<KT>(__uint_as_float(s[8 + e])));
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const float pa = p_of_s<KT>(__uint_as_float(s[2 * e]));
-        const float pb = p_of_s<KT>(__uint_as_float(s[2 * e + 1]));
-        split_pair<HALF>(pa, pb, hi[e], lo[e]);
+        for (int e = 0; e < 8; ++e) {
+            const float pa = p_of_s<KT>(__uint_as_float(s[2 * e]));
+            const float pb = p_of_s<KT>(__uint_as_float(s[2 * e + 1]));
+            split_pair<HALF>(pa, pb, hi[e], lo[e]);
+        }
     }
 }
 
@@ -427,7 +427,6 @@ __device__ __forceinline__ void mvm_tc_body(const TcPoints& p, const MvmArgs<flo
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = p.nsplit;
-    const int64_t i0 = tile * kTcBM;
     const int ntot = (int)(a.Npad / kTcKN);
     const int st0 = (int)((int64_t)split * ntot / S);
     const int nt = (int)((int64_t)(split + 1) * ntot / S) - st0;   // steps of this CTA (>= 1)
