@@ -26,10 +26,9 @@ namespace ciq {
 
 namespace {
 
-constexpr int kRedRT = 64;      // r (basis column) tile of the reduction
+constexpr int kRedRT = 128;     // r (basis column) tile of the reduction
 constexpr int kRedTT = 64;      // t (right-hand side) tile
 constexpr int kRedSub = 32;     // rows per shared-memory stage
-constexpr int kRedLd = 68;      // padded row of the shared tiles (16-byte aligned)
 
 int64_t chunk_rows(int64_t Npad, int R, int T) {
     // Row chunks for one wave of three blocks per SM (148 SMs), each chunk at
@@ -76,73 +75,102 @@ __device__ __forceinline__ FPair pair_warp_sum(FPair a) {
     return a;
 }
 
-// cpart[chunk][r][t] = sum over the chunk's rows of Qh[r][i] X[t][i].
-__global__ void __launch_bounds__(256, 3) pc_reduce(PrecondState pc, const float* X, int64_t ldx, int T,
+// cpart[chunk][t][r] = sum over the chunk's rows of Qh[r][i] X[t][i].  A block
+// takes a 128 (r) x 64 (t) tile of one row chunk with 128 threads, each an
+// 8 x 8 register tile (64 FMAs per 16 floats read from shared memory); the
+// next 32-row stage is loaded into registers while the current one is
+// multiplied.
+__global__ void __launch_bounds__(128, 3) pc_reduce(PrecondState pc, const float* X, int64_t ldx, int T,
                                                     int64_t rows_per_chunk, const int* stop) {
     if (stop && *stop) return;
-    constexpr int M = (kRedRT * kRedSub) / 256;           // elements per thread and stage, per operand
-    __shared__ __align__(16) float As[kRedSub][kRedLd];
-    __shared__ __align__(16) float Bs[kRedSub][kRedLd];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    constexpr int LA = kRedRT + 4, LB = kRedTT + 4;        // padded rows (16-byte aligned)
+    __shared__ __align__(16) float As[kRedSub][LA];
+    __shared__ __align__(16) float Bs[kRedSub][LB];
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
     const int r0 = blockIdx.x * kRedRT, t0 = blockIdx.y * kRedTT;
     const int64_t i_begin = (int64_t)blockIdx.z * rows_per_chunk;
     const int64_t i_end = min(i_begin + rows_per_chunk, pc.Npad);
-    float acc[4][4] = {};
-    // Stage s + 1 is loaded into registers while stage s is multiplied.
-    float na[M], nb[M];
+    float acc[8][8] = {};
+    // Per stage: 128 r x 32 rows of Qh (8 float4 per thread, 8 threads per
+    // 128-byte row segment) and 64 t x 32 rows of X (4 float4 per thread).
+    float4 na[8], nb[4];
     auto load = [&](int64_t i0) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const int e = tid + 256 * m;
-            const int ii = e & (kRedSub - 1), rr = e / kRedSub;
-            const int64_t i = i0 + ii;
-            const int r = r0 + rr, t = t0 + rr;
-            na[m] = (r < pc.rank && i < i_end) ? pc.Qh[(int64_t)r * pc.Npad + i] : 0.f;
-            nb[m] = (t < T && i < pc.N) ? X[(int64_t)t * ldx + i] : 0.f;
+        for (int m = 0; m < 8; ++m) {
+            const int e = tid + 128 * m;
+            const int q4 = e & 7, rr = e >> 3;
+            const int r = r0 + rr;
+            const int64_t i = i0 + 4 * q4;                  // i_end and Npad are multiples of 4
+            na[m] = (r < pc.rank && i < i_end) ? *reinterpret_cast<const float4*>(pc.Qh + (int64_t)r * pc.Npad + i)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = tid + 128 * m;
+            const int q4 = e & 7, tt = e >> 3;
+            const int t = t0 + tt;
+            const int64_t i = i0 + 4 * q4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < T && i < i_end) {
+                const float* src = X + (int64_t)t * ldx + i;
+                v.x = i < pc.N ? src[0] : 0.f;
+                v.y = i + 1 < pc.N ? src[1] : 0.f;
+                v.z = i + 2 < pc.N ? src[2] : 0.f;
+                v.w = i + 3 < pc.N ? src[3] : 0.f;
+            }
+            nb[m] = v;
         }
     };
     if (i_begin < i_end) load(i_begin);
     for (int64_t i0 = i_begin; i0 < i_end; i0 += kRedSub) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const int e = tid + 256 * m;
-            const int ii = e & (kRedSub - 1), rr = e / kRedSub;
-            As[ii][rr] = na[m];
-            Bs[ii][rr] = nb[m];
+        for (int m = 0; m < 8; ++m) {
+            const int e = tid + 128 * m;
+            const int q4 = e & 7, rr = e >> 3;
+            As[4 * q4][rr] = na[m].x;
+            As[4 * q4 + 1][rr] = na[m].y;
+            As[4 * q4 + 2][rr] = na[m].z;
+            As[4 * q4 + 3][rr] = na[m].w;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = tid + 128 * m;
+            const int q4 = e & 7, tt = e >> 3;
+            Bs[4 * q4][tt] = nb[m].x;
+            Bs[4 * q4 + 1][tt] = nb[m].y;
+            Bs[4 * q4 + 2][tt] = nb[m].z;
+            Bs[4 * q4 + 3][tt] = nb[m].w;
         }
         __syncthreads();
         if (i0 + kRedSub < i_end) load(i0 + kRedSub);
-#pragma unroll 8
+#pragma unroll 4
         for (int ii = 0; ii < kRedSub; ++ii) {
-            const float4 a = *reinterpret_cast<const float4*>(&As[ii][ty * 4]);
-            const float4 b = *reinterpret_cast<const float4*>(&Bs[ii][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[ii][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[ii][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[ii][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[ii][tx * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
         }
         __syncthreads();
     }
     float* dst = pc.cpart + (int64_t)blockIdx.z * pc.rank * T;      // [chunk][t][r]
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int r = r0 + ty * 4 + u;
-        if (r >= pc.rank) continue;
+    for (int v = 0; v < 8; ++v) {
+        const int t = t0 + tx * 8 + v;
+        if (t >= T) break;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int t = t0 + tx * 4 + v;
-            if (t < T) dst[(int64_t)t * pc.rank + r] = acc[u][v];
+        for (int u = 0; u < 8; ++u) {
+            const int r = r0 + ty * 8 + u;
+            if (r < pc.rank) dst[(int64_t)t * pc.rank + r] = acc[u][v];
         }
     }
 }
 
-// coef[r][t] = g[r] * sum over chunks (FP64, fixed order); one block per
-// column t.  vscale (optional, inverse root of a unit column v only): the
-// power-of-two operand scale the tensor-core MVM takes for U = P^{-1/2} v,
-// from ||U||^2 = sigma^{-2} + sum_r (g_r^2 + 2 g_r / sigma) (Qh^T v)_r^2 (the
-// formula of its own scale kernel, without another pass over U); columns
-// [T, TP) get the scale of a unit column.
 __global__ void __launch_bounds__(256) pc_coef(PrecondState pc, int T, int nchunks, bool inverse_root,
                                                float* vscale, int TP, const int* stop) {
     if (stop && *stop) return;
@@ -184,82 +212,131 @@ __global__ void pc_unit_scale(PrecondState pc, int T, int TP, float* vscale, con
 // out[t][i] = alpha X[t][i] + sum_r Qh[r][i] coef[r][t] over a 128-row tile
 // and 64 columns; LANCZOS: p = out - beta_t qprev[t][i] with partial sums.
 template <bool LANCZOS>
-__global__ void __launch_bounds__(256, 3) pc_expand(PrecondState pc, const float* X, int64_t ldx, int T, float alpha,
+__global__ void __launch_bounds__(128, 3) pc_expand(PrecondState pc, const float* X, int64_t ldx, int T, float alpha,
                                                  float* out, int64_t ldo, const float* q, float* qprev,
                                                  float* pout, const double* beta, double* partials,
                                                  const int* stop) {
+    // A 128-row x 64-column tile of alpha X + Qh C with 128 threads, each 8
+    // rows x 8 columns (64 FMAs per 16 floats read from shared memory); the
+    // next 32 basis columns are loaded into registers while the current ones
+    // are multiplied.
     if (stop && *stop) return;
     constexpr int RT = 32;
     __shared__ __align__(16) float Qs[RT][128];
     __shared__ __align__(16) float Cs[RT][64];
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    __shared__ double red[4][8][3];
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3, lane = tid & 31, warp = tid >> 5;
     const int64_t i0 = (int64_t)blockIdx.x * 128;
     const int t0 = blockIdx.y * 64;
-    float acc[4][8] = {};
+    float acc[8][8] = {};
+    float4 nq[8], nc[4];
+    auto load = [&](int r0) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int e = tid + 128 * m;
+            const int q4 = e & 31, rr = e >> 5;
+            const int r = r0 + rr;
+            nq[m] = r < pc.rank ? *reinterpret_cast<const float4*>(pc.Qh + (int64_t)r * pc.Npad + i0 + 4 * q4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = tid + 128 * m;
+            const int q4 = e & 15, rr = e >> 4;
+            const int r = r0 + rr;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < pc.rank) {
+                const float* src = pc.coef + (int64_t)r * T + t0 + 4 * q4;
+                const int tb = t0 + 4 * q4;
+                v.x = tb < T ? src[0] : 0.f;
+                v.y = tb + 1 < T ? src[1] : 0.f;
+                v.z = tb + 2 < T ? src[2] : 0.f;
+                v.w = tb + 3 < T ? src[3] : 0.f;
+            }
+            nc[m] = v;
+        }
+    };
+    if (pc.rank > 0) load(0);
     for (int r0 = 0; r0 < pc.rank; r0 += RT) {
 #pragma unroll
-        for (int m = 0; m < (RT * 128) / 256; ++m) {
-            const int e = tid + 256 * m;
-            const int ii = e & 127, rr = e >> 7;
-            const int r = r0 + rr;
-            Qs[rr][ii] = r < pc.rank ? pc.Qh[(int64_t)r * pc.Npad + i0 + ii] : 0.f;
+        for (int m = 0; m < 8; ++m) {
+            const int e = tid + 128 * m;
+            *reinterpret_cast<float4*>(&Qs[e >> 5][4 * (e & 31)]) = nq[m];
         }
 #pragma unroll
-        for (int m = 0; m < (RT * 64) / 256; ++m) {
-            const int e = tid + 256 * m;
-            const int tt = e & 63, rr = e >> 6;
-            const int r = r0 + rr, t = t0 + tt;
-            Cs[rr][tt] = (r < pc.rank && t < T) ? pc.coef[(int64_t)r * T + t] : 0.f;
+        for (int m = 0; m < 4; ++m) {
+            const int e = tid + 128 * m;
+            *reinterpret_cast<float4*>(&Cs[e >> 4][4 * (e & 15)]) = nc[m];
         }
         __syncthreads();
+        if (r0 + RT < pc.rank) load(r0 + RT);
 #pragma unroll 4
         for (int rr = 0; rr < RT; ++rr) {
-            float qv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) qv[u] = Qs[rr][tx + 32 * u];
-            const float4 c0 = *reinterpret_cast<const float4*>(&Cs[rr][ty * 8]);
-            const float4 c1 = *reinterpret_cast<const float4*>(&Cs[rr][ty * 8 + 4]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&Qs[rr][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Qs[rr][ty * 8 + 4]);
+            const float4 c0 = *reinterpret_cast<const float4*>(&Cs[rr][tx * 8]);
+            const float4 c1 = *reinterpret_cast<const float4*>(&Cs[rr][tx * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(qv[u], cv[v], acc[u][v]);
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], cv[v], acc[u][v]);
         }
         __syncthreads();
     }
+    // Thread (tx, ty) holds rows i0 + 8 ty + u and columns t0 + 8 tx + v.
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-        const int t = t0 + ty * 8 + v;
-        if (t >= T) break;                       // warp-uniform: every lane has the same ty
+        const int t = t0 + tx * 8 + v;
+        const bool col = t < T;
         FPair qp, pp, qq;
+        if (col) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t i = i0 + tx + 32 * u;
-            const float x = i < pc.N ? X[(int64_t)t * ldx + i] : 0.f;
-            const float o = fmaf(alpha, x, acc[u][v]);
-            if (!LANCZOS) {
-                if (i < pc.N) out[(int64_t)t * ldo + i] = o;
-                else if (ldo >= pc.Npad) out[(int64_t)t * ldo + i] = 0.f;
-            } else {
-                const int64_t idx = (int64_t)t * pc.Npad + i;
-                const float p = i < pc.N ? o - (float)beta[t] * qprev[idx] : 0.f;
-                (pout ? pout : qprev)[idx] = p;
-                const float qv = q[idx];
-                pair_fma(qp, qv, p);
-                pair_fma(pp, p, p);
-                pair_fma(qq, qv, qv);
+            for (int u = 0; u < 8; ++u) {
+                const int64_t i = i0 + ty * 8 + u;
+                const float x = i < pc.N ? X[(int64_t)t * ldx + i] : 0.f;
+                const float o = fmaf(alpha, x, acc[u][v]);
+                if (!LANCZOS) {
+                    if (i < pc.N) out[(int64_t)t * ldo + i] = o;
+                    else if (ldo >= pc.Npad) out[(int64_t)t * ldo + i] = 0.f;
+                } else {
+                    const int64_t idx = (int64_t)t * pc.Npad + i;
+                    const float p = i < pc.N ? o - (float)beta[t] * qprev[idx] : 0.f;
+                    (pout ? pout : qprev)[idx] = p;
+                    const float qv = q[idx];
+                    pair_fma(qp, qv, p);
+                    pair_fma(pp, p, p);
+                    pair_fma(qq, qv, qv);
+                }
             }
         }
         if (LANCZOS) {
-            qp = pair_warp_sum(qp);
-            pp = pair_warp_sum(pp);
-            qq = pair_warp_sum(qq);
-            if (tx == 0) {
-                double* dst = partials + ((int64_t)blockIdx.x * T + t) * 3;
-                dst[0] = (double)qp.hi + (double)qp.lo;
-                dst[1] = (double)pp.hi + (double)pp.lo;
-                dst[2] = (double)qq.hi + (double)qq.lo;
+            // The 4 threads of a warp with this tx (lanes tx, tx + 8, ...), then the 4 warps.
+#pragma unroll
+            for (int o = 8; o < 32; o <<= 1) {
+                FPair* ps[3] = {&qp, &pp, &qq};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float h = __shfl_xor_sync(0xffffffffu, ps[k]->hi, o);
+                    const float l = __shfl_xor_sync(0xffffffffu, ps[k]->lo, o);
+                    pair_add(*ps[k], h);
+                    ps[k]->lo = __fadd_rn(ps[k]->lo, l);
+                }
             }
+            if (lane < 8) {
+                red[warp][lane][0] = (double)qp.hi + (double)qp.lo;
+                red[warp][lane][1] = (double)pp.hi + (double)pp.lo;
+                red[warp][lane][2] = (double)qq.hi + (double)qq.lo;
+            }
+            __syncthreads();
+            if (tid < 8 && t0 + tid * 8 + v < T) {
+                const int tc = t0 + tid * 8 + v;
+                double* dst = partials + ((int64_t)blockIdx.x * T + tc) * 3;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) dst[k] = red[0][tid][k] + red[1][tid][k] + red[2][tid][k] + red[3][tid][k];
+            }
+            __syncthreads();
         }
     }
 }
@@ -516,13 +593,13 @@ cudaError_t launch_pc_apply(const PrecondState& pc, const float* X, int64_t ldx,
         const int64_t rows = chunk_rows(pc.Npad, pc.rank, T);
         const int nch = (int)((pc.Npad + rows - 1) / rows);
         dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
-        pc_reduce<<<g1, 256, 0, st>>>(pc, X, ldx, T, rows, stop);
+        pc_reduce<<<g1, 128, 0, st>>>(pc, X, ldx, T, rows, stop);
         pc_coef<<<T, 256, 0, st>>>(pc, T, nch, inverse_root, vscale, TP, stop);
     } else if (vscale) {
         pc_unit_scale<<<1, 256, 0, st>>>(pc, T, TP, vscale, stop);
     }
     dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
-    pc_expand<false><<<g2, 256, 0, st>>>(pc, X, ldx, T, inverse_root ? pc.inv_sigma : pc.sigma, out, ldo, nullptr,
+    pc_expand<false><<<g2, 128, 0, st>>>(pc, X, ldx, T, inverse_root ? pc.inv_sigma : pc.sigma, out, ldo, nullptr,
                                          nullptr, nullptr, nullptr, nullptr, stop);
     return cudaGetLastError();
 }
@@ -533,11 +610,11 @@ cudaError_t launch_pc_lanczos(const PrecondState& pc, const float* Oraw, const f
         const int64_t rows = chunk_rows(pc.Npad, pc.rank, T);
         const int nch = (int)((pc.Npad + rows - 1) / rows);
         dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
-        pc_reduce<<<g1, 256, 0, st>>>(pc, Oraw, pc.Npad, T, rows, stop);
+        pc_reduce<<<g1, 128, 0, st>>>(pc, Oraw, pc.Npad, T, rows, stop);
         pc_coef<<<T, 256, 0, st>>>(pc, T, nch, true, nullptr, 0, stop);
     }
     dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
-    pc_expand<true><<<g2, 256, 0, st>>>(pc, Oraw, pc.Npad, T, pc.inv_sigma, nullptr, 0, q, qprev, pout, beta,
+    pc_expand<true><<<g2, 128, 0, st>>>(pc, Oraw, pc.Npad, T, pc.inv_sigma, nullptr, 0, q, qprev, pout, beta,
                                         partials, stop);
     return cudaGetLastError();
 }
@@ -606,11 +683,11 @@ cudaError_t launch_lowrank_lanczos(const PrecondState& pc, const float* V, const
         const int64_t rows = chunk_rows(pc.Npad, pc.rank, T);
         const int nch = (int)((pc.Npad + rows - 1) / rows);
         dim3 g1((pc.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
-        pc_reduce<<<g1, 256, 0, st>>>(pc, V, pc.Npad, T, rows, stop);
+        pc_reduce<<<g1, 128, 0, st>>>(pc, V, pc.Npad, T, rows, stop);
         pc_coef<<<T, 256, 0, st>>>(pc, T, nch, true, nullptr, 0, stop);
     }
     dim3 g2((unsigned)(pc.Npad / 128), (T + 63) / 64);
-    pc_expand<true><<<g2, 256, 0, st>>>(pc, Oraw, pc.Npad, T, 1.f, nullptr, 0, q, qprev, pout, beta, partials, stop);
+    pc_expand<true><<<g2, 128, 0, st>>>(pc, Oraw, pc.Npad, T, 1.f, nullptr, 0, q, qprev, pout, beta, partials, stop);
     return cudaGetLastError();
 }
 
