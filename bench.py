@@ -1255,7 +1255,11 @@ def precond_oracle_check(P, torch, opts):
 
 
 POSTERIOR = dict(n_train=256, n_cand=50_000, d=6, kind="matern52", ls=(0.2, 0.25, 0.3, 0.35, 0.4, 0.45),
-                 s=1.0, noise=1e-4, jitter=1e-4, mean=0.0, t=64, q=12, seed=20201112, check_n=4096)
+                 s=1.0, noise=1e-4, jitter=1e-4, mean=0.0, t=64, q=12, seed=20201112, check_n=4096,
+                 pc_check_n=1024)
+# Ranks of the posterior's pivoted-Cholesky preconditioner timed beside the
+# unpreconditioned draws (the paper's BO runs use a rank-200 preconditioner).
+POSTERIOR_PRECOND_RANKS = (100, 200)
 
 
 def posterior_inputs(n_cand):
@@ -1308,6 +1312,21 @@ def run_posterior(args):
     ms = e0.elapsed_time(e1) / reps
     _, pinf = P.ciq_posterior_sample(Xtr_d, y_d, Xc_d, c["kind"], c["ls"], c["s"], c["noise"], c["jitter"], c["mean"],
                                      eps_d, c["q"], TOL, profile=1, **opts)
+    # The same draws with a pivoted-Cholesky preconditioner of COV* (the
+    # rotated root R, R R^T = COV*: draws of the same distribution).
+    precond = {}
+    for rank in POSTERIOR_PRECOND_RANKS:
+        pcall = lambda: P.ciq_posterior_sample(Xtr_d, y_d, Xc_d, c["kind"], c["ls"], c["s"], c["noise"],
+                                               c["jitter"], c["mean"], eps_d, c["q"], TOL, precond_rank=rank, **opts)
+        pcall()
+        torch.cuda.synchronize()
+        e0.record()
+        pinfos = [pcall()[1] for _ in range(reps)]
+        e1.record()
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / reps
+        precond[str(rank)] = {"draws_per_s": c["t"] / (pms * 1e-3), "ms": pms, "iterations": pinfos[-1]["iters"],
+                              "speedup": ms / pms, "precond_rank": pinfos[-1]["precond_rank"]}
     check = None
     if not args.no_cpu_baseline:
         from oracle import posterior as PO
@@ -1327,6 +1346,19 @@ def run_posterior(args):
                  "fluctuation": {"max": float(e_fl.max()), "median": float(np.median(e_fl))},
                  "iterations": inf["iters"], "oracle": "O1: FP64 eigendecomposition of the dense posterior covariance",
                  "oracle_seconds": time.perf_counter() - t0}
+        # Preconditioned draws: R R^T against COV* on the first pc_check_n
+        # candidates (all columns of the identity), the root's defining property.
+        m = c["pc_check_n"]
+        Xtr3, y3, Xc3, _ = posterior_inputs(m)
+        eye = np.eye(m, dtype=np.float32)
+        for rank in POSTERIOR_PRECOND_RANKS:
+            o3, i3 = P.ciq_posterior_sample(Xtr3, y3, Xc3, c["kind"], c["ls"], c["s"], c["noise"], c["jitter"],
+                                            c["mean"], eye, c["q"], TOL, precond_rank=min(rank, m), **opts)
+            mu3, cov3 = PO.posterior(Xtr3.astype(np.float64), y3.astype(np.float64), Xc3.astype(np.float64),
+                                     c["kind"], np.array(c["ls"]), c["s"], c["noise"], c["jitter"], c["mean"])
+            R = (o3.astype(np.float64) - mu3[None, :]).T
+            check[f"precond_{rank}_RRt_rel_err"] = float(np.linalg.norm(R @ R.T - cov3) / np.linalg.norm(cov3))
+            check[f"precond_{rank}_iterations"] = i3["iters"]
     line = {"metric": "posterior Thompson draws/s (mu* + COV*^{1/2} eps) at error bound 1e-3",
             "value": c["t"] / (ms * 1e-3), "unit": "draws/s", "n_gpus": 1, "steps": reps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1339,7 +1371,7 @@ def run_posterior(args):
             "iterations": [i["iters"] for i in infos], "profile": {k: pinf[k] for k in
                                                                    ("t_total_ms", "t_prepass_ms", "t_mvm_ms",
                                                                     "t_step_ms", "mvm_launches")},
-            "oracle_check": check, "clocks": clocks}
+            "preconditioned": precond, "oracle_check": check, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -159,6 +159,9 @@ typedef struct {
     int batch_split_rows;     /* tensor-core batches: problems of at least this many 128-row tiles
                                  run batch_split CTAs per row tile (0 = off, the default) */
     int batch_split;          /* 1..8 (used when batch_split_rows > 0) */
+    int precond_rank;         /* ciq_posterior_sample: rank of a pivoted-Cholesky preconditioner of
+                                 COV* (0 = none, the default; 1..1024); the draws then use the
+                                 rotated root R (R R^T = COV*) instead of the principal one */
 } ciq_options;
 
 typedef struct {

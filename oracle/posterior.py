@@ -18,7 +18,10 @@ the coordinates divided by their own lengthscales (App. BO setup names
 "Matern-5/2 with ARD"); the mean is a constant m ("constant mean function");
 the 1e-4 the paper adds "to the diagonal of the kernel matrix" is the jitter
 of COV*; COV*^{1/2} is the principal root (what msMINRES-CIQ approximates;
-Cholesky would give a rotated one, Sec. 2).
+Cholesky would give a rotated one, Sec. 2).  With a preconditioner (App.
+"Preconditioning msMINRES-CIQ"), the draw uses the rotated root R with
+R R^T = COV* that the preconditioned solve defines; any root of COV* gives
+draws of the same distribution.
 """
 from __future__ import annotations
 
@@ -55,3 +58,19 @@ def posterior(Xtr, y, Xc, kind, lengthscales, outputscale, noise, jitter, mean):
 def thompson_draws(mu, cov, eps):
     """O1: mu + COV^{1/2} eps for eps of shape (T, N*) (rows are draws)."""
     return mu[None, :] + eig.sqrt_apply(cov, np.asarray(eps, dtype=np.float64).T).T
+
+
+def preconditioned_draws(mu, cov, jitter, rank, eps):
+    """mu + R eps for eps of shape (T, N*): R = P^{1/2} A^{1/2}, A = P^{-1/2}
+    COV* P^{-1/2}, P = L L^T + jitter I with L the rank-`rank` pivoted Cholesky
+    factor of COV* - jitter I (the noise-free posterior covariance), so that
+    R R^T = COV* (Eq. precond_sqrt with sigma^2 = jitter)."""
+    from . import precond as PC
+
+    cov = np.asarray(cov, dtype=np.float64)
+    n = cov.shape[0]
+    C0 = cov - jitter * np.eye(n)
+    L, _ = PC.pivoted_cholesky(np.diag(C0).copy(), lambda i: C0[:, i], rank)
+    Pm = L @ L.T + jitter * np.eye(n)
+    Rb, _ = PC.rotated_roots_exact(cov, Pm, np.asarray(eps, dtype=np.float64))
+    return mu[None, :] + Rb

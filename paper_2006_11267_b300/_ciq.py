@@ -59,7 +59,7 @@ class _Options(ctypes.Structure):
                 ("quad_w", ctypes.c_void_p), ("quad_t", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("graph", ctypes.c_int),
                 ("tc_split", ctypes.c_int), ("fault_inject", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("batch_split_rows", ctypes.c_int), ("batch_split", ctypes.c_int)]
+                ("batch_split_rows", ctypes.c_int), ("batch_split", ctypes.c_int), ("precond_rank", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):

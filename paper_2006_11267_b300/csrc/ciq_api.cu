@@ -85,7 +85,8 @@ bool valid_options(const ciq_options& o) {
              (o.mvm < CIQ_MVM_AUTO || o.mvm > CIQ_MVM_STORED) || o.tc_split < 0 || o.tc_split > 8 ||
              o.fault_inject < 0 || o.fault_inject > 1 || o.krylov < CIQ_KRYLOV_AUTO ||
              o.krylov > CIQ_KRYLOV_BASIS || o.batch_split_rows < 0 ||
-             (o.batch_split_rows > 0 && (o.batch_split < 1 || o.batch_split > 8)));
+             (o.batch_split_rows > 0 && (o.batch_split < 1 || o.batch_split > 8)) || o.precond_rank < 0 ||
+             o.precond_rank > kPcMaxRank);
 }
 
 // Pinned host words for the convergence flag, one set per host thread.
@@ -135,6 +136,7 @@ struct Plan {
     bool vjp = false;             // backward pass: T = 2 T_B columns [B | G], basis form
     int pc_rank = 0;              // pivoted-Cholesky preconditioner rank (0: none)
     int lr_rank = -1;             // low-rank correction -C C^T of the MVM (>= 0: on)
+    float *lr_g = nullptr, *lr_s = nullptr;   // its g = -1 and reduction scratch
     bool stage_l = false;         // the caller's factor L is on the host
     // pointers (valid once an arena base is set)
     R *Xp, *QA, *QB, *Y, *Ylo, *Bw, *D, *LA, *LB, *V, *sco;
@@ -221,9 +223,9 @@ struct Plan {
         Kst = stored ? a.take<float>((size_t)Npad * Npad) : nullptr;
         if (lr_rank >= 0) {
             const int rk = std::max(lr_rank, 1);
-            pc_g = a.take<float>((size_t)rk);
-            pcs = a.take<float>(pc_scratch_floats(Npad, rk, T));
-            Op = a.take<float>((size_t)T * Npad);
+            lr_g = a.take<float>((size_t)rk);
+            lr_s = a.take<float>(pc_scratch_floats(Npad, rk, T));
+            if (pc_rank <= 0) Op = a.take<float>((size_t)T * Npad);
         }
         if (pc_rank > 0) {
             const size_t RK = (size_t)pc_rank;
@@ -337,7 +339,7 @@ cudaError_t launch_mvm(const Plan<R>& p, const MvmArgs<R>& a, bool unit_columns,
 // p = P^{-1/2} O' - beta q_prev and the partial sums.
 template <typename R>
 cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<R>& a, cudaStream_t st,
-                        bool scale_ready = false) {
+                        bool scale_ready = false, const PrecondState* lr = nullptr) {
     if constexpr (sizeof(R) == 4) {
         if (pc.lowrank) {
             // (K - C C^T) q: the plain MVM of the unit columns q, then the
@@ -366,6 +368,9 @@ cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<
         m.lz_sco = nullptr;
         e = launch_mvm(p, m, p.tc, st, p.tc);
         if (e != cudaSuccess) return e;
+        // A low-rank term under the preconditioner (posterior covariance):
+        // O' = K U - C C^T U before the second application of P^{-1/2}.
+        if (lr && (e = launch_lowrank_apply(*lr, p.Up, p.Op, a.T, a.stop, st)) != cudaSuccess) return e;
         return launch_pc_lanczos(pc, p.Op, a.V, a.qprev, a.pout, a.beta, a.partials, a.T, a.stop, st);
     }
     return cudaErrorNotSupported;
@@ -375,7 +380,8 @@ cudaError_t precond_mvm(const Plan<R>& p, const PrecondState& pc, const MvmArgs<
 // preconditioner the pre-pass runs on A and lambda_min = 1 (P <= K).
 template <typename R>
 cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options& o, int Q,
-                        const R* start_dev, cudaStream_t st, const PrecondState* pc = nullptr) {
+                        const R* start_dev, cudaStream_t st, const PrecondState* pc = nullptr,
+                        const PrecondState* lr = nullptr) {
     LanczosState<R> ls = lanczos_state(p);
     cudaError_t e = launch_lanczos_init(ls, start_dev, o.seed, st);
     if (e != cudaSuccess) return e;
@@ -388,7 +394,7 @@ cudaError_t run_prepass(const Plan<R>& p, const ciq_kernel& k, const ciq_options
         a.V = (j & 1) ? p.LA : p.LB;
         a.qprev = (j & 1) ? p.LB : p.LA;
         a.beta = p.bpar + (j & 1);
-        if (pc) e = precond_mvm(p, *pc, a, st);
+        if (pc) e = precond_mvm(p, *pc, a, st, false, lr);
         else e = (p.stored || p.tc) ? launch_mvm(p, a, true, st) : launch_mvm_simt(a, st);
         if (e != cudaSuccess) return e;
         if ((e = launch_lanczos_step(ls, j, st)) != cudaSuccess) return e;
@@ -479,7 +485,7 @@ struct LrSpec {
 // Qh = L U diag(s)^{-1/2} of the directions with s > 1e-10 max(s) and the
 // coefficients of P^{+-1/2}.  Synchronises the stream (the host reads G).
 ciq_status build_precond(const Plan<float>& p, const ciq_kernel& k, const PcSpec& spec, const float* Ld,
-                         cudaStream_t st, PrecondState* pc, int* launches) {
+                         cudaStream_t st, PrecondState* pc, int* launches, const float* Ct = nullptr, int rk = 0) {
     int R = spec.rank;
     cudaError_t e = cudaSuccess;
     if (Ld) {
@@ -489,8 +495,8 @@ ciq_status build_precond(const Plan<float>& p, const ciq_kernel& k, const PcSpec
                                   cudaMemcpyDeviceToDevice, st);
     } else {
         e = launch_pivoted_cholesky(p.Xp, p.N, p.Npad, p.dp, k.type, (float)k.outputscale, R, p.Lf, p.piv, p.dres,
-                                    p.cwork, p.rank_out, st);
-        *launches += R + 1;
+                                    p.cwork, p.rank_out, st, Ct, rk);
+        *launches += R + 1 + (rk > 0 ? 1 : 0);
         int rr = R;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&rr, p.rank_out, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -556,7 +562,8 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                  double tol, const ciq_options* opt, R* out, ciq_info* info, cudaStream_t st,
                  int op, bool fp64, const float* Kd = nullptr, int64_t ldk = 0, double* vjp_grad = nullptr,
                  const PcSpec* pcs = nullptr, const LrSpec* lrs = nullptr) {
-    if (lrs && (fp64 || Kd || vjp_grad || pcs || lrs->rank < 0 || (lrs->rank > 0 && !lrs->Ct)))
+    // A low-rank term may sit under a preconditioner that the device factors (no caller's L).
+    if (lrs && (fp64 || Kd || vjp_grad || (pcs && pcs->L) || lrs->rank < 0 || (lrs->rank > 0 && !lrs->Ct)))
         return CIQ_ERR_ARG;
     const bool dense = Kd != nullptr;
     const bool vjp = vjp_grad != nullptr;
@@ -639,7 +646,8 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
     int last_j = 0;
     int launches = 0;
     PrecondState pcst;
-    bool pc_on = false;
+    PrecondState lrst;                 // the low-rank term when it sits under a preconditioner
+    bool pc_on = false, lr_under_pc = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     Profile prof;
     prof.on = o.profile != 0;
@@ -691,23 +699,30 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         if constexpr (sizeof(R) == 4) {
             if (lrs) {
                 std::vector<float> neg((size_t)std::max(lrs->rank, 1), -1.f);
-                CIQ_TRY(cudaMemcpyAsync(p.pc_g, neg.data(), sizeof(float) * neg.size(), cudaMemcpyHostToDevice, st));
+                CIQ_TRY(cudaMemcpyAsync(p.lr_g, neg.data(), sizeof(float) * neg.size(), cudaMemcpyHostToDevice, st));
                 CIQ_TRY(cudaStreamSynchronize(st));
-                pcst.N = N;
-                pcst.Npad = p.Npad;
-                pcst.rank = lrs->rank;
-                pcst.Qh = lrs->Ct;
-                pcst.gm = p.pc_g;
-                pcst.gp = p.pc_g;
-                pcst.sigma = 1.f;
-                pcst.inv_sigma = 1.f;
-                pcst.cpart = p.pcs;
-                pcst.coef = p.pcs + (pc_scratch_floats(p.Npad, std::max(lrs->rank, 1), T) -
-                                     (size_t)std::max(lrs->rank, 1) * T);
-                pcst.T = T;
-                pcst.lowrank = true;
-                pcst.mu = lrs->mu;
-                pc_on = true;
+                PrecondState l;
+                l.N = N;
+                l.Npad = p.Npad;
+                l.rank = lrs->rank;
+                l.Qh = lrs->Ct;
+                l.gm = p.lr_g;
+                l.gp = p.lr_g;
+                l.sigma = 1.f;
+                l.inv_sigma = 1.f;
+                l.cpart = p.lr_s;
+                l.coef = p.lr_s + (pc_scratch_floats(p.Npad, std::max(lrs->rank, 1), T) -
+                                   (size_t)std::max(lrs->rank, 1) * T);
+                l.T = T;
+                l.lowrank = true;
+                l.mu = lrs->mu;
+                if (p.pc_rank > 0) {
+                    lrst = l;
+                    lr_under_pc = true;
+                } else {
+                    pcst = l;
+                    pc_on = true;
+                }
             }
             if (p.pc_rank > 0) {
                 const float* Ld = pcs->L;
@@ -718,7 +733,8 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                 }
                 PcSpec spec = *pcs;
                 if (p.stage_l) spec.ldl = N;
-                rc = build_precond(p, *kern, spec, Ld, st, &pcst, &launches);
+                rc = build_precond(p, *kern, spec, Ld, st, &pcst, &launches, lrs ? lrs->Ct : nullptr,
+                                   lrs ? lrs->rank : 0);
                 if (rc != CIQ_OK) goto done;
                 pc_on = true;
             }
@@ -740,7 +756,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             CIQ_TRY(launch_nodes_from_bounds(p.nodes, Q, o.lmin, o.lmax, st));
             launches += 1;
         } else {
-            CIQ_TRY(run_prepass(p, *kern, o, Q, startd, st, pc_on ? &pcst : nullptr));
+            CIQ_TRY(run_prepass(p, *kern, o, Q, startd, st, pc_on ? &pcst : nullptr, lr_under_pc ? &lrst : nullptr));
             launches += 3 + p.JL * (1 + (p.tc ? 4 : 1) + (pc_on ? 6 : 0));   // tensor cores: V scale, V split,
                                                                              // product, finish
         }
@@ -802,7 +818,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                         a.qprev = (jj & 1) ? p.QB : p.QA;
                     }
                     a.beta = p.beta + (size_t)(jj & 1) * T;
-                    if (pc_on) CIQ_TRY(precond_mvm(p, pcst, a, st, jj > 1));
+                    if (pc_on) CIQ_TRY(precond_mvm(p, pcst, a, st, jj > 1, lr_under_pc ? &lrst : nullptr));
                     else CIQ_TRY(launch_mvm(p, a, true, st, jj > 1));
                     if (prof.on) CIQ_TRY(cudaEventRecord(prof.ev[slot][2 * (jj - j) + 1], st));
                     CIQ_TRY(launch_msminres_step(s, jj, false, st, !lz));
@@ -861,17 +877,28 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
             m.V = p.Y;
             m.out = outd;
             m.ldo = N;
-            CIQ_TRY(launch_mvm(p, m, false, st));
+            if constexpr (sizeof(R) == 4) {
+                if (lrs) {
+                    // (K - C C^T) Y: the MVM into Op, the low-rank term, then out.
+                    m.out = p.Op;
+                    m.ldo = p.Npad;
+                    CIQ_TRY(launch_mvm(p, m, false, st));
+                    CIQ_TRY(launch_lowrank_apply(lr_under_pc ? lrst : pcst, p.Y, p.Op, T, nullptr, st));
+                    CIQ_TRY(cudaMemcpy2DAsync(outd, sizeof(R) * N, p.Op, sizeof(R) * p.Npad, sizeof(R) * N, T,
+                                              cudaMemcpyDeviceToDevice, st));
+                    launches += 3;
+                } else {
+                    CIQ_TRY(launch_mvm(p, m, false, st));
+                }
+            } else {
+                CIQ_TRY(launch_mvm(p, m, false, st));
+            }
             launches += p.basis ? 1 : 2;
         } else if (!p.basis) {
             CIQ_TRY(launch_combine(s, comb, st));
             launches += 1;
         }
         if constexpr (sizeof(R) == 4) {
-            if (pc_on && pcst.lowrank && pcst.mu) {
-                CIQ_TRY(launch_add_mean(outd, N, N, T, pcst.mu, st));
-                launches += 1;
-            }
             if (pc_map) {
                 if (pc_literal) {
                     // R' b into the MVM's input buffer, then R b = K (R' b).
@@ -882,12 +909,29 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
                     m.V = p.Up;
                     m.out = outd;
                     m.ldo = N;
-                    CIQ_TRY(launch_mvm(p, m, false, st));
+                    if (lr_under_pc) {
+                        // (K - C C^T)(R' b) for the posterior covariance.
+                        m.out = p.Op;
+                        m.ldo = p.Npad;
+                        CIQ_TRY(launch_mvm(p, m, false, st));
+                        CIQ_TRY(launch_lowrank_apply(lrst, p.Up, p.Op, T, nullptr, st));
+                        CIQ_TRY(cudaMemcpy2DAsync(outd, sizeof(R) * N, p.Op, sizeof(R) * p.Npad, sizeof(R) * N, T,
+                                                  cudaMemcpyDeviceToDevice, st));
+                        launches += 3;
+                    } else {
+                        CIQ_TRY(launch_mvm(p, m, false, st));
+                    }
                     launches += mvm_launches + 1;
                 } else {
                     CIQ_TRY(launch_pc_apply(pcst, p.Apre, N, T, op == kOpInvSqrt, outd, N, nullptr, st));
                 }
                 launches += pcst.rank > 0 ? 3 : 1;
+            }
+            // The posterior mean, after the map back through P^{1/2}.
+            const float* mu = lr_under_pc ? lrst.mu : (pc_on && pcst.lowrank ? pcst.mu : nullptr);
+            if (mu) {
+                CIQ_TRY(launch_add_mean(outd, N, N, T, mu, st));
+                launches += 1;
             }
         }
         CIQ_TRY(launch_summary(s, last_j, st));
@@ -1969,8 +2013,12 @@ ciq_status ciq_posterior_sample(const float* Xtr, int64_t n, const float* y, con
     if (rc == CIQ_OK) {
         const ciq_kernel kc{kernel_type, 1.0, outputscale, jitter};       // candidates already divided by l_d
         const LrSpec lr{b.Ct, rk, b.mu};
+        // With opt->precond_rank, a pivoted-Cholesky preconditioner of
+        // COV* - jitter I (the device factors K** - C C^T).
+        const int prk = opt ? opt->precond_rank : 0;
+        const PcSpec pspec{nullptr, 0, prk};
         rc = solve<float>(b.Xcs, Nc, d, &kc, eps, T, Q, tol, opt, out, info, st, kOpSqrtIdentity, false, nullptr, 0,
-                          nullptr, nullptr, &lr);
+                          nullptr, prk > 0 ? &pspec : nullptr, &lr);
     }
     cudaFreeAsync(base, st);
     cudaStreamSynchronize(st);

@@ -367,10 +367,20 @@ CholWork chol_work(void* base, int64_t Npad) {
 }
 
 __global__ void pc_cholesky_init(int64_t N, int64_t Npad, double s, double* dres, CholWork w, int* piv,
-                                 int* rank_out, int rank) {
+                                 int* rank_out, int rank, const float* Ct, int rk) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < Npad) {
-        dres[i] = i < N ? s : -1.0;
+        double d = i < N ? s : -1.0;
+        if (i < N && rk > 0) {
+            // Diagonal of K - C C^T: s - |c_i|^2 (float pair of exact squares).
+            FPair c2;
+            for (int k = 0; k < rk; ++k) {
+                const float c = Ct[(int64_t)k * Npad + i];
+                pair_fma(c2, c, c);
+            }
+            d = s - ((double)c2.hi + (double)c2.lo);
+        }
+        dres[i] = d;
         w.ispiv[i] = 0;
     }
     if (i == 0) {
@@ -381,11 +391,39 @@ __global__ void pc_cholesky_init(int64_t N, int64_t Npad, double s, double* dres
     }
 }
 
+// First pivot of K - C C^T: the largest residual diagonal entry (smallest
+// index on ties), one block.
+__global__ void __launch_bounds__(1024) pc_cholesky_first(int64_t N, const double* dres, CholWork w, int* piv) {
+    __shared__ double rv[32];
+    __shared__ int ri[32];
+    double bv = -2.0;
+    int bi = INT_MAX;
+    for (int64_t i = threadIdx.x; i < N; i += 1024)
+        if (dres[i] > bv) { bv = dres[i]; bi = (int)i; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = bv; ri[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bv = rv[0];
+        bi = ri[0];
+        for (int q = 1; q < 32; ++q)
+            if (rv[q] > bv || (rv[q] == bv && ri[q] < bi)) { bv = rv[q]; bi = ri[q]; }
+        piv[0] = bi == INT_MAX ? 0 : bi;
+        w.dmax[0] = bv;
+    }
+}
+
 template <int KT>
 __global__ void __launch_bounds__(256) pc_cholesky_step(const float* Xp, int64_t N, int64_t Npad, int dp, float s,
                                                         int k, float* L, int* piv, double* dres, CholWork w,
-                                                        int* rank_out) {
+                                                        int* rank_out, const float* Ct, int rk) {
     __shared__ float Lp[kPcMaxRank];
+    __shared__ float Cp[kPcMaxTrain];
     __shared__ float xp[kMaxDimPad];
     __shared__ double rv[8];
     __shared__ int ri[8];
@@ -401,6 +439,7 @@ __global__ void __launch_bounds__(256) pc_cholesky_step(const float* Xp, int64_t
     const int ip = piv[k];
     const int tid = threadIdx.x;
     for (int m = tid; m < k; m += 256) Lp[m] = L[(int64_t)m * Npad + ip];
+    for (int m = tid; m < rk; m += 256) Cp[m] = Ct[(int64_t)m * Npad + ip];
     if (tid < dp) xp[tid] = Xp[(int64_t)ip * dp + tid];
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * 256 + tid;
@@ -413,8 +452,10 @@ __global__ void __launch_bounds__(256) pc_cholesky_step(const float* Xp, int64_t
         }
         // The kernel value minus the earlier columns' contributions, summed as
         // a float pair of exact products (FP64 is slow here; see FPair).
+        // With a low-rank term, the column of K - C C^T: c_i . c_p joins the dot.
         FPair dot;
         for (int m = 0; m < k; ++m) pair_fma(dot, L[(int64_t)m * Npad + i], Lp[m]);
+        for (int m = 0; m < rk; ++m) pair_fma(dot, Ct[(int64_t)m * Npad + i], Cp[m]);
         double col = (double)kernel_value<KT>(r2, s) - ((double)dot.hi + (double)dot.lo);
         const bool was_pivot = w.ispiv[i] != 0;
         if (was_pivot) col = 0.0;              // earlier pivot rows of the Schur complement are 0
@@ -627,21 +668,22 @@ size_t pc_cholesky_work_bytes(int64_t Npad) {
 
 cudaError_t launch_pivoted_cholesky(const float* Xp, int64_t N, int64_t Npad, int dp, int kt, float outputscale,
                                     int rank, float* L, int* piv, double* dres, void* work, int* rank_out,
-                                    cudaStream_t st) {
-    if (rank < 1 || rank > kPcMaxRank) return cudaErrorInvalidValue;
+                                    cudaStream_t st, const float* Ct, int rk) {
+    if (rank < 1 || rank > kPcMaxRank || rk < 0 || rk > kPcMaxTrain || (rk > 0 && !Ct)) return cudaErrorInvalidValue;
     CholWork w = chol_work(work, Npad);
     cudaError_t e = cudaMemsetAsync(L, 0, sizeof(float) * (size_t)rank * Npad, st);
     if (e != cudaSuccess) return e;
     pc_cholesky_init<<<(unsigned)((Npad + 255) / 256), 256, 0, st>>>(N, Npad, (double)outputscale, dres, w, piv,
-                                                                      rank_out, rank);
+                                                                      rank_out, rank, Ct, rk);
+    if (rk > 0) pc_cholesky_first<<<1, 1024, 0, st>>>(N, dres, w, piv);
     const unsigned blocks = (unsigned)((Npad + 255) / 256);
     for (int k = 0; k < rank; ++k) {
         if (kt == CIQ_RBF)
             pc_cholesky_step<CIQ_RBF><<<blocks, 256, 0, st>>>(Xp, N, Npad, dp, outputscale, k, L, piv, dres, w,
-                                                               rank_out);
+                                                               rank_out, Ct, rk);
         else
             pc_cholesky_step<CIQ_MATERN52><<<blocks, 256, 0, st>>>(Xp, N, Npad, dp, outputscale, k, L, piv, dres,
-                                                                    w, rank_out);
+                                                                    w, rank_out, Ct, rk);
     }
     return cudaGetLastError();
 }
@@ -673,6 +715,20 @@ cudaError_t launch_product_f64(const double* A, int64_t Npad, int R, const doubl
                                cudaStream_t st) {
     if (Rk < 1) return cudaSuccess;
     basis_from_factor<double><<<dim3((unsigned)(Npad / 128), (Rk + 31) / 32), 128, 0, st>>>(A, Npad, R, W, Rk, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lowrank_apply(const PrecondState& lr, const float* V, float* O, int T, const int* stop,
+                                  cudaStream_t st) {
+    if (lr.rank <= 0) return cudaSuccess;
+    const int64_t rows = chunk_rows(lr.Npad, lr.rank, T);
+    const int nch = (int)((lr.Npad + rows - 1) / rows);
+    dim3 g1((lr.rank + kRedRT - 1) / kRedRT, (T + kRedTT - 1) / kRedTT, nch);
+    pc_reduce<<<g1, 128, 0, st>>>(lr, V, lr.Npad, T, rows, stop);
+    pc_coef<<<T, 256, 0, st>>>(lr, T, nch, true, nullptr, 0, stop);
+    dim3 g2((unsigned)(lr.Npad / 128), (T + 63) / 64);
+    pc_expand<false><<<g2, 128, 0, st>>>(lr, O, lr.Npad, T, 1.f, O, lr.Npad, nullptr, nullptr, nullptr, nullptr,
+                                         nullptr, stop);
     return cudaGetLastError();
 }
 

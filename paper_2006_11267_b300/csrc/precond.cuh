@@ -20,6 +20,7 @@
 namespace ciq {
 
 constexpr int kPcMaxRank = 1024;    // largest preconditioner rank
+constexpr int kPcMaxTrain = 2048;   // largest rank of a low-rank term (training points of a posterior)
 
 struct PrecondState {
     int64_t N = 0, Npad = 0;
@@ -67,9 +68,11 @@ inline int64_t pc_row_tiles(int64_t Npad) { return Npad / 128; }
 // `work` of pc_cholesky_work_bytes(Npad) bytes.  *rank_out (device int) is
 // the number of columns formed (smaller when the residual diagonal vanishes).
 size_t pc_cholesky_work_bytes(int64_t Npad);
+// With Ct (device, [rk][Npad], rk <= kPcMaxTrain), the factor is that of
+// K_XX - C C^T (its columns and diagonal lose the low-rank term).
 cudaError_t launch_pivoted_cholesky(const float* Xp, int64_t N, int64_t Npad, int dp, int kt, float outputscale,
                                     int rank, float* L, int* piv, double* dres, void* work, int* rank_out,
-                                    cudaStream_t st);
+                                    cudaStream_t st, const float* Ct = nullptr, int rk = 0);
 
 // G = L^T L (FP64, R x R, column-major) from L [R][Npad]; gpart: scratch of
 // pc_gram_scratch(Npad, R) doubles.
@@ -90,6 +93,11 @@ cudaError_t launch_product_f64(const double* A, int64_t Npad, int R, const doubl
 // Qh^T V (V: the MVM's input, O': its plain output, both leading dimension
 // Npad), then p = O - beta q_prev and the partial sums as launch_pc_lanczos.
 // With gm = -1 this is (K - C C^T) V for C = Qh.
+// O += Qh diag(gm) Qh^T V in place (O, V: leading dimension Npad): the
+// low-rank term of the MVM on its own (gm = -1: O - C C^T V).
+cudaError_t launch_lowrank_apply(const PrecondState& lr, const float* V, float* O, int T, const int* stop,
+                                 cudaStream_t st);
+
 cudaError_t launch_lowrank_lanczos(const PrecondState& pc, const float* V, const float* Oraw, const float* q,
                                    float* qprev, float* pout, const double* beta, double* partials, int T,
                                    const int* stop, cudaStream_t st);

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_sizes_match_header_layout():
-    assert ctypes.sizeof(_ciq._Options) == 136
+    assert ctypes.sizeof(_ciq._Options) == 144
     assert ctypes.sizeof(_ciq._Kernel) == 32
     assert ctypes.sizeof(_ciq._Info) == 16 + 6 * 8 + 2 * 32 * 8 + 8 + 4 * 8 + 8 + 8 + 8
     # ciq_problem: X, N, d (+pad), kern, B, T (+pad), out, lmin, lmax

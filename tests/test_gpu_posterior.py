@@ -89,3 +89,62 @@ def test_prior_draws_without_training_data_and_interpolation():
     out, _ = P.ciq_posterior_sample(Xtr, y, Xc2, "matern52", LS, S, 1e-8, JITTER, MEAN, eps2, 15, 1e-6,
                                     stop_rule="errbound", max_iter=3000)
     assert np.abs(out[:, :60] - y[None, :]).max() < 6 * np.sqrt(JITTER)
+
+
+@pytest.mark.parametrize("form", ["identity", "mvm"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_preconditioned_draws_use_a_root_of_the_posterior_covariance(prec, form):
+    # opt.precond_rank: the device factors K** - C C^T (pivoted Cholesky
+    # with the low-rank term in its columns and diagonal) and the draws use
+    # the rotated root R (R R^T = COV*), the mean added after the map back
+    # through P^{1/2} (identity form) or the final (K** - C C^T) MVM (printed
+    # form).  Checked on all N* columns of the identity: (out - mu) holds R^T,
+    # so R R^T against the dense covariance (a property of any valid root,
+    # whichever pivots the device chose).  Gate: P^{1/2} and P^{-1/2} use the
+    # FP32 basis Qh, whose orthonormality error (~1e-7) enters P^{1/2} P^{-1/2}
+    # through g^+ g^- ~ sqrt(kappa(P)) (about 300 at jitter 1e-4): a few 1e-4
+    # whatever the solve's precision (measured 3.0-3.3e-4; 4e-6 without the
+    # preconditioner), below the mode's 1e-3.
+    Xtr, y, Xc, _ = data(60, 700, 1, 21)
+    mu, cov = oracle("matern52", Xtr, y, Xc)
+    nc = Xc.shape[0]
+    eye = np.eye(nc, dtype=np.float32)
+    kw = dict(max_iter=3000, stop_rule="errbound", precision=prec, sqrt_form=form, precond_rank=40)
+    out, info = P.ciq_posterior_sample(Xtr, y, Xc, "matern52", LS, S, NOISE, JITTER, MEAN, torch.from_numpy(eye).cuda(),
+                                       15, 1e-7, **kw)
+    assert info["status"] == 0 and info["precond_rank"] == 40
+    R = (out.cpu().numpy().astype(np.float64) - mu[None, :]).T
+    assert np.linalg.norm(R @ R.T - cov) / np.linalg.norm(cov) < 1e-3
+    zero = torch.zeros((1, nc), device="cuda")
+    m, _ = P.ciq_posterior_sample(Xtr, y, Xc, "matern52", LS, S, NOISE, JITTER, MEAN, zero, 15, 1e-7, **kw)
+    assert rel(m.cpu().numpy(), mu[None, :]) < 1e-5
+
+
+def test_unpreconditioned_printed_form_includes_the_low_rank_term():
+    # sqrt_form "mvm" without a preconditioner: COV* (sum_q w_q x_q), the
+    # final MVM with the -C C^T term: a root of COV* as well.
+    Xtr, y, Xc, _ = data(60, 500, 1, 23)
+    mu, cov = oracle("rbf", Xtr, y, Xc)
+    nc = Xc.shape[0]
+    eye = torch.eye(nc, device="cuda")
+    out, info = P.ciq_posterior_sample(Xtr, y, Xc, "rbf", LS, S, NOISE, JITTER, MEAN, eye, 15, 1e-7, max_iter=3000,
+                                       stop_rule="errbound", sqrt_form="mvm")
+    assert info["status"] == 0
+    R = (out.cpu().numpy().astype(np.float64) - mu[None, :]).T
+    assert np.linalg.norm(R @ R.T - cov) / np.linalg.norm(cov) < 1e-4
+
+
+def test_preconditioned_draws_need_fewer_iterations():
+    # The posterior covariance at jitter 1e-4 is ill-conditioned; a rank-100
+    # preconditioner takes its largest directions out of A, so the solve in
+    # the space of A needs fewer iterations (measured 218 against 283 here;
+    # the spectrum of this 4000-candidate covariance decays slowly past its
+    # first 100 directions).
+    Xtr, y, Xc, eps = data(100, 4000, 16, 31)
+    Xd, ed = torch.from_numpy(Xc).cuda(), torch.from_numpy(eps).cuda()
+    kw = dict(max_iter=4000, stop_rule="errbound", precision="fp16")
+    _, i0 = P.ciq_posterior_sample(Xtr, y, Xd, "matern52", LS, S, NOISE, JITTER, MEAN, ed, 12, 1e-3, **kw)
+    _, i1 = P.ciq_posterior_sample(Xtr, y, Xd, "matern52", LS, S, NOISE, JITTER, MEAN, ed, 12, 1e-3, precond_rank=100,
+                                   **kw)
+    assert i0["status"] == 0 and i1["status"] == 0 and i1["precond_rank"] == 100
+    assert i1["iters"] < 0.9 * i0["iters"], (i1["iters"], i0["iters"])

@@ -77,3 +77,18 @@ def test_ciq_on_the_posterior_covariance_converges_to_the_exact_draw():
     got = mu[None, :] + A
     err = np.linalg.norm(got - exact, axis=1) / np.linalg.norm(exact - mu[None, :], axis=1)
     assert err.max() < 1e-6
+
+
+def test_preconditioned_draws_use_a_root_of_the_posterior_covariance():
+    # R R^T = COV* for the rotated root of the preconditioned draw (the draws'
+    # covariance), checked on all N* columns of the identity; the rotation
+    # differs from the principal root (R is not symmetric); eps = 0 gives the mean.
+    Xtr, y, Xc = _data()
+    jitter = 1e-3
+    mu, cov = PO.posterior(Xtr, y, Xc, "matern52", LS, 1.2, 1e-2, jitter, 0.1)
+    n = len(mu)
+    D = PO.preconditioned_draws(mu, cov, jitter, 12, np.eye(n)) - mu[None, :]
+    R = D.T                                                    # column c = R e_c
+    assert np.abs(R @ R.T - cov).max() < 1e-10 * np.abs(cov).max()
+    assert np.abs(R - R.T).max() > 1e-3 * np.abs(R).max()
+    assert np.array_equal(PO.preconditioned_draws(mu, cov, jitter, 12, np.zeros((1, n)))[0], mu)
