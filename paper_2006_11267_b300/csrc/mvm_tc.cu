@@ -1480,8 +1480,8 @@ cudaError_t launch_stored_mvm_tc(const float* Kmat, int64_t ldk, const TcPoints&
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // K as a 2-D tensor of Npad x Npad floats, row pitch ldk floats; boxes of
     // 32 columns x 128 rows with the 128-byte swizzle.
-    // The driver's encoder is reached through the runtime (the library does
-    // not link the driver library).
+    // cuTensorMapEncodeTiled is reached through the runtime's entry-point
+    // lookup (the library does not link libcuda).
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
         void* fn = nullptr;

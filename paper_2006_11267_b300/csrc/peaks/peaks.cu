@@ -1,6 +1,6 @@
-// Throughput microbenchmarks for the roofline denominators that the driver
-// does not measure: SFU exp2 (ex2.approx.ftz.f32, the SFU op of every kernel
-// entry), FP32 FMA and FP64 FMA.  Each thread runs 8 independent dependent
+// Throughput microbenchmarks for the roofline denominators beyond the copy
+// rate and the BF16 GEMM rate: SFU exp2 (ex2.approx.ftz.f32, the SFU op of
+// every kernel entry), FP32 FMA and FP64 FMA.  Each thread runs 8 independent dependent
 // chains; the grid is 8 CTAs of 256 threads per SM.  Built as its own library
 // (libciq_peaks.so); the solver does not use it.
 #include <cuda_runtime.h>
