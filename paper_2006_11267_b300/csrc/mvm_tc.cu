@@ -9,9 +9,11 @@
 //         -c^2 |x - m|^2 / 2], so S = -c^2 r^2 / 2 directly (norm expansion of
 //         the distance; m is the centre of the points).  Each operand is split
 //         into a 16-bit leading part and a 16-bit trailing part and S =
-//         U_h V_h + U_h V_l + U_l V_h (three K-chunks of one MMA sequence;
-//         two MMAs for d <= 6, whose 8 augmented features fill half a
-//         chunk): about 22 significant bits with FP16 parts.
+//         U_h V_h + U_h V_l + U_l V_h (three K-chunks of one MMA sequence):
+//         about 22 significant bits with FP16 parts.  For d <= 6 the 8
+//         augmented features fill half a chunk: two MMAs; with BF16 parts the
+//         free half of the last chunk carries U_l V_l, so S has all four
+//         products.
 //   P   = k(r) / s from S on the SFU (RBF: ex2(S) with c^2 = log2 e; Matern-5/2:
 //         a = sqrt(-10 S), (1 + a + a^2/3) ex2(-a log2 e)), split again into
 //         leading/trailing 16-bit parts and written back over S in tensor
@@ -168,13 +170,23 @@ __device__ __forceinline__ void tc_points_body(const float* Xp, int64_t N, int64
     }
     const uint16_t* achunk[3] = {uh, uh, ul};
     const uint16_t* bchunk[3] = {vh, vl, vh};
+    // BF16 parts with at most 8 augmented features: only K-core 0 of each
+    // chunk carries them, and K-core 1 of chunk 2 takes (u_l, v_l), so the
+    // MMA over chunk 2 adds u_l v_l to u_l v_h and S has all four products of
+    // the split (measured: 1.4e-4 against 2.4e-4 MVM error for Matern-5/2 at
+    // lengthscale 0.1).  With FP16 parts the fourth product is below the
+    // MVM's other errors (1.85e-6 either way at d = 6) and the 50,000-point
+    // solve took 905 iterations with it against 897 without, so FP16 keeps
+    // three.
+    const bool narrow = !HALF && d + 2 <= 8;
     const size_t base = (size_t)(row >> 3) * kTcRowBytes * 8 + (size_t)(row & 7) * 16;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
 #pragma unroll
         for (int kc = 0; kc < 2; ++kc) {
-            const uint16_t* a = achunk[ch] + kc * 8;
-            const uint16_t* b = bchunk[ch] + kc * 8;
+            const bool ll = narrow && ch == 2 && kc == 1;
+            const uint16_t* a = ll ? ul : achunk[ch] + kc * 8;
+            const uint16_t* b = ll ? vl : bchunk[ch] + kc * 8;
             const size_t off = base + (size_t)ch * 256 + (size_t)kc * 128;
             *reinterpret_cast<uint4*>(ua + off) =
                 make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
