@@ -143,6 +143,7 @@ struct Plan {
     double *rcoef, *gauss, *bco, *ycoef, *vpart, *vgrad;
     float* Xq;
     R *sx, *sb, *sout, *sstart;
+    R* plo = nullptr;                 // trailing part of the Lanczos p (FP32 CUDA-core basis solves)
     float* Kst;
     double *partials, *ynp, *beta, *beta1, *giv, *phifinal, *nodes, *summary, *tri;
     double *lpart, *lynp, *bpar, *lalpha, *lbeta;
@@ -176,6 +177,9 @@ struct Plan {
         Ylo = a.take<R>((size_t)T * Npad);
         Bw = a.take<R>((size_t)T * Npad);
         D = basis ? nullptr : a.take<R>((size_t)2 * Q * T * Npad);
+        // FP32 CUDA-core basis solves keep p as a float pair.
+        plo = (basis && !tc && !stored && sizeof(R) == 4 && pc_rank <= 0 && lr_rank < 0)
+                  ? a.take<R>((size_t)T * Npad) : nullptr;
         rcoef = basis ? a.take<double>((size_t)jmax * Q * T * 4) : nullptr;
         gauss = basis ? a.take<double>((size_t)2 * T * 4) : nullptr;
         bco = basis ? a.take<double>(((size_t)jmax + 1) * T) : nullptr;
@@ -308,6 +312,7 @@ KrylovState<R> krylov_state(const Plan<R>& p, int op, const ciq_options& o, doub
     s.brk = p.brk; s.cnt = p.cnt; s.all_done = p.all_done; s.nodes = p.nodes;
     s.summary = p.summary; s.tri = p.tri; s.jmax = p.jmax; s.op = op; s.stop_rule = o.stop_rule; s.tol = tol;
     s.basis = p.V; s.rcoef = p.rcoef; s.gauss = p.gauss; s.bco = p.bco; s.sco = p.sco; s.ycoef = p.ycoef;
+    s.plo = p.plo;
     s.breakdown_rtol = sizeof(R) == 4 ? 1e-6 : 1e-13;
     return s;
 }
@@ -766,6 +771,7 @@ ciq_status solve(const R* X, int64_t N, int d, const ciq_kernel* kern, const R* 
         a.mode = kLanczos;
         a.partials = p.partials;
         a.stop = p.all_done;
+        a.plo = p.plo;
         // Kernels per MVM: one on CUDA cores; on tensor cores the V split
         // and, per column group, the product and the finish (the V scale of
         // unit columns is set by the first MVM only).

@@ -38,6 +38,11 @@ struct MvmArgs {
     const double* beta;    // kLanczos: beta_j per column
     double* partials;      // kLanczos: [ntiles][T][3]
     const int* stop;       // optional: skip the launch when *stop != 0
+    // Optional (CUDA-core MVM, kLanczos): p as a float pair.  p is formed in
+    // FP64 from the MVM's compensated sum, its leading part goes where p
+    // goes and its trailing part to plo (T x ldv), and the partial sums use
+    // the unrounded p.
+    R* plo = nullptr;
 };
 
 // Epilogue of one output entry O[i][col] (before the noise term): kPlain
@@ -46,9 +51,22 @@ struct MvmArgs {
 // accumulates q.p, p.p, q.q in FP64.
 template <typename R>
 __device__ __forceinline__ void lanczos_epilogue_value(const MvmArgs<R>& a, int64_t i, int col, R o,
-                                                       double& qp, double& pp, double& qq) {
+                                                       double& qp, double& pp, double& qq, R olo = (R)0) {
     const int64_t idx = (int64_t)col * a.ldv + i;
     const R v = a.V[idx];
+    if (a.mode == kLanczos && a.plo) {
+        // o + olo is the MVM's sum as a pair; p = O + sigma^2 v - beta q_prev in FP64.
+        const double pd = i < a.N ? (double)o + (double)olo + (double)a.noise * (double)v -
+                                        a.beta[col] * (double)a.qprev[idx]
+                                  : 0.0;
+        const R ph = (R)pd;
+        (a.pout ? a.pout : a.qprev)[idx] = ph;
+        a.plo[idx] = (R)(pd - (double)ph);
+        qp += (double)v * pd;
+        pp += pd * pd;
+        qq += (double)v * (double)v;
+        return;
+    }
     o += a.noise * v;
     if (a.mode == kPlain) {
         if (i < a.N) a.out[(int64_t)col * a.ldo + i] = o;

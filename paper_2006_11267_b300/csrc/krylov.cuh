@@ -69,6 +69,7 @@ struct KrylovState {
     double* tri;                // optional: column 0's T_j, diagonal [jmax + 1] then off-diagonal [jmax + 2]
     // Stored-basis form (basis != nullptr): no directions, no Y updates per step.
     R* basis;                   // [jmax + 2][T][Npad]; slot 0 = q_0 = 0, slot j = q_j (slot j + 1 holds p first)
+    R* plo = nullptr;           // [T][Npad] or null: trailing part of p (the MVM's float-pair p)
     double* rcoef;              // [jmax][Q][T][4]: 1/gamma_j, delta_j, eps_j, tau_j of shift q at step j
     double* gauss;              // [2][T][4]: LDL^T pivot d_j, u_j^2, sum_k u_k^2/d_k, alpha_1 (parity of j)
     double* bco;                // [jmax + 1][T]: sum_q c_q y_q(j), the coefficient of q_j

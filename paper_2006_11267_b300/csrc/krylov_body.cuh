@@ -302,16 +302,20 @@ __device__ __forceinline__ void step_vectors(const KrylovState<R>& s, int j, int
         if constexpr (sizeof(R) == 4) {
             const float4* q4 = reinterpret_cast<const float4*>(qj);
             float4* p4 = reinterpret_cast<float4*>(pn);
+            // With a float-pair p its trailing part joins before the scaling.
+            const float4* l4 = s.plo ? reinterpret_cast<const float4*>(s.plo + col) : nullptr;
             for (int64_t i4 = i0 / 4 + tid; i4 < i1 / 4; i4 += 256) {
                 const float4 qv = q4[i4];
                 const float4 pv = p4[i4];
+                const float4 lv = l4 ? l4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float qa[4] = {qv.x, qv.y, qv.z, qv.w}, pa[4] = {pv.x, pv.y, pv.z, pv.w};
+                const float la[4] = {lv.x, lv.y, lv.z, lv.w};
                 float o[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     float t = fmaf(-(float)ahi, qa[e], pa[e]);
                     t = fmaf(-(float)alo, qa[e], t);
-                    o[e] = t * (float)invb;
+                    o[e] = (t + la[e]) * (float)invb;
                 }
                 p4[i4] = make_float4(o[0], o[1], o[2], o[3]);
             }

@@ -74,7 +74,7 @@ __device__ __forceinline__ void mvm_narrow_body(const MvmArgs<R>& a, int bx, int
         for (int w = 0; w < 8; ++w) od += (double)red[w][lane][c] + (double)redlo[w][lane][c];
         const R o = (R)od;
         double qp = 0, pp = 0, qq = 0;
-        lanczos_epilogue_value(a, i, col, o, qp, pp, qq);
+        lanczos_epilogue_value(a, i, col, o, qp, pp, qq, (R)(od - (double)o));
         if (a.mode == kLanczos) {
             qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
             if (lane == 0) {
@@ -155,11 +155,19 @@ __device__ __forceinline__ void mvm_wide_body(const MvmArgs<float>& a, int bx, i
             for (int c = 0; c < MC; ++c) two_sum_into(hi[r][c], lo[r][c], acc[r][c]);
     }
     __syncthreads();
+    // The output tile as a (leading, trailing) pair: leading parts over the
+    // P buffer, trailing parts over the V buffer (both free now).
     float* sO = sP;
+    float* sOlo = sV;
+    static_assert(BN * LDV >= BM * LDO, "trailing parts must fit in the V buffer");
 #pragma unroll
     for (int r = 0; r < MR; ++r)
 #pragma unroll
-        for (int c = 0; c < MC; ++c) sO[(ty * MR + r) * LDO + tx * MC + c] = hi[r][c] + lo[r][c];
+        for (int c = 0; c < MC; ++c) {
+            const float sum = hi[r][c] + lo[r][c];
+            sO[(ty * MR + r) * LDO + tx * MC + c] = sum;
+            sOlo[(ty * MR + r) * LDO + tx * MC + c] = (hi[r][c] - sum) + lo[r][c];
+        }
     __syncthreads();
     constexpr int TPC = 256 / TC;          // threads per column
     constexpr int RPT = BM / TPC;          // rows per thread
@@ -169,7 +177,7 @@ __device__ __forceinline__ void mvm_wide_body(const MvmArgs<float>& a, int bx, i
     if (col < a.T) {
         for (int rr = 0; rr < RPT; ++rr) {
             const int r = part * RPT + rr;
-            lanczos_epilogue_value(a, i0 + r, col, sO[r * LDO + col_l], qp, pp, qq);
+            lanczos_epilogue_value(a, i0 + r, col, sO[r * LDO + col_l], qp, pp, qq, sOlo[r * LDO + col_l]);
         }
     }
     if (a.mode == kLanczos) {

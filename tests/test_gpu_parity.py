@@ -93,10 +93,10 @@ def _oracle(op, X, k, B, Q, J, nodes, tol=0.0, stop_rule="residual"):
                        stop_rule=stop_rule, nodes=nodes, lmin=k.noise, lmax=None)
 
 
-def fp32_tol(op, K, ref, run):
-    """1e-5, or 15 times the change that rounding K's entries to FP32 alone
-    makes to the oracle's result when that is larger (relerr.fp32_gate)."""
-    return fp32_gate(run, K, ref)
+def fp32_tol(op, K, ref, run, factor=15.0):
+    """1e-5, or `factor` times the change that rounding K's entries to FP32
+    alone makes to the oracle's result when that is larger (relerr.fp32_gate)."""
+    return fp32_gate(run, K, ref, factor=factor)
 
 
 @pytest.mark.parametrize("krylov", ["recurrence", "basis"])
@@ -114,8 +114,12 @@ def test_fp32_solve_matches_serial_oracle_at_equal_nodes_and_J(op, kind, n, d, t
     out, info = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), Q, 0.0,
                    max_iter=J, nodes=nodes, lmin=k.noise, krylov=krylov)
     assert info["iters"] == J and info["krylov"] == krylov
+    # The stored-basis form keeps the Lanczos p as a float pair (measured 6-9x
+    # the floor for K^{-1/2}b, against 9-11x with FP32 p, which the direction
+    # recurrence still uses): 12x and 15x.
     tol, floor = fp32_tol(op, K, ref, lambda Km: O.ciq_apply(O.dense_mvm(Km), B.astype(np.float64), Q, op,
-                                                             max_iter=J, nodes=nodes, lmin=k.noise)[0])
+                                                             max_iter=J, nodes=nodes, lmin=k.noise)[0],
+                          factor=12.0 if krylov == "basis" else 15.0)
     err = rel(out.cpu().numpy(), ref)
     assert err < tol, (err, tol, floor)
 
