@@ -133,6 +133,7 @@ struct Plan {
     int tc_max_split = 8;         // CTAs per row tile of the tensor-core MVM (batches: 1)
     int fault_inject = 0;         // ciq_options.fault_inject (testing the bounded-wait path)
     bool basis = false;           // stored-basis form (CIQ_KRYLOV_BASIS)
+    bool pair_p = false;          // a solve: keeps p as a float pair where the MVM runs on CUDA cores
     bool vjp = false;             // backward pass: T = 2 T_B columns [B | G], basis form
     int pc_rank = 0;              // pivoted-Cholesky preconditioner rank (0: none)
     int lr_rank = -1;             // low-rank correction -C C^T of the MVM (>= 0: on)
@@ -177,8 +178,8 @@ struct Plan {
         Ylo = a.take<R>((size_t)T * Npad);
         Bw = a.take<R>((size_t)T * Npad);
         D = basis ? nullptr : a.take<R>((size_t)2 * Q * T * Npad);
-        // FP32 CUDA-core basis solves keep p as a float pair.
-        plo = (basis && !tc && !stored && sizeof(R) == 4 && pc_rank <= 0 && lr_rank < 0)
+        // FP32 CUDA-core solves keep p as a float pair (both Krylov forms, batched too).
+        plo = (pair_p && !tc && !stored && sizeof(R) == 4 && pc_rank <= 0 && lr_rank < 0)
                   ? a.take<R>((size_t)T * Npad) : nullptr;
         rcoef = basis ? a.take<double>((size_t)jmax * Q * T * 4) : nullptr;
         gauss = basis ? a.take<double>((size_t)2 * T * 4) : nullptr;
@@ -297,6 +298,7 @@ Plan<R> make_plan(int64_t N, int d, int T, int Q, const ciq_options& o, bool pre
     choose_chunks(p.Npad, 1, &p.nchunks1, &p.rpc1);
     p.prepass = prepass;
     p.basis = allow_basis && use_basis(o, sizeof(R), p.Npad, T);
+    p.pair_p = allow_basis;
     p.layout(nullptr);
     return p;
 }
@@ -1100,6 +1102,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         if (o.batch_split_rows > 0 && plans.back().Npad / kTcBM >= o.batch_split_rows)
             plans.back().tc_max_split = o.batch_split;
         plans.back().tri_on = record_tri;
+        plans.back().pair_p = true;
         plans.back().layout(nullptr);
         offs[p] = off;
         off += round_up((int64_t)plans.back().bytes, kAlign);
@@ -1240,6 +1243,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                 m.V = par ? pl.QA : pl.QB;
                 m.qprev = par ? pl.QB : pl.QA;
                 m.beta = pl.beta + (size_t)par * T;
+                m.plo = pl.plo;
                 b.mvm[par] = m;
                 MvmArgs<float> r = a;
                 r.T = 1;

@@ -350,6 +350,8 @@ __device__ __forceinline__ void step_vectors(const KrylovState<R>& s, int j, int
         float4* y4 = reinterpret_cast<float4*>(y);
         float4* l4 = reinterpret_cast<float4*>(ylo);
         const float4* b4 = reinterpret_cast<const float4*>(b);
+        // With a float-pair p its trailing part joins before the scaling.
+        const float4* pl4 = s.plo ? reinterpret_cast<const float4*>(s.plo + col) : nullptr;
         const float4* dp4 = reinterpret_cast<const float4*>(d_prev);
         float4* do4 = reinterpret_cast<float4*>(d_old);
         const int64_t ds4 = dstride / 4;
@@ -363,6 +365,7 @@ __device__ __forceinline__ void step_vectors(const KrylovState<R>& s, int j, int
             const float4 yv4 = y4[i4];
             const float4 lv4 = l4[i4];
             const float4 bv4 = s.op == kOpSqrtIdentity ? b4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 plv = pl4 ? pl4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
             for (int q0 = 0; q0 < Q; q0 += QB) {
@@ -394,12 +397,13 @@ __device__ __forceinline__ void step_vectors(const KrylovState<R>& s, int j, int
             const float ya[4] = {yv4.x, yv4.y, yv4.z, yv4.w};
             const float la[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
             const float ba[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
+            const float pla[4] = {plv.x, plv.y, plv.z, plv.w};
             float pn[4], ys[4], yl[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 float t = fmaf(-(float)ahi, qa[e], pa[e]);
                 t = fmaf(-(float)alo, qa[e], t);
-                pn[e] = t * (float)invb;
+                pn[e] = (t + pla[e]) * (float)invb;
                 // y += acc as a (leading, trailing) pair (Knuth's 2Sum).
                 const float sum = ya[e] + acc[e];
                 const float bp = sum - ya[e];

@@ -114,9 +114,10 @@ def test_fp32_solve_matches_serial_oracle_at_equal_nodes_and_J(op, kind, n, d, t
     out, info = fn(torch.from_numpy(X).to(DEV), k, torch.from_numpy(B).to(DEV), Q, 0.0,
                    max_iter=J, nodes=nodes, lmin=k.noise, krylov=krylov)
     assert info["iters"] == J and info["krylov"] == krylov
-    # The stored-basis form keeps the Lanczos p as a float pair (measured 6-9x
-    # the floor for K^{-1/2}b, against 9-11x with FP32 p, which the direction
-    # recurrence still uses): 12x and 15x.
+    # Both forms keep the Lanczos p as a float pair (measured 6-10x the floor
+    # for K^{-1/2}b in either, against 9-11x with FP32 p); the recurrence's
+    # identity-form K^{1/2}b adds its FP32 direction updates (9-14x): 12x for
+    # the stored basis and 15x for the recurrence.
     tol, floor = fp32_tol(op, K, ref, lambda Km: O.ciq_apply(O.dense_mvm(Km), B.astype(np.float64), Q, op,
                                                              max_iter=J, nodes=nodes, lmin=k.noise)[0],
                           factor=12.0 if krylov == "basis" else 15.0)
