@@ -49,12 +49,16 @@ struct MvmArgs {
 // stores O + sigma^2 v; kLanczos forms p = O + sigma^2 v - beta q_prev (0 on
 // padded rows), writes it to pout (over q_prev when pout is null) and
 // accumulates q.p, p.p, q.q in FP64.
-template <typename R>
+// PAIR: the caller supplies the trailing part olo of its sum and honours
+// a.plo (the CUDA-core MVMs); without it the float-pair branch is not
+// compiled in (it would change the register allocation of the stored-K
+// kernels' main loops: measured 2x slower at T = 8).
+template <typename R, bool PAIR = false>
 __device__ __forceinline__ void lanczos_epilogue_value(const MvmArgs<R>& a, int64_t i, int col, R o,
                                                        double& qp, double& pp, double& qq, R olo = (R)0) {
     const int64_t idx = (int64_t)col * a.ldv + i;
     const R v = a.V[idx];
-    if (a.mode == kLanczos && a.plo) {
+    if (PAIR && a.mode == kLanczos && a.plo) {
         // o + olo is the MVM's sum as a pair; p = O + sigma^2 v - beta q_prev in FP64.
         const double pd = i < a.N ? (double)o + (double)olo + (double)a.noise * (double)v -
                                         a.beta[col] * (double)a.qprev[idx]

@@ -74,7 +74,7 @@ __device__ __forceinline__ void mvm_narrow_body(const MvmArgs<R>& a, int bx, int
         for (int w = 0; w < 8; ++w) od += (double)red[w][lane][c] + (double)redlo[w][lane][c];
         const R o = (R)od;
         double qp = 0, pp = 0, qq = 0;
-        lanczos_epilogue_value(a, i, col, o, qp, pp, qq, (R)(od - (double)o));
+        lanczos_epilogue_value<R, true>(a, i, col, o, qp, pp, qq, (R)(od - (double)o));
         if (a.mode == kLanczos) {
             qp = warp_sum(qp); pp = warp_sum(pp); qq = warp_sum(qq);
             if (lane == 0) {
@@ -177,7 +177,7 @@ __device__ __forceinline__ void mvm_wide_body(const MvmArgs<float>& a, int bx, i
     if (col < a.T) {
         for (int rr = 0; rr < RPT; ++rr) {
             const int r = part * RPT + rr;
-            lanczos_epilogue_value(a, i0 + r, col, sO[r * LDO + col_l], qp, pp, qq, sOlo[r * LDO + col_l]);
+            lanczos_epilogue_value<float, true>(a, i0 + r, col, sO[r * LDO + col_l], qp, pp, qq, sOlo[r * LDO + col_l]);
         }
     }
     if (a.mode == kLanczos) {

@@ -981,7 +981,7 @@ __host__ __device__ constexpr int st_chunk() {
 }
 template <int TP>
 __host__ __device__ constexpr int st_smem_bytes() {
-    return 1024 + kStKStages * kStKBytes + kStVStages * st_vstep_bytes<TP>() + 2 * TP * kTcBM * 4 + 512;
+    return 1024 + kStKStages * kStKBytes + kStVStages * st_vstep_bytes<TP>() + 512;
 }
 enum StBar {
     kSbKFull = 0,      // [3] tile of K landed
@@ -1007,8 +1007,7 @@ __global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant
     // The swizzled boxes need 1024-byte aligned stages (1024 bytes reserved).
     uint8_t* sK = st_smem + ((1024u - (tc::smem_u32(st_smem) & 1023u)) & 1023u);
     uint8_t* sV = sK + kStKStages * kStKBytes;
-    float* sR = reinterpret_cast<float*>(sV + kStVStages * VSTEP);   // running sum [2][TP][128]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sR + 2 * TP * kTcBM);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sV + kStVStages * VSTEP);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kSbCount);
     volatile int* serr = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -1020,7 +1019,6 @@ __global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant
     const int ntot = (int)(a.Npad / kStKN);
     const int st0 = (int)((int64_t)split * ntot / S);
     const int nt = (int)((int64_t)(split + 1) * ntot / S) - st0;   // steps of this CTA (>= 1)
-    const int nfold = (nt - 1) / C;
     constexpr uint32_t IDESC_O = tc::idesc_f16(kTcBM, TP, !HALF);
     constexpr uint32_t IDESC_O2 = tc::idesc_f16(kTcBM, 2 * TP, !HALF);
 
@@ -1046,6 +1044,11 @@ __global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t tO0 = tmem + kStNB * kStKN;            // O accumulator, 2 TP columns
+    // Exp warps: compensated running sum (leading, trailing FP32 parts) of
+    // the TP / 2 columns this thread folds, for its row, in registers.
+    float acc_h[TP / 2], acc_l[TP / 2];
+#pragma unroll
+    for (int i = 0; i < TP / 2; ++i) acc_h[i] = acc_l[i] = 0.f;
     auto uni = [&](bool b) { return __shfl_sync(0xffffffffu, (int)b, 0) != 0; };
 
     if (warp == 0) {
@@ -1167,13 +1170,12 @@ __global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant
             // At the start of a chunk, fold the previous chunk of O into the
             // running sum (half of the columns per warpgroup).
             if (t >= C && (t % C) == 0) {
-                const int c = t / C - 1;
                 const int te = t - 1;
                 const bool okc = tc::mbar_wait(&bars[kSbODone + te % kRing], (uint32_t)((te / kRing) & 1), kWaitLimit);
                 if (__shfl_sync(0xffffffffu, (int)(!okc || *serr), 0)) { *serr = 1; break; }
                 tc::fence_after_sync();
                 constexpr int HB = TP / 2 / 16;
-#pragma unroll 1
+#pragma unroll
                 for (int cb = 0; cb < HB; ++cb) {
                     const int col0 = g * (TP / 2) + 16 * cb;
                     uint32_t oa[16], ob[16];
@@ -1187,14 +1189,8 @@ __global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant
                     }
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
-                        float* rh = sR + (col0 + e) * kTcBM + r;
-                        float* rl = rh + TP * kTcBM;
-                        float h = c > 0 ? *rh : 0.f;
-                        float l = c > 0 ? *rl : 0.f;
-                        two_sum_into(h, l, __uint_as_float(oa[e]));
-                        two_sum_into(h, l, __uint_as_float(ob[e]));
-                        *rh = h;
-                        *rl = l;
+                        two_sum_into(acc_h[16 * cb + e], acc_l[16 * cb + e], __uint_as_float(oa[e]));
+                        two_sum_into(acc_h[16 * cb + e], acc_l[16 * cb + e], __uint_as_float(ob[e]));
                     }
                 }
             }
@@ -1212,7 +1208,7 @@ __global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant
         if (!ok) *serr = 1;
         tc::fence_after_sync();
         float* part = p.part + ((int64_t)tile * S + split) * TP * kTcBM;
-#pragma unroll 1
+#pragma unroll
         for (int cb = 0; cb < TP / 32; ++cb) {
             const int col0 = g * (TP / 2) + 16 * cb;
             uint32_t oa[16], ob[16];
@@ -1226,9 +1222,9 @@ __global__ void __launch_bounds__(384, 1) stored_tc_kernel(const __grid_constant
             for (int e = 0; e < 16; ++e) {
                 const int cl = col0 + e;
                 float h = 0.f, l = 0.f;
-                if (ok && nfold > 0) {
-                    h = sR[cl * kTcBM + r];
-                    l = sR[(TP + cl) * kTcBM + r];
+                if (ok) {
+                    h = acc_h[16 * cb + e];
+                    l = acc_l[16 * cb + e];
                 }
                 if (ok) {
                     two_sum_into(h, l, __uint_as_float(oa[e]));
