@@ -212,16 +212,16 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int* t
 
 // Block l rebuilds dynamic list l over the problems with list_items[l] > 0
 // whose columns have not all stopped (*all_done == 0).
-__global__ void __launch_bounds__(1024) rebuild_lists_kernel(const BatchProblem* probs, int P, DynLists lists,
-                                                             int* totals) {
+__global__ void __launch_bounds__(1024) rebuild_lists_kernel(const BatchProblem* probs, int P, const int* order,
+                                                             DynLists lists, int* totals) {
     __shared__ int warp_tot[32];
     const int l = blockIdx.x;
     const DevList L = lists.l[l];
     const int per = (P + 1023) / 1024;
     const int p0 = min(P, (int)threadIdx.x * per), p1 = min(P, p0 + per);
     int n = 0, items = 0;
-    for (int p = p0; p < p1; ++p) {
-        const BatchProblem& bp = probs[p];
+    for (int q = p0; q < p1; ++q) {
+        const BatchProblem& bp = probs[order[q]];
         const int c = bp.list_items[l];
         if (c <= 0 || *bp.ks.all_done) continue;
         items += c;
@@ -231,7 +231,8 @@ __global__ void __launch_bounds__(1024) rebuild_lists_kernel(const BatchProblem*
     int pos = block_exclusive_scan(n, warp_tot, &n_total);
     __syncthreads();
     int off = block_exclusive_scan(items, warp_tot, &item_total);
-    for (int p = p0; p < p1; ++p) {
+    for (int q = p0; q < p1; ++q) {
+        const int p = order[q];
         const BatchProblem& bp = probs[p];
         const int c = bp.list_items[l];
         if (c <= 0 || *bp.ks.all_done) continue;
@@ -335,9 +336,9 @@ cudaError_t launch_batched_summary(const BatchProblem* probs, int final_j, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_rebuild_lists(const BatchProblem* probs, int P, const DynLists& lists, int* totals,
-                                 cudaStream_t st) {
-    rebuild_lists_kernel<<<kBatchDynLists, 1024, 0, st>>>(probs, P, lists, totals);
+cudaError_t launch_rebuild_lists(const BatchProblem* probs, int P, const int* order, const DynLists& lists,
+                                 int* totals, cudaStream_t st) {
+    rebuild_lists_kernel<<<kBatchDynLists, 1024, 0, st>>>(probs, P, order, lists, totals);
     return cudaGetLastError();
 }
 

@@ -130,8 +130,9 @@ cudaError_t launch_batched_tc_finish(const BatchProblem* probs, int TP, int pari
 cudaError_t prepare_batched_tc_mvm(int TP, bool half);
 
 // Rebuild the kBatchDynLists main-loop lists over problems whose columns
-// have not all stopped; totals[l] = the new item total of list l.
-cudaError_t launch_rebuild_lists(const BatchProblem* probs, int P, const DynLists& lists, int* totals,
-                                 cudaStream_t st);
+// have not all stopped, in the order order[0..P) (a permutation of the
+// problems); totals[l] = the new item total of list l.
+cudaError_t launch_rebuild_lists(const BatchProblem* probs, int P, const int* order, const DynLists& lists,
+                                 int* totals, cudaStream_t st);
 
 }  // namespace ciq

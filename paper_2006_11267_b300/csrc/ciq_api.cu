@@ -1142,8 +1142,6 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         }
         b.list_items[kBatchClasses] = pl.nchunks * T;
         b.list_items[kListStepScalar] = T;
-        for (int l = 0; l < kBatchDynLists; ++l)
-            if (b.list_items[l] > 0) dyn[l].add(p, b.list_items[l]);
         if (given[p]) {
             given_one.add(p, 1);
         } else {
@@ -1157,6 +1155,19 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                 pre_mvm[b.cls].add(p, b.pre_tiles);
             }
         }
+    }
+    // The main-loop lists hold the problems longest first (decreasing padded
+    // N: a CTA of the tensor-core MVM walks Npad / 128 column steps), so the
+    // longest CTAs start in the first wave and short ones fill in behind them
+    // (longest-processing-time order); the list rebuilds keep that order.
+    // Each problem's arithmetic does not depend on it.
+    std::vector<int> order(P);
+    for (int p = 0; p < P; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return plans[a].Npad > plans[b].Npad; });
+    for (int q = 0; q < P; ++q) {
+        const int p = order[q];
+        for (int l = 0; l < kBatchDynLists; ++l)
+            if (hp[p].list_items[l] > 0) dyn[l].add(p, hp[p].list_items[l]);
     }
     // Item totals index blocks as int.
     {
@@ -1185,6 +1196,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
     const size_t tables = round_up((int64_t)(sizeof(BatchProblem) * P), kAlign) +
                           round_up((int64_t)(sizeof(int) * list_ints * all_lists.size()), kAlign) +
                           round_up((int64_t)(sizeof(int) * kBatchDynLists), kAlign) +
+                          round_up((int64_t)(sizeof(int) * P), kAlign) +
                           round_up((int64_t)(sizeof(double) * kSummaryStride * P), kAlign);
     char* base = nullptr;
     ciq_status rc = CIQ_OK;
@@ -1207,6 +1219,8 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         tb += round_up((int64_t)(sizeof(int) * list_ints * all_lists.size()), kAlign);
         int* totals_d = reinterpret_cast<int*>(tb);
         tb += round_up((int64_t)(sizeof(int) * kBatchDynLists), kAlign);
+        int* order_d = reinterpret_cast<int*>(tb);
+        tb += round_up((int64_t)(sizeof(int) * P), kAlign);
         double* packed_d = reinterpret_cast<double*>(tb);
         // Device lists: [np][ids P][prefix P + 1] each.
         std::vector<DevList> dl(all_lists.size());
@@ -1268,6 +1282,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
         }
         CIQ_TRY(cudaMemcpyAsync(probs_d, hp.data(), sizeof(BatchProblem) * P, cudaMemcpyHostToDevice, st));
         CIQ_TRY(cudaMemcpyAsync(lists_d, list_img.data(), sizeof(int) * list_img.size(), cudaMemcpyHostToDevice, st));
+        CIQ_TRY(cudaMemcpyAsync(order_d, order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
         auto setup = [&](int phase, const HostList& h) -> cudaError_t {
             if (h.total() == 0) return cudaSuccess;
             ++launches;
@@ -1360,7 +1375,7 @@ ciq_status solve_batched(const ciq_problem* probs, int P, int Q, double tol, con
                     launches += 2;
                 }
                 last_j = jb;
-                CIQ_TRY(launch_rebuild_lists(probs_d, P, dyn_d, totals_d, ls));
+                CIQ_TRY(launch_rebuild_lists(probs_d, P, order_d, dyn_d, totals_d, ls));
                 ++launches;
                 if (o.graph) {
                     cudaGraph_t g = nullptr;
