@@ -262,6 +262,18 @@ def device_peaks():
 MVM_TC_DRAM_BYTES = {"rbf_n50000_d6_t64_q12": 22.473e6 + 0.147e6}
 
 
+def headline_config(precision, world=1):
+    """The headline workload's configuration, the same object on both arms
+    (the GPU path and the oracle); what a run found (iterations, Krylov form,
+    bound reached) goes in the line's "run" object."""
+    W = WORKLOAD
+    return {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
+            "noise": W.noise, "T": W.t, "Q": W.q, "op": "sqrt", "tol": TOL, "stop_rule": "errbound",
+            "precision": precision, "lanczos_iters": LANCZOS_ITERS, "parallelism": f"replicas{world}",
+            "l2": "no flush: a step of the GPU arm streams > 40 GB through HBM (48 GiB stored basis, "
+                  "> 126 MB L2); the reference arm runs on the host"}
+
+
 def roofline_tc(W, t_launch_ms, dev, pk, sm_mhz=None):
     # One kernel MVM on tensor cores.  Algorithmic work per kernel entry:
     # 2T flops of the product with V plus 2(d+2) flops of the augmented
@@ -372,11 +384,8 @@ def run_reference(args):
             "unit": "RHS-solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
-                       "noise": W.noise, "T": W.t, "Q": Q, "op": "sqrt", "tol": TOL, "stop_rule": "errbound",
-                       "precision": "fp64", "krylov": "recurrence", "iterations": [J_WORKLOAD] * args.steps,
-                       "lanczos_iters": LANCZOS_ITERS, "parallelism": "replicas1",
-                       "l2": "host oracle (no device)"},
+            "config": headline_config(args.precision, world),
+            "run": {"arithmetic": "fp64 (the oracle)", "krylov": "recurrence", "iterations": [J_WORKLOAD] * args.steps},
             "cpu_baseline": {"value": value, "unit": "RHS-solves/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": f"per step: oracle kernel MVM on {rows} of {W.n} rows (scaled x{W.n / rows:.2f}) "
                                        f"+ one full-size oracle msMINRES vector step; x{LANCZOS_ITERS + J_WORKLOAD} iterations"},
@@ -514,12 +523,9 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else f"{args.precision}x2-split tiles, f32 vectors, f64 scalars",
                 "data": "synthetic",
-                "config": {"workload": W.name, "N": W.n, "d": W.d, "kernel": W.kernel, "lengthscale": W.lengthscale,
-                           "noise": W.noise, "T": W.t, "Q": W.q, "op": "sqrt", "tol": TOL,
-                           "stop_rule": "errbound", "precision": args.precision, "krylov": infos[0].get("krylov"), "iterations": it,
-                           "lanczos_iters": LANCZOS_ITERS, "errbound_max": max(i["errbound_max"] for i in infos),
-                           "parallelism": f"replicas{world}",
-                           "l2": "no flush: every step streams > 40 GB through HBM (48 GiB stored basis, > 126 MB L2)"},
+                "config": headline_config(args.precision, world),
+                "run": {"krylov": infos[0].get("krylov"), "iterations": it,
+                        "errbound_max": max(i["errbound_max"] for i in infos)},
                 "roofline": roof,
                 "kernels": {"mvm_ms_per_launch": t_mvm, "recurrence_ms_per_launch": t_rec,
                             "mvm_share": pinfo["t_mvm_ms"] / max(pinfo["t_total_ms"], 1e-9),
