@@ -105,6 +105,9 @@ def parse():
                     help="run the headline solve on the first N points only (for profiling captures)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="N",
                     help="time only the kernel MVM on the first N points of the workload (for profiling)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="batched512: only the batched calls, without CUDA graphs (a plain launch sequence "
+                         "for profiling captures)")
     return ap.parse_args()
 
 
@@ -560,6 +563,8 @@ def run_batched(args):
         pr["out"] = torch.empty_like(pr["B"])
     opts = dict(max_iter=BATCH_MAX_ITER, lanczos_iters=LANCZOS_ITERS, check_every=8)
     bopts = dict(opts, precision=args.precision)
+    if args.batch_only:
+        bopts["graph"] = 0
     stream = torch.cuda.current_stream()
 
     def step():
@@ -583,6 +588,11 @@ def run_batched(args):
     elapsed_ms = e0.elapsed_time(e1)
     rhs = BATCH_COUNT * BATCH_T
     value = rhs * args.steps / (elapsed_ms * 1e-3)
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps({"batch_only": True, "ms_per_batch": elapsed_ms / args.steps,
+                              "launches_per_batch": launches // max(args.steps, 1)}), flush=True)
+        return 0
     # Plain FP32 GPU path: the same problems, one ciq_sqrt call each.
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
