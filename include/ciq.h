@@ -118,7 +118,10 @@ typedef enum {
  * form's bound is multiplied by lmax_used) or times the Gauss-quadrature lower
  * bound of ||K^{-1/2}b|| from T_j (inverse root), instead of tol times the
  * running estimate's norm; the bound is then <= tol ||a_j|| as well.  AUTO: BASIS for FP32 solves whose basis takes at
- * most a quarter of the device memory, else RECURRENCE. */
+ * most a quarter of the device memory, else RECURRENCE.  In either form an FP32
+ * solve whose MVM runs on CUDA cores (batched problems included) forms the Lanczos
+ * p = O + sigma^2 v - beta q_{j-1} in FP64 from the MVM's compensated sum and keeps
+ * it as a float pair (T Npad more floats of workspace); q_{j+1} is rounded once. */
 typedef enum {
     CIQ_KRYLOV_AUTO = 0,
     CIQ_KRYLOV_RECURRENCE = 1,
