@@ -2,7 +2,8 @@
 sigma^2 = 1e-2, d = 4): K^{-1/2}B with Q = 15 through the plain FP32 path and
 the FP16 / BF16 hi/lo-split tensor-core tiles, each against the FP64
 eigendecomposition oracle on a 4096-point subsample, and the full-size
-tensor-core MVMs against the FP32 MVM on sampled rows.
+MVMs of every mode against the FP32 MVM and against the FP64 oracle on
+sampled rows.
 
 Tolerances come from the arithmetic of each mode:
   * FP32 and FP16 split: the solve error is dominated by the stop rule
@@ -89,3 +90,35 @@ def test_full_size_tensor_core_mvm_against_fp32_mvm():
     bound = 2.0 ** -10 * np.linalg.norm(absref, axis=1) / np.linalg.norm(r64, axis=1) + 1e-5
     err = np.linalg.norm(out - r64, axis=1) / np.linalg.norm(r64, axis=1)
     assert np.all(err < bound), (err.max(), bound.min())
+
+
+def test_full_size_mvm_each_precision_against_oracle_sampled_rows():
+    # The 200,000-point MVM with T = 256 (the sweep's launch shape: four
+    # 64-column groups), each mode against the FP64 oracle on sampled rows
+    # (the first, last and a middle row tile's rows), per column of the
+    # sampled block.  Bounds: the measured full-size errors against the FP32
+    # MVM (FP16 4.2e-6, BF16 9.5e-5) with the FP32 MVM's own error on top;
+    # TF32 within its rounding bound 2^-10 ||K|V|||/||KV|| (rows sampled).
+    n, t = W.n, 256
+    Xf = ci.points(W.seed, n, W.d).astype(np.float32)
+    Vf = ci.rhs(W.seed + 2, n, t).astype(np.float32)
+    X = torch.from_numpy(Xf).to(DEV)
+    V = torch.from_numpy(Vf).to(DEV)
+    k = P.Kernel(W.kernel, W.lengthscale, W.outputscale, W.noise)
+    rows = np.concatenate([np.arange(0, 64), np.arange(n - 64, n), np.arange(100000, 100128)])
+    Kr = kernels.kernel_matrix(Xf[rows].astype(np.float64), Xf.astype(np.float64), W.kernel, W.lengthscale,
+                               W.outputscale)
+    V64 = Vf.T.astype(np.float64)
+    ref = (Kr @ V64 + W.noise * V64[rows]).T                  # (t, rows)
+    absref = (Kr @ np.abs(V64) + W.noise * np.abs(V64[rows])).T
+    def colerr(out):
+        o = out.cpu().numpy()[:, rows].astype(np.float64)
+        return np.linalg.norm(o - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    e32 = colerr(P.ciq_kernel_mvm(X, k, V, precision="fp32"))
+    assert e32.max() < 2e-6, e32.max()
+    for prec, tol in (("fp16", 2e-5), ("bf16", 2e-4)):
+        e = colerr(P.ciq_kernel_mvm(X, k, V, precision=prec))
+        assert e.max() < tol, (prec, e.max())
+    bound = 2.0 ** -10 * np.linalg.norm(absref, axis=1) / np.linalg.norm(ref, axis=1) + 1e-5
+    e = colerr(P.ciq_kernel_mvm(X, k, V, precision="tf32"))
+    assert np.all(e < bound), (e.max(), bound.min())
