@@ -148,3 +148,42 @@ def test_preconditioned_draws_need_fewer_iterations():
                                    **kw)
     assert i0["status"] == 0 and i1["status"] == 0 and i1["precond_rank"] == 100
     assert i1["iters"] < 0.9 * i0["iters"], (i1["iters"], i0["iters"])
+
+
+def test_full_size_posterior_draws_on_sampled_candidates():
+    # The bench's posterior workload at full size and in its launch shape
+    # (50,000 candidates, 256 observations, Matern-5/2 ARD, 64 draws, error
+    # bound 1e-3, FP16 split), checked where the oracle can compute outputs
+    # one by one: the posterior mean (eps = 0) on sampled candidates, and the
+    # root applied twice, R (R eps) = COV* eps, on the same candidates (rows
+    # of COV* from the oracle's kernels and the exact inner solve).
+    import bench
+    from oracle import kernels as OK
+
+    c = bench.POSTERIOR
+    Xtr, y, Xc, eps = bench.posterior_inputs(c["n_cand"])
+    ls = np.array(c["ls"])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (dev(Xtr), dev(y), dev(Xc), c["kind"], ls, c["s"], c["noise"], c["jitter"], c["mean"])
+    kw = dict(stop_rule="errbound", max_iter=4000, precision="fp16")
+    zero = np.zeros((1, c["n_cand"]), np.float32)
+    mu_d, _ = P.ciq_posterior_sample(*args, dev(zero), c["q"], 1e-3, **kw)
+    f, info = P.ciq_posterior_sample(*args, dev(eps), c["q"], 1e-3, **kw)
+    assert info["status"] == 0
+    g = (f - mu_d).cpu().numpy()                                   # R eps
+    f2, _ = P.ciq_posterior_sample(*args, dev(g), c["q"], 1e-3, **kw)
+    h = (f2 - mu_d).cpu().numpy().astype(np.float64)               # R (R eps)
+    n = c["n_cand"]
+    rows = np.concatenate([np.arange(0, 64), np.arange(n - 64, n), np.arange(25000, 25128)])
+    X64, Xtr64, E = Xc.astype(np.float64), Xtr.astype(np.float64), eps.astype(np.float64).T
+    kern = lambda A, B: PO.kernel_ard(A, B, c["kind"], ls, c["s"])
+    M = kern(Xtr64, Xtr64) + c["noise"] * np.eye(Xtr.shape[0])
+    Kr = kern(X64[rows], Xtr64)                                    # K*X on the sampled rows
+    mu_rows = c["mean"] + Kr @ np.linalg.solve(M, y.astype(np.float64) - c["mean"])
+    assert np.linalg.norm(mu_d.cpu().numpy()[0, rows] - mu_rows) / np.linalg.norm(mu_rows) < 1e-5
+    KxE = kern(Xtr64, X64) @ E                                     # K_X* eps, all candidates
+    cov_e = kern(X64[rows], X64) @ E - Kr @ np.linalg.solve(M, KxE) + c["jitter"] * E[rows]
+    err = np.linalg.norm(h[:, rows] - cov_e.T, axis=1) / np.linalg.norm(cov_e.T, axis=1)
+    # Two applications of a root, each stopped at the 1e-3 bound: to first
+    # order their relative errors add (measured 4.2e-4, median 3.4e-4).
+    assert err.max() < 2e-3, err.max()
