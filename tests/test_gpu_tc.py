@@ -141,6 +141,16 @@ def test_tc_fp16_full_size_square_root_property():
     KB = P.ciq_kernel_mvm(X, k, B[:4].contiguous(), precision="fp32")
     e = (torch.linalg.norm(A2 - KB, dim=1) / torch.linalg.norm(KB, dim=1)).cpu().numpy()
     assert e.max() < 3e-4
+    # The same property against the FP64 oracle's K b on sampled rows (first,
+    # middle and last row tiles), computed entry by entry on the host.
+    rows = np.concatenate([np.arange(0, 64), np.arange(20000, 20128), np.arange(W.n - 64, W.n)])
+    Xh = X.cpu().numpy().astype(np.float64)
+    Bh = B[:4].cpu().numpy().astype(np.float64)
+    Kr = kernels.kernel_matrix(Xh[rows], Xh, W.kernel, W.lengthscale, W.outputscale)
+    ref = Kr @ Bh.T + W.noise * Bh.T[rows]                     # (rows, 4)
+    got = A2.cpu().numpy().astype(np.float64)[:, rows].T
+    e = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert e.max() < 3e-4, e.max()
 
 
 def test_tc_split_k_changes_only_the_summation_order():
