@@ -341,11 +341,13 @@ constexpr int kRing = 8;                         // completion barriers per kind
 //     residual 1e-4: 12 steps, 108 columns left at the iteration cap; 8
 //     steps, 77 and 4 % faster; 6, 67 and 4 % faster again; 4 steps, 34 at
 //     the same speed as 6.  The 8-column K^{-1/2} solve: 2833, 2704, 2650 and
-//     2581 iterations, 2249, 2223, 2235 and 2306 ms.  Batched and single
-//     solves share the interval (their results are equal bit for bit).
+//     2581 iterations, 2249, 2223, 2235 and 2306 ms.  With the running sum in
+//     registers: 3 steps, 23 columns at the cap and 0.6 % faster than 4; 2
+//     steps, 17 and 0.8 % slower than 4.  Batched and single solves share the
+//     interval (their results are equal bit for bit).
 template <int TP>
 __host__ __device__ constexpr int tc_chunk() {
-    return TP <= 32 ? 4 : 12;
+    return TP <= 32 ? 3 : 12;
 }
 
 // TMEM: three S buffers of 128 columns, each overwritten by its P in place,
@@ -974,7 +976,7 @@ template <int TP>
 __host__ __device__ constexpr int st_vstep_bytes() {
     return 2 * TP * 128;                           // one 64-row tile of split V
 }
-// Steps per fold: the same 1,536 (TP = 64) or 512 columns as the on-the-fly kernel.
+// Steps per fold: 1,536 columns (TP = 64), as in the on-the-fly kernel, or 512 (TP <= 32).
 template <int TP>
 __host__ __device__ constexpr int st_chunk() {
     return TP <= 32 ? 8 : 24;
