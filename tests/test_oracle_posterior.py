@@ -92,3 +92,17 @@ def test_preconditioned_draws_use_a_root_of_the_posterior_covariance():
     assert np.abs(R @ R.T - cov).max() < 1e-10 * np.abs(cov).max()
     assert np.abs(R - R.T).max() > 1e-3 * np.abs(R).max()
     assert np.array_equal(PO.preconditioned_draws(mu, cov, jitter, 12, np.zeros((1, n)))[0], mu)
+
+
+def test_full_rank_preconditioned_draws_are_the_principal_root_draws():
+    # At full rank the pivoted Cholesky factor reproduces COV* - jitter I, so
+    # P = COV*, A = P^{-1/2} COV* P^{-1/2} = I and R = P^{1/2} = COV*^{1/2}:
+    # the preconditioned draw is the principal-root draw (O1).
+    Xtr, y, Xc = _data()
+    jitter = 1e-2
+    mu, cov = PO.posterior(Xtr, y, Xc, "rbf", LS, 0.8, 1e-2, jitter, -0.3)
+    n = len(mu)
+    eps = ci.rhs(7, n, 3)
+    got = PO.preconditioned_draws(mu, cov, jitter, n, eps)
+    want = PO.thompson_draws(mu, cov, eps)
+    assert np.abs(got - want).max() < 1e-8 * np.abs(want).max()
