@@ -334,7 +334,9 @@ typedef struct {
  * ciq_invsqrt with the same options, so each output equals the
  * single-problem call's bit for bit (tensor-core batches run one CTA per
  * row tile unless opt->tc_split says otherwise, so the single call is
- * compared with the same tc_split).  1 <= P <= CIQ_MAX_BATCH.
+ * compared with the same tc_split).  The work lists hold the problems in
+ * decreasing padded N (longest CTAs first); order and batch composition
+ * change only the schedule, never a result.  1 <= P <= CIQ_MAX_BATCH.
  * CIQ_ERR_UNSUPPORTED if opt->mvm is CIQ_MVM_STORED, opt->sqrt_form is not
  * CIQ_SQRT_IDENTITY, quad_w, quad_t, lanczos_start or workspace is set, or a
  * tensor-core batch breaks its limits.  The device workspace (the sum of
